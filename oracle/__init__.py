@@ -1,0 +1,176 @@
+"""Python access to the FP64 Lloyd k-means oracle (``kmref.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the benchmark's CPU-baseline leg, never by the library. It shares no code
+with the GPU path; the only thing both sides take from the same place is the
+seeded input generator (``synth``).
+
+Every function here marshals numpy arrays into the C oracle and back; the
+arithmetic is all in ``kmref.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kmref.c")
+_LIB = os.path.join(_HERE, "libkmref.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def compile_oracle(src: str, out: str) -> str:
+    """gcc -O2 -fopenmp build of an oracle source file into a shared library."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", src, "-o",
+                           tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        compile_oracle(_SRC, _LIB)
+    return _LIB
+
+
+def bind(path: str):
+    """Load an oracle shared library and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+    lib.kmref_set_threads.restype = ctypes.c_int
+    lib.kmref_set_threads.argtypes = [ctypes.c_int]
+    lib.kmref_assign.restype = ctypes.c_int
+    lib.kmref_assign.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, vp]
+    lib.kmref_update.restype = ctypes.c_int
+    lib.kmref_update.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, vp]
+    lib.kmref_objective.restype = dbl
+    lib.kmref_objective.argtypes = [vp, i64, i32, vp, i32, vp]
+    lib.kmref_step.restype = ctypes.c_int
+    lib.kmref_step.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, vp, vp]
+    lib.kmref_run.restype = ctypes.c_int
+    lib.kmref_run.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, i32, dbl, vp, vp]
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = bind(build())
+    return _lib
+
+
+def _f32(X):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1)
+    return X
+
+
+def _f64(C, d):
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    return C.reshape(-1, d)
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None else None
+
+
+class Oracle:
+    """Thin marshalling layer over one loaded oracle library (the real one or a test mutant)."""
+
+    def __init__(self, lib=None):
+        self.lib = lib if lib is not None else _load()
+
+    def set_threads(self, n: int = 0) -> int:
+        return int(self.lib.kmref_set_threads(n))
+
+    def assign(self, X, C):
+        """(assign int32[n], dmin f64[n], gap f64[n], second int32[n])."""
+        X = _f32(X)
+        n, d = X.shape
+        C = _f64(C, d)
+        k = C.shape[0]
+        a = np.empty(n, np.int32)
+        dmin = np.empty(n, np.float64)
+        gap = np.empty(n, np.float64)
+        second = np.empty(n, np.int32)
+        rc = self.lib.kmref_assign(_ptr(X), n, d, _ptr(C), k, _ptr(a), _ptr(dmin), _ptr(gap),
+                                   _ptr(second))
+        if rc:
+            raise ValueError(f"kmref_assign failed ({rc})")
+        return a, dmin, gap, second
+
+    def update(self, X, assign, Cprev):
+        """(sums f64[k,d], counts int64[k], Cnew f64[k,d]) from a given assignment."""
+        X = _f32(X)
+        n, d = X.shape
+        Cprev = _f64(Cprev, d)
+        k = Cprev.shape[0]
+        a = np.ascontiguousarray(assign, dtype=np.int32)
+        sums = np.empty((k, d), np.float64)
+        counts = np.empty(k, np.int64)
+        Cnew = np.empty((k, d), np.float64)
+        rc = self.lib.kmref_update(_ptr(X), n, d, _ptr(a), k, _ptr(Cprev), _ptr(sums),
+                                   _ptr(counts), _ptr(Cnew))
+        if rc:
+            raise ValueError(f"kmref_update failed ({rc})")
+        return sums, counts, Cnew
+
+    def objective(self, X, C, assign) -> float:
+        X = _f32(X)
+        n, d = X.shape
+        C = _f64(C, d)
+        a = np.ascontiguousarray(assign, dtype=np.int32)
+        return float(self.lib.kmref_objective(_ptr(X), n, d, _ptr(C), C.shape[0], _ptr(a)))
+
+    def step(self, X, C):
+        """One Lloyd step: dict(assign, sums, counts, C (new), objective, shift)."""
+        X = _f32(X)
+        n, d = X.shape
+        C = _f64(C, d).copy()
+        k = C.shape[0]
+        a = np.empty(n, np.int32)
+        sums = np.empty((k, d), np.float64)
+        counts = np.empty(k, np.int64)
+        J = ctypes.c_double()
+        sh = ctypes.c_double()
+        rc = self.lib.kmref_step(_ptr(X), n, d, _ptr(C), k, _ptr(a), _ptr(sums), _ptr(counts),
+                                 ctypes.byref(J), ctypes.byref(sh))
+        if rc:
+            raise ValueError(f"kmref_step failed ({rc})")
+        return dict(assign=a, sums=sums, counts=counts, C=C, objective=J.value, shift=sh.value)
+
+    def run(self, X, C, iters: int, tol: float = 0.0):
+        """Up to ``iters`` steps: dict(assign, sums, counts, C, objectives, iters_done)."""
+        X = _f32(X)
+        n, d = X.shape
+        C = _f64(C, d).copy()
+        k = C.shape[0]
+        a = np.empty(n, np.int32)
+        sums = np.empty((k, d), np.float64)
+        counts = np.empty(k, np.int64)
+        hist = np.zeros(max(iters, 1), np.float64)
+        done = ctypes.c_int32()
+        rc = self.lib.kmref_run(_ptr(X), n, d, _ptr(C), k, _ptr(a), _ptr(sums), _ptr(counts),
+                                iters, tol, _ptr(hist), ctypes.byref(done))
+        if rc:
+            raise ValueError(f"kmref_run failed ({rc})")
+        return dict(assign=a, sums=sums, counts=counts, C=C, objectives=hist[: done.value],
+                    iters_done=done.value)
+
+
+_default = None
+
+
+def oracle() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle()
+    return _default

@@ -1,0 +1,204 @@
+/*
+ * kmref -- plain FP64 CPU oracle of one Lloyd k-means iteration.
+ *
+ * TEST INFRASTRUCTURE ONLY. It exists so that tests (and the benchmark's CPU
+ * baseline leg) can check the GPU library against an obviously correct
+ * reference. No product code path may link, load or call it, and it shares no
+ * code, header, helper or constant with the GPU library.
+ *
+ * What it computes is the textbook definition of a Lloyd iteration
+ * (S. P. Lloyd, "Least squares quantization in PCM", IEEE Trans. IT 28(2), 1982),
+ * built from the paper's loop patterns:
+ *   - the assignment is a collect over the point range whose body runs once per
+ *     index in no set order (DeliteOpLoop with a DeliteCollectElem, Sec. 2.4),
+ *     with the distance of Sec. 3.4 (dist = norm(v1 - v2), the norm being the
+ *     square root of the summed squares). The square root is monotone, so the
+ *     argmin is taken over squared distances and never rounds two distinct
+ *     distances into a false tie;
+ *   - sums and counts are a keyed reduce over the same range (DeliteReduceElem,
+ *     Sec. 2.4); fused or not (Sec. 3.5) the result is the same, so the oracle
+ *     runs them as separate plain loops;
+ *   - the new centroid is the member mean, avg = sum / length (the VectorOpsExp
+ *     listing of Sec. 2.1).
+ * Everything is FP64. Inputs X are FP32 and promote exactly; C is FP64.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - metric: squared Euclidean distance (Lloyd); the paper's only generated
+ *     distance loop (the SPADE example of Sec. 4.1) is L1 and belongs to SPADE;
+ *   - ties: the lowest centroid index wins (strict < scan from j = 0);
+ *   - empty cluster: keeps its previous centroid, sums = 0, counts = 0;
+ *   - objective of a step: J(a^t, C^t) = sum_i D(i, a_i) with the centroids
+ *     used for the assignment;
+ *   - stop rule of a run with tol > 0: after the first step whose assignment
+ *     equals the previous step's, or whose largest centroid shift is <= tol.
+ */
+#include <float.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by the point loops (0 = OpenMP default). Returns the count in effect. */
+int kmref_set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  return omp_get_max_threads();
+#else
+  (void)nthreads;
+  return 1;
+#endif
+}
+
+static int bad_args(const float* X, int64_t n, int32_t d, const void* C, int32_t k) {
+  return !X || !C || n < 1 || d < 1 || k < 1 || (int64_t)k > n;
+}
+
+/* Squared Euclidean distance, direct differences, summed in index order (Sec. 3.4). */
+static double sqdist(const float* x, const double* c, int32_t d) {
+  double s = 0.0;
+  for (int32_t t = 0; t < d; ++t) {
+    double diff = (double)x[t] - c[t];
+    s += diff * diff;
+  }
+  return s;
+}
+
+/*
+ * Assignment step. For each point i:
+ *   D_ij = sum_t (x_it - c_jt)^2,  a_i = min{ j : D_ij <= D_ij' for all j' }.
+ * Optional outputs (NULL to skip): dmin[i] = D_{i,a_i}; second[i] = the index
+ * of the second-smallest distance (lowest index among equals, excluding a_i;
+ * -1 when k = 1); gap[i] = (D_(2) - D_(1)) / max(D_(2), DBL_MIN), +inf when k = 1.
+ */
+int kmref_assign(const float* X, int64_t n, int32_t d, const double* C, int32_t k,
+                 int32_t* assign, double* dmin, double* gap, int32_t* second) {
+  if (bad_args(X, n, d, C, k) || !assign) return -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    const float* x = X + i * (int64_t)d;
+    double b1 = HUGE_VAL, b2 = HUGE_VAL;
+    int32_t j1 = -1, j2 = -1;
+    for (int32_t j = 0; j < k; ++j) {
+      double D = sqdist(x, C + (int64_t)j * d, d);
+      if (D < b1) {
+        b2 = b1; j2 = j1;
+        b1 = D; j1 = j;
+      } else if (D < b2) {
+        b2 = D; j2 = j;
+      }
+    }
+    assign[i] = j1;
+    if (dmin) dmin[i] = b1;
+    if (second) second[i] = j2;
+    if (gap) gap[i] = (k == 1) ? HUGE_VAL : (b2 - b1) / (b2 > DBL_MIN ? b2 : DBL_MIN);
+  }
+  return 0;
+}
+
+/*
+ * Update step from a given assignment: counts_j = |{i : a_i = j}|,
+ * sums_j = sum_{a_i = j} x_i (index order), Cnew_j = sums_j / counts_j, or
+ * Cprev_j when counts_j = 0. sums is k*d, counts is k, Cnew is k*d
+ * (Cnew may alias Cprev).
+ */
+int kmref_update(const float* X, int64_t n, int32_t d, const int32_t* assign, int32_t k,
+                 const double* Cprev, double* sums, int64_t* counts, double* Cnew) {
+  if (!X || !assign || !Cprev || !sums || !counts || !Cnew || n < 1 || d < 1 || k < 1) return -1;
+  memset(sums, 0, sizeof(double) * (size_t)k * (size_t)d);
+  memset(counts, 0, sizeof(int64_t) * (size_t)k);
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t j = assign[i];
+    if (j < 0 || j >= k) return -2;
+    counts[j] += 1;
+    double* s = sums + (int64_t)j * d;
+    const float* x = X + i * (int64_t)d;
+    for (int32_t t = 0; t < d; ++t) s[t] += (double)x[t];
+  }
+  for (int32_t j = 0; j < k; ++j) {
+    double* c = Cnew + (int64_t)j * d;
+    const double* cp = Cprev + (int64_t)j * d;
+    const double* s = sums + (int64_t)j * d;
+    for (int32_t t = 0; t < d; ++t) c[t] = counts[j] > 0 ? s[t] / (double)counts[j] : cp[t];
+  }
+  return 0;
+}
+
+/* Objective J = sum_i D(i, a_i) for the given centroids and assignment. */
+double kmref_objective(const float* X, int64_t n, int32_t d, const double* C, int32_t k,
+                       const int32_t* assign) {
+  if (bad_args(X, n, d, C, k) || !assign) return NAN;
+  double J = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t j = assign[i];
+    if (j < 0 || j >= k) return NAN;
+    J += sqdist(X + i * (int64_t)d, C + (int64_t)j * d, d);
+  }
+  return J;
+}
+
+/* Largest centroid shift max_j ||a_j - b_j||_2. */
+static double max_shift(const double* a, const double* b, int32_t k, int32_t d) {
+  double m = 0.0;
+  for (int32_t j = 0; j < k; ++j) {
+    double s = 0.0;
+    for (int32_t t = 0; t < d; ++t) {
+      double e = a[(int64_t)j * d + t] - b[(int64_t)j * d + t];
+      s += e * e;
+    }
+    if (sqrt(s) > m) m = sqrt(s);
+  }
+  return m;
+}
+
+/*
+ * One Lloyd step: assignment with C, then update. C (k*d, FP64) is replaced by
+ * the new centroids. objective (optional) receives J(a, C_old); shift
+ * (optional) receives the largest centroid shift.
+ */
+int kmref_step(const float* X, int64_t n, int32_t d, double* C, int32_t k, int32_t* assign,
+               double* sums, int64_t* counts, double* objective, double* shift) {
+  if (bad_args(X, n, d, C, k) || !assign || !sums || !counts) return -1;
+  double* Cold = (double*)malloc(sizeof(double) * (size_t)k * (size_t)d);
+  if (!Cold) return -3;
+  memcpy(Cold, C, sizeof(double) * (size_t)k * (size_t)d);
+  int rc = kmref_assign(X, n, d, Cold, k, assign, NULL, NULL, NULL);
+  if (rc == 0) rc = kmref_update(X, n, d, assign, k, Cold, sums, counts, C);
+  if (rc == 0 && objective) *objective = kmref_objective(X, n, d, Cold, k, assign);
+  if (rc == 0 && shift) *shift = max_shift(C, Cold, k, d);
+  free(Cold);
+  return rc;
+}
+
+/*
+ * Up to `iters` Lloyd steps from C. tol <= 0: exactly `iters` steps. tol > 0:
+ * stop after the first step whose assignment equals the previous step's or
+ * whose largest centroid shift is <= tol. obj_hist (optional, length iters)
+ * receives J of each step; *iters_done (optional) the number of steps run.
+ */
+int kmref_run(const float* X, int64_t n, int32_t d, double* C, int32_t k, int32_t* assign,
+              double* sums, int64_t* counts, int32_t iters, double tol, double* obj_hist,
+              int32_t* iters_done) {
+  if (bad_args(X, n, d, C, k) || !assign || !sums || !counts || iters < 0) return -1;
+  int32_t* prev = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!prev) return -3;
+  int32_t done = 0;
+  int rc = 0;
+  for (int32_t t = 0; t < iters; ++t) {
+    if (t > 0) memcpy(prev, assign, sizeof(int32_t) * (size_t)n);
+    double J = 0.0, shift = 0.0;
+    rc = kmref_step(X, n, d, C, k, assign, sums, counts, &J, &shift);
+    if (rc) break;
+    if (obj_hist) obj_hist[t] = J;
+    done = t + 1;
+    if (tol > 0.0) {
+      int same = t > 0 && memcmp(prev, assign, sizeof(int32_t) * (size_t)n) == 0;
+      if (same || shift <= tol) break;
+    }
+  }
+  if (iters_done) *iters_done = done;
+  free(prev);
+  return rc;
+}
