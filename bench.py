@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Lloyd k-means benchmark: prints ONE JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step is one ``kmeans_run`` call: every Lloyd iteration of the workload (20 for
+the default 1M x 64 x 256 FP32 workload) as one graph-captured sequence of the
+library's kernels, on inputs already resident in HBM. ``value`` is Lloyd
+iterations per second over all ranks; the distance TFLOP/s (2nkd per iteration)
+is reported beside it. ``e2e`` times the same runs through ``kmeans_run_host``
+from pinned host buffers, copies included.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step), the one other place this script
+runs oracle code; so does the ``cpu_baseline`` leg of the default arm.
+
+Multi-GPU (torchrun): every rank runs its own replica of the workload (the step
+needs no exchange between independent problems); value = all ranks' iterations /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+from synth import WORKLOADS  # noqa: E402
+
+METRIC = "Lloyd iter/s + distance TFLOP/s: FP32 vs BF16/FP8+recheck, exact assignments"
+DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
+STAGE_KERNELS = ("prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
+# Source file of each stage's kernel (a change to it voids a stored ncu traffic figure).
+KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu"}}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 (default: the workload's first)")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- clocks
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs (read-only)."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- peaks / profiles
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_simt_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FFMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def kernel_source_sha(stage: str, precision: str) -> str | None:
+    src = KERNEL_SOURCES.get(stage, {}).get(precision)
+    if not src:
+        return None
+    with open(os.path.join(ROOT, "paper_1109_0778_b300", "csrc", src), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def stored_traffic(stage: str, precision: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_{precision}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"^traffic_bytes_per_launch:\s*([0-9.eE+]+)", text, re.M)
+    s = re.search(r"^source_sha256_16:\s*([0-9a-f]+)", text, re.M)
+    if not m or not s or s.group(1) != kernel_source_sha(stage, precision):
+        return None
+    return float(m.group(1))
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+
+def oracle_sample_rate(w, target_s: float, X=None):
+    """Lloyd iterations/s of the FP64 oracle on the host cores, extrapolated linearly in n from a
+    bounded row sample (full centroid set)."""
+    import oracle
+
+    orc = oracle.oracle()
+    cores = orc.set_threads(0)
+    rows = min(w.n, 1 << 18)
+    if X is None:
+        X, C0 = synth.workload_data(w, rows=max(rows, w.k))
+        X = X[:rows]
+    else:
+        X, C0 = X[:rows], X[: w.k].copy()
+    C = C0.astype(np.float64)
+    t0 = time.perf_counter()
+    orc.step(X[: min(rows, 4096)], C)  # calibrate on a few rows
+    t_small = time.perf_counter() - t0
+    per_row = max(t_small / min(rows, 4096), 1e-9)
+    rows = int(min(rows, max(4096, target_s / per_row)))
+    Xs = np.ascontiguousarray(X[:rows])
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        orc.step(Xs, C)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or steps >= 50:
+            break
+    rate = steps / el * rows / w.n
+    return rate, cores, (f"{steps} oracle Lloyd steps on the first {rows} of {w.n} points with the full "
+                         f"k={w.k} centroid set, {el:.1f} s; iter/s extrapolated linearly in n")
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.workload]
+    import oracle
+
+    orc = oracle.oracle()
+    cores = orc.set_threads(0)
+    rows = min(w.n, 1 << 16)
+    X, C0 = synth.workload_data(w, rows=max(rows, w.k))
+    Xs = np.ascontiguousarray(X[:rows])
+    C = C0.astype(np.float64)
+    for _ in range(args.warmup):
+        orc.step(Xs, C)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step(Xs, C)
+    el = time.perf_counter() - t0
+    value = args.steps * rows / w.n / el
+    sample = (f"each step: one oracle Lloyd step on the first {rows} of {w.n} points with the full k={w.k} "
+              f"centroid set; iter/s extrapolated linearly in n")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(w, "f64-oracle"), step=sample),
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(w, precision):
+    return {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "iters_per_step": w.iters, "precision": precision,
+            "mixture": {"m": w.m, "R": w.R, "sigma": w.sigma, "seed": hex(w.seed)}, "init": "first k points",
+            "l2": f"inputs larger than L2 (X = {w.n * w.d * 4 / 1e6:.0f} MB > 126 MB)",
+            "step": f"one kmeans_run call = {w.iters} graph-captured Lloyd iterations"}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init(world, "nccl")
+    from paper_1109_0778_b300 import kmeans as km
+
+    w = WORKLOADS[args.workload]
+    prec = args.precision or w.precision[0]
+    iters = w.iters
+    # pinned host copy of the workload, then the device copy
+    Xh = torch.empty((w.n, w.d), dtype=torch.float32, pin_memory=True)
+    synth.mixture(w.seed, w.n, w.d, w.m, w.R, w.sigma, out=Xh.numpy())
+    C0h = Xh[: w.k].clone().pin_memory()
+    Xd = Xh.to(dev)
+    C0d = C0h.to(dev)
+    Cd = C0d.clone()
+    a, s, c = km.alloc_outputs(Xd, Cd)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step():
+        Cd.copy_(C0d)
+        return km.run(Xd, Cd, iters, assign=a, sums=s, counts=c, precision=prec, profile=True, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
+    flagged = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = one_step()
+            for kname, v in out.stats["stage_ms"].items():
+                stage_tot[kname] += v
+            flagged.append(out.stats["n_flagged"])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    clocks = clk.summary()
+    t = ev0.elapsed_time(ev1) / 1e3
+    t_max = max_over_ranks(dist, t, dev)
+    total_iters = world * args.steps * iters
+    value = total_iters / t_max
+    flops_iter = 2.0 * w.n * w.k * w.d
+
+    # dominant kernel: the fused assignment (per-launch time from the events around it)
+    launches = args.steps * iters
+    assign_ms = stage_tot["assign"] / launches
+    achieved = flops_iter / (assign_ms / 1e3) / 1e12
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if prec == "fp32":
+        peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FFMA: {sms} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz",
+                "kernel": "assign_simt", "launch_ms": assign_ms,
+                "traffic": stored_traffic("assign", prec, w.name)}
+    else:
+        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else ""),
+                "kernel": f"assign_{prec}", "launch_ms": assign_ms, "traffic": stored_traffic("assign", prec, w.name)}
+    stage_share = {k: v / args.steps / iters for k, v in stage_tot.items()}
+
+    # end to end through the host-pointer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Ch = C0h.clone().pin_memory()
+        ah = torch.empty(w.n, dtype=torch.int32, pin_memory=True)
+        sh = torch.empty((w.k, w.d), dtype=torch.float32, pin_memory=True)
+        ch = torch.empty(w.k, dtype=torch.int32, pin_memory=True)
+        Ch.copy_(C0h)
+        km.run_host(Xh, Ch, iters, 0.0, ah, sh, ch, precision=prec)  # warm-up (staging buffers)
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Ch.copy_(C0h)
+            km.run_host(Xh, Ch, iters, 0.0, ah, sh, ch, precision=prec)
+        te = time.perf_counter() - t0
+        te = max_over_ranks(dist, te, dev)
+        e2e = {"value": world * args.steps * iters / te, "unit": "iter/s",
+               "h2d_bytes_per_step": 4 * w.n * w.d + 4 * w.k * w.d,
+               "d2h_bytes_per_step": 4 * w.k * w.d * 2 + 4 * w.n + 4 * w.k,
+               "api": "kmeans_run_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_sample_rate(w, args.cpu_seconds, X=Xh.numpy())
+        cpu = {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else prec,
+            "data": "synthetic", "config": workload_config(w, prec),
+            "distance_tflops": value * flops_iter / 1e12,
+            "roofline": roof, "stage_ms_per_iter": stage_share,
+            "flagged_per_step_last_iter": flagged[-1] if flagged else None,
+            "clocks": clocks, "e2e": e2e,
+            "gpu_launches": args.steps * (1 + len(STAGE_KERNELS) * iters),
+            "cpu_baseline": cpu,
+            "peaks_source": peak_src,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

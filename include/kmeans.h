@@ -1,0 +1,164 @@
+/*
+ * kmeans.h -- C ABI of the B300 fused Lloyd k-means library (libkmeans.so).
+ *
+ * One Lloyd iteration is the loop nest that the paper's fusion (Sec. 3.5)
+ * collapses into a single pass over the points: for every point the distance
+ * to every centroid (dist = norm(v1 - v2), Sec. 3.4), the argmin (a
+ * DeliteCollectElem over the point range, Sec. 2.4), and a keyed reduce of
+ * per-cluster sums and counts (DeliteReduceElem, Sec. 2.4), followed by the
+ * per-cluster divide avg = sum / length (the VectorOpsExp listing, Sec. 2.1).
+ *
+ * Definitions shared by every entry point (X is n x d, C is k x d, both FP32
+ * row-major; a is the assignment):
+ *   a_i      = min { j : ||x_i - c_j||^2 <= ||x_i - c_j'||^2 for all j' }
+ *              (squared Euclidean distance; the lowest index wins ties)
+ *   counts_j = |{ i : a_i = j }|,   sums_j = sum_{a_i = j} x_i
+ *   c_j'     = sums_j / counts_j, computed in FP64 and rounded to FP32;
+ *              an empty cluster (counts_j = 0) keeps c_j
+ *   J        = sum_i ||x_i - c_{a_i}||^2 with the centroids used for the
+ *              assignment (reported in FP64)
+ *
+ * Accuracy contract (all precisions): a_i equals the exact argmin for every
+ * point whose relative top-2 distance gap (D_(2) - D_(1)) / D_(2) is at least
+ * 1e-6. Points whose low-precision top-2 margin falls under a bound derived
+ * from the rounding errors are re-checked with compensated FP32 distances.
+ * Every centroid coordinate is within 1e-5 of the exact member mean, relative
+ * to the mean of |x_it| over the cluster's members.
+ *
+ * Memory and ownership: unless a function says otherwise, every array pointer
+ * is a DEVICE pointer (cudaMalloc'd or managed) owned by the caller; the
+ * library never frees it. The library owns only its workspace (cached per
+ * device, grown on demand, released at process exit). X must not overlap any
+ * output array.
+ *
+ * Streams: work is issued on opts->stream (NULL = the legacy default stream)
+ * and the call synchronises that stream before it returns, so outputs and
+ * statistics are complete on return. Calls on one device are serialised by
+ * a library lock.
+ *
+ * Errors: every function returns a km_status. On KM_EINVAL / KM_EUNSUPPORTED
+ * nothing was launched. On any other error the outputs are unspecified but C
+ * holds its value on entry. kmeans_last_error() returns a thread-local
+ * message for the last failing call of the calling thread.
+ *
+ * Preconditions: 1 <= k <= n < 2^31, 1 <= d <= 256, X and C finite with
+ * ||x_i||^2 and ||c_j||^2 finite in FP32 (else KM_ENONFINITE).
+ */
+#ifndef KMEANS_H
+#define KMEANS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KM_OK = 0,
+  KM_EINVAL = -1,        /* bad argument: sizes, null or host pointer, overlap */
+  KM_ECUDA = -2,         /* a CUDA runtime call failed */
+  KM_ENOMEM = -3,        /* workspace allocation failed */
+  KM_EUNSUPPORTED = -4,  /* valid but not supported (precision, shape) */
+  KM_ETIMEOUT = -5,      /* a bounded device-side wait expired */
+  KM_ENONFINITE = -6     /* X or C holds a NaN / Inf (or a norm overflows FP32) */
+} km_status;
+
+/* Arithmetic of the distance contraction. FP32 is exact up to FP32 rounding
+ * (SIMT FFMA); BF16 and FP8 run on the tensor cores with FP32 accumulation
+ * and per-row scales; all three re-check near-ties in FP32. */
+typedef enum { KM_FP32 = 0, KM_BF16 = 1, KM_FP8E4M3 = 2 } km_precision;
+
+typedef struct {
+  int32_t precision;  /* km_precision; default KM_FP32 */
+  int32_t recheck;    /* 1 (default): re-check flagged near-ties in FP32.
+                         0: keep the low-precision argmin (no accuracy contract) */
+  int32_t profile;    /* 1: time every stage with CUDA events recorded between
+                         the stages (captured into the run's graph) and report
+                         the per-stage totals in km_stats.stage_ms */
+  int32_t reserved1;
+  void* stream;       /* cudaStream_t to issue work on; NULL = legacy stream */
+} km_opts;
+
+/* Stages of one Lloyd step, in launch order (indexes of km_stats.stage_ms).
+ * KM_STAGE_XNORM runs once per call (point norms, hoisted out of the loop). */
+enum {
+  KM_STAGE_XNORM = 0,   /* ||x_i|| bounds and the finiteness check of X */
+  KM_STAGE_PREP = 1,    /* centroid half-norms h_j and the error-bound maxima */
+  KM_STAGE_ASSIGN = 2,  /* fused distance + argmin + near-tie flagging */
+  KM_STAGE_RECHECK = 3, /* compensated FP32 re-check of flagged points */
+  KM_STAGE_COUNT = 4,   /* cluster histogram */
+  KM_STAGE_SCAN = 5,    /* segment offsets */
+  KM_STAGE_SCATTER = 6, /* point indices sorted by cluster */
+  KM_STAGE_SEGSUM = 7,  /* segmented sums and the objective */
+  KM_STAGE_DIVIDE = 8,  /* FP64 divide, shift, stop rule */
+  KM_NSTAGES = 9
+};
+
+/* Statistics of a call (the last step for the run variants). */
+typedef struct {
+  double objective;     /* J(a^t, C^t) of the last step, FP64 */
+  double shift;         /* max_j ||c_j^{t+1} - c_j^t||_2 of the last step */
+  int64_t n_changed;    /* points whose assignment changed in the last step
+                           (all n in the first step of a call) */
+  int64_t n_flagged;    /* points re-checked in FP32 in the last step */
+  int64_t n_full;       /* of those, points re-checked against all k centroids */
+  int32_t n_empty;      /* empty clusters after the last step */
+  int32_t iters_done;   /* Lloyd steps executed */
+  float ms;             /* device time of the call (CUDA events) */
+  int32_t reserved;
+  float stage_ms[12];   /* with opts->profile: device time per stage summed
+                           over the call's steps (KM_STAGE_*), else zeros */
+} km_stats;
+
+/* Fills *opts with the defaults (FP32, recheck on, legacy stream). */
+void kmeans_default_opts(km_opts* opts);
+
+/*
+ * One Lloyd step. X: const float[n*d]. C: float[k*d], in: the centroids used
+ * for the assignment, out: the updated centroids. assign: int32[n] out.
+ * sums: float[k*d] out (per-cluster sums of X, rounded from FP64 partials).
+ * counts: int32[k] out.
+ */
+int kmeans_step(const float* X, int64_t n, int32_t d, float* C, int32_t k,
+                int32_t* assign, float* sums, int32_t* counts);
+
+/*
+ * Up to `iters` Lloyd steps from C (iters >= 1). tol <= 0: exactly `iters`
+ * steps. tol > 0: stop after the first step whose assignment equals the
+ * previous step's, or whose largest centroid shift is <= tol. Outputs are
+ * those of the last step executed. The iterations run as one captured CUDA
+ * graph with the stop test evaluated on the device.
+ */
+int kmeans_run(const float* X, int64_t n, int32_t d, float* C, int32_t k,
+               int32_t* assign, float* sums, int32_t* counts, int32_t iters,
+               double tol);
+
+/* As kmeans_step / kmeans_run with options (NULL = defaults) and statistics
+ * (NULL = not wanted). */
+int kmeans_step_ex(const km_opts* opts, const float* X, int64_t n, int32_t d,
+                   float* C, int32_t k, int32_t* assign, float* sums,
+                   int32_t* counts, km_stats* stats);
+int kmeans_run_ex(const km_opts* opts, const float* X, int64_t n, int32_t d,
+                  float* C, int32_t k, int32_t* assign, float* sums,
+                  int32_t* counts, int32_t iters, double tol, km_stats* stats);
+
+/*
+ * As kmeans_run_ex, but every array is a HOST pointer (pageable or pinned).
+ * The library copies X and C to device memory it owns, runs, and copies
+ * C, assign, sums and counts back before returning.
+ */
+int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32_t d,
+                    float* C, int32_t k, int32_t* assign, float* sums,
+                    int32_t* counts, int32_t iters, double tol, km_stats* stats);
+
+/* Message of the calling thread's last failing call ("" if none). */
+const char* kmeans_last_error(void);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int32_t kmeans_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMEANS_H */

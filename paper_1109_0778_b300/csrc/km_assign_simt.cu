@@ -1,0 +1,219 @@
+// FP32 fused distance + argmin on the SIMT FFMA pipes.
+//
+// The distance loop, the argmin and the error test are one pass over a
+// 128-point row tile (vertical fusion with array contraction, Sec. 3.5): the
+// n x k score matrix lives only in registers, one 128 x 128 chunk at a time,
+// the way the Stream of Sec. 4.1 evaluates its distance matrix chunk by chunk
+// into the consumer.
+//
+// Score. With h_j = ||c_j||^2 / 2 (prepared once per iteration, Sec. 3.1),
+//   ||x - c_j||^2 = ||x||^2 + 2 (h_j - x.c_j),
+// so the argmin over j of s_j = h_j - x.c_j is the distance argmin, and
+// ||x||^2 never has to be added.
+//
+// Error bound (u = 2^-24, gamma_m = m u / (1 - m u)). The dot product is an
+// FMA chain over d terms: |fl(x.c) - x.c| <= gamma_d sum_t |x_t c_t|
+// <= gamma_d ||x|| ||c||. h_j carries <= 2u h_j (FP64 norm rounded to FP32),
+// and the subtraction one more rounding, so for every j
+//   |s^_j - s_j| <= E_i = 3u H + gamma_{d+1} ||x_i|| Cmax,
+// with H = max_j h_j and Cmax = max_j ||c_j|| (rounded up). If the computed
+// top-2 scores satisfy s^_2 - s^_1 > 2 E_i, every other centroid is strictly
+// farther than j1 in exact arithmetic, so j1 is the exact argmin. Otherwise
+// the point is flagged and re-checked with compensated FP32 distances.
+#include "km_internal.cuh"
+
+namespace km {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, PAD = 4;
+constexpr int THREADS = 256;
+
+__device__ __forceinline__ int row_of(int ty, int r) { return r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4); }
+__device__ __forceinline__ int col_of(int tx, int c) { return c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
+
+// Best score and index of a row, and the second-best score (its index is not
+// needed: a flagged point is re-checked against every centroid).
+struct Top2 {
+  float b1, b2;
+  int i1;
+};
+
+__device__ __forceinline__ void top2_push(Top2& t, float s, int j) {
+  // Columns arrive in increasing j, so strict comparisons keep the lowest
+  // index among equal scores.
+  if (s < t.b2) {
+    if (s < t.b1) {
+      t.b2 = t.b1;
+      t.b1 = s; t.i1 = j;
+    } else {
+      t.b2 = s;
+    }
+  }
+}
+
+__device__ __forceinline__ Top2 top2_merge(const Top2& a, const Top2& b) {
+  Top2 r;
+  if (lex_less(b.b1, b.i1, a.b1, a.i1)) {
+    r.b1 = b.b1; r.i1 = b.i1;
+    r.b2 = fminf(a.b1, b.b2);
+  } else {
+    r.b1 = a.b1; r.i1 = a.i1;
+    r.b2 = fminf(b.b1, a.b2);
+  }
+  return r;
+}
+
+// Loads a BK-wide slice [k0, k0+BK) of `rows` rows starting at r0 of a
+// row-major (nrows x d) matrix into registers (coalesced along d).
+__device__ __forceinline__ void load_slice(const float* __restrict__ M, int64_t nrows, int d,
+                                           int64_t r0, int k0, float (&v)[BM * BK / THREADS]) {
+#pragma unroll
+  for (int q = 0; q < BM * BK / THREADS; ++q) {
+    int e = threadIdx.x + q * THREADS;
+    int r = e / BK, c = e % BK;
+    int64_t row = r0 + r;
+    int col = k0 + c;
+    v[q] = (row < nrows && col < d) ? __ldg(M + row * d + col) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const float (&v)[BM * BK / THREADS]) {
+#pragma unroll
+  for (int q = 0; q < BM * BK / THREADS; ++q) {
+    int e = threadIdx.x + q * THREADS;
+    S[e % BK][e / BK] = v[q];
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C, int k,
+                   const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
+                   int32_t* __restrict__ assign, FlagRec* __restrict__ flags, int first, float gam) {
+  if (ctl->done) return;
+  extern __shared__ __align__(16) float smem[];
+  float (*As)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem);
+  float (*Bs)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem + BK * (BM + PAD));
+  __shared__ unsigned int s_changed;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float H = __uint_as_float(ctl->hmax_bits);
+  const float Cmax = __uint_as_float(ctl->cmax_bits);
+  const int64_t ntiles = (n + BM - 1) / BM;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t m0 = tile * BM;
+    Top2 top[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) top[r] = Top2{INFINITY, INFINITY, 0};
+
+    for (int j0 = 0; j0 < k; j0 += BN) {
+      float acc[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+
+      float va[BM * BK / THREADS], vb[BM * BK / THREADS];
+      load_slice(X, n, d, m0, 0, va);
+      load_slice(C, k, d, j0, 0, vb);
+      for (int k0 = 0; k0 < d; k0 += BK) {
+        __syncthreads();
+        store_slice(As, va);
+        store_slice(Bs, vb);
+        __syncthreads();
+        if (k0 + BK < d) {  // prefetch the next slice while this one is consumed
+          load_slice(X, n, d, m0, k0 + BK, va);
+          load_slice(C, k, d, j0, k0 + BK, vb);
+        }
+        const int kend = min(BK, d - k0);
+#pragma unroll 8
+        for (int kk = 0; kk < kend; ++kk) {
+          float a[8], b[8];
+          *reinterpret_cast<float4*>(&a[0]) = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+          *reinterpret_cast<float4*>(&a[4]) = *reinterpret_cast<const float4*>(&As[kk][64 + ty * 4]);
+          *reinterpret_cast<float4*>(&b[0]) = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+          *reinterpret_cast<float4*>(&b[4]) = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+      }
+      // epilogue of this chunk: scores and running top-2 per row
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int j = j0 + col_of(tx, c);
+        if (j < k) {
+          const float hj = __ldg(chalf + j);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) top2_push(top[r], __fsub_rn(hj, acc[r][c]), j);
+        }
+      }
+    }
+
+    // merge the 16 column-threads that share each row (lanes differ in tx only)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int o = 8; o; o >>= 1) {
+        Top2 p;
+        p.b1 = __shfl_xor_sync(0xffffffffu, top[r].b1, o);
+        p.b2 = __shfl_xor_sync(0xffffffffu, top[r].b2, o);
+        p.i1 = __shfl_xor_sync(0xffffffffu, top[r].i1, o);
+        top[r] = top2_merge(top[r], p);
+      }
+    }
+    if (tid == 0) s_changed = 0;
+    __syncthreads();
+    if (tx == 0) {
+      unsigned int changed = 0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t i = m0 + row_of(ty, r);
+        if (i < n) {
+          const int old = first ? -1 : assign[i];
+          const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
+          const float margin = 2.f * E * (1.f + 0x1p-10f);
+          const int j1 = top[r].i1;
+          if (__fsub_rn(top[r].b2, top[r].b1) <= margin) {
+            unsigned long long slot = atomicAdd(&ctl->n_flagged, 1ull);
+            FlagRec rec;
+            rec.i = (int32_t)i; rec.old = old; rec.nc = 0; rec.pad = 0;
+            rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
+            flags[slot] = rec;
+            atomicAdd(&ctl->n_full, 1ull);
+          } else {
+            changed += (old != j1);
+          }
+          assign[i] = j1;
+        }
+      }
+      if (changed) atomicAdd(&s_changed, changed);
+    }
+    __syncthreads();
+    if (tid == 0 && s_changed) atomicAdd(&ctl->n_changed, (unsigned long long)s_changed);
+  }
+}
+
+}  // namespace
+
+cudaError_t init_assign_simt() {
+  return cudaFuncSetAttribute(assign_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * BK * (BM + PAD) * sizeof(float)));
+}
+
+cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s) {
+  const size_t smem = 2 * BK * (BM + PAD) * sizeof(float);
+  const double u = 1.0 / 16777216.0;
+  const double m = p.d + 1;
+  const float gam = (float)(m * u / (1.0 - m * u) * (1.0 + 1e-6));
+  int64_t tiles = (p.n + BM - 1) / BM;
+  int64_t cap = (int64_t)num_sms();
+  int blocks = (int)(tiles < cap ? tiles : cap);
+  assign_simt_kernel<<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, p.C, p.k, w.chalf, w.xnorm, w.ctl,
+                                                   p.assign, w.flags, first, gam);
+  return cudaGetLastError();
+}
+
+}  // namespace km

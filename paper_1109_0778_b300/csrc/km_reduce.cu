@@ -1,0 +1,292 @@
+// Keyed reduce of the Lloyd step (DeliteReduceElem keyed by cluster, Sec. 2.4)
+// and the per-cluster divide avg = sum / length (Sec. 2.1).
+//
+// The sums are formed by a counting sort of the point indices by cluster
+// followed by a segmented sum over the sorted order:
+//   count   -- counts_j = |{i : a_i = j}| (shared-memory histogram when k is
+//              small enough, else global atomics), exact integers;
+//   scan    -- segment starts offs_j = sum_{j' < j} counts_j';
+//   scatter -- perm[offs_j + r] = i for the r-th member found (warp-aggregated
+//              cursors, order within a segment unspecified);
+//   segsum  -- each warp walks a run of sorted positions: while the cluster
+//              stays the same it Kahan-accumulates the rows in FP32 registers,
+//              and on every cluster change it flushes its partial into an FP64
+//              sum (one atomic add per coordinate). The objective term
+//              ||x_i - c_{a_i}||^2 is formed in the same pass from the
+//              centroid held in registers for the segment.
+// Error: a Kahan-summed run of m rows carries <= 2u + O(m u^2) of the summed
+// magnitudes, and the FP64 combine adds ~2^-53 per partial, so every sum is
+// within ~1.2e-7 of sum |x_it| regardless of cluster size or order, far
+// inside the 1e-5 centroid tolerance.
+#include "km_internal.cuh"
+
+namespace km {
+
+namespace {
+
+constexpr int kSmemHistMax = 12288;  // bins held in shared memory by the count stage
+constexpr int RW = 64;               // sorted positions per warp in the segmented sum
+
+__global__ void __launch_bounds__(256)
+count_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ counts,
+             const Ctl* ctl) {
+  if (ctl->done) return;
+  extern __shared__ int hist[];
+  const bool use_smem = k <= kSmemHistMax;
+  if (use_smem) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) hist[j] = 0;
+    __syncthreads();
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int j = assign[i];
+    if (use_smem) atomicAdd(&hist[j], 1);
+    else atomicAdd(&counts[j], 1);
+  }
+  if (use_smem) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      if (hist[j]) atomicAdd(&counts[j], hist[j]);
+  }
+}
+
+// Exclusive scan of counts into offs[0..k] and the scatter cursors. One block.
+__global__ void __launch_bounds__(1024)
+scan_kernel(const int32_t* __restrict__ counts, int k, int32_t* __restrict__ offs,
+            int32_t* __restrict__ cursor, const Ctl* ctl) {
+  if (ctl->done) return;
+  __shared__ int warp_tot[32];
+  __shared__ int carry_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < k; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int v = j < k ? counts[j] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const int carry = carry_s;
+    const int excl = carry + (wid ? warp_tot[wid - 1] : 0) + x - v;
+    if (j < k) {
+      offs[j] = excl;
+      cursor[j] = excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offs[k] = carry_s;
+}
+
+__global__ void __launch_bounds__(256)
+scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int32_t* __restrict__ cursor,
+               int32_t* __restrict__ perm, const Ctl* ctl) {
+  if (ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    const bool valid = i < n;
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      const int j = assign[i];
+      const unsigned peers = __match_any_sync(active, j);
+      const int leader = __ffs(peers) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&cursor[j], __popc(peers));
+      pos = __shfl_sync(peers, pos, leader);
+      pos += __popc(peers & ((1u << lane) - 1));
+      perm[pos] = (int32_t)i;
+    }
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, int d, int lane,
+                                           float (&s)[V], float (&c)[V]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int t = v * 32 + lane;
+    if (t < d) atomicAdd(sums64 + (int64_t)j * d + t, (double)s[v] - (double)c[v]);
+    s[v] = 0.f;
+    c[v] = 0.f;
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256)
+segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
+              const int32_t* __restrict__ assign, const int32_t* __restrict__ perm,
+              double* __restrict__ sums64, Ctl* ctl) {
+  if (ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float objS = 0.f, objC = 0.f;
+  for (int64_t p0 = gw * RW; p0 < n; p0 += nw * RW) {
+    const int64_t p1 = min(p0 + (int64_t)RW, n);
+    float s[V], c[V], cj[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
+    int cur = -1;
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+      // each lane fetches one position of this batch; rows are then walked in order
+      const int64_t pl = pb + lane;
+      int my_i = 0, my_j = -1;
+      if (pl < p1) {
+        my_i = perm[pl];
+        my_j = assign[my_i];
+      }
+      const int cnt = (int)min((int64_t)32, p1 - pb);
+      for (int r = 0; r < cnt; ++r) {
+        const int i = __shfl_sync(0xffffffffu, my_i, r);
+        const int j = __shfl_sync(0xffffffffu, my_j, r);
+        if (j != cur) {
+          if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+          cur = j;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+          }
+        }
+        const float* x = X + (int64_t)i * d;
+        float q = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          const float xv = t < d ? __ldg(x + t) : 0.f;
+          kahan_add(s[v], c[v], xv);
+          const float df = __fsub_rn(xv, cj[v]);
+          q = fmaf(df, df, q);
+        }
+        kahan_add(objS, objC, q);
+      }
+    }
+    if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+  }
+  double o = (double)objS - (double)objC;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+  if (lane == 0 && o != 0.0) atomicAdd(&ctl->objective, o);
+}
+
+// c_j = sums_j / counts_j in FP64, rounded to FP32 (an empty cluster keeps
+// c_j); sums are returned rounded to FP32 and the FP64 accumulators are
+// cleared for the next step. The last block to finish records the step's
+// statistics and evaluates the stop rule. One warp per centroid.
+__global__ void __launch_bounds__(256)
+divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ counts,
+              double* __restrict__ sums64, float* __restrict__ sums, Ctl* ctl, Work w, double tol) {
+  if (ctl->done) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = gw; j < k; j += nw) {
+    const int cnt = counts[j];
+    double acc = 0.0;
+    for (int t = lane; t < d; t += 32) {
+      const int64_t e = (int64_t)j * d + t;
+      const double sv = sums64[e];
+      sums64[e] = 0.0;
+      sums[e] = (float)sv;
+      const float co = C[e];
+      const float cn = cnt > 0 ? (float)(sv / (double)cnt) : co;
+      C[e] = cn;
+      const double df = (double)cn - (double)co;
+      acc = fma(df, df, acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      atomic_max_nonneg(&ctl->shift2_bits, acc);
+      if (cnt == 0) atomicAdd(&ctl->n_empty, 1);
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(&ctl->blocks_done, 1u);
+    if (ticket == gridDim.x - 1) {  // last block: every other block's atomics are visible
+      __threadfence();
+      volatile Ctl* vc = ctl;
+      const int it = vc->iters_done;
+      const double shift = sqrt(__longlong_as_double((long long)vc->shift2_bits));
+      const unsigned long long changed = vc->n_changed;
+      w.obj_hist[it] = vc->objective;
+      w.shift_hist[it] = shift;
+      w.changed_hist[it] = changed;
+      w.flagged_hist[it] = vc->n_flagged;
+      w.full_hist[it] = vc->n_full;
+      w.empty_hist[it] = vc->n_empty;
+      vc->iters_done = it + 1;
+      if (tol > 0.0 && (changed == 0 || shift <= tol)) vc->done = 1;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_count(const Problem& p, const Work& w, cudaStream_t s) {
+  const size_t smem = p.k <= kSmemHistMax ? (size_t)p.k * sizeof(int) : 0;
+  int64_t blocks = (p.n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 2;
+  if (blocks > cap) blocks = cap;
+  count_kernel<<<(int)blocks, 256, smem, s>>>(p.assign, p.n, p.k, p.counts, w.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s) {
+  scan_kernel<<<1, 1024, 0, s>>>(p.counts, p.k, w.offs, w.cursor, w.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
+  int64_t blocks = (p.n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  scatter_kernel<<<(int)blocks, 256, 0, s>>>(p.assign, p.n, w.cursor, w.perm, w.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s) {
+  int64_t warps = (p.n + RW - 1) / RW;
+  int64_t blocks = (warps + 7) / 8;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (blocks > cap) blocks = cap;
+  const int V = (p.d + 31) / 32;
+  switch (V) {
+#define KM_CASE(v) case v: segsum_kernel<v><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl); break;
+    KM_CASE(1) KM_CASE(2) KM_CASE(3) KM_CASE(4) KM_CASE(5) KM_CASE(6) KM_CASE(7) KM_CASE(8)
+#undef KM_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s) {
+  (void)iter;
+  int blocks = (p.k + 7) / 8;
+  const int cap = num_sms() * 4;
+  if (blocks > cap) blocks = cap;
+  divide_kernel<<<blocks, 256, 0, s>>>(p.C, p.k, p.d, p.counts, w.sums64, p.sums, w.ctl, w, tol);
+  return cudaGetLastError();
+}
+
+}  // namespace km

@@ -1,0 +1,190 @@
+"""Python binding of libkmeans.so (include/kmeans.h): argument marshalling only.
+
+Every stage of the Lloyd step runs in the library's CUDA kernels; this module
+checks tensor types and shapes, passes raw pointers and sizes through ctypes,
+and turns a km_status into an exception. There is no CPU path: if the shared
+library is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkmeans.so")
+
+KM_OK, KM_EINVAL, KM_ECUDA, KM_ENOMEM, KM_EUNSUPPORTED, KM_ETIMEOUT, KM_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ECUDA", -3: "KM_ENOMEM", -4: "KM_EUNSUPPORTED",
+                -5: "KM_ETIMEOUT", -6: "KM_ENONFINITE"}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
+
+#: Entry points declared in include/kmeans.h (checked by the ABI test).
+EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
+           "kmeans_run_host", "kmeans_last_error", "kmeans_version")
+
+
+class KMeansError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("recheck", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("objective", ctypes.c_double), ("shift", ctypes.c_double),
+                ("n_changed", ctypes.c_int64), ("n_flagged", ctypes.c_int64),
+                ("n_full", ctypes.c_int64), ("n_empty", ctypes.c_int32),
+                ("iters_done", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "stage_ms")}
+        d["stage_ms"] = {name: float(self.stage_ms[i]) for i, name in enumerate(STAGES)}
+        return d
+
+
+def load(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libkmeans.so not built at {path}: run paper_1109_0778_b300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    P = ctypes.POINTER
+    lib.kmeans_default_opts.restype = None
+    lib.kmeans_default_opts.argtypes = [P(Opts)]
+    lib.kmeans_step.restype = ctypes.c_int
+    lib.kmeans_step.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp]
+    lib.kmeans_run.restype = ctypes.c_int
+    lib.kmeans_run.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, i32, dbl]
+    lib.kmeans_step_ex.restype = ctypes.c_int
+    lib.kmeans_step_ex.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, vp, P(Stats)]
+    lib.kmeans_run_ex.restype = ctypes.c_int
+    lib.kmeans_run_ex.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, vp, i32, dbl, P(Stats)]
+    lib.kmeans_run_host.restype = ctypes.c_int
+    lib.kmeans_run_host.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, vp, i32, dbl, P(Stats)]
+    lib.kmeans_last_error.restype = ctypes.c_char_p
+    lib.kmeans_last_error.argtypes = []
+    lib.kmeans_version.restype = ctypes.c_int32
+    lib.kmeans_version.argtypes = []
+    return lib
+
+
+_lib = load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != KM_OK:
+        raise KMeansError(rc, _lib.kmeans_last_error().decode())
+
+
+def make_opts(precision: str = "fp32", recheck: bool = True, stream=None, profile: bool = False) -> Opts:
+    o = Opts()
+    _lib.kmeans_default_opts(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.recheck = 1 if recheck else 0
+    o.profile = 1 if profile else 0
+    o.stream = stream
+    return o
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+def _check_tensors(X, C, assign, sums, counts):
+    import torch
+
+    n, d = X.shape
+    k = C.shape[0]
+    for name, t, dt, shape in (("X", X, torch.float32, (n, d)), ("C", C, torch.float32, (k, d)),
+                               ("assign", assign, torch.int32, (n,)), ("sums", sums, torch.float32, (k, d)),
+                               ("counts", counts, torch.int32, (k,))):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor of shape {shape}")
+    return n, d, k
+
+
+@dataclass
+class Outputs:
+    assign: "object"
+    sums: "object"
+    counts: "object"
+    stats: dict
+
+
+def alloc_outputs(X, C):
+    import torch
+
+    n, _ = X.shape
+    k, d = C.shape
+    return (torch.empty(n, dtype=torch.int32, device=X.device),
+            torch.empty(k, d, dtype=torch.float32, device=X.device),
+            torch.empty(k, dtype=torch.int32, device=X.device))
+
+
+def step(X, C, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True, stream=None,
+         profile=False) -> Outputs:
+    """One Lloyd step on device tensors; C is updated in place (kmeans_step_ex)."""
+    if assign is None:
+        assign, sums, counts = alloc_outputs(X, C)
+    n, d, k = _check_tensors(X, C, assign, sums, counts)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile)
+    st = Stats()
+    _check(_lib.kmeans_step_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
+                               sums.data_ptr(), counts.data_ptr(), ctypes.byref(st)))
+    return Outputs(assign, sums, counts, st.as_dict())
+
+
+def run(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True,
+        stream=None, profile=False) -> Outputs:
+    """Up to ``iters`` Lloyd steps on device tensors; C is updated in place (kmeans_run_ex)."""
+    if assign is None:
+        assign, sums, counts = alloc_outputs(X, C)
+    n, d, k = _check_tensors(X, C, assign, sums, counts)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile)
+    st = Stats()
+    _check(_lib.kmeans_run_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
+                              sums.data_ptr(), counts.data_ptr(), int(iters), float(tol), ctypes.byref(st)))
+    return Outputs(assign, sums, counts, st.as_dict())
+
+
+def run_host(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True,
+             stream=None):
+    """kmeans_run_host on host arrays (numpy arrays or CPU tensors, pinned or not).
+
+    C is updated in place; assign, sums and counts are filled. Returns the stats dict.
+    """
+    import numpy as np
+
+    def ptr(a):
+        return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+    n, d = X.shape
+    k = C.shape[0]
+    o = make_opts(precision, recheck, stream)
+    st = Stats()
+    _check(_lib.kmeans_run_host(ctypes.byref(o), ptr(X), n, d, ptr(C), k, ptr(assign), ptr(sums), ptr(counts),
+                                int(iters), float(tol), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def version() -> int:
+    return int(_lib.kmeans_version())

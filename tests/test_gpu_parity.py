@@ -1,0 +1,231 @@
+"""GPU parity of the fused Lloyd step against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import parity
+import synth
+from synth import WORKLOADS
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def km():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1109_0778_b300 import kmeans
+
+    return kmeans
+
+
+DEV = "cuda:0"
+
+
+def gpu_steps(km, orc, X, C0, steps, precision="fp32", rows=None):
+    """Teacher-forced per-step parity; returns the number of near-tie mismatches and the stats."""
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(np.ascontiguousarray(C0, dtype=np.float32)).to(DEV)
+    near = 0
+    stats = []
+    for _ in range(steps):
+        C_in = Cd.cpu().numpy().astype(np.float64)
+        out = km.step(Xd, Cd, precision=precision)
+        a = out.assign.cpu().numpy()
+        m, _ = parity.check_assign(orc, X, C_in, a, rows=rows)
+        near += m
+        parity.check_update(orc, X, C_in, a, Cd.cpu().numpy(), out.sums.cpu().numpy(), out.counts.cpu().numpy())
+        parity.check_objective(orc, X, C_in, a, out.stats["objective"])
+        assert out.stats["iters_done"] == 1
+        stats.append(out.stats)
+    return near, stats
+
+
+def test_plain_workload_all_iterations(km, ref):
+    w = WORKLOADS["plain_n10k_d16_k8"]
+    X, C0 = synth.workload_data(w)
+    near, stats = gpu_steps(km, ref, X, C0, w.iters)
+    assert stats[0]["n_changed"] == w.n
+    assert near <= 2
+
+
+@pytest.mark.parametrize("n,d,k", [
+    (1, 1, 1), (5, 3, 5), (7, 1, 2), (1000, 1, 7), (129, 2, 128), (4099, 33, 130),
+    (2000, 17, 129), (3000, 256, 20), (1500, 255, 300), (20037, 64, 256), (513, 96, 511),
+])
+def test_shapes_ragged(km, ref, n, d, k):
+    X = synth.mixture(1000 + n + d + k, n, d, max(k, 1), 5.0, 1.0)
+    near, _ = gpu_steps(km, ref, X, X[:k].copy(), 3)
+    assert near <= max(2, n // 1000)
+
+
+def test_k_equals_one_and_n(km, ref):
+    X = synth.mixture(77, 700, 9, 3, 4.0, 1.0)
+    gpu_steps(km, ref, X, X[:1].copy(), 2)
+    # k = n with distinct points and C0 = X: identity assignment, nothing moves
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = Xd.clone()
+    out = km.step(Xd, Cd)
+    assert np.array_equal(out.assign.cpu().numpy(), np.arange(700, dtype=np.int32))
+    assert torch.equal(Cd, Xd)
+    assert out.stats["objective"] == 0.0
+
+
+def test_exact_ties_and_empty_clusters(km, ref):
+    # integer data with duplicated centroids: exact ties must go to the lowest index and the
+    # duplicates must stay empty with their centroid unchanged
+    rng = np.random.default_rng(5)
+    X = rng.integers(-4, 5, size=(5000, 3)).astype(np.float32)
+    C0 = np.concatenate([X[:6], X[:6], X[6:10]])  # 6 duplicated pairs
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.step(Xd, Cd)
+    a = out.assign.cpu().numpy()
+    ra, *_ = ref.assign(X, C0.astype(np.float64))
+    assert np.array_equal(a, ra), "exact ties must resolve to the lowest index"
+    counts = out.counts.cpu().numpy()
+    assert np.all(counts[6:12] == 0)
+    assert np.array_equal(Cd.cpu().numpy()[6:12], C0[6:12])
+    assert out.stats["n_empty"] >= 6
+    parity.check_update(ref, X, C0.astype(np.float64), a, Cd.cpu().numpy(), out.sums.cpu().numpy(), counts)
+
+
+def test_golden_examples_on_gpu(km):
+    import oracle_pins
+
+    for path in oracle_pins.golden_files():
+        d, Xf, C0f, steps = oracle_pins.parse_golden(path)
+        X = torch.tensor([float(v) for v in Xf], dtype=torch.float32, device=DEV).reshape(-1, d)
+        C = torch.tensor([float(v) for v in C0f], dtype=torch.float32, device=DEV).reshape(-1, d)
+        for exp in steps:
+            out = km.step(X, C)
+            assert out.assign.cpu().tolist() == exp["assign"], path
+            assert out.counts.cpu().tolist() == exp["counts"], path
+            assert np.allclose(C.cpu().numpy().ravel(), [float(v) for v in exp["C"]], rtol=2e-7, atol=0), path
+            assert abs(out.stats["objective"] - float(exp["J"])) <= 1e-6 * max(1.0, float(exp["J"])), path
+
+
+def test_run_matches_free_running_oracle(km, ref):
+    w = WORKLOADS["plain_n10k_d16_k8"]
+    X, C0 = synth.workload_data(w)
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.run(Xd, Cd, w.iters)
+    r = ref.run(X, C0.astype(np.float64), w.iters)
+    assert out.stats["iters_done"] == w.iters
+    a = out.assign.cpu().numpy()
+    assert (a != r["assign"]).sum() <= 2
+    assert abs(out.stats["objective"] - r["objectives"][-1]) <= 1e-5 * r["objectives"][-1]
+    scale, _ = parity.member_scale(X, r["assign"], w.k)
+    assert np.all(np.abs(Cd.cpu().numpy() - r["C"]).max(axis=1) <= 1e-5 * scale + 1e-6)
+
+
+def test_run_graph_replay_and_resume(km, ref):
+    X = synth.mixture(31, 6000, 12, 10, 6.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    C0 = torch.from_numpy(X[:10].copy()).to(DEV)
+    C1 = C0.clone()
+    o1 = km.run(Xd, C1, 8)
+    # same call again replays the cached graph and must give the same result
+    C2 = C0.clone()
+    a2, s2, c2 = km.alloc_outputs(Xd, C2)
+    o2 = km.run(Xd, C2, 8, assign=a2, sums=s2, counts=c2)
+    C3 = C0.clone()
+    o3 = km.run(Xd, C3, 8, assign=a2, sums=s2, counts=c2)  # identical pointers: cached graph
+    assert torch.equal(o2.assign, o3.assign) and torch.equal(C2, C3)
+    # 4 + 4 steps reach the state of 8 steps (C is the whole state)
+    C4 = C0.clone()
+    km.run(Xd, C4, 4)
+    o4 = km.run(Xd, C4, 4)
+    assert (o4.assign != o1.assign).sum().item() <= 2
+    assert torch.allclose(C4, C1, rtol=0, atol=1e-4)
+
+
+def test_stop_rule(km, ref):
+    X = synth.mixture(9, 4000, 5, 4, 30.0, 0.5)  # well separated: converges in a few steps
+    Xd = torch.from_numpy(X).to(DEV)
+    C = torch.from_numpy(X[:4].copy()).to(DEV)
+    out = km.run(Xd, C, 50, tol=1e-300)
+    r = ref.run(X, X[:4].astype(np.float64), 50, tol=1e-300)
+    assert out.stats["iters_done"] == r["iters_done"] < 50
+    assert out.stats["n_changed"] == 0
+
+
+def test_permutation_equivariance(km):
+    X = synth.mixture(12, 5000, 20, 16, 5.0, 1.0)
+    perm = np.random.default_rng(0).permutation(5000)
+    C0 = torch.from_numpy(X[:16].copy()).to(DEV)
+    o1 = km.step(torch.from_numpy(X).to(DEV), C0.clone())
+    o2 = km.step(torch.from_numpy(np.ascontiguousarray(X[perm])).to(DEV), C0.clone())
+    assert np.array_equal(o2.assign.cpu().numpy(), o1.assign.cpu().numpy()[perm])
+    assert torch.equal(o1.counts, o2.counts)
+
+
+def test_host_entry_point(km, ref):
+    X = synth.mixture(44, 9000, 24, 30, 8.0, 1.0)
+    C0 = X[:30].copy()
+    Ch = C0.copy()
+    a = np.empty(9000, np.int32)
+    s = np.empty((30, 24), np.float32)
+    c = np.empty(30, np.int32)
+    st = km.run_host(X, Ch, 5, 0.0, a, s, c)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.run(torch.from_numpy(X).to(DEV), Cd, 5)
+    assert st["iters_done"] == 5
+    assert (a != out.assign.cpu().numpy()).sum() <= 2
+    assert np.allclose(Ch, Cd.cpu().numpy(), rtol=0, atol=1e-4)
+    assert c.sum() == 9000
+
+
+def test_errors(km):
+    X = torch.randn(100, 4, device=DEV)
+    C = X[:5].clone()
+    a, s, c = km.alloc_outputs(X, C)
+    # a host array through the device entry point is rejected by the C ABI itself
+    import ctypes
+
+    Xh = np.zeros((100, 4), np.float32)
+    st = km.Stats()
+    rc = km.lib().kmeans_step_ex(None, Xh.ctypes.data, 100, 4, C.data_ptr(), 5, a.data_ptr(), s.data_ptr(),
+                                 c.data_ptr(), ctypes.byref(st))
+    assert rc == km.KM_EINVAL and b"device memory" in km.lib().kmeans_last_error()
+    Xn = X.clone()
+    Xn[17, 2] = float("nan")
+    C_before = C.clone()
+    with pytest.raises(km.KMeansError) as e:
+        km.step(Xn, C, a, s, c)
+    assert e.value.status == km.KM_ENONFINITE
+    assert torch.equal(C, C_before), "C must hold its value on entry after an error"
+    Cn = C.clone()
+    Cn[1, 0] = float("inf")
+    with pytest.raises(km.KMeansError) as e:
+        km.step(X, Cn, a, s, c)
+    assert e.value.status == km.KM_ENONFINITE
+    # the library still works after the errors
+    out = km.step(X, C, a, s, c)
+    assert out.counts.sum().item() == 100
+
+
+@pytest.mark.slow
+def test_full_size_fp32_workload(km, ref):
+    """The benchmark's launch configuration (kmeans_run, 20 graph-captured steps) at full size,
+    checked by the O(nd) update in full and the O(nkd) assignment on a random sample of rows."""
+    w = WORKLOADS["fp32_n1M_d64_k256"]
+    X, C0 = synth.workload_data(w)
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.run(Xd, Cd, w.iters)
+    assert out.stats["iters_done"] == w.iters
+    a20 = out.assign.cpu().numpy()
+    C20 = Cd.cpu().numpy()
+    counts = out.counts.cpu().numpy()
+    assert counts.sum() == w.n and np.array_equal(counts, np.bincount(a20, minlength=w.k))
+    # one more step from C^20: sampled argmin parity and the full update
+    C_in = C20.astype(np.float64)
+    o = km.step(Xd, Cd)
+    a21 = o.assign.cpu().numpy()
+    rows = np.sort(np.random.default_rng(1).choice(w.n, 8192, replace=False))
+    parity.check_assign(ref, X, C_in, a21, rows=rows)
+    parity.check_update(ref, X, C_in, a21, Cd.cpu().numpy(), o.sums.cpu().numpy(), o.counts.cpu().numpy())
+    parity.check_objective(ref, X, C_in, a21, o.stats["objective"])
+    assert o.stats["objective"] <= out.stats["objective"] * (1 + 1e-6)
