@@ -132,13 +132,26 @@ def test_run_graph_replay_and_resume(km, ref):
     o2 = km.run(Xd, C2, 8, assign=a2, sums=s2, counts=c2)
     C3 = C0.clone()
     o3 = km.run(Xd, C3, 8, assign=a2, sums=s2, counts=c2)  # identical pointers: cached graph
-    assert torch.equal(o2.assign, o3.assign) and torch.equal(C2, C3)
+    # the segmented sums add FP64 partials in no set order, so centroids may differ in the last ulp
+    assert (o2.assign != o3.assign).sum().item() <= 2
+    assert torch.allclose(C2, C3, rtol=1e-6, atol=1e-6)
     # 4 + 4 steps reach the state of 8 steps (C is the whole state)
     C4 = C0.clone()
     km.run(Xd, C4, 4)
     o4 = km.run(Xd, C4, 4)
     assert (o4.assign != o1.assign).sum().item() <= 2
     assert torch.allclose(C4, C1, rtol=0, atol=1e-4)
+
+
+def test_assignment_is_deterministic(km):
+    # the assignment of a step depends only on X and C, never on reduction order
+    X = synth.mixture(13, 20000, 40, 64, 5.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    C0 = torch.from_numpy(X[:64].copy()).to(DEV)
+    outs = [km.step(Xd, C0.clone()) for _ in range(3)]
+    for o in outs[1:]:
+        assert torch.equal(o.assign, outs[0].assign)
+        assert torch.equal(o.counts, outs[0].counts)
 
 
 def test_stop_rule(km, ref):
