@@ -151,6 +151,28 @@ int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32_t d,
                     float* C, int32_t k, int32_t* assign, float* sums,
                     int32_t* counts, int32_t iters, double tol, km_stats* stats);
 
+/*
+ * Keyed reduce of a Lloyd step for a given assignment, without allocating:
+ * counts_j = |{i : a_i = j}|, sums_j = sum_{a_i = j} x_i (FP64 partials rounded
+ * to FP32), *objective = sum_i ||x_i - c_{a_i}||^2 (FP64; objective may be NULL).
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory (a host framework that owns all device memory,
+ * code that must not trigger cudaFree's device-wide synchronisation). It calls
+ * no cudaMalloc / cudaFree; its scratch is a fixed ~6.1 MB static device array
+ * that every GPU loading the library holds until exit. Limits: n <= 1048576,
+ * k <= 8192, k * d <= 262144, 1 <= d <= 256; larger sizes return KM_EINVAL.
+ * X: const float[n*d], C: const float[k*d], assign: const int32[n] with labels
+ * in [0, k) (else KM_EINVAL), sums: float[k*d] out, counts: int32[k] out; all
+ * device pointers. Work is issued on `stream` (NULL = legacy stream), which is
+ * synchronised before returning. The first call on a device looks up the
+ * scratch array's device address and should come before any stream capture.
+ * Every call shares the one scratch array (it clears what must start at
+ * zero), so calls that overlap on the GPU race with each other.
+ */
+int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C,
+                          int32_t k, const int32_t* assign, float* sums,
+                          int32_t* counts, double* objective, void* stream);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* kmeans_last_error(void);
 

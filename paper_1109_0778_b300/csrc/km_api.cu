@@ -35,6 +35,12 @@ using namespace km;
 
 thread_local std::string g_err;
 
+}  // namespace
+
+void km::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -90,6 +90,7 @@ cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
 
 int num_sms();
+void set_last_error(const char* msg);  // message returned by kmeans_last_error()
 cudaError_t init_assign_simt();  // one-time kernel attributes (per device)
 
 // ---- device helpers ----

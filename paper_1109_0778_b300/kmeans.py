@@ -22,7 +22,7 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 
 #: Entry points declared in include/kmeans.h (checked by the ABI test).
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
-           "kmeans_run_host", "kmeans_last_error", "kmeans_version")
+           "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc")
 
 
 class KMeansError(RuntimeError):
@@ -72,6 +72,8 @@ def load(path: str = LIB_PATH):
     lib.kmeans_last_error.argtypes = []
     lib.kmeans_version.restype = ctypes.c_int32
     lib.kmeans_version.argtypes = []
+    lib.kmeans_reduce_noalloc.restype = ctypes.c_int
+    lib.kmeans_reduce_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, P(dbl), vp]
     return lib
 
 
