@@ -44,7 +44,7 @@ METRIC = "Lloyd iter/s + distance TFLOP/s: FP32 vs BF16/FP8+recheck, exact assig
 DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
 STAGE_KERNELS = ("prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
 # Source file of each stage's kernel (a change to it voids a stored ncu traffic figure).
-KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu"}}
+KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu", "bf16": "km_assign_tc.cu", "fp8": "km_assign_tc.cu"}}
 
 
 def parse_args(argv=None):
@@ -56,6 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 (default: the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -278,6 +279,10 @@ def run_ours(args):
     from paper_1109_0778_b300 import kmeans as km
 
     w = WORKLOADS[args.workload]
+    if args.rows:
+        import dataclasses
+
+        w = dataclasses.replace(w, n=min(w.n, args.rows), name=f"{w.name}[:{min(w.n, args.rows)}]")
     prec = args.precision or w.precision[0]
     iters = w.iters
     # pinned host copy of the workload, then the device copy

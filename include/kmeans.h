@@ -75,7 +75,11 @@ typedef struct {
   int32_t profile;    /* 1: time every stage with CUDA events recorded between
                          the stages (captured into the run's graph) and report
                          the per-stage totals in km_stats.stage_ms */
-  int32_t reserved1;
+  int32_t warm_start; /* 1: assign holds a valid assignment on entry (e.g. the
+                         previous step's). It seeds the tensor-core epilogue
+                         threshold and n_changed counts against it. Labels
+                         outside [0, k) are ignored. 0 (default): assign is
+                         output only and every point counts as changed */
   void* stream;       /* cudaStream_t to issue work on; NULL = legacy stream */
 } km_opts;
 
@@ -99,7 +103,8 @@ typedef struct {
   double objective;     /* J(a^t, C^t) of the last step, FP64 */
   double shift;         /* max_j ||c_j^{t+1} - c_j^t||_2 of the last step */
   int64_t n_changed;    /* points whose assignment changed in the last step
-                           (all n in the first step of a call) */
+                           (all n in the first step of a call without
+                           warm_start) */
   int64_t n_flagged;    /* points re-checked in FP32 in the last step */
   int64_t n_full;       /* of those, points re-checked against all k centroids */
   int32_t n_empty;      /* empty clusters after the last step */

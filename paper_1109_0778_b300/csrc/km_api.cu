@@ -3,12 +3,17 @@
 // multi-step runs, and statistics. Declarations and contracts: include/kmeans.h.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "km_internal.cuh"
+#include "km_tc.cuh"
 
 #define KM_API extern "C" __attribute__((visibility("default")))
 
@@ -127,18 +132,41 @@ int init_ctx(DevCtx* c) {
   KM_CUDA(cudaEventCreate(&c->ev0));
   KM_CUDA(cudaEventCreate(&c->ev1));
   KM_CUDA(init_assign_simt());
+  KM_CUDA(init_assign_tc());
   c->inited = true;
   return KM_OK;
 }
 
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
-struct Layout {
-  size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
-      flagged, full, empty, total;
+// Shape of the tensor-core path for (d, k, precision).
+struct TcShape {
+  int fp8, esz, Kp, nkb, bn, kp, nchunks, stages;
 };
 
-Layout layout_for(int64_t n, int k, int d, int iters) {
+TcShape tc_shape(int precision, int d, int k) {
+  TcShape t{};
+  t.fp8 = precision == KM_FP8E4M3;
+  t.esz = t.fp8 ? 1 : 2;
+  const int kbe = 128 / t.esz;
+  t.Kp = (d + kbe - 1) / kbe * kbe;
+  t.nkb = t.Kp / kbe;
+  t.bn = t.nkb <= 2 ? 128 : 64;
+  t.kp = (k + t.bn - 1) / t.bn * t.bn;
+  t.nchunks = t.kp / t.bn;
+  // dynamic shared memory: 227 KB opt-in, minus 1 KB of alignment slack and 1 KB for static smem
+  const size_t budget = 227 * 1024 - 1024 - 1024;
+  const size_t a = 2 * (size_t)t.nkb * 128 * 128, b = (size_t)t.nkb * t.bn * 128;
+  t.stages = a + 2 * b <= budget ? (int)std::min<size_t>(8, (budget - a) / b) : 0;
+  return t;
+}
+
+struct Layout {
+  size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
+      flagged, full, empty, Xq, xs, Cq, hsc, state, total;
+};
+
+Layout layout_for(int64_t n, int k, int d, int iters, int precision) {
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
@@ -159,6 +187,18 @@ Layout layout_for(int64_t n, int k, int d, int iters) {
   L.flagged = take(8 * (size_t)iters);
   L.full = take(8 * (size_t)iters);
   L.empty = take(4 * (size_t)iters);
+  if (precision != KM_FP32) {
+    const TcShape t = tc_shape(precision, d, k);
+    L.Xq = take((size_t)n * t.Kp * t.esz);
+    L.xs = take(16 * (size_t)n);
+    L.Cq = take((size_t)t.kp * t.Kp * t.esz);
+    L.hsc = take(8 * (size_t)t.kp);
+    L.state = 0;
+  } else {
+    L.Xq = L.xs = L.Cq = L.hsc = 0;
+    const int width = simt_slab_width(d);
+    L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;
+  }
   L.total = o;
   return L;
 }
@@ -204,8 +244,54 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.flagged_hist = (unsigned long long*)(b + L.flagged);
   w.full_hist = (unsigned long long*)(b + L.full);
   w.empty_hist = (int*)(b + L.empty);
+  w.Xq = L.Xq ? (uint8_t*)(b + L.Xq) : nullptr;
+  w.xs = L.xs ? (float4*)(b + L.xs) : nullptr;
+  w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
+  w.hsc = L.hsc ? (float2*)(b + L.hsc) : nullptr;
+  w.state = L.state ? (float4*)(b + L.state) : nullptr;
   return w;
 }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D K-major code matrix [rows][Kp] -> boxes of (128 bytes of K) x box_rows, 128-byte swizzle.
+int encode_codes_map(CUtensorMap* m, void* base, int64_t rows, int Kp, int esz, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(KM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims,
+                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(KM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return KM_OK;
+}
+
+// Per-call state of a step sequence: precision, recheck switch, tensor-core launch data.
+struct StepCfg {
+  int precision;
+  int recheck;
+  int warm;  // assign holds a valid assignment on entry
+  TcShape t;
+  TcLaunch L;
+  TcParams P;
+};
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   const char *pa = (const char*)a, *pb = (const char*)b;
@@ -234,8 +320,8 @@ int validate_args(const km_opts& o, const Problem& p, int iters) {
   if (iters < 1) return fail(KM_EINVAL, "iters = %d < 1", iters);
   if (o.precision != KM_FP32 && o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
     return fail(KM_EINVAL, "unknown precision %d", o.precision);
-  if (o.precision != KM_FP32)
-    return fail(KM_EUNSUPPORTED, "precision %d is not built into this library", o.precision);
+  if (o.precision != KM_FP32 && tc_shape(o.precision, p.d, p.k).stages < 2)
+    return fail(KM_EUNSUPPORTED, "d = %d does not fit the tensor-core tile pipeline", p.d);
   const size_t nd = (size_t)p.n * p.d * 4, kd = (size_t)p.k * p.d * 4;
   const size_t na = (size_t)p.n * 4, nk = (size_t)p.k * 4;
   if (overlaps(p.X, nd, p.C, kd) || overlaps(p.X, nd, p.assign, na) || overlaps(p.X, nd, p.sums, kd) ||
@@ -258,17 +344,27 @@ int validate_device_ptrs(const Problem& p, int dev) {
 
 // The stage sequence of one Lloyd step (all on stream s). With `ev`
 // (kEvPerStep events) every stage boundary is recorded.
-cudaError_t enqueue_step(const Problem& p, const Work& w, int first, double tol, cudaStream_t s,
-                         const cudaEvent_t* ev) {
+cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, int first, double tol,
+                         cudaStream_t s, const cudaEvent_t* ev) {
   cudaError_t e;
   auto at = [&](int i) { return ev ? mark(ev[i], s) : cudaSuccess; };
+  const bool tcp = cfg.precision != KM_FP32;
   if ((e = cudaMemsetAsync(w.ctl, 0, kCtlIterBytes, s))) return e;
   if ((e = at(0))) return e;
-  if ((e = launch_prep(p, w, s))) return e;
+  if (tcp) e = launch_quant_c(p, w, cfg.t.fp8, cfg.t.kp, cfg.t.Kp, w.Cq, w.hsc, s);
+  else e = launch_prep(p, w, s);
+  if (e) return e;
   if ((e = at(1))) return e;
-  if ((e = launch_assign_simt(p, w, first, s))) return e;
+  if (tcp) {
+    TcParams P = cfg.P;
+    P.first = first;
+    e = launch_assign_tc(p, cfg.L, P, s);
+  } else {
+    e = launch_assign_simt(p, w, first, s);
+  }
+  if (e) return e;
   if ((e = at(2))) return e;
-  if ((e = launch_recheck(p, w, first, s))) return e;
+  if (cfg.recheck && (e = launch_recheck(p, w, first, s))) return e;
   if ((e = at(3))) return e;
   if ((e = launch_count(p, w, s))) return e;
   if ((e = at(4))) return e;
@@ -287,8 +383,8 @@ const cudaEvent_t* step_events(DevCtx* c, bool profile, int it) {
   return profile ? c->prof.data() + 2 + (size_t)it * kEvPerStep : nullptr;
 }
 
-int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, int iters, double tol,
-              bool profile, cudaGraphExec_t* out) {
+int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, const StepCfg& cfg, int iters,
+              double tol, bool profile, cudaGraphExec_t* out) {
   if (c->graph_valid && c->gkey == key) {
     *out = c->gexec;
     return KM_OK;
@@ -302,7 +398,7 @@ int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, i
   KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < iters && e == cudaSuccess; ++it)
-    e = enqueue_step(p, w, it == 0, tol, c->cap_stream, step_events(c, profile, it));
+    e = enqueue_step(p, w, cfg, it == 0 && !cfg.warm, tol, c->cap_stream, step_events(c, profile, it));
   cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -331,7 +427,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   int rc = init_ctx(c);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)o.stream;
-  const Layout L = layout_for(p.n, p.k, p.d, iters);
+  const Layout L = layout_for(p.n, p.k, p.d, iters, o.precision);
   if ((rc = ensure_ws(c, L, s))) return rc;
   const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 5 + 4) + 64;
   if (host_need > c->host_bytes) {
@@ -346,26 +442,58 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   }
   const Work w = make_work(c, L);
   const bool profile = o.profile != 0;
+  StepCfg cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.precision = o.precision;
+  cfg.recheck = o.recheck;
+  cfg.warm = o.warm_start;
+  if (o.precision != KM_FP32) {
+    cfg.t = tc_shape(o.precision, p.d, p.k);
+    cfg.L.fp8 = cfg.t.fp8;
+    if ((rc = encode_codes_map(&cfg.L.mapX, w.Xq, p.n, cfg.t.Kp, cfg.t.esz, 128))) return rc;
+    if ((rc = encode_codes_map(&cfg.L.mapC, w.Cq, cfg.t.kp, cfg.t.Kp, cfg.t.esz, cfg.t.bn))) return rc;
+    TcParams& P = cfg.P;
+    P.hsc = w.hsc;
+    P.xs = w.xs;
+    P.Cq = w.Cq;
+    P.assign = p.assign;
+    P.flags = w.flags;
+    P.ctl = w.ctl;
+    P.n = p.n;
+    P.k = p.k;
+    P.Kp = cfg.t.Kp;
+    P.nkb = cfg.t.nkb;
+    P.bn = cfg.t.bn;
+    P.nchunks = cfg.t.nchunks;
+    P.stages = cfg.t.stages;
+    P.idesc = tc::idesc_f32acc(cfg.t.fp8 ? 0u : 1u, 128, (uint32_t)cfg.t.bn);
+    const double K = cfg.t.Kp;
+    P.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));   // truncating FP32 accumulation
+    P.gam_simt = (float)(K * 0x1p-24 / (1.0 - K * 0x1p-24) * (1.0 + 1e-6));
+    P.wait_ns = 2000000000ull;
+  }
   if (profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   KM_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
   KM_CUDA(cudaMemsetAsync(w.sums64, 0, 8 * (size_t)p.k * p.d, s));
   KM_CUDA(cudaMemcpyAsync(w.Csave, p.C, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
-  KM_CUDA(launch_xnorm(p, w, s));
+  if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.fp8, cfg.t.Kp, w.Xq, w.xs, s));
+  else KM_CUDA(launch_xnorm(p, w, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[1], s));
   if (graph && iters > 1) {
     GraphKey key;
     memset(&key, 0, sizeof key);
     key.X = p.X; key.C = p.C; key.assign = p.assign; key.sums = p.sums; key.counts = p.counts;
     key.n = p.n; key.d = p.d; key.k = p.k; key.iters = iters; key.prec = o.precision; key.tol = tol;
-    key.profile = profile ? 1 : 0;
+    key.profile = (profile ? 1 : 0) | (o.recheck ? 2 : 0) | (o.warm_start ? 4 : 0);
     key.ws_gen = c->ws_gen;
     cudaGraphExec_t ge = nullptr;
-    if ((rc = get_graph(c, key, p, w, iters, tol, profile, &ge))) return rc;
+    if ((rc = get_graph(c, key, p, w, cfg, iters, tol, profile, &ge))) return rc;
     KM_CUDA(cudaGraphLaunch(ge, s));
   } else {
-    for (int it = 0; it < iters; ++it) KM_CUDA(enqueue_step(p, w, it == 0, tol, s, step_events(c, profile, it)));
+    for (int it = 0; it < iters; ++it)
+      KM_CUDA(enqueue_step(p, w, cfg, it == 0 && !cfg.warm, tol, s, step_events(c, profile, it)));
   }
   KM_CUDA(cudaEventRecord(c->ev1, s));
   char* h = (char*)c->host;
@@ -389,6 +517,11 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     KM_CUDA(cudaStreamSynchronize(s));
     if (hc->nonfinite) return fail(KM_ENONFINITE, "X or C holds a non-finite value (or a norm overflows FP32)");
     return fail(hc->error, "device stage reported error %d", hc->error);
+  }
+  if (getenv("KM_LOG")) {  // per-step history on stderr, for diagnosis
+    for (int it = 0; it < hc->iters_done; ++it)
+      fprintf(stderr, "[kmeans] step %d: J=%.9g changed=%llu flagged=%llu full=%llu empty=%d shift=%.3g\n", it,
+              hobj[it], hchanged[it], hflag[it], hfull[it], hempty[it], hshift[it]);
   }
   if (st) {
     memset(st, 0, sizeof *st);

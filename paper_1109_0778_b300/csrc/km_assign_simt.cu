@@ -172,7 +172,8 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
       for (int r = 0; r < 8; ++r) {
         const int64_t i = m0 + row_of(ty, r);
         if (i < n) {
-          const int old = first ? -1 : assign[i];
+          int old = first ? -1 : assign[i];
+          if (old < 0 || old >= k) old = -1;
           const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
           const float margin = 2.f * E * (1.f + 0x1p-10f);
           const int j1 = top[r].i1;
@@ -196,14 +197,245 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Slab-resident variant (d <= 128). A slab of up to kSlab centroids is loaded
+// into shared memory once per CTA (transposed, with its h_j); point tiles
+// stream through a cp.async double buffer, and each thread reads its 8 rows
+// four K-elements at a time. A row's running (best, index, second) lives in
+// registers within a slab and in `state` between slabs; the last slab applies
+// the same error-bound test as the streaming kernel above.
+constexpr int kSlabMaxD = 128;
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Issues the copies of point tile `tile` (rows of d floats) into Xs (row stride xs_stride floats).
+template <bool V16>
+__device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const float* __restrict__ X, int64_t n,
+                                                int d, int64_t tile) {
+  const int64_t m0 = tile * BM;
+  if (V16) {
+    const int per_row = d >> 2;
+    for (int e = threadIdx.x; e < BM * per_row; e += THREADS) {
+      const int r = e / per_row, c4 = e - r * per_row;
+      if (m0 + r < n) cp_async16(Xs + r * xs_stride + 4 * c4, X + (m0 + r) * d + 4 * c4);
+    }
+  } else {
+    for (int e = threadIdx.x; e < BM * d; e += THREADS) {
+      const int r = e / d, c = e - r * d;
+      if (m0 + r < n) cp_async4(Xs + r * xs_stride + c, X + (m0 + r) * d + c);
+    }
+  }
+}
+
+template <bool V16>
+__global__ void __launch_bounds__(THREADS, 1)
+assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
+                   int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
+                   int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
+                   int first, int first_slab, int last_slab, float gam) {
+  if (ctl->done) return;
+  extern __shared__ __align__(16) float smem[];
+  const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
+  const int xs_stride = dp + 4;             // floats per staged point row
+  float* Cs = smem;                          // [dp][nsp]
+  float* Hs = Cs + (size_t)dp * nsp;         // [nsp]
+  float* Xs0 = Hs + nsp;                     // 2 x [BM][xs_stride]
+  __shared__ unsigned int s_changed;
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // slab of centroids, transposed; zero padding in [d, dp) and [ns, nsp)
+  for (int e = tid; e < dp * nsp; e += THREADS) {
+    const int j = e % nsp, t = e / nsp;
+    Cs[e] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
+  }
+  for (int j = tid; j < nsp; j += THREADS) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
+  // zero both point buffers once: padding columns [d, dp) and rows past n stay zero
+  for (int e = tid; e < 2 * BM * xs_stride; e += THREADS) Xs0[e] = 0.f;
+  __syncthreads();
+
+  const float H = __uint_as_float(ctl->hmax_bits);
+  const float Cmax = __uint_as_float(ctl->cmax_bits);
+  const int64_t ntiles = (n + BM - 1) / BM;
+  int buf = 0;
+  if ((int64_t)blockIdx.x < ntiles) load_tile_async<V16>(Xs0, xs_stride, X, n, d, blockIdx.x);
+  cp_async_commit();
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    float* Xs = Xs0 + buf * BM * xs_stride;
+    if (next < ntiles) load_tile_async<V16>(Xs0 + (buf ^ 1) * BM * xs_stride, xs_stride, X, n, d, next);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+
+    const int64_t m0 = tile * BM;
+    Top2 top[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t i = m0 + row_of(ty, r);
+      // the carried state enters through one of the 16 threads sharing the row,
+      // so the cross-thread merge sees it once
+      if (!first_slab && tx == 0 && i < n) {
+        const float4 st = state[i];
+        top[r] = Top2{st.x, st.z, __float_as_int(st.y)};
+      } else {
+        top[r] = Top2{INFINITY, INFINITY, 0};
+      }
+    }
+    for (int j0 = 0; j0 < nsp; j0 += BN) {
+      float acc[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+      for (int kk = 0; kk < dp; kk += 4) {
+        float a[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          *reinterpret_cast<float4*>(a[r]) = *reinterpret_cast<const float4*>(Xs + row_of(ty, r) * xs_stride + kk);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float b[8];
+          const float* cr = Cs + (size_t)(kk + q) * nsp + j0;
+          *reinterpret_cast<float4*>(&b[0]) = *reinterpret_cast<const float4*>(cr + tx * 4);
+          *reinterpret_cast<float4*>(&b[4]) = *reinterpret_cast<const float4*>(cr + 64 + tx * 4);
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r][q], b[c], acc[r][c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int jl = j0 + col_of(tx, c);
+        const float hj = Hs[jl];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) top2_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int o = 8; o; o >>= 1) {
+        Top2 p;
+        p.b1 = __shfl_xor_sync(0xffffffffu, top[r].b1, o);
+        p.b2 = __shfl_xor_sync(0xffffffffu, top[r].b2, o);
+        p.i1 = __shfl_xor_sync(0xffffffffu, top[r].i1, o);
+        top[r] = top2_merge(top[r], p);
+      }
+    }
+    if (tid == 0) s_changed = 0;
+    __syncthreads();  // also: every thread is done reading Xs before it is refilled
+    if (tx == 0) {
+      unsigned int changed = 0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t i = m0 + row_of(ty, r);
+        if (i >= n) continue;
+        if (!last_slab) {
+          state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
+          continue;
+        }
+        int old = first ? -1 : assign[i];
+        if (old < 0 || old >= k) old = -1;
+        const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
+        const float margin = 2.f * E * (1.f + 0x1p-10f);
+        const int j1 = top[r].i1;
+        if (__fsub_rn(top[r].b2, top[r].b1) <= margin) {
+          const unsigned long long slot = atomicAdd(&ctl->n_flagged, 1ull);
+          FlagRec rec;
+          rec.i = (int32_t)i; rec.old = old; rec.nc = 0; rec.pad = 0;
+          rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
+          flags[slot] = rec;
+          atomicAdd(&ctl->n_full, 1ull);
+        } else {
+          changed += (old != j1);
+        }
+        assign[i] = j1;
+      }
+      if (changed) atomicAdd(&s_changed, changed);
+    }
+    __syncthreads();
+    if (tid == 0 && s_changed) atomicAdd(&ctl->n_changed, (unsigned long long)s_changed);
+    buf ^= 1;
+  }
+  cp_async_wait_1();
+}
+
+size_t slab_smem_bytes(int dp, int nsp) {
+  return ((size_t)dp * nsp + nsp + 2 * (size_t)BM * (dp + 4)) * sizeof(float);
+}
+
 }  // namespace
 
 cudaError_t init_assign_simt() {
-  return cudaFuncSetAttribute(assign_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * BK * (BM + PAD) * sizeof(float)));
+  cudaError_t e = cudaFuncSetAttribute(assign_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * BK * (BM + PAD) * sizeof(float)));
+  int dev = 0, optin = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, assign_slab_kernel<true>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(assign_slab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, assign_slab_kernel<false>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(assign_slab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+  return e;
+}
+
+// Centroids per slab for dimension d (0: the slab kernel does not apply).
+int simt_slab_width(int d) {
+  if (d > kSlabMaxD) return 0;
+  const int dp = (d + 3) / 4 * 4;
+  const size_t budget = 227 * 1024 - 2048;
+  const size_t fixed = 2 * (size_t)BM * (dp + 4) * sizeof(float);
+  if (fixed >= budget) return 0;
+  int ns = (int)((budget - fixed) / (((size_t)dp + 1) * sizeof(float))) / BN * BN;
+  return ns >= BN ? ns : 0;
+}
+
+cudaError_t launch_assign_slab(const Problem& p, const Work& w, int first, cudaStream_t s) {
+  const double u = 1.0 / 16777216.0;
+  const double m = p.d + 1;
+  const float gam = (float)(m * u / (1.0 - m * u) * (1.0 + 1e-6));
+  const int dp = (p.d + 3) / 4 * 4;
+  const int width = simt_slab_width(p.d);
+  const int64_t tiles = (p.n + BM - 1) / BM;
+  const int blocks = (int)(tiles < num_sms() ? tiles : num_sms());
+  const bool v16 = (p.d % 4 == 0) && ((uintptr_t)p.X % 16 == 0);
+  for (int j_lo = 0; j_lo < p.k; j_lo += width) {
+    const int ns = p.k - j_lo < width ? p.k - j_lo : width;
+    const int nsp = (ns + BN - 1) / BN * BN;
+    const size_t smem = slab_smem_bytes(dp, nsp);
+    const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
+    if (v16)
+      assign_slab_kernel<true><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, w.chalf, w.xnorm,
+                                                            w.ctl, p.assign, w.flags, w.state, first, first_slab,
+                                                            last_slab, gam);
+    else
+      assign_slab_kernel<false><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, w.chalf,
+                                                             w.xnorm, w.ctl, p.assign, w.flags, w.state, first,
+                                                             first_slab, last_slab, gam);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s) {
+  if (simt_slab_width(p.d) > 0) return launch_assign_slab(p, w, first, s);
   const size_t smem = 2 * BK * (BM + PAD) * sizeof(float);
   const double u = 1.0 / 16777216.0;
   const double m = p.d + 1;

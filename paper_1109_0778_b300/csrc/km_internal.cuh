@@ -3,6 +3,7 @@
 // helpers. Nothing here is part of the C ABI (include/kmeans.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,10 +26,10 @@ struct Ctl {
   unsigned long long shift2_bits;  // max_j ||dc_j||^2 as FP64 bits (>= 0)
   unsigned int cmax_bits;          // max_j ||c_j|| (FP32 bits, rounded up)
   unsigned int hmax_bits;          // max_j h_j = max_j ||c_j||^2 / 2
-  unsigned int qcmax_bits;         // max_j ||c_j - q(c_j)|| (quantised paths)
+  unsigned int qcmax_bits;         // max_j ||c~_j|| of the quantised centroids (rounded up)
+  unsigned int dcmax_bits;         // max_j ||c~_j - c_j|| (quantisation residual, rounded up)
   int n_empty;
   unsigned int blocks_done;        // last-block detection in the divide stage
-  int pad0;
   // ---- per run (cleared once) ----
   int done;          // the stop rule fired: every later stage returns at entry
   int iters_done;
@@ -65,6 +66,34 @@ struct Work {
   unsigned long long* flagged_hist;  // [iters]
   unsigned long long* full_hist;     // [iters]
   int* empty_hist;     // [iters]
+  // quantised operands of the tensor-core path (null for FP32)
+  uint8_t* Xq;         // [n][Kp] point codes (cached for the call)
+  float4* xs;          // [n] row scale and norm bounds
+  uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
+  float2* hsc;         // [kp] (h_j, sc_j)
+  float4* state;       // [n] per-row (best, index, second) between centroid slabs (FP32 path)
+};
+
+// Tensor-core assignment: quantised operands and launch shape.
+struct TcParams {
+  const float2* hsc;  // [kp] (h_j, sc_j); h_j = +inf for padding rows j >= k
+  const float4* xs;   // [n] (sx_i, ||x~_i||, ||x~_i - x_i||, ||x_i||), norms rounded up
+  const uint8_t* Cq;  // [kp][Kp] centroid codes (row stride Kp * element size)
+  int32_t* assign;
+  FlagRec* flags;
+  Ctl* ctl;
+  int64_t n;
+  int k, Kp, nkb, bn, nchunks, stages, first;
+  uint32_t idesc;
+  float gam_tc;       // accumulation bound of the tensor-core sum over Kp terms
+  float gam_simt;     // accumulation bound of the FP32 SIMT seed over Kp terms
+  uint64_t wait_ns;   // bound of every mbarrier wait
+};
+
+struct TcLaunch {
+  CUtensorMap mapX;   // codes of X: rows n, Kp elements, box (128 B, 128 rows), 128B swizzle
+  CUtensorMap mapC;   // codes of C: rows kp, Kp elements, box (128 B, bn rows), 128B swizzle
+  int fp8;
 };
 
 struct Problem {
@@ -88,10 +117,18 @@ cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
+cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uint8_t* Xq, float4* xs,
+                           cudaStream_t s);
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float2* hsc,
+                           cudaStream_t s);
+cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
+cudaError_t init_assign_tc();
+size_t tc_smem_bytes(int nkb, int bn, int stages);
 
 int num_sms();
 void set_last_error(const char* msg);  // message returned by kmeans_last_error()
 cudaError_t init_assign_simt();  // one-time kernel attributes (per device)
+int simt_slab_width(int d);       // centroids per shared-memory slab of the FP32 kernel (0: streamed)
 
 // ---- device helpers ----
 __device__ __forceinline__ void atomic_max_nonneg(unsigned int* addr, float v) {

@@ -6,9 +6,11 @@
 //   count   -- counts_j = |{i : a_i = j}| (shared-memory histogram when k is
 //              small enough, else global atomics), exact integers;
 //   scan    -- segment starts offs_j = sum_{j' < j} counts_j';
-//   scatter -- perm[offs_j + r] = i for the r-th member found (warp-aggregated
-//              cursors, order within a segment unspecified);
-//   segsum  -- each warp walks a run of sorted positions: while the cluster
+//   scatter -- perm[offs_j + r] = i for the r-th member found (cursors
+//              reserved once per block and cluster for k <= 8192, else
+//              warp-aggregated; order within a segment unspecified);
+//   segsum  -- each warp walks a run of sorted positions (the loads of 4-8
+//              rows in flight at once): while the cluster
 //              stays the same it Kahan-accumulates the rows in FP32 registers,
 //              and on every cluster change it flushes its partial into an FP64
 //              sum (one atomic add per coordinate). The objective term
@@ -117,6 +119,42 @@ scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int32_t* __restric
   }
 }
 
+// Scatter with block-level aggregation (k <= kSmemScatterMax): each block takes
+// a contiguous chunk of points, ranks them per cluster with shared-memory
+// atomics, reserves one range per (block, cluster) in the global cursors, and
+// writes its points there.
+constexpr int kSmemScatterMax = 8192;
+constexpr int kScatterPerThread = 16;
+
+__global__ void __launch_bounds__(256)
+scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ cursor,
+                     int32_t* __restrict__ perm, const Ctl* ctl) {
+  if (ctl->done) return;
+  extern __shared__ int cnt[];  // per-cluster count, then the block's base position
+  const int64_t chunk = (int64_t)blockDim.x * kScatterPerThread;
+  for (int64_t c0 = blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
+    __syncthreads();
+    int lab[kScatterPerThread], rank[kScatterPerThread];
+#pragma unroll
+    for (int q = 0; q < kScatterPerThread; ++q) {
+      const int64_t i = c0 + (int64_t)q * blockDim.x + threadIdx.x;
+      lab[q] = i < n ? assign[i] : -1;
+      rank[q] = lab[q] >= 0 ? atomicAdd(&cnt[lab[q]], 1) : 0;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x)
+      if (cnt[j]) cnt[j] = atomicAdd(&cursor[j], cnt[j]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kScatterPerThread; ++q) {
+      const int64_t i = c0 + (int64_t)q * blockDim.x + threadIdx.x;
+      if (lab[q] >= 0) perm[cnt[lab[q]] + rank[q]] = (int32_t)i;
+    }
+    __syncthreads();
+  }
+}
+
 template <int V>
 __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, int d, int lane,
                                            float (&s)[V], float (&c)[V]) {
@@ -134,6 +172,7 @@ __global__ void __launch_bounds__(256)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
               const int32_t* __restrict__ assign, const int32_t* __restrict__ perm,
               double* __restrict__ sums64, Ctl* ctl) {
+  constexpr int U = V <= 2 ? 8 : 4;  // rows whose loads are in flight together
   if (ctl->done) return;
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -154,29 +193,42 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
         my_j = assign[my_i];
       }
       const int cnt = (int)min((int64_t)32, p1 - pb);
-      for (int r = 0; r < cnt; ++r) {
-        const int i = __shfl_sync(0xffffffffu, my_i, r);
-        const int j = __shfl_sync(0xffffffffu, my_j, r);
-        if (j != cur) {
-          if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
-          cur = j;
+      for (int r0 = 0; r0 < cnt; r0 += U) {
+        float xr[U][V];
+        int ir[U], jr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {  // issue the loads of U rows before using any
+          ir[u] = __shfl_sync(0xffffffffu, my_i, (r0 + u) & 31);
+          jr[u] = __shfl_sync(0xffffffffu, my_j, (r0 + u) & 31);
+          const float* x = X + (int64_t)ir[u] * d;
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             const int t = v * 32 + lane;
-            cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+            xr[u][v] = (r0 + u < cnt && t < d) ? __ldg(x + t) : 0.f;
           }
         }
-        const float* x = X + (int64_t)i * d;
-        float q = 0.f;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
-          const float xv = t < d ? __ldg(x + t) : 0.f;
-          kahan_add(s[v], c[v], xv);
-          const float df = __fsub_rn(xv, cj[v]);
-          q = fmaf(df, df, q);
+        for (int u = 0; u < U; ++u) {
+          if (r0 + u >= cnt) break;
+          const int j = jr[u];
+          if (j != cur) {
+            if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+            cur = j;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const int t = v * 32 + lane;
+              cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+            }
+          }
+          float q = 0.f;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            kahan_add(s[v], c[v], xr[u][v]);
+            const float df = __fsub_rn(xr[u][v], cj[v]);
+            q = fmaf(df, df, q);
+          }
+          kahan_add(objS, objC, q);
         }
-        kahan_add(objS, objC, q);
       }
     }
     if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
@@ -258,6 +310,14 @@ cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s) {
 }
 
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
+  if (p.k <= kSmemScatterMax) {
+    int64_t blocks = (p.n + 256 * kScatterPerThread - 1) / (256 * kScatterPerThread);
+    const int64_t cap = (int64_t)num_sms() * 4;
+    if (blocks > cap) blocks = cap;
+    scatter_block_kernel<<<(int)blocks, 256, (size_t)p.k * sizeof(int), s>>>(p.assign, p.n, p.k, w.cursor, w.perm,
+                                                                              w.ctl);
+    return cudaGetLastError();
+  }
   int64_t blocks = (p.n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;

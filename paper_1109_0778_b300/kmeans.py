@@ -33,7 +33,7 @@ class KMeansError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("recheck", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -89,12 +89,14 @@ def _check(rc: int):
         raise KMeansError(rc, _lib.kmeans_last_error().decode())
 
 
-def make_opts(precision: str = "fp32", recheck: bool = True, stream=None, profile: bool = False) -> Opts:
+def make_opts(precision: str = "fp32", recheck: bool = True, stream=None, profile: bool = False,
+              warm_start: bool = False) -> Opts:
     o = Opts()
     _lib.kmeans_default_opts(ctypes.byref(o))
     o.precision = PRECISION[precision]
     o.recheck = 1 if recheck else 0
     o.profile = 1 if profile else 0
+    o.warm_start = 1 if warm_start else 0
     o.stream = stream
     return o
 
@@ -143,12 +145,12 @@ def alloc_outputs(X, C):
 
 
 def step(X, C, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True, stream=None,
-         profile=False) -> Outputs:
+         profile=False, warm_start=False) -> Outputs:
     """One Lloyd step on device tensors; C is updated in place (kmeans_step_ex)."""
     if assign is None:
         assign, sums, counts = alloc_outputs(X, C)
     n, d, k = _check_tensors(X, C, assign, sums, counts)
-    o = make_opts(precision, recheck, _stream_handle(stream), profile)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
     st = Stats()
     _check(_lib.kmeans_step_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
                                sums.data_ptr(), counts.data_ptr(), ctypes.byref(st)))
@@ -156,12 +158,12 @@ def step(X, C, assign=None, sums=None, counts=None, *, precision="fp32", recheck
 
 
 def run(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True,
-        stream=None, profile=False) -> Outputs:
+        stream=None, profile=False, warm_start=False) -> Outputs:
     """Up to ``iters`` Lloyd steps on device tensors; C is updated in place (kmeans_run_ex)."""
     if assign is None:
         assign, sums, counts = alloc_outputs(X, C)
     n, d, k = _check_tensors(X, C, assign, sums, counts)
-    o = make_opts(precision, recheck, _stream_handle(stream), profile)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
     st = Stats()
     _check(_lib.kmeans_run_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
                               sums.data_ptr(), counts.data_ptr(), int(iters), float(tol), ctypes.byref(st)))

@@ -22,15 +22,19 @@ def km():
 DEV = "cuda:0"
 
 
-def gpu_steps(km, orc, X, C0, steps, precision="fp32", rows=None):
-    """Teacher-forced per-step parity; returns the number of near-tie mismatches and the stats."""
+def gpu_steps(km, orc, X, C0, steps, precision="fp32", rows=None, warm=True):
+    """Teacher-forced per-step parity; returns the number of near-tie mismatches and the stats.
+
+    With ``warm`` every step after the first passes the previous step's assignment in
+    (warm_start), as the steps of a run do."""
     Xd = torch.from_numpy(X).to(DEV)
     Cd = torch.from_numpy(np.ascontiguousarray(C0, dtype=np.float32)).to(DEV)
+    assign, sums, counts = km.alloc_outputs(Xd, Cd)
     near = 0
     stats = []
-    for _ in range(steps):
+    for it in range(steps):
         C_in = Cd.cpu().numpy().astype(np.float64)
-        out = km.step(Xd, Cd, precision=precision)
+        out = km.step(Xd, Cd, assign, sums, counts, precision=precision, warm_start=warm and it > 0)
         a = out.assign.cpu().numpy()
         m, _ = parity.check_assign(orc, X, C_in, a, rows=rows)
         near += m
@@ -242,3 +246,78 @@ def test_full_size_fp32_workload(km, ref):
     parity.check_update(ref, X, C_in, a21, Cd.cpu().numpy(), o.sums.cpu().numpy(), o.counts.cpu().numpy())
     parity.check_objective(ref, X, C_in, a21, o.stats["objective"])
     assert o.stats["objective"] <= out.stats["objective"] * (1 + 1e-6)
+
+
+# ----------------------------------------------------------------------------- tensor-core path
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_tc_smoke(km, ref, precision):
+    X = synth.mixture(5, 1000, 16, 8, 10.0, 1.0)
+    near, stats = gpu_steps(km, ref, X, X[:8].copy(), 2, precision=precision)
+    assert near <= 2
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,d,k", [
+    (1, 1, 1), (5, 3, 5), (129, 2, 128), (4099, 33, 130), (2000, 17, 129), (3000, 256, 20),
+    (1500, 255, 300), (20037, 64, 256), (513, 96, 511), (700, 128, 700), (3333, 200, 1000),
+])
+def test_tc_shapes_ragged(km, ref, precision, n, d, k):
+    X = synth.mixture(2000 + n + d + k, n, d, max(k, 1), 5.0, 1.0)
+    near, stats = gpu_steps(km, ref, X, X[:k].copy(), 3, precision=precision)
+    assert near <= max(2, n // 1000)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_tc_precision_workload_sample(km, ref, precision):
+    """The first 65,536 points of the 4M x 128 x 1024 workload, 3 teacher-forced steps."""
+    w = WORKLOADS["prec_n4M_d128_k1024"]
+    X, C0 = synth.workload_data(w, rows=65536)
+    near, stats = gpu_steps(km, ref, X, C0, 3, precision=precision)
+    assert near <= 20
+    assert all(s["n_flagged"] < 65536 for s in stats)
+
+
+@pytest.mark.slow
+def test_tc_large_workload_sample(km, ref):
+    """The first 16,384 points of the 8M x 256 x 8192 workload with FP8, 2 teacher-forced steps."""
+    w = WORKLOADS["large_n8M_d256_k8192"]
+    X, C0 = synth.workload_data(w, rows=16384)
+    near, stats = gpu_steps(km, ref, X, C0, 2, precision="fp8")
+    assert near <= 20
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_tc_run_matches_free_running_oracle(km, ref, precision):
+    """Graph-captured runs (seeded from the second step on) against the free-running oracle."""
+    X = synth.mixture(77, 30000, 48, 40, 8.0, 1.0)
+    C0 = X[:40].copy()
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.run(Xd, Cd, 8, precision=precision)
+    r = ref.run(X, C0.astype(np.float64), 8)
+    assert out.stats["iters_done"] == 8
+    a = out.assign.cpu().numpy()
+    assert (a != r["assign"]).sum() <= 3
+    assert abs(out.stats["objective"] - r["objectives"][-1]) <= 1e-5 * r["objectives"][-1]
+
+
+def test_warm_start_ignores_bad_labels(km, ref):
+    X = synth.mixture(8, 3000, 24, 12, 6.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    for precision in ("fp32", "bf16", "fp8"):
+        Cd = torch.from_numpy(X[:12].copy()).to(DEV)
+        a, s, c = km.alloc_outputs(Xd, Cd)
+        a.copy_(torch.randint(-5, 20, (3000,), dtype=torch.int32))  # garbage, some out of range
+        C_in = Cd.cpu().numpy().astype(np.float64)
+        out = km.step(Xd, Cd, a, s, c, precision=precision, warm_start=True)
+        parity.check_assign(ref, X, C_in, out.assign.cpu().numpy())
+
+
+def test_tc_recheck_off_still_runs(km):
+    X = synth.mixture(3, 5000, 32, 20, 5.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(X[:20].copy()).to(DEV)
+    out = km.step(Xd, Cd, precision="bf16", recheck=False)
+    a = out.assign.cpu().numpy()
+    assert a.min() >= 0 and a.max() < 20 and out.counts.sum().item() == 5000
