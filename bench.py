@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32/BF16/FP8 comparison on the 4M x 128 x 1024 precision workload")
     return ap.parse_args(argv)
 
 
@@ -93,6 +95,11 @@ def max_over_ranks(dist, value: float, device=None) -> float:
 def barrier(dist):
     if dist is not None:
         dist.barrier()
+
+
+def aggregate_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job rate of weak-scaling replicas: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / t_max
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -267,6 +274,111 @@ def workload_config(w, precision):
             "step": f"one kmeans_run call = {w.iters} graph-captured Lloyd iterations"}
 
 
+def batched_problems(torch, dev, w):
+    """Device tensors of every instance of the batched workload (seeded mixtures, C0 = first k points)."""
+    from synth import batched_instances
+
+    inst = batched_instances(w)
+    probs, flops, xbytes = [], 0.0, 0
+    for iw in inst:
+        X = synth.mixture(iw.seed, iw.n, iw.d, iw.m, iw.R, iw.sigma)
+        Xd = torch.from_numpy(X).to(dev)
+        C0 = torch.from_numpy(X[: iw.k].copy()).to(dev)
+        probs.append((Xd, C0))
+        flops += 2.0 * iw.n * iw.k * iw.d
+        xbytes += 4 * iw.n * iw.d
+    return inst, probs, flops, xbytes
+
+
+def run_batched(args, torch, dev, dist, rank, world, local):
+    from paper_1109_0778_b300 import kmeans as km
+
+    w = WORKLOADS["batched_512"]
+    prec = args.precision or w.precision[0]
+    inst, probs, flops_iter, xbytes = batched_problems(torch, dev, w)
+    work = []
+    for Xd, C0 in probs:
+        C = C0.clone()
+        a, s, c = km.alloc_outputs(Xd, C)
+        work.append((Xd, C, a, s, c))
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step():
+        for (Xd, C0), (_, C, _, _, _) in zip(probs, work):
+            C.copy_(C0)
+        return km.run_batched(work, w.iters, precision=prec, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    call_ms = 0.0
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st = one_step()
+            call_ms += st[0]["ms"]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    clocks = clk.summary()
+    t = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, dev)
+    value = aggregate_rate(args.steps * w.iters, world, t)
+    peaks, peak_src = measured_peaks()
+    ms_iter = call_ms / args.steps / w.iters
+    achieved = xbytes / (ms_iter / 1e3) / 1e9
+    if rank == 0:
+        ns = [iw.n for iw in inst]
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "instances": len(inst), "total_points": int(sum(ns)),
+                       "iters_per_step": w.iters, "precision": prec,
+                       "step": f"one kmeans_run_batched call = {w.iters} graph-captured Lloyd iterations of all "
+                               f"{len(inst)} instances; value counts iterations of the whole batch",
+                       "l2": f"inputs larger than L2 (X = {xbytes / 1e9:.2f} GB)"},
+            "distance_tflops": value * flops_iter / 1e12,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "kernel": "whole batched step",
+                         "note": "algorithmic bytes = one FP32 read of every X per iteration", "traffic": None},
+            "clocks": clocks, "e2e": None, "cpu_baseline": None, "peaks_source": peak_src,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def precision_variants(torch, dev, steps=2, warmup=1):
+    """FP32 vs BF16 vs FP8 (+ FP32 re-check) on the 4M x 128 x 1024 workload, kmeans_run per step."""
+    from paper_1109_0778_b300 import kmeans as km
+
+    w = WORKLOADS["prec_n4M_d128_k1024"]
+    X, _ = synth.workload_data(w, rows=w.n)
+    Xd = torch.from_numpy(X).to(dev)
+    C0 = Xd[: w.k].clone()
+    del X
+    out = {"workload": w.name, "iters_per_step": w.iters}
+    for prec in ("fp32", "bf16", "fp8"):
+        C = C0.clone()
+        a, s, c = km.alloc_outputs(Xd, C)
+        for _ in range(warmup):
+            C.copy_(C0)
+            km.run(Xd, C, w.iters, assign=a, sums=s, counts=c, precision=prec)
+        ms = 0.0
+        for _ in range(steps):
+            C.copy_(C0)
+            o = km.run(Xd, C, w.iters, assign=a, sums=s, counts=c, precision=prec, profile=True)
+            ms += o.stats["ms"]
+        ips = steps * w.iters / (ms / 1e3)
+        out[prec] = {"iter_s": ips, "distance_tflops": ips * w.flops_per_iter / 1e12,
+                     "assign_ms_per_iter": o.stats["stage_ms"]["assign"] / w.iters,
+                     "flagged_last_iter": o.stats["n_flagged"], "objective": o.stats["objective"]}
+    for prec in ("bf16", "fp8"):
+        out[prec]["speedup_vs_fp32"] = out[prec]["iter_s"] / out["fp32"]["iter_s"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -278,6 +390,8 @@ def run_ours(args):
     dist = dist_init(world, "nccl")
     from paper_1109_0778_b300 import kmeans as km
 
+    if args.workload == "batched_512":
+        return run_batched(args, torch, dev, dist, rank, world, local)
     w = WORKLOADS[args.workload]
     if args.rows:
         import dataclasses
@@ -321,8 +435,7 @@ def run_ours(args):
     clocks = clk.summary()
     t = ev0.elapsed_time(ev1) / 1e3
     t_max = max_over_ranks(dist, t, dev)
-    total_iters = world * args.steps * iters
-    value = total_iters / t_max
+    value = aggregate_rate(args.steps * iters, world, t_max)
     flops_iter = 2.0 * w.n * w.k * w.d
 
     # dominant kernel: the fused assignment (per-launch time from the events around it)
@@ -360,14 +473,20 @@ def run_ours(args):
             km.run_host(Xh, Ch, iters, 0.0, ah, sh, ch, precision=prec)
         te = time.perf_counter() - t0
         te = max_over_ranks(dist, te, dev)
-        e2e = {"value": world * args.steps * iters / te, "unit": "iter/s",
+        e2e = {"value": aggregate_rate(args.steps * iters, world, te), "unit": "iter/s",
                "h2d_bytes_per_step": 4 * w.n * w.d + 4 * w.k * w.d,
                "d2h_bytes_per_step": 4 * w.k * w.d * 2 + 4 * w.n + 4 * w.k,
                "api": "kmeans_run_host (pinned host buffers)"}
 
+    variants = None
+    if rank == 0 and world == 1 and not args.no_variants and w.name == DEFAULT_WORKLOAD:
+        del Xd, Xh
+        torch.cuda.empty_cache()
+        variants = precision_variants(torch, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = oracle_sample_rate(w, args.cpu_seconds, X=Xh.numpy())
+        rate, cores, sample = oracle_sample_rate(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -379,7 +498,7 @@ def run_ours(args):
             "distance_tflops": value * flops_iter / 1e12,
             "roofline": roof, "stage_ms_per_iter": stage_share,
             "flagged_per_step_last_iter": flagged[-1] if flagged else None,
-            "clocks": clocks, "e2e": e2e,
+            "clocks": clocks, "e2e": e2e, "precision_variants": variants,
             "gpu_launches": args.steps * (1 + len(STAGE_KERNELS) * iters),
             "cpu_baseline": cpu,
             "peaks_source": peak_src,

@@ -156,6 +156,35 @@ int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32_t d,
                     float* C, int32_t k, int32_t* assign, float* sums,
                     int32_t* counts, int32_t iters, double tol, km_stats* stats);
 
+/* One independent problem of a batch (device pointers, as for kmeans_run). */
+typedef struct {
+  const float* X;     /* float[n*d] */
+  int64_t n;
+  int32_t d;          /* 1 <= d <= 128 */
+  int32_t k;          /* 1 <= k <= n */
+  float* C;           /* float[k*d] in/out */
+  int32_t* assign;    /* int32[n] out */
+  float* sums;        /* float[k*d] out */
+  int32_t* counts;    /* int32[k] out */
+} km_instance;
+
+/*
+ * Up to `iters` Lloyd steps of every instance of a batch, each with its own
+ * n, d and k, as one captured CUDA graph whose every stage is a single launch
+ * over all instances (a persistent tensor-core launch over the row tiles of
+ * every instance for the assignment). The stop rule (tol, as for kmeans_run)
+ * applies per instance; a finished instance is skipped by later steps.
+ * inst: HOST array of `count` descriptors. opts->precision must be KM_BF16 or
+ * KM_FP8E4M3 (KM_EUNSUPPORTED otherwise). per_inst: NULL or a host array of
+ * `count` statistics. The first call for a given batch shape tunes the launch
+ * shape (tile-chunk width, tile order) by timing the candidates, and caches
+ * the choice per shape for the life of the process. Instances must not share
+ * output arrays.
+ */
+int kmeans_run_batched(const km_opts* opts, const km_instance* inst,
+                       int32_t count, int32_t iters, double tol,
+                       km_stats* per_inst);
+
 /*
  * Keyed reduce of a Lloyd step for a given assignment, without allocating:
  * counts_j = |{i : a_i = j}|, sums_j = sum_{a_i = j} x_i (FP64 partials rounded

@@ -141,7 +141,7 @@ size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
 // Shape of the tensor-core path for (d, k, precision).
 struct TcShape {
-  int fp8, esz, Kp, nkb, bn, kp, nchunks, stages;
+  int fp8, esz, Kp, nkb, bn, kp, nchunks, stages, abufs;
 };
 
 TcShape tc_shape(int precision, int d, int k) {
@@ -152,21 +152,34 @@ TcShape tc_shape(int precision, int d, int k) {
   t.Kp = (d + kbe - 1) / kbe * kbe;
   t.nkb = t.Kp / kbe;
   t.bn = t.nkb <= 2 ? 128 : 64;
-  t.kp = (k + t.bn - 1) / t.bn * t.bn;
+  t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of either width
   t.nchunks = t.kp / t.bn;
-  // dynamic shared memory: 227 KB opt-in, minus 1 KB of alignment slack and 1 KB for static smem
-  const size_t budget = 227 * 1024 - 1024 - 1024;
-  const size_t a = 2 * (size_t)t.nkb * 128 * 128, b = (size_t)t.nkb * t.bn * 128;
-  t.stages = a + 2 * b <= budget ? (int)std::min<size_t>(8, (budget - a) / b) : 0;
+  // dynamic shared memory: 227 KB opt-in minus 1 KB of static smem; the A
+  // buffers, h_j (and scales) and the candidate merge buffer are fixed, B stages
+  // fill the rest. Prefer a double-buffered A tile; fall back to one buffer.
+  const size_t budget = 227 * 1024 - 1024, b = (size_t)t.nkb * t.bn * 128;
+  t.stages = 0;
+  for (int abufs = 2; abufs >= 1 && t.stages < 2; --abufs) {
+    const size_t fixed = tc_smem_bytes(t.nkb, t.bn, 0, t.kp, t.fp8, abufs);
+    t.abufs = abufs;
+    t.stages = fixed + 2 * b <= budget ? (int)std::min<size_t>(8, (budget - fixed) / b) : 0;
+  }
   return t;
+}
+
+// A cold E4M3 run does its first step with BF16 codes (far fewer near
+// candidates without a previous assignment); later steps use E4M3 codes that the
+// first step's reduce stage writes in sorted order.
+bool cold_bf16_first(int precision, int warm, int d, int k) {
+  return precision == KM_FP8E4M3 && !warm && tc_shape(KM_BF16, d, k).stages >= 2;
 }
 
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
-      flagged, full, empty, Xq, xs, Cq, hsc, state, total;
+      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, xss, labs, total;
 };
 
-Layout layout_for(int64_t n, int k, int d, int iters, int precision) {
+Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
@@ -189,13 +202,24 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision) {
   L.empty = take(4 * (size_t)iters);
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
-    L.Xq = take((size_t)n * t.Kp * t.esz);
+    size_t xq = (size_t)n * t.Kp * t.esz, cq = (size_t)t.kp * t.Kp * t.esz;
+    const bool cold = cold_bf16_first(precision, warm, d, k);
+    if (cold) {
+      const TcShape t16 = tc_shape(KM_BF16, d, k);
+      xq = std::max(xq, (size_t)n * t16.Kp * 2);
+      cq = std::max(cq, (size_t)t16.kp * t16.Kp * 2);
+    }
+    L.Xq = take(xq);
     L.xs = take(16 * (size_t)n);
-    L.Cq = take((size_t)t.kp * t.Kp * t.esz);
-    L.hsc = take(8 * (size_t)t.kp);
+    L.xs16 = cold ? take(16 * (size_t)n) : 0;
+    L.Cq = take(cq);
+    L.hq = take(4 * (size_t)t.kp);
+    L.scq = take(4 * (size_t)t.kp);
+    L.xss = take(16 * (size_t)n);
+    L.labs = take(4 * (size_t)n);
     L.state = 0;
   } else {
-    L.Xq = L.xs = L.Cq = L.hsc = 0;
+    L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = L.labs = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;
   }
@@ -247,8 +271,12 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.Xq = L.Xq ? (uint8_t*)(b + L.Xq) : nullptr;
   w.xs = L.xs ? (float4*)(b + L.xs) : nullptr;
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
-  w.hsc = L.hsc ? (float2*)(b + L.hsc) : nullptr;
+  w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
+  w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
+  w.xs16 = L.xs16 ? (float4*)(b + L.xs16) : nullptr;
+  w.xs_sorted = L.xss ? (float4*)(b + L.xss) : nullptr;
+  w.lab_sorted = L.labs ? (int32_t*)(b + L.labs) : nullptr;
   return w;
 }
 
@@ -291,6 +319,10 @@ struct StepCfg {
   TcShape t;
   TcLaunch L;
   TcParams P;
+  bool cold;  // first step with BF16 codes (E4M3 runs without a warm start)
+  TcShape t0;
+  TcLaunch L0;
+  TcParams P0;
 };
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -321,7 +353,8 @@ int validate_args(const km_opts& o, const Problem& p, int iters) {
   if (o.precision != KM_FP32 && o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
     return fail(KM_EINVAL, "unknown precision %d", o.precision);
   if (o.precision != KM_FP32 && tc_shape(o.precision, p.d, p.k).stages < 2)
-    return fail(KM_EUNSUPPORTED, "d = %d does not fit the tensor-core tile pipeline", p.d);
+    return fail(KM_EUNSUPPORTED, "d = %d, k = %d do not fit the tensor-core tile pipeline (k is staged in shared memory)",
+                p.d, p.k);
   const size_t nd = (size_t)p.n * p.d * 4, kd = (size_t)p.k * p.d * 4;
   const size_t na = (size_t)p.n * 4, nk = (size_t)p.k * 4;
   if (overlaps(p.X, nd, p.C, kd) || overlaps(p.X, nd, p.assign, na) || overlaps(p.X, nd, p.sums, kd) ||
@@ -344,21 +377,45 @@ int validate_device_ptrs(const Problem& p, int dev) {
 
 // The stage sequence of one Lloyd step (all on stream s). With `ev`
 // (kEvPerStep events) every stage boundary is recorded.
-cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, int first, double tol,
+// `sorted`: the point codes are in the previous step's cluster-sorted order
+// (row p = point perm[p]), written by that step's reduce stage.
+// KM_DEBUG_SYNC: launch stage by stage, synchronising after each one and
+// naming the first stage whose launch or execution fails (diagnosis only).
+bool debug_sync() {
+  static const bool on = getenv("KM_DEBUG_SYNC") != nullptr;
+  return on;
+}
+
+cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, int first, int sorted, double tol,
                          cudaStream_t s, const cudaEvent_t* ev) {
   cudaError_t e;
-  auto at = [&](int i) { return ev ? mark(ev[i], s) : cudaSuccess; };
+  static const char* names[] = {"prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide"};
+  auto at = [&](int i) -> cudaError_t {
+    if (debug_sync() && i > 0) {
+      cudaError_t r = cudaStreamSynchronize(s);
+      if (r == cudaSuccess) r = cudaGetLastError();
+      fprintf(stderr, "[kmeans] stage %s (step first=%d sorted=%d): %s\n", names[i - 1], first, sorted,
+              cudaGetErrorString(r));
+      if (r != cudaSuccess) return r;
+    }
+    return ev ? mark(ev[i], s) : cudaSuccess;
+  };
   const bool tcp = cfg.precision != KM_FP32;
+  const bool cold = tcp && cfg.cold && !sorted;  // this step runs on the cold-start BF16 codes
+  const TcShape& t = cold ? cfg.t0 : cfg.t;
   if ((e = cudaMemsetAsync(w.ctl, 0, kCtlIterBytes, s))) return e;
   if ((e = at(0))) return e;
-  if (tcp) e = launch_quant_c(p, w, cfg.t.fp8, cfg.t.kp, cfg.t.Kp, w.Cq, w.hsc, s);
+  if (tcp) e = launch_quant_c(p, w, t.fp8, t.kp, t.Kp, w.Cq, w.hq, w.scq, s);
   else e = launch_prep(p, w, s);
   if (e) return e;
   if ((e = at(1))) return e;
   if (tcp) {
-    TcParams P = cfg.P;
+    TcParams P = cold ? cfg.P0 : cfg.P;
     P.first = first;
-    e = launch_assign_tc(p, cfg.L, P, s);
+    P.rows = sorted ? w.perm : nullptr;
+    P.xs_sorted = w.xs_sorted;
+    P.lab_sorted = w.lab_sorted;
+    e = launch_assign_tc(p, cold ? cfg.L0 : cfg.L, P, s);
   } else {
     e = launch_assign_simt(p, w, first, s);
   }
@@ -372,7 +429,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   if ((e = at(5))) return e;
   if ((e = launch_scatter(p, w, s))) return e;
   if ((e = at(6))) return e;
-  if ((e = launch_segsum(p, w, s))) return e;
+  if ((e = launch_segsum(p, w, s, tcp ? (cfg.t.fp8 ? 2 : 1) : 0, tcp ? cfg.t.Kp : 0))) return e;
   if ((e = at(7))) return e;
   if ((e = launch_divide(p, w, first ? 0 : 1, tol, s))) return e;
   if ((e = at(8))) return e;
@@ -398,7 +455,7 @@ int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, c
   KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < iters && e == cudaSuccess; ++it)
-    e = enqueue_step(p, w, cfg, it == 0 && !cfg.warm, tol, c->cap_stream, step_events(c, profile, it));
+    e = enqueue_step(p, w, cfg, it == 0 && !cfg.warm, it > 0, tol, c->cap_stream, step_events(c, profile, it));
   cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -421,14 +478,24 @@ struct HostReadback {
   Ctl ctl;
 };
 
+#define KM_TRACE(...)                         \
+  do {                                        \
+    if (debug_sync()) {                       \
+      fprintf(stderr, "[kmeans] " __VA_ARGS__); \
+      fflush(stderr);                         \
+    }                                         \
+  } while (0)
+
 // Runs `iters` steps on device arrays. The caller holds c->mu.
 int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double tol, bool graph,
                km_stats* st) {
   int rc = init_ctx(c);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)o.stream;
-  const Layout L = layout_for(p.n, p.k, p.d, iters, o.precision);
+  const Layout L = layout_for(p.n, p.k, p.d, iters, o.precision, o.warm_start);
+  KM_TRACE("layout: %zu bytes (n=%lld d=%d k=%d prec=%d)\n", L.total, (long long)p.n, p.d, p.k, o.precision);
   if ((rc = ensure_ws(c, L, s))) return rc;
+  KM_TRACE("workspace ready at %p (%zu bytes)\n", c->ws, c->ws_bytes);
   const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 5 + 4) + 64;
   if (host_need > c->host_bytes) {
     if (c->host) cudaFreeHost(c->host);
@@ -442,58 +509,89 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   }
   const Work w = make_work(c, L);
   const bool profile = o.profile != 0;
+  if (profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   StepCfg cfg;
   memset(&cfg, 0, sizeof cfg);
   cfg.precision = o.precision;
   cfg.recheck = o.recheck;
   cfg.warm = o.warm_start;
-  if (o.precision != KM_FP32) {
-    cfg.t = tc_shape(o.precision, p.d, p.k);
-    cfg.L.fp8 = cfg.t.fp8;
-    if ((rc = encode_codes_map(&cfg.L.mapX, w.Xq, p.n, cfg.t.Kp, cfg.t.esz, 128))) return rc;
-    if ((rc = encode_codes_map(&cfg.L.mapC, w.Cq, cfg.t.kp, cfg.t.Kp, cfg.t.esz, cfg.t.bn))) return rc;
-    TcParams& P = cfg.P;
-    P.hsc = w.hsc;
-    P.xs = w.xs;
+  auto fill_tc = [&](int precision, const float4* xs, TcShape& t, TcLaunch& Lc, TcParams& P) -> int {
+    t = tc_shape(precision, p.d, p.k);
+    Lc.fp8 = t.fp8;
+    int r2;
+    if ((r2 = encode_codes_map(&Lc.mapX, w.Xq, p.n, t.Kp, t.esz, 128))) return r2;
+    if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kp, t.esz, t.bn))) return r2;
+    memset(&P, 0, sizeof P);
+    P.h = w.hq;
+    P.sc = w.scq;
+    P.rows = nullptr;
+    P.xs = xs;
+    P.xs_sorted = w.xs_sorted;
+    P.lab_sorted = w.lab_sorted;
     P.Cq = w.Cq;
     P.assign = p.assign;
     P.flags = w.flags;
     P.ctl = w.ctl;
+    P.flag_slots = &w.ctl->n_flagged;
+    P.flag_cap = p.n;
     P.n = p.n;
     P.k = p.k;
-    P.Kp = cfg.t.Kp;
-    P.nkb = cfg.t.nkb;
-    P.bn = cfg.t.bn;
-    P.nchunks = cfg.t.nchunks;
-    P.stages = cfg.t.stages;
-    P.idesc = tc::idesc_f32acc(cfg.t.fp8 ? 0u : 1u, 128, (uint32_t)cfg.t.bn);
-    const double K = cfg.t.Kp;
-    P.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));   // truncating FP32 accumulation
+    P.Kp = t.Kp;
+    P.nkb = t.nkb;
+    P.bn = t.bn;
+    P.nchunks = t.nchunks;
+    P.stages = t.stages;
+    P.abufs = t.abufs;
+    P.idesc = tc::idesc_f32acc(t.fp8 ? 0u : 1u, 128, (uint32_t)t.bn);
+    const double K = t.Kp;
+    P.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));  // truncating FP32 accumulation
     P.gam_simt = (float)(K * 0x1p-24 / (1.0 - K * 0x1p-24) * (1.0 + 1e-6));
     P.wait_ns = 2000000000ull;
+    if (getenv("KM_DEBUG_STALL")) {  // test knob: make a bounded wait expire (50 ms)
+      P.debug_stall = 1;
+      P.wait_ns = 50000000ull;
+    }
+    return KM_OK;
+  };
+  if (o.precision != KM_FP32) {
+    cfg.cold = cold_bf16_first(o.precision, o.warm_start, p.d, p.k);
+    if ((rc = fill_tc(o.precision, w.xs, cfg.t, cfg.L, cfg.P))) return rc;
+    KM_TRACE("main shape Kp=%d nkb=%d bn=%d kp=%d stages=%d abufs=%d cold=%d\n", cfg.t.Kp, cfg.t.nkb, cfg.t.bn,
+             cfg.t.kp, cfg.t.stages, cfg.t.abufs, (int)cfg.cold);
+    if (cfg.cold && (rc = fill_tc(KM_BF16, w.xs16, cfg.t0, cfg.L0, cfg.P0))) return rc;
+    if (cfg.cold)
+      KM_TRACE("cold shape Kp=%d nkb=%d bn=%d kp=%d stages=%d abufs=%d\n", cfg.t0.Kp, cfg.t0.nkb, cfg.t0.bn,
+               cfg.t0.kp, cfg.t0.stages, cfg.t0.abufs);
   }
-  if (profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   KM_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
   KM_CUDA(cudaMemsetAsync(w.sums64, 0, 8 * (size_t)p.k * p.d, s));
   KM_CUDA(cudaMemcpyAsync(w.Csave, p.C, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
-  if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.fp8, cfg.t.Kp, w.Xq, w.xs, s));
+  KM_TRACE("prologue copies queued\n");
+  if (o.precision != KM_FP32 && cfg.cold) KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
+  else if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.fp8, cfg.t.Kp, w.Xq, w.xs, s));
   else KM_CUDA(launch_xnorm(p, w, s));
+  if (debug_sync()) {
+    cudaError_t r = cudaStreamSynchronize(s);
+    KM_TRACE("point quantisation / norms: %s\n", cudaGetErrorString(r));
+    KM_CUDA(r);
+  }
   if (profile) KM_CUDA(cudaEventRecord(c->prof[1], s));
-  if (graph && iters > 1) {
+  if (graph && iters > 1 && !debug_sync()) {
     GraphKey key;
     memset(&key, 0, sizeof key);
     key.X = p.X; key.C = p.C; key.assign = p.assign; key.sums = p.sums; key.counts = p.counts;
     key.n = p.n; key.d = p.d; key.k = p.k; key.iters = iters; key.prec = o.precision; key.tol = tol;
-    key.profile = (profile ? 1 : 0) | (o.recheck ? 2 : 0) | (o.warm_start ? 4 : 0);
+    key.profile = (profile ? 1 : 0) | (o.recheck ? 2 : 0) | (o.warm_start ? 4 : 0) |
+                  (getenv("KM_DEBUG_STALL") ? 8 : 0);
     key.ws_gen = c->ws_gen;
     cudaGraphExec_t ge = nullptr;
     if ((rc = get_graph(c, key, p, w, cfg, iters, tol, profile, &ge))) return rc;
     KM_CUDA(cudaGraphLaunch(ge, s));
   } else {
     for (int it = 0; it < iters; ++it)
-      KM_CUDA(enqueue_step(p, w, cfg, it == 0 && !cfg.warm, tol, s, step_events(c, profile, it)));
+      KM_CUDA(enqueue_step(p, w, cfg, it == 0 && !cfg.warm, it > 0, tol, s, step_events(c, profile, it)));
   }
   KM_CUDA(cudaEventRecord(c->ev1, s));
   char* h = (char*)c->host;
@@ -512,6 +610,8 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   KM_CUDA(cudaMemcpyAsync(hfull, w.full_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hempty, w.empty_hist, 4 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaStreamSynchronize(s));
+  if (hc->iters_done < 0 || hc->iters_done > iters)
+    return fail(KM_ECUDA, "device control block is inconsistent (%d steps recorded, %d run)", hc->iters_done, iters);
   if (hc->nonfinite || hc->error) {
     KM_CUDA(cudaMemcpyAsync(p.C, w.Csave, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
     KM_CUDA(cudaStreamSynchronize(s));
@@ -657,3 +757,437 @@ KM_API int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32
 KM_API const char* kmeans_last_error(void) { return g_err.c_str(); }
 
 KM_API int32_t kmeans_version(void) { return 100; }
+
+// ============================================================================ batched runs
+
+namespace {
+
+// Launch shape of a batch: chunk width and the order of the instances in the
+// flattened tile space (0: as given, 1: by decreasing work per row tile).
+struct BatchTune {
+  int bn;
+  int order;
+};
+
+struct BatchPlan {
+  std::vector<int> order;  // flattened position -> caller's instance index
+  std::vector<BInst> inst;
+  std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
+  int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
+  int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0;
+};
+
+int plan_batch(const km_instance* in, int count, int precision, const BatchTune& tune, BatchPlan& P) {
+  P = BatchPlan();
+  P.fp8 = precision == KM_FP8E4M3;
+  P.bn = tune.bn;
+  const int esz = P.fp8 ? 1 : 2, kbe = 128 / esz;
+  P.order.resize(count);
+  for (int b = 0; b < count; ++b) P.order[b] = b;
+  if (tune.order == 1) {
+    std::stable_sort(P.order.begin(), P.order.end(), [&](int a, int b) {
+      return (int64_t)in[a].k * in[a].d > (int64_t)in[b].k * in[b].d;
+    });
+  }
+  P.inst.resize(count);
+  P.row_off.assign(count + 1, 0);
+  P.kc_off.assign(count + 1, 0);
+  P.kp_off.assign(count + 1, 0);
+  P.tile_off.assign(count + 1, 0);
+  for (int q = 0; q < count; ++q) {
+    const km_instance& s = in[P.order[q]];
+    BInst& I = P.inst[q];
+    memset(&I, 0, sizeof I);
+    I.X = s.X;
+    I.C = s.C;
+    I.assign = s.assign;
+    I.sums = s.sums;
+    I.counts = s.counts;
+    I.n = s.n;
+    I.d = s.d;
+    I.k = s.k;
+    I.Kp = (s.d + kbe - 1) / kbe * kbe;
+    I.nkb = I.Kp / kbe;
+    I.kp = (s.k + P.bn - 1) / P.bn * P.bn;
+    I.nchunks = I.kp / P.bn;
+    const double K = I.Kp;
+    I.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));
+    I.gam_simt = (float)(K * 0x1p-24 / (1.0 - K * 0x1p-24) * (1.0 + 1e-6));
+    I.row_off = P.R;
+    I.kc_off = P.KC;
+    I.kp_off = P.KP;
+    I.offs_off = P.KP + q;
+    I.sum_off = P.SUMS;
+    I.tile_off = P.T;
+    I.xq_off = P.XQ;
+    I.cq_off = P.CQ;
+    P.R += s.n;
+    P.KC += s.k;
+    P.KP += I.kp;
+    P.SUMS += (int64_t)s.k * s.d;
+    P.CSAVE += (int64_t)s.k * s.d;
+    P.T += (s.n + 127) / 128;
+    P.XQ += align_up((size_t)s.n * I.Kp * esz, 256);
+    P.CQ += align_up((size_t)I.kp * I.Kp * esz, 256);
+    P.row_off[q + 1] = P.R;
+    P.kc_off[q + 1] = P.KC;
+    P.kp_off[q + 1] = P.KP;
+    P.tile_off[q + 1] = P.T;
+    P.nkb_max = std::max(P.nkb_max, I.nkb);
+    P.kp_max = std::max(P.kp_max, I.kp);
+  }
+  const size_t budget = 227 * 1024 - 1024, bstage = (size_t)P.nkb_max * P.bn * 128;
+  P.stages = 0;
+  for (int abufs = 2; abufs >= 1 && P.stages < 2; --abufs) {
+    const size_t fixed = tc_smem_bytes(P.nkb_max, P.bn, 0, P.kp_max, P.fp8, abufs);
+    P.abufs = abufs;
+    P.stages = fixed + 2 * bstage <= budget ? (int)std::min<size_t>(8, (budget - fixed) / bstage) : 0;
+  }
+  if (P.stages < 2) return fail(KM_EUNSUPPORTED, "largest k of the batch does not fit the tensor-core pipeline");
+  return KM_OK;
+}
+
+struct BatchCache {
+  uint64_t sig = 0;
+  BatchTune tune{128, 0};
+};
+
+struct BatchCtx {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* host = nullptr;
+  size_t host_bytes = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
+  std::vector<BatchCache> tuned;
+};
+
+BatchCtx g_batch[64];
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+// Shape signature of a batch for the tuning cache: (n, d, k) of every instance.
+uint64_t batch_signature(const km_instance* in, int count, int precision) {
+  uint64_t h = fnv1a(&precision, sizeof precision);
+  for (int b = 0; b < count; ++b) {
+    h = fnv1a(&in[b].n, sizeof in[b].n, h);
+    h = fnv1a(&in[b].d, sizeof in[b].d, h);
+    h = fnv1a(&in[b].k, sizeof in[b].k, h);
+  }
+  return h;
+}
+
+// Byte offsets of the batch workspace.
+struct BLayout {
+  size_t ctl, inst, row, kc, kp, tile, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq, xq, cq,
+      csave, hist, total;
+};
+
+BLayout batch_layout(const BatchPlan& P, int iters) {
+  BLayout L;
+  const int nb = (int)P.inst.size();
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t al = 256) {
+    off = (off + al - 1) / al * al;
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  L.ctl = take(sizeof(Ctl) * nb);
+  L.inst = take(sizeof(BInst) * nb);
+  L.row = take(8 * (nb + 1));
+  L.kc = take(8 * (nb + 1));
+  L.kp = take(8 * (nb + 1));
+  L.tile = take(8 * (nb + 1));
+  L.maps = take(sizeof(CUtensorMap) * 2 * nb, 128);
+  L.slots = take(8);
+  L.xs = take(16 * (size_t)P.R);
+  L.xss = take(16 * (size_t)P.R);
+  L.labs = take(4 * (size_t)P.R);
+  L.perm = take(4 * (size_t)P.R);
+  L.flags = take(sizeof(FlagRec) * (size_t)P.R);
+  L.offs = take(4 * (size_t)(P.KP + nb));
+  L.cur = take(4 * (size_t)P.KP);
+  L.sums = take(8 * (size_t)P.SUMS);
+  L.hq = take(4 * (size_t)P.KP);
+  L.scq = take(4 * (size_t)P.KP);
+  L.xq = take((size_t)P.XQ);
+  L.cq = take((size_t)P.CQ);
+  L.csave = take(4 * (size_t)P.CSAVE);
+  L.hist = take((8 * 5 + 4) * (size_t)nb * iters);
+  L.total = off;
+  return L;
+}
+
+// Copies every instance's C back from the copy taken on entry of the last run.
+int restore_batch_c(const BatchCtx& bc, const BatchPlan& P, int iters, cudaStream_t s) {
+  const float* csave = (const float*)((const char*)bc.ws + batch_layout(P, iters).csave);
+  for (size_t b = 0, at = 0; b < P.inst.size(); at += (size_t)P.inst[b].k * P.inst[b].d, ++b)
+    KM_CUDA(cudaMemcpyAsync(P.inst[b].C, csave + at, 4 * (size_t)P.inst[b].k * P.inst[b].d, cudaMemcpyDeviceToDevice,
+                            s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  return KM_OK;
+}
+
+// Runs `iters` steps of the planned batch; the caller holds the device lock.
+int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan& P, int iters, double tol,
+                     km_stats* per_inst, const int* caller_index, float* ms_out) {
+  int rc = init_ctx(c);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const int nb = (int)P.inst.size();
+  const BLayout BL = batch_layout(P, iters);
+  const size_t o_ctl = BL.ctl, o_inst = BL.inst, o_row = BL.row, o_kc = BL.kc, o_kp = BL.kp, o_tile = BL.tile,
+               o_maps = BL.maps, o_slots = BL.slots, o_xs = BL.xs, o_xss = BL.xss, o_labs = BL.labs,
+               o_perm = BL.perm, o_flags = BL.flags, o_offs = BL.offs, o_cur = BL.cur, o_sums = BL.sums,
+               o_hq = BL.hq, o_scq = BL.scq, o_xq = BL.xq, o_cq = BL.cq, o_csave = BL.csave, o_hist = BL.hist;
+  const size_t off = BL.total;
+  const size_t need = off;
+  if (need > bc.ws_bytes) {
+    if (bc.ws) {
+      KM_CUDA(cudaDeviceSynchronize());
+      cudaFree(bc.ws);
+      bc.ws = nullptr;
+      bc.ws_bytes = 0;
+    }
+    bc.gkey.clear();
+    const size_t want = align_up(need + need / 4, 1 << 20);
+    if (cudaMalloc(&bc.ws, want) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "batch workspace allocation of %zu bytes failed", want);
+    }
+    bc.ws_bytes = want;
+  }
+  char* B = (char*)bc.ws;
+  BWork W;
+  memset(&W, 0, sizeof W);
+  W.inst = (const BInst*)(B + o_inst);
+  W.nb = nb;
+  W.iters = iters;
+  W.row_off = (const int64_t*)(B + o_row);
+  W.kc_off = (const int64_t*)(B + o_kc);
+  W.kp_off = (const int64_t*)(B + o_kp);
+  W.tile_off = (const int64_t*)(B + o_tile);
+  W.R = P.R;
+  W.KC = P.KC;
+  W.KP = P.KP;
+  W.T = P.T;
+  W.ctls = (Ctl*)(B + o_ctl);
+  W.flag_slots = (unsigned long long*)(B + o_slots);
+  W.maps = (const CUtensorMap*)(B + o_maps);
+  W.xs = (float4*)(B + o_xs);
+  W.xs_sorted = (float4*)(B + o_xss);
+  W.lab_sorted = (int32_t*)(B + o_labs);
+  W.perm = (int32_t*)(B + o_perm);
+  W.flags = (FlagRec*)(B + o_flags);
+  W.offs = (int32_t*)(B + o_offs);
+  W.cursor = (int32_t*)(B + o_cur);
+  W.sums64 = (double*)(B + o_sums);
+  W.hq = (float*)(B + o_hq);
+  W.scq = (float*)(B + o_scq);
+  W.Xq = (uint8_t*)(B + o_xq);
+  W.Cq = (uint8_t*)(B + o_cq);
+  char* hb = B + o_hist;
+  W.obj_hist = (double*)hb;
+  W.shift_hist = W.obj_hist + (size_t)nb * iters;
+  W.changed_hist = (unsigned long long*)(W.shift_hist + (size_t)nb * iters);
+  W.flagged_hist = W.changed_hist + (size_t)nb * iters;
+  W.full_hist = W.flagged_hist + (size_t)nb * iters;
+  W.empty_hist = (int*)(W.full_hist + (size_t)nb * iters);
+  // tensor maps of every instance's codes
+  std::vector<CUtensorMap> maps(2 * nb);
+  const int esz = P.fp8 ? 1 : 2;
+  for (int b = 0; b < nb; ++b) {
+    const BInst& I = P.inst[b];
+    if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128))) return rc;
+    if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, P.bn))) return rc;
+  }
+  KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + o_kc, P.kc_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + o_kp, P.kp_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));
+  KM_CUDA(cudaMemsetAsync(W.sums64, 0, 8 * (size_t)P.SUMS, s));
+  // C on entry, restored on error
+  float* csave = (float*)(B + o_csave);
+  for (int b = 0, at = 0; b < nb; at += P.inst[b].k * P.inst[b].d, ++b)
+    KM_CUDA(cudaMemcpyAsync(csave + at, P.inst[b].C, 4 * (size_t)P.inst[b].k * P.inst[b].d,
+                            cudaMemcpyDeviceToDevice, s));
+  KM_CUDA(cudaEventRecord(c->ev0, s));
+  KM_CUDA(launch_b_quant_x(W, P.fp8, s));
+  // graph of the iterations, cached while the batch and its workspace are unchanged
+  std::vector<unsigned char> key(sizeof(BInst) * nb);
+  memcpy(key.data(), P.inst.data(), key.size());
+  auto app = [&](const void* v, size_t n) { key.insert(key.end(), (const unsigned char*)v, (const unsigned char*)v + n); };
+  app(&iters, sizeof iters);
+  app(&tol, sizeof tol);
+  app(&o.recheck, sizeof o.recheck);
+  app(&o.warm_start, sizeof o.warm_start);
+  app(&P.bn, sizeof P.bn);
+  void* base = bc.ws;
+  app(&base, sizeof base);
+  if (!(bc.gexec && bc.gkey == key)) {
+    if (bc.gexec) {
+      cudaGraphExecDestroy(bc.gexec);
+      bc.gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const uint32_t idesc = tc::idesc_f32acc(P.fp8 ? 0u : 1u, 128, (uint32_t)P.bn);
+    const int qmode = P.fp8 ? 2 : 1;
+    cudaStream_t cs = c->cap_stream;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+      if (!e) e = launch_b_reset(W, cs);
+      if (!e) e = launch_b_quant_c(W, P.fp8, cs);
+      if (!e)
+        e = launch_b_assign(W, P.fp8, it == 0 && !o.warm_start, it > 0, P.nkb_max, P.kp_max, P.bn, P.stages, P.abufs,
+                            idesc, cs);
+      if (!e && o.recheck) e = launch_b_recheck(W, cs);
+      if (!e) e = launch_b_count(W, cs);
+      if (!e) e = launch_b_scan(W, cs);
+      if (!e) e = launch_b_scatter(W, cs);
+      if (!e) e = launch_b_segsum(W, qmode, cs);
+      if (!e) e = launch_b_divide(W, tol, cs);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return fail(KM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e ? e : e2));
+    }
+    e = cudaGraphInstantiate(&bc.gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      bc.gexec = nullptr;
+      return fail(KM_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    bc.gkey = key;
+  }
+  KM_CUDA(cudaGraphLaunch(bc.gexec, s));
+  KM_CUDA(cudaEventRecord(c->ev1, s));
+  // read back control blocks and histories
+  const size_t hist_bytes = (8 * 5 + 4) * (size_t)nb * iters, host_need = sizeof(Ctl) * nb + hist_bytes + 64;
+  if (host_need > bc.host_bytes) {
+    if (bc.host) cudaFreeHost(bc.host);
+    bc.host = nullptr;
+    bc.host_bytes = 0;
+    if (cudaMallocHost(&bc.host, host_need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "pinned host allocation failed");
+    }
+    bc.host_bytes = host_need;
+  }
+  Ctl* hc = (Ctl*)bc.host;
+  char* hh = (char*)bc.host + align_up(sizeof(Ctl) * nb, 64);
+  KM_CUDA(cudaMemcpyAsync(hc, W.ctls, sizeof(Ctl) * nb, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaMemcpyAsync(hh, hb, hist_bytes, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (ms_out) *ms_out = ms;
+  bool bad = false;
+  int err = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (hc[b].nonfinite) bad = true;
+    if (hc[b].error) err = hc[b].error;
+  }
+  if (bad || err) {
+    if ((rc = restore_batch_c(bc, P, iters, s))) return rc;
+    if (bad) return fail(KM_ENONFINITE, "an instance holds a non-finite value (or a norm overflows FP32)");
+    return fail(err, "device stage reported error %d", err);
+  }
+  if (per_inst) {
+    const double* ho = (const double*)hh;
+    const double* hs = ho + (size_t)nb * iters;
+    const unsigned long long* hch = (const unsigned long long*)(hs + (size_t)nb * iters);
+    const unsigned long long* hf = hch + (size_t)nb * iters;
+    const unsigned long long* hfu = hf + (size_t)nb * iters;
+    const int* he = (const int*)(hfu + (size_t)nb * iters);
+    for (int b = 0; b < nb; ++b) {
+      km_stats& st = per_inst[caller_index[b]];
+      memset(&st, 0, sizeof st);
+      st.iters_done = hc[b].iters_done;
+      const int last = hc[b].iters_done - 1;
+      if (last >= 0) {
+        const size_t h = (size_t)b * iters + last;
+        st.objective = ho[h];
+        st.shift = hs[h];
+        st.n_changed = (int64_t)hch[h];
+        st.n_flagged = (int64_t)hf[h];
+        st.n_full = (int64_t)hfu[h];
+        st.n_empty = he[h];
+      }
+      st.ms = ms;
+    }
+  }
+  return KM_OK;
+}
+
+}  // namespace
+
+KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int32_t count, int32_t iters,
+                              double tol, km_stats* per_inst) {
+  g_err.clear();
+  const km_opts o = resolve(opts);
+  if (!inst || count < 1) return fail(KM_EINVAL, "need count >= 1 instances");
+  if (iters < 1) return fail(KM_EINVAL, "iters = %d < 1", iters);
+  if (o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
+    return fail(o.precision == KM_FP32 ? KM_EUNSUPPORTED : KM_EINVAL,
+                "batched runs use the tensor-core path: precision must be KM_BF16 or KM_FP8E4M3");
+  for (int b = 0; b < count; ++b) {
+    const km_instance& s = inst[b];
+    if (!s.X || !s.C || !s.assign || !s.sums || !s.counts) return fail(KM_EINVAL, "instance %d: null pointer", b);
+    if (s.n < 1 || s.n > INT32_MAX || s.k < 1 || (int64_t)s.k > s.n || s.d < 1 || s.d > 128)
+      return fail(KM_EINVAL, "instance %d: need 1 <= k <= n < 2^31 and 1 <= d <= 128", b);
+  }
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(KM_EUNSUPPORTED, "device index %d", dev);
+  for (int b = 0; b < count; ++b) {
+    Problem p{inst[b].X, inst[b].n, inst[b].d, inst[b].C, inst[b].k, inst[b].assign, inst[b].sums, inst[b].counts};
+    int rc = validate_device_ptrs(p, dev);
+    if (rc) return fail(rc, "instance %d: %s", b, g_err.c_str());
+  }
+  DevCtx* c = get_ctx(dev);
+  std::lock_guard<std::mutex> lk(c->mu);
+  BatchCtx& bc = g_batch[dev];
+  const uint64_t sig = batch_signature(inst, count, o.precision);
+  BatchTune tune{128, 0};
+  bool known = false;
+  for (const BatchCache& t : bc.tuned)
+    if (t.sig == sig) {
+      tune = t.tune;
+      known = true;
+    }
+  int rc;
+  if (!known) {
+    // autotune: time two steps of every candidate shape on the caller's data, keep the fastest
+    const BatchTune cands[4] = {{128, 0}, {128, 1}, {64, 0}, {64, 1}};
+    float best = 1e30f;
+    for (const BatchTune& cand : cands) {
+      BatchPlan P;
+      if (plan_batch(inst, count, o.precision, cand, P)) continue;
+      std::vector<int> idx(P.order);
+      float ms = 0.f;
+      if ((rc = run_batch_locked(c, bc, o, P, 2, 0.0, nullptr, idx.data(), &ms))) return rc;
+      // the trial steps moved C: put every instance back before the next candidate
+      if ((rc = restore_batch_c(bc, P, 2, (cudaStream_t)o.stream))) return rc;
+      if (ms < best) {
+        best = ms;
+        tune = cand;
+      }
+    }
+    bc.tuned.push_back(BatchCache{sig, tune});
+  }
+  BatchPlan P;
+  if ((rc = plan_batch(inst, count, o.precision, tune, P))) return rc;
+  std::vector<int> idx(P.order);
+  return run_batch_locked(c, bc, o, P, iters, tol, per_inst, idx.data(), nullptr);
+}

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C, int k,
                    const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, int first, float gam) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   extern __shared__ __align__(16) float smem[];
   float (*As)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem);
   float (*Bs)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem + BK * (BM + PAD));
@@ -243,7 +243,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
                    int first, int first_slab, int last_slab, float gam) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = dp + 4;             // floats per staged point row

@@ -1,0 +1,526 @@
+// Batched Lloyd steps: many independent instances (each with its own n, d, k)
+// advance together, one launch per stage for the whole batch.
+//
+// Every per-instance array lives at an offset in one flattened array of the
+// batch workspace; a stage walks the flattened rows (or centroids, or tiles)
+// and finds the instance of an element by binary search over the offsets. A
+// finished instance (its stop rule fired) is skipped element by element. The
+// arithmetic of each stage is the single-instance one (km_quant.cu,
+// km_recheck.cu, km_reduce.cu): the same codes, error bounds, compensated
+// sums and FP64 divide, so every instance gets the same accuracy contract.
+#include "km_internal.cuh"
+#include "km_quant.cuh"
+
+namespace km {
+
+namespace {
+
+constexpr int kMaxV = 4;   // d <= 128 in batched runs: 4 floats per lane
+constexpr int RWB = 64;    // sorted positions per warp in the segmented sum
+
+__global__ void b_reset_kernel(Ctl* ctls, int nb, unsigned long long* flag_slots) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) *flag_slots = 0;
+  if (b < nb) {
+    unsigned int* w = reinterpret_cast<unsigned int*>(ctls + b);
+    for (size_t e = 0; e < kCtlIterBytes / 4; ++e) w[e] = 0;
+  }
+}
+
+template <int FP8>
+__global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
+  constexpr int ESZ = FP8 ? 1 : 2;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < W.R; g += nwarps) {
+    const int b = find_block(W.row_off, W.nb, g);
+    const BInst& I = W.inst[b];
+    const int64_t i = g - I.row_off;
+    const int d = I.d, Kp = I.Kp;
+    const float* x = I.X + i * d;
+    float amax = 0.f;
+    if (FP8)
+      for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
+    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    float sxx = 0.f, sqq = 0.f, sdd = 0.f;
+    uint8_t* row = W.Xq + I.xq_off + i * (int64_t)Kp * ESZ;
+    for (int t = lane; t < Kp; t += 32) {
+      const float v = t < d ? x[t] : 0.f;
+      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      sxx = fmaf(v, v, sxx);
+      sqq = fmaf(vq, vq, sqq);
+      sdd = fmaf(vq - v, vq - v, sdd);
+    }
+    sxx = warp_sum(sxx);
+    sqq = warp_sum(sqq);
+    sdd = warp_sum(sdd);
+    if (lane == 0) {
+      if (!isfinite(sxx) || !isfinite(sqq)) W.ctls[b].nonfinite = 1;
+      W.xs[g] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+    }
+  }
+}
+
+template <int FP8>
+__global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
+  constexpr int ESZ = FP8 ? 1 : 2;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < W.KP; g += nwarps) {
+    const int b = find_block(W.kp_off, W.nb, g);
+    Ctl* ctl = W.ctls + b;
+    if (halted(ctl)) continue;
+    const BInst& I = W.inst[b];
+    const int j = (int)(g - I.kp_off);
+    const int d = I.d, Kp = I.Kp;
+    uint8_t* row = W.Cq + I.cq_off + (int64_t)j * Kp * ESZ;
+    if (j >= I.k) {  // padding centroid: zero codes, score +inf
+      for (int t = lane; t < Kp * ESZ; t += 32) row[t] = 0;
+      if (lane == 0) {
+        W.hq[g] = INFINITY;
+        W.scq[g] = 1.f;
+      }
+      continue;
+    }
+    const float* c = I.C + (int64_t)j * d;
+    double s2 = 0.0;
+    float amax = 0.f;
+    for (int t = lane; t < d; t += 32) {
+      s2 = fma((double)c[t], (double)c[t], s2);
+      amax = fmaxf(amax, fabsf(c[t]));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    float sqq = 0.f, sdd = 0.f;
+    for (int t = lane; t < Kp; t += 32) {
+      const float v = t < d ? c[t] : 0.f;
+      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      sqq = fmaf(vq, vq, sqq);
+      sdd = fmaf(vq - v, vq - v, sdd);
+    }
+    sqq = warp_sum(sqq);
+    sdd = warp_sum(sdd);
+    if (lane == 0) {
+      const float h = __double2float_rn(0.5 * s2);
+      const float cn = __double2float_ru(sqrt(s2) * (1.0 + 1e-13));
+      const float qn = norm_bound(sqq, d), dn = norm_bound(sdd, d);
+      if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
+      W.hq[g] = h;
+      W.scq[g] = sc;
+      I.counts[j] = 0;
+      atomic_max_nonneg(&ctl->hmax_bits, h);
+      atomic_max_nonneg(&ctl->cmax_bits, cn);
+      atomic_max_nonneg(&ctl->qcmax_bits, qn);
+      atomic_max_nonneg(&ctl->dcmax_bits, dn);
+    }
+  }
+}
+
+// Flagged points of all instances (FlagRec.pad = instance): the re-check of
+// km_recheck.cu with lanes over dimensions (d <= 128).
+__global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
+  __shared__ __align__(16) float xs_all[8][kMaxV * 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* xsh = xs_all[wib];
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  const int64_t nflag = min((int64_t)*W.flag_slots, W.R);
+  for (int64_t f = warp; f < nflag; f += nwarps) {
+    const FlagRec rec = W.flags[f];
+    const int b = rec.pad;
+    if (halted(W.ctls + b)) continue;
+    const BInst& I = W.inst[b];
+    const int d = I.d, k = I.k;
+    const float* x = I.X + (int64_t)rec.i * d;
+    float xv[kMaxV];
+#pragma unroll
+    for (int v = 0; v < kMaxV; ++v) {
+      const int t = v * 32 + lane;
+      xv[v] = t < d ? x[t] : 0.f;
+    }
+    float best = INFINITY;
+    int jb;
+    if (rec.nc > 0) {
+      jb = rec.cand[0];
+      for (int q = 0; q < rec.nc; ++q) {
+        const int j = rec.cand[q];
+        const float* c = I.C + (int64_t)j * d;
+        float s = 0.f, comp = 0.f;
+#pragma unroll
+        for (int v = 0; v < kMaxV; ++v) {
+          const int t = v * 32 + lane;
+          if (t < d) {
+            const float diff = __fsub_rn(xv[v], c[t]);
+            kahan_add(s, comp, __fmul_rn(diff, diff));
+          }
+        }
+        float hi = s, lo = -comp;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+          const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+          float sh, e;
+          two_sum(hi, ohi, sh, e);
+          lo = __fadd_rn(__fadd_rn(lo, olo), e);
+          hi = sh;
+        }
+        const float D = __fadd_rn(hi, lo);
+        if (D < best) {
+          best = D;
+          jb = j;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < kMaxV; ++v) xsh[v * 32 + lane] = xv[v];
+      __syncwarp();
+      jb = k;
+      for (int j = lane; j < k; j += 32) {
+        const float* c = I.C + (int64_t)j * d;
+        float s = 0.f, comp = 0.f;
+        for (int t = 0; t < d; ++t) {
+          const float diff = __fsub_rn(xsh[t], __ldg(c + t));
+          kahan_add(s, comp, __fmul_rn(diff, diff));
+        }
+        const float D = __fsub_rn(s, comp);
+        if (D < best) {
+          best = D;
+          jb = j;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
+        if (lex_less(ob, oj, best, jb)) {
+          best = ob;
+          jb = oj;
+        }
+      }
+      if (jb >= k) jb = 0;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      I.assign[rec.i] = jb;
+      if (rec.old != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) b_count_kernel(BWork W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride) {
+    const int64_t g = base + threadIdx.x;
+    bool act = g < W.R;
+    int b = 0, j = 0;
+    if (act) {
+      b = find_block(W.row_off, W.nb, g);
+      act = !halted(W.ctls + b);
+      if (act) j = W.inst[b].assign[g - W.inst[b].row_off];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      const unsigned long long key = ((unsigned long long)b << 32) | (unsigned)j;
+      const unsigned peers = __match_any_sync(m, key);
+      if (lane == __ffs(peers) - 1) atomicAdd(&W.inst[b].counts[j], __popc(peers));
+    }
+  }
+}
+
+// Exclusive scan of one instance's counts per block (k <= 1024 * 64).
+__global__ void __launch_bounds__(1024) b_scan_kernel(BWork W) {
+  const int b = blockIdx.x;
+  if (halted(W.ctls + b)) return;
+  const BInst& I = W.inst[b];
+  __shared__ int warp_tot[32];
+  __shared__ int carry_s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < I.k; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int v = j < I.k ? I.counts[j] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int excl = carry_s + (wid ? warp_tot[wid - 1] : 0) + x - v;
+    if (j < I.k) {
+      W.offs[I.offs_off + j] = excl;
+      W.cursor[I.kp_off + j] = excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) W.offs[I.offs_off + I.k] = carry_s;
+}
+
+__global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride) {
+    const int64_t g = base + threadIdx.x;
+    bool act = g < W.R;
+    int b = 0, j = 0;
+    int64_t i = 0;
+    if (act) {
+      b = find_block(W.row_off, W.nb, g);
+      act = !halted(W.ctls + b);
+      if (act) {
+        i = g - W.inst[b].row_off;
+        j = W.inst[b].assign[i];
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, act);
+    if (act) {
+      const unsigned long long key = ((unsigned long long)b << 32) | (unsigned)j;
+      const unsigned peers = __match_any_sync(m, key);
+      const int leader = __ffs(peers) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&W.cursor[W.inst[b].kp_off + j], __popc(peers));
+      pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1));
+      W.perm[W.inst[b].row_off + pos] = (int32_t)i;
+    }
+  }
+}
+
+// Segmented sums over the flattened sorted positions: the run of a warp may
+// cross instance boundaries, which flush like cluster boundaries. With QM the
+// codes of each row are rewritten at its sorted position (as km_reduce.cu).
+template <int QM>
+__global__ void __launch_bounds__(256) b_segsum_kernel(BWork W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p0 = gw * RWB; p0 < W.R; p0 += nw * RWB) {
+    const int64_t p1 = min(p0 + (int64_t)RWB, W.R);
+    float s[kMaxV], c[kMaxV], cj[kMaxV];
+#pragma unroll
+    for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
+    float objS = 0.f, objC = 0.f;
+    int cur_b = -1, cur_j = -1;
+    const BInst* I = nullptr;
+    auto flush = [&]() {
+      if (cur_j < 0) return;
+#pragma unroll
+      for (int v = 0; v < kMaxV; ++v) {
+        const int t = v * 32 + lane;
+        if (t < I->d) atomicAdd(W.sums64 + I->sum_off + (int64_t)cur_j * I->d + t, (double)s[v] - (double)c[v]);
+        s[v] = 0.f;
+        c[v] = 0.f;
+      }
+    };
+    auto flush_obj = [&]() {
+      if (cur_b < 0) return;
+      double o = (double)objS - (double)objC;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+      if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[cur_b].objective, o);
+      objS = objC = 0.f;
+    };
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+      const int64_t pl = pb + lane;
+      int my_b = -1, my_i = 0, my_j = -1;
+      if (pl < p1) {
+        my_b = find_block(W.row_off, W.nb, pl);
+        if (halted(W.ctls + my_b)) {
+          my_b = -1;
+        } else {
+          my_i = W.perm[pl];
+          my_j = W.inst[my_b].assign[my_i];
+        }
+      }
+      const int cnt = (int)min((int64_t)32, p1 - pb);
+      for (int r = 0; r < cnt; ++r) {
+        const int b = __shfl_sync(0xffffffffu, my_b, r);
+        const int i = __shfl_sync(0xffffffffu, my_i, r);
+        const int j = __shfl_sync(0xffffffffu, my_j, r);
+        if (b < 0) continue;  // finished instance
+        if (b != cur_b || j != cur_j) {
+          flush();
+          if (b != cur_b) {
+            flush_obj();
+            cur_b = b;
+            I = W.inst + b;
+          }
+          cur_j = j;
+#pragma unroll
+          for (int v = 0; v < kMaxV; ++v) {
+            const int t = v * 32 + lane;
+            cj[v] = t < I->d ? I->C[(int64_t)j * I->d + t] : 0.f;
+          }
+        }
+        const int d = I->d;
+        const float* x = I->X + (int64_t)i * d;
+        float q = 0.f, xr[kMaxV];
+#pragma unroll
+        for (int v = 0; v < kMaxV; ++v) {
+          const int t = v * 32 + lane;
+          xr[v] = t < d ? __ldg(x + t) : 0.f;
+          kahan_add(s[v], c[v], xr[v]);
+          const float df = __fsub_rn(xr[v], cj[v]);
+          q = fmaf(df, df, q);
+        }
+        kahan_add(objS, objC, q);
+        if constexpr (QM != 0) {
+          const int64_t g = pb + r;  // flattened sorted position
+          const int64_t pr = g - I->row_off;
+          const float4 xsr = __ldg(&W.xs[I->row_off + i]);
+          if (lane == 0) {
+            W.xs_sorted[g] = xsr;
+            W.lab_sorted[g] = j;
+          }
+#pragma unroll
+          for (int v = 0; v < kMaxV; ++v) {
+            const int t = v * 32 + lane;
+            if (t < d) {
+              if constexpr (QM == 1) {
+                reinterpret_cast<__nv_bfloat16*>(W.Xq + I->xq_off)[pr * I->Kp + t] = __float2bfloat16_rn(xr[v]);
+              } else {
+                __nv_fp8_e4m3 code(xr[v] / xsr.x);
+                (W.Xq + I->xq_off)[pr * I->Kp + t] = code.__x;
+              }
+            }
+          }
+        }
+      }
+    }
+    flush();
+    flush_obj();
+  }
+}
+
+// Divide per centroid of every instance; the warp that finishes an instance's
+// last centroid records its step statistics and evaluates its stop rule.
+__global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = gw; g < W.KC; g += nw) {
+    const int b = find_block(W.kc_off, W.nb, g);
+    Ctl* ctl = W.ctls + b;
+    if (halted(ctl)) continue;
+    const BInst& I = W.inst[b];
+    const int j = (int)(g - I.kc_off), d = I.d;
+    const int cnt = I.counts[j];
+    double acc = 0.0;
+    for (int t = lane; t < d; t += 32) {
+      const int64_t e = (int64_t)j * d + t;
+      double* sp = W.sums64 + I.sum_off + e;
+      const double sv = *sp;
+      *sp = 0.0;
+      I.sums[e] = (float)sv;
+      const float co = I.C[e];
+      const float cn = cnt > 0 ? (float)(sv / (double)cnt) : co;
+      I.C[e] = cn;
+      const double df = (double)cn - (double)co;
+      acc = fma(df, df, acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      atomic_max_nonneg(&ctl->shift2_bits, acc);
+      if (cnt == 0) atomicAdd(&ctl->n_empty, 1);
+      __threadfence();
+      const unsigned ticket = atomicAdd(&ctl->blocks_done, 1u);
+      if (ticket == (unsigned)I.k - 1) {  // this instance's last centroid
+        __threadfence();
+        volatile Ctl* vc = ctl;
+        const int it = vc->iters_done;
+        const int64_t h = (int64_t)b * W.iters + it;
+        const double shift = sqrt(__longlong_as_double((long long)vc->shift2_bits));
+        const unsigned long long changed = vc->n_changed;
+        W.obj_hist[h] = vc->objective;
+        W.shift_hist[h] = shift;
+        W.changed_hist[h] = changed;
+        W.flagged_hist[h] = vc->n_flagged;
+        W.full_hist[h] = vc->n_full;
+        W.empty_hist[h] = vc->n_empty;
+        vc->iters_done = it + 1;
+        if (tol > 0.0 && (changed == 0 || shift <= tol)) vc->done = 1;
+      }
+    }
+  }
+}
+
+int grid_for(int64_t work_items, int per_block, int cap_per_sm) {
+  int64_t blocks = (work_items + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)num_sms() * cap_per_sm;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks > 0 ? blocks : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_b_reset(const BWork& W, cudaStream_t s) {
+  b_reset_kernel<<<(W.nb + 255) / 256, 256, 0, s>>>(W.ctls, W.nb, W.flag_slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s) {
+  const int grid = grid_for(W.R, 8, 16);
+  if (fp8) b_quant_x_kernel<1><<<grid, 256, 0, s>>>(W);
+  else b_quant_x_kernel<0><<<grid, 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s) {
+  const int grid = grid_for(W.KP, 8, 8);
+  if (fp8) b_quant_c_kernel<1><<<grid, 256, 0, s>>>(W);
+  else b_quant_c_kernel<0><<<grid, 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
+  b_recheck_kernel<<<num_sms() * 4, 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_count(const BWork& W, cudaStream_t s) {
+  b_count_kernel<<<grid_for(W.R, 256, 8), 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_scan(const BWork& W, cudaStream_t s) {
+  b_scan_kernel<<<W.nb, 1024, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s) {
+  b_scatter_kernel<<<grid_for(W.R, 256, 8), 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s) {
+  const int grid = grid_for((W.R + RWB - 1) / RWB, 8, 8);
+  if (qmode == 1) b_segsum_kernel<1><<<grid, 256, 0, s>>>(W);
+  else if (qmode == 2) b_segsum_kernel<2><<<grid, 256, 0, s>>>(W);
+  else b_segsum_kernel<0><<<grid, 256, 0, s>>>(W);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_divide(const BWork& W, double tol, cudaStream_t s) {
+  b_divide_kernel<<<grid_for(W.KC, 8, 8), 256, 0, s>>>(W, tol);
+  return cudaGetLastError();
+}
+
+}  // namespace km

@@ -12,7 +12,7 @@
 namespace km {
 
 constexpr int kMaxD = 256;      // largest supported dimension
-constexpr int kMaxCand = 4;     // candidates kept per flagged point
+constexpr int kMaxCand = 8;     // candidates kept per flagged point
 constexpr float kU = 5.9604644775390625e-8f;  // FP32 unit roundoff 2^-24
 
 // Per-run device control block. The first block of fields is per-iteration
@@ -45,7 +45,7 @@ struct __align__(16) FlagRec {
   int32_t old;
   int32_t nc;
   int32_t pad;
-  int32_t cand[kMaxCand];
+  int32_t cand[kMaxCand];  // increasing index order
 };
 
 // Device workspace of one call (pointers into one allocation).
@@ -70,24 +70,52 @@ struct Work {
   uint8_t* Xq;         // [n][Kp] point codes (cached for the call)
   float4* xs;          // [n] row scale and norm bounds
   uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
-  float2* hsc;         // [kp] (h_j, sc_j)
+  float* hq;           // [kp] h_j of the quantised path (+inf for padding)
+  float* scq;          // [kp] centroid code scales
   float4* state;       // [n] per-row (best, index, second) between centroid slabs (FP32 path)
+  float4* xs16;        // [n] BF16 statistics of a cold first step of an E4M3 run
+  float4* xs_sorted;   // [n] xs in this step's cluster-sorted order (quantised paths)
+  int32_t* lab_sorted; // [n] label of each sorted position (quantised paths)
 };
+
+struct BInst;
 
 // Tensor-core assignment: quantised operands and launch shape.
 struct TcParams {
-  const float2* hsc;  // [kp] (h_j, sc_j); h_j = +inf for padding rows j >= k
+  const float* h;     // [kp] h_j = ||c_j||^2 / 2; +inf for padding rows j >= k
+  const float* sc;    // [kp] power-of-two row scale of the centroid codes
+  const int32_t* rows;  // row p of the code matrix holds point rows[p] (null: point p)
   const float4* xs;   // [n] (sx_i, ||x~_i||, ||x~_i - x_i||, ||x_i||), norms rounded up
+  const float4* xs_sorted;  // with rows: xs of row p's point, written by the reduce stage
+  const int32_t* lab_sorted;  // with rows: previous label of row p's point
   const uint8_t* Cq;  // [kp][Kp] centroid codes (row stride Kp * element size)
   int32_t* assign;
   FlagRec* flags;
   Ctl* ctl;
   int64_t n;
-  int k, Kp, nkb, bn, nchunks, stages, first;
+  int k, Kp, nkb, bn, nchunks, stages, abufs, first;
   uint32_t idesc;
   float gam_tc;       // accumulation bound of the tensor-core sum over Kp terms
   float gam_simt;     // accumulation bound of the FP32 SIMT seed over Kp terms
   uint64_t wait_ns;   // bound of every mbarrier wait
+  int debug_stall;    // test knob: the epilogue also waits on a barrier nothing arrives on
+  unsigned long long* flag_slots;  // slot counter of the flag list
+  int64_t flag_cap;                // entries the flag list holds
+  // batched mode (binst != null): per-instance descriptors; the fields above
+  // then give only the launch shape (nkb, kp maxima), first, wait_ns and idesc
+  const struct BInst* binst;
+  const int64_t* btile_off;
+  int nb, sorted;
+  int64_t ntiles;
+  Ctl* bctls;
+  const CUtensorMap* bmaps;
+  float* bh;
+  float* bsc;
+  const uint8_t* bCq;
+  const float4* bxs;
+  const float4* bxs_sorted;
+  const int32_t* blab_sorted;
+  const int32_t* bperm;
 };
 
 struct TcLaunch {
@@ -95,6 +123,83 @@ struct TcLaunch {
   CUtensorMap mapC;   // codes of C: rows kp, Kp elements, box (128 B, bn rows), 128B swizzle
   int fp8;
 };
+
+// ---------------------------------------------------------------- batched runs
+// One device descriptor per independent instance; every per-instance array of
+// the batch lives at an offset in one flattened array of the batch workspace.
+struct BInst {
+  const float* X;
+  float* C;
+  int32_t* assign;
+  float* sums;
+  int32_t* counts;
+  int64_t n;
+  int d, k;
+  int64_t row_off;   // rows: xs, xs_sorted, lab_sorted, perm
+  int64_t kc_off;    // centroids (unpadded): divide
+  int64_t kp_off;    // centroids padded to whole chunks: h, sc, cursors
+  int64_t offs_off;  // segment offsets (kp_off + instance index)
+  int64_t sum_off;   // FP64 sums, k * d per instance
+  int64_t tile_off;  // 128-row tiles
+  int64_t xq_off;    // bytes: point codes [n][Kp]
+  int64_t cq_off;    // bytes: centroid codes [kp][Kp]
+  int Kp, nkb, kp, nchunks;
+  float gam_tc, gam_simt;
+  int pad0, pad1;
+};
+
+struct BWork {
+  const BInst* inst;
+  int nb, iters;
+  const int64_t* row_off;   // [nb + 1] prefix sums (binary searched)
+  const int64_t* kc_off;    // [nb + 1]
+  const int64_t* kp_off;    // [nb + 1]
+  const int64_t* tile_off;  // [nb + 1]
+  int64_t R, KC, KP, T;     // totals: rows, centroids, padded centroids, tiles
+  Ctl* ctls;                // [nb]
+  unsigned long long* flag_slots;  // entries in the shared flag list
+  const CUtensorMap* maps;  // [2 nb]: codes of X, codes of C
+  float4* xs;
+  float4* xs_sorted;
+  int32_t* lab_sorted;
+  int32_t* perm;
+  FlagRec* flags;           // FlagRec.pad holds the instance
+  int32_t* offs;
+  int32_t* cursor;
+  double* sums64;
+  float* hq;
+  float* scq;
+  uint8_t* Xq;
+  uint8_t* Cq;
+  double* obj_hist;                  // [nb][iters]
+  double* shift_hist;
+  unsigned long long* changed_hist;
+  unsigned long long* flagged_hist;
+  unsigned long long* full_hist;
+  int* empty_hist;
+};
+
+__device__ __forceinline__ int find_block(const int64_t* off, int nb, int64_t g) {
+  int lo = 0, hi = nb;  // off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+cudaError_t launch_b_reset(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s);
+cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s);
+cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int nkb_max, int kp_max, int bn,
+                            int stages, int abufs, uint32_t idesc, cudaStream_t s);
+cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_count(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_scan(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s);
+cudaError_t launch_b_divide(const BWork& W, double tol, cudaStream_t s);
 
 struct Problem {
   const float* X;
@@ -115,15 +220,19 @@ cudaError_t launch_recheck(const Problem& p, const Work& w, int first, cudaStrea
 cudaError_t launch_count(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
-cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s);
+// qmode 0: sums only; 1 / 2: also rewrite the BF16 / E4M3 point codes in the
+// cluster-sorted order of this step (row p of w.Xq = point perm[p]).
+cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
 cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uint8_t* Xq, float4* xs,
                            cudaStream_t s);
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float2* hsc,
-                           cudaStream_t s);
+cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
+                                cudaStream_t s);
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float* h,
+                           float* sc, cudaStream_t s);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
-size_t tc_smem_bytes(int nkb, int bn, int stages);
+size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs);
 
 int num_sms();
 void set_last_error(const char* msg);  // message returned by kmeans_last_error()
@@ -156,6 +265,10 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float term) {
 
 // Lexicographic (value, index) order used by every argmin: lower value first,
 // then lower index.
+// A stage skips its work once the stop rule fired or an earlier stage of the
+// same step recorded an error (its outputs, e.g. labels, are then not valid).
+__device__ __forceinline__ bool halted(const Ctl* c) { return (c->done | c->error) != 0; }
+
 __device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
   return a < b || (a == b && ia < ib);
 }

@@ -46,7 +46,7 @@ cudaError_t launch_xnorm(const Problem& p, const Work& w, cudaStream_t s) {
 // Also clears counts (the histogram of this iteration).
 __global__ void prep_kernel(const float* __restrict__ C, int k, int d, float* __restrict__ chalf,
                             float* __restrict__ cnorm, int32_t* __restrict__ counts, Ctl* ctl) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;

@@ -12,49 +12,11 @@
 #include <cuda_fp8.h>
 
 #include "km_internal.cuh"
+#include "km_quant.cuh"
 
 namespace km {
 
 namespace {
-
-__device__ __forceinline__ float pow2_scale(float amax) {
-  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
-  int e;
-  const float m = frexpf(amax / 448.f, &e);  // amax / 448 = m 2^e, m in [0.5, 1)
-  return ldexpf(1.f, m == 0.5f ? e - 1 : e);
-}
-
-// One quantised element: stores the code, returns the dequantised value.
-template <int FP8>
-__device__ __forceinline__ float quantise(float v, float sc, uint8_t* dst) {
-  if constexpr (FP8) {
-    __nv_fp8_e4m3 q(v / sc);  // RN, satfinite
-    *dst = q.__x;
-    return (float)q * sc;
-  } else {
-    const __nv_bfloat16 q = __float2bfloat16_rn(v);
-    *reinterpret_cast<__nv_bfloat16*>(dst) = q;
-    return __bfloat162float(q);
-  }
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// sqrt of an FP32 sum of m non-negative terms, rounded up and widened to cover
-// the sum's rounding (relative error < gamma_m).
-__device__ __forceinline__ float norm_bound(float sumsq, int m) {
-  return __fmul_ru(__fsqrt_ru(sumsq), 1.f + (float)(m + 8) * kU);
-}
 
 template <int FP8>
 __global__ void __launch_bounds__(256)
@@ -90,12 +52,53 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
   }
 }
 
+// BF16 codes and statistics for a cold first step, plus the E4M3 row scale and
+// statistics the later E4M3 steps use (their codes are written by the reduce
+// stage in sorted order).
+__global__ void __launch_bounds__(256)
+quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uint8_t* __restrict__ Xq,
+                    float4* __restrict__ xs16, float4* __restrict__ xs8, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const float* x = X + i * d;
+    float amax = 0.f;
+    for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
+    const float sc8 = pow2_scale(warp_max(amax));
+    float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f;
+    uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
+    for (int t = lane; t < Kp16; t += 32) {
+      const float v = t < d ? x[t] : 0.f;
+      const float q16 = quantise<0>(v, 1.f, row + t * 2);
+      uint8_t dummy;
+      const float q8 = quantise<1>(v, sc8, &dummy);
+      sxx = fmaf(v, v, sxx);
+      sqq16 = fmaf(q16, q16, sqq16);
+      sdd16 = fmaf(q16 - v, q16 - v, sdd16);
+      sqq8 = fmaf(q8, q8, sqq8);
+      sdd8 = fmaf(q8 - v, q8 - v, sdd8);
+    }
+    sxx = warp_sum(sxx);
+    sqq16 = warp_sum(sqq16);
+    sdd16 = warp_sum(sdd16);
+    sqq8 = warp_sum(sqq8);
+    sdd8 = warp_sum(sdd8);
+    if (lane == 0) {
+      if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8)) ctl->nonfinite = 1;
+      const float xn = norm_bound(sxx, d);
+      xs16[i] = make_float4(1.f, norm_bound(sqq16, d), norm_bound(sdd16, d), xn);
+      xs8[i] = make_float4(sc8, norm_bound(sqq8, d), norm_bound(sdd8, d), xn);
+    }
+  }
+}
+
 template <int FP8>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
-               float2* __restrict__ hsc, int32_t* __restrict__ counts, Ctl* ctl) {
+               float* __restrict__ hq, float* __restrict__ scq, int32_t* __restrict__ counts, Ctl* ctl) {
   constexpr int ESZ = FP8 ? 1 : 2;
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -103,7 +106,10 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     uint8_t* row = Cq + (int64_t)j * Kp * ESZ;
     if (j >= k) {  // padding centroid: zero codes, score +inf
       for (int t = lane; t < Kp * ESZ; t += 32) row[t] = 0;
-      if (lane == 0) hsc[j] = make_float2(INFINITY, 1.f);
+      if (lane == 0) {
+        hq[j] = INFINITY;
+        scq[j] = 1.f;
+      }
       continue;
     }
     const float* c = C + (int64_t)j * d;
@@ -131,7 +137,8 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       const float cn = __double2float_ru(sqrt(s2) * (1.0 + 1e-13));
       const float qn = norm_bound(sqq, d), dn = norm_bound(sdd, d);
       if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
-      hsc[j] = make_float2(h, sc);
+      hq[j] = h;
+      scq[j] = sc;
       counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
       atomic_max_nonneg(&ctl->cmax_bits, cn);
@@ -153,13 +160,22 @@ cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uin
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float2* hsc,
-                           cudaStream_t s) {
+cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
+                                cudaStream_t s) {
+  int64_t blocks = (p.n + 7) / 8;
+  const int64_t cap = (int64_t)num_sms() * 16;
+  if (blocks > cap) blocks = cap;
+  quant_x_dual_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float* h,
+                           float* sc, cudaStream_t s) {
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (fp8) quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hsc, p.counts, w.ctl);
-  else quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hsc, p.counts, w.ctl);
+  if (fp8) quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+  else quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,53 @@
+// Device helpers of the quantisation stages (single-instance and batched):
+// power-of-two row scales, one quantised element, warp reductions, and norm
+// upper bounds. See km_quant.cu for the scheme.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "km_internal.cuh"
+
+namespace km {
+
+static __device__ __forceinline__ float pow2_scale(float amax) {
+  if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+  int e;
+  const float m = frexpf(amax / 448.f, &e);  // amax / 448 = m 2^e, m in [0.5, 1)
+  return ldexpf(1.f, m == 0.5f ? e - 1 : e);
+}
+
+// One quantised element: stores the code, returns the dequantised value.
+template <int FP8>
+static __device__ __forceinline__ float quantise(float v, float sc, uint8_t* dst) {
+  if constexpr (FP8) {
+    __nv_fp8_e4m3 q(v / sc);  // RN, satfinite
+    *dst = q.__x;
+    return (float)q * sc;
+  } else {
+    const __nv_bfloat16 q = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(dst) = q;
+    return __bfloat162float(q);
+  }
+}
+
+static __device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+static __device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// sqrt of an FP32 sum of m non-negative terms, rounded up and widened to cover
+// the sum's rounding (relative error < gamma_m).
+static __device__ __forceinline__ float norm_bound(float sumsq, int m) {
+  return __fmul_ru(__fsqrt_ru(sumsq), 1.f + (float)(m + 8) * kU);
+}
+
+
+}  // namespace km

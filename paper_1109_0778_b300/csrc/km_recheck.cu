@@ -48,7 +48,7 @@ template <int V>
 __global__ void __launch_bounds__(256)
 recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, int k,
                const FlagRec* __restrict__ flags, Ctl* ctl, int32_t* __restrict__ assign) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   __shared__ __align__(16) float xs_all[8][V * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* xsh = xs_all[wib];

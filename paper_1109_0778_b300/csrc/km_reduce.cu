@@ -20,6 +20,9 @@
 // magnitudes, and the FP64 combine adds ~2^-53 per partial, so every sum is
 // within ~1.2e-7 of sum |x_it| regardless of cluster size or order, far
 // inside the 1e-5 centroid tolerance.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "km_internal.cuh"
 
 namespace km {
@@ -32,7 +35,7 @@ constexpr int RW = 64;               // sorted positions per warp in the segment
 __global__ void __launch_bounds__(256)
 count_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ counts,
              const Ctl* ctl) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   extern __shared__ int hist[];
   const bool use_smem = k <= kSmemHistMax;
   if (use_smem) {
@@ -56,7 +59,7 @@ count_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __re
 __global__ void __launch_bounds__(1024)
 scan_kernel(const int32_t* __restrict__ counts, int k, int32_t* __restrict__ offs,
             int32_t* __restrict__ cursor, const Ctl* ctl) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   __shared__ int warp_tot[32];
   __shared__ int carry_s;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -99,7 +102,7 @@ scan_kernel(const int32_t* __restrict__ counts, int k, int32_t* __restrict__ off
 __global__ void __launch_bounds__(256)
 scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int32_t* __restrict__ cursor,
                int32_t* __restrict__ perm, const Ctl* ctl) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
@@ -129,7 +132,7 @@ constexpr int kScatterPerThread = 16;
 __global__ void __launch_bounds__(256)
 scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ cursor,
                      int32_t* __restrict__ perm, const Ctl* ctl) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   extern __shared__ int cnt[];  // per-cluster count, then the block's base position
   const int64_t chunk = (int64_t)blockDim.x * kScatterPerThread;
   for (int64_t c0 = blockIdx.x * chunk; c0 < n; c0 += (int64_t)gridDim.x * chunk) {
@@ -167,13 +170,17 @@ __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, i
   }
 }
 
-template <int V>
+// QM = 1 / 2: the pass also writes the BF16 / E4M3 codes of each row it reads
+// at its sorted position p (row stride Kp elements), using the row scale in xs;
+// the codes equal those the quantisation stage produces for the same point.
+template <int V, int QM>
 __global__ void __launch_bounds__(256)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
               const int32_t* __restrict__ assign, const int32_t* __restrict__ perm,
-              double* __restrict__ sums64, Ctl* ctl) {
+              double* __restrict__ sums64, Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs,
+              int Kp, float4* __restrict__ xs_sorted, int32_t* __restrict__ lab_sorted) {
   constexpr int U = V <= 2 ? 8 : 4;  // rows whose loads are in flight together
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -228,6 +235,27 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
             q = fmaf(df, df, q);
           }
           kahan_add(objS, objC, q);
+          if constexpr (QM != 0) {
+            const int64_t prow = pb + r0 + u;
+            const float4 xsr = __ldg(&xs[ir[u]]);
+            const float sxr = QM == 2 ? xsr.x : 1.f;
+            if (lane == 0) {
+              xs_sorted[prow] = xsr;
+              lab_sorted[prow] = j;
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const int t = v * 32 + lane;
+              if (t < d) {
+                if constexpr (QM == 1) {
+                  reinterpret_cast<__nv_bfloat16*>(Xq)[prow * Kp + t] = __float2bfloat16_rn(xr[u][v]);
+                } else {
+                  __nv_fp8_e4m3 code(xr[u][v] / sxr);
+                  Xq[prow * Kp + t] = code.__x;
+                }
+              }
+            }
+          }
         }
       }
     }
@@ -246,7 +274,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
 __global__ void __launch_bounds__(256)
 divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ counts,
               double* __restrict__ sums64, float* __restrict__ sums, Ctl* ctl, Work w, double tol) {
-  if (ctl->done) return;
+  if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -325,14 +353,25 @@ cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s) {
+cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode, int Kp) {
   int64_t warps = (p.n + RW - 1) / RW;
   int64_t blocks = (warps + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   const int V = (p.d + 31) / 32;
   switch (V) {
-#define KM_CASE(v) case v: segsum_kernel<v><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl); break;
+#define KM_CASE(v)                                                                                              \
+  case v:                                                                                                        \
+    if (qmode == 1)                                                                                              \
+      segsum_kernel<v, 1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
+                                                      w.Xq, w.xs, Kp, w.xs_sorted, w.lab_sorted);                \
+    else if (qmode == 2)                                                                                         \
+      segsum_kernel<v, 2><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
+                                                      w.Xq, w.xs, Kp, w.xs_sorted, w.lab_sorted);                \
+    else                                                                                                         \
+      segsum_kernel<v, 0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
+                                                      nullptr, nullptr, 0, nullptr, nullptr);                    \
+    break;
     KM_CASE(1) KM_CASE(2) KM_CASE(3) KM_CASE(4) KM_CASE(5) KM_CASE(6) KM_CASE(7) KM_CASE(8)
 #undef KM_CASE
     default: return cudaErrorInvalidValue;

@@ -22,7 +22,8 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 
 #: Entry points declared in include/kmeans.h (checked by the ABI test).
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
-           "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc")
+           "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc",
+           "kmeans_run_batched")
 
 
 class KMeansError(RuntimeError):
@@ -35,6 +36,12 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("recheck", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("C", ctypes.c_void_p), ("assign", ctypes.c_void_p), ("sums", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -72,6 +79,8 @@ def load(path: str = LIB_PATH):
     lib.kmeans_last_error.argtypes = []
     lib.kmeans_version.restype = ctypes.c_int32
     lib.kmeans_version.argtypes = []
+    lib.kmeans_run_batched.restype = ctypes.c_int
+    lib.kmeans_run_batched.argtypes = [P(Opts), P(Instance), i32, i32, dbl, P(Stats)]
     lib.kmeans_reduce_noalloc.restype = ctypes.c_int
     lib.kmeans_reduce_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, P(dbl), vp]
     return lib
@@ -188,6 +197,22 @@ def run_host(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, preci
     _check(_lib.kmeans_run_host(ctypes.byref(o), ptr(X), n, d, ptr(C), k, ptr(assign), ptr(sums), ptr(counts),
                                 int(iters), float(tol), ctypes.byref(st)))
     return st.as_dict()
+
+
+def run_batched(problems, iters, tol=0.0, *, precision="bf16", recheck=True, stream=None, warm_start=False):
+    """kmeans_run_batched over a list of (X, C, assign, sums, counts) device-tensor tuples.
+
+    Every C is updated in place. Returns the list of per-instance stats dicts.
+    """
+    count = len(problems)
+    arr = (Instance * count)()
+    for b, (X, C, assign, sums, counts) in enumerate(problems):
+        n, d, k = _check_tensors(X, C, assign, sums, counts)
+        arr[b] = Instance(X.data_ptr(), n, d, k, C.data_ptr(), assign.data_ptr(), sums.data_ptr(), counts.data_ptr())
+    o = make_opts(precision, recheck, _stream_handle(stream), False, warm_start)
+    st = (Stats * count)()
+    _check(_lib.kmeans_run_batched(ctypes.byref(o), arr, count, int(iters), float(tol), st))
+    return [s.as_dict() for s in st]
 
 
 def version() -> int:

@@ -1,0 +1,134 @@
+"""Batched runs (kmeans_run_batched) against the FP64 oracle, instance by instance."""
+import numpy as np
+import pytest
+
+import parity
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def km():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1109_0778_b300 import kmeans
+
+    return kmeans
+
+
+SHAPES = [(1000, 8, 4), (5000, 32, 40), (3001, 64, 7), (2500, 128, 300), (129, 8, 129), (777, 17, 1),
+          (4096, 64, 512), (10000, 32, 130), (600, 100, 60), (2048, 128, 64), (1500, 8, 100), (300, 1, 3)]
+
+
+def make_batch(shapes, seed0=500):
+    data = []
+    for b, (n, d, k) in enumerate(shapes):
+        X = synth.mixture(seed0 + b, n, d, max(k, 1), 10.0, 1.0)
+        data.append((X, X[:k].copy()))
+    return data
+
+
+def to_device(km, data):
+    probs = []
+    for X, C0 in data:
+        Xd = torch.from_numpy(X).to(DEV)
+        Cd = torch.from_numpy(C0).to(DEV)
+        a, s, c = km.alloc_outputs(Xd, Cd)
+        probs.append((Xd, Cd, a, s, c))
+    return probs
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_single_step_parity(km, ref, precision):
+    data = make_batch(SHAPES)
+    probs = to_device(km, data)
+    stats = km.run_batched(probs, 1, precision=precision)
+    for (X, C0), (Xd, Cd, a, s, c), st in zip(data, probs, stats):
+        C_in = C0.astype(np.float64)
+        ag = a.cpu().numpy()
+        parity.check_assign(ref, X, C_in, ag)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
+        parity.check_objective(ref, X, C_in, ag, st["objective"])
+        assert st["iters_done"] == 1
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_warm_steps_parity(km, ref, precision):
+    """Steps after the first pass the previous assignment in (warm start), one step per call."""
+    data = make_batch(SHAPES, seed0=900)
+    probs = to_device(km, data)
+    km.run_batched(probs, 1, precision=precision)
+    for _ in range(2):
+        C_ins = [p[1].cpu().numpy().astype(np.float64) for p in probs]
+        stats = km.run_batched(probs, 1, precision=precision, warm_start=True)
+        for (X, _), (Xd, Cd, a, s, c), C_in, st in zip(data, probs, C_ins, stats):
+            ag = a.cpu().numpy()
+            parity.check_assign(ref, X, C_in, ag)
+            parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
+
+
+def test_batched_run_matches_free_running_oracle(km, ref):
+    data = make_batch(SHAPES, seed0=1300)
+    probs = to_device(km, data)
+    stats = km.run_batched(probs, 6, precision="bf16")
+    for (X, C0), (Xd, Cd, a, s, c), st in zip(data, probs, stats):
+        r = ref.run(X, C0.astype(np.float64), 6)
+        assert st["iters_done"] == 6
+        ag = a.cpu().numpy()
+        assert (ag != r["assign"]).sum() <= max(3, X.shape[0] // 500)
+        assert abs(st["objective"] - r["objectives"][-1]) <= 1e-4 * max(r["objectives"][-1], 1e-12)
+
+
+def test_batched_equals_single_instance_runs(km):
+    """The batched graph and separate kmeans_run calls give the same assignments (up to near-ties)."""
+    data = make_batch(SHAPES[:6], seed0=77)
+    probs = to_device(km, data)
+    km.run_batched(probs, 4, precision="bf16")
+    for (X, C0), (Xd, Cd, a, s, c) in zip(data, probs):
+        Cs = torch.from_numpy(C0).to(DEV)
+        out = km.run(Xd, Cs, 4, precision="bf16")
+        assert (out.assign != a).sum().item() <= max(2, X.shape[0] // 1000)
+        assert torch.allclose(Cs, Cd, rtol=1e-4, atol=1e-4)
+
+
+def test_batched_stop_rule_per_instance(km, ref):
+    # well separated instances converge at different steps; each stops on its own
+    shapes = [(2000, 4, 3), (3000, 8, 5), (1500, 16, 2)]
+    data = []
+    for b, (n, d, k) in enumerate(shapes):
+        X = synth.mixture(40 + b, n, d, k, 40.0, 0.5)
+        data.append((X, X[:k].copy()))
+    probs = to_device(km, data)
+    stats = km.run_batched(probs, 40, tol=1e-300, precision="bf16")
+    for (X, C0), st in zip(data, stats):
+        r = ref.run(X, C0.astype(np.float64), 40, tol=1e-300)
+        assert st["iters_done"] == r["iters_done"] < 40
+        assert st["n_changed"] == 0
+
+
+def test_batched_repeat_uses_tuned_shape(km):
+    data = make_batch(SHAPES[:4], seed0=11)
+    p1 = to_device(km, data)
+    s1 = km.run_batched(p1, 3, precision="bf16")
+    p2 = to_device(km, data)
+    s2 = km.run_batched(p2, 3, precision="bf16")  # same shapes: cached tuning and graph
+    for a, b in zip(p1, p2):
+        assert (a[2] != b[2]).sum().item() <= 2
+
+
+def test_batched_errors(km):
+    X = torch.randn(100, 200, device=DEV)
+    C = X[:4].clone()
+    a, s, c = km.alloc_outputs(X, C)
+    with pytest.raises(km.KMeansError) as e:
+        km.run_batched([(X, C, a, s, c)], 1, precision="bf16")  # d > 128
+    assert e.value.status == km.KM_EINVAL
+    X = torch.randn(100, 20, device=DEV)
+    C = X[:4].clone()
+    a, s, c = km.alloc_outputs(X, C)
+    with pytest.raises(km.KMeansError) as e:
+        km.run_batched([(X, C, a, s, c)], 1, precision="fp32")
+    assert e.value.status == km.KM_EUNSUPPORTED

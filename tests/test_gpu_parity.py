@@ -321,3 +321,20 @@ def test_tc_recheck_off_still_runs(km):
     out = km.step(Xd, Cd, precision="bf16", recheck=False)
     a = out.assign.cpu().numpy()
     assert a.min() >= 0 and a.max() < 20 and out.counts.sum().item() == 5000
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_profiled_runs(km, ref, precision):
+    """opts.profile records stage events inside the captured graph; results are unchanged."""
+    X = synth.mixture(21, 20000, 64, 50, 8.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    C0 = torch.from_numpy(X[:50].copy()).to(DEV)
+    for iters in (1, 5):
+        C = C0.clone()
+        out = km.run(Xd, C, iters, precision=precision, profile=True)
+        st = out.stats["stage_ms"]
+        assert st["assign"] > 0 and st["divide"] > 0 and st["xnorm"] > 0
+        assert out.stats["iters_done"] == iters
+    C = C0.clone()
+    r = ref.run(X, X[:50].astype(np.float64), 5)
+    assert (out.assign.cpu().numpy() != r["assign"]).sum() <= 3
