@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 (default: the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="batched workload: use only the first INSTANCES instances (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
@@ -274,11 +276,13 @@ def workload_config(w, precision):
             "step": f"one kmeans_run call = {w.iters} graph-captured Lloyd iterations"}
 
 
-def batched_problems(torch, dev, w):
-    """Device tensors of every instance of the batched workload (seeded mixtures, C0 = first k points)."""
+def batched_problems(torch, dev, w, limit=0):
+    """Device tensors of the batched workload's instances (seeded mixtures, C0 = first k points)."""
     from synth import batched_instances
 
     inst = batched_instances(w)
+    if limit:
+        inst = inst[:limit]
     probs, flops, xbytes = [], 0.0, 0
     for iw in inst:
         X = synth.mixture(iw.seed, iw.n, iw.d, iw.m, iw.R, iw.sigma)
@@ -295,7 +299,7 @@ def run_batched(args, torch, dev, dist, rank, world, local):
 
     w = WORKLOADS["batched_512"]
     prec = args.precision or w.precision[0]
-    inst, probs, flops_iter, xbytes = batched_problems(torch, dev, w)
+    inst, probs, flops_iter, xbytes = batched_problems(torch, dev, w, args.instances)
     work = []
     for Xd, C0 in probs:
         C = C0.clone()
@@ -306,7 +310,7 @@ def run_batched(args, torch, dev, dist, rank, world, local):
     def one_step():
         for (Xd, C0), (_, C, _, _, _) in zip(probs, work):
             C.copy_(C0)
-        return km.run_batched(work, w.iters, precision=prec, stream=stream)
+        return km.run_batched(work, w.iters, precision=prec, stream=stream, profile=True)
 
     for _ in range(max(args.warmup, 0)):
         one_step()
@@ -314,11 +318,15 @@ def run_batched(args, torch, dev, dist, rank, world, local):
     barrier(dist)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     call_ms = 0.0
+    stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             st = one_step()
             call_ms += st[0]["ms"]
+            for kname, v in st[0]["stage_ms"].items():
+                stage_tot[kname] += v
+            flagged = (sum(x["n_flagged"] for x in st), sum(x["n_full"] for x in st))
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(dist)
@@ -340,6 +348,9 @@ def run_batched(args, torch, dev, dist, rank, world, local):
                                f"{len(inst)} instances; value counts iterations of the whole batch",
                        "l2": f"inputs larger than L2 (X = {xbytes / 1e9:.2f} GB)"},
             "distance_tflops": value * flops_iter / 1e12,
+            "stage_ms_per_iter": {k: v / args.steps / w.iters for k, v in stage_tot.items()},
+            "flagged_last_iter": {"flagged": flagged[0], "full_recheck": flagged[1],
+                                  "note": "summed over instances, each at its last iteration"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "kernel": "whole batched step",
                          "note": "algorithmic bytes = one FP32 read of every X per iteration", "traffic": None},

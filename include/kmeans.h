@@ -192,7 +192,7 @@ int kmeans_run_batched(const km_opts* opts, const km_instance* inst,
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory (a host framework that owns all device memory,
  * code that must not trigger cudaFree's device-wide synchronisation). It calls
- * no cudaMalloc / cudaFree; its scratch is a fixed ~6.1 MB static device array
+ * no cudaMalloc / cudaFree; its scratch is a fixed ~10.5 MB static device array
  * that every GPU loading the library holds until exit. Limits: n <= 1048576,
  * k <= 8192, k * d <= 262144, 1 <= d <= 256; larger sizes return KM_EINVAL.
  * X: const float[n*d], C: const float[k*d], assign: const int32[n] with labels

@@ -133,6 +133,8 @@ int init_ctx(DevCtx* c) {
   KM_CUDA(cudaEventCreate(&c->ev1));
   KM_CUDA(init_assign_simt());
   KM_CUDA(init_assign_tc());
+  KM_CUDA(init_segsum());
+  KM_CUDA(init_batched());
   c->inited = true;
   return KM_OK;
 }
@@ -200,6 +202,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   L.flagged = take(8 * (size_t)iters);
   L.full = take(8 * (size_t)iters);
   L.empty = take(4 * (size_t)iters);
+  L.labs = take(4 * (size_t)n);  // labels in cluster-sorted order (scatter stage)
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
     size_t xq = (size_t)n * t.Kp * t.esz, cq = (size_t)t.kp * t.Kp * t.esz;
@@ -216,10 +219,9 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
     L.hq = take(4 * (size_t)t.kp);
     L.scq = take(4 * (size_t)t.kp);
     L.xss = take(16 * (size_t)n);
-    L.labs = take(4 * (size_t)n);
     L.state = 0;
   } else {
-    L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = L.labs = 0;
+    L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;
   }
@@ -421,7 +423,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   }
   if (e) return e;
   if ((e = at(2))) return e;
-  if (cfg.recheck && (e = launch_recheck(p, w, first, s))) return e;
+  if (cfg.recheck && (e = launch_recheck(p, w, tcp ? w.hq : w.chalf, first, s))) return e;
   if ((e = at(3))) return e;
   if ((e = launch_count(p, w, s))) return e;
   if ((e = at(4))) return e;
@@ -545,7 +547,6 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     P.idesc = tc::idesc_f32acc(t.fp8 ? 0u : 1u, 128, (uint32_t)t.bn);
     const double K = t.Kp;
     P.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));  // truncating FP32 accumulation
-    P.gam_simt = (float)(K * 0x1p-24 / (1.0 - K * 0x1p-24) * (1.0 + 1e-6));
     P.wait_ns = 2000000000ull;
     if (getenv("KM_DEBUG_STALL")) {  // test knob: make a bounded wait expire (50 ms)
       P.debug_stall = 1;
@@ -773,6 +774,7 @@ struct BatchPlan {
   std::vector<int> order;  // flattened position -> caller's instance index
   std::vector<BInst> inst;
   std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
+  std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
   int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
   int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0;
 };
@@ -812,7 +814,6 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     I.nchunks = I.kp / P.bn;
     const double K = I.Kp;
     I.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));
-    I.gam_simt = (float)(K * 0x1p-24 / (1.0 - K * 0x1p-24) * (1.0 + 1e-6));
     I.row_off = P.R;
     I.kc_off = P.KC;
     I.kp_off = P.KP;
@@ -844,6 +845,27 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.stages = fixed + 2 * bstage <= budget ? (int)std::min<size_t>(8, (budget - fixed) / bstage) : 0;
   }
   if (P.stages < 2) return fail(KM_EUNSUPPORTED, "largest k of the batch does not fit the tensor-core pipeline");
+  // contiguous tile ranges per CTA, balanced by a work model of a tile: MMA
+  // and epilogue work ~ chunks x K blocks, plus a fixed per-tile cost
+  const int grid = (int)std::min<int64_t>(P.T, num_sms());
+  std::vector<double> wsum(count + 1, 0.0);
+  for (int q = 0; q < count; ++q) {
+    const BInst& I = P.inst[q];
+    const double per_tile = (double)I.nchunks * I.nkb + 2.0;
+    wsum[q + 1] = wsum[q] + per_tile * (double)(P.tile_off[q + 1] - P.tile_off[q]);
+  }
+  P.cta_tile.assign(grid + 1, P.T);
+  P.cta_tile[0] = 0;
+  int q = 0;
+  for (int c = 1; c < grid; ++c) {
+    const double target = wsum[count] * c / grid;
+    while (q < count - 1 && wsum[q + 1] <= target) ++q;
+    const BInst& I = P.inst[q];
+    const double per_tile = (double)I.nchunks * I.nkb + 2.0;
+    int64_t t = P.tile_off[q] + (int64_t)((target - wsum[q]) / per_tile);
+    t = std::min(std::max(t, P.cta_tile[c - 1]), P.tile_off[q + 1]);
+    P.cta_tile[c] = t;
+  }
   return KM_OK;
 }
 
@@ -883,8 +905,8 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 
 // Byte offsets of the batch workspace.
 struct BLayout {
-  size_t ctl, inst, row, kc, kp, tile, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq, xq, cq,
-      csave, hist, total;
+  size_t ctl, inst, row, kc, kp, tile, cta, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq, xq,
+      cq, csave, hist, total;
 };
 
 BLayout batch_layout(const BatchPlan& P, int iters) {
@@ -903,6 +925,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.kc = take(8 * (nb + 1));
   L.kp = take(8 * (nb + 1));
   L.tile = take(8 * (nb + 1));
+  L.cta = take(8 * P.cta_tile.size());
   L.maps = take(sizeof(CUtensorMap) * 2 * nb, 128);
   L.slots = take(8);
   L.xs = take(16 * (size_t)P.R);
@@ -972,6 +995,8 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.kc_off = (const int64_t*)(B + o_kc);
   W.kp_off = (const int64_t*)(B + o_kp);
   W.tile_off = (const int64_t*)(B + o_tile);
+  W.cta_tile = (const int64_t*)(B + BL.cta);
+  W.cta_grid = (int)P.cta_tile.size() - 1;
   W.R = P.R;
   W.KC = P.KC;
   W.KP = P.KP;
@@ -1011,6 +1036,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   KM_CUDA(cudaMemcpyAsync(B + o_kc, P.kc_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_kp, P.kp_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));
   KM_CUDA(cudaMemsetAsync(W.sums64, 0, 8 * (size_t)P.SUMS, s));
@@ -1019,8 +1045,11 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   for (int b = 0, at = 0; b < nb; at += P.inst[b].k * P.inst[b].d, ++b)
     KM_CUDA(cudaMemcpyAsync(csave + at, P.inst[b].C, 4 * (size_t)P.inst[b].k * P.inst[b].d,
                             cudaMemcpyDeviceToDevice, s));
+  if (o.profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   KM_CUDA(cudaEventRecord(c->ev0, s));
+  if (o.profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
   KM_CUDA(launch_b_quant_x(W, P.fp8, s));
+  if (o.profile) KM_CUDA(cudaEventRecord(c->prof[1], s));
   // graph of the iterations, cached while the batch and its workspace are unchanged
   std::vector<unsigned char> key(sizeof(BInst) * nb);
   memcpy(key.data(), P.inst.data(), key.size());
@@ -1030,6 +1059,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   app(&o.recheck, sizeof o.recheck);
   app(&o.warm_start, sizeof o.warm_start);
   app(&P.bn, sizeof P.bn);
+  app(&o.profile, sizeof o.profile);
   void* base = bc.ws;
   app(&base, sizeof base);
   if (!(bc.gexec && bc.gkey == key)) {
@@ -1044,17 +1074,29 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
     const int qmode = P.fp8 ? 2 : 1;
     cudaStream_t cs = c->cap_stream;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+      // stage boundaries as in enqueue_step (events only when profiling)
+      const cudaEvent_t* ev = step_events(c, o.profile != 0, it);
+      auto at = [&](int i) { return ev ? mark(ev[i], cs) : cudaSuccess; };
       if (!e) e = launch_b_reset(W, cs);
+      if (!e) e = at(0);
       if (!e) e = launch_b_quant_c(W, P.fp8, cs);
+      if (!e) e = at(1);
       if (!e)
         e = launch_b_assign(W, P.fp8, it == 0 && !o.warm_start, it > 0, P.nkb_max, P.kp_max, P.bn, P.stages, P.abufs,
                             idesc, cs);
+      if (!e) e = at(2);
       if (!e && o.recheck) e = launch_b_recheck(W, cs);
+      if (!e) e = at(3);
       if (!e) e = launch_b_count(W, cs);
+      if (!e) e = at(4);
       if (!e) e = launch_b_scan(W, cs);
+      if (!e) e = at(5);
       if (!e) e = launch_b_scatter(W, cs);
+      if (!e) e = at(6);
       if (!e) e = launch_b_segsum(W, qmode, cs);
+      if (!e) e = at(7);
       if (!e) e = launch_b_divide(W, tol, cs);
+      if (!e) e = at(8);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1092,6 +1134,19 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   if (ms_out) *ms_out = ms;
+  float stage_ms[12] = {0.f};
+  if (o.profile) {
+    float t = 0.f;
+    KM_CUDA(cudaEventElapsedTime(&t, c->prof[0], c->prof[1]));
+    stage_ms[KM_STAGE_XNORM] = t;
+    for (int it = 0; it < iters; ++it) {
+      const cudaEvent_t* ev = step_events(c, true, it);
+      for (int sg = 0; sg < kEvPerStep - 1; ++sg) {
+        KM_CUDA(cudaEventElapsedTime(&t, ev[sg], ev[sg + 1]));
+        stage_ms[KM_STAGE_PREP + sg] += t;
+      }
+    }
+  }
   bool bad = false;
   int err = 0;
   for (int b = 0; b < nb; ++b) {
@@ -1125,6 +1180,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
         st.n_empty = he[h];
       }
       st.ms = ms;
+      memcpy(st.stage_ms, stage_ms, sizeof stage_ms);
     }
   }
   return KM_OK;

@@ -3,11 +3,18 @@
 // One pass per 128-point row tile (vertical fusion with array contraction,
 // Sec. 3.5): TMA stages the point codes (A, once per tile) and 128-centroid
 // chunks of the centroid codes (B) into shared memory with the 128-byte
-// swizzle; one thread issues tcgen05.mma into a TMEM accumulator (two buffers,
-// so the MMA of chunk c+1 overlaps the epilogue of chunk c); four epilogue
-// warps read their TMEM lane quarter with tcgen05.ld -- thread t of warp q
-// owns point row 32q + t -- and fold the chunk's scores into a per-row
-// candidate list in registers. The n x k score matrix never leaves TMEM.
+// swizzle; one thread issues tcgen05.mma into TMEM accumulators (four buffers,
+// so the MMAs of the next chunks overlap the epilogue of chunk c); the
+// epilogue warps read their TMEM lane quarter with tcgen05.ld -- thread t of a
+// warp of quarter q owns point row 32q + t -- and fold the chunk's scores into
+// a per-row candidate list in registers. The n x k score matrix never leaves
+// TMEM.
+//
+// Tiles. A single-instance launch deals row tiles round-robin to the CTAs; a
+// batched launch gives each CTA one contiguous range of the flattened tiles
+// (ranges balanced by MMA + epilogue work on the host), so a CTA meets each
+// instance once and walks its tiles in order. The epilogue loads the row
+// metadata of the CTA's next tile while it works on the current one.
 //
 // Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and TMEM
 // owner, warps 2-9 = epilogue (two per TMEM lane quarter, each taking half of
@@ -33,20 +40,20 @@
 // candidates (or, past 7 of them, all k) go to the FP32 re-check.
 //
 // Threshold. Rows keep the 8 smallest scores seen among elements <= thr, with
-// thr = min(thr0, best + margin) rounded up. From the second step on thr0 is
-// the score of the point's previous centroid, recomputed from the same codes
-// in FP32 SIMT (plus its bound against the tensor-core sum and the margin), so
-// a 32-column chunk costs one minimum unless it holds a candidate. From the
+// thr = best + margin rounded up (infinite before the first chunk), so a
+// 32-column block costs one minimum unless it holds a candidate. From the
 // second step of a call on, rows are the points in the previous step's
 // cluster-sorted order (the codes are rewritten in that order by the reduce
-// stage), so the 32 rows of a warp share their previous centroid and the
-// candidate branch is taken in about one chunk per warp.
+// stage) and a tile's chunks are visited starting with the chunk of its first
+// row's previous centroid: most rows of the tile meet their nearest centroid in
+// the first chunk, and the later chunks rarely hold a candidate.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
 #include "km_internal.cuh"
 #include "km_tc.cuh"
 
+#include <cfloat>
 #include <cstring>
 
 namespace km {
@@ -92,23 +99,14 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   return r;
 }
 
-template <int FP8>
-__device__ __forceinline__ float code_to_float(const uint8_t* p) {
-  if constexpr (FP8) {
-    __nv_fp8_e4m3 q;
-    q.__x = *p;
-    return (float)q;
-  } else {
-    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
-  }
-}
-
-// Per-tile parameters: one instance (single launches) or the instance that
-// owns flattened tile gt (batched launches).
+// Per-instance parameters of the tiles a role is working on: the only
+// instance (single launches) or the instance that owns the current flattened
+// tile (batched launches).
 struct Item {
   int b;
   bool skip;        // the instance's stop rule fired
-  int64_t tile;     // tile index within the instance
+  int64_t tile0;    // first flattened tile of the instance
+  int64_t tend;     // one past its last flattened tile
   int64_t n;
   int k, Kp, nkb, nchunks;
   const CUtensorMap* mapX;
@@ -122,16 +120,16 @@ struct Item {
   const uint8_t* Cq;
   int32_t* assign;
   Ctl* ctl;
-  float gam_tc, gam_simt;
+  float gam_tc;
 };
 
 template <bool BATCH>
-__device__ __forceinline__ Item get_item(const TcParams& P, const CUtensorMap* mx, const CUtensorMap* mc,
-                                         int64_t gt) {
-  Item it;
+__device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMap* mx, const CUtensorMap* mc, int b,
+                                             Item& it) {
   if constexpr (!BATCH) {
     it.b = 0;
-    it.tile = gt;
+    it.tile0 = 0;
+    it.tend = INT64_MAX;
     it.n = P.n;
     it.k = P.k;
     it.Kp = P.Kp;
@@ -149,12 +147,11 @@ __device__ __forceinline__ Item get_item(const TcParams& P, const CUtensorMap* m
     it.assign = P.assign;
     it.ctl = P.ctl;
     it.gam_tc = P.gam_tc;
-    it.gam_simt = P.gam_simt;
   } else {
-    const int b = find_block(P.btile_off, P.nb, gt);
     const BInst& I = P.binst[b];
     it.b = b;
-    it.tile = gt - I.tile_off;
+    it.tile0 = I.tile_off;
+    it.tend = P.btile_off[b + 1];
     it.n = I.n;
     it.k = I.k;
     it.Kp = I.Kp;
@@ -172,14 +169,39 @@ __device__ __forceinline__ Item get_item(const TcParams& P, const CUtensorMap* m
     it.assign = I.assign;
     it.ctl = P.bctls + b;
     it.gam_tc = I.gam_tc;
-    it.gam_simt = I.gam_simt;
   }
   it.skip = it.ctl->done != 0;
-  return it;
 }
 
-// A wait that ran out: the error goes to every control block of the launch, so
-// that no later stage consumes the labels this step did not write.
+// Tile range of this CTA: [t0, t1) with stride ts.
+struct TileRange {
+  int64_t t0, t1, ts;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ TileRange tile_range(const TcParams& P) {
+  if constexpr (BATCH) return TileRange{P.bcta[blockIdx.x], P.bcta[blockIdx.x + 1], 1};
+  else return TileRange{blockIdx.x, (P.n + BM - 1) / BM, gridDim.x};
+}
+
+// Moves `it` to the instance of flattened tile gt (tiles are visited in
+// increasing order). Returns true when the instance changed.
+template <bool BATCH>
+__device__ __forceinline__ bool seek(const TcParams& P, const CUtensorMap* mx, const CUtensorMap* mc, int64_t gt,
+                                     Item& it) {
+  if constexpr (!BATCH) {
+    if (it.b >= 0) return false;
+    set_instance<false>(P, mx, mc, 0, it);
+    return true;
+  } else {
+    if (it.b >= 0 && gt < it.tend) return false;
+    int b = it.b < 0 ? find_block(P.btile_off, P.nb, gt) : it.b + 1;
+    while (P.btile_off[b + 1] <= gt) ++b;
+    set_instance<true>(P, mx, mc, b, it);
+    return true;
+  }
+}
+
 template <bool BATCH>
 __device__ void record_timeout(const TcParams& P) {
   if constexpr (BATCH) {
@@ -189,12 +211,121 @@ __device__ void record_timeout(const TcParams& P) {
   }
 }
 
+// Row metadata of one tile row: the point, its norm bounds and its previous label.
+struct RowMeta {
+  int64_t i;
+  float4 xs;
+  int old;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ RowMeta fetch_meta(const TcParams& P, const Item& it, int64_t tile, int r) {
+  RowMeta m{0, make_float4(0.f, 0.f, 0.f, 0.f), -1};
+  const int64_t prow = tile * BM + r;
+  if (prow < it.n) {
+    if (it.rows) {  // cluster-sorted order: contiguous metadata written by the reduce stage
+      m.i = __ldg(it.rows + prow);
+      m.xs = __ldg(it.xs_sorted + prow);
+      if (!P.first) m.old = __ldg(it.lab_sorted + prow);
+    } else {
+      m.i = prow;
+      m.xs = __ldg(it.xs + prow);
+      if (!P.first) m.old = it.assign[prow];
+    }
+  }
+  return m;
+}
+
+// Chunk order of a tile. In cluster-sorted order the tile's rows mostly share
+// the previous label of its first row; its chunks are visited starting with the
+// chunk that holds that centroid, so that the first chunk already gives most
+// rows a tight threshold. Any order gives the same candidates. Every role of
+// the CTA derives the order from the same label.
+__device__ __forceinline__ int tile_label(const TcParams& P, const Item& it, int64_t tile) {
+  if (P.first || !it.rows || it.nchunks == 1) return -1;
+  return __ldg(it.lab_sorted + tile * BM);
+}
+
+__device__ __forceinline__ int first_chunk(int lab, const Item& it, int bn) {
+  return (lab >= 0 && lab < it.k) ? lab / bn : 0;
+}
+
+// Folds a 32-column score block into the row's candidate list: the columns
+// within min(thr, mn + margin) of the block minimum mn (every column that can
+// end within the margin of the row's final minimum), in index order.
+__device__ __forceinline__ void fold_block(Cand (&top)[kT], const float (&s)[32], float mn, int j0, float& thr,
+                                           float margin) {
+  const float lim = fminf(thr, __fadd_ru(mn, margin));
+  unsigned mask = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) mask |= (s[t] <= lim ? 1u : 0u) << t;
+#pragma unroll 1
+  while (mask) {
+    const int t = __ffs(mask) - 1;
+    mask &= mask - 1;
+    // s[t] through a 5-level select tree
+    float x16[16], x8[8], x4[4];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x16[u] = (t & 1) ? s[2 * u + 1] : s[2 * u];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x8[u] = (t & 2) ? x16[2 * u + 1] : x16[2 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x4[u] = (t & 4) ? x8[2 * u + 1] : x8[2 * u];
+    const float x2a = (t & 8) ? x4[1] : x4[0], x2b = (t & 8) ? x4[3] : x4[2];
+    const float v = (t & 16) ? x2b : x2a;
+    if (v <= thr) {
+      cand_insert(top, v, j0 + t);
+      thr = fminf(thr, __fadd_ru(top[0].v, margin));
+    }
+  }
+}
+
+// Scores of one 32-column block from its TMEM accumulators,
+// s_j = h_j - (sx sc_j) acc_j (two columns per packed operation), their
+// minimum, and the fold of the block's candidates (rare once thr is tight).
+template <int FP8>
+__device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float* hb, const float* scb, float nsx,
+                                            Cand (&top)[kT], int j0, float& thr, float margin) {
+  float s[32];
+  const float4* h4 = reinterpret_cast<const float4*>(hb);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const float4 hh = h4[t];
+    const float2 a0 = make_float2(__uint_as_float(v[4 * t]), __uint_as_float(v[4 * t + 1]));
+    const float2 a1 = make_float2(__uint_as_float(v[4 * t + 2]), __uint_as_float(v[4 * t + 3]));
+    float2 w0, w1;
+    if constexpr (FP8) {
+      const float4 sc4 = reinterpret_cast<const float4*>(scb)[t];
+      w0 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.x, sc4.y));
+      w1 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.z, sc4.w));
+    } else {
+      w0 = make_float2(-1.f, -1.f);
+      w1 = w0;
+    }
+    const float2 s0 = __ffma2_rn(w0, a0, make_float2(hh.x, hh.y));
+    const float2 s1 = __ffma2_rn(w1, a1, make_float2(hh.z, hh.w));
+    s[4 * t] = s0.x;
+    s[4 * t + 1] = s0.y;
+    s[4 * t + 2] = s1.x;
+    s[4 * t + 3] = s1.y;
+  }
+  // block minimum by a 4-level tree of 3-input minima
+  float m11[11];
+#pragma unroll
+  for (int u = 0; u < 10; ++u) m11[u] = min3f(s[3 * u], s[3 * u + 1], s[3 * u + 2]);
+  m11[10] = fminf(s[30], s[31]);
+  const float mn = fminf(min3f(min3f(m11[0], m11[1], m11[2]), min3f(m11[3], m11[4], m11[5]),
+                               min3f(m11[6], m11[7], m11[8])),
+                         fminf(m11[9], m11[10]));
+  if (__any_sync(0xffffffffu, mn <= thr))
+    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin);
+}
+
 template <int FP8, bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 1)
 assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
                  const TcParams P) {
-  constexpr int ESZ = FP8 ? 1 : 2;
-  constexpr int KBE = ROWB / ESZ;  // elements per 128-byte K block
+  constexpr int KBE = ROWB / (FP8 ? 1 : 2);  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t a_full[2], a_empty[2], b_full[MAX_STAGES], b_empty[MAX_STAGES], acc_full[NACC], acc_empty[NACC];
@@ -221,13 +352,13 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   float* Hs = reinterpret_cast<float*>(B0 + (size_t)stages * b_bytes);  // [kpmax]
   float* SCs = Hs + kpmax;                                               // [kpmax] (FP8)
   Cand* Ms = reinterpret_cast<Cand*>(SCs + (FP8 ? kpmax : 0));           // [BM][kT] merge buffer
-  const int64_t ntiles = BATCH ? P.ntiles : (P.n + BM - 1) / BM;
+  const TileRange tr = tile_range<BATCH>(P);
 
   if (threadIdx.x == 0) {
     abort_s = 0;
     for (int b = 0; b < 2; ++b) {
       mbar_init(&a_full[b], 1);
-      mbar_init(&a_empty[b], 1 + NEPI);  // MMA commit + the epilogue warps (seed reads)
+      mbar_init(&a_empty[b], 1);  // the MMA commit of the tile's last chunk
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -263,27 +394,34 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      int lt = 0, gc = 0, cur_b = -1;  // tiles and chunks issued so far by this CTA
+      int lt = 0, gc = 0;              // tiles and chunks issued so far by this CTA
       int last_a = -1, last_s = -1;    // barrier slots of the most recent A and B loads
       uint32_t last_aph = 0, last_sph = 0;
       bool ok = true;
-      for (int64_t gt = blockIdx.x; gt < ntiles && ok; gt += gridDim.x) {
-        const Item it = get_item<BATCH>(P, &mapX, &mapC, gt);
-        if (it.skip) continue;
-        if (BATCH && it.b != cur_b) {
-          // tensor maps in global memory: order the host's writes before the async proxy reads them
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
-          cur_b = it.b;
+      Item it;
+      it.b = -1;
+      int labn = -2;                   // label of the next tile, loaded one tile ahead (-2: not loaded)
+      for (int64_t gt = tr.t0; gt < tr.t1 && ok; gt += tr.ts) {
+        if (seek<BATCH>(P, &mapX, &mapC, gt, it)) {
+          labn = -2;
+          if (BATCH && !it.skip) {
+            // tensor maps in global memory: order the host's writes before the async proxy reads them
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
+          }
         }
+        if (it.skip) continue;
+        const int64_t tile = gt - it.tile0;
+        const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile), it, BN);
+        labn = (gt + tr.ts < tr.t1 && gt + tr.ts < it.tend) ? tile_label(P, it, tile + tr.ts) : -2;
         const int ab = lt % nab;
         if (!mbar_wait(&a_empty[ab], ((lt / nab) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
         mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB);
         for (int kb = 0; kb < it.nkb; ++kb)
-          tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, (int)(it.tile * BM));
+          tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, (int)(tile * BM));
         last_a = ab;
         last_aph = (lt / nab) & 1;
-        for (int c = 0; c < it.nchunks; ++c, ++gc) {
+        for (int cc = 0, c = c0; cc < it.nchunks; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
           const int s = gc % stages;
           if (!mbar_wait(&b_empty[s], ((gc / stages) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk);
@@ -308,14 +446,16 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     if (lane == 0) {
       int lt = 0, gc = 0;
       bool ok = true, issued = false;
-      for (int64_t gt = blockIdx.x; gt < ntiles && ok; gt += gridDim.x) {
-        const Item it = get_item<BATCH>(P, &mapX, &mapC, gt);
+      Item it;
+      it.b = -1;
+      for (int64_t gt = tr.t0; gt < tr.t1 && ok; gt += tr.ts) {
+        seek<BATCH>(P, &mapX, &mapC, gt, it);
         if (it.skip) continue;
         const int ab = lt % nab;
         if (!mbar_wait(&a_full[ab], (lt / nab) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
         tc_fence_after_sync();
         const uint32_t a_addr = smem_u32(A0 + ab * a_bytes);
-        for (int c = 0; c < it.nchunks; ++c, ++gc) {
+        for (int cc = 0; cc < it.nchunks; ++cc, ++gc) {
           const int s = gc % stages, buf = gc % NACC;
           if (!mbar_wait(&b_full[s], (gc / stages) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
           if (!mbar_wait(&acc_empty[buf], ((gc / NACC) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
@@ -354,91 +494,70 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const int half = (warp - 2) >> 2;  // which half of each chunk's columns
     const int r = q * 32 + lane;
     const int nsub = BN / 64;          // 32-column sub-chunks per half
-    int lt = 0, gc = 0, cur_b = -1;
+    int gc = 0;
     bool ok = true;
     unsigned int changed = 0;
+    Item it;
+    it.b = -1;
+    float H = 0.f, Cmax = 0.f, QCmax = 0.f, DCmax = 0.f;  // per-step maxima of the instance
+    RowMeta nxt;
+    bool have_nxt = false;
+    int labn = -2;
     // Every epilogue warp runs every tile to the end, even after a timeout (then
     // skipping waits and work), so that all of them reach the named barriers of
     // the candidate merge the same number of times.
-    for (int64_t gt = blockIdx.x; gt < ntiles; gt += gridDim.x) {
-      const Item it = get_item<BATCH>(P, &mapX, &mapC, gt);
+    for (int64_t gt = tr.t0; gt < tr.t1; gt += tr.ts) {
+      if (seek<BATCH>(P, &mapX, &mapC, gt, it)) {
+        have_nxt = false;
+        labn = -2;
+        if (BATCH && !it.skip) {
+          // this instance's h_j (and scales) into shared memory
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
+          for (int j = threadIdx.x - 64; j < it.nchunks * BN; j += 32 * NEPI) {
+            Hs[j] = __ldg(it.h + j);
+            if (FP8) SCs[j] = __ldg(it.sc + j);
+          }
+          asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
+        }
+        if (!it.skip) {
+          const Ctl* ctl = it.ctl;
+          H = __uint_as_float(ctl->hmax_bits);
+          Cmax = __uint_as_float(ctl->cmax_bits);
+          QCmax = __uint_as_float(ctl->qcmax_bits);
+          DCmax = __uint_as_float(ctl->dcmax_bits);
+        }
+      }
       if (it.skip) continue;
-      if (BATCH && it.b != cur_b) {
-        // this instance's h_j (and scales) into shared memory
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-        if (cur_b >= 0 && changed) {
-          atomicAdd(&P.bctls[cur_b].n_changed, (unsigned long long)changed);
-          changed = 0;
-        }
-        for (int j = threadIdx.x - 64; j < it.nchunks * BN; j += 32 * NEPI) {
-          Hs[j] = __ldg(it.h + j);
-          if (FP8) SCs[j] = __ldg(it.sc + j);
-        }
-        asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-        cur_b = it.b;
+      const int64_t tile = gt - it.tile0;
+      const RowMeta m = have_nxt ? nxt : fetch_meta<BATCH>(P, it, tile, r);
+      const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile), it, BN);
+      // the next tile of this CTA, when it belongs to the same instance: its loads overlap this tile
+      have_nxt = gt + tr.ts < tr.t1 && gt + tr.ts < it.tend;
+      if (have_nxt) {
+        nxt = fetch_meta<BATCH>(P, it, tile + tr.ts, r);
+        labn = tile_label(P, it, tile + tr.ts);
+      } else {
+        labn = -2;
       }
-      const Ctl* ctl = it.ctl;
-      const float H = __uint_as_float(ctl->hmax_bits);
-      const float Cmax = __uint_as_float(ctl->cmax_bits);
-      const float QCmax = __uint_as_float(ctl->qcmax_bits);
-      const float DCmax = __uint_as_float(ctl->dcmax_bits);
-      const int ab = lt % nab;
-      const int64_t prow = it.tile * BM + r;  // row of the code matrix
-      const bool valid = prow < it.n;
-      int64_t i = 0;                          // point of this row
-      float4 xs = make_float4(0.f, 0.f, 0.f, 0.f);
-      int old = -1;
-      if (valid) {
-        if (it.rows) {  // cluster-sorted order: contiguous metadata written by the reduce stage
-          i = it.rows[prow];
-          xs = it.xs_sorted[prow];
-          if (!P.first) old = it.lab_sorted[prow];
-        } else {
-          i = prow;
-          xs = it.xs[prow];
-          if (!P.first) old = it.assign[prow];
-        }
-      }
-      if (old < 0 || old >= it.k) old = -1;  // not a label: no seed
+      const bool valid = tile * BM + r < it.n;
+      const int64_t i = m.i;
+      const float4 xs = m.xs;
+      int old = m.old;
+      if (old < 0 || old >= it.k) old = -1;
       // per-row error bound and margin
       const float E = fmaf(3.f * kU, H,
                            fmaf(it.gam_tc + 2.f * kU, xs.y * QCmax,
                                 fmaf(xs.z, Cmax, fmaf(xs.w, DCmax, xs.z * DCmax))));
       const float margin = 2.f * E * (1.f + 0x1p-10f);
-      float thr = INFINITY;
-      if (ok && !__all_sync(0xffffffffu, mbar_wait(&a_full[ab], (lt / nab) & 1, &abort_s, P.wait_ns))) ok = false;
+      float thr = FLT_MAX;  // finite: padding columns (score +inf) never become candidates
       if (ok && P.debug_stall && !__all_sync(0xffffffffu, mbar_wait(&never_bar, 0, &abort_s, P.wait_ns))) ok = false;
-      if (ok && old >= 0) {
-        // seed: score of the previous centroid from the same codes, in FP32 SIMT
-        const uint8_t* arow = A0 + ab * a_bytes + r * ROWB;
-        const uint8_t* crow = it.Cq + (size_t)old * it.Kp * ESZ;
-        float dot = 0.f;
-        for (int kb = 0; kb < it.nkb; ++kb) {
-          const uint8_t* ab_row = arow + kb * (BM * ROWB);
-#pragma unroll
-          for (int ch = 0; ch < 8; ++ch) {  // 16-byte chunks, stored at chunk ^ (row & 7)
-            const uint4 av = *reinterpret_cast<const uint4*>(ab_row + ((ch ^ (r & 7)) << 4));
-            const uint4 cv = __ldg(reinterpret_cast<const uint4*>(crow + kb * ROWB + ch * 16));
-            const uint8_t* ap = reinterpret_cast<const uint8_t*>(&av);
-            const uint8_t* cp = reinterpret_cast<const uint8_t*>(&cv);
-#pragma unroll
-            for (int e = 0; e < 16 / ESZ; ++e) dot = fmaf(code_to_float<FP8>(ap + e * ESZ), code_to_float<FP8>(cp + e * ESZ), dot);
-          }
-        }
-        const float w = FP8 ? xs.x * SCs[old] : 1.f;
-        const float s_seed = __fsub_rn(Hs[old], w * dot);
-        const float Eseed = fmaf(it.gam_tc + it.gam_simt, xs.y * QCmax, 2.f * kU * (H + 2.f * xs.y * QCmax));
-        thr = __fadd_ru(__fadd_ru(s_seed, Eseed * (1.f + 0x1p-10f)), margin);
-        if (!(thr == thr)) thr = INFINITY;  // NaN seed: scan everything
-      }
-      __syncwarp();
-      if (ok && lane == 0) mbar_arrive(&a_empty[ab]);  // this warp is done reading the A tile
 
       Cand top[kT];
 #pragma unroll
       for (int t = 0; t < kT; ++t) top[t] = Cand{INFINITY, -1};
       const float nsx = -xs.x;
-      for (int c = 0; c < it.nchunks; ++c, ++gc) {
+#pragma unroll 1
+      for (int cc = 0, c = c0; cc < it.nchunks; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
         if (!ok) continue;
         const int buf = gc % NACC;
         if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gc / NACC) & 1, &abort_s, P.wait_ns))) {
@@ -446,53 +565,19 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           continue;
         }
         tc_fence_after_sync();
+        // this warp's BN/2 columns of the chunk: one or two 32-column loads, one wait
         const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + half * (BN / 2));
-        uint32_t v[32];
-        tmem_ld_32x32b_x32(tbase, v);
-        for (int sub = 0; sub < nsub; ++sub) {
-          tmem_ld_wait();
-          const int j0 = c * BN + half * (BN / 2) + sub * 32;
-          // scores s_j = h_j - (sx sc_j) acc_j, two columns per packed operation
-          float s[32];
-          const float4* h4 = reinterpret_cast<const float4*>(Hs + j0);
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const float4 hh = h4[t];
-            float2 a0 = make_float2(__uint_as_float(v[4 * t]), __uint_as_float(v[4 * t + 1]));
-            float2 a1 = make_float2(__uint_as_float(v[4 * t + 2]), __uint_as_float(v[4 * t + 3]));
-            float2 w0, w1;
-            if constexpr (FP8) {
-              const float4 sc4 = reinterpret_cast<const float4*>(SCs + j0)[t];
-              w0 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.x, sc4.y));
-              w1 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.z, sc4.w));
-            } else {
-              w0 = make_float2(-1.f, -1.f);
-              w1 = w0;
-            }
-            const float2 s0 = __ffma2_rn(w0, a0, make_float2(hh.x, hh.y));
-            const float2 s1 = __ffma2_rn(w1, a1, make_float2(hh.z, hh.w));
-            s[4 * t] = s0.x;
-            s[4 * t + 1] = s0.y;
-            s[4 * t + 2] = s1.x;
-            s[4 * t + 3] = s1.y;
-          }
-          if (sub + 1 < nsub) tmem_ld_32x32b_x32(tbase + (uint32_t)((sub + 1) * 32), v);  // next sub-chunk in flight
-          float m = INFINITY;
-#pragma unroll
-          for (int t = 0; t < 32; t += 2) m = min3f(m, s[t], s[t + 1]);
-          if (__any_sync(0xffffffffu, m <= thr)) {
-#pragma unroll
-            for (int t = 0; t < 32; ++t) {
-              if (s[t] <= thr) {
-                cand_insert(top, s[t], j0 + t);
-                thr = fminf(thr, __fadd_ru(top[0].v, margin));
-              }
-            }
-          }
-        }
+        uint32_t v0[32], v1[32];
+        tmem_ld_32x32b_x32(tbase, v0);
+        if (nsub == 2) tmem_ld_32x32b_x32(tbase + 32u, v1);
+        tmem_ld_wait();
+        // the accumulator buffer is free as soon as its values are in registers
         tc_fence_before_sync();
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        const int jb = c * BN + half * (BN / 2);
+        score_block<FP8>(v0, Hs + jb, SCs + jb, nsx, top, jb, thr, margin);
+        if (nsub == 2) score_block<FP8>(v1, Hs + jb + 32, SCs + jb + 32, nsx, top, jb + 32, thr, margin);
       }
       // merge the second half's list into the first half's (named barrier of the epilogue warps)
       if (half == 1) {
@@ -501,67 +586,81 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
       if (half == 0) {
-#pragma unroll
+#pragma unroll 1
         for (int t = 0; t < kT; ++t) {
           const Cand o = Ms[r * kT + t];
-          if (o.i >= 0) cand_insert(top, o.v, o.i);
+          if (o.i < 0) break;  // lists are sorted: the empty slots come last
+          cand_insert(top, o.v, o.i);
         }
       }
       asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-      if (ok && valid && half == 0) {
+      if (half == 0) {  // warp-uniform: the flag slots are reserved once per warp
+        const bool live = ok && valid;
         int nc = -1;  // -1: final; 0: all k; >0: candidate count
-        int cands[kT];
-        if (top[0].i < 0) {
-          nc = 0;
-        } else {
-          int cnt = 1;
-          cands[0] = top[0].i;
+        if (live) {
+          if (top[0].i < 0) {
+            nc = 0;
+          } else {
+            int cnt = 1;
 #pragma unroll
-          for (int t = 1; t < kT; ++t)
-            if (top[t].i >= 0 && __fsub_rn(top[t].v, top[0].v) <= margin) cands[cnt++] = top[t].i;
-          if (cnt == kT) nc = 0;        // maybe more than kT within the margin
-          else if (cnt > 1) nc = cnt;
+            for (int t = 1; t < kT; ++t) cnt += (top[t].i >= 0 && __fsub_rn(top[t].v, top[0].v) <= margin) ? 1 : 0;
+            if (cnt == kT) nc = 0;        // maybe more than kT within the margin
+            else if (cnt > 1) nc = cnt;
+          }
         }
-        if (nc < 0) {
+        const bool flag = live && nc >= 0;
+        const unsigned fm = __ballot_sync(0xffffffffu, flag);
+        unsigned long long slot = 0;
+        if (fm) {
+          const unsigned fullm = __ballot_sync(0xffffffffu, flag && nc == 0);
+          const int leader = __ffs(fm) - 1;
+          if (lane == leader) {
+            slot = atomicAdd(P.flag_slots, (unsigned long long)__popc(fm));
+            if (BATCH) atomicAdd(&it.ctl->n_flagged, (unsigned long long)__popc(fm));
+            if (fullm) atomicAdd(&it.ctl->n_full, (unsigned long long)__popc(fullm));
+          }
+          slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(fm & ((1u << lane) - 1u));
+        }
+        if (live && !flag) {
           it.assign[i] = top[0].i;
           changed += (old != top[0].i);
-        } else {
+        } else if (flag) {
           FlagRec rec;
           rec.i = (int32_t)i;
           rec.old = old;
           rec.nc = nc;
           rec.pad = it.b;
+          // the candidates within the margin, in increasing index order (the
+          // re-check breaks exact ties toward the lowest index)
+          int prev = -1;
 #pragma unroll
-          for (int t = 0; t < kT; ++t) rec.cand[t] = 0;
-          if (nc > 0) {
-            // increasing index order: the re-check breaks exact ties toward the lowest index
-            for (int a = 0; a < nc; ++a) {
-              int mn = a;
-              for (int b = a + 1; b < nc; ++b)
-                if (cands[b] < cands[mn]) mn = b;
-              const int tmp = cands[a];
-              cands[a] = cands[mn];
-              cands[mn] = tmp;
-              rec.cand[a] = cands[a];
+          for (int a = 0; a < kT; ++a) {
+            int nxt_j = INT_MAX;
+            if (nc > 0) {
+#pragma unroll
+              for (int t = 0; t < kT; ++t) {
+                const bool in = t < nc;  // the first nc entries are the ones within the margin
+                const int j = top[t].i;
+                if (in && j > prev && j < nxt_j) nxt_j = j;
+              }
             }
+            rec.cand[a] = (a < nc) ? nxt_j : 0;
+            if (a < nc) prev = nxt_j;
           }
-          const unsigned long long slot = atomicAdd(P.flag_slots, 1ull);
           if (slot < (unsigned long long)P.flag_cap) P.flags[slot] = rec;
-          if (BATCH) atomicAdd(&it.ctl->n_flagged, 1ull);
-          if (nc == 0) atomicAdd(&it.ctl->n_full, 1ull);
           it.assign[i] = top[0].i >= 0 ? top[0].i : 0;
         }
       }
-      ++lt;
+      if (BATCH && changed && (gt + tr.ts >= it.tend || gt + tr.ts >= tr.t1)) {
+        atomicAdd(&it.ctl->n_changed, (unsigned long long)changed);  // leaving this instance
+        changed = 0;
+      }
     }
     if (!ok) {
       abort_s = 1;
       record_timeout<BATCH>(P);
     }
-    if (changed) {
-      Ctl* cc = BATCH ? (cur_b >= 0 ? P.bctls + cur_b : nullptr) : P.ctl;
-      if (cc) atomicAdd(&cc->n_changed, (unsigned long long)changed);
-    }
+    if (!BATCH && changed) atomicAdd(&P.ctl->n_changed, (unsigned long long)changed);
   }
 
   tc_fence_before_sync();
@@ -632,6 +731,7 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   P.flag_cap = W.R;
   P.binst = W.inst;
   P.btile_off = W.tile_off;
+  P.bcta = W.cta_tile;
   P.nb = W.nb;
   P.sorted = sorted;
   P.ntiles = W.T;
@@ -644,7 +744,7 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   P.bxs_sorted = W.xs_sorted;
   P.blab_sorted = W.lab_sorted;
   P.bperm = W.perm;
-  const int grid = (int)(W.T < num_sms() ? W.T : num_sms());
+  const int grid = W.cta_grid;
   const size_t smem = tc_smem_bytes(nkb_max, bn, stages, kp_max, fp8, abufs);
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);

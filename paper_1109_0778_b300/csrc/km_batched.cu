@@ -10,13 +10,13 @@
 // sums and FP64 divide, so every instance gets the same accuracy contract.
 #include "km_internal.cuh"
 #include "km_quant.cuh"
+#include "km_recheck.cuh"
 
 namespace km {
 
 namespace {
 
 constexpr int kMaxV = 4;   // d <= 128 in batched runs: 4 floats per lane
-constexpr int RWB = 64;    // sorted positions per warp in the segmented sum
 
 __global__ void b_reset_kernel(Ctl* ctls, int nb, unsigned long long* flag_slots) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -141,67 +141,21 @@ __global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
       const int t = v * 32 + lane;
       xv[v] = t < d ? x[t] : 0.f;
     }
-    float best = INFINITY;
     int jb;
     if (rec.nc > 0) {
+      float best = INFINITY;
       jb = rec.cand[0];
       for (int q = 0; q < rec.nc; ++q) {
         const int j = rec.cand[q];
-        const float* c = I.C + (int64_t)j * d;
-        float s = 0.f, comp = 0.f;
-#pragma unroll
-        for (int v = 0; v < kMaxV; ++v) {
-          const int t = v * 32 + lane;
-          if (t < d) {
-            const float diff = __fsub_rn(xv[v], c[t]);
-            kahan_add(s, comp, __fmul_rn(diff, diff));
-          }
-        }
-        float hi = s, lo = -comp;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-          const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-          const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
-          float sh, e;
-          two_sum(hi, ohi, sh, e);
-          lo = __fadd_rn(__fadd_rn(lo, olo), e);
-          hi = sh;
-        }
-        const float D = __fadd_rn(hi, lo);
-        if (D < best) {
+        const float D = warp_sqdist<kMaxV>(xv, I.C + (int64_t)j * d, d, lane);
+        if (D < best) {  // candidates arrive in increasing index order
           best = D;
           jb = j;
         }
       }
     } else {
-#pragma unroll
-      for (int v = 0; v < kMaxV; ++v) xsh[v * 32 + lane] = xv[v];
-      __syncwarp();
-      jb = k;
-      for (int j = lane; j < k; j += 32) {
-        const float* c = I.C + (int64_t)j * d;
-        float s = 0.f, comp = 0.f;
-        for (int t = 0; t < d; ++t) {
-          const float diff = __fsub_rn(xsh[t], __ldg(c + t));
-          kahan_add(s, comp, __fmul_rn(diff, diff));
-        }
-        const float D = __fsub_rn(s, comp);
-        if (D < best) {
-          best = D;
-          jb = j;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, jb, o);
-        if (lex_less(ob, oj, best, jb)) {
-          best = ob;
-          jb = oj;
-        }
-      }
-      if (jb >= k) jb = 0;
-      __syncwarp();
+      jb = nearest_all<kMaxV>(xv, xsh, I.C, W.hq + I.kp_off, k, d, lane, __uint_as_float(W.ctls[b].hmax_bits),
+                              __uint_as_float(W.ctls[b].cmax_bits));
     }
     if (lane == 0) {
       I.assign[rec.i] = jb;
@@ -299,114 +253,185 @@ __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
       if (lane == leader) pos = atomicAdd(&W.cursor[W.inst[b].kp_off + j], __popc(peers));
       pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1));
       W.perm[W.inst[b].row_off + pos] = (int32_t)i;
+      W.lab_sorted[W.inst[b].row_off + pos] = j;
     }
   }
 }
 
-// Segmented sums over the flattened sorted positions: the run of a warp may
-// cross instance boundaries, which flush like cluster boundaries. With QM the
-// codes of each row are rewritten at its sorted position (as km_reduce.cu).
+// Segmented sums over the flattened sorted positions: each warp walks one
+// contiguous range; the rows are gathered into shared memory with cp.async one
+// batch ahead (as in km_reduce.cu). A run may cross instance boundaries, which
+// flush like cluster boundaries. With QM the codes and row statistics of each
+// row are rewritten at its sorted position.
+constexpr int kSegRB = 8;                                               // rows per batch
+constexpr size_t kSegSmem = (size_t)8 * 2 * kSegRB * 32 * kMaxV * 4;  // 8 warps x 2 stages
+
+__device__ __forceinline__ void b_cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void b_cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
 template <int QM>
-__global__ void __launch_bounds__(256) b_segsum_kernel(BWork W) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t p0 = gw * RWB; p0 < W.R; p0 += nw * RWB) {
-    const int64_t p1 = min(p0 + (int64_t)RWB, W.R);
-    float s[kMaxV], c[kMaxV], cj[kMaxV];
-#pragma unroll
-    for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
-    float objS = 0.f, objC = 0.f;
-    int cur_b = -1, cur_j = -1;
-    const BInst* I = nullptr;
-    auto flush = [&]() {
-      if (cur_j < 0) return;
-#pragma unroll
-      for (int v = 0; v < kMaxV; ++v) {
-        const int t = v * 32 + lane;
-        if (t < I->d) atomicAdd(W.sums64 + I->sum_off + (int64_t)cur_j * I->d + t, (double)s[v] - (double)c[v]);
-        s[v] = 0.f;
-        c[v] = 0.f;
+__global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
+  constexpr int RB = kSegRB, RS = 32 * kMaxV;
+  extern __shared__ __align__(16) float bseg_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* stage0 = bseg_smem + (size_t)wib * 2 * RB * RS;
+  float* stage1 = stage0 + RB * RS;
+  const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
+  const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
+  const int64_t nbat = (P1 - P0 + RB - 1) / RB;
+
+  // lane r < RB: instance (-1: finished or past the range), local point, label,
+  // row address and dimension of position P0 + b RB + r
+  auto meta = [&](int64_t b, int& ib, int& i, int& j, const float*& x, int& d) {
+    const int64_t p = P0 + b * RB + lane;
+    ib = -1;
+    i = 0;
+    j = -1;
+    x = nullptr;
+    d = 0;
+    if (lane < RB && p < P1) {
+      const int q = find_block(W.row_off, W.nb, p);
+      if (!halted(W.ctls + q)) {
+        ib = q;
+        i = W.perm[p];
+        j = W.lab_sorted[p];
+        d = W.inst[q].d;
+        x = W.inst[q].X + (int64_t)i * d;
       }
-    };
-    auto flush_obj = [&]() {
-      if (cur_b < 0) return;
-      double o = (double)objS - (double)objC;
-#pragma unroll
-      for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
-      if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[cur_b].objective, o);
-      objS = objC = 0.f;
-    };
-    for (int64_t pb = p0; pb < p1; pb += 32) {
-      const int64_t pl = pb + lane;
-      int my_b = -1, my_i = 0, my_j = -1;
-      if (pl < p1) {
-        my_b = find_block(W.row_off, W.nb, pl);
-        if (halted(W.ctls + my_b)) {
-          my_b = -1;
-        } else {
-          my_i = W.perm[pl];
-          my_j = W.inst[my_b].assign[my_i];
-        }
+    }
+  };
+  auto gather = [&](int64_t b, float* st, int ib_lane, const float* x_lane, int d_lane) {
+    const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
+    for (int r = 0; r < rows; ++r) {
+      const int q = __shfl_sync(0xffffffffu, ib_lane, r);
+      const float* x = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)x_lane, r);
+      const int d = __shfl_sync(0xffffffffu, d_lane, r);
+      if (q < 0) continue;
+      if ((d & 3) == 0) {
+        for (int o = lane; o < (d >> 2); o += 32) b_cp_async16(st + r * RS + 4 * o, x + 4 * o);
+      } else {
+        for (int o = lane; o < d; o += 32) b_cp_async4(st + r * RS + o, x + o);
       }
-      const int cnt = (int)min((int64_t)32, p1 - pb);
-      for (int r = 0; r < cnt; ++r) {
-        const int b = __shfl_sync(0xffffffffu, my_b, r);
-        const int i = __shfl_sync(0xffffffffu, my_i, r);
-        const int j = __shfl_sync(0xffffffffu, my_j, r);
-        if (b < 0) continue;  // finished instance
-        if (b != cur_b || j != cur_j) {
-          flush();
-          if (b != cur_b) {
-            flush_obj();
-            cur_b = b;
-            I = W.inst + b;
-          }
-          cur_j = j;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  float s[kMaxV], c[kMaxV], cj[kMaxV];
 #pragma unroll
-          for (int v = 0; v < kMaxV; ++v) {
-            const int t = v * 32 + lane;
-            cj[v] = t < I->d ? I->C[(int64_t)j * I->d + t] : 0.f;
-          }
+  for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
+  float objS = 0.f, objC = 0.f;
+  int cur_b = -1, cur_j = -1, cur_d = 0;
+  const BInst* I = nullptr;
+  auto flush = [&]() {
+    if (cur_j < 0) return;
+#pragma unroll
+    for (int v = 0; v < kMaxV; ++v) {
+      const int t = v * 32 + lane;
+      if (t < I->d) atomicAdd(W.sums64 + I->sum_off + (int64_t)cur_j * I->d + t, (double)s[v] - (double)c[v]);
+      s[v] = 0.f;
+      c[v] = 0.f;
+    }
+  };
+  auto flush_obj = [&]() {
+    if (cur_b < 0) return;
+    double o = (double)objS - (double)objC;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+    if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[cur_b].objective, o);
+    objS = objC = 0.f;
+  };
+
+  int b_c = -1, i_c = 0, j_c = -1, b_n = -1, i_n = 0, j_n = -1, d_c = 0, d_n = 0;
+  const float *x_c = nullptr, *x_n = nullptr;
+  float4 xs_c = make_float4(1.f, 0.f, 0.f, 0.f), xs_n = xs_c;
+  if (nbat > 0) {
+    meta(0, b_c, i_c, j_c, x_c, d_c);
+    gather(0, stage0, b_c, x_c, d_c);
+    if (QM != 0 && b_c >= 0) xs_c = __ldg(&W.xs[W.inst[b_c].row_off + i_c]);
+    if (nbat > 1) meta(1, b_n, i_n, j_n, x_n, d_n);
+  }
+  for (int64_t bt = 0; bt < nbat; ++bt) {
+    float* st = (bt & 1) ? stage1 : stage0;
+    if (bt + 1 < nbat) {
+      gather(bt + 1, (bt & 1) ? stage0 : stage1, b_n, x_n, d_n);
+      if (QM != 0 && b_n >= 0) xs_n = __ldg(&W.xs[W.inst[b_n].row_off + i_n]);
+    }
+    int b_nn = -1, i_nn = 0, j_nn = -1, d_nn = 0;
+    const float* x_nn = nullptr;
+    if (bt + 2 < nbat) meta(bt + 2, b_nn, i_nn, j_nn, x_nn, d_nn);
+    if (bt + 1 < nbat) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const int rows = (int)min((int64_t)RB, P1 - (P0 + bt * RB));
+    for (int r = 0; r < rows; ++r) {
+      const int b = __shfl_sync(0xffffffffu, b_c, r);
+      const int j = __shfl_sync(0xffffffffu, j_c, r);
+      const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, xs_c.x, r) : 1.f;
+      if (b < 0) continue;  // finished instance
+      if (b != cur_b || j != cur_j) {
+        flush();
+        if (b != cur_b) {
+          flush_obj();
+          cur_b = b;
+          I = W.inst + b;
+          cur_d = I->d;
         }
-        const int d = I->d;
-        const float* x = I->X + (int64_t)i * d;
-        float q = 0.f, xr[kMaxV];
+        cur_j = j;
 #pragma unroll
         for (int v = 0; v < kMaxV; ++v) {
           const int t = v * 32 + lane;
-          xr[v] = t < d ? __ldg(x + t) : 0.f;
-          kahan_add(s[v], c[v], xr[v]);
-          const float df = __fsub_rn(xr[v], cj[v]);
-          q = fmaf(df, df, q);
+          cj[v] = t < cur_d ? I->C[(int64_t)j * cur_d + t] : 0.f;
         }
-        kahan_add(objS, objC, q);
-        if constexpr (QM != 0) {
-          const int64_t g = pb + r;  // flattened sorted position
-          const int64_t pr = g - I->row_off;
-          const float4 xsr = __ldg(&W.xs[I->row_off + i]);
-          if (lane == 0) {
-            W.xs_sorted[g] = xsr;
-            W.lab_sorted[g] = j;
-          }
+      }
+      const int d = cur_d;
+      float xr[kMaxV], qd = 0.f;
 #pragma unroll
-          for (int v = 0; v < kMaxV; ++v) {
-            const int t = v * 32 + lane;
-            if (t < d) {
-              if constexpr (QM == 1) {
-                reinterpret_cast<__nv_bfloat16*>(W.Xq + I->xq_off)[pr * I->Kp + t] = __float2bfloat16_rn(xr[v]);
-              } else {
-                __nv_fp8_e4m3 code(xr[v] / xsr.x);
-                (W.Xq + I->xq_off)[pr * I->Kp + t] = code.__x;
-              }
+      for (int v = 0; v < kMaxV; ++v) {
+        const int t = v * 32 + lane;
+        xr[v] = t < d ? st[r * RS + t] : 0.f;
+        kahan_add(s[v], c[v], xr[v]);
+        const float df = __fsub_rn(xr[v], cj[v]);
+        qd = fmaf(df, df, qd);
+      }
+      kahan_add(objS, objC, qd);
+      if constexpr (QM != 0) {
+        const int64_t g = P0 + bt * RB + r;  // flattened sorted position
+        const int64_t pr = g - I->row_off;
+        if (lane == r) W.xs_sorted[g] = xs_c;
+#pragma unroll
+        for (int v = 0; v < kMaxV; ++v) {
+          const int t = v * 32 + lane;
+          if (t < d) {
+            if constexpr (QM == 1) {
+              reinterpret_cast<__nv_bfloat16*>(W.Xq + I->xq_off)[pr * I->Kp + t] = __float2bfloat16_rn(xr[v]);
+            } else {
+              __nv_fp8_e4m3 code(xr[v] / sxr);
+              (W.Xq + I->xq_off)[pr * I->Kp + t] = code.__x;
             }
           }
         }
       }
     }
-    flush();
-    flush_obj();
+    __syncwarp();  // every lane is done with this stage before it is refilled
+    b_c = b_n;
+    i_c = i_n;
+    j_c = j_n;
+    xs_c = xs_n;
+    b_n = b_nn;
+    i_n = i_nn;
+    j_n = j_nn;
+    x_n = x_nn;
+    d_n = d_nn;
   }
+  flush();
+  flush_obj();
 }
 
 // Divide per centroid of every instance; the warp that finishes an instance's
@@ -510,11 +535,21 @@ cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t init_batched() {
+  cudaError_t e = cudaFuncSetAttribute(b_segsum_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(b_segsum_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(b_segsum_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
+  return e;
+}
+
 cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s) {
-  const int grid = grid_for((W.R + RWB - 1) / RWB, 8, 8);
-  if (qmode == 1) b_segsum_kernel<1><<<grid, 256, 0, s>>>(W);
-  else if (qmode == 2) b_segsum_kernel<2><<<grid, 256, 0, s>>>(W);
-  else b_segsum_kernel<0><<<grid, 256, 0, s>>>(W);
+  int64_t blocks = (W.R + 8 * 64 - 1) / (8 * 64);
+  if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
+  if (qmode == 1) b_segsum_kernel<1><<<(int)blocks, 256, kSegSmem, s>>>(W);
+  else if (qmode == 2) b_segsum_kernel<2><<<(int)blocks, 256, kSegSmem, s>>>(W);
+  else b_segsum_kernel<0><<<(int)blocks, 256, kSegSmem, s>>>(W);
   return cudaGetLastError();
 }
 

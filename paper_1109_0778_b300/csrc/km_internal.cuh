@@ -96,7 +96,6 @@ struct TcParams {
   int k, Kp, nkb, bn, nchunks, stages, abufs, first;
   uint32_t idesc;
   float gam_tc;       // accumulation bound of the tensor-core sum over Kp terms
-  float gam_simt;     // accumulation bound of the FP32 SIMT seed over Kp terms
   uint64_t wait_ns;   // bound of every mbarrier wait
   int debug_stall;    // test knob: the epilogue also waits on a barrier nothing arrives on
   unsigned long long* flag_slots;  // slot counter of the flag list
@@ -105,6 +104,7 @@ struct TcParams {
   // then give only the launch shape (nkb, kp maxima), first, wait_ns and idesc
   const struct BInst* binst;
   const int64_t* btile_off;
+  const int64_t* bcta;  // [grid + 1] first flattened tile of each CTA
   int nb, sorted;
   int64_t ntiles;
   Ctl* bctls;
@@ -144,7 +144,7 @@ struct BInst {
   int64_t xq_off;    // bytes: point codes [n][Kp]
   int64_t cq_off;    // bytes: centroid codes [kp][Kp]
   int Kp, nkb, kp, nchunks;
-  float gam_tc, gam_simt;
+  float gam_tc;
   int pad0, pad1;
 };
 
@@ -155,6 +155,8 @@ struct BWork {
   const int64_t* kc_off;    // [nb + 1]
   const int64_t* kp_off;    // [nb + 1]
   const int64_t* tile_off;  // [nb + 1]
+  const int64_t* cta_tile;  // [cta_grid + 1] tile range of each CTA of the assignment launch
+  int cta_grid;
   int64_t R, KC, KP, T;     // totals: rows, centroids, padded centroids, tiles
   Ctl* ctls;                // [nb]
   unsigned long long* flag_slots;  // entries in the shared flag list
@@ -189,6 +191,7 @@ __device__ __forceinline__ int find_block(const int64_t* off, int nb, int64_t g)
   return lo;
 }
 
+cudaError_t init_batched();
 cudaError_t launch_b_reset(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s);
 cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s);
@@ -216,12 +219,13 @@ struct Problem {
 cudaError_t launch_xnorm(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_prep(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s);
-cudaError_t launch_recheck(const Problem& p, const Work& w, int first, cudaStream_t s);
+cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s);
 cudaError_t launch_count(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
 // qmode 0: sums only; 1 / 2: also rewrite the BF16 / E4M3 point codes in the
 // cluster-sorted order of this step (row p of w.Xq = point perm[p]).
+cudaError_t init_segsum();
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
 cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uint8_t* Xq, float4* xs,

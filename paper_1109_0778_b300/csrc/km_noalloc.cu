@@ -34,13 +34,15 @@ constexpr size_t kOffCtl = 0;
 constexpr size_t kOffOffs = a256(sizeof(Ctl));
 constexpr size_t kOffCursor = kOffOffs + a256(4 * (kNaMaxK + 1));
 constexpr size_t kOffPerm = kOffCursor + a256(4 * kNaMaxK);
-constexpr size_t kOffSums = kOffPerm + a256(4 * kNaMaxN);
-constexpr size_t kScratchBytes = kOffSums + a256(8 * kNaMaxKD);  // about 6.1 MB
+constexpr size_t kOffSlab = kOffPerm + a256(4 * kNaMaxN);
+constexpr size_t kOffSums = kOffSlab + a256(4 * kNaMaxN);
+constexpr size_t kScratchBytes = kOffSums + a256(8 * kNaMaxKD);  // about 10.5 MB
 
 static __device__ __align__(256) unsigned char km_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_ptr[64] = {nullptr};  // device address of the array, per device
+bool g_kernels_ready[64] = {false};   // stage kernels' shared-memory limits raised on this device
 
 int na_fail(int code, const char* msg) {
   set_last_error(msg);
@@ -103,6 +105,13 @@ KM_API int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const flo
       }
       g_scratch_ptr[dev] = p;
     }
+    if (!g_kernels_ready[dev]) {
+      if (init_segsum() != cudaSuccess) {
+        cudaGetLastError();
+        return na_fail(KM_ECUDA, "raising the segmented sum's shared-memory limit failed");
+      }
+      g_kernels_ready[dev] = true;
+    }
     base = g_scratch_ptr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -113,6 +122,7 @@ KM_API int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const flo
   w.offs = (int32_t*)(b + kOffOffs);
   w.cursor = (int32_t*)(b + kOffCursor);
   w.perm = (int32_t*)(b + kOffPerm);
+  w.lab_sorted = (int32_t*)(b + kOffSlab);
   w.sums64 = (double*)(b + kOffSums);
   Problem p{X, n, d, const_cast<float*>(C), k, const_cast<int32_t*>(assign), sums, counts};
   const size_t kd = (size_t)k * d;

@@ -6,14 +6,16 @@
 //   count   -- counts_j = |{i : a_i = j}| (shared-memory histogram when k is
 //              small enough, else global atomics), exact integers;
 //   scan    -- segment starts offs_j = sum_{j' < j} counts_j';
-//   scatter -- perm[offs_j + r] = i for the r-th member found (cursors
-//              reserved once per block and cluster for k <= 8192, else
-//              warp-aggregated; order within a segment unspecified);
-//   segsum  -- each warp walks a run of sorted positions (the loads of 4-8
-//              rows in flight at once): while the cluster
-//              stays the same it Kahan-accumulates the rows in FP32 registers,
-//              and on every cluster change it flushes its partial into an FP64
-//              sum (one atomic add per coordinate). The objective term
+//   scatter -- perm[offs_j + r] = i and slab[offs_j + r] = j for the r-th
+//              member found (cursors reserved once per block and cluster for
+//              k <= 8192, else warp-aggregated; order within a segment
+//              unspecified);
+//   segsum  -- each warp walks one contiguous range of sorted positions; the
+//              rows are gathered into shared memory with cp.async, one batch
+//              ahead of the batch being summed. While the cluster stays the
+//              same the warp Kahan-accumulates the rows in FP32 registers, and
+//              on every cluster change it flushes its partial into an FP64 sum
+//              (one atomic add per coordinate). The objective term
 //              ||x_i - c_{a_i}||^2 is formed in the same pass from the
 //              centroid held in registers for the segment.
 // Error: a Kahan-summed run of m rows carries <= 2u + O(m u^2) of the summed
@@ -30,7 +32,6 @@ namespace km {
 namespace {
 
 constexpr int kSmemHistMax = 12288;  // bins held in shared memory by the count stage
-constexpr int RW = 64;               // sorted positions per warp in the segmented sum
 
 __global__ void __launch_bounds__(256)
 count_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ counts,
@@ -101,7 +102,7 @@ scan_kernel(const int32_t* __restrict__ counts, int k, int32_t* __restrict__ off
 
 __global__ void __launch_bounds__(256)
 scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int32_t* __restrict__ cursor,
-               int32_t* __restrict__ perm, const Ctl* ctl) {
+               int32_t* __restrict__ perm, int32_t* __restrict__ slab, const Ctl* ctl) {
   if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -118,6 +119,7 @@ scatter_kernel(const int32_t* __restrict__ assign, int64_t n, int32_t* __restric
       pos = __shfl_sync(peers, pos, leader);
       pos += __popc(peers & ((1u << lane) - 1));
       perm[pos] = (int32_t)i;
+      slab[pos] = j;
     }
   }
 }
@@ -131,7 +133,7 @@ constexpr int kScatterPerThread = 16;
 
 __global__ void __launch_bounds__(256)
 scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ cursor,
-                     int32_t* __restrict__ perm, const Ctl* ctl) {
+                     int32_t* __restrict__ perm, int32_t* __restrict__ slab, const Ctl* ctl) {
   if (halted(ctl)) return;
   extern __shared__ int cnt[];  // per-cluster count, then the block's base position
   const int64_t chunk = (int64_t)blockDim.x * kScatterPerThread;
@@ -152,7 +154,10 @@ scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32
 #pragma unroll
     for (int q = 0; q < kScatterPerThread; ++q) {
       const int64_t i = c0 + (int64_t)q * blockDim.x + threadIdx.x;
-      if (lab[q] >= 0) perm[cnt[lab[q]] + rank[q]] = (int32_t)i;
+      if (lab[q] >= 0) {
+        perm[cnt[lab[q]] + rank[q]] = (int32_t)i;
+        slab[cnt[lab[q]] + rank[q]] = lab[q];
+      }
     }
     __syncthreads();
   }
@@ -170,97 +175,154 @@ __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, i
   }
 }
 
+// Rows of one gathered batch per stage of the segmented sum (two stages of at
+// most 4 KB per warp, so that two CTAs of 8 warps share an SM).
+template <int V>
+__host__ __device__ constexpr int seg_rows() {
+  return V == 1 ? 32 : (V == 2 ? 16 : (V <= 4 ? 8 : 4));
+}
+
+template <int V>
+__host__ __device__ constexpr size_t seg_smem_bytes() {
+  return (size_t)8 * 2 * seg_rows<V>() * 32 * V * sizeof(float);  // 8 warps x 2 stages x rows x 32V floats
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // QM = 1 / 2: the pass also writes the BF16 / E4M3 codes of each row it reads
-// at its sorted position p (row stride Kp elements), using the row scale in xs;
-// the codes equal those the quantisation stage produces for the same point.
+// at its sorted position p (row stride Kp elements), using the row scale in xs,
+// and the row statistics xs at p; the codes equal those the quantisation stage
+// produces for the same point.
 template <int V, int QM>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
-              const int32_t* __restrict__ assign, const int32_t* __restrict__ perm,
-              double* __restrict__ sums64, Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs,
-              int Kp, float4* __restrict__ xs_sorted, int32_t* __restrict__ lab_sorted) {
-  constexpr int U = V <= 2 ? 8 : 4;  // rows whose loads are in flight together
+              const int32_t* __restrict__ perm, const int32_t* __restrict__ slab, double* __restrict__ sums64,
+              Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs, int Kp,
+              float4* __restrict__ xs_sorted) {
+  constexpr int RB = seg_rows<V>();  // rows per batch (lane r < RB holds row r's indices)
+  constexpr int RS = 32 * V;         // shared-memory floats per row
+  extern __shared__ __align__(16) float seg_smem[];
   if (halted(ctl)) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float objS = 0.f, objC = 0.f;
-  for (int64_t p0 = gw * RW; p0 < n; p0 += nw * RW) {
-    const int64_t p1 = min(p0 + (int64_t)RW, n);
-    float s[V], c[V], cj[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
-    int cur = -1;
-    for (int64_t pb = p0; pb < p1; pb += 32) {
-      // each lane fetches one position of this batch; rows are then walked in order
-      const int64_t pl = pb + lane;
-      int my_i = 0, my_j = -1;
-      if (pl < p1) {
-        my_i = perm[pl];
-        my_j = assign[my_i];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* stage0 = seg_smem + (size_t)wib * 2 * RB * RS;
+  float* stage1 = stage0 + RB * RS;
+  const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
+  const int64_t P0 = n * gw / nw, P1 = n * (gw + 1) / nw;  // this warp's sorted positions
+  const int64_t nb = (P1 - P0 + RB - 1) / RB;
+  const bool vec = (d & 3) == 0;  // rows start on 16-byte boundaries: 16-byte copies
+  const int cpr = vec ? d >> 2 : d;  // copies per row
+  const int ncp = RB * cpr;
+
+  // indices of batch b: lane r < RB takes position P0 + b RB + r
+  auto meta = [&](int64_t b, int& i, int& j) {
+    const int64_t p = P0 + b * RB + lane;
+    i = 0;
+    j = -1;
+    if (lane < RB && p < P1) {
+      i = perm[p];
+      j = slab[p];
+    }
+  };
+  // gathers the rows of batch b into a stage (one commit group)
+  auto gather = [&](int64_t b, float* st, int i_lane) {
+    const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
+    for (int c0 = 0; c0 < ncp; c0 += 32) {
+      const int c = c0 + lane;
+      const int r = min(c / cpr, RB - 1), o = c - r * cpr;
+      const int ir = __shfl_sync(0xffffffffu, i_lane, r);
+      if (c < ncp && r < rows) {
+        if (vec) cp_async16(st + r * RS + 4 * o, X + (int64_t)ir * d + 4 * o);
+        else cp_async4(st + r * RS + o, X + (int64_t)ir * d + o);
       }
-      const int cnt = (int)min((int64_t)32, p1 - pb);
-      for (int r0 = 0; r0 < cnt; r0 += U) {
-        float xr[U][V];
-        int ir[U], jr[U];
+    }
+    cp_async_commit();
+  };
+
+  float s[V], c[V], cj[V];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {  // issue the loads of U rows before using any
-          ir[u] = __shfl_sync(0xffffffffu, my_i, (r0 + u) & 31);
-          jr[u] = __shfl_sync(0xffffffffu, my_j, (r0 + u) & 31);
-          const float* x = X + (int64_t)ir[u] * d;
+  for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
+  float objS = 0.f, objC = 0.f;
+  int cur = -1;
+  int i_c = 0, j_c = -1, i_n = 0, j_n = -1;
+  float4 xs_c = make_float4(1.f, 0.f, 0.f, 0.f), xs_n = xs_c;
+  if (nb > 0) {
+    meta(0, i_c, j_c);
+    gather(0, stage0, i_c);
+    if (QM != 0 && lane < RB && j_c >= 0) xs_c = __ldg(&xs[i_c]);
+    if (nb > 1) meta(1, i_n, j_n);
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    float* st = (b & 1) ? stage1 : stage0;
+    if (b + 1 < nb) {
+      gather(b + 1, (b & 1) ? stage0 : stage1, i_n);
+      if (QM != 0 && lane < RB && j_n >= 0) xs_n = __ldg(&xs[i_n]);
+    }
+    int i_nn = 0, j_nn = -1;
+    if (b + 2 < nb) meta(b + 2, i_nn, j_nn);
+    if (b + 1 < nb) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncwarp();
+    const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
+    for (int r = 0; r < rows; ++r) {
+      const int j = __shfl_sync(0xffffffffu, j_c, r);
+      if (j != cur) {
+        if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+        cur = j;
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            xr[u][v] = (r0 + u < cnt && t < d) ? __ldg(x + t) : 0.f;
-          }
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
         }
+      }
+      float xr[V], q = 0.f;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (r0 + u >= cnt) break;
-          const int j = jr[u];
-          if (j != cur) {
-            if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
-            cur = j;
+      for (int v = 0; v < V; ++v) {
+        const int t = v * 32 + lane;
+        xr[v] = t < d ? st[r * RS + t] : 0.f;
+        kahan_add(s[v], c[v], xr[v]);
+        const float df = __fsub_rn(xr[v], cj[v]);
+        q = fmaf(df, df, q);
+      }
+      kahan_add(objS, objC, q);
+      if constexpr (QM != 0) {
+        const int64_t prow = P0 + b * RB + r;
+        const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, xs_c.x, r) : 1.f;
+        if (lane == r) xs_sorted[prow] = xs_c;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const int t = v * 32 + lane;
-              cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
-            }
-          }
-          float q = 0.f;
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            kahan_add(s[v], c[v], xr[u][v]);
-            const float df = __fsub_rn(xr[u][v], cj[v]);
-            q = fmaf(df, df, q);
-          }
-          kahan_add(objS, objC, q);
-          if constexpr (QM != 0) {
-            const int64_t prow = pb + r0 + u;
-            const float4 xsr = __ldg(&xs[ir[u]]);
-            const float sxr = QM == 2 ? xsr.x : 1.f;
-            if (lane == 0) {
-              xs_sorted[prow] = xsr;
-              lab_sorted[prow] = j;
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const int t = v * 32 + lane;
-              if (t < d) {
-                if constexpr (QM == 1) {
-                  reinterpret_cast<__nv_bfloat16*>(Xq)[prow * Kp + t] = __float2bfloat16_rn(xr[u][v]);
-                } else {
-                  __nv_fp8_e4m3 code(xr[u][v] / sxr);
-                  Xq[prow * Kp + t] = code.__x;
-                }
-              }
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          if (t < d) {
+            if constexpr (QM == 1) {
+              reinterpret_cast<__nv_bfloat16*>(Xq)[prow * Kp + t] = __float2bfloat16_rn(xr[v]);
+            } else {
+              __nv_fp8_e4m3 code(xr[v] / sxr);
+              Xq[prow * Kp + t] = code.__x;
             }
           }
         }
       }
     }
-    if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+    __syncwarp();  // every lane is done with this stage before it is refilled
+    i_c = i_n;
+    j_c = j_n;
+    xs_c = xs_n;
+    i_n = i_nn;
+    j_n = j_nn;
   }
+  if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
   double o = (double)objS - (double)objC;
 #pragma unroll
   for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
@@ -343,34 +405,62 @@ cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
     const int64_t cap = (int64_t)num_sms() * 4;
     if (blocks > cap) blocks = cap;
     scatter_block_kernel<<<(int)blocks, 256, (size_t)p.k * sizeof(int), s>>>(p.assign, p.n, p.k, w.cursor, w.perm,
-                                                                              w.ctl);
+                                                                              w.lab_sorted, w.ctl);
     return cudaGetLastError();
   }
   int64_t blocks = (p.n + 255) / 256;
   const int64_t cap = (int64_t)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  scatter_kernel<<<(int)blocks, 256, 0, s>>>(p.assign, p.n, w.cursor, w.perm, w.ctl);
+  scatter_kernel<<<(int)blocks, 256, 0, s>>>(p.assign, p.n, w.cursor, w.perm, w.lab_sorted, w.ctl);
   return cudaGetLastError();
 }
 
+template <int V, int QM>
+cudaError_t seg_attr() {
+  return cudaFuncSetAttribute(segsum_kernel<V, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)seg_smem_bytes<V>());
+}
+
+template <int V>
+cudaError_t seg_attrs() {
+  cudaError_t e = seg_attr<V, 0>();
+  if (e == cudaSuccess) e = seg_attr<V, 1>();
+  if (e == cudaSuccess) e = seg_attr<V, 2>();
+  return e;
+}
+
+cudaError_t init_segsum() {
+  cudaError_t e = seg_attrs<1>();
+  if (e == cudaSuccess) e = seg_attrs<2>();
+  if (e == cudaSuccess) e = seg_attrs<3>();
+  if (e == cudaSuccess) e = seg_attrs<4>();
+  if (e == cudaSuccess) e = seg_attrs<5>();
+  if (e == cudaSuccess) e = seg_attrs<6>();
+  if (e == cudaSuccess) e = seg_attrs<7>();
+  if (e == cudaSuccess) e = seg_attrs<8>();
+  return e;
+}
+
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode, int Kp) {
-  int64_t warps = (p.n + RW - 1) / RW;
-  int64_t blocks = (warps + 7) / 8;
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (blocks > cap) blocks = cap;
+  // two CTAs of 8 warps per SM; each warp takes a contiguous range of at least 64 positions
+  int64_t blocks = (p.n + 8 * 64 - 1) / (8 * 64);
+  if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
   const int V = (p.d + 31) / 32;
   switch (V) {
-#define KM_CASE(v)                                                                                              \
-  case v:                                                                                                        \
-    if (qmode == 1)                                                                                              \
-      segsum_kernel<v, 1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
-                                                      w.Xq, w.xs, Kp, w.xs_sorted, w.lab_sorted);                \
-    else if (qmode == 2)                                                                                         \
-      segsum_kernel<v, 2><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
-                                                      w.Xq, w.xs, Kp, w.xs_sorted, w.lab_sorted);                \
-    else                                                                                                         \
-      segsum_kernel<v, 0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, p.C, p.assign, w.perm, w.sums64, w.ctl,     \
-                                                      nullptr, nullptr, 0, nullptr, nullptr);                    \
+#define KM_CASE(v)                                                                                               \
+  case v:                                                                                                         \
+    if (qmode == 1)                                                                                               \
+      segsum_kernel<v, 1><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
+                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
+                                                                        w.xs_sorted);                             \
+    else if (qmode == 2)                                                                                          \
+      segsum_kernel<v, 2><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
+                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
+                                                                        w.xs_sorted);                             \
+    else                                                                                                          \
+      segsum_kernel<v, 0><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
+                                                                        w.sums64, w.ctl, nullptr, nullptr, 0,     \
+                                                                        nullptr);                                 \
     break;
     KM_CASE(1) KM_CASE(2) KM_CASE(3) KM_CASE(4) KM_CASE(5) KM_CASE(6) KM_CASE(7) KM_CASE(8)
 #undef KM_CASE

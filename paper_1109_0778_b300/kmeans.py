@@ -199,17 +199,19 @@ def run_host(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, preci
     return st.as_dict()
 
 
-def run_batched(problems, iters, tol=0.0, *, precision="bf16", recheck=True, stream=None, warm_start=False):
+def run_batched(problems, iters, tol=0.0, *, precision="bf16", recheck=True, stream=None, warm_start=False,
+                profile=False):
     """kmeans_run_batched over a list of (X, C, assign, sums, counts) device-tensor tuples.
 
-    Every C is updated in place. Returns the list of per-instance stats dicts.
+    Every C is updated in place. Returns the list of per-instance stats dicts
+    (with ``profile``, each carries the batch's device time per stage).
     """
     count = len(problems)
     arr = (Instance * count)()
     for b, (X, C, assign, sums, counts) in enumerate(problems):
         n, d, k = _check_tensors(X, C, assign, sums, counts)
         arr[b] = Instance(X.data_ptr(), n, d, k, C.data_ptr(), assign.data_ptr(), sums.data_ptr(), counts.data_ptr())
-    o = make_opts(precision, recheck, _stream_handle(stream), False, warm_start)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
     st = (Stats * count)()
     _check(_lib.kmeans_run_batched(ctypes.byref(o), arr, count, int(iters), float(tol), st))
     return [s.as_dict() for s in st]
