@@ -156,16 +156,8 @@ TcShape tc_shape(int precision, int d, int k) {
   t.bn = t.nkb <= 2 ? 128 : 64;
   t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of either width
   t.nchunks = t.kp / t.bn;
-  // dynamic shared memory: 227 KB opt-in minus 1 KB of static smem; the A
-  // buffers, h_j (and scales) and the candidate merge buffer are fixed, B stages
-  // fill the rest. Prefer a double-buffered A tile; fall back to one buffer.
-  const size_t budget = 227 * 1024 - 1024, b = (size_t)t.nkb * t.bn * 128;
-  t.stages = 0;
-  for (int abufs = 2; abufs >= 1 && t.stages < 2; --abufs) {
-    const size_t fixed = tc_smem_bytes(t.nkb, t.bn, 0, t.kp, t.fp8, abufs);
-    t.abufs = abufs;
-    t.stages = fixed + 2 * b <= budget ? (int)std::min<size_t>(8, (budget - fixed) / b) : 0;
-  }
+  // dynamic shared memory: A slots, B stages, h_j (and scales)
+  t.stages = tc_pick_buffers(t.nkb, t.bn, t.kp, t.fp8, &t.abufs);
   return t;
 }
 
@@ -837,13 +829,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.nkb_max = std::max(P.nkb_max, I.nkb);
     P.kp_max = std::max(P.kp_max, I.kp);
   }
-  const size_t budget = 227 * 1024 - 1024, bstage = (size_t)P.nkb_max * P.bn * 128;
-  P.stages = 0;
-  for (int abufs = 2; abufs >= 1 && P.stages < 2; --abufs) {
-    const size_t fixed = tc_smem_bytes(P.nkb_max, P.bn, 0, P.kp_max, P.fp8, abufs);
-    P.abufs = abufs;
-    P.stages = fixed + 2 * bstage <= budget ? (int)std::min<size_t>(8, (budget - fixed) / bstage) : 0;
-  }
+  P.stages = tc_pick_buffers(P.nkb_max, P.bn, P.kp_max, P.fp8, &P.abufs);
   if (P.stages < 2) return fail(KM_EUNSUPPORTED, "largest k of the batch does not fit the tensor-core pipeline");
   // contiguous tile ranges per CTA, balanced by a work model of a tile: MMA
   // and epilogue work ~ chunks x K blocks, plus a fixed per-tile cost

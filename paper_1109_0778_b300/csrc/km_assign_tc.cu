@@ -17,10 +17,12 @@
 // metadata of the CTA's next tile while it works on the current one.
 //
 // Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and TMEM
-// owner, warps 2-9 = epilogue (two per TMEM lane quarter, each taking half of
-// every chunk's columns; the two candidate lists of a row are merged through
-// shared memory at the end of the tile). h_j (and the FP8 scales) are staged in
-// shared memory once per CTA. Every mbarrier wait is bounded in time; on
+// owner, warps 2-9 = epilogue in two groups of four (one warp per TMEM lane
+// quarter). Row tiles go in pairs: each B chunk is loaded once and multiplied
+// with both tiles of the pair, group u scores tile u (accumulators in TMEM
+// buffers u and u + 2), and each row has a single owner thread that sees all of
+// its columns. h_j (and the FP8 scales) are staged in shared memory once per
+// CTA. Every mbarrier wait is bounded in time; on
 // expiry the kernel records KM_ETIMEOUT, drains what it issued, frees TMEM and
 // returns.
 //
@@ -69,6 +71,7 @@ constexpr uint32_t ROWB = 128;               // bytes of one K block row
 constexpr uint32_t TMEM_COLS = 512;          // 4 accumulator buffers x up to 128 columns
 constexpr int NACC = 4;
 constexpr int MAX_STAGES = 8;
+constexpr int MAX_ABUF = 4;                  // A slots (row tiles) in the smem ring
 
 constexpr int kT = kMaxCand;  // candidate slots per row
 
@@ -78,19 +81,14 @@ struct Cand {
 };
 
 // Sorted insert into the row's candidate list (ascending score; strict
-// comparisons keep the earlier, lower index first among equal scores).
+// comparisons keep the earlier, lower index first among equal scores). Written
+// without branches so that the list stays in registers.
 __device__ __forceinline__ void cand_insert(Cand (&top)[kT], float v, int j) {
-  if (!(v < top[kT - 1].v)) return;
 #pragma unroll
-  for (int t = kT - 1; t > 0; --t) {
-    if (v < top[t - 1].v) {
-      top[t] = top[t - 1];
-    } else {
-      top[t] = Cand{v, j};
-      return;
-    }
+  for (int t = kT - 1; t >= 0; --t) {
+    const bool here = (t == 0) || !(v < top[t > 0 ? t - 1 : 0].v);
+    if (v < top[t].v) top[t] = here ? Cand{v, j} : top[t > 0 ? t - 1 : 0];
   }
-  top[0] = Cand{v, j};
 }
 
 __device__ __forceinline__ float min3f(float a, float b, float c) {
@@ -328,8 +326,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   constexpr int KBE = ROWB / (FP8 ? 1 : 2);  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t a_full[2], a_empty[2], b_full[MAX_STAGES], b_empty[MAX_STAGES], acc_full[NACC], acc_empty[NACC];
-  __shared__ uint64_t drain_bar, never_bar;
+  __shared__ uint64_t a_full[MAX_ABUF], a_empty[MAX_ABUF], b_full[MAX_STAGES], b_empty[MAX_STAGES];
+  __shared__ uint64_t acc_full[NACC], acc_empty[NACC], drain_bar, never_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s, halt_s;
 
@@ -342,27 +340,27 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // buffer sizes follow the launch maxima (P.nkb, P.nchunks); a tile uses its own nkb, nchunks
   const int BN = P.bn, stages = P.stages;
-  const uint32_t a_bytes = (uint32_t)P.nkb * BM * ROWB;      // one A buffer
+  const uint32_t a_bytes = (uint32_t)P.nkb * BM * ROWB;      // one A slot
   const uint32_t b_kblk = (uint32_t)BN * ROWB;               // one K block of a B stage
   const uint32_t b_bytes = (uint32_t)P.nkb * b_kblk;         // one B stage
+  const int nab = P.abufs;                                    // A slots (ring)
+  const bool pairs = nab >= 2;                                // two row tiles per B chunk
   uint8_t* A0 = smem;
-  const int nab = P.abufs;                                    // A buffers: 2 (double) or 1
   uint8_t* B0 = smem + nab * a_bytes;
   const int kpmax = P.nchunks * BN;
   float* Hs = reinterpret_cast<float*>(B0 + (size_t)stages * b_bytes);  // [kpmax]
   float* SCs = Hs + kpmax;                                               // [kpmax] (FP8)
-  Cand* Ms = reinterpret_cast<Cand*>(SCs + (FP8 ? kpmax : 0));           // [BM][kT] merge buffer
   const TileRange tr = tile_range<BATCH>(P);
 
   if (threadIdx.x == 0) {
     abort_s = 0;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < nab; ++b) {
       mbar_init(&a_full[b], 1);
-      mbar_init(&a_empty[b], 1);  // the MMA commit of the tile's last chunk
+      mbar_init(&a_empty[b], 1);  // the MMA commit after the tile's last chunk
     }
     for (int b = 0; b < NACC; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], NEPI);
+      mbar_init(&acc_empty[b], NEPI / 2);  // the four warps of the buffer's group
     }
     for (int s = 0; s < stages; ++s) {
       mbar_init(&b_full[s], 1);
@@ -391,37 +389,44 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   tc_fence_after_sync();
   const uint32_t tmem_base = tmem_base_s;
 
+  // Every role walks the same sequence of tile pairs: the CTA's tiles in order,
+  // two consecutive ones of the same instance at a time (one when the next
+  // tile is absent or belongs to another instance). Tile u of a pair is read
+  // by epilogue group u; its accumulators are TMEM buffers u and u + 2.
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      int lt = 0, gc = 0;              // tiles and chunks issued so far by this CTA
+      int lt = 0, gc = 0;              // tiles and chunks loaded so far by this CTA
       int last_a = -1, last_s = -1;    // barrier slots of the most recent A and B loads
       uint32_t last_aph = 0, last_sph = 0;
       bool ok = true;
       Item it;
       it.b = -1;
-      int labn = -2;                   // label of the next tile, loaded one tile ahead (-2: not loaded)
-      for (int64_t gt = tr.t0; gt < tr.t1 && ok; gt += tr.ts) {
-        if (seek<BATCH>(P, &mapX, &mapC, gt, it)) {
-          labn = -2;
-          if (BATCH && !it.skip) {
-            // tensor maps in global memory: order the host's writes before the async proxy reads them
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
-          }
+      for (int64_t ga = tr.t0; ga < tr.t1 && ok;) {
+        if (seek<BATCH>(P, &mapX, &mapC, ga, it) && BATCH && !it.skip) {
+          // tensor maps in global memory: order the host's writes before the async proxy reads them
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
+          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
         }
-        if (it.skip) continue;
-        const int64_t tile = gt - it.tile0;
-        const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile), it, BN);
-        labn = (gt + tr.ts < tr.t1 && gt + tr.ts < it.tend) ? tile_label(P, it, tile + tr.ts) : -2;
-        const int ab = lt % nab;
-        if (!mbar_wait(&a_empty[ab], ((lt / nab) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
-        mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB);
-        for (int kb = 0; kb < it.nkb; ++kb)
-          tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, (int)(tile * BM));
-        last_a = ab;
-        last_aph = (lt / nab) & 1;
-        for (int cc = 0, c = c0; cc < it.nchunks; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
+        if (it.skip) {
+          ga += tr.ts;
+          continue;
+        }
+        const int64_t gb = ga + tr.ts;
+        const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
+        const int64_t tile0 = ga - it.tile0;
+        const int c0 = first_chunk(tile_label(P, it, tile0), it, BN);
+        for (int u = 0; u < ntp && ok; ++u, ++lt) {
+          const int ab = lt % nab;
+          if (!mbar_wait(&a_empty[ab], ((lt / nab) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
+          mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB);
+          const int row0 = (int)((u ? gb - it.tile0 : tile0) * BM);
+          for (int kb = 0; kb < it.nkb; ++kb)
+            tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, row0);
+          last_a = ab;
+          last_aph = (lt / nab) & 1;
+        }
+        for (int cc = 0, c = c0; cc < it.nchunks && ok; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
           const int s = gc % stages;
           if (!mbar_wait(&b_empty[s], ((gc / stages) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk);
@@ -430,7 +435,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           last_s = s;
           last_sph = (gc / stages) & 1;
         }
-        ++lt;
+        ga = ntp == 2 ? gb + tr.ts : gb;
       }
       if (!ok) {
         abort_s = 1;
@@ -445,38 +450,55 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       int lt = 0, gc = 0;
+      int gu[2] = {0, 0};  // chunks issued per epilogue group
       bool ok = true, issued = false;
       Item it;
       it.b = -1;
-      for (int64_t gt = tr.t0; gt < tr.t1 && ok; gt += tr.ts) {
-        seek<BATCH>(P, &mapX, &mapC, gt, it);
-        if (it.skip) continue;
-        const int ab = lt % nab;
-        if (!mbar_wait(&a_full[ab], (lt / nab) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
+      for (int64_t ga = tr.t0; ga < tr.t1 && ok;) {
+        seek<BATCH>(P, &mapX, &mapC, ga, it);
+        if (it.skip) {
+          ga += tr.ts;
+          continue;
+        }
+        const int64_t gb = ga + tr.ts;
+        const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
+        int abs_[2];
+        for (int u = 0; u < ntp; ++u) {
+          abs_[u] = (lt + u) % nab;
+          if (!mbar_wait(&a_full[abs_[u]], ((lt + u) / nab) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
+        }
+        if (!ok) break;
         tc_fence_after_sync();
-        const uint32_t a_addr = smem_u32(A0 + ab * a_bytes);
-        for (int cc = 0; cc < it.nchunks; ++cc, ++gc) {
-          const int s = gc % stages, buf = gc % NACC;
+        for (int cc = 0; cc < it.nchunks && ok; ++cc, ++gc) {
+          const int s = gc % stages;
           if (!mbar_wait(&b_full[s], (gc / stages) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
-          if (!mbar_wait(&acc_empty[buf], ((gc / NACC) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
           tc_fence_after_sync();
           const uint32_t b_addr = smem_u32(B0 + s * b_bytes);
-          const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
-          for (int kb = 0; kb < it.nkb; ++kb) {
+          for (int u = 0; u < ntp; ++u) {
+            const int buf = 2 * (gu[u] & 1) + u;
+            if (!mbar_wait(&acc_empty[buf], ((gu[u] >> 1) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
+            tc_fence_after_sync();
+            const uint32_t a_addr = smem_u32(A0 + abs_[u] * a_bytes);
+            const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
+            for (int kb = 0; kb < it.nkb; ++kb) {
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ad = sdesc_k_sw128(a_addr + kb * (BM * ROWB) + kk * 32);
-              const uint64_t bd = sdesc_k_sw128(b_addr + kb * b_kblk + kk * 32);
-              if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
-              else mma_bf16(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
+              for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = sdesc_k_sw128(a_addr + kb * (BM * ROWB) + kk * 32);
+                const uint64_t bd = sdesc_k_sw128(b_addr + kb * b_kblk + kk * 32);
+                if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
+                else mma_bf16(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
+              }
             }
+            issued = true;
+            mma_commit(&acc_full[buf]);
+            ++gu[u];
           }
-          issued = true;
-          mma_commit(&b_empty[s]);
-          mma_commit(&acc_full[buf]);
+          if (ok) mma_commit(&b_empty[s]);
         }
-        if (ok) mma_commit(&a_empty[ab]);
-        ++lt;
+        if (ok)
+          for (int u = 0; u < ntp; ++u) mma_commit(&a_empty[abs_[u]]);
+        lt += ntp;
+        ga = ntp == 2 ? gb + tr.ts : gb;
       }
       if (!ok) {
         abort_s = 1;
@@ -490,11 +512,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
   } else {
     // ---------------------------------------------------------------- epilogue (warps 2..9)
-    const int q = warp & 3;            // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;  // which half of each chunk's columns
-    const int r = q * 32 + lane;
-    const int nsub = BN / 64;          // 32-column sub-chunks per half
-    int gc = 0;
+    const int q = warp & 3;                // TMEM lane quarter this warp may access
+    const int grp = (warp - 2) >> 2;       // epilogue group: tile u = grp of each pair
+    const int r = q * 32 + lane;           // row of the tile this thread owns
+    const int nblk = BN / 32;              // 32-column blocks per chunk
+    int gu = 0;                            // chunks of this group consumed so far
     bool ok = true;
     unsigned int changed = 0;
     Item it;
@@ -502,14 +524,12 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     float H = 0.f, Cmax = 0.f, QCmax = 0.f, DCmax = 0.f;  // per-step maxima of the instance
     RowMeta nxt;
     bool have_nxt = false;
-    int labn = -2;
-    // Every epilogue warp runs every tile to the end, even after a timeout (then
-    // skipping waits and work), so that all of them reach the named barriers of
-    // the candidate merge the same number of times.
-    for (int64_t gt = tr.t0; gt < tr.t1; gt += tr.ts) {
-      if (seek<BATCH>(P, &mapX, &mapC, gt, it)) {
+    // Every epilogue warp walks every pair to the end, even after a timeout
+    // (then skipping waits and work), so that all of them reach the named
+    // barrier of the batched h staging the same number of times.
+    for (int64_t ga = tr.t0; ga < tr.t1;) {
+      if (seek<BATCH>(P, &mapX, &mapC, ga, it)) {
         have_nxt = false;
-        labn = -2;
         if (BATCH && !it.skip) {
           // this instance's h_j (and scales) into shared memory
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
@@ -527,17 +547,28 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           DCmax = __uint_as_float(ctl->dcmax_bits);
         }
       }
-      if (it.skip) continue;
-      const int64_t tile = gt - it.tile0;
+      if (it.skip) {
+        ga += tr.ts;
+        continue;
+      }
+      const int64_t gb = ga + tr.ts;
+      const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
+      const int64_t ga_next = ntp == 2 ? gb + tr.ts : gb;
+      const int64_t tile0 = ga - it.tile0;
+      if (grp >= ntp) {  // no tile for this group in this pair
+        ga = ga_next;
+        continue;
+      }
+      const int64_t tile = grp ? gb - it.tile0 : tile0;
+      const int c0 = first_chunk(tile_label(P, it, tile0), it, BN);
       const RowMeta m = have_nxt ? nxt : fetch_meta<BATCH>(P, it, tile, r);
-      const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile), it, BN);
-      // the next tile of this CTA, when it belongs to the same instance: its loads overlap this tile
-      have_nxt = gt + tr.ts < tr.t1 && gt + tr.ts < it.tend;
-      if (have_nxt) {
-        nxt = fetch_meta<BATCH>(P, it, tile + tr.ts, r);
-        labn = tile_label(P, it, tile + tr.ts);
-      } else {
-        labn = -2;
+      // this group's tile of the next pair, when it belongs to the same instance: its loads overlap this tile
+      {
+        const int64_t na = ga_next, nb2 = ga_next + tr.ts;
+        const int64_t ntile = grp ? nb2 : na;
+        have_nxt = na < tr.t1 && na < it.tend && ntile < tr.t1 && ntile < it.tend &&
+                   (grp == 0 || (pairs && nb2 < tr.t1 && nb2 < it.tend));
+        if (have_nxt) nxt = fetch_meta<BATCH>(P, it, ntile - it.tile0, r);
       }
       const bool valid = tile * BM + r < it.n;
       const int64_t i = m.i;
@@ -556,45 +587,37 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 #pragma unroll
       for (int t = 0; t < kT; ++t) top[t] = Cand{INFINITY, -1};
       const float nsx = -xs.x;
+      const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
+      // the tile's 32-column blocks in chunk order
+      const int nall = it.nchunks * nblk;
+      uint32_t v[32];
+      int c = c0;
 #pragma unroll 1
-      for (int cc = 0, c = c0; cc < it.nchunks; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
-        if (!ok) continue;
-        const int buf = gc % NACC;
-        if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gc / NACC) & 1, &abort_s, P.wait_ns))) {
-          ok = false;
-          continue;
+      for (int kb = 0; kb < nall && ok; ++kb) {
+        const int blk = kb % nblk;
+        const int buf = 2 * (gu & 1) + grp;
+        if (blk == 0) {  // a new chunk: wait for its accumulators
+          if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gu >> 1) & 1, &abort_s, P.wait_ns))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after_sync();
         }
-        tc_fence_after_sync();
-        // this warp's BN/2 columns of the chunk: one or two 32-column loads, one wait
-        const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + half * (BN / 2));
-        uint32_t v0[32], v1[32];
-        tmem_ld_32x32b_x32(tbase, v0);
-        if (nsub == 2) tmem_ld_32x32b_x32(tbase + 32u, v1);
+        tmem_ld_32x32b_x32(trow + (uint32_t)(buf * 128 + blk * 32), v);
         tmem_ld_wait();
-        // the accumulator buffer is free as soon as its values are in registers
-        tc_fence_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
-        const int jb = c * BN + half * (BN / 2);
-        score_block<FP8>(v0, Hs + jb, SCs + jb, nsx, top, jb, thr, margin);
-        if (nsub == 2) score_block<FP8>(v1, Hs + jb + 32, SCs + jb + 32, nsx, top, jb + 32, thr, margin);
-      }
-      // merge the second half's list into the first half's (named barrier of the epilogue warps)
-      if (half == 1) {
-#pragma unroll
-        for (int t = 0; t < kT; ++t) Ms[r * kT + t] = top[t];
-      }
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-      if (half == 0) {
-#pragma unroll 1
-        for (int t = 0; t < kT; ++t) {
-          const Cand o = Ms[r * kT + t];
-          if (o.i < 0) break;  // lists are sorted: the empty slots come last
-          cand_insert(top, o.v, o.i);
+        if (blk == nblk - 1) {  // the chunk's accumulators are all in registers: release the buffer
+          tc_fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        const int j0 = c * BN + blk * 32;
+        score_block<FP8>(v, Hs + j0, SCs + j0, nsx, top, j0, thr, margin);
+        if (blk == nblk - 1) {
+          ++gu;
+          c = (c + 1 == it.nchunks) ? 0 : c + 1;
         }
       }
-      asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-      if (half == 0) {  // warp-uniform: the flag slots are reserved once per warp
+      {  // warp-uniform: the flag slots are reserved once per warp
         const bool live = ok && valid;
         int nc = -1;  // -1: final; 0: all k; >0: candidate count
         if (live) {
@@ -651,10 +674,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           it.assign[i] = top[0].i >= 0 ? top[0].i : 0;
         }
       }
-      if (BATCH && changed && (gt + tr.ts >= it.tend || gt + tr.ts >= tr.t1)) {
+      if (BATCH && changed && (ga_next >= it.tend || ga_next >= tr.t1)) {
         atomicAdd(&it.ctl->n_changed, (unsigned long long)changed);  // leaving this instance
         changed = 0;
       }
+      ga = ga_next;
     }
     if (!ok) {
       abort_s = 1;
@@ -674,8 +698,31 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 }  // namespace
 
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs) {
-  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * nkb * bn * ROWB + (size_t)kp * 4 * (fp8 ? 2 : 1) +
-         (size_t)BM * kT * sizeof(Cand);
+  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * nkb * bn * ROWB + (size_t)kp * 4 * (fp8 ? 2 : 1);
+}
+
+// A slots and B stages that fit the shared memory: the most A slots (up to 4,
+// so that the next tile pair's A tiles load while a pair is scored) that leave
+// at least three B stages; failing that two A slots and at least two stages;
+// failing that one slot. Returns the number of B stages (< 2: does not fit).
+int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs) {
+  const size_t budget = 227 * 1024 - 1024, b = (size_t)nkb * bn * ROWB;
+  auto stages_for = [&](int na) -> int {
+    const size_t fixed = tc_smem_bytes(nkb, bn, 0, kp, fp8, na);
+    return fixed + 2 * b <= budget ? (int)std::min<size_t>(MAX_STAGES, (budget - fixed) / b) : 0;
+  };
+  for (int na = MAX_ABUF; na >= 3; --na)
+    if (stages_for(na) >= 3) {
+      *abufs = na;
+      return stages_for(na);
+    }
+  for (int na = 2; na >= 1; --na)
+    if (stages_for(na) >= 2) {
+      *abufs = na;
+      return stages_for(na);
+    }
+  *abufs = 1;
+  return 0;
 }
 
 // Raises the dynamic shared-memory limit of both instantiations to the

@@ -237,6 +237,7 @@ cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs);
+int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs);
 
 int num_sms();
 void set_last_error(const char* msg);  // message returned by kmeans_last_error()
