@@ -11,6 +11,7 @@
 #include "km_internal.cuh"
 #include "km_quant.cuh"
 #include "km_recheck.cuh"
+#include "km_gather.cuh"
 
 namespace km {
 
@@ -43,11 +44,12 @@ __global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
     if (FP8)
       for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
     const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sxx = 0.f, sqq = 0.f, sdd = 0.f;
     uint8_t* row = W.Xq + I.xq_off + i * (int64_t)Kp * ESZ;
     for (int t = lane; t < Kp; t += 32) {
       const float v = t < d ? x[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
       sxx = fmaf(v, v, sxx);
       sqq = fmaf(vq, vq, sqq);
       sdd = fmaf(vq - v, vq - v, sdd);
@@ -94,10 +96,11 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sqq = 0.f, sdd = 0.f;
     for (int t = lane; t < Kp; t += 32) {
       const float v = t < d ? c[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
       sqq = fmaf(vq, vq, sqq);
       sdd = fmaf(vq - v, vq - v, sdd);
     }
@@ -260,81 +263,130 @@ __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
 
 // Segmented sums over the flattened sorted positions: each warp walks one
 // contiguous range; the rows are gathered into shared memory with cp.async one
-// batch ahead (as in km_reduce.cu). A run may cross instance boundaries, which
-// flush like cluster boundaries. With QM the codes and row statistics of each
-// row are rewritten at its sorted position.
-constexpr int kSegRB = 8;                                               // rows per batch
-constexpr size_t kSegSmem = (size_t)8 * 2 * kSegRB * 32 * kMaxV * 4;  // 8 warps x 2 stages
+// batch ahead (as in km_reduce.cu). A batch never crosses an instance
+// boundary and holds as many rows of its instance's width as fit a stage, up
+// to 32. A run may cross instance boundaries, which flush like cluster
+// boundaries. With QM the codes and row statistics of each row are rewritten at
+// its sorted position.
+constexpr int kSegStage = 1024;                                 // floats per stage (8 rows of 128)
+constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;      // 8 warps x 2 stages
 
-__device__ __forceinline__ void b_cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void b_cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
+// One batch of the segmented sum: rows [bs, bs + bn) of instance q (halted
+// instances: q = -1), row stride rs floats in the stage; lane r < bn holds row
+// r's point i, label j and (with QM) row statistics.
+struct SegBatch {
+  int64_t bs;
+  int bn, rs, q, d;
+  const float* X;
+  int i, j;
+  float4 xs;
+};
+
+// The rows of one batch, V = ceil(d / 32) registers per lane (only the first V
+// of the kMaxV accumulators are touched). cur_j: the cluster being summed;
+// `flush` adds the partial sums of cur_j to the FP64 sums.
+template <int QM, int V, typename Flush>
+__device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int lane, int d, const float* C,
+                                         uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&s)[kMaxV],
+                                         float (&c)[kMaxV], float (&cj)[kMaxV], float& objS, float& objC,
+                                         int& cur_j, Flush&& flush) {
+  for (int r = 0; r < B.bn; ++r) {
+    const int j = __shfl_sync(0xffffffffu, B.j, r);
+    const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
+    if (j != cur_j) {
+      flush();
+      cur_j = j;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int t = v * 32 + lane;
+        cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+      }
+    }
+    float xr[V], qd = 0.f;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = v * 32 + lane;
+      xr[v] = t < d ? st[r * B.rs + t] : 0.f;
+      kahan_add(s[v], c[v], xr[v]);
+      const float df = __fsub_rn(xr[v], cj[v]);
+      qd = fmaf(df, df, qd);
+    }
+    kahan_add(objS, objC, qd);
+    if constexpr (QM != 0) {
+      const int64_t g = B.bs + r;  // flattened sorted position
+      const int64_t pr = g - row0;
+      if (lane == r) xs_sorted[g] = B.xs;
+      if constexpr (QM == 1) {
+        __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(xq) + pr * kp;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+        }
+      } else {
+        const float inv = pow2_inv(sxr);  // 1 / row scale, exact
+        uint8_t* row = xq + pr * kp;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+        }
+      }
+    }
+  }
 }
 
 template <int QM>
 __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
-  constexpr int RB = kSegRB, RS = 32 * kMaxV;
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float* stage0 = bseg_smem + (size_t)wib * 2 * RB * RS;
-  float* stage1 = stage0 + RB * RS;
+  float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
+  float* stage1 = stage0 + kSegStage;
   const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
   const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
-  const int64_t nbat = (P1 - P0 + RB - 1) / RB;
 
-  // lane r < RB: instance (-1: finished or past the range), local point, label,
-  // row address and dimension of position P0 + b RB + r
-  auto meta = [&](int64_t b, int& ib, int& i, int& j, const float*& x, int& d) {
-    const int64_t p = P0 + b * RB + lane;
-    ib = -1;
-    i = 0;
-    j = -1;
-    x = nullptr;
-    d = 0;
-    if (lane < RB && p < P1) {
-      const int q = find_block(W.row_off, W.nb, p);
-      if (!halted(W.ctls + q)) {
-        ib = q;
-        i = W.perm[p];
-        j = W.lab_sorted[p];
-        d = W.inst[q].d;
-        x = W.inst[q].X + (int64_t)i * d;
-      }
+  // batch cursor: batches are cut in increasing order, the instance found by walking forward
+  int64_t cursor = P0;
+  int qw = P0 < P1 ? find_block(W.row_off, W.nb, P0) : 0;
+  auto cut = [&](SegBatch& B) {
+    B.bn = 0;
+    B.q = -1;
+    B.i = 0;
+    B.j = -1;
+    if (cursor >= P1) return;
+    while (W.row_off[qw + 1] <= cursor) ++qw;
+    const BInst& I = W.inst[qw];
+    B.d = I.d;
+    B.X = I.X;
+    B.rs = 32 * ((B.d + 31) / 32);
+    B.bs = cursor;
+    B.bn = (int)min(min((int64_t)min(32, kSegStage / B.rs), W.row_off[qw + 1] - cursor), P1 - cursor);
+    cursor += B.bn;
+    B.q = halted(W.ctls + qw) ? -1 : qw;
+    if (B.q >= 0 && lane < B.bn) {
+      B.i = W.perm[B.bs + lane];
+      B.j = W.lab_sorted[B.bs + lane];
     }
   };
-  auto gather = [&](int64_t b, float* st, int ib_lane, const float* x_lane, int d_lane) {
-    const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
-    for (int r = 0; r < rows; ++r) {
-      const int q = __shfl_sync(0xffffffffu, ib_lane, r);
-      const float* x = (const float*)__shfl_sync(0xffffffffu, (unsigned long long)x_lane, r);
-      const int d = __shfl_sync(0xffffffffu, d_lane, r);
-      if (q < 0) continue;
-      if ((d & 3) == 0) {
-        for (int o = lane; o < (d >> 2); o += 32) b_cp_async16(st + r * RS + 4 * o, x + 4 * o);
-      } else {
-        for (int o = lane; o < d; o += 32) b_cp_async4(st + r * RS + o, x + o);
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+  auto gather = [&](const SegBatch& B, float* st) {
+    if (B.q >= 0) gather_rows(st, B.rs, B.X, B.d, B.bn, (int64_t)B.i * B.d, lane);
+    else cp_async_commit();
   };
 
   float s[kMaxV], c[kMaxV], cj[kMaxV];
 #pragma unroll
   for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
   float objS = 0.f, objC = 0.f;
-  int cur_b = -1, cur_j = -1, cur_d = 0;
-  const BInst* I = nullptr;
+  int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0;
+  int64_t cur_row0 = 0, cur_sum0 = 0;
+  const float* cur_C = nullptr;
+  uint8_t* cur_xq = nullptr;
   auto flush = [&]() {
     if (cur_j < 0) return;
 #pragma unroll
     for (int v = 0; v < kMaxV; ++v) {
       const int t = v * 32 + lane;
-      if (t < I->d) atomicAdd(W.sums64 + I->sum_off + (int64_t)cur_j * I->d + t, (double)s[v] - (double)c[v]);
+      if (t < cur_d) atomicAdd(W.sums64 + cur_sum0 + (int64_t)cur_j * cur_d + t, (double)s[v] - (double)c[v]);
       s[v] = 0.f;
       c[v] = 0.f;
     }
@@ -348,87 +400,53 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
     objS = objC = 0.f;
   };
 
-  int b_c = -1, i_c = 0, j_c = -1, b_n = -1, i_n = 0, j_n = -1, d_c = 0, d_n = 0;
-  const float *x_c = nullptr, *x_n = nullptr;
-  float4 xs_c = make_float4(1.f, 0.f, 0.f, 0.f), xs_n = xs_c;
-  if (nbat > 0) {
-    meta(0, b_c, i_c, j_c, x_c, d_c);
-    gather(0, stage0, b_c, x_c, d_c);
-    if (QM != 0 && b_c >= 0) xs_c = __ldg(&W.xs[W.inst[b_c].row_off + i_c]);
-    if (nbat > 1) meta(1, b_n, i_n, j_n, x_n, d_n);
+  SegBatch Bc, Bn, Bnn;
+  cut(Bc);
+  if (Bc.bn > 0) {
+    gather(Bc, stage0);
+    if (QM != 0 && Bc.q >= 0 && lane < Bc.bn) Bc.xs = __ldg(&W.xs[W.inst[Bc.q].row_off + Bc.i]);
   }
-  for (int64_t bt = 0; bt < nbat; ++bt) {
+  cut(Bn);
+  for (int64_t bt = 0; Bc.bn > 0; ++bt) {
     float* st = (bt & 1) ? stage1 : stage0;
-    if (bt + 1 < nbat) {
-      gather(bt + 1, (bt & 1) ? stage0 : stage1, b_n, x_n, d_n);
-      if (QM != 0 && b_n >= 0) xs_n = __ldg(&W.xs[W.inst[b_n].row_off + i_n]);
+    if (Bn.bn > 0) {
+      gather(Bn, (bt & 1) ? stage0 : stage1);
+      if (QM != 0 && Bn.q >= 0 && lane < Bn.bn) Bn.xs = __ldg(&W.xs[W.inst[Bn.q].row_off + Bn.i]);
     }
-    int b_nn = -1, i_nn = 0, j_nn = -1, d_nn = 0;
-    const float* x_nn = nullptr;
-    if (bt + 2 < nbat) meta(bt + 2, b_nn, i_nn, j_nn, x_nn, d_nn);
-    if (bt + 1 < nbat) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    cut(Bnn);
+    if (Bn.bn > 0) cp_async_wait<1>();
+    else cp_async_wait<0>();
     __syncwarp();
-    const int rows = (int)min((int64_t)RB, P1 - (P0 + bt * RB));
-    for (int r = 0; r < rows; ++r) {
-      const int b = __shfl_sync(0xffffffffu, b_c, r);
-      const int j = __shfl_sync(0xffffffffu, j_c, r);
-      const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, xs_c.x, r) : 1.f;
-      if (b < 0) continue;  // finished instance
-      if (b != cur_b || j != cur_j) {
+    const int b = Bc.q;
+    if (b >= 0) {
+      if (b != cur_b) {
         flush();
-        if (b != cur_b) {
-          flush_obj();
-          cur_b = b;
-          I = W.inst + b;
-          cur_d = I->d;
-        }
-        cur_j = j;
-#pragma unroll
-        for (int v = 0; v < kMaxV; ++v) {
-          const int t = v * 32 + lane;
-          cj[v] = t < cur_d ? I->C[(int64_t)j * cur_d + t] : 0.f;
-        }
+        flush_obj();
+        cur_b = b;
+        cur_j = -1;
+        const BInst* I = W.inst + b;
+        // the instance's fields in registers (the code stores below may alias them)
+        cur_d = I->d;
+        cur_kp = I->Kp;
+        cur_row0 = I->row_off;
+        cur_sum0 = I->sum_off;
+        cur_C = I->C;
+        cur_xq = W.Xq + I->xq_off;
       }
       const int d = cur_d;
-      float xr[kMaxV], qd = 0.f;
-#pragma unroll
-      for (int v = 0; v < kMaxV; ++v) {
-        const int t = v * 32 + lane;
-        xr[v] = t < d ? st[r * RS + t] : 0.f;
-        kahan_add(s[v], c[v], xr[v]);
-        const float df = __fsub_rn(xr[v], cj[v]);
-        qd = fmaf(df, df, qd);
-      }
-      kahan_add(objS, objC, qd);
-      if constexpr (QM != 0) {
-        const int64_t g = P0 + bt * RB + r;  // flattened sorted position
-        const int64_t pr = g - I->row_off;
-        if (lane == r) W.xs_sorted[g] = xs_c;
-#pragma unroll
-        for (int v = 0; v < kMaxV; ++v) {
-          const int t = v * 32 + lane;
-          if (t < d) {
-            if constexpr (QM == 1) {
-              reinterpret_cast<__nv_bfloat16*>(W.Xq + I->xq_off)[pr * I->Kp + t] = __float2bfloat16_rn(xr[v]);
-            } else {
-              __nv_fp8_e4m3 code(xr[v] / sxr);
-              (W.Xq + I->xq_off)[pr * I->Kp + t] = code.__x;
-            }
-          }
-        }
-      }
+      if (d <= 32)
+        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
+                        flush);
+      else if (d <= 64)
+        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
+                        flush);
+      else
+        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC,
+                            cur_j, flush);
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
-    b_c = b_n;
-    i_c = i_n;
-    j_c = j_n;
-    xs_c = xs_n;
-    b_n = b_nn;
-    i_n = i_nn;
-    j_n = j_nn;
-    x_n = x_nn;
-    d_n = d_nn;
+    Bc = Bn;
+    Bn = Bnn;
   }
   flush();
   flush_obj();

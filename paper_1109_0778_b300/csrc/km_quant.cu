@@ -32,11 +32,12 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
     if (FP8)
       for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
     const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sxx = 0.f, sqq = 0.f, sdd = 0.f;
     uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
     for (int t = lane; t < Kp; t += 32) {
       const float v = t < d ? x[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
       const float r = vq - v;
       sxx = fmaf(v, v, sxx);
       sqq = fmaf(vq, vq, sqq);
@@ -66,13 +67,14 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
     float amax = 0.f;
     for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
     const float sc8 = pow2_scale(warp_max(amax));
+    const float inv8 = pow2_inv(sc8);
     float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f;
     uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
     for (int t = lane; t < Kp16; t += 32) {
       const float v = t < d ? x[t] : 0.f;
-      const float q16 = quantise<0>(v, 1.f, row + t * 2);
+      const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
       uint8_t dummy;
-      const float q8 = quantise<1>(v, sc8, &dummy);
+      const float q8 = quantise<1>(v, sc8, inv8, &dummy);
       sxx = fmaf(v, v, sxx);
       sqq16 = fmaf(q16, q16, sqq16);
       sdd16 = fmaf(q16 - v, q16 - v, sdd16);
@@ -122,10 +124,11 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
 #pragma unroll
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sqq = 0.f, sdd = 0.f;
     for (int t = lane; t < Kp; t += 32) {
       const float v = t < d ? c[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, row + t * ESZ);
+      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
       const float r = vq - v;
       sqq = fmaf(vq, vq, sqq);
       sdd = fmaf(r, r, sdd);

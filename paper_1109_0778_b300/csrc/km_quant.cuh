@@ -14,14 +14,18 @@ static __device__ __forceinline__ float pow2_scale(float amax) {
   if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
   int e;
   const float m = frexpf(amax / 448.f, &e);  // amax / 448 = m 2^e, m in [0.5, 1)
-  return ldexpf(1.f, m == 0.5f ? e - 1 : e);
+  e = m == 0.5f ? e - 1 : e;
+  return ldexpf(1.f, e < -126 ? -126 : e);  // a normal power of two: its reciprocal is exact
 }
+
+// 1 / sc for a scale from pow2_scale: exact, so v * pow2_inv(sc) == v / sc.
+static __device__ __forceinline__ float pow2_inv(float sc) { return __frcp_rn(sc); }
 
 // One quantised element: stores the code, returns the dequantised value.
 template <int FP8>
-static __device__ __forceinline__ float quantise(float v, float sc, uint8_t* dst) {
+static __device__ __forceinline__ float quantise(float v, float sc, float inv, uint8_t* dst) {
   if constexpr (FP8) {
-    __nv_fp8_e4m3 q(v / sc);  // RN, satfinite
+    __nv_fp8_e4m3 q(v * inv);  // RN, satfinite; inv = 1 / sc exactly
     *dst = q.__x;
     return (float)q * sc;
   } else {

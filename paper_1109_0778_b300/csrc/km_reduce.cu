@@ -25,7 +25,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "km_gather.cuh"
 #include "km_internal.cuh"
+#include "km_quant.cuh"
 
 namespace km {
 
@@ -187,21 +189,6 @@ __host__ __device__ constexpr size_t seg_smem_bytes() {
   return (size_t)8 * 2 * seg_rows<V>() * 32 * V * sizeof(float);  // 8 warps x 2 stages x rows x 32V floats
 }
 
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // QM = 1 / 2: the pass also writes the BF16 / E4M3 codes of each row it reads
 // at its sorted position p (row stride Kp elements), using the row scale in xs,
 // and the row statistics xs at p; the codes equal those the quantisation stage
@@ -222,9 +209,6 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
   const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
   const int64_t P0 = n * gw / nw, P1 = n * (gw + 1) / nw;  // this warp's sorted positions
   const int64_t nb = (P1 - P0 + RB - 1) / RB;
-  const bool vec = (d & 3) == 0;  // rows start on 16-byte boundaries: 16-byte copies
-  const int cpr = vec ? d >> 2 : d;  // copies per row
-  const int ncp = RB * cpr;
 
   // indices of batch b: lane r < RB takes position P0 + b RB + r
   auto meta = [&](int64_t b, int& i, int& j) {
@@ -239,16 +223,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
   // gathers the rows of batch b into a stage (one commit group)
   auto gather = [&](int64_t b, float* st, int i_lane) {
     const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
-    for (int c0 = 0; c0 < ncp; c0 += 32) {
-      const int c = c0 + lane;
-      const int r = min(c / cpr, RB - 1), o = c - r * cpr;
-      const int ir = __shfl_sync(0xffffffffu, i_lane, r);
-      if (c < ncp && r < rows) {
-        if (vec) cp_async16(st + r * RS + 4 * o, X + (int64_t)ir * d + 4 * o);
-        else cp_async4(st + r * RS + o, X + (int64_t)ir * d + o);
-      }
-    }
-    cp_async_commit();
+    gather_rows(st, RS, X, d, rows, (int64_t)i_lane * d, lane);
   };
 
   float s[V], c[V], cj[V];
@@ -299,18 +274,21 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       kahan_add(objS, objC, q);
       if constexpr (QM != 0) {
         const int64_t prow = P0 + b * RB + r;
-        const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, xs_c.x, r) : 1.f;
         if (lane == r) xs_sorted[prow] = xs_c;
+        if constexpr (QM == 1) {
+          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * Kp;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
-          if (t < d) {
-            if constexpr (QM == 1) {
-              reinterpret_cast<__nv_bfloat16*>(Xq)[prow * Kp + t] = __float2bfloat16_rn(xr[v]);
-            } else {
-              __nv_fp8_e4m3 code(xr[v] / sxr);
-              Xq[prow * Kp + t] = code.__x;
-            }
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+          }
+        } else {
+          const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
+          uint8_t* row = Xq + prow * Kp;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
           }
         }
       }
