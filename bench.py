@@ -365,6 +365,8 @@ def precision_variants(torch, dev, steps=2, warmup=1):
     from paper_1109_0778_b300 import kmeans as km
 
     w = WORKLOADS["prec_n4M_d128_k1024"]
+    peaks, _ = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     X, _ = synth.workload_data(w, rows=w.n)
     Xd = torch.from_numpy(X).to(dev)
     C0 = Xd[: w.k].clone()
@@ -382,8 +384,19 @@ def precision_variants(torch, dev, steps=2, warmup=1):
             o = km.run(Xd, C, w.iters, assign=a, sums=s, counts=c, precision=prec, profile=True)
             ms += o.stats["ms"]
         ips = steps * w.iters / (ms / 1e3)
+        assign_ms = o.stats["stage_ms"]["assign"] / w.iters
+        achieved = w.flops_per_iter / (assign_ms / 1e3) / 1e12
+        if prec == "fp32":
+            peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
+            bound = "alu"
+        else:
+            peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
+            bound = "tensor"
         out[prec] = {"iter_s": ips, "distance_tflops": ips * w.flops_per_iter / 1e12,
-                     "assign_ms_per_iter": o.stats["stage_ms"]["assign"] / w.iters,
+                     "assign_ms_per_iter": assign_ms,
+                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": achieved / peak, "traffic": stored_traffic("assign", prec, w.name)},
+                     "stage_ms_per_iter": {k: v / w.iters for k, v in o.stats["stage_ms"].items()},
                      "flagged_last_iter": o.stats["n_flagged"], "objective": o.stats["objective"]}
     for prec in ("bf16", "fp8"):
         out[prec]["speedup_vs_fp32"] = out[prec]["iter_s"] / out["fp32"]["iter_s"]

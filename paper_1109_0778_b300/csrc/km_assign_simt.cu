@@ -19,7 +19,9 @@
 // with H = max_j h_j and Cmax = max_j ||c_j|| (rounded up). If the computed
 // top-2 scores satisfy s^_2 - s^_1 > 2 E_i, every other centroid is strictly
 // farther than j1 in exact arithmetic, so j1 is the exact argmin. Otherwise
-// the point is flagged and re-checked with compensated FP32 distances.
+// the point is flagged and re-checked with compensated FP32 distances. The
+// FMA chain is the same whether it runs as scalar or paired (FFMA2) FMAs: each
+// accumulator takes one rounding per term, so the bound does not change.
 #include "km_internal.cuh"
 
 namespace km {
@@ -108,11 +110,11 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
     for (int r = 0; r < 8; ++r) top[r] = Top2{INFINITY, INFINITY, 0};
 
     for (int j0 = 0; j0 < k; j0 += BN) {
-      float acc[8][8];
+      float2 acc2[8][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc2[r][c] = make_float2(0.f, 0.f);
 
       float va[BM * BK / THREADS], vb[BM * BK / THREADS];
       load_slice(X, n, d, m0, 0, va);
@@ -135,11 +137,21 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
           *reinterpret_cast<float4*>(&b[0]) = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
           *reinterpret_cast<float4*>(&b[4]) = *reinterpret_cast<const float4*>(&Bs[kk][64 + tx * 4]);
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
+          for (int r = 0; r < 8; ++r) {
+            const float2 ar = make_float2(a[r], a[r]);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) acc2[r][c] = __ffma2_rn(ar, make_float2(b[2 * c], b[2 * c + 1]), acc2[r][c]);
+          }
         }
       }
+      float acc[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][2 * c] = acc2[r][c].x;
+          acc[r][2 * c + 1] = acc2[r][c].y;
+        }
       // epilogue of this chunk: scores and running top-2 per row
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
@@ -292,11 +304,11 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
       }
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
-      float acc[8][8];
+      float2 acc2[8][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc2[r][c] = make_float2(0.f, 0.f);
       for (int kk = 0; kk < dp; kk += 4) {
         float a[8][4];
 #pragma unroll
@@ -304,16 +316,28 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
           *reinterpret_cast<float4*>(a[r]) = *reinterpret_cast<const float4*>(Xs + row_of(ty, r) * xs_stride + kk);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          float b[8];
+          float2 b2[4];
           const float* cr = Cs + (size_t)(kk + q) * nsp + j0;
-          *reinterpret_cast<float4*>(&b[0]) = *reinterpret_cast<const float4*>(cr + tx * 4);
-          *reinterpret_cast<float4*>(&b[4]) = *reinterpret_cast<const float4*>(cr + 64 + tx * 4);
+          const float4 b0 = *reinterpret_cast<const float4*>(cr + tx * 4);
+          const float4 b1 = *reinterpret_cast<const float4*>(cr + 64 + tx * 4);
+          b2[0] = make_float2(b0.x, b0.y); b2[1] = make_float2(b0.z, b0.w);
+          b2[2] = make_float2(b1.x, b1.y); b2[3] = make_float2(b1.z, b1.w);
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
+          for (int r = 0; r < 8; ++r) {
+            const float2 ar = make_float2(a[r][q], a[r][q]);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r][q], b[c], acc[r][c]);
+            for (int c = 0; c < 4; ++c) acc2[r][c] = __ffma2_rn(ar, b2[c], acc2[r][c]);
+          }
         }
       }
+      float acc[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][2 * c] = acc2[r][c].x;
+          acc[r][2 * c + 1] = acc2[r][c].y;
+        }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int jl = j0 + col_of(tx, c);
