@@ -170,8 +170,14 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
-      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, xss, labs, total;
+      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, xss, labs, fq_rows, fq_old, X_sub, xn_sub, flags2,
+      total;
+  int64_t fq_cap;
 };
+
+// Rows the re-check queue of the quantised paths holds: an eighth of the points
+// (at least 4096, at most n); further unresolved points are settled one by one.
+int64_t requeue_cap(int64_t n) { return std::min<int64_t>(n, std::max<int64_t>(4096, n / 8)); }
 
 Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   Layout L;
@@ -211,9 +217,18 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
     L.hq = take(4 * (size_t)t.kp);
     L.scq = take(4 * (size_t)t.kp);
     L.xss = take(16 * (size_t)n);
-    L.state = 0;
+    L.fq_cap = requeue_cap(n);
+    L.fq_rows = take(4 * (size_t)L.fq_cap);
+    L.fq_old = take(4 * (size_t)L.fq_cap);
+    L.X_sub = take(4 * (size_t)L.fq_cap * d);
+    L.xn_sub = take(4 * (size_t)L.fq_cap);
+    L.flags2 = take(sizeof(FlagRec) * (size_t)L.fq_cap);
+    const int width = simt_slab_width(d);  // the queued rows' FP32 pass may carry state across slabs
+    L.state = (width > 0 && width < k) ? take(16 * (size_t)L.fq_cap) : 0;
   } else {
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
+    L.fq_rows = L.fq_old = L.X_sub = L.xn_sub = L.flags2 = 0;
+    L.fq_cap = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;
   }
@@ -271,6 +286,12 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.xs16 = L.xs16 ? (float4*)(b + L.xs16) : nullptr;
   w.xs_sorted = L.xss ? (float4*)(b + L.xss) : nullptr;
   w.lab_sorted = L.labs ? (int32_t*)(b + L.labs) : nullptr;
+  w.fq_cap = L.fq_cap;
+  w.fq_rows = L.fq_rows ? (int32_t*)(b + L.fq_rows) : nullptr;
+  w.fq_old = L.fq_old ? (int32_t*)(b + L.fq_old) : nullptr;
+  w.X_sub = L.X_sub ? (float*)(b + L.X_sub) : nullptr;
+  w.xn_sub = L.xn_sub ? (float*)(b + L.xn_sub) : nullptr;
+  w.flags2 = L.flags2 ? (FlagRec*)(b + L.flags2) : nullptr;
   return w;
 }
 

@@ -91,8 +91,10 @@ __device__ __forceinline__ void store_slice(float (*S)[BM + PAD], const float (&
 __global__ void __launch_bounds__(THREADS, 1)
 assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C, int k,
                    const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
-                   int32_t* __restrict__ assign, FlagRec* __restrict__ flags, int first, float gam) {
+                   int32_t* __restrict__ assign, FlagRec* __restrict__ flags, int first, float gam,
+                   const SubRows sr) {
   if (halted(ctl)) return;
+  if (sr.n_dev) n = min(n, (int64_t)*sr.n_dev);  // gathered rows of the re-check stage (n = capacity)
   extern __shared__ __align__(16) float smem[];
   float (*As)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem);
   float (*Bs)[BM + PAD] = reinterpret_cast<float (*)[BM + PAD]>(smem + BK * (BM + PAD));
@@ -184,22 +186,23 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
       for (int r = 0; r < 8; ++r) {
         const int64_t i = m0 + row_of(ty, r);
         if (i < n) {
-          int old = first ? -1 : assign[i];
+          const int64_t pt = sr.rows ? (int64_t)sr.rows[i] : i;  // the point of row i
+          int old = sr.rows ? sr.old[i] : (first ? -1 : assign[pt]);
           if (old < 0 || old >= k) old = -1;
           const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
           const float margin = 2.f * E * (1.f + 0x1p-10f);
           const int j1 = top[r].i1;
           if (__fsub_rn(top[r].b2, top[r].b1) <= margin) {
-            unsigned long long slot = atomicAdd(&ctl->n_flagged, 1ull);
+            unsigned long long slot = atomicAdd(sr.nflag ? sr.nflag : &ctl->n_flagged, 1ull);
             FlagRec rec;
-            rec.i = (int32_t)i; rec.old = old; rec.nc = 0; rec.pad = 0;
+            rec.i = (int32_t)pt; rec.old = old; rec.nc = 0; rec.pad = 0;
             rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
-            flags[slot] = rec;
-            atomicAdd(&ctl->n_full, 1ull);
+            (sr.flags ? sr.flags : flags)[slot] = rec;
+            if (!sr.rows) atomicAdd(&ctl->n_full, 1ull);
           } else {
             changed += (old != j1);
           }
-          assign[i] = j1;
+          assign[pt] = j1;
         }
       }
       if (changed) atomicAdd(&s_changed, changed);
@@ -254,8 +257,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
-                   int first, int first_slab, int last_slab, float gam) {
+                   int first, int first_slab, int last_slab, float gam, const SubRows sr) {
   if (halted(ctl)) return;
+  if (sr.n_dev) n = min(n, (int64_t)*sr.n_dev);  // gathered rows of the re-check stage (n = capacity)
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = dp + 4;             // floats per staged point row
@@ -369,22 +373,23 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
           state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
           continue;
         }
-        int old = first ? -1 : assign[i];
+        const int64_t pt = sr.rows ? (int64_t)sr.rows[i] : i;  // the point of row i
+        int old = sr.rows ? sr.old[i] : (first ? -1 : assign[pt]);
         if (old < 0 || old >= k) old = -1;
         const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
         const float margin = 2.f * E * (1.f + 0x1p-10f);
         const int j1 = top[r].i1;
         if (__fsub_rn(top[r].b2, top[r].b1) <= margin) {
-          const unsigned long long slot = atomicAdd(&ctl->n_flagged, 1ull);
+          const unsigned long long slot = atomicAdd(sr.nflag ? sr.nflag : &ctl->n_flagged, 1ull);
           FlagRec rec;
-          rec.i = (int32_t)i; rec.old = old; rec.nc = 0; rec.pad = 0;
+          rec.i = (int32_t)pt; rec.old = old; rec.nc = 0; rec.pad = 0;
           rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
-          flags[slot] = rec;
-          atomicAdd(&ctl->n_full, 1ull);
+          (sr.flags ? sr.flags : flags)[slot] = rec;
+          if (!sr.rows) atomicAdd(&ctl->n_full, 1ull);
         } else {
           changed += (old != j1);
         }
-        assign[i] = j1;
+        assign[pt] = j1;
       }
       if (changed) atomicAdd(&s_changed, changed);
     }
@@ -430,7 +435,10 @@ int simt_slab_width(int d) {
   return ns >= BN ? ns : 0;
 }
 
-cudaError_t launch_assign_slab(const Problem& p, const Work& w, int first, cudaStream_t s) {
+// p.X / p.n: the rows to assign (the gathered rows and their capacity for a
+// re-check pass); chalf, xnorm: h_j and the rows' norm bounds.
+cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* chalf, const float* xnorm, int first,
+                               const SubRows& sr, cudaStream_t s) {
   const double u = 1.0 / 16777216.0;
   const double m = p.d + 1;
   const float gam = (float)(m * u / (1.0 - m * u) * (1.0 + 1e-6));
@@ -445,21 +453,22 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, int first, cudaS
     const size_t smem = slab_smem_bytes(dp, nsp);
     const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
     if (v16)
-      assign_slab_kernel<true><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, w.chalf, w.xnorm,
+      assign_slab_kernel<true><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
                                                             w.ctl, p.assign, w.flags, w.state, first, first_slab,
-                                                            last_slab, gam);
+                                                            last_slab, gam, sr);
     else
-      assign_slab_kernel<false><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, w.chalf,
-                                                             w.xnorm, w.ctl, p.assign, w.flags, w.state, first,
-                                                             first_slab, last_slab, gam);
+      assign_slab_kernel<false><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
+                                                             w.ctl, p.assign, w.flags, w.state, first, first_slab,
+                                                             last_slab, gam, sr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s) {
-  if (simt_slab_width(p.d) > 0) return launch_assign_slab(p, w, first, s);
+cudaError_t launch_assign_any(const Problem& p, const Work& w, const float* chalf, const float* xnorm, int first,
+                              const SubRows& sr, cudaStream_t s) {
+  if (simt_slab_width(p.d) > 0) return launch_assign_slab(p, w, chalf, xnorm, first, sr, s);
   const size_t smem = 2 * BK * (BM + PAD) * sizeof(float);
   const double u = 1.0 / 16777216.0;
   const double m = p.d + 1;
@@ -467,9 +476,22 @@ cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaS
   int64_t tiles = (p.n + BM - 1) / BM;
   int64_t cap = (int64_t)num_sms();
   int blocks = (int)(tiles < cap ? tiles : cap);
-  assign_simt_kernel<<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, p.C, p.k, w.chalf, w.xnorm, w.ctl,
-                                                   p.assign, w.flags, first, gam);
+  assign_simt_kernel<<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, p.C, p.k, chalf, xnorm, w.ctl, p.assign, w.flags,
+                                                   first, gam, sr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s) {
+  const SubRows none{nullptr, nullptr, nullptr, nullptr, nullptr};
+  return launch_assign_any(p, w, w.chalf, w.xnorm, first, none, s);
+}
+
+cudaError_t launch_assign_simt_sub(const Problem& p, const Work& w, const float* h, cudaStream_t s) {
+  const SubRows sr{w.fq_rows, w.fq_old, &w.ctl->n_fullq, &w.ctl->n_flagged2, w.flags2};
+  Problem q = p;
+  q.X = w.X_sub;
+  q.n = w.fq_cap;
+  return launch_assign_any(q, w, h, w.xn_sub, 0, sr, s);
 }
 
 }  // namespace km

@@ -22,6 +22,8 @@ struct Ctl {
   unsigned long long n_changed;
   unsigned long long n_flagged;    // entries in the flag list
   unsigned long long n_full;       // flagged points that need all k candidates
+  unsigned long long n_fullq;      // of those, queued for the tiled FP32 pass (re-check stage)
+  unsigned long long n_flagged2;   // points the tiled FP32 pass leaves flagged
   double objective;                // J(a^t, C^t)
   unsigned long long shift2_bits;  // max_j ||dc_j||^2 as FP64 bits (>= 0)
   unsigned int cmax_bits;          // max_j ||c_j|| (FP32 bits, rounded up)
@@ -75,7 +77,25 @@ struct Work {
   float4* state;       // [n] per-row (best, index, second) between centroid slabs (FP32 path)
   float4* xs16;        // [n] BF16 statistics of a cold first step of an E4M3 run
   float4* xs_sorted;   // [n] xs in this step's cluster-sorted order (quantised paths)
-  int32_t* lab_sorted; // [n] label of each sorted position (quantised paths)
+  int32_t* lab_sorted; // [n] label of each sorted position (scatter stage)
+  // points the quantised assignment could not narrow to a short list: gathered
+  // and re-scored by the tiled FP32 kernel (quantised paths; null for FP32)
+  int64_t fq_cap;      // rows the queue holds
+  int32_t* fq_rows;    // [fq_cap] point index
+  int32_t* fq_old;     // [fq_cap] previous label
+  float* X_sub;        // [fq_cap][d] gathered rows
+  float* xn_sub;       // [fq_cap] ||x|| bounds of the gathered rows
+  FlagRec* flags2;     // [fq_cap] points the tiled FP32 pass leaves flagged
+};
+
+// Row map of an FP32 assignment pass over gathered rows: row r of X is point
+// rows[r] with previous label old[r]; *n_dev rows; flags go to flags / *nflag.
+struct SubRows {
+  const int32_t* rows;  // null: row r is point r (the regular pass)
+  const int32_t* old;
+  const unsigned long long* n_dev;
+  unsigned long long* nflag;
+  FlagRec* flags;
 };
 
 struct BInst;
@@ -219,6 +239,8 @@ struct Problem {
 cudaError_t launch_xnorm(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_prep(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s);
+// FP32 assignment of the queued rows of the re-check stage (quantised paths); h = h_j of C.
+cudaError_t launch_assign_simt_sub(const Problem& p, const Work& w, const float* h, cudaStream_t s);
 cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s);
 cudaError_t launch_count(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s);

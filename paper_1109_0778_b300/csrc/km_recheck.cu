@@ -13,18 +13,33 @@ namespace {
 template <int V>
 __global__ void __launch_bounds__(256)
 recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, const float* __restrict__ h, int k,
-               const FlagRec* __restrict__ flags, Ctl* ctl, int32_t* __restrict__ assign) {
+               const FlagRec* __restrict__ flags, const unsigned long long* nflag_ptr, Ctl* ctl,
+               int32_t* __restrict__ assign, int32_t* __restrict__ q_rows, int32_t* __restrict__ q_old,
+               int64_t q_cap) {
   if (halted(ctl)) return;
   __shared__ __align__(16) float xs_all[8][V * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* xsh = xs_all[wib];
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
-  const int64_t nflag = (int64_t)ctl->n_flagged;
+  const int64_t nflag = (int64_t)*nflag_ptr;
   const float H = __uint_as_float(ctl->hmax_bits), Cmax = __uint_as_float(ctl->cmax_bits);
   unsigned int changed = 0;
   for (int64_t f = warp; f < nflag; f += nwarps) {
     const FlagRec rec = flags[f];
+    if (rec.nc == 0 && q_rows) {
+      // all k candidates: queue the point for the tiled FP32 pass while the queue has room
+      unsigned long long slot = 0;
+      if (lane == 0) slot = atomicAdd(&ctl->n_fullq, 1ull);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot < (unsigned long long)q_cap) {
+        if (lane == 0) {
+          q_rows[slot] = rec.i;
+          q_old[slot] = rec.old;
+        }
+        continue;
+      }
+    }
     const float* x = X + (int64_t)rec.i * d;
     float xv[V];
 #pragma unroll
@@ -55,19 +70,68 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
   if (lane == 0 && changed) atomicAdd(&ctl->n_changed, (unsigned long long)changed);
 }
 
+// Copies the queued rows into X_sub and their norm bounds (xs.w) into xn_sub;
+// one warp per row.
+__global__ void __launch_bounds__(256)
+gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict__ xs, const Ctl* ctl,
+                    const int32_t* __restrict__ q_rows, int64_t q_cap, float* __restrict__ X_sub,
+                    float* __restrict__ xn_sub) {
+  if (halted(ctl)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  const int64_t nq = min((int64_t)ctl->n_fullq, q_cap);
+  for (int64_t r = warp; r < nq; r += nwarps) {
+    const int64_t i = q_rows[r];
+    const float* x = X + i * d;
+    float* y = X_sub + r * d;
+    for (int t = lane; t < d; t += 32) y[t] = x[t];
+    if (lane == 0) xn_sub[r] = xs[i].w;
+  }
+}
+
 }  // namespace
 
-cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s) {
-  (void)first;  // the stored old label is -1 in a call's first step
+template <int V>
+cudaError_t recheck_v(const Problem& p, const Work& w, const float* h, const FlagRec* flags,
+                      const unsigned long long* nflag, bool queue, cudaStream_t s) {
   const int blocks = num_sms() * 4;
-  const int V = (p.d + 31) / 32;
-  switch (V) {
-#define KM_CASE(v) case v: recheck_kernel<v><<<blocks, 256, 0, s>>>(p.X, p.d, p.C, h, p.k, w.flags, w.ctl, p.assign); break;
-    KM_CASE(1) KM_CASE(2) KM_CASE(3) KM_CASE(4) KM_CASE(5) KM_CASE(6) KM_CASE(7) KM_CASE(8)
-#undef KM_CASE
+  recheck_kernel<V><<<blocks, 256, 0, s>>>(p.X, p.d, p.C, h, p.k, flags, nflag, w.ctl, p.assign,
+                                           queue ? w.fq_rows : nullptr, queue ? w.fq_old : nullptr,
+                                           queue ? w.fq_cap : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t recheck_pass(const Problem& p, const Work& w, const float* h, const FlagRec* flags,
+                         const unsigned long long* nflag, bool queue, cudaStream_t s) {
+  switch ((p.d + 31) / 32) {
+    case 1: return recheck_v<1>(p, w, h, flags, nflag, queue, s);
+    case 2: return recheck_v<2>(p, w, h, flags, nflag, queue, s);
+    case 3: return recheck_v<3>(p, w, h, flags, nflag, queue, s);
+    case 4: return recheck_v<4>(p, w, h, flags, nflag, queue, s);
+    case 5: return recheck_v<5>(p, w, h, flags, nflag, queue, s);
+    case 6: return recheck_v<6>(p, w, h, flags, nflag, queue, s);
+    case 7: return recheck_v<7>(p, w, h, flags, nflag, queue, s);
+    case 8: return recheck_v<8>(p, w, h, flags, nflag, queue, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+// The re-check stage. Short candidate lists are settled directly. On the
+// quantised paths, points whose candidates could not be narrowed are queued,
+// gathered, and assigned again by the tiled FP32 kernel (the distances of many
+// points against all centroids, each centroid tile read once per 128 points);
+// the few it still flags get the compensated distances against all k. The FP32
+// path settles every flag directly (its flags come from that same kernel).
+cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s) {
+  (void)first;  // the stored old label is -1 in a call's first step
+  const bool queue = w.fq_rows != nullptr;
+  cudaError_t e = recheck_pass(p, w, h, w.flags, &w.ctl->n_flagged, queue, s);
+  if (e != cudaSuccess || !queue) return e;
+  gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xs, w.ctl, w.fq_rows, w.fq_cap, w.X_sub, w.xn_sub);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_assign_simt_sub(p, w, h, s)) != cudaSuccess) return e;
+  return recheck_pass(p, w, h, w.flags2, &w.ctl->n_flagged2, false, s);
 }
 
 }  // namespace km

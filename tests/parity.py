@@ -21,11 +21,17 @@ CENTROID_TOL = 1e-5
 OBJECTIVE_TOL = 1e-6
 
 
-def member_scale(X, a, k):
+def member_scale(X, a, k, chunk=1 << 18):
     """max_t of mean |x_it| over the members of each cluster (0 for empty clusters)."""
+    import torch
+
     d = X.shape[1]
-    acc = np.zeros((k, d))
-    np.add.at(acc, a, np.abs(X.astype(np.float64)))
+    acc = torch.zeros((k, d), dtype=torch.float64)
+    at = torch.from_numpy(np.ascontiguousarray(a, dtype=np.int64))
+    for r0 in range(0, X.shape[0], chunk):  # FP64 sums of |x| in row chunks (bounded host memory)
+        xs = torch.from_numpy(X[r0:r0 + chunk]).abs().double()
+        acc.index_add_(0, at[r0:r0 + chunk], xs)
+    acc = acc.numpy()
     cnt = np.bincount(a, minlength=k).astype(np.float64)
     scale = np.zeros(k)
     nz = cnt > 0

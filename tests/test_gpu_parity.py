@@ -287,6 +287,38 @@ def test_tc_large_workload_sample(km, ref):
     assert near <= 20
 
 
+def _full_size_tc(km, ref, w, precision, sample):
+    """kmeans_run of the workload's iterations at full size (the bench's launch configuration),
+    then one more step from the result: the assignment on a random row sample, the O(nd)
+    update and the objective in full."""
+    X, C0 = synth.workload_data(w)
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    out = km.run(Xd, Cd, w.iters, precision=precision)
+    assert out.stats["iters_done"] == w.iters
+    counts = out.counts.cpu().numpy()
+    assert counts.sum() == w.n and np.array_equal(counts, np.bincount(out.assign.cpu().numpy(), minlength=w.k))
+    C_in = Cd.cpu().numpy().astype(np.float64)
+    o = km.step(Xd, Cd, out.assign, out.sums, out.counts, precision=precision, warm_start=True)
+    a1 = o.assign.cpu().numpy()
+    rows = np.sort(np.random.default_rng(7).choice(w.n, sample, replace=False))
+    parity.check_assign(ref, X, C_in, a1, rows=rows)
+    parity.check_update(ref, X, C_in, a1, Cd.cpu().numpy(), o.sums.cpu().numpy(), o.counts.cpu().numpy())
+    parity.check_objective(ref, X, C_in, a1, o.stats["objective"])
+    assert o.stats["objective"] <= out.stats["objective"] * (1 + 1e-6)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_full_size_precision_workload(km, ref, precision):
+    _full_size_tc(km, ref, WORKLOADS["prec_n4M_d128_k1024"], precision, 8192)
+
+
+@pytest.mark.slow
+def test_full_size_large_workload(km, ref):
+    _full_size_tc(km, ref, WORKLOADS["large_n8M_d256_k8192"], "fp8", 8192)  # sample >= k (oracle precondition)
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_tc_run_matches_free_running_oracle(km, ref, precision):
     """Graph-captured runs (seeded from the second step on) against the free-running oracle."""
