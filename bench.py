@@ -284,14 +284,21 @@ def batched_problems(torch, dev, w, limit=0):
     if limit:
         inst = inst[:limit]
     probs, flops, xbytes = [], 0.0, 0
-    for iw in inst:
+    # every instance's C is a view of one flat buffer, so a step resets all of them with one copy
+    kd = [iw.k * iw.d for iw in inst]
+    c_flat = torch.empty(sum(kd), dtype=torch.float32, device=dev)
+    c0_flat = torch.empty_like(c_flat)
+    at = 0
+    for iw, m in zip(inst, kd):
         X = synth.mixture(iw.seed, iw.n, iw.d, iw.m, iw.R, iw.sigma)
         Xd = torch.from_numpy(X).to(dev)
-        C0 = torch.from_numpy(X[: iw.k].copy()).to(dev)
-        probs.append((Xd, C0))
+        c0_flat[at:at + m].copy_(torch.from_numpy(X[: iw.k].reshape(-1)))
+        probs.append((Xd, c_flat[at:at + m].view(iw.k, iw.d)))
+        at += m
         flops += 2.0 * iw.n * iw.k * iw.d
         xbytes += 4 * iw.n * iw.d
-    return inst, probs, flops, xbytes
+    c_flat.copy_(c0_flat)
+    return inst, probs, flops, xbytes, (c_flat, c0_flat)
 
 
 def run_batched(args, torch, dev, dist, rank, world, local):
@@ -299,18 +306,17 @@ def run_batched(args, torch, dev, dist, rank, world, local):
 
     w = WORKLOADS["batched_512"]
     prec = args.precision or w.precision[0]
-    inst, probs, flops_iter, xbytes = batched_problems(torch, dev, w, args.instances)
+    inst, probs, flops_iter, xbytes, (c_flat, c0_flat) = batched_problems(torch, dev, w, args.instances)
     work = []
-    for Xd, C0 in probs:
-        C = C0.clone()
+    for Xd, C in probs:
         a, s, c = km.alloc_outputs(Xd, C)
         work.append((Xd, C, a, s, c))
+    batch = km.Batch(work)  # checked and marshalled once; the tensors' contents change per step
     stream = torch.cuda.current_stream(dev)
 
     def one_step():
-        for (Xd, C0), (_, C, _, _, _) in zip(probs, work):
-            C.copy_(C0)
-        return km.run_batched(work, w.iters, precision=prec, stream=stream, profile=True)
+        c_flat.copy_(c0_flat)
+        return batch.run(w.iters, precision=prec, stream=stream, profile=True)
 
     for _ in range(max(args.warmup, 0)):
         one_step()
@@ -323,10 +329,10 @@ def run_batched(args, torch, dev, dist, rank, world, local):
         ev0.record(stream)
         for _ in range(args.steps):
             st = one_step()
-            call_ms += st[0]["ms"]
-            for kname, v in st[0]["stage_ms"].items():
-                stage_tot[kname] += v
-            flagged = (sum(x["n_flagged"] for x in st), sum(x["n_full"] for x in st))
+            call_ms += float(st["ms"][0])
+            for si, kname in enumerate(km.STAGES):
+                stage_tot[kname] += float(st["stage_ms"][0][si])
+            flagged = (int(st["n_flagged"].sum()), int(st["n_full"].sum()))
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(dist)

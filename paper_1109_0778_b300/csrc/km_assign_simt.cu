@@ -260,6 +260,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
                    int first, int first_slab, int last_slab, float gam, const SubRows sr) {
   if (halted(ctl)) return;
   if (sr.n_dev) n = min(n, (int64_t)*sr.n_dev);  // gathered rows of the re-check stage (n = capacity)
+  if ((int64_t)blockIdx.x * BM >= n) return;    // no tile for this CTA: skip the slab load
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = dp + 4;             // floats per staged point row

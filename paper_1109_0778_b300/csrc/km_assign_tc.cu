@@ -26,9 +26,10 @@
 // expiry the kernel records KM_ETIMEOUT, drains what it issued, frees TMEM and
 // returns.
 //
-// Scores. With codes q and power-of-two row scales (x~ = sx q_x, c~ = sc q_c;
-// BF16 uses sx = sc = 1), the epilogue computes
-//   s^_j = h_j - (sx sc_j) acc_j,  acc_j = sum_t q_x,t q_c,jt  (TMEM, FP32),
+// Scores. With codes q and power-of-two scales (x~ = sx q_x with a scale per
+// point row, c~ = sc q_c with one scale for all centroids of the step; BF16
+// uses sx = sc = 1), the epilogue computes
+//   s^_j = h_j - (sx sc) acc_j,  acc_j = sum_t q_x,t q_c,jt  (TMEM, FP32),
 // whose argmin over j is the distance argmin up to the quantisation error.
 //
 // Error bound (u = 2^-24; the tensor core accumulates in FP32 with truncation,
@@ -279,29 +280,21 @@ __device__ __forceinline__ void fold_block(Cand (&top)[kT], const float (&s)[32]
 }
 
 // Scores of one 32-column block from its TMEM accumulators,
-// s_j = h_j - (sx sc_j) acc_j (two columns per packed operation), their
-// minimum, and the fold of the block's candidates (rare once thr is tight).
-template <int FP8>
-__device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float* hb, const float* scb, float nsx,
-                                            Cand (&top)[kT], int j0, float& thr, float margin) {
+// s_j = h_j + w acc_j with the row's factor w = -(sx sc) (two columns per
+// packed operation), their minimum, and the fold of the block's candidates
+// (rare once thr is tight).
+__device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float* hb, float w, Cand (&top)[kT],
+                                            int j0, float& thr, float margin) {
   float s[32];
   const float4* h4 = reinterpret_cast<const float4*>(hb);
+  const float2 w2 = make_float2(w, w);
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
     const float4 hh = h4[t];
     const float2 a0 = make_float2(__uint_as_float(v[4 * t]), __uint_as_float(v[4 * t + 1]));
     const float2 a1 = make_float2(__uint_as_float(v[4 * t + 2]), __uint_as_float(v[4 * t + 3]));
-    float2 w0, w1;
-    if constexpr (FP8) {
-      const float4 sc4 = reinterpret_cast<const float4*>(scb)[t];
-      w0 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.x, sc4.y));
-      w1 = __fmul2_rn(make_float2(nsx, nsx), make_float2(sc4.z, sc4.w));
-    } else {
-      w0 = make_float2(-1.f, -1.f);
-      w1 = w0;
-    }
-    const float2 s0 = __ffma2_rn(w0, a0, make_float2(hh.x, hh.y));
-    const float2 s1 = __ffma2_rn(w1, a1, make_float2(hh.z, hh.w));
+    const float2 s0 = __ffma2_rn(w2, a0, make_float2(hh.x, hh.y));
+    const float2 s1 = __ffma2_rn(w2, a1, make_float2(hh.z, hh.w));
     s[4 * t] = s0.x;
     s[4 * t + 1] = s0.y;
     s[4 * t + 2] = s1.x;
@@ -349,7 +342,6 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   uint8_t* B0 = smem + nab * a_bytes;
   const int kpmax = P.nchunks * BN;
   float* Hs = reinterpret_cast<float*>(B0 + (size_t)stages * b_bytes);  // [kpmax]
-  float* SCs = Hs + kpmax;                                               // [kpmax] (FP8)
   const TileRange tr = tile_range<BATCH>(P);
 
   if (threadIdx.x == 0) {
@@ -379,10 +371,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     tmem_relinquish();
   }
   if (!BATCH && warp >= 2) {  // batched launches stage h per instance in the epilogue
-    for (int j = threadIdx.x - 64; j < kpmax; j += 32 * NEPI) {
-      Hs[j] = __ldg(P.h + j);
-      if (FP8) SCs[j] = __ldg(P.sc + j);
-    }
+    for (int j = threadIdx.x - 64; j < kpmax; j += 32 * NEPI) Hs[j] = __ldg(P.h + j);
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -522,6 +511,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     Item it;
     it.b = -1;
     float H = 0.f, Cmax = 0.f, QCmax = 0.f, DCmax = 0.f;  // per-step maxima of the instance
+    float csc = 1.f;                                      // the instance's centroid code scale (E4M3)
     RowMeta nxt;
     bool have_nxt = false;
     // Every epilogue warp walks every pair to the end, even after a timeout
@@ -533,10 +523,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (BATCH && !it.skip) {
           // this instance's h_j (and scales) into shared memory
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-          for (int j = threadIdx.x - 64; j < it.nchunks * BN; j += 32 * NEPI) {
-            Hs[j] = __ldg(it.h + j);
-            if (FP8) SCs[j] = __ldg(it.sc + j);
-          }
+          for (int j = threadIdx.x - 64; j < it.nchunks * BN; j += 32 * NEPI) Hs[j] = __ldg(it.h + j);
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
         }
         if (!it.skip) {
@@ -545,6 +532,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           Cmax = __uint_as_float(ctl->cmax_bits);
           QCmax = __uint_as_float(ctl->qcmax_bits);
           DCmax = __uint_as_float(ctl->dcmax_bits);
+          if (FP8) csc = __ldg(it.sc);  // the same for every centroid of the step
         }
       }
       if (it.skip) {
@@ -586,7 +574,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       Cand top[kT];
 #pragma unroll
       for (int t = 0; t < kT; ++t) top[t] = Cand{INFINITY, -1};
-      const float nsx = -xs.x;
+      const float wrow = FP8 ? -xs.x * csc : -1.f;  // exact: a product of powers of two
       const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
       // the tile's 32-column blocks in chunk order
       const int nall = it.nchunks * nblk;
@@ -611,7 +599,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
         const int j0 = c * BN + blk * 32;
-        score_block<FP8>(v, Hs + j0, SCs + j0, nsx, top, j0, thr, margin);
+        score_block(v, Hs + j0, wrow, top, j0, thr, margin);
         if (blk == nblk - 1) {
           ++gu;
           c = (c + 1 == it.nchunks) ? 0 : c + 1;
@@ -698,7 +686,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 }  // namespace
 
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs) {
-  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * nkb * bn * ROWB + (size_t)kp * 4 * (fp8 ? 2 : 1);
+  (void)fp8;
+  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * nkb * bn * ROWB + (size_t)kp * 4;
 }
 
 // A slots and B stages that fit the shared memory: the most A slots (up to 4,

@@ -28,40 +28,80 @@ __global__ void b_reset_kernel(Ctl* ctls, int nb, unsigned long long* flag_slots
   }
 }
 
+// Codes and row statistics of every point of the batch. Each warp walks one
+// contiguous range of the flattened rows (instances found by walking forward
+// from one search), four rows of one instance at a time with their loads in
+// flight together; lanes over the Kp <= 128 code columns.
 template <int FP8>
 __global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
   constexpr int ESZ = FP8 ? 1 : 2;
+  constexpr int U = 4;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g = warp; g < W.R; g += nwarps) {
-    const int b = find_block(W.row_off, W.nb, g);
-    const BInst& I = W.inst[b];
-    const int64_t i = g - I.row_off;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
+  int q = P0 < P1 ? find_block(W.row_off, W.nb, P0) : 0;
+  for (int64_t p = P0; p < P1;) {
+    while (W.row_off[q + 1] <= p) ++q;
+    const BInst& I = W.inst[q];
     const int d = I.d, Kp = I.Kp;
-    const float* x = I.X + i * d;
-    float amax = 0.f;
-    if (FP8)
-      for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
-    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
-    const float inv = FP8 ? pow2_inv(sc) : 1.f;
-    float sxx = 0.f, sqq = 0.f, sdd = 0.f;
-    uint8_t* row = W.Xq + I.xq_off + i * (int64_t)Kp * ESZ;
-    for (int t = lane; t < Kp; t += 32) {
-      const float v = t < d ? x[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
-      sxx = fmaf(v, v, sxx);
-      sqq = fmaf(vq, vq, sqq);
-      sdd = fmaf(vq - v, vq - v, sdd);
+    const int64_t i0 = p - I.row_off;
+    const int rows = (int)min(min((int64_t)U, W.row_off[q + 1] - p), P1 - p);
+    float xv[U][kMaxV];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float* x = I.X + (i0 + u) * d;
+#pragma unroll
+      for (int v = 0; v < kMaxV; ++v) {
+        const int t = v * 32 + lane;
+        xv[u][v] = (u < rows && t < d) ? x[t] : 0.f;
+      }
     }
-    sxx = warp_sum(sxx);
-    sqq = warp_sum(sqq);
-    sdd = warp_sum(sdd);
-    if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(sqq)) W.ctls[b].nonfinite = 1;
-      W.xs[g] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (u >= rows) break;
+      float amax = 0.f;
+      if (FP8) {
+#pragma unroll
+        for (int v = 0; v < kMaxV; ++v) amax = fmaxf(amax, fabsf(xv[u][v]));
+      }
+      const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+      const float inv = FP8 ? pow2_inv(sc) : 1.f;
+      float sxx = 0.f, sqq = 0.f, sdd = 0.f;
+      uint8_t* row = W.Xq + I.xq_off + (i0 + u) * (int64_t)Kp * ESZ;
+#pragma unroll
+      for (int v = 0; v < kMaxV; ++v) {
+        const int t = v * 32 + lane;
+        if (t < Kp) {
+          const float xt = xv[u][v];
+          const float vq = quantise<FP8>(xt, sc, inv, row + t * ESZ);
+          sxx = fmaf(xt, xt, sxx);
+          sqq = fmaf(vq, vq, sqq);
+          sdd = fmaf(vq - xt, vq - xt, sdd);
+        }
+      }
+      sxx = warp_sum(sxx);
+      sqq = warp_sum(sqq);
+      sdd = warp_sum(sdd);
+      if (lane == 0) {
+        if (!isfinite(sxx) || !isfinite(sqq)) W.ctls[q].nonfinite = 1;
+        W.xs[p + u] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+      }
     }
+    p += rows;
   }
+}
+
+// max_{j,t} |c_jt| of every instance (one block per instance) for its E4M3 centroid scale.
+__global__ void __launch_bounds__(256) b_camax_kernel(BWork W) {
+  const int b = blockIdx.x;
+  if (halted(W.ctls + b)) return;
+  const BInst& I = W.inst[b];
+  const int64_t kd = (int64_t)I.k * I.d;
+  float m = 0.f;
+  for (int64_t e = threadIdx.x; e < kd; e += blockDim.x) m = fmaxf(m, fabsf(I.C[e]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomic_max_nonneg(&W.ctls[b].camax_bits, m);
 }
 
 template <int FP8>
@@ -88,14 +128,10 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
     }
     const float* c = I.C + (int64_t)j * d;
     double s2 = 0.0;
-    float amax = 0.f;
-    for (int t = lane; t < d; t += 32) {
-      s2 = fma((double)c[t], (double)c[t], s2);
-      amax = fmaxf(amax, fabsf(c[t]));
-    }
+    for (int t = lane; t < d; t += 32) s2 = fma((double)c[t], (double)c[t], s2);
 #pragma unroll
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float sc = FP8 ? pow2_scale(__uint_as_float(ctl->camax_bits)) : 1.f;  // one scale per instance
     const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sqq = 0.f, sdd = 0.f;
     for (int t = lane; t < Kp; t += 32) {
@@ -124,6 +160,35 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
 
 // Flagged points of all instances (FlagRec.pad = instance): the re-check of
 // km_recheck.cu with lanes over dimensions (d <= 128).
+// Settles one flagged point of instance I with V = ceil(d / 32) registers per lane.
+template <int V>
+__device__ __forceinline__ int b_settle(const BWork& W, const FlagRec& rec, const BInst& I, int b, float* xsh,
+                                        int lane) {
+  const int d = I.d, k = I.k;
+  const float* x = I.X + (int64_t)rec.i * d;
+  float xv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int t = v * 32 + lane;
+    xv[v] = t < d ? x[t] : 0.f;
+  }
+  if (rec.nc > 0) {
+    float best = INFINITY;
+    int jb = rec.cand[0];
+    for (int q = 0; q < rec.nc; ++q) {
+      const int j = rec.cand[q];
+      const float D = warp_sqdist<V>(xv, I.C + (int64_t)j * d, d, lane);
+      if (D < best) {  // candidates arrive in increasing index order
+        best = D;
+        jb = j;
+      }
+    }
+    return jb;
+  }
+  return nearest_all<V>(xv, xsh, I.C, W.hq + I.kp_off, k, d, lane, __uint_as_float(W.ctls[b].hmax_bits),
+                        __uint_as_float(W.ctls[b].cmax_bits));
+}
+
 __global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
   __shared__ __align__(16) float xs_all[8][kMaxV * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -136,30 +201,9 @@ __global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
     const int b = rec.pad;
     if (halted(W.ctls + b)) continue;
     const BInst& I = W.inst[b];
-    const int d = I.d, k = I.k;
-    const float* x = I.X + (int64_t)rec.i * d;
-    float xv[kMaxV];
-#pragma unroll
-    for (int v = 0; v < kMaxV; ++v) {
-      const int t = v * 32 + lane;
-      xv[v] = t < d ? x[t] : 0.f;
-    }
-    int jb;
-    if (rec.nc > 0) {
-      float best = INFINITY;
-      jb = rec.cand[0];
-      for (int q = 0; q < rec.nc; ++q) {
-        const int j = rec.cand[q];
-        const float D = warp_sqdist<kMaxV>(xv, I.C + (int64_t)j * d, d, lane);
-        if (D < best) {  // candidates arrive in increasing index order
-          best = D;
-          jb = j;
-        }
-      }
-    } else {
-      jb = nearest_all<kMaxV>(xv, xsh, I.C, W.hq + I.kp_off, k, d, lane, __uint_as_float(W.ctls[b].hmax_bits),
-                              __uint_as_float(W.ctls[b].cmax_bits));
-    }
+    const int d = I.d;
+    const int jb = d <= 32 ? b_settle<1>(W, rec, I, b, xsh, lane)
+                           : (d <= 64 ? b_settle<2>(W, rec, I, b, xsh, lane) : b_settle<kMaxV>(W, rec, I, b, xsh, lane));
     if (lane == 0) {
       I.assign[rec.i] = jb;
       if (rec.old != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
@@ -528,13 +572,14 @@ cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s) {
 
 cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s) {
   const int grid = grid_for(W.KP, 8, 8);
+  if (fp8) b_camax_kernel<<<W.nb, 256, 0, s>>>(W);
   if (fp8) b_quant_c_kernel<1><<<grid, 256, 0, s>>>(W);
   else b_quant_c_kernel<0><<<grid, 256, 0, s>>>(W);
   return cudaGetLastError();
 }
 
 cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
-  b_recheck_kernel<<<num_sms() * 4, 256, 0, s>>>(W);
+  b_recheck_kernel<<<num_sms() * 8, 256, 0, s>>>(W);  // latency-bound: many warps in flight
   return cudaGetLastError();
 }
 

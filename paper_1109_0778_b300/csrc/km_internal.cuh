@@ -30,6 +30,7 @@ struct Ctl {
   unsigned int hmax_bits;          // max_j h_j = max_j ||c_j||^2 / 2
   unsigned int qcmax_bits;         // max_j ||c~_j|| of the quantised centroids (rounded up)
   unsigned int dcmax_bits;         // max_j ||c~_j - c_j|| (quantisation residual, rounded up)
+  unsigned int camax_bits;         // max_{j,t} |c_jt| (FP32 bits): sets the E4M3 centroid scale
   int n_empty;
   unsigned int blocks_done;        // last-block detection in the divide stage
   // ---- per run (cleared once) ----

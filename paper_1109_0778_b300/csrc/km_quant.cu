@@ -3,7 +3,9 @@
 // X is quantised once per call (it does not change between iterations, Sec.
 // 3.1 code motion) and C once per step. Codes: BF16 round-to-nearest with
 // scale 1, or E4M3 round-to-nearest, saturating, of v / s with a power-of-two
-// row scale s = 2^ceil(log2(amax / 448)), so that v / s and s * code are exact.
+// scale s = 2^ceil(log2(amax / 448)), so that v / s and s * code are exact:
+// one scale per point row (amax over the row), and one for all centroids of
+// the step (amax over C), so that a score needs a single per-row factor.
 // Every row also gets upper bounds of ||v~||, of the residual ||v~ - v|| (each
 // residual v~_t - v_t is exact in FP32) and of ||v||, which size the
 // assignment error bound. Codes are stored K-major with Kp >= d columns
@@ -95,6 +97,16 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
   }
 }
 
+// max_{j,t} |c_jt| of the step's centroids into ctl->camax_bits.
+__global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C, int64_t kd, Ctl* ctl) {
+  if (halted(ctl)) return;
+  float m = 0.f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kd; e += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(C[e]));
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomic_max_nonneg(&ctl->camax_bits, m);
+}
+
 template <int FP8>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
@@ -116,14 +128,10 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     }
     const float* c = C + (int64_t)j * d;
     double s2 = 0.0;
-    float amax = 0.f;
-    for (int t = lane; t < d; t += 32) {
-      s2 = fma((double)c[t], (double)c[t], s2);
-      amax = fmaxf(amax, fabsf(c[t]));
-    }
+    for (int t = lane; t < d; t += 32) s2 = fma((double)c[t], (double)c[t], s2);
 #pragma unroll
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+    const float sc = FP8 ? pow2_scale(__uint_as_float(ctl->camax_bits)) : 1.f;  // one scale for all centroids
     const float inv = FP8 ? pow2_inv(sc) : 1.f;
     float sqq = 0.f, sdd = 0.f;
     for (int t = lane; t < Kp; t += 32) {
@@ -177,8 +185,15 @@ cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (fp8) quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
-  else quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+  if (fp8) {
+    const int64_t kd = (int64_t)p.k * p.d;
+    int mb = (int)((kd + 255) / 256);
+    if (mb > num_sms() * 4) mb = num_sms() * 4;
+    camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, w.ctl);
+    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+  } else {
+    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+  }
   return cudaGetLastError();
 }
 

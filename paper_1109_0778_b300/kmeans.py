@@ -199,22 +199,45 @@ def run_host(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, preci
     return st.as_dict()
 
 
+class Batch:
+    """A list of (X, C, assign, sums, counts) device-tensor tuples checked and marshalled once.
+
+    ``run`` calls kmeans_run_batched on it as often as needed; the tensors are
+    referenced, not copied, so their contents may change between runs (their
+    shapes, dtypes and storage must not).
+    """
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.count = len(self.problems)
+        self.arr = (Instance * self.count)()
+        for b, (X, C, assign, sums, counts) in enumerate(self.problems):
+            n, d, k = _check_tensors(X, C, assign, sums, counts)
+            self.arr[b] = Instance(X.data_ptr(), n, d, k, C.data_ptr(), assign.data_ptr(), sums.data_ptr(),
+                                   counts.data_ptr())
+        self.stats = (Stats * self.count)()
+
+    def run(self, iters, tol=0.0, *, precision="bf16", recheck=True, stream=None, warm_start=False,
+            profile=False):
+        """Runs the batch; returns the per-instance stats as a numpy structured array."""
+        import numpy as np
+
+        o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
+        _check(_lib.kmeans_run_batched(ctypes.byref(o), self.arr, self.count, int(iters), float(tol), self.stats))
+        return np.ctypeslib.as_array(self.stats).copy()
+
+
 def run_batched(problems, iters, tol=0.0, *, precision="bf16", recheck=True, stream=None, warm_start=False,
                 profile=False):
-    """kmeans_run_batched over a list of (X, C, assign, sums, counts) device-tensor tuples.
+    """kmeans_run_batched over a list of (X, C, assign, sums, counts) device-tensor tuples (or a Batch).
 
     Every C is updated in place. Returns the list of per-instance stats dicts
     (with ``profile``, each carries the batch's device time per stage).
     """
-    count = len(problems)
-    arr = (Instance * count)()
-    for b, (X, C, assign, sums, counts) in enumerate(problems):
-        n, d, k = _check_tensors(X, C, assign, sums, counts)
-        arr[b] = Instance(X.data_ptr(), n, d, k, C.data_ptr(), assign.data_ptr(), sums.data_ptr(), counts.data_ptr())
-    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
-    st = (Stats * count)()
-    _check(_lib.kmeans_run_batched(ctypes.byref(o), arr, count, int(iters), float(tol), st))
-    return [s.as_dict() for s in st]
+    batch = problems if isinstance(problems, Batch) else Batch(problems)
+    batch.run(iters, tol, precision=precision, recheck=recheck, stream=stream, warm_start=warm_start,
+              profile=profile)
+    return [s.as_dict() for s in batch.stats]
 
 
 def version() -> int:
