@@ -30,6 +30,8 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, PAD = 4;
 constexpr int THREADS = 256;
+constexpr int ST = 512, SR = 4;  // slab kernel: 512 threads, 4 rows x 8 columns each (16 warps per SM)
+__device__ __forceinline__ int srow_of(int ty, int r) { return ty * 4 + r; }
 
 __device__ __forceinline__ int row_of(int ty, int r) { return r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4); }
 __device__ __forceinline__ int col_of(int tx, int c) { return c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
@@ -43,15 +45,11 @@ struct Top2 {
 
 __device__ __forceinline__ void top2_push(Top2& t, float s, int j) {
   // Columns arrive in increasing j, so strict comparisons keep the lowest
-  // index among equal scores.
-  if (s < t.b2) {
-    if (s < t.b1) {
-      t.b2 = t.b1;
-      t.b1 = s; t.i1 = j;
-    } else {
-      t.b2 = s;
-    }
-  }
+  // index among equal scores. Branch-free: a NaN score changes nothing.
+  const bool lt1 = s < t.b1;
+  t.b2 = lt1 ? t.b1 : fminf(t.b2, s);
+  t.i1 = lt1 ? j : t.i1;
+  t.b1 = lt1 ? s : t.b1;
 }
 
 __device__ __forceinline__ Top2 top2_merge(const Top2& a, const Top2& b) {
@@ -216,8 +214,8 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
 // ---------------------------------------------------------------------------
 // Slab-resident variant (d <= 128). A slab of up to kSlab centroids is loaded
 // into shared memory once per CTA (transposed, with its h_j); point tiles
-// stream through a cp.async double buffer, and each thread reads its 8 rows
-// four K-elements at a time. A row's running (best, index, second) lives in
+// stream through a cp.async double buffer, and each of 512 threads reads its
+// 4 rows four K-elements at a time. A row's running (best, index, second) lives in
 // registers within a slab and in `state` between slabs; the last slab applies
 // the same error-bound test as the streaming kernel above.
 constexpr int kSlabMaxD = 128;
@@ -240,12 +238,12 @@ __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const 
   const int64_t m0 = tile * BM;
   if (V16) {
     const int per_row = d >> 2;
-    for (int e = threadIdx.x; e < BM * per_row; e += THREADS) {
+    for (int e = threadIdx.x; e < BM * per_row; e += ST) {
       const int r = e / per_row, c4 = e - r * per_row;
       if (m0 + r < n) cp_async16(Xs + r * xs_stride + 4 * c4, X + (m0 + r) * d + 4 * c4);
     }
   } else {
-    for (int e = threadIdx.x; e < BM * d; e += THREADS) {
+    for (int e = threadIdx.x; e < BM * d; e += ST) {
       const int r = e / d, c = e - r * d;
       if (m0 + r < n) cp_async4(Xs + r * xs_stride + c, X + (m0 + r) * d + c);
     }
@@ -253,7 +251,7 @@ __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const 
 }
 
 template <bool V16>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(ST, 1)
 assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
@@ -271,13 +269,13 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   // slab of centroids, transposed; zero padding in [d, dp) and [ns, nsp)
-  for (int e = tid; e < dp * nsp; e += THREADS) {
+  for (int e = tid; e < dp * nsp; e += ST) {
     const int j = e % nsp, t = e / nsp;
     Cs[e] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
   }
-  for (int j = tid; j < nsp; j += THREADS) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
+  for (int j = tid; j < nsp; j += ST) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
   // zero both point buffers once: padding columns [d, dp) and rows past n stay zero
-  for (int e = tid; e < 2 * BM * xs_stride; e += THREADS) Xs0[e] = 0.f;
+  for (int e = tid; e < 2 * BM * xs_stride; e += ST) Xs0[e] = 0.f;
   __syncthreads();
 
   const float H = __uint_as_float(ctl->hmax_bits);
@@ -295,10 +293,10 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     __syncthreads();
 
     const int64_t m0 = tile * BM;
-    Top2 top[8];
+    Top2 top[SR];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int64_t i = m0 + row_of(ty, r);
+    for (int r = 0; r < SR; ++r) {
+      const int64_t i = m0 + srow_of(ty, r);
       // the carried state enters through one of the 16 threads sharing the row,
       // so the cross-thread merge sees it once
       if (!first_slab && tx == 0 && i < n) {
@@ -309,16 +307,17 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
       }
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
-      float2 acc2[8][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
+      float2 acc2[SR][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int r = 0; r < SR; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc2[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
       for (int kk = 0; kk < dp; kk += 4) {
-        float a[8][4];
+        float a[SR][4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
-          *reinterpret_cast<float4*>(a[r]) = *reinterpret_cast<const float4*>(Xs + row_of(ty, r) * xs_stride + kk);
+        for (int r = 0; r < SR; ++r)
+          *reinterpret_cast<float4*>(a[r]) = *reinterpret_cast<const float4*>(Xs + srow_of(ty, r) * xs_stride + kk);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float2 b2[4];
@@ -328,16 +327,16 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
           b2[0] = make_float2(b0.x, b0.y); b2[1] = make_float2(b0.z, b0.w);
           b2[2] = make_float2(b1.x, b1.y); b2[3] = make_float2(b1.z, b1.w);
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
+          for (int r = 0; r < SR; ++r) {
             const float2 ar = make_float2(a[r][q], a[r][q]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc2[r][c] = __ffma2_rn(ar, b2[c], acc2[r][c]);
           }
         }
       }
-      float acc[8][8];
+      float acc[SR][8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+      for (int r = 0; r < SR; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           acc[r][2 * c] = acc2[r][c].x;
@@ -348,11 +347,11 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
         const int jl = j0 + col_of(tx, c);
         const float hj = Hs[jl];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) top2_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
+        for (int r = 0; r < SR; ++r) top2_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
       }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
+    for (int r = 0; r < SR; ++r) {
 #pragma unroll
       for (int o = 8; o; o >>= 1) {
         Top2 p;
@@ -367,8 +366,8 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     if (tx == 0) {
       unsigned int changed = 0;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int64_t i = m0 + row_of(ty, r);
+      for (int r = 0; r < SR; ++r) {
+        const int64_t i = m0 + srow_of(ty, r);
         if (i >= n) continue;
         if (!last_slab) {
           state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
@@ -454,11 +453,11 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* cha
     const size_t smem = slab_smem_bytes(dp, nsp);
     const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
     if (v16)
-      assign_slab_kernel<true><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
+      assign_slab_kernel<true><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
                                                             w.ctl, p.assign, w.flags, w.state, first, first_slab,
                                                             last_slab, gam, sr);
     else
-      assign_slab_kernel<false><<<blocks, THREADS, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
+      assign_slab_kernel<false><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
                                                              w.ctl, p.assign, w.flags, w.state, first, first_slab,
                                                              last_slab, gam, sr);
     cudaError_t e = cudaGetLastError();
