@@ -55,6 +55,10 @@ def bind(path: str):
     lib.kmref_step.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, vp, vp]
     lib.kmref_run.restype = ctypes.c_int
     lib.kmref_run.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, i32, dbl, vp, vp]
+    lib.kmref_gda.restype = ctypes.c_int
+    lib.kmref_gda.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp]
+    lib.kmref_nb.restype = ctypes.c_int
+    lib.kmref_nb.argtypes = [vp, i64, i32, vp, i32, vp, vp]
     return lib
 
 
@@ -164,6 +168,34 @@ class Oracle:
             raise ValueError(f"kmref_run failed ({rc})")
         return dict(assign=a, sums=sums, counts=counts, C=C, objectives=hist[: done.value],
                     iters_done=done.value)
+
+
+    # ---------------------------------------------------------------- keyed-reduce training
+
+    def gda(self, X, y, ncls: int):
+        """(phi f64[ncls], mu f64[ncls,d], sigma f64[d,d]): shared-covariance GDA."""
+        X = _f32(X)
+        n, d = X.shape
+        yy = np.ascontiguousarray(y, dtype=np.int32)
+        phi = np.empty(ncls, np.float64)
+        mu = np.empty((ncls, d), np.float64)
+        sigma = np.empty((d, d), np.float64)
+        rc = self.lib.kmref_gda(_ptr(X), n, d, _ptr(yy), ncls, _ptr(phi), _ptr(mu), _ptr(sigma))
+        if rc:
+            raise ValueError(f"kmref_gda failed ({rc})")
+        return phi, mu, sigma
+
+    def nb(self, X, y, ncls: int):
+        """(prior f64[ncls], theta f64[ncls,d]): multinomial naive Bayes, add-one smoothing."""
+        X = _f32(X)
+        n, d = X.shape
+        yy = np.ascontiguousarray(y, dtype=np.int32)
+        prior = np.empty(ncls, np.float64)
+        theta = np.empty((ncls, d), np.float64)
+        rc = self.lib.kmref_nb(_ptr(X), n, d, _ptr(yy), ncls, _ptr(prior), _ptr(theta))
+        if rc:
+            raise ValueError(f"kmref_nb failed ({rc})")
+        return prior, theta
 
 
 _default = None

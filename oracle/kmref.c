@@ -202,3 +202,93 @@ int kmref_run(const float* X, int64_t n, int32_t d, double* C, int32_t k, int32_
   free(prev);
   return rc;
 }
+
+/*
+ * Keyed-reduce training of the paper's two GPU classifiers, naive Bayes (NB)
+ * and Gaussian discriminant analysis (GDA) (the GPU results of Sec. 5): both
+ * reduce labelled rows keyed by class (DeliteReduceElem, Sec. 2.4), the same
+ * pattern as the k-means sums with the label in place of the assignment.
+ * FP64, rows in index order. y_i must lie in [0, ncls).
+ *
+ * Readings where the paper gives no formula (also in the design notes):
+ *   - GDA: shared covariance for any number of classes,
+ *       phi_c = n_c / n,  mu_c = (1 / n_c) sum_{y_i = c} x_i  (0 when n_c = 0),
+ *       Sigma = (1 / n) sum_i (x_i - mu_{y_i}) (x_i - mu_{y_i})^T;
+ *   - NB: multinomial with add-one (Laplace) smoothing over d features,
+ *       prior_c = n_c / n,  S_cj = sum_{y_i = c} x_ij,
+ *       theta_cj = (S_cj + 1) / (sum_j S_cj + d).
+ */
+
+/* n_c and the class sums S_c (ncls x d), index order. */
+static int class_sums(const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls, double* sums,
+                      int64_t* counts) {
+  if (!X || !y || !sums || !counts || n < 1 || d < 1 || ncls < 1) return -1;
+  memset(sums, 0, sizeof(double) * (size_t)ncls * (size_t)d);
+  memset(counts, 0, sizeof(int64_t) * (size_t)ncls);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t c = y[i];
+    if (c < 0 || c >= ncls) return -2;
+    counts[c] += 1;
+    double* s = sums + (int64_t)c * d;
+    const float* x = X + i * (int64_t)d;
+    for (int32_t t = 0; t < d; ++t) s[t] += (double)x[t];
+  }
+  return 0;
+}
+
+/* GDA: phi (ncls), mu (ncls x d), sigma (d x d, row-major, symmetric). */
+int kmref_gda(const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls, double* phi, double* mu,
+              double* sigma) {
+  if (!phi || !mu || !sigma) return -1;
+  int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncls);
+  double* c = (double*)malloc(sizeof(double) * (size_t)d);
+  if (!counts || !c) {
+    free(counts);
+    free(c);
+    return -3;
+  }
+  int rc = class_sums(X, n, d, y, ncls, mu, counts);
+  if (rc == 0) {
+    for (int32_t k = 0; k < ncls; ++k) {
+      phi[k] = (double)counts[k] / (double)n;
+      for (int32_t t = 0; t < d; ++t)
+        mu[(int64_t)k * d + t] = counts[k] > 0 ? mu[(int64_t)k * d + t] / (double)counts[k] : 0.0;
+    }
+    memset(sigma, 0, sizeof(double) * (size_t)d * (size_t)d);
+    for (int64_t i = 0; i < n; ++i) {
+      const float* x = X + i * (int64_t)d;
+      const double* m = mu + (int64_t)y[i] * d;
+      for (int32_t t = 0; t < d; ++t) c[t] = (double)x[t] - m[t];
+      for (int32_t a = 0; a < d; ++a)
+        for (int32_t b = a; b < d; ++b) sigma[(int64_t)a * d + b] += c[a] * c[b];
+    }
+    for (int32_t a = 0; a < d; ++a)
+      for (int32_t b = a; b < d; ++b) {
+        const double v = sigma[(int64_t)a * d + b] / (double)n;
+        sigma[(int64_t)a * d + b] = v;
+        sigma[(int64_t)b * d + a] = v;
+      }
+  }
+  free(counts);
+  free(c);
+  return rc;
+}
+
+/* NB: prior (ncls), theta (ncls x d). */
+int kmref_nb(const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls, double* prior, double* theta) {
+  if (!prior || !theta) return -1;
+  int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncls);
+  if (!counts) return -3;
+  int rc = class_sums(X, n, d, y, ncls, theta, counts);
+  if (rc == 0) {
+    for (int32_t k = 0; k < ncls; ++k) {
+      prior[k] = (double)counts[k] / (double)n;
+      double* s = theta + (int64_t)k * d;
+      double total = 0.0;
+      for (int32_t t = 0; t < d; ++t) total += s[t];
+      for (int32_t t = 0; t < d; ++t) s[t] = (s[t] + 1.0) / (total + (double)d);
+    }
+  }
+  free(counts);
+  return rc;
+}
