@@ -207,6 +207,33 @@ int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C,
                           int32_t k, const int32_t* assign, float* sums,
                           int32_t* counts, double* objective, void* stream);
 
+/*
+ * Keyed-reduce training of the paper's GPU classifiers (Sec. 5: naive Bayes and
+ * Gaussian discriminant analysis): the keyed reduce of a Lloyd step (Sec. 2.4)
+ * keyed by a class label y_i in [0, ncls) instead of the assignment. With
+ * n_c = |{i : y_i = c}| and S_c = sum_{y_i = c} x_i (FP32 Kahan runs combined in
+ * FP64, as the k-means sums):
+ *
+ * kmeans_gda_train -- shared-covariance GDA:
+ *   phi[c] = n_c / n; mu[c] = S_c / n_c (0 for an empty class), rounded to FP32;
+ *   sigma = (1/n) sum_i (x_i - mu_{y_i})(x_i - mu_{y_i})^T, d x d row-major,
+ *   symmetric (FP32 partials over 32 rows, FP64 accumulation, rounded to FP32).
+ * kmeans_nb_train -- multinomial naive Bayes with add-one smoothing (X holds
+ *   non-negative feature counts):
+ *   prior[c] = n_c / n; theta[c][j] = (S_cj + 1) / (sum_j S_cj + d).
+ *
+ * X: const float[n*d] row-major, y: const int32[n]; outputs phi/prior float[ncls],
+ * mu/theta float[ncls*d], sigma float[d*d]; all device pointers owned by the
+ * caller. 1 <= n < 2^31, 1 <= d <= 256, 1 <= ncls <= 2^20; a label outside
+ * [0, ncls) gives KM_EINVAL (outputs unspecified). opts: only `stream` is used
+ * (NULL opts = defaults); the stream is synchronised before returning. The
+ * library's workspace is reused (grown with cudaMalloc when needed).
+ */
+int kmeans_gda_train(const km_opts* opts, const float* X, int64_t n, int32_t d,
+                     const int32_t* y, int32_t ncls, float* phi, float* mu, float* sigma);
+int kmeans_nb_train(const km_opts* opts, const float* X, int64_t n, int32_t d,
+                    const int32_t* y, int32_t ncls, float* prior, float* theta);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* kmeans_last_error(void);
 

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <initializer_list>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -83,6 +84,8 @@ struct DevCtx {
   size_t ws_bytes = 0;
   uint64_t ws_gen = 0;
   void* stage = nullptr;  // device copies for the host-pointer entry point
+  void* cls = nullptr;    // class counts and covariance accumulators of the training entry points
+  size_t cls_bytes = 0;
   size_t stage_bytes = 0;
   void* host = nullptr;   // pinned read-back of Ctl and the per-step history
   size_t host_bytes = 0;
@@ -766,6 +769,108 @@ KM_API int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32
   KM_CUDA(cudaMemcpyAsync(counts, p.counts, (size_t)k * 4, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaStreamSynchronize(s));
   return KM_OK;
+}
+
+// ============================================================================ keyed-reduce training
+
+namespace {
+
+// The class keyed reduce shared by GDA and NB: n_c into counts, S_c into
+// w.sums64 (FP64), then `finish` enqueues the method's own kernels. Runs
+// synchronously on opts->stream; bad labels give KM_EINVAL.
+template <typename Finish>
+int class_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls,
+                std::initializer_list<std::pair<const void*, const char*>> outs, size_t cov_bytes,
+                Finish&& finish) {
+  g_err.clear();
+  const km_opts o = resolve(opts);
+  if (!X || !y) return fail(KM_EINVAL, "X and y must be non-null");
+  if (n < 1 || n > INT32_MAX) return fail(KM_EINVAL, "n = %lld outside [1, 2^31)", (long long)n);
+  if (d < 1 || d > kMaxD) return fail(KM_EINVAL, "d = %d outside [1, %d]", d, kMaxD);
+  if (ncls < 1 || ncls > (1 << 20)) return fail(KM_EINVAL, "ncls = %d outside [1, 2^20]", ncls);
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(KM_EUNSUPPORTED, "device index %d", dev);
+  int rc;
+  if ((rc = check_device_ptr(X, "X", dev)) || (rc = check_device_ptr(y, "y", dev))) return rc;
+  for (const auto& op : outs) {
+    if (!op.first) return fail(KM_EINVAL, "%s must be non-null", op.second);
+    if ((rc = check_device_ptr(op.first, op.second, dev))) return rc;
+  }
+  DevCtx* c = get_ctx(dev);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((rc = init_ctx(c))) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  const Layout L = layout_for(n, ncls, d, 1, KM_FP32, 0);
+  if ((rc = ensure_ws(c, L, s))) return rc;
+  const Work w = make_work(c, L);
+  const size_t cnt_bytes = align_up(4 * (size_t)ncls), need = cnt_bytes + align_up(cov_bytes) + 1024;
+  if (need > c->cls_bytes) {
+    if (c->cls) {
+      KM_CUDA(cudaDeviceSynchronize());
+      cudaFree(c->cls);
+      c->cls = nullptr;
+      c->cls_bytes = 0;
+    }
+    if (cudaMalloc(&c->cls, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "class buffer allocation of %zu bytes failed", need);
+    }
+    c->cls_bytes = need;
+  }
+  char* cb = (char*)c->cls;
+  int32_t* counts = (int32_t*)cb;
+  double* cov64 = (double*)(cb + cnt_bytes);
+  int2* tiles = (int2*)(cb + cnt_bytes + align_up(cov_bytes));
+  KM_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
+  KM_CUDA(cudaMemsetAsync(w.sums64, 0, 8 * (size_t)ncls * d, s));
+  KM_CUDA(cudaMemsetAsync(counts, 0, 4 * (size_t)ncls, s));
+  KM_CUDA(cudaMemsetAsync(w.Csave, 0, 4 * (size_t)ncls * d, s));  // zero centres: the reduce's objective is unused
+  if (cov_bytes) KM_CUDA(cudaMemsetAsync(cov64, 0, cov_bytes, s));
+  // the keyed reduce of a Lloyd step with the labels as keys
+  Problem p{X, n, d, w.Csave, ncls, const_cast<int32_t*>(y), nullptr, counts};
+  KM_CUDA(launch_check_classes(y, n, ncls, w.ctl, s));
+  KM_CUDA(launch_count(p, w, s));
+  KM_CUDA(launch_scan(p, w, s));
+  KM_CUDA(launch_scatter(p, w, s));
+  KM_CUDA(launch_segsum(p, w, s));
+  KM_CUDA(finish(w, counts, cov64, tiles, s));
+  if (sizeof(Ctl) > c->host_bytes) {  // pinned read-back of the control block
+    if (c->host) cudaFreeHost(c->host);
+    c->host = nullptr;
+    c->host_bytes = 0;
+    if (cudaMallocHost(&c->host, 4096) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "pinned host allocation failed");
+    }
+    c->host_bytes = 4096;
+  }
+  Ctl* hc = (Ctl*)c->host;
+  KM_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  if (hc->error) return fail(hc->error, "a label lies outside [0, %d)", ncls);
+  return KM_OK;
+}
+
+}  // namespace
+
+KM_API int kmeans_gda_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls,
+                        float* phi, float* mu, float* sigma) {
+  return class_train(opts, X, n, d, y, ncls, {{phi, "phi"}, {mu, "mu"}, {sigma, "sigma"}},
+                     8 * (size_t)d * (size_t)d,
+                     [&](const Work& w, const int32_t* counts, double* cov64, int2* tiles, cudaStream_t s) {
+                       cudaError_t e = launch_gda_means(w.sums64, counts, n, d, ncls, phi, mu, w.ctl, s);
+                       if (e == cudaSuccess) e = launch_gda_cov(X, n, d, y, mu, tiles, cov64, sigma, w.ctl, s);
+                       return e;
+                     });
+}
+
+KM_API int kmeans_nb_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls,
+                       float* prior, float* theta) {
+  return class_train(opts, X, n, d, y, ncls, {{prior, "prior"}, {theta, "theta"}}, 0,
+                     [&](const Work& w, const int32_t* counts, double*, int2*, cudaStream_t s) {
+                       return launch_nb_theta(w.sums64, counts, n, d, ncls, prior, theta, w.ctl, s);
+                     });
 }
 
 KM_API const char* kmeans_last_error(void) { return g_err.c_str(); }

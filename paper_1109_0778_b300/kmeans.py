@@ -23,7 +23,7 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 #: Entry points declared in include/kmeans.h (checked by the ABI test).
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
            "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc",
-           "kmeans_run_batched")
+           "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train")
 
 
 class KMeansError(RuntimeError):
@@ -83,6 +83,10 @@ def load(path: str = LIB_PATH):
     lib.kmeans_run_batched.argtypes = [P(Opts), P(Instance), i32, i32, dbl, P(Stats)]
     lib.kmeans_reduce_noalloc.restype = ctypes.c_int
     lib.kmeans_reduce_noalloc.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp, P(dbl), vp]
+    lib.kmeans_gda_train.restype = ctypes.c_int
+    lib.kmeans_gda_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, vp]
+    lib.kmeans_nb_train.restype = ctypes.c_int
+    lib.kmeans_nb_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp]
     return lib
 
 
@@ -238,6 +242,48 @@ def run_batched(problems, iters, tol=0.0, *, precision="bf16", recheck=True, str
     batch.run(iters, tol, precision=precision, recheck=recheck, stream=stream, warm_start=warm_start,
               profile=profile)
     return [s.as_dict() for s in batch.stats]
+
+
+def _check_labelled(X, y, ncls):
+    import torch
+
+    if not (X.is_cuda and y.is_cuda):
+        raise ValueError("X and y must be CUDA tensors")
+    if X.dtype != torch.float32 or X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous float32 (n, d) tensor")
+    n, d = X.shape
+    if y.dtype != torch.int32 or tuple(y.shape) != (n,) or not y.is_contiguous():
+        raise ValueError(f"y must be a contiguous int32 tensor of shape ({n},)")
+    if ncls < 1:
+        raise ValueError("ncls must be >= 1")
+    return n, d
+
+
+def gda_train(X, y, ncls, *, stream=None):
+    """kmeans_gda_train: (phi [ncls], mu [ncls, d], sigma [d, d]) as float32 device tensors."""
+    import torch
+
+    n, d = _check_labelled(X, y, ncls)
+    phi = torch.empty(ncls, dtype=torch.float32, device=X.device)
+    mu = torch.empty(ncls, d, dtype=torch.float32, device=X.device)
+    sigma = torch.empty(d, d, dtype=torch.float32, device=X.device)
+    o = make_opts(stream=_stream_handle(stream))
+    _check(_lib.kmeans_gda_train(ctypes.byref(o), X.data_ptr(), n, d, y.data_ptr(), int(ncls), phi.data_ptr(),
+                                 mu.data_ptr(), sigma.data_ptr()))
+    return phi, mu, sigma
+
+
+def nb_train(X, y, ncls, *, stream=None):
+    """kmeans_nb_train: (prior [ncls], theta [ncls, d]) as float32 device tensors."""
+    import torch
+
+    n, d = _check_labelled(X, y, ncls)
+    prior = torch.empty(ncls, dtype=torch.float32, device=X.device)
+    theta = torch.empty(ncls, d, dtype=torch.float32, device=X.device)
+    o = make_opts(stream=_stream_handle(stream))
+    _check(_lib.kmeans_nb_train(ctypes.byref(o), X.data_ptr(), n, d, y.data_ptr(), int(ncls), prior.data_ptr(),
+                                theta.data_ptr()))
+    return prior, theta
 
 
 def version() -> int:
