@@ -53,7 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(TRAIN_WORKLOADS))
     ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 (default: the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
@@ -409,6 +409,87 @@ def precision_variants(torch, dev, steps=2, warmup=1):
     return out
 
 
+# Keyed-reduce training workloads (GDA: labelled Gaussian mixture; NB: Poisson feature counts).
+TRAIN_WORKLOADS = {
+    "gda_n1M_d64_c16": {"kind": "gda", "n": 1 << 20, "d": 64, "ncls": 16, "seed": 0x5EED0100},
+    "nb_n1M_d256_c20": {"kind": "nb", "n": 1 << 20, "d": 256, "ncls": 20, "seed": 0x5EED0101},
+}
+
+
+def training_data(tw):
+    if tw["kind"] == "gda":
+        X, y = synth.mixture(tw["seed"], tw["n"], tw["d"], tw["ncls"], 6.0, 1.5, with_comp=True)
+        return X, y.astype(np.int32)
+    rng = np.random.default_rng(tw["seed"])
+    y = rng.integers(0, tw["ncls"], tw["n"]).astype(np.int32)
+    X = rng.poisson(rng.uniform(0.2, 3.0, (tw["ncls"], tw["d"]))[y]).astype(np.float32)
+    return X, y
+
+
+def run_training(args, torch, dev, dist, rank, world, local):
+    """One step = one training call (kmeans_gda_train / kmeans_nb_train) on HBM-resident inputs."""
+    from paper_1109_0778_b300 import kmeans as km
+
+    tw = TRAIN_WORKLOADS[args.workload]
+    X, y = training_data(tw)
+    n, d, ncls = tw["n"], tw["d"], tw["ncls"]
+    Xd, yd = torch.from_numpy(X).to(dev), torch.from_numpy(y).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    train = km.gda_train if tw["kind"] == "gda" else km.nb_train
+    for _ in range(max(args.warmup, 0)):
+        train(Xd, yd, ncls, stream=stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            train(Xd, yd, ncls, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    t = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, dev)
+    value = aggregate_rate(args.steps, world, t)
+    peaks, peak_src = measured_peaks()
+    # algorithmic bytes: X once for the class sums (+ once more for the covariance), labels twice
+    passes = 2 if tw["kind"] == "gda" else 1
+    algo = passes * 4.0 * n * d + 8.0 * n
+    achieved = algo / (t / args.steps) / 1e9
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        orc = oracle.oracle()
+        cores = orc.set_threads(0)
+        rows = 1 << 16
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0) or reps == 0:
+            (orc.gda if tw["kind"] == "gda" else orc.nb)(X[:rows], y[:rows], ncls)
+            reps += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": reps * rows / n / el, "unit": "trainings/s", "cores": cores, "kind": "oracle",
+               "sample": f"{reps} oracle trainings on the first {rows} of {n} rows, {el:.1f} s; "
+                         f"trainings/s extrapolated linearly in n"}
+    if rank == 0:
+        line = {
+            "metric": f"{tw['kind'].upper()} trainings/s (keyed reduce by class)", "value": value,
+            "unit": "trainings/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "d": d, "ncls": ncls, "seed": hex(tw["seed"]),
+                       "l2": f"inputs larger than L2 (X = {4 * n * d / 1e6:.0f} MB)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "kernel": "whole training call",
+                         "note": f"algorithmic bytes = {passes} FP32 read(s) of X + labels", "traffic": None},
+            "clocks": clk.summary(), "e2e": None, "cpu_baseline": cpu, "peaks_source": peak_src,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -420,6 +501,8 @@ def run_ours(args):
     dist = dist_init(world, "nccl")
     from paper_1109_0778_b300 import kmeans as km
 
+    if args.workload in TRAIN_WORKLOADS:
+        return run_training(args, torch, dev, dist, rank, world, local)
     if args.workload == "batched_512":
         return run_batched(args, torch, dev, dist, rank, world, local)
     w = WORKLOADS[args.workload]

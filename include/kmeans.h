@@ -217,7 +217,8 @@ int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C,
  * kmeans_gda_train -- shared-covariance GDA:
  *   phi[c] = n_c / n; mu[c] = S_c / n_c (0 for an empty class), rounded to FP32;
  *   sigma = (1/n) sum_i (x_i - mu_{y_i})(x_i - mu_{y_i})^T, d x d row-major,
- *   symmetric (FP32 partials over 32 rows, FP64 accumulation, rounded to FP32).
+ *   symmetric (FP32 partials over 64 rows, Kahan-added, combined in FP64, rounded
+ *   to FP32; the same on every run).
  * kmeans_nb_train -- multinomial naive Bayes with add-one smoothing (X holds
  *   non-negative feature counts):
  *   prior[c] = n_c / n; theta[c][j] = (S_cj + 1) / (sum_j S_cj + d).

@@ -826,7 +826,6 @@ int class_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const
   KM_CUDA(cudaMemsetAsync(w.sums64, 0, 8 * (size_t)ncls * d, s));
   KM_CUDA(cudaMemsetAsync(counts, 0, 4 * (size_t)ncls, s));
   KM_CUDA(cudaMemsetAsync(w.Csave, 0, 4 * (size_t)ncls * d, s));  // zero centres: the reduce's objective is unused
-  if (cov_bytes) KM_CUDA(cudaMemsetAsync(cov64, 0, cov_bytes, s));
   // the keyed reduce of a Lloyd step with the labels as keys
   Problem p{X, n, d, w.Csave, ncls, const_cast<int32_t*>(y), nullptr, counts};
   KM_CUDA(launch_check_classes(y, n, ncls, w.ctl, s));
@@ -857,7 +856,7 @@ int class_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const
 KM_API int kmeans_gda_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncls,
                         float* phi, float* mu, float* sigma) {
   return class_train(opts, X, n, d, y, ncls, {{phi, "phi"}, {mu, "mu"}, {sigma, "sigma"}},
-                     8 * (size_t)d * (size_t)d,
+                     gda_cov_scratch_bytes(n, d),
                      [&](const Work& w, const int32_t* counts, double* cov64, int2* tiles, cudaStream_t s) {
                        cudaError_t e = launch_gda_means(w.sums64, counts, n, d, ncls, phi, mu, w.ctl, s);
                        if (e == cudaSuccess) e = launch_gda_cov(X, n, d, y, mu, tiles, cov64, sigma, w.ctl, s);

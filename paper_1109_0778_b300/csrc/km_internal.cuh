@@ -220,7 +220,8 @@ cudaError_t launch_gda_means(const double* sums64, const int32_t* counts, int64_
 cudaError_t launch_nb_theta(const double* sums64, const int32_t* counts, int64_t n, int d, int ncls, float* prior,
                             float* theta, const Ctl* ctl, cudaStream_t s);
 cudaError_t launch_gda_cov(const float* X, int64_t n, int d, const int32_t* y, const float* mu, int2* tiles_dev,
-                           double* sigma64, float* sigma, const Ctl* ctl, cudaStream_t s);
+                           double* part, float* sigma, const Ctl* ctl, cudaStream_t s);
+size_t gda_cov_scratch_bytes(int64_t n, int d);
 cudaError_t launch_b_reset(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s);
 cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s);

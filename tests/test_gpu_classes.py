@@ -5,7 +5,7 @@ Tolerances (derived from the arithmetic, as for the k-means sums):
   - mu: the class sums are FP32 Kahan runs combined in FP64 (error ~1e-7 of the sum
     of |x|), so |mu - mu_ref| <= 1e-5 * max_t mean_{y_i = c} |x_it| (the k-means
     centroid tolerance);
-  - sigma: each entry is a sum of FP32 partials over 32 rows (<= 33u of the partial's
+  - sigma: each entry is a sum of FP32 partials over 64 rows (<= 65u of the partial's
     sum of |terms|) accumulated in FP64, from rows centred with the FP32 class mean
     (a second-order change), so |sigma_ab - ref_ab| <= 1e-5 * S_ab with
     S_ab = (1/n) sum_i |c_ia| |c_ib|, c the rows centred with the FP64 means;
