@@ -44,7 +44,8 @@ METRIC = "Lloyd iter/s + distance TFLOP/s: FP32 vs BF16/FP8+recheck, exact assig
 DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
 STAGE_KERNELS = ("prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
 # Source file of each stage's kernel (a change to it voids a stored ncu traffic figure).
-KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu", "bf16": "km_assign_tc.cu", "fp8": "km_assign_tc.cu"}}
+KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu", "bf16": "km_assign_tc.cu", "fp8": "km_assign_tc.cu",
+                             "bf16x3": "km_assign_tc.cu"}}
 
 
 def parse_args(argv=None):
@@ -54,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(TRAIN_WORKLOADS))
-    ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 (default: the workload's first)")
+    ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 | bf16x3 (default: the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
     ap.add_argument("--instances", type=int, default=0,
@@ -367,7 +368,9 @@ def run_batched(args, torch, dev, dist, rank, world, local):
 
 
 def precision_variants(torch, dev, steps=2, warmup=1):
-    """FP32 vs BF16 vs FP8 (+ FP32 re-check) on the 4M x 128 x 1024 workload, kmeans_run per step."""
+    """FP32 vs BF16 vs FP8 vs two-part BF16 (each + FP32 re-check) on the 4M x 128 x 1024 workload,
+    kmeans_run per step. The two-part BF16 path runs three BF16 products per distance, so its
+    tensor roofline counts 3 x 2nkd flops per iteration."""
     from paper_1109_0778_b300 import kmeans as km
 
     w = WORKLOADS["prec_n4M_d128_k1024"]
@@ -378,7 +381,7 @@ def precision_variants(torch, dev, steps=2, warmup=1):
     C0 = Xd[: w.k].clone()
     del X
     out = {"workload": w.name, "iters_per_step": w.iters}
-    for prec in ("fp32", "bf16", "fp8"):
+    for prec in ("fp32", "bf16", "fp8", "bf16x3"):
         C = C0.clone()
         a, s, c = km.alloc_outputs(Xd, C)
         for _ in range(warmup):
@@ -391,7 +394,8 @@ def precision_variants(torch, dev, steps=2, warmup=1):
             ms += o.stats["ms"]
         ips = steps * w.iters / (ms / 1e3)
         assign_ms = o.stats["stage_ms"]["assign"] / w.iters
-        achieved = w.flops_per_iter / (assign_ms / 1e3) / 1e12
+        products = 3 if prec == "bf16x3" else 1
+        achieved = products * w.flops_per_iter / (assign_ms / 1e3) / 1e12
         if prec == "fp32":
             peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
             bound = "alu"
@@ -404,7 +408,7 @@ def precision_variants(torch, dev, steps=2, warmup=1):
                                   "frac": achieved / peak, "traffic": stored_traffic("assign", prec, w.name)},
                      "stage_ms_per_iter": {k: v / w.iters for k, v in o.stats["stage_ms"].items()},
                      "flagged_last_iter": o.stats["n_flagged"], "objective": o.stats["objective"]}
-    for prec in ("bf16", "fp8"):
+    for prec in ("bf16", "fp8", "bf16x3"):
         out[prec]["speedup_vs_fp32"] = out[prec]["iter_s"] / out["fp32"]["iter_s"]
     return out
 
@@ -554,7 +558,7 @@ def run_ours(args):
     # dominant kernel: the fused assignment (per-launch time from the events around it)
     launches = args.steps * iters
     assign_ms = stage_tot["assign"] / launches
-    achieved = flops_iter / (assign_ms / 1e3) / 1e12
+    achieved = (3 if prec == "bf16x3" else 1) * flops_iter / (assign_ms / 1e3) / 1e12  # tensor products run
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if prec == "fp32":

@@ -65,8 +65,14 @@ typedef enum {
 
 /* Arithmetic of the distance contraction. FP32 is exact up to FP32 rounding
  * (SIMT FFMA); BF16 and FP8 run on the tensor cores with FP32 accumulation
- * and per-row scales; all three re-check near-ties in FP32. */
-typedef enum { KM_FP32 = 0, KM_BF16 = 1, KM_FP8E4M3 = 2 } km_precision;
+ * and per-row scales; all of them re-check near-ties in FP32.
+ * KM_BF16X3 splits every FP32 value v into two BF16 parts, v ~ hi + lo with
+ * hi = RN(v), lo = RN(v - hi), and forms x.c from the three products
+ * hi.hi + lo.hi + hi.lo on the tensor cores (the dropped lo.lo term and the
+ * residuals v - hi - lo enter the error bound), so that its near-tie margin is
+ * about 2^-8 of the BF16 one at three times the tensor work. Single-instance
+ * calls only; K blocks are 64 elements wide as for BF16. */
+typedef enum { KM_FP32 = 0, KM_BF16 = 1, KM_FP8E4M3 = 2, KM_BF16X3 = 3 } km_precision;
 
 typedef struct {
   int32_t precision;  /* km_precision; default KM_FP32 */

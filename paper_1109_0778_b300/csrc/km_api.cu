@@ -145,22 +145,32 @@ int init_ctx(DevCtx* c) {
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
 // Shape of the tensor-core path for (d, k, precision).
+// Kp: d padded to whole 128-byte K blocks; Kw: elements of one code row (Kp,
+// or 2 Kp for the two-part BF16 codes); nkb: K blocks of one code row.
 struct TcShape {
-  int fp8, esz, Kp, nkb, bn, kp, nchunks, stages, abufs;
+  int fp8, split, esz, Kp, Kw, nkb, bn, kp, nchunks, stages, abufs;
+  int qmode() const { return split ? 2 : fp8 ? 1 : 0; }  // quantisation stage mode
 };
 
 TcShape tc_shape(int precision, int d, int k) {
   TcShape t{};
   t.fp8 = precision == KM_FP8E4M3;
+  t.split = precision == KM_BF16X3;
   t.esz = t.fp8 ? 1 : 2;
   const int kbe = 128 / t.esz;
   t.Kp = (d + kbe - 1) / kbe * kbe;
-  t.nkb = t.Kp / kbe;
-  t.bn = t.nkb <= 2 ? 128 : 64;
-  t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of either width
-  t.nchunks = t.kp / t.bn;
-  // dynamic shared memory: A slots, B stages, h_j (and scales)
-  t.stages = tc_pick_buffers(t.nkb, t.bn, t.kp, t.fp8, &t.abufs);
+  t.Kw = t.split ? 2 * t.Kp : t.Kp;
+  t.nkb = t.Kw / kbe;
+  t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of any width
+  // chunk width: 128 centroids for short rows, else 64; 32 when only that
+  // leaves room for two B stages (the widest two-part codes)
+  for (int bn = t.nkb <= 2 ? 128 : 64; bn >= 32; bn /= 2) {
+    t.bn = bn;
+    t.nchunks = t.kp / t.bn;
+    // dynamic shared memory: A slots, B stages, h_j (and scales)
+    t.stages = tc_pick_buffers(t.nkb, t.bn, t.kp, t.fp8, &t.abufs);
+    if (t.stages >= 2 || (!t.split && bn == 64)) break;
+  }
   return t;
 }
 
@@ -206,7 +216,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   L.labs = take(4 * (size_t)n);  // labels in cluster-sorted order (scatter stage)
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
-    size_t xq = (size_t)n * t.Kp * t.esz, cq = (size_t)t.kp * t.Kp * t.esz;
+    size_t xq = (size_t)n * t.Kw * t.esz, cq = (size_t)t.kp * t.Kw * t.esz;
     const bool cold = cold_bf16_first(precision, warm, d, k);
     if (cold) {
       const TcShape t16 = tc_shape(KM_BF16, d, k);
@@ -368,7 +378,7 @@ int validate_args(const km_opts& o, const Problem& p, int iters) {
   if (p.k < 1 || (int64_t)p.k > p.n) return fail(KM_EINVAL, "k = %d outside [1, n]", p.k);
   if (p.d < 1 || p.d > kMaxD) return fail(KM_EINVAL, "d = %d outside [1, %d]", p.d, kMaxD);
   if (iters < 1) return fail(KM_EINVAL, "iters = %d < 1", iters);
-  if (o.precision != KM_FP32 && o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
+  if (o.precision != KM_FP32 && o.precision != KM_BF16 && o.precision != KM_FP8E4M3 && o.precision != KM_BF16X3)
     return fail(KM_EINVAL, "unknown precision %d", o.precision);
   if (o.precision != KM_FP32 && tc_shape(o.precision, p.d, p.k).stages < 2)
     return fail(KM_EUNSUPPORTED, "d = %d, k = %d do not fit the tensor-core tile pipeline (k is staged in shared memory)",
@@ -423,7 +433,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   const TcShape& t = cold ? cfg.t0 : cfg.t;
   if ((e = cudaMemsetAsync(w.ctl, 0, kCtlIterBytes, s))) return e;
   if ((e = at(0))) return e;
-  if (tcp) e = launch_quant_c(p, w, t.fp8, t.kp, t.Kp, w.Cq, w.hq, w.scq, s);
+  if (tcp) e = launch_quant_c(p, w, t.qmode(), t.kp, t.Kp, w.Cq, w.hq, w.scq, s);
   else e = launch_prep(p, w, s);
   if (e) return e;
   if ((e = at(1))) return e;
@@ -447,7 +457,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   if ((e = at(5))) return e;
   if ((e = launch_scatter(p, w, s))) return e;
   if ((e = at(6))) return e;
-  if ((e = launch_segsum(p, w, s, tcp ? (cfg.t.fp8 ? 2 : 1) : 0, tcp ? cfg.t.Kp : 0))) return e;
+  if ((e = launch_segsum(p, w, s, tcp ? cfg.t.qmode() + 1 : 0, tcp ? cfg.t.Kp : 0))) return e;
   if ((e = at(7))) return e;
   if ((e = launch_divide(p, w, first ? 0 : 1, tol, s))) return e;
   if ((e = at(8))) return e;
@@ -537,8 +547,8 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     t = tc_shape(precision, p.d, p.k);
     Lc.fp8 = t.fp8;
     int r2;
-    if ((r2 = encode_codes_map(&Lc.mapX, w.Xq, p.n, t.Kp, t.esz, 128))) return r2;
-    if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kp, t.esz, t.bn))) return r2;
+    if ((r2 = encode_codes_map(&Lc.mapX, w.Xq, p.n, t.Kw, t.esz, 128))) return r2;
+    if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kw, t.esz, t.bn))) return r2;
     memset(&P, 0, sizeof P);
     P.h = w.hq;
     P.sc = w.scq;
@@ -561,8 +571,14 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     P.stages = t.stages;
     P.abufs = t.abufs;
     P.idesc = tc::idesc_f32acc(t.fp8 ? 0u : 1u, 128, (uint32_t)t.bn);
-    const double K = t.Kp;
-    P.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));  // truncating FP32 accumulation
+    P.split = t.split;
+    // truncating FP32 accumulation of K products; the two-part codes sum 3 Kp
+    // products and drop lo.lo, |x_lo . c_lo| <= u^2 (1 + u)^2 ||x_hi|| ||c_hi||
+    // (u = 2^-8, split_bf16 keeps |lo| <= u (1 + u) |hi| per element)
+    const double K = t.split ? 3.0 * t.Kp : t.Kp;
+    double gam = K * 0x1p-23 / (1.0 - K * 0x1p-23);
+    if (t.split) gam += 0x1p-16 * (1.0 + 0x1p-8) * (1.0 + 0x1p-8);
+    P.gam_tc = (float)(gam * (1.0 + 1e-6));
     P.wait_ns = 2000000000ull;
     if (getenv("KM_DEBUG_STALL")) {  // test knob: make a bounded wait expire (50 ms)
       P.debug_stall = 1;
@@ -587,7 +603,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
   KM_TRACE("prologue copies queued\n");
   if (o.precision != KM_FP32 && cfg.cold) KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
-  else if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.fp8, cfg.t.Kp, w.Xq, w.xs, s));
+  else if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.qmode(), cfg.t.Kp, w.Xq, w.xs, s));
   else KM_CUDA(launch_xnorm(p, w, s));
   if (debug_sync()) {
     cudaError_t r = cudaStreamSynchronize(s);
@@ -1306,7 +1322,7 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
   if (!inst || count < 1) return fail(KM_EINVAL, "need count >= 1 instances");
   if (iters < 1) return fail(KM_EINVAL, "iters = %d < 1", iters);
   if (o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
-    return fail(o.precision == KM_FP32 ? KM_EUNSUPPORTED : KM_EINVAL,
+    return fail(o.precision == KM_FP32 || o.precision == KM_BF16X3 ? KM_EUNSUPPORTED : KM_EINVAL,
                 "batched runs use the tensor-core path: precision must be KM_BF16 or KM_FP8E4M3");
   for (int b = 0; b < count; ++b) {
     const km_instance& s = inst[b];

@@ -391,11 +391,15 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       bool ok = true;
       Item it;
       it.b = -1;
+      int labn = -2;                   // label of the next pair's first row, loaded a pair ahead (-2: not loaded)
       for (int64_t ga = tr.t0; ga < tr.t1 && ok;) {
-        if (seek<BATCH>(P, &mapX, &mapC, ga, it) && BATCH && !it.skip) {
-          // tensor maps in global memory: order the host's writes before the async proxy reads them
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
-          asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
+        if (seek<BATCH>(P, &mapX, &mapC, ga, it)) {
+          labn = -2;
+          if (BATCH && !it.skip) {
+            // tensor maps in global memory: order the host's writes before the async proxy reads them
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapX) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(it.mapC) : "memory");
+          }
         }
         if (it.skip) {
           ga += tr.ts;
@@ -404,7 +408,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int64_t gb = ga + tr.ts;
         const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
         const int64_t tile0 = ga - it.tile0;
-        const int c0 = first_chunk(tile_label(P, it, tile0), it, BN);
+        const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile0), it, BN);
+        {
+          const int64_t gn = ntp == 2 ? gb + tr.ts : gb;
+          labn = (gn < tr.t1 && gn < it.tend) ? tile_label(P, it, gn - it.tile0) : -2;
+        }
         for (int u = 0; u < ntp && ok; ++u, ++lt) {
           const int ab = lt % nab;
           if (!mbar_wait(&a_empty[ab], ((lt / nab) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
@@ -441,6 +449,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       int lt = 0, gc = 0;
       int gu[2] = {0, 0};  // chunks issued per epilogue group
       bool ok = true, issued = false;
+      const bool split = !BATCH && !FP8 && P.split;
       Item it;
       it.b = -1;
       for (int64_t ga = tr.t0; ga < tr.t1 && ok;) {
@@ -469,13 +478,18 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             tc_fence_after_sync();
             const uint32_t a_addr = smem_u32(A0 + abs_[u] * a_bytes);
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
-            for (int kb = 0; kb < it.nkb; ++kb) {
+            // K blocks of one product; two-part codes take three: (hi, hi), (lo, hi), (hi, lo)
+            const int mk = split ? it.nkb >> 1 : it.nkb;
+            for (int seg = 0; seg < (split ? 3 : 1); ++seg) {
+              const int ka = seg == 1 ? mk : 0, kc = seg == 2 ? mk : 0;
+              for (int kb = 0; kb < mk; ++kb) {
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk) {
-                const uint64_t ad = sdesc_k_sw128(a_addr + kb * (BM * ROWB) + kk * 32);
-                const uint64_t bd = sdesc_k_sw128(b_addr + kb * b_kblk + kk * 32);
-                if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
-                else mma_bf16(d_tmem, ad, bd, P.idesc, (kb | kk) != 0);
+                for (int kk = 0; kk < 4; ++kk) {
+                  const uint64_t ad = sdesc_k_sw128(a_addr + (ka + kb) * (BM * ROWB) + kk * 32);
+                  const uint64_t bd = sdesc_k_sw128(b_addr + (kc + kb) * b_kblk + kk * 32);
+                  if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
+                  else mma_bf16(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
+                }
               }
             }
             issued = true;
@@ -514,12 +528,14 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     float csc = 1.f;                                      // the instance's centroid code scale (E4M3)
     RowMeta nxt;
     bool have_nxt = false;
+    int labn = -2;  // label of the next pair's first row, loaded a pair ahead (-2: not loaded)
     // Every epilogue warp walks every pair to the end, even after a timeout
     // (then skipping waits and work), so that all of them reach the named
     // barrier of the batched h staging the same number of times.
     for (int64_t ga = tr.t0; ga < tr.t1;) {
       if (seek<BATCH>(P, &mapX, &mapC, ga, it)) {
         have_nxt = false;
+        labn = -2;
         if (BATCH && !it.skip) {
           // this instance's h_j (and scales) into shared memory
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
@@ -543,12 +559,14 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
       const int64_t ga_next = ntp == 2 ? gb + tr.ts : gb;
       const int64_t tile0 = ga - it.tile0;
+      const int lab = labn != -2 ? labn : tile_label(P, it, tile0);
+      labn = (ga_next < tr.t1 && ga_next < it.tend) ? tile_label(P, it, ga_next - it.tile0) : -2;
       if (grp >= ntp) {  // no tile for this group in this pair
         ga = ga_next;
         continue;
       }
       const int64_t tile = grp ? gb - it.tile0 : tile0;
-      const int c0 = first_chunk(tile_label(P, it, tile0), it, BN);
+      const int c0 = first_chunk(lab, it, BN);
       const RowMeta m = have_nxt ? nxt : fetch_meta<BATCH>(P, it, tile, r);
       // this group's tile of the next pair, when it belongs to the same instance: its loads overlap this tile
       {

@@ -116,7 +116,9 @@ struct TcParams {
   int64_t n;
   int k, Kp, nkb, bn, nchunks, stages, abufs, first;
   uint32_t idesc;
-  float gam_tc;       // accumulation bound of the tensor-core sum over Kp terms
+  int split;          // two-part BF16 codes: a row holds nkb / 2 blocks of hi, then as many of lo;
+                      // x.c = hi.hi + lo.hi + hi.lo (single launches only)
+  float gam_tc;       // coefficient of ||x~|| max ||c~|| in the contraction's error bound
   uint64_t wait_ns;   // bound of every mbarrier wait
   int debug_stall;    // test knob: the epilogue also waits on a barrier nothing arrives on
   unsigned long long* flag_slots;  // slot counter of the flag list
@@ -260,11 +262,11 @@ cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t init_segsum();
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
-cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uint8_t* Xq, float4* xs,
+cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
                            cudaStream_t s);
 cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
                                 cudaStream_t s);
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float* h,
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
                            float* sc, cudaStream_t s);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();

@@ -1,5 +1,8 @@
 // Quantisation stages of the tensor-core path.
 //
+// Code modes: 0 BF16, 1 E4M3, 2 two-part BF16 (split_bf16; rows of 2 Kp
+// codes, hi then lo).
+//
 // X is quantised once per call (it does not change between iterations, Sec.
 // 3.1 code motion) and C once per step. Codes: BF16 round-to-nearest with
 // scale 1, or E4M3 round-to-nearest, saturating, of v / s with a power-of-two
@@ -51,6 +54,40 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
     if (lane == 0) {
       if (!isfinite(sxx) || !isfinite(sqq)) ctl->nonfinite = 1;
       xs[i] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+    }
+  }
+}
+
+// Two-part BF16 codes (split_bf16): row i holds hi in columns [0, Kp) and lo
+// in [Kp, 2 Kp). Statistics: (1, ||hi|| + ||lo||, ||v - hi - lo||, ||v||),
+// norms rounded up.
+__global__ void __launch_bounds__(256)
+quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
+                     float4* __restrict__ xs, Ctl* ctl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const float* x = X + i * d;
+    float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f;
+    __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
+    for (int t = lane; t < Kp; t += 32) {
+      const float v = t < d ? x[t] : 0.f;
+      float hi, lo;
+      const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
+      sxx = fmaf(v, v, sxx);
+      shh = fmaf(hi, hi, shh);
+      sll = fmaf(lo, lo, sll);
+      sdd = fmaf(r, r, sdd);
+    }
+    sxx = warp_sum(sxx);
+    shh = warp_sum(shh);
+    sll = warp_sum(sll);
+    sdd = warp_sum(sdd);
+    if (lane == 0) {
+      if (!isfinite(sxx) || !isfinite(shh)) ctl->nonfinite = 1;
+      xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)), norm_bound(sdd, d),
+                          norm_bound(sxx, d));
     }
   }
 }
@@ -107,19 +144,23 @@ __global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C,
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomic_max_nonneg(&ctl->camax_bits, m);
 }
 
-template <int FP8>
+// MODE 0: BF16, 1: E4M3, 2: two-part BF16 (hi in columns [0, Kp), lo in
+// [Kp, 2 Kp); the code norm statistic is ||hi|| + ||lo||).
+template <int MODE>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
                float* __restrict__ hq, float* __restrict__ scq, int32_t* __restrict__ counts, Ctl* ctl) {
+  constexpr int FP8 = MODE == 1;
   constexpr int ESZ = FP8 ? 1 : 2;
+  constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
   if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int j = warp; j < kp; j += nwarps) {
-    uint8_t* row = Cq + (int64_t)j * Kp * ESZ;
+    uint8_t* row = Cq + (int64_t)j * W * Kp * ESZ;
     if (j >= k) {  // padding centroid: zero codes, score +inf
-      for (int t = lane; t < Kp * ESZ; t += 32) row[t] = 0;
+      for (int t = lane; t < W * Kp * ESZ; t += 32) row[t] = 0;
       if (lane == 0) {
         hq[j] = INFINITY;
         scq[j] = 1.f;
@@ -133,20 +174,31 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     const float sc = FP8 ? pow2_scale(__uint_as_float(ctl->camax_bits)) : 1.f;  // one scale for all centroids
     const float inv = FP8 ? pow2_inv(sc) : 1.f;
-    float sqq = 0.f, sdd = 0.f;
+    float sqq = 0.f, sll = 0.f, sdd = 0.f;
     for (int t = lane; t < Kp; t += 32) {
       const float v = t < d ? c[t] : 0.f;
-      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
-      const float r = vq - v;
-      sqq = fmaf(vq, vq, sqq);
-      sdd = fmaf(r, r, sdd);
+      if constexpr (MODE == 2) {
+        __nv_bfloat16* r16 = reinterpret_cast<__nv_bfloat16*>(row);
+        float hi, lo;
+        const float r = split_bf16(v, r16 + t, r16 + Kp + t, hi, lo);
+        sqq = fmaf(hi, hi, sqq);
+        sll = fmaf(lo, lo, sll);
+        sdd = fmaf(r, r, sdd);
+      } else {
+        const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
+        const float r = vq - v;
+        sqq = fmaf(vq, vq, sqq);
+        sdd = fmaf(r, r, sdd);
+      }
     }
     sqq = warp_sum(sqq);
+    if (MODE == 2) sll = warp_sum(sll);
     sdd = warp_sum(sdd);
     if (lane == 0) {
       const float h = __double2float_rn(0.5 * s2);
       const float cn = __double2float_ru(sqrt(s2) * (1.0 + 1e-13));
-      const float qn = norm_bound(sqq, d), dn = norm_bound(sdd, d);
+      const float qn = MODE == 2 ? __fadd_ru(norm_bound(sqq, d), norm_bound(sll, d)) : norm_bound(sqq, d);
+      const float dn = norm_bound(sdd, d);
       if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
       hq[j] = h;
       scq[j] = sc;
@@ -161,12 +213,13 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
 
 }  // namespace
 
-cudaError_t launch_quant_x(const Problem& p, const Work& w, int fp8, int Kp, uint8_t* Xq, float4* xs,
+cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
                            cudaStream_t s) {
   int64_t blocks = (p.n + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
-  if (fp8) quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
+  if (mode == 2) quant_x_split_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
+  else if (mode == 1) quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
   else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
   return cudaGetLastError();
 }
@@ -180,12 +233,14 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int fp8, int kp, int Kp, uint8_t* Cq, float* h,
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
                            float* sc, cudaStream_t s) {
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (fp8) {
+  if (mode == 2) {
+    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+  } else if (mode == 1) {
     const int64_t kd = (int64_t)p.k * p.d;
     int mb = (int)((kd + 255) / 256);
     if (mb > num_sms() * 4) mb = num_sms() * 4;

@@ -35,6 +35,28 @@ static __device__ __forceinline__ float quantise(float v, float sc, float inv, u
   }
 }
 
+// Two-part BF16 split of v: hi = RN(v), lo = RN(v - hi), stored at hi_dst and
+// lo_dst. v - hi and v - hi - lo are exact in FP32 (each operand pair is
+// within a factor of two, Sterbenz). lo is kept only while |lo| <= u (1 + u)
+// |hi| with u = 2^-8, which holds for every normal hi; otherwise (subnormal
+// hi) lo = 0 and the residual carries the difference. Returns the residual
+// v - hi - lo; hi and lo come back as floats.
+static __device__ __forceinline__ float split_bf16(float v, __nv_bfloat16* hi_dst, __nv_bfloat16* lo_dst, float& hi,
+                                                   float& lo) {
+  const __nv_bfloat16 qh = __float2bfloat16_rn(v);
+  hi = __bfloat162float(qh);
+  const float r1 = v - hi;
+  __nv_bfloat16 ql = __float2bfloat16_rn(r1);
+  lo = __bfloat162float(ql);
+  if (!(fabsf(lo) <= fabsf(hi) * (0x1p-8f + 0x1p-16f))) {  // exact product: a power-of-two sum times hi
+    ql = __float2bfloat16_rn(0.f);
+    lo = 0.f;
+  }
+  *hi_dst = qh;
+  *lo_dst = ql;
+  return r1 - lo;
+}
+
 static __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -189,10 +189,11 @@ __host__ __device__ constexpr size_t seg_smem_bytes() {
   return (size_t)8 * 2 * seg_rows<V>() * 32 * V * sizeof(float);  // 8 warps x 2 stages x rows x 32V floats
 }
 
-// QM = 1 / 2: the pass also writes the BF16 / E4M3 codes of each row it reads
-// at its sorted position p (row stride Kp elements), using the row scale in xs,
-// and the row statistics xs at p; the codes equal those the quantisation stage
-// produces for the same point.
+// QM = 1 / 2 / 3: the pass also writes the BF16 / E4M3 / two-part BF16 codes
+// of each row it reads at its sorted position p (row stride Kp elements, 2 Kp
+// for the two-part codes), using the row scale in xs, and the row statistics
+// xs at p; the codes equal those the quantisation stage produces for the same
+// point.
 template <int V, int QM>
 __global__ void __launch_bounds__(256, 2)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
@@ -281,6 +282,14 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
           for (int v = 0; v < V; ++v) {
             const int t = v * 32 + lane;
             if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+          }
+        } else if constexpr (QM == 3) {
+          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * 2 * Kp;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            float hi, lo;
+            if (t < d) split_bf16(xr[v], row + t, row + Kp + t, hi, lo);
           }
         } else {
           const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
@@ -404,6 +413,7 @@ cudaError_t seg_attrs() {
   cudaError_t e = seg_attr<V, 0>();
   if (e == cudaSuccess) e = seg_attr<V, 1>();
   if (e == cudaSuccess) e = seg_attr<V, 2>();
+  if (e == cudaSuccess) e = seg_attr<V, 3>();
   return e;
 }
 
@@ -433,6 +443,10 @@ cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int q
                                                                         w.xs_sorted);                             \
     else if (qmode == 2)                                                                                          \
       segsum_kernel<v, 2><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
+                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
+                                                                        w.xs_sorted);                             \
+    else if (qmode == 3)                                                                                          \
+      segsum_kernel<v, 3><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
                                                                         w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
                                                                         w.xs_sorted);                             \
     else                                                                                                          \

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libkmeans.so")
 KM_OK, KM_EINVAL, KM_ECUDA, KM_ENOMEM, KM_EUNSUPPORTED, KM_ETIMEOUT, KM_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "KM_OK", -1: "KM_EINVAL", -2: "KM_ECUDA", -3: "KM_ENOMEM", -4: "KM_EUNSUPPORTED",
                 -5: "KM_ETIMEOUT", -6: "KM_ENONFINITE"}
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16x3": 3}
 STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
 
 #: Entry points declared in include/kmeans.h (checked by the ABI test).

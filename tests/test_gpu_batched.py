@@ -132,3 +132,6 @@ def test_batched_errors(km):
     with pytest.raises(km.KMeansError) as e:
         km.run_batched([(X, C, a, s, c)], 1, precision="fp32")
     assert e.value.status == km.KM_EUNSUPPORTED
+    with pytest.raises(km.KMeansError) as e:
+        km.run_batched([(X, C, a, s, c)], 1, precision="bf16x3")
+    assert e.value.status == km.KM_EUNSUPPORTED

@@ -250,14 +250,14 @@ def test_full_size_fp32_workload(km, ref):
 
 # ----------------------------------------------------------------------------- tensor-core path
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
 def test_tc_smoke(km, ref, precision):
     X = synth.mixture(5, 1000, 16, 8, 10.0, 1.0)
     near, stats = gpu_steps(km, ref, X, X[:8].copy(), 2, precision=precision)
     assert near <= 2
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
 @pytest.mark.parametrize("n,d,k", [
     (1, 1, 1), (5, 3, 5), (129, 2, 128), (4099, 33, 130), (2000, 17, 129), (3000, 256, 20),
     (1500, 255, 300), (20037, 64, 256), (513, 96, 511), (700, 128, 700), (3333, 200, 1000),
@@ -268,7 +268,7 @@ def test_tc_shapes_ragged(km, ref, precision, n, d, k):
     assert near <= max(2, n // 1000)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
 def test_tc_precision_workload_sample(km, ref, precision):
     """The first 65,536 points of the 4M x 128 x 1024 workload, 3 teacher-forced steps."""
     w = WORKLOADS["prec_n4M_d128_k1024"]
@@ -276,6 +276,23 @@ def test_tc_precision_workload_sample(km, ref, precision):
     near, stats = gpu_steps(km, ref, X, C0, 3, precision=precision)
     assert near <= 20
     assert all(s["n_flagged"] < 65536 for s in stats)
+
+
+def test_split_bf16_margin_is_tighter(km, ref):
+    """Two-part BF16 codes shrink the near-tie margin by about 2^-8 against BF16 (the
+    residual terms drop from 2^-9 ||x|| ||c|| to the accumulation bound), so far fewer
+    points are flagged on the same step; both assignments are exact."""
+    w = WORKLOADS["prec_n4M_d128_k1024"]
+    X, C0 = synth.workload_data(w, rows=65536)
+    Xd = torch.from_numpy(X).to(DEV)
+    flagged = {}
+    for precision in ("bf16", "bf16x3"):
+        Cd = torch.from_numpy(C0).to(DEV)
+        out = km.step(Xd, Cd, precision=precision)
+        parity.check_assign(ref, X, C0.astype(np.float64), out.assign.cpu().numpy())
+        flagged[precision] = out.stats["n_flagged"]
+    assert flagged["bf16"] > 1000
+    assert flagged["bf16x3"] * 10 <= flagged["bf16"], flagged
 
 
 @pytest.mark.slow
@@ -309,7 +326,7 @@ def _full_size_tc(km, ref, w, precision, sample):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
 def test_full_size_precision_workload(km, ref, precision):
     _full_size_tc(km, ref, WORKLOADS["prec_n4M_d128_k1024"], precision, 8192)
 
@@ -319,7 +336,7 @@ def test_full_size_large_workload(km, ref):
     _full_size_tc(km, ref, WORKLOADS["large_n8M_d256_k8192"], "fp8", 8192)  # sample >= k (oracle precondition)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
 def test_tc_run_matches_free_running_oracle(km, ref, precision):
     """Graph-captured runs (seeded from the second step on) against the free-running oracle."""
     X = synth.mixture(77, 30000, 48, 40, 8.0, 1.0)
@@ -337,7 +354,7 @@ def test_tc_run_matches_free_running_oracle(km, ref, precision):
 def test_warm_start_ignores_bad_labels(km, ref):
     X = synth.mixture(8, 3000, 24, 12, 6.0, 1.0)
     Xd = torch.from_numpy(X).to(DEV)
-    for precision in ("fp32", "bf16", "fp8"):
+    for precision in ("fp32", "bf16", "fp8", "bf16x3"):
         Cd = torch.from_numpy(X[:12].copy()).to(DEV)
         a, s, c = km.alloc_outputs(Xd, Cd)
         a.copy_(torch.randint(-5, 20, (3000,), dtype=torch.int32))  # garbage, some out of range
@@ -355,7 +372,7 @@ def test_tc_recheck_off_still_runs(km):
     assert a.min() >= 0 and a.max() < 20 and out.counts.sum().item() == 5000
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8", "bf16x3"])
 def test_profiled_runs(km, ref, precision):
     """opts.profile records stage events inside the captured graph; results are unchanged."""
     X = synth.mixture(21, 20000, 64, 50, 8.0, 1.0)
