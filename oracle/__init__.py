@@ -59,6 +59,12 @@ def bind(path: str):
     lib.kmref_gda.argtypes = [vp, i64, i32, vp, i32, vp, vp, vp]
     lib.kmref_nb.restype = ctypes.c_int
     lib.kmref_nb.argtypes = [vp, i64, i32, vp, i32, vp, vp]
+    lib.spaderef_densities.restype = ctypes.c_int
+    lib.spaderef_densities.argtypes = [vp, i64, i32, dbl, dbl, i32, vp, vp, vp]
+    lib.spaderef_count.restype = i64
+    lib.spaderef_count.argtypes = [vp, i64, i32, i64, dbl]
+    lib.spaderef_cover.restype = ctypes.c_int
+    lib.spaderef_cover.argtypes = [vp, i64, i32, i64, dbl, vp, vp, vp]
     return lib
 
 
@@ -198,6 +204,44 @@ class Oracle:
         return prior, theta
 
 
+    # ---------------------------------------------------------------- SPADE downsampling
+
+    def spade(self, X, apprx: float, kernel: float, policy: int = 0):
+        """(densities int32[n], counts int32[n] (-1 for skipped rows), processed uint8[n]):
+        the downsampling loop of Sec. 4.1 run sequentially (policy 0: generated code, 1: C++ snippet)."""
+        X = _f32(X)
+        n, d = X.shape
+        dens = np.empty(n, np.int32)
+        counts = np.empty(n, np.int32)
+        proc = np.empty(n, np.uint8)
+        rc = self.lib.spaderef_densities(_ptr(X), n, d, float(apprx), float(kernel), int(policy), _ptr(dens),
+                                         _ptr(counts), _ptr(proc))
+        if rc:
+            raise ValueError(f"spaderef_densities failed ({rc})")
+        return dens, counts, proc
+
+    def spade_count(self, X, i: int, width: float) -> int:
+        """#{j : D(i, j) < width} with the FP64 L1 distance."""
+        X = _f32(X)
+        n, d = X.shape
+        c = int(self.lib.spaderef_count(_ptr(X), n, d, int(i), float(width)))
+        if c < 0:
+            raise ValueError("spaderef_count failed")
+        return c
+
+    def spade_cover(self, X, i: int, apprx: float, processed):
+        """(first, last): lowest and highest processed row within apprx of row i (-1: none)."""
+        X = _f32(X)
+        n, d = X.shape
+        p = np.ascontiguousarray(processed, dtype=np.uint8)
+        first, last = ctypes.c_int64(), ctypes.c_int64()
+        rc = self.lib.spaderef_cover(_ptr(X), n, d, int(i), float(apprx), _ptr(p), ctypes.byref(first),
+                                     ctypes.byref(last))
+        if rc:
+            raise ValueError("spaderef_cover failed")
+        return first.value, last.value
+
+
 _default = None
 
 
@@ -206,3 +250,4 @@ def oracle() -> Oracle:
     if _default is None:
         _default = Oracle()
     return _default
+

@@ -1,5 +1,6 @@
 /*
- * kmref -- plain FP64 CPU oracle of one Lloyd k-means iteration.
+ * kmref -- plain FP64 CPU oracle of one Lloyd k-means iteration (and of the
+ * keyed-reduce training and SPADE downsampling sections at the end).
  *
  * TEST INFRASTRUCTURE ONLY. It exists so that tests (and the benchmark's CPU
  * baseline leg) can check the GPU library against an obviously correct
@@ -291,4 +292,104 @@ int kmref_nb(const float* X, int64_t n, int32_t d, const int32_t* y, int32_t ncl
   }
   free(counts);
   return rc;
+}
+
+/* ------------------------------------------------------------------------
+ * SPADE density downsampling (Sec. 4.1, "Downsampling in Bioinformatics").
+ *
+ * The paper's loop over the rows of a distance Stream: a row whose density is
+ * still 0 is evaluated, i.e. its distances to every row are formed, the rows
+ * within apprx_width are found and the rows within kernel_width are counted
+ * (find and count fused into one pass), and every found row's density is set
+ * to that count; rows with a density already set are skipped. Distances are
+ * L1 in FP64 (the generated code's inner loop: difference, absolute value,
+ * running sum over the columns in order; the Stream holds Doubles).
+ *
+ * Readings (each also listed in the design notes):
+ *   - order: the loop runs as if sequentially over i = 0..n-1 (the C++
+ *     snippet's OpenMP loop races on the skip test; its sequential reading is
+ *     the one the generated code has);
+ *   - policy 0 (the generated OptiML code): c = #{j : D(i,j) < kernel_width},
+ *     and the bulk update overwrites every found row's density;
+ *   - policy 1 (the C++ snippet): c also counts D < apprx_width (its else-if),
+ *     a found row's density is set only while it is still 0 (the
+ *     compare-and-swap), and the row's own density is set to c.
+ * ------------------------------------------------------------------------ */
+
+/* D(i, j): the generated code's L1 loop in FP64, columns in increasing order. */
+static double l1dist(const float* x, const float* y, int32_t d) {
+  double s = 0.0;
+  for (int32_t t = 0; t < d; ++t) s += fabs((double)x[t] - (double)y[t]);
+  return s;
+}
+
+/* #{j : D(i, j) < width} over all n rows (row i itself included). */
+int64_t spaderef_count(const float* X, int64_t n, int32_t d, int64_t i, double width) {
+  if (!X || n < 1 || d < 1 || i < 0 || i >= n) return -1;
+  const float* xi = X + i * (int64_t)d;
+  int64_t c = 0;
+#pragma omp parallel for reduction(+ : c) schedule(static)
+  for (int64_t j = 0; j < n; ++j) c += l1dist(xi, X + j * (int64_t)d, d) < width;
+  return c;
+}
+
+/* The downsampling loop. dens[n]: the final densities. counts[n]: c of every
+ * evaluated row, -1 for skipped rows. processed[n]: 1 for evaluated rows.
+ * Requires apprx_width > 0 and kernel_width > 0 (every evaluated row then
+ * finds itself, so its density becomes nonzero). */
+int spaderef_densities(const float* X, int64_t n, int32_t d, double apprx, double kernel, int32_t policy,
+                       int32_t* dens, int32_t* counts, uint8_t* processed) {
+  if (!X || !dens || !counts || !processed || n < 1 || d < 1 || !(apprx > 0.0) || !(kernel > 0.0) ||
+      (policy != 0 && policy != 1))
+    return -1;
+  uint8_t* found = (uint8_t*)malloc((size_t)n);
+  if (!found) return -2;
+  for (int64_t i = 0; i < n; ++i) {
+    dens[i] = 0;
+    counts[i] = -1;
+    processed[i] = 0;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (dens[i] != 0) continue;  /* the skip test */
+    processed[i] = 1;
+    const float* xi = X + i * (int64_t)d;
+    int64_t c = 0;
+    /* one fused pass over the row: find (< apprx) and count (< kernel) */
+#pragma omp parallel for reduction(+ : c) schedule(static)
+    for (int64_t j = 0; j < n; ++j) {
+      const double D = l1dist(xi, X + j * (int64_t)d, d);
+      found[j] = D < apprx;
+      c += policy == 0 ? (D < kernel) : (D < apprx || D < kernel);
+    }
+    /* the bulk update of the found rows */
+    for (int64_t j = 0; j < n; ++j) {
+      if (!found[j]) continue;
+      if (policy == 0 || dens[j] == 0) dens[j] = (int32_t)c;
+    }
+    if (policy == 1) dens[i] = (int32_t)c;
+    counts[i] = (int32_t)c;
+  }
+  free(found);
+  return 0;
+}
+
+/* For row i and a given evaluated-row set: the lowest and highest evaluated
+ * row j with D(i, j) < apprx (-1 when there is none). Used to check a result
+ * at sizes where the whole loop is too slow to rerun. */
+int spaderef_cover(const float* X, int64_t n, int32_t d, int64_t i, double apprx, const uint8_t* processed,
+                   int64_t* first, int64_t* last) {
+  if (!X || !processed || !first || !last || n < 1 || d < 1 || i < 0 || i >= n) return -1;
+  const float* xi = X + i * (int64_t)d;
+  int64_t lo = INT64_MAX, hi = -1;
+#pragma omp parallel for reduction(min : lo) reduction(max : hi) schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    if (!processed[j]) continue;
+    if (l1dist(xi, X + j * (int64_t)d, d) < apprx) {
+      if (j < lo) lo = j;
+      if (j > hi) hi = j;
+    }
+  }
+  *first = hi < 0 ? -1 : lo;
+  *last = hi;
+  return 0;
 }

@@ -16,7 +16,7 @@ import threading
 
 import numpy as np
 
-from .workloads import WORKLOADS, Workload, batched_instances  # noqa: F401
+from .workloads import SPADE_WORKLOADS, WORKLOADS, SpadeWorkload, Workload, batched_instances  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.c")
@@ -113,3 +113,8 @@ def workload_data(w: "Workload", *, rows: int | None = None, out: np.ndarray | N
     X = mixture(w.seed, n, w.d, w.m, w.R, w.sigma, out=out)
     C0 = X[: w.k].copy() if n >= w.k else mixture(w.seed, w.k, w.d, w.m, w.R, w.sigma)
     return X, C0
+
+
+def spade_data(w: "SpadeWorkload", *, rows: int | None = None) -> np.ndarray:
+    """X rows ``[0, rows)`` of a SPADE downsampling workload."""
+    return mixture(w.seed, w.n if rows is None else rows, w.d, w.m, w.R, w.sigma)

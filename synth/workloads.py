@@ -69,3 +69,29 @@ def batched_instances(w: Workload = WORKLOADS["batched_512"]):
         out.append(Workload(f"{w.name}[{b}]", n=n, d=d, k=k, m=k, R=w.R, sigma=w.sigma,
                             iters=w.iters, precision=w.precision, seed=seed))
     return out
+
+
+@dataclass(frozen=True)
+class SpadeWorkload:
+    """SPADE downsampling input (Sec. 4.1): n rows of a Gaussian mixture (cell
+    populations) with the two widths the paper's generated code prints. The
+    paper gives neither d nor the data; sigma is chosen so that apprx_width is
+    about 1.5 x the median nearest-neighbour L1 distance of a row."""
+    name: str
+    n: int
+    d: int
+    m: int
+    R: float
+    sigma: float
+    apprx: float
+    kernel: float
+    seed: int
+    note: str = ""
+
+
+SPADE_WORKLOADS = {
+    "spade_n235k_d16": SpadeWorkload(
+        "spade_n235k_d16", n=235_000, d=16, m=40, R=10.0, sigma=0.55,
+        apprx=6.689027961, kernel=22.29675987, seed=SEED_BASE + 0x200,
+        note="row length 235,000 as in the paper's typical dataset; widths as printed in its generated code"),
+}
