@@ -241,6 +241,50 @@ int kmeans_gda_train(const km_opts* opts, const float* X, int64_t n, int32_t d,
 int kmeans_nb_train(const km_opts* opts, const float* X, int64_t n, int32_t d,
                     const int32_t* y, int32_t ncls, float* prior, float* theta);
 
+/* ------------------------------------------------------------------------
+ * SPADE density downsampling (Sec. 4.1, "Downsampling in Bioinformatics"),
+ * the paper's second fused-loop workload, on the same library.
+ *
+ * With D(i, j) = sum_t |x_it - x_jt| evaluated in FP64 (columns in increasing
+ * order) over the rows of X (n x d, FP32, row-major, DEVICE), the result is
+ * that of the paper's loop run sequentially over i = 0..n-1:
+ *   if the density of row i is still 0, row i is evaluated: its count
+ *   c = #{j : D(i, j) < kernel_width} (policy KM_SPADE_FIRST also counts
+ *   D < apprx_width, as the C++ snippet's else-if does), and every row j with
+ *   D(i, j) < apprx_width gets density c: always (KM_SPADE_LAST, the
+ *   generated code's bulk update) or only while its density is still 0
+ *   (KM_SPADE_FIRST, the snippet's compare-and-swap).
+ * Every threshold decision equals the FP64 loop's (pairs whose FP32 distance
+ * lies within the rounding bound of a width are re-evaluated in FP64).
+ *
+ * Outputs (DEVICE, caller-owned): densities int32[n]; counts int32[n] or NULL
+ * (c of every evaluated row, -1 for skipped rows); processed uint8[n] or NULL
+ * (1 for evaluated rows). stats: HOST pointer or NULL.
+ * Preconditions: 1 <= n < 2^31 - 1, 1 <= d <= 4096, apprx_width and
+ * kernel_width finite and > 0, policy KM_SPADE_LAST or KM_SPADE_FIRST
+ * (KM_EINVAL otherwise); X finite (KM_ENONFINITE otherwise). opts: only
+ * opts->stream is used (NULL = defaults); the call synchronises that stream.
+ * Workspace (about 13 n bytes + 64 MiB) is owned by the library and reused.
+ */
+typedef enum { KM_SPADE_LAST = 0, KM_SPADE_FIRST = 1 } km_spade_policy;
+
+typedef struct {
+  int64_t n_evaluated;   /* rows the loop evaluates (density still 0 when reached) */
+  int64_t n_computed;    /* rows whose distances were computed: evaluated rows plus
+                            candidates of a batch that an earlier evaluated
+                            candidate of the same batch turned out to find */
+  int64_t n_found_pairs; /* (computed row, row) pairs within apprx_width */
+  int64_t n_exact;       /* distances re-evaluated in FP64 near a width */
+  int32_t batches;       /* candidate batches */
+  int32_t overflow_batches; /* batches whose found-row list overflowed (slower path) */
+  float ms;              /* device time of the call */
+  int32_t reserved;
+} km_spade_stats;
+
+int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n, int32_t d, double apprx_width,
+                           double kernel_width, int32_t policy, int32_t* densities, int32_t* counts,
+                           uint8_t* processed, km_spade_stats* stats);
+
 /* Message of the calling thread's last failing call ("" if none). */
 const char* kmeans_last_error(void);
 

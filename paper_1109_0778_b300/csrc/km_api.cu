@@ -1,7 +1,9 @@
 // C ABI of the fused Lloyd k-means library: argument validation, the per-device
 // context and workspace, the stage sequence of one Lloyd step, graph capture of
 // multi-step runs, and statistics. Declarations and contracts: include/kmeans.h.
+#include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -86,6 +88,8 @@ struct DevCtx {
   void* stage = nullptr;  // device copies for the host-pointer entry point
   void* cls = nullptr;    // class counts and covariance accumulators of the training entry points
   size_t cls_bytes = 0;
+  void* spade = nullptr;  // downsampling state (km_spade.cu)
+  size_t spade_bytes = 0;
   size_t stage_bytes = 0;
   void* host = nullptr;   // pinned read-back of Ctl and the per-step history
   size_t host_bytes = 0;
@@ -138,6 +142,7 @@ int init_ctx(DevCtx* c) {
   KM_CUDA(init_assign_tc());
   KM_CUDA(init_segsum());
   KM_CUDA(init_batched());
+  KM_CUDA(init_spade());
   c->inited = true;
   return KM_OK;
 }
@@ -886,6 +891,152 @@ KM_API int kmeans_nb_train(const km_opts* opts, const float* X, int64_t n, int32
                      [&](const Work& w, const int32_t* counts, double*, int2*, cudaStream_t s) {
                        return launch_nb_theta(w.sums64, counts, n, d, ncls, prior, theta, w.ctl, s);
                      });
+}
+
+// ============================================================================ SPADE downsampling
+
+namespace {
+
+// Largest float <= v (lo) or smallest float >= v (hi).
+float float_below(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float float_above(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+
+}  // namespace
+
+KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n, int32_t d, double apprx_width,
+                                  double kernel_width, int32_t policy, int32_t* densities, int32_t* counts,
+                                  uint8_t* processed, km_spade_stats* stats) {
+  g_err.clear();
+  const km_opts o = resolve(opts);
+  if (!X || !densities) return fail(KM_EINVAL, "X and densities must be non-null");
+  if (n < 1 || n >= INT32_MAX) return fail(KM_EINVAL, "n = %lld outside [1, 2^31 - 1)", (long long)n);
+  if (d < 1 || d > 4096) return fail(KM_EINVAL, "d = %d outside [1, 4096]", d);
+  if (!(apprx_width > 0.0) || !std::isfinite(apprx_width) || !(kernel_width > 0.0) || !std::isfinite(kernel_width))
+    return fail(KM_EINVAL, "widths must be finite and > 0 (apprx %g, kernel %g)", apprx_width, kernel_width);
+  if (policy != KM_SPADE_LAST && policy != KM_SPADE_FIRST) return fail(KM_EINVAL, "unknown policy %d", policy);
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(KM_EUNSUPPORTED, "device index %d", dev);
+  int rc;
+  if ((rc = check_device_ptr(X, "X", dev)) || (rc = check_device_ptr(densities, "densities", dev))) return rc;
+  if (counts && (rc = check_device_ptr(counts, "counts", dev))) return rc;
+  if (processed && (rc = check_device_ptr(processed, "processed", dev))) return rc;
+  const size_t nd = (size_t)n * d * 4;
+  if (overlaps(X, nd, densities, 4 * (size_t)n) || (counts && overlaps(X, nd, counts, 4 * (size_t)n)) ||
+      (processed && overlaps(X, nd, processed, (size_t)n)))
+    return fail(KM_EINVAL, "outputs overlap X");
+  DevCtx* c = get_ctx(dev);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((rc = init_ctx(c))) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+
+  // workspace: control block, per-row state, batch state, found-row list
+  const int64_t cap = std::min<int64_t>((int64_t)8 << 20, std::max<int64_t>((int64_t)1 << 16, (int64_t)kSB * n));
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes); return at; };
+  const size_t o_ctl = take(sizeof(SpadeCtl)), o_q = take(4 * (size_t)n), o_slot = take(4 * (size_t)n),
+               o_cnt = take(4 * (size_t)n), o_proc = take((size_t)n), o_cand = take(4 * (size_t)kSB),
+               o_cc = take(4 * (size_t)kSB), o_inp = take((size_t)kSB), o_nbr = take(4 * (size_t)kSB * (kSB / 32)),
+               o_pairs = take(8 * (size_t)cap);
+  if (off > c->spade_bytes) {
+    if (c->spade) {
+      KM_CUDA(cudaDeviceSynchronize());
+      cudaFree(c->spade);
+      c->spade = nullptr;
+      c->spade_bytes = 0;
+    }
+    if (cudaMalloc(&c->spade, off) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "downsampling workspace of %zu bytes failed", off);
+    }
+    c->spade_bytes = off;
+  }
+  char* base = (char*)c->spade;
+  SpadeArgs A;
+  memset(&A, 0, sizeof A);
+  A.X = X;
+  A.n = n;
+  A.d = d;
+  A.vec = (d % 4 == 0) && ((uintptr_t)X % 16 == 0);
+  // decision bands: |D^ - D| <= gamma D (FP32 sum of d rounded terms), |D64 - D| <= g64 D
+  const double g32 = (double)(d + 2) * 0x1p-24 / (1.0 - (double)(d + 2) * 0x1p-24);
+  const double g64 = (double)(d + 2) * 0x1p-53 / (1.0 - (double)(d + 2) * 0x1p-53);
+  const double cw = policy == KM_SPADE_LAST ? kernel_width : std::max(apprx_width, kernel_width);
+  auto band = [&](double w, float& lo, float& hi) {
+    lo = float_below(w * (1.0 - g32) / (1.0 + g64) * (1.0 - 0x1p-40));
+    hi = float_above(w * (1.0 + g32) / (1.0 - g64) * (1.0 + 0x1p-40));
+  };
+  band(apprx_width, A.a_lo, A.a_hi);
+  band(cw, A.w_lo, A.w_hi);
+  A.apprx = apprx_width;
+  A.cw = cw;
+  A.policy = policy;
+  A.none = policy == KM_SPADE_LAST ? -1 : INT32_MAX;
+  A.ctl = (SpadeCtl*)(base + o_ctl);
+  A.q = (int32_t*)(base + o_q);
+  A.slot = (int32_t*)(base + o_slot);
+  A.counts = (int32_t*)(base + o_cnt);
+  A.processed = (uint8_t*)(base + o_proc);
+  A.cand = (int32_t*)(base + o_cand);
+  A.ccount = (int32_t*)(base + o_cc);
+  A.inP = (uint8_t*)(base + o_inp);
+  A.nbr = (uint32_t*)(base + o_nbr);
+  A.pairs = (int2*)(base + o_pairs);
+  A.pair_cap = cap;
+  if (sizeof(SpadeCtl) > c->host_bytes) {
+    if (c->host) cudaFreeHost(c->host);
+    c->host = nullptr;
+    c->host_bytes = 0;
+    if (cudaMallocHost(&c->host, 4096) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "pinned host allocation failed");
+    }
+    c->host_bytes = 4096;
+  }
+  SpadeCtl* hc = (SpadeCtl*)c->host;
+  KM_CUDA(cudaMemsetAsync(A.ctl, 0, sizeof(SpadeCtl), s));
+  KM_CUDA(cudaEventRecord(c->ev0, s));
+  KM_CUDA(launch_spade_init(A, s));
+  KM_CUDA(cudaMemcpyAsync(hc, A.ctl, sizeof(SpadeCtl), cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  if (hc->nonfinite) return fail(KM_ENONFINITE, "X holds a NaN or Inf");
+  // batches until one finds no candidate; every other batch settles at least one row,
+  // so at most n + 1 batches run (read back every few batches)
+  constexpr int kGroup = 4;
+  for (int64_t b = 0; b <= n + kGroup; b += kGroup) {
+    for (int g = 0; g < kGroup; ++g) KM_CUDA(launch_spade_batch(A, s));
+    KM_CUDA(cudaMemcpyAsync(hc, A.ctl, sizeof(SpadeCtl), cudaMemcpyDeviceToHost, s));
+    KM_CUDA(cudaStreamSynchronize(s));
+    if (hc->done) break;
+  }
+  if (!hc->done) return fail(KM_ECUDA, "downsampling did not settle every row");
+  KM_CUDA(launch_spade_density(A, densities, s));
+  if (counts) KM_CUDA(cudaMemcpyAsync(counts, A.counts, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  if (processed) KM_CUDA(cudaMemcpyAsync(processed, A.processed, (size_t)n, cudaMemcpyDeviceToDevice, s));
+  KM_CUDA(cudaEventRecord(c->ev1, s));
+  KM_CUDA(cudaMemcpyAsync(hc, A.ctl, sizeof(SpadeCtl), cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->n_evaluated = (int64_t)hc->n_evaluated;
+    stats->n_computed = (int64_t)hc->n_computed;
+    stats->n_found_pairs = (int64_t)hc->n_apprx;
+    stats->n_exact = (int64_t)hc->n_exact;
+    stats->batches = hc->batches;
+    stats->overflow_batches = hc->overflow_batches;
+    float ms = 0.f;
+    KM_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    stats->ms = ms;
+  }
+  return KM_OK;
 }
 
 KM_API const char* kmeans_last_error(void) { return g_err.c_str(); }

@@ -312,4 +312,51 @@ __device__ __forceinline__ bool lex_less(float a, int ia, float b, int ib) {
   return a < b || (a == b && ia < ib);
 }
 
+// ---------------------------------------------------------------- SPADE downsampling (km_spade.cu)
+
+constexpr int kSB = 1024;  // candidate rows per batch
+
+// Device control block of one downsampling call.
+struct SpadeCtl {
+  int64_t cursor;                   // rows below it are settled
+  int32_t nb;                       // candidates of the current batch
+  int32_t overflow;                 // the batch's found-row list overflowed
+  int32_t done;                     // a batch found no candidate
+  int32_t nonfinite;                // X holds a NaN / Inf
+  int32_t batches, overflow_batches;
+  unsigned long long n_pairs;       // found-row pairs listed in the current batch (may exceed the capacity)
+  unsigned long long n_exact;       // distances re-evaluated in FP64
+  unsigned long long n_computed;    // candidate rows whose distances were computed
+  unsigned long long n_evaluated;   // rows the loop evaluates
+  unsigned long long n_apprx;       // (candidate, row) pairs within apprx_width, all batches
+};
+
+struct SpadeArgs {
+  const float* X;
+  int64_t n;
+  int d;
+  int vec;                      // rows start on 16-byte boundaries (d % 4 == 0, aligned X)
+  float a_lo, a_hi, w_lo, w_hi;  // FP32 decision bands of D < apprx and D < cw
+  double apprx, cw;             // the widths (cw: the counting width of the policy)
+  int policy;                   // 0: last writer (overwrite), 1: first writer (fill if zero)
+  int32_t none;                 // writer value of a row no evaluated row has found
+  int32_t* q;                   // [n] writer of each row
+  int32_t* slot;                // [n] position in the current batch, -1 otherwise
+  int32_t* cand;                // [kSB] candidate rows
+  int32_t* ccount;              // [kSB] their counts
+  uint32_t* nbr;                // [kSB][kSB / 32] bit k' of row k: earlier candidate k' found by k
+  uint8_t* inP;                 // [kSB] evaluated by the loop
+  int2* pairs;                  // (candidate, row) pairs within apprx_width
+  int64_t pair_cap;
+  int32_t* counts;              // [n] count of each evaluated row, -1 otherwise
+  uint8_t* processed;           // [n] 1 for evaluated rows
+  SpadeCtl* ctl;
+};
+
+cudaError_t init_spade();
+size_t spade_pairs_smem();
+cudaError_t launch_spade_init(const SpadeArgs& A, cudaStream_t s);
+cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s);
+cudaError_t launch_spade_density(const SpadeArgs& A, int32_t* dens, cudaStream_t s);
+
 }  // namespace km

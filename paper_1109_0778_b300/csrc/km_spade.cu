@@ -1,0 +1,474 @@
+// SPADE density downsampling (Sec. 4.1, "Downsampling in Bioinformatics").
+//
+// The paper's loop visits the rows in order and evaluates a row only while its
+// density is still 0: one fused pass over the row's L1 distances finds the rows
+// within apprx_width and counts the rows within kernel_width, and the found
+// rows take the count as their density (so they are skipped later). The
+// evaluated rows form the greedy set P: row i is in P exactly when no earlier
+// row of P lies within apprx_width of it.
+//
+// Here the rows are evaluated in batches of up to kSB candidates, the first
+// kSB rows (from a cursor) that no evaluated row has found yet:
+//   select   one block collects the candidates in index order;
+//   pairs    a tile pass computes every candidate's distances to all n rows:
+//            its count, the rows it finds (a list), and which earlier
+//            candidates of the batch it finds (a bit matrix);
+//   resolve  one block settles, in index order, which candidates the loop
+//            evaluates: a candidate found by an evaluated earlier candidate of
+//            the batch is skipped (its row was computed speculatively);
+//   apply    every row found by an evaluated candidate records it as a writer:
+//            the highest (policy 0, the generated code's overwriting bulk
+//            update) or lowest (policy 1, the C++ snippet's fill-if-zero)
+//            index; when the list overflowed, a second tile pass over the
+//            evaluated candidates records the writers directly;
+//   finish   counts and flags of the evaluated rows, cursor bookkeeping.
+// At the end a row's density is the count of its writer.
+//
+// Distances. The FP32 sum D^ of |x_t - y_t| (d terms, each difference rounded
+// once) satisfies |D^ - D| <= gamma_d D for the exact D (u = 2^-24), and the
+// loop's FP64 distance D64 (columns in order) satisfies |D64 - D| <= g64 D.
+// So D64 < w is certain when D^ < w (1 - gamma)/(1 + g64) and impossible when
+// D^ > w (1 + gamma)/(1 - g64); in between the pair is re-evaluated in FP64
+// exactly as the loop does (same operations, same order), so every decision
+// equals the FP64 loop's.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "km_gather.cuh"
+#include "km_internal.cuh"
+
+namespace km {
+
+namespace {
+
+constexpr int kTile = 128;   // candidates x rows per tile
+constexpr int kKC = 32;      // feature columns per shared-memory stage
+constexpr int kPad = 36;     // floats per staged row (16-byte aligned, spreads banks)
+constexpr int kThreads = 256;
+constexpr int kSideFloats = kTile * kPad;
+
+// The loop's distance: FP64, columns in increasing order.
+__device__ __forceinline__ double l1_fp64(const float* __restrict__ x, const float* __restrict__ y, int d) {
+  double s = 0.0;
+  for (int t = 0; t < d; ++t) s += fabs((double)x[t] - (double)y[t]);
+  return s;
+}
+
+__device__ __forceinline__ void cp_async16_zfill(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+// Stages columns [c0, c0 + 32) of 128 rows into side (row r at side + r * kPad):
+// row r < nrows is X row rowof(r); columns past d and rows past nrows are zero.
+// 16-byte copies when every row starts on a 16-byte boundary (vec), else 4-byte.
+template <typename RowOf>
+__device__ __forceinline__ void stage_rows(float* side, const float* __restrict__ X, int d, int vec, int c0,
+                                           int nrows, RowOf rowof, int tid) {
+  if (vec) {
+#pragma unroll
+    for (int m = 0; m < (kTile * kKC / 4) / kThreads; ++m) {
+      const int p = tid + m * kThreads, r = p >> 3, c = c0 + 4 * (p & 7);
+      const bool ok = r < nrows && c < d;
+      const float* src = ok ? X + (int64_t)rowof(r) * d + c : X;
+      cp_async16_zfill(side + r * kPad + 4 * (p & 7), src, ok);
+    }
+  } else {
+#pragma unroll 4
+    for (int m = 0; m < (kTile * kKC) / kThreads; ++m) {
+      const int p = tid + m * kThreads, r = p >> 5, c = c0 + (p & 31);
+      const bool ok = r < nrows && c < d;
+      const float* src = ok ? X + (int64_t)rowof(r) * d + c : X;
+      cp_async4_zfill(side + r * kPad + (p & 31), src, ok);
+    }
+  }
+}
+
+// The slow path of one (candidate k, row j) pair whose FP32 distance D lies in
+// a decision band or below apprx_width's: FP64 re-evaluation where the band
+// requires it (nex counts them), then the found-row record (APPLY = 0: list
+// entry and in-batch bit; APPLY = 1: writer, evaluated candidates only).
+// Returns 1 when the pair adds to the candidate's count beyond D < w_lo.
+template <int APPLY>
+__device__ __noinline__ int settle_pair(const SpadeArgs& A, int k, int64_t j, float D, int& nex) {
+  if (APPLY && !A.inP[k]) return 0;
+  const int d = A.d;
+  const int32_t ci = A.cand[k];
+  int add = 0;
+  double D64 = -1.0;  // FP64 distance once evaluated
+  if (!APPLY && D >= A.w_lo && D <= A.w_hi) {
+    D64 = l1_fp64(A.X + (int64_t)ci * d, A.X + j * d, d);
+    ++nex;
+    add = D64 < A.cw ? 1 : 0;
+  }
+  bool near = D < A.a_lo;
+  if (!near && D <= A.a_hi) {
+    if (D64 < 0.0) {
+      D64 = l1_fp64(A.X + (int64_t)ci * d, A.X + j * d, d);
+      ++nex;
+    }
+    near = D64 < A.apprx;
+  }
+  if (!near) return add;
+  if (APPLY) {
+    if (A.policy == 0) atomicMax(&A.q[j], ci);
+    else atomicMin(&A.q[j], ci);
+  } else {
+    SpadeCtl* ctl = A.ctl;
+    const unsigned long long at = atomicAdd(&ctl->n_pairs, 1ull);
+    if (at < (unsigned long long)A.pair_cap) A.pairs[at] = make_int2(k, (int)j);
+    else ctl->overflow = 1;
+    const int kj = A.slot[j];
+    if (kj >= 0 && kj < k) atomicOr(&A.nbr[(size_t)k * (kSB / 32) + (kj >> 5)], 1u << (kj & 31));
+  }
+  return add;
+}
+
+// Tile pass over (candidate, row) pairs. APPLY = 0: counts, found-row list and
+// in-batch bits of every candidate. APPLY = 1 (only after a list overflow):
+// the evaluated candidates record themselves as writers of their found rows.
+template <int APPLY>
+__global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
+  extern __shared__ __align__(16) float sp_smem[];
+  __shared__ int s_cnt[kTile];
+  SpadeCtl* ctl = A.ctl;
+  const int nb = ctl->nb;
+  if (nb == 0 || (APPLY && !ctl->overflow)) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t n = A.n;
+  const int d = A.d;
+  const int nct = (nb + kTile - 1) / kTile;
+  const int64_t nrt = (n + kTile - 1) / kTile;
+  const int64_t ntiles = nct * nrt;
+  const int nkc = (d + kKC - 1) / kKC;
+  const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t nsteps = my_tiles * nkc;
+  if (nsteps == 0) return;
+
+  auto stage_step = [&](int64_t s, int buf) {
+    const int64_t t = blockIdx.x + (s / nkc) * (int64_t)gridDim.x;
+    const int c0 = (int)(s % nkc) * kKC;
+    const int ct = (int)(t / nrt);
+    const int64_t rt = t % nrt;
+    float* sa = sp_smem + (size_t)buf * 2 * kSideFloats;
+    float* sb = sa + kSideFloats;
+    const int32_t* cand = A.cand + ct * kTile;
+    stage_rows(sa, A.X, d, A.vec, c0, min(kTile, nb - ct * kTile), [&](int r) { return cand[r]; }, tid);
+    stage_rows(sb, A.X, d, A.vec, c0, (int)min((int64_t)kTile, n - rt * kTile), [&](int r) { return rt * kTile + r; },
+               tid);
+    cp_async_commit();
+  };
+
+  for (int r = tid; r < kTile; r += kThreads) s_cnt[r] = 0;
+  int cur_ct = -1;
+  float acc[8][8];
+  stage_step(0, 0);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const int buf = (int)(s & 1);
+    if (s + 1 < nsteps) {
+      stage_step(s + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const int kc = (int)(s % nkc);
+    if (kc == 0) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    }
+    {
+      const float* sa = sp_smem + (size_t)buf * 2 * kSideFloats;
+      const float* sb = sa + kSideFloats;
+      const int nq = (min(kKC, d - kc * kKC) + 3) >> 2;
+      for (int q = 0; q < nq; ++q) {
+        float4 xa[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) xa[a] = *reinterpret_cast<const float4*>(sa + (ty + 16 * a) * kPad + 4 * q);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float4 yb = *reinterpret_cast<const float4*>(sb + (tx + 16 * b) * kPad + 4 * q);
+#pragma unroll
+          for (int a = 0; a < 8; ++a) {
+            float v = acc[a][b];
+            v += fabsf(xa[a].x - yb.x);
+            v += fabsf(xa[a].y - yb.y);
+            v += fabsf(xa[a].z - yb.z);
+            v += fabsf(xa[a].w - yb.w);
+            acc[a][b] = v;
+          }
+        }
+      }
+    }
+    __syncthreads();  // the stage is consumed before it is refilled
+    if (kc != nkc - 1) continue;
+
+    // ---------------------------------------------------------------- tile epilogue
+    const int64_t t = blockIdx.x + (s / nkc) * (int64_t)gridDim.x;
+    const int ct = (int)(t / nrt);
+    const int64_t rt = t % nrt;
+    if (!APPLY && ct != cur_ct) {  // candidate counts accumulate while the candidate tile stays
+      if (cur_ct >= 0) {
+        for (int r = tid; r < kTile; r += kThreads) {
+          const int k = cur_ct * kTile + r;
+          if (k < nb && s_cnt[r]) atomicAdd(&A.ccount[k], s_cnt[r]);
+        }
+        __syncthreads();
+        for (int r = tid; r < kTile; r += kThreads) s_cnt[r] = 0;
+        __syncthreads();
+      }
+      cur_ct = ct;
+    }
+    int cnt[8];
+    bool slow = false;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      cnt[a] = 0;
+      const int k = ct * kTile + ty + 16 * a;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const int64_t j = rt * kTile + tx + 16 * b;
+        const float D = acc[a][b];
+        const bool valid = k < nb && j < n;
+        cnt[a] += (valid && D < A.w_lo) ? 1 : 0;
+        slow |= valid && (D <= A.a_hi || (D >= A.w_lo && D <= A.w_hi));
+      }
+    }
+    if (__any_sync(0xffffffffu, slow) && slow) {
+      int nex = 0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const int k = ct * kTile + ty + 16 * a;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int64_t j = rt * kTile + tx + 16 * b;
+          const float D = acc[a][b];
+          if (k < nb && j < n && (D <= A.a_hi || (!APPLY && D >= A.w_lo && D <= A.w_hi)))
+            cnt[a] += settle_pair<APPLY>(A, k, j, D, nex);
+        }
+      }
+      if (nex) atomicAdd(&ctl->n_exact, (unsigned long long)nex);
+    }
+    if (!APPLY) {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        int v = cnt[a];
+#pragma unroll
+        for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (tx == 0) s_cnt[ty + 16 * a] += v;  // one writer per candidate row
+      }
+    }
+  }
+  if (!APPLY && cur_ct >= 0) {
+    __syncthreads();
+    for (int r = tid; r < kTile; r += kThreads) {
+      const int k = cur_ct * kTile + r;
+      if (k < nb && s_cnt[r]) atomicAdd(&A.ccount[k], s_cnt[r]);
+    }
+  }
+}
+
+// Rows not yet found by any evaluated row, from the cursor, become the next
+// batch's candidates (in index order). One block of kSB threads.
+__global__ void __launch_bounds__(kSB) spade_select_kernel(SpadeArgs A) {
+  __shared__ int s_warp[kSB / 32];
+  __shared__ int s_found;
+  __shared__ int64_t s_next;
+  SpadeCtl* ctl = A.ctl;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t start = ctl->cursor;
+  if (tid == 0) {
+    s_found = 0;
+    s_next = A.n;
+  }
+  // clear the batch state
+  A.ccount[tid] = 0;
+  A.inP[tid] = 0;
+  for (int w = 0; w < kSB / 32; ++w) A.nbr[(size_t)tid * (kSB / 32) + w] = 0u;
+  __syncthreads();
+  for (int64_t base = start; base < A.n; base += kSB) {
+    const int found = s_found;
+    if (found >= kSB) break;
+    const int64_t row = base + tid;
+    const bool f = row < A.n && A.q[row] == A.none;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kSB / 32; ++w) {
+      const int c = s_warp[w];
+      before += w < warp ? c : 0;
+      total += c;
+    }
+    const int pos = found + before + __popc(bal & ((1u << lane) - 1u));
+    if (f && pos < kSB) {
+      A.cand[pos] = (int32_t)row;
+      A.slot[row] = pos;
+      if (pos == kSB - 1) s_next = row + 1;  // the batch is full: the next one starts after this row
+    }
+    __syncthreads();
+    if (tid == 0) s_found = min(kSB, found + total);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    ctl->nb = s_found;
+    ctl->cursor = s_found >= kSB ? s_next : A.n;
+    ctl->n_pairs = 0;
+    ctl->overflow = 0;
+  }
+}
+
+// Settles which candidates the loop evaluates: candidate k is evaluated exactly
+// when no evaluated candidate k' < k of the batch finds it. Rounds over the
+// batch: a candidate decides once every earlier candidate that finds it has
+// decided; the lowest undecided one always can, so at most nb rounds run.
+__global__ void __launch_bounds__(kSB) spade_resolve_kernel(SpadeArgs A) {
+  __shared__ unsigned s_in[kSB / 32], s_und[kSB / 32];
+  const int nb = A.ctl->nb;
+  if (nb == 0) return;
+  const int k = threadIdx.x, lane = k & 31, warp = k >> 5;
+  uint32_t w[kSB / 32];
+#pragma unroll
+  for (int i = 0; i < kSB / 32; ++i) w[i] = k < nb ? A.nbr[(size_t)k * (kSB / 32) + i] : 0u;
+  int st = k < nb ? 0 : 2;  // 0 undecided, 1 evaluated, 2 skipped
+  {
+    const unsigned u = __ballot_sync(0xffffffffu, st == 0);
+    if (lane == 0) {
+      s_und[warp] = u;
+      s_in[warp] = 0u;
+    }
+  }
+  __syncthreads();
+  for (int round = 0; round <= kSB; ++round) {
+    if (st == 0) {
+      uint32_t any_in = 0, any_und = 0;
+#pragma unroll
+      for (int i = 0; i < kSB / 32; ++i) {
+        any_in |= w[i] & s_in[i];
+        any_und |= w[i] & s_und[i];
+      }
+      if (any_in) st = 2;
+      else if (!any_und) st = 1;
+    }
+    __syncthreads();
+    const unsigned bi = __ballot_sync(0xffffffffu, st == 1), bu = __ballot_sync(0xffffffffu, st == 0);
+    if (lane == 0) {
+      s_in[warp] = bi;
+      s_und[warp] = bu;
+    }
+    if (!__syncthreads_or(st == 0)) break;
+  }
+  if (k < nb) A.inP[k] = st == 1;
+}
+
+// Every row found by an evaluated candidate records it as a writer.
+__global__ void __launch_bounds__(256) spade_apply_kernel(SpadeArgs A) {
+  const SpadeCtl* ctl = A.ctl;
+  if (ctl->nb == 0 || ctl->overflow) return;
+  const int64_t np = (int64_t)min(ctl->n_pairs, (unsigned long long)A.pair_cap);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < np; e += (int64_t)gridDim.x * blockDim.x) {
+    const int2 p = A.pairs[e];
+    if (!A.inP[p.x]) continue;
+    const int32_t ci = A.cand[p.x];
+    if (A.policy == 0) atomicMax(&A.q[p.y], ci);
+    else atomicMin(&A.q[p.y], ci);
+  }
+}
+
+// Counts and flags of the evaluated candidates; releases the batch slots.
+__global__ void __launch_bounds__(kSB) spade_finish_kernel(SpadeArgs A) {
+  SpadeCtl* ctl = A.ctl;
+  const int nb = ctl->nb, k = threadIdx.x;
+  const bool ev = k < nb && A.inP[k];
+  if (k < nb) {
+    const int32_t r = A.cand[k];
+    A.slot[r] = -1;
+    if (ev) {
+      A.processed[r] = 1;
+      A.counts[r] = A.ccount[k];
+    }
+  }
+  const int nev = __syncthreads_count(ev);
+  if (k == 0) {
+    ctl->n_computed += (unsigned long long)nb;
+    ctl->n_evaluated += (unsigned long long)nev;
+    ctl->n_apprx += ctl->n_pairs;
+    ctl->overflow_batches += ctl->overflow ? 1 : 0;
+    ctl->batches += nb > 0 ? 1 : 0;
+    if (nb == 0) ctl->done = 1;
+  }
+}
+
+__global__ void __launch_bounds__(256) spade_init_kernel(SpadeArgs A) {
+  const int64_t nd = A.n * (int64_t)A.d;
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nd; e += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(A.X[e]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) A.ctl->nonfinite = 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+    A.q[i] = A.none;
+    A.slot[i] = -1;
+    A.counts[i] = -1;
+    A.processed[i] = 0;
+  }
+}
+
+// densities[i] = count of row i's writer.
+__global__ void __launch_bounds__(256) spade_density_kernel(SpadeArgs A, int32_t* __restrict__ dens) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = A.q[i];
+    dens[i] = (w >= 0 && w < A.n) ? A.counts[w] : 0;
+  }
+}
+
+constexpr size_t kPairSmem = (size_t)2 * 2 * kSideFloats * sizeof(float);
+
+}  // namespace
+
+size_t spade_pairs_smem() { return kPairSmem; }
+
+cudaError_t init_spade() {
+  cudaError_t e = cudaFuncSetAttribute(spade_pairs_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPairSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spade_pairs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
+  return e;
+}
+
+cudaError_t launch_spade_init(const SpadeArgs& A, cudaStream_t s) {
+  int64_t blocks = (A.n * A.d + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  spade_init_kernel<<<(int)blocks, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s) {
+  spade_select_kernel<<<1, kSB, 0, s>>>(A);
+  const int64_t tiles = (int64_t)(kSB / kTile) * ((A.n + kTile - 1) / kTile);
+  const int grid = (int)std::min<int64_t>(tiles, 2 * (int64_t)num_sms());
+  spade_pairs_kernel<0><<<grid, kThreads, kPairSmem, s>>>(A);
+  spade_resolve_kernel<<<1, kSB, 0, s>>>(A);
+  int ab = (int)std::min<int64_t>((A.pair_cap + 255) / 256, num_sms() * 8);
+  spade_apply_kernel<<<ab, 256, 0, s>>>(A);
+  spade_pairs_kernel<1><<<grid, kThreads, kPairSmem, s>>>(A);
+  spade_finish_kernel<<<1, kSB, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spade_density(const SpadeArgs& A, int32_t* dens, cudaStream_t s) {
+  int64_t blocks = (A.n + 255) / 256;
+  if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+  spade_density_kernel<<<(int)blocks, 256, 0, s>>>(A, dens);
+  return cudaGetLastError();
+}
+
+}  // namespace km

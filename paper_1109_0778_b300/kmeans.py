@@ -23,7 +23,8 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 #: Entry points declared in include/kmeans.h (checked by the ABI test).
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
            "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc",
-           "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train")
+           "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train", "kmeans_spade_densities")
+SPADE_POLICY = {"last": 0, "first": 1}
 
 
 class KMeansError(RuntimeError):
@@ -42,6 +43,16 @@ class Instance(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("C", ctypes.c_void_p), ("assign", ctypes.c_void_p), ("sums", ctypes.c_void_p),
                 ("counts", ctypes.c_void_p)]
+
+
+class SpadeStats(ctypes.Structure):
+    _fields_ = [("n_evaluated", ctypes.c_int64), ("n_computed", ctypes.c_int64),
+                ("n_found_pairs", ctypes.c_int64), ("n_exact", ctypes.c_int64),
+                ("batches", ctypes.c_int32), ("overflow_batches", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.kmeans_gda_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, vp]
     lib.kmeans_nb_train.restype = ctypes.c_int
     lib.kmeans_nb_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp]
+    lib.kmeans_spade_densities.restype = ctypes.c_int
+    lib.kmeans_spade_densities.argtypes = [P(Opts), vp, i64, i32, dbl, dbl, i32, vp, vp, vp, P(SpadeStats)]
     return lib
 
 
@@ -284,6 +297,25 @@ def nb_train(X, y, ncls, *, stream=None):
     _check(_lib.kmeans_nb_train(ctypes.byref(o), X.data_ptr(), n, d, y.data_ptr(), int(ncls), prior.data_ptr(),
                                 theta.data_ptr()))
     return prior, theta
+
+
+def spade_densities(X, apprx_width: float, kernel_width: float, *, policy: str = "last", stream=None):
+    """kmeans_spade_densities: (densities int32 [n], counts int32 [n] (-1: skipped row),
+    processed uint8 [n], stats dict) for the rows of a CUDA float32 (n, d) tensor."""
+    import torch
+
+    if not X.is_cuda or X.dtype != torch.float32 or X.dim() != 2 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous float32 (n, d) CUDA tensor")
+    n, d = X.shape
+    dens = torch.empty(n, dtype=torch.int32, device=X.device)
+    counts = torch.empty(n, dtype=torch.int32, device=X.device)
+    proc = torch.empty(n, dtype=torch.uint8, device=X.device)
+    o = make_opts(stream=_stream_handle(stream))
+    st = SpadeStats()
+    _check(_lib.kmeans_spade_densities(ctypes.byref(o), X.data_ptr(), n, d, float(apprx_width), float(kernel_width),
+                                       SPADE_POLICY[policy], dens.data_ptr(), counts.data_ptr(), proc.data_ptr(),
+                                       ctypes.byref(st)))
+    return dens, counts, proc, st.as_dict()
 
 
 def version() -> int:
