@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
-from synth import WORKLOADS  # noqa: E402
+from synth import SPADE_WORKLOADS, WORKLOADS  # noqa: E402
 
 METRIC = "Lloyd iter/s + distance TFLOP/s: FP32 vs BF16/FP8+recheck, exact assignments"
 DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
@@ -54,7 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(TRAIN_WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + sorted(TRAIN_WORKLOADS) + sorted(SPADE_WORKLOADS))
     ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 | bf16x3 (default: the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
@@ -494,6 +495,106 @@ def run_training(args, torch, dev, dist, rank, world, local):
     return 0
 
 
+def run_spade(args, torch, dev, dist, rank, world, local):
+    """One step = one kmeans_spade_densities call (policy last: the generated code's bulk update)
+    on an HBM-resident X. Roofline: the tile passes are FP32 ALU work, one subtract and one add of
+    the absolute value per (row, row, column) element; the algorithmic elements of a pass are
+    n_evaluated x n x d (the rows the loop evaluates), timed by the library's CUDA events around
+    each tile pass."""
+    from paper_1109_0778_b300 import kmeans as km
+
+    sw = SPADE_WORKLOADS[args.workload]
+    X = synth.spade_data(sw)
+    n, d = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 0)):
+        km.spade_densities(Xd, sw.apprx, sw.kernel, stream=stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    # X (15 MB) fits in L2: every step starts from a flushed L2 (a 256 MB write outside the timed spans)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pairs_ms, stats = 0.0, None
+    with ClockSampler(local) as clk:
+        for e0, e1 in evs:
+            flush.fill_(1.0)
+            e0.record(stream)
+            _, _, _, stats = km.spade_densities(Xd, sw.apprx, sw.kernel, stream=stream)
+            e1.record(stream)
+            pairs_ms += stats["ms_pairs"]
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    clocks = clk.summary()
+    t = max_over_ranks(dist, sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3, dev)
+    value = aggregate_rate(args.steps, world, t)
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    peak = sms * 128 * mhz * 1e6 / 2 / 1e12  # element-pairs/s: 2 FP32 lane ops each
+    algo = float(stats["n_evaluated"]) * n * d
+    issued = float(stats["n_computed"]) * n * d
+    achieved = algo / (pairs_ms / args.steps / 1e3) / 1e12
+    batches = stats["batches"]
+    launched = ((batches + 1 + 3) // 4) * 4  # batches run in groups of four until one finds no candidate
+    launches = args.steps * (6 * launched + 2)
+
+    # e2e: the same call with X copied in from pinned host memory and the densities read back
+    Xh = torch.from_numpy(X).pin_memory()
+    dens_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    Xe = torch.empty_like(Xd)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        Xe.copy_(Xh, non_blocking=True)
+        dens, _, _, _ = km.spade_densities(Xe, sw.apprx, sw.kernel, stream=stream)
+        dens_h.copy_(dens, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    te = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3, dev)
+    e2e = {"value": aggregate_rate(args.steps, world, te), "unit": "pass/s", "h2d_bytes_per_step": 4 * n * d,
+           "d2h_bytes_per_step": 4 * n}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        orc = oracle.oracle()
+        cores = orc.set_threads(0)
+        rows = n // 2
+        t0 = time.perf_counter()
+        _, _, proc = orc.spade(X[:rows], sw.apprx, sw.kernel, 0)
+        el = time.perf_counter() - t0
+        rate = float(proc.sum()) * rows * d / el  # oracle element-pairs/s on the sample
+        cpu = {"value": rate / algo, "unit": "pass/s", "cores": cores, "kind": "oracle",
+               "sample": f"the oracle's loop on the first {rows} of {n} rows ({int(proc.sum())} evaluated), "
+                         f"{el:.1f} s; pass/s = its element-pair rate over the full pass's {algo:.3g} elements"}
+    if rank == 0:
+        line = {
+            "metric": "SPADE downsampling passes/s (fused L1 find + count, Sec. 4.1)", "value": value,
+            "unit": "pass/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": sw.name, "n": n, "d": d, "mixture": {"m": sw.m, "R": sw.R, "sigma": sw.sigma,
+                                                                         "seed": hex(sw.seed)},
+                       "apprx_width": sw.apprx, "kernel_width": sw.kernel, "policy": "last",
+                       "l2": f"L2 flushed before every step (256 MB write outside the timed spans); X = {4 * n * d / 1e6:.0f} MB"},
+            "stats_last_step": stats,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Telem/s",
+                         "frac": achieved / peak, "kernel": "spade_pairs (tile passes)",
+                         "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz / 2 FP32 ops per element",
+                         "issued_frac": (issued / (pairs_ms / args.steps / 1e3) / 1e12) / peak,
+                         "note": "algorithmic elements = evaluated rows x n x d; issued adds speculative rows",
+                         "traffic": None},
+            "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "peaks_source": peak_src,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -507,6 +608,8 @@ def run_ours(args):
 
     if args.workload in TRAIN_WORKLOADS:
         return run_training(args, torch, dev, dist, rank, world, local)
+    if args.workload in SPADE_WORKLOADS:
+        return run_spade(args, torch, dev, dist, rank, world, local)
     if args.workload == "batched_512":
         return run_batched(args, torch, dev, dist, rank, world, local)
     w = WORKLOADS[args.workload]

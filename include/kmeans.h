@@ -278,7 +278,7 @@ typedef struct {
   int32_t batches;       /* candidate batches */
   int32_t overflow_batches; /* batches whose found-row list overflowed (slower path) */
   float ms;              /* device time of the call */
-  int32_t reserved;
+  float ms_pairs;        /* device time of the tile passes (CUDA events around each) */
 } km_spade_stats;
 
 int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n, int32_t d, double apprx_width,

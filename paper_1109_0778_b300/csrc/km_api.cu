@@ -976,6 +976,9 @@ KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n
   };
   band(apprx_width, A.a_lo, A.a_hi);
   band(cw, A.w_lo, A.w_hi);
+  // |fl(D - w_mid)| <= w_half for every D in [w_lo, w_hi] (rounding is monotone)
+  A.w_mid = (float)(0.5 * ((double)A.w_lo + (double)A.w_hi));
+  A.w_half = float_above(std::max((double)A.w_mid - (double)A.w_lo, (double)A.w_hi - (double)A.w_mid));
   A.apprx = apprx_width;
   A.cw = cw;
   A.policy = policy;
@@ -1011,11 +1014,20 @@ KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n
   // batches until one finds no candidate; every other batch settles at least one row,
   // so at most n + 1 batches run (read back every few batches)
   constexpr int kGroup = 4;
+  int64_t launched = 0;
   for (int64_t b = 0; b <= n + kGroup; b += kGroup) {
-    for (int g = 0; g < kGroup; ++g) KM_CUDA(launch_spade_batch(A, s));
+    if ((rc = ensure_events(c, 2 * (size_t)(launched + kGroup)))) return rc;
+    for (int g = 0; g < kGroup; ++g, ++launched)
+      KM_CUDA(launch_spade_batch(A, s, c->prof[2 * launched], c->prof[2 * launched + 1]));
     KM_CUDA(cudaMemcpyAsync(hc, A.ctl, sizeof(SpadeCtl), cudaMemcpyDeviceToHost, s));
     KM_CUDA(cudaStreamSynchronize(s));
     if (hc->done) break;
+  }
+  float ms_pairs = 0.f;
+  for (int64_t b = 0; b < launched; ++b) {
+    float m = 0.f;
+    KM_CUDA(cudaEventElapsedTime(&m, c->prof[2 * b], c->prof[2 * b + 1]));
+    ms_pairs += m;
   }
   if (!hc->done) return fail(KM_ECUDA, "downsampling did not settle every row");
   KM_CUDA(launch_spade_density(A, densities, s));
@@ -1035,6 +1047,7 @@ KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n
     float ms = 0.f;
     KM_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     stats->ms = ms;
+    stats->ms_pairs = ms_pairs;
   }
   return KM_OK;
 }

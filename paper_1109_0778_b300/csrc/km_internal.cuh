@@ -337,6 +337,7 @@ struct SpadeArgs {
   int d;
   int vec;                      // rows start on 16-byte boundaries (d % 4 == 0, aligned X)
   float a_lo, a_hi, w_lo, w_hi;  // FP32 decision bands of D < apprx and D < cw
+  float w_mid, w_half;          // [w_lo, w_hi] inside [w_mid - w_half, w_mid + w_half]
   double apprx, cw;             // the widths (cw: the counting width of the policy)
   int policy;                   // 0: last writer (overwrite), 1: first writer (fill if zero)
   int32_t none;                 // writer value of a row no evaluated row has found
@@ -356,7 +357,9 @@ struct SpadeArgs {
 cudaError_t init_spade();
 size_t spade_pairs_smem();
 cudaError_t launch_spade_init(const SpadeArgs& A, cudaStream_t s);
-cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s);
+// One batch: select, tile pass (between events e0 and e1 when given), resolve, apply, finish.
+cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s, cudaEvent_t e0 = nullptr,
+                               cudaEvent_t e1 = nullptr);
 cudaError_t launch_spade_density(const SpadeArgs& A, int32_t* dens, cudaStream_t s);
 
 }  // namespace km

@@ -66,27 +66,28 @@ __device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bo
                : "memory");
 }
 
-// Stages columns [c0, c0 + 32) of 128 rows into side (row r at side + r * kPad):
-// row r < nrows is X row rowof(r); columns past d and rows past nrows are zero.
-// 16-byte copies when every row starts on a 16-byte boundary (vec), else 4-byte.
-template <typename RowOf>
-__device__ __forceinline__ void stage_rows(float* side, const float* __restrict__ X, int d, int vec, int c0,
+// Stages columns [c0, c0 + NC) of 128 rows into side (row r at side + r * rs
+// floats): row r < nrows is X row rowof(r); columns past d and rows past
+// nrows are zero. 16-byte copies when every row starts on a 16-byte boundary
+// (vec), else 4-byte. Issues the copies; the caller commits the group.
+template <int NC, typename RowOf>
+__device__ __forceinline__ void stage_cols(float* side, int rs, const float* __restrict__ X, int d, int vec, int c0,
                                            int nrows, RowOf rowof, int tid) {
   if (vec) {
 #pragma unroll
-    for (int m = 0; m < (kTile * kKC / 4) / kThreads; ++m) {
-      const int p = tid + m * kThreads, r = p >> 3, c = c0 + 4 * (p & 7);
-      const bool ok = r < nrows && c < d;
-      const float* src = ok ? X + (int64_t)rowof(r) * d + c : X;
-      cp_async16_zfill(side + r * kPad + 4 * (p & 7), src, ok);
+    for (int m = 0; m < (kTile * NC / 4) / kThreads; ++m) {
+      const int p = tid + m * kThreads, r = p / (NC / 4), c = 4 * (p % (NC / 4));
+      const bool ok = r < nrows && c0 + c < d;
+      const float* src = ok ? X + (int64_t)rowof(r) * d + c0 + c : X;
+      cp_async16_zfill(side + r * rs + c, src, ok);
     }
   } else {
 #pragma unroll 4
-    for (int m = 0; m < (kTile * kKC) / kThreads; ++m) {
-      const int p = tid + m * kThreads, r = p >> 5, c = c0 + (p & 31);
-      const bool ok = r < nrows && c < d;
-      const float* src = ok ? X + (int64_t)rowof(r) * d + c : X;
-      cp_async4_zfill(side + r * kPad + (p & 31), src, ok);
+    for (int m = 0; m < (kTile * NC) / kThreads; ++m) {
+      const int p = tid + m * kThreads, r = p / NC, c = p % NC;
+      const bool ok = r < nrows && c0 + c < d;
+      const float* src = ok ? X + (int64_t)rowof(r) * d + c0 + c : X;
+      cp_async4_zfill(side + r * rs + c, src, ok);
     }
   }
 }
@@ -131,6 +132,81 @@ __device__ __noinline__ int settle_pair(const SpadeArgs& A, int k, int64_t j, fl
   return add;
 }
 
+// The slow path of a thread's 8 x 8 pairs (candidates k0 + 16 a, rows j0 + 16 b):
+// the pairs whose D lies at or below a_hi or in the counting band go through
+// settle_pair, one at a time (D read through select trees, so acc stays in
+// registers). With count_certain the certain counts (D < w_lo) are added too
+// (tiles whose fast path did not count).
+template <int APPLY>
+__device__ __forceinline__ void slow_pairs(const SpadeArgs& A, const float (&acc)[8][8], int k0, int64_t j0, bool full,
+                                           bool count_certain, int nb, int64_t n, int (&cnt)[8], int& nex) {
+  uint32_t msk[2] = {0u, 0u};  // bit (a % 4) * 8 + b of word a / 4
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const float D = acc[a][b];
+      const bool valid = full || (k0 + 16 * a < nb && j0 + 16 * b < n);
+      if (count_certain) cnt[a] += (valid && D < A.w_lo) ? 1 : 0;
+      const bool sl = valid && (D <= A.a_hi || fabsf(D - A.w_mid) <= A.w_half);
+      msk[a >> 2] |= (sl ? 1u : 0u) << ((a & 3) * 8 + b);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t m = msk[h];
+#pragma unroll 1
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      const int a = h * 4 + (bit >> 3), b = bit & 7;
+      float ra[8];
+#pragma unroll
+      for (int aa = 0; aa < 8; ++aa) {
+        const float b0 = (b & 1) ? acc[aa][1] : acc[aa][0], b1 = (b & 1) ? acc[aa][3] : acc[aa][2];
+        const float b2 = (b & 1) ? acc[aa][5] : acc[aa][4], b3 = (b & 1) ? acc[aa][7] : acc[aa][6];
+        const float c0 = (b & 2) ? b1 : b0, c1 = (b & 2) ? b3 : b2;
+        ra[aa] = (b & 4) ? c1 : c0;
+      }
+      const float e0 = (a & 1) ? ra[1] : ra[0], e1 = (a & 1) ? ra[3] : ra[2];
+      const float e2 = (a & 1) ? ra[5] : ra[4], e3 = (a & 1) ? ra[7] : ra[6];
+      const float f0 = (a & 2) ? e1 : e0, f1 = (a & 2) ? e3 : e2;
+      const float D = (a & 4) ? f1 : f0;
+      const int add = settle_pair<APPLY>(A, k0 + 16 * a, j0 + 16 * b, D, nex);
+#pragma unroll
+      for (int aa = 0; aa < 8; ++aa) cnt[aa] += aa == a ? add : 0;
+    }
+  }
+}
+
+// acc[a][b] += sum over the staged columns [0, 4 nq) of |xa - yb| for candidate
+// rows ty + 16 a of sa and rows tx + 16 b of sb (row stride rs floats): the
+// differences two columns at a time (packed), the absolute values added in order.
+__device__ __forceinline__ void accumulate_l1(float (&acc)[8][8], const float* sa, const float* sb, int rs, int nq,
+                                              int tx, int ty) {
+  for (int q = 0; q < nq; ++q) {
+    float4 xa[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) xa[a] = *reinterpret_cast<const float4*>(sa + (ty + 16 * a) * rs + 4 * q);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const float4 yb = *reinterpret_cast<const float4*>(sb + (tx + 16 * b) * rs + 4 * q);
+      const float2 ny01 = make_float2(-yb.x, -yb.y), ny23 = make_float2(-yb.z, -yb.w);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const float2 d01 = __fadd2_rn(make_float2(xa[a].x, xa[a].y), ny01);
+        const float2 d23 = __fadd2_rn(make_float2(xa[a].z, xa[a].w), ny23);
+        float v = acc[a][b];
+        v += fabsf(d01.x);
+        v += fabsf(d01.y);
+        v += fabsf(d23.x);
+        v += fabsf(d23.y);
+        acc[a][b] = v;
+      }
+    }
+  }
+}
+
 // Tile pass over (candidate, row) pairs. APPLY = 0: counts, found-row list and
 // in-batch bits of every candidate. APPLY = 1 (only after a list overflow):
 // the evaluated candidates record themselves as writers of their found rows.
@@ -145,41 +221,58 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
   const int64_t n = A.n;
   const int d = A.d;
   const int nct = (nb + kTile - 1) / kTile;
-  const int64_t nrt = (n + kTile - 1) / kTile;
-  const int64_t ntiles = nct * nrt;
+  const int nrt = (int)((n + kTile - 1) / kTile);
+  const int64_t ntiles = (int64_t)nct * nrt;
   const int nkc = (d + kKC - 1) / kKC;
   const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t nsteps = my_tiles * nkc;
   if (nsteps == 0) return;
 
-  auto stage_step = [&](int64_t s, int buf) {
-    const int64_t t = blockIdx.x + (s / nkc) * (int64_t)gridDim.x;
-    const int c0 = (int)(s % nkc) * kKC;
-    const int ct = (int)(t / nrt);
-    const int64_t rt = t % nrt;
+  // this CTA's steps: tiles t = blockIdx.x + m gridDim.x (candidate tile ct = t / nrt, row
+  // tile rt = t % nrt), each in nkc column chunks; positions advance without division
+  struct Pos {
+    int ct, rt, kc;
+  };
+  auto advance = [&](Pos& p) {
+    if (++p.kc == nkc) {
+      p.kc = 0;
+      p.rt += gridDim.x;
+      while (p.rt >= nrt) {
+        p.rt -= nrt;
+        ++p.ct;
+      }
+    }
+  };
+  auto stage_step = [&](const Pos& p, int buf) {
+    const int c0 = p.kc * kKC;
     float* sa = sp_smem + (size_t)buf * 2 * kSideFloats;
     float* sb = sa + kSideFloats;
-    const int32_t* cand = A.cand + ct * kTile;
-    stage_rows(sa, A.X, d, A.vec, c0, min(kTile, nb - ct * kTile), [&](int r) { return cand[r]; }, tid);
-    stage_rows(sb, A.X, d, A.vec, c0, (int)min((int64_t)kTile, n - rt * kTile), [&](int r) { return rt * kTile + r; },
-               tid);
+    const int32_t* cand = A.cand + p.ct * kTile;
+    const int64_t r0 = (int64_t)p.rt * kTile;
+    stage_cols<kKC>(sa, kPad, A.X, d, A.vec, c0, min(kTile, nb - p.ct * kTile), [&](int r) { return cand[r]; }, tid);
+    stage_cols<kKC>(sb, kPad, A.X, d, A.vec, c0, (int)min((int64_t)kTile, n - r0), [&](int r) { return r0 + r; },
+                    tid);
     cp_async_commit();
   };
 
   for (int r = tid; r < kTile; r += kThreads) s_cnt[r] = 0;
   int cur_ct = -1;
   float acc[8][8];
-  stage_step(0, 0);
-  for (int64_t s = 0; s < nsteps; ++s) {
+  Pos ld{(int)(blockIdx.x / nrt), (int)(blockIdx.x % nrt), 0};
+  Pos cp = ld;
+  stage_step(ld, 0);
+  advance(ld);
+  for (int64_t s = 0; s < nsteps; ++s, advance(cp)) {
     const int buf = (int)(s & 1);
     if (s + 1 < nsteps) {
-      stage_step(s + 1, buf ^ 1);
+      stage_step(ld, buf ^ 1);
+      advance(ld);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int kc = (int)(s % nkc);
+    const int kc = cp.kc;
     if (kc == 0) {
 #pragma unroll
       for (int a = 0; a < 8; ++a)
@@ -188,34 +281,14 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
     }
     {
       const float* sa = sp_smem + (size_t)buf * 2 * kSideFloats;
-      const float* sb = sa + kSideFloats;
-      const int nq = (min(kKC, d - kc * kKC) + 3) >> 2;
-      for (int q = 0; q < nq; ++q) {
-        float4 xa[8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a) xa[a] = *reinterpret_cast<const float4*>(sa + (ty + 16 * a) * kPad + 4 * q);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const float4 yb = *reinterpret_cast<const float4*>(sb + (tx + 16 * b) * kPad + 4 * q);
-#pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            float v = acc[a][b];
-            v += fabsf(xa[a].x - yb.x);
-            v += fabsf(xa[a].y - yb.y);
-            v += fabsf(xa[a].z - yb.z);
-            v += fabsf(xa[a].w - yb.w);
-            acc[a][b] = v;
-          }
-        }
-      }
+      accumulate_l1(acc, sa, sa + kSideFloats, kPad, (min(kKC, d - kc * kKC) + 3) >> 2, tx, ty);
     }
     __syncthreads();  // the stage is consumed before it is refilled
     if (kc != nkc - 1) continue;
 
     // ---------------------------------------------------------------- tile epilogue
-    const int64_t t = blockIdx.x + (s / nkc) * (int64_t)gridDim.x;
-    const int ct = (int)(t / nrt);
-    const int64_t rt = t % nrt;
+    const int ct = cp.ct;
+    const int64_t rt = cp.rt;
     if (!APPLY && ct != cur_ct) {  // candidate counts accumulate while the candidate tile stays
       if (cur_ct >= 0) {
         for (int r = tid; r < kTile; r += kThreads) {
@@ -228,34 +301,24 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
       }
       cur_ct = ct;
     }
+    // certain counts (D < w_lo); pairs at or below a_hi or in the counting band take the slow path
     int cnt[8];
     bool slow = false;
+    const bool full = (ct + 1) * kTile <= nb && (rt + 1) * kTile <= n;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
       cnt[a] = 0;
-      const int k = ct * kTile + ty + 16 * a;
 #pragma unroll
       for (int b = 0; b < 8; ++b) {
-        const int64_t j = rt * kTile + tx + 16 * b;
         const float D = acc[a][b];
-        const bool valid = k < nb && j < n;
+        const bool valid = full || (ct * kTile + ty + 16 * a < nb && rt * kTile + tx + 16 * b < n);
         cnt[a] += (valid && D < A.w_lo) ? 1 : 0;
-        slow |= valid && (D <= A.a_hi || (D >= A.w_lo && D <= A.w_hi));
+        slow |= valid && (D <= A.a_hi || fabsf(D - A.w_mid) <= A.w_half);
       }
     }
     if (__any_sync(0xffffffffu, slow) && slow) {
       int nex = 0;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const int k = ct * kTile + ty + 16 * a;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const int64_t j = rt * kTile + tx + 16 * b;
-          const float D = acc[a][b];
-          if (k < nb && j < n && (D <= A.a_hi || (!APPLY && D >= A.w_lo && D <= A.w_hi)))
-            cnt[a] += settle_pair<APPLY>(A, k, j, D, nex);
-        }
-      }
+      slow_pairs<APPLY>(A, acc, ct * kTile + ty, rt * kTile + tx, full, false, nb, n, cnt, nex);
       if (nex) atomicAdd(&ctl->n_exact, (unsigned long long)nex);
     }
     if (!APPLY) {
@@ -275,6 +338,98 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
       if (k < nb && s_cnt[r]) atomicAdd(&A.ccount[k], s_cnt[r]);
     }
   }
+}
+
+// The counting pass with the candidate tile resident in shared memory (d <=
+// DMAX): CTA b keeps candidate tile ct = b % nct and streams the row tiles
+// rt = b / nct + m G (G = gridDim.x / nct) through a two-stage cp.async ring;
+// the candidates' counts stay in registers until the CTA ends. Full tiles test
+// the slow-path conditions on the 64 pairs' minima (of D and of |D - w_mid|).
+template <int DMAX>
+__global__ void __launch_bounds__(kThreads, 2) spade_pairs_res_kernel(SpadeArgs A) {
+  constexpr int RS = DMAX + 4;  // floats per staged row (16-byte aligned, spreads banks)
+  extern __shared__ __align__(16) float sp_smem[];
+  __shared__ int s_cnt[kTile];
+  SpadeCtl* ctl = A.ctl;
+  const int nb = ctl->nb;
+  if (nb == 0) return;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t n = A.n;
+  const int d = A.d;
+  const int nct = (nb + kTile - 1) / kTile;
+  const int G = (int)gridDim.x / nct;
+  if ((int)blockIdx.x >= nct * G) return;
+  const int ct = (int)blockIdx.x % nct, g = (int)blockIdx.x / nct;
+  const int nrt = (int)((n + kTile - 1) / kTile);
+  if (g >= nrt) return;
+  const int my = (nrt - 1 - g) / G + 1;  // row tiles of this CTA
+  float* sa = sp_smem;
+  float* sb0 = sa + kTile * RS;
+  const int32_t* cand = A.cand + ct * kTile;
+  stage_cols<DMAX>(sa, RS, A.X, d, A.vec, 0, min(kTile, nb - ct * kTile), [&](int r) { return cand[r]; }, tid);
+  auto stage_b = [&](int rt, float* dst) {
+    const int64_t r0 = (int64_t)rt * kTile;
+    stage_cols<DMAX>(dst, RS, A.X, d, A.vec, 0, (int)min((int64_t)kTile, n - r0), [&](int r) { return r0 + r; },
+                     tid);
+  };
+  stage_b(g, sb0);
+  cp_async_commit();
+  int cnt[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) cnt[a] = 0;
+  int nex = 0;
+  const int nq = (d + 3) >> 2;
+  const int k0 = ct * kTile + ty;
+  for (int m = 0; m < my; ++m) {
+    const int rt = g + m * G;
+    if (m + 1 < my) {
+      stage_b(rt + G, sb0 + ((m + 1) & 1) * kTile * RS);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    accumulate_l1(acc, sa, sb0 + (m & 1) * kTile * RS, RS, nq, tx, ty);
+    __syncthreads();  // this stage is refilled by the next iteration's prefetch
+
+    const int64_t j0 = (int64_t)rt * kTile + tx;
+    const bool full = (ct + 1) * kTile <= nb && (int64_t)(rt + 1) * kTile <= n;
+    bool slow = !full;
+    if (full) {
+      float mnD = INFINITY, mnB = INFINITY;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const float D = acc[a][b];
+          cnt[a] += D < A.w_lo ? 1 : 0;
+          mnD = fminf(mnD, D);
+          mnB = fminf(mnB, fabsf(D - A.w_mid));
+        }
+      }
+      slow = mnD <= A.a_hi || mnB <= A.w_half;
+    }
+    if (__any_sync(0xffffffffu, slow) && slow) slow_pairs<0>(A, acc, k0, j0, full, !full, nb, n, cnt, nex);
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    int v = cnt[a];
+#pragma unroll
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tx == 0) s_cnt[ty + 16 * a] = v;  // one writer per candidate row
+  }
+  __syncthreads();
+  for (int r = tid; r < kTile; r += kThreads) {
+    const int k = ct * kTile + r;
+    if (k < nb && s_cnt[r]) atomicAdd(&A.ccount[k], s_cnt[r]);
+  }
+  if (nex) atomicAdd(&ctl->n_exact, (unsigned long long)nex);
 }
 
 // Rows not yet found by any evaluated row, from the cursor, become the next
@@ -431,6 +586,10 @@ __global__ void __launch_bounds__(256) spade_density_kernel(SpadeArgs A, int32_t
 }
 
 constexpr size_t kPairSmem = (size_t)2 * 2 * kSideFloats * sizeof(float);
+template <int DMAX>
+constexpr size_t res_smem() {
+  return (size_t)3 * kTile * (DMAX + 4) * sizeof(float);  // candidates + two row stages
+}
 
 }  // namespace
 
@@ -441,6 +600,12 @@ cudaError_t init_spade() {
                                        (int)kPairSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(spade_pairs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spade_pairs_res_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)res_smem<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(spade_pairs_res_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)res_smem<64>());
   return e;
 }
 
@@ -451,11 +616,16 @@ cudaError_t launch_spade_init(const SpadeArgs& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s) {
+cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
   spade_select_kernel<<<1, kSB, 0, s>>>(A);
   const int64_t tiles = (int64_t)(kSB / kTile) * ((A.n + kTile - 1) / kTile);
   const int grid = (int)std::min<int64_t>(tiles, 2 * (int64_t)num_sms());
-  spade_pairs_kernel<0><<<grid, kThreads, kPairSmem, s>>>(A);
+  cudaError_t e;
+  if (e0 && (e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
+  if (A.d <= 32) spade_pairs_res_kernel<32><<<grid, kThreads, res_smem<32>(), s>>>(A);
+  else if (A.d <= 64) spade_pairs_res_kernel<64><<<grid, kThreads, res_smem<64>(), s>>>(A);
+  else spade_pairs_kernel<0><<<grid, kThreads, kPairSmem, s>>>(A);
+  if (e1 && (e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
   spade_resolve_kernel<<<1, kSB, 0, s>>>(A);
   int ab = (int)std::min<int64_t>((A.pair_cap + 255) / 256, num_sms() * 8);
   spade_apply_kernel<<<ab, 256, 0, s>>>(A);

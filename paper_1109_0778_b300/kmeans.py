@@ -49,10 +49,10 @@ class SpadeStats(ctypes.Structure):
     _fields_ = [("n_evaluated", ctypes.c_int64), ("n_computed", ctypes.c_int64),
                 ("n_found_pairs", ctypes.c_int64), ("n_exact", ctypes.c_int64),
                 ("batches", ctypes.c_int32), ("overflow_batches", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("ms", ctypes.c_float), ("ms_pairs", ctypes.c_float)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
