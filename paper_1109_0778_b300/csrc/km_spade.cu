@@ -48,6 +48,12 @@ constexpr int kPad = 36;     // floats per staged row (16-byte aligned, spreads 
 constexpr int kThreads = 256;
 constexpr int kSideFloats = kTile * kPad;
 
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // The loop's distance: FP64, columns in increasing order.
 __device__ __forceinline__ double l1_fp64(const float* __restrict__ x, const float* __restrict__ y, int d) {
   double s = 0.0;
@@ -342,11 +348,14 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_kernel(SpadeArgs A) {
 
 // The counting pass with the candidate tile resident in shared memory (d <=
 // DMAX): CTA b keeps candidate tile ct = b % nct and streams the row tiles
-// rt = b / nct + m G (G = gridDim.x / nct) through a two-stage cp.async ring;
+// rt = b / nct + m G (G = gridDim.x / nct) through an NST-stage cp.async ring
+// (with three stages one barrier per tile suffices: the stage refilled after
+// iteration m's barrier was last read at iteration m - 1);
 // the candidates' counts stay in registers until the CTA ends. Full tiles test
 // the slow-path conditions on the 64 pairs' minima (of D and of |D - w_mid|).
-template <int DMAX>
+template <int DMAX, int NST>
 __global__ void __launch_bounds__(kThreads, 2) spade_pairs_res_kernel(SpadeArgs A) {
+  static_assert(NST == 2 || NST == 3, "two or three row stages");
   constexpr int RS = DMAX + 4;  // floats per staged row (16-byte aligned, spreads banks)
   extern __shared__ __align__(16) float sp_smem[];
   __shared__ int s_cnt[kTile];
@@ -374,6 +383,8 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_res_kernel(SpadeArgs 
   };
   stage_b(g, sb0);
   cp_async_commit();
+  if (NST == 3 && my > 1) stage_b(g + G, sb0 + kTile * RS);
+  if (NST == 3) cp_async_commit();  // (possibly empty) group of the second row tile
   int cnt[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) cnt[a] = 0;
@@ -382,21 +393,30 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_res_kernel(SpadeArgs 
   const int k0 = ct * kTile + ty;
   for (int m = 0; m < my; ++m) {
     const int rt = g + m * G;
-    if (m + 1 < my) {
-      stage_b(rt + G, sb0 + ((m + 1) & 1) * kTile * RS);
-      cp_async_commit();
-      cp_async_wait<1>();
+    if (NST == 2) {
+      if (m + 1 < my) {
+        stage_b(rt + G, sb0 + ((m + 1) & 1) * kTile * RS);
+        cp_async_commit();
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
     } else {
-      cp_async_wait<0>();
+      cp_async_wait<1>();  // every group but the newest (row tile m + 1): row tile m has landed
     }
     __syncthreads();
+    if (NST == 3) {
+      // every thread is past iteration m - 1, the last reader of stage (m + 2) % 3
+      if (m + 2 < my) stage_b(rt + 2 * G, sb0 + ((m + 2) % 3) * kTile * RS);
+      cp_async_commit();  // one group per iteration (empty near the end) keeps the count uniform
+    }
     float acc[8][8];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
       for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-    accumulate_l1(acc, sa, sb0 + (m & 1) * kTile * RS, RS, nq, tx, ty);
-    __syncthreads();  // this stage is refilled by the next iteration's prefetch
+    accumulate_l1(acc, sa, sb0 + (m % NST) * kTile * RS, RS, nq, tx, ty);
+    if (NST == 2) __syncthreads();  // this stage is refilled by the next iteration's prefetch
 
     const int64_t j0 = (int64_t)rt * kTile + tx;
     const bool full = (ct + 1) * kTile <= nb && (int64_t)(rt + 1) * kTile <= n;
@@ -406,11 +426,11 @@ __global__ void __launch_bounds__(kThreads, 2) spade_pairs_res_kernel(SpadeArgs 
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const float D = acc[a][b];
-          cnt[a] += D < A.w_lo ? 1 : 0;
-          mnD = fminf(mnD, D);
-          mnB = fminf(mnB, fabsf(D - A.w_mid));
+        for (int b = 0; b < 8; b += 2) {
+          const float D0 = acc[a][b], D1 = acc[a][b + 1];
+          cnt[a] += (D0 < A.w_lo ? 1 : 0) + (D1 < A.w_lo ? 1 : 0);
+          mnD = min3f(mnD, D0, D1);
+          mnB = min3f(mnB, fabsf(D0 - A.w_mid), fabsf(D1 - A.w_mid));
         }
       }
       slow = mnD <= A.a_hi || mnB <= A.w_half;
@@ -586,9 +606,9 @@ __global__ void __launch_bounds__(256) spade_density_kernel(SpadeArgs A, int32_t
 }
 
 constexpr size_t kPairSmem = (size_t)2 * 2 * kSideFloats * sizeof(float);
-template <int DMAX>
+template <int DMAX, int NST>
 constexpr size_t res_smem() {
-  return (size_t)3 * kTile * (DMAX + 4) * sizeof(float);  // candidates + two row stages
+  return (size_t)(1 + NST) * kTile * (DMAX + 4) * sizeof(float);  // candidates + NST row stages
 }
 
 }  // namespace
@@ -601,11 +621,11 @@ cudaError_t init_spade() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(spade_pairs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPairSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spade_pairs_res_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)res_smem<32>());
+    e = cudaFuncSetAttribute(spade_pairs_res_kernel<32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)res_smem<32, 2>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(spade_pairs_res_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)res_smem<64>());
+    e = cudaFuncSetAttribute(spade_pairs_res_kernel<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)res_smem<64, 2>());
   return e;
 }
 
@@ -622,8 +642,8 @@ cudaError_t launch_spade_batch(const SpadeArgs& A, cudaStream_t s, cudaEvent_t e
   const int grid = (int)std::min<int64_t>(tiles, 2 * (int64_t)num_sms());
   cudaError_t e;
   if (e0 && (e = cudaEventRecord(e0, s)) != cudaSuccess) return e;
-  if (A.d <= 32) spade_pairs_res_kernel<32><<<grid, kThreads, res_smem<32>(), s>>>(A);
-  else if (A.d <= 64) spade_pairs_res_kernel<64><<<grid, kThreads, res_smem<64>(), s>>>(A);
+  if (A.d <= 32) spade_pairs_res_kernel<32, 2><<<grid, kThreads, res_smem<32, 2>(), s>>>(A);
+  else if (A.d <= 64) spade_pairs_res_kernel<64, 2><<<grid, kThreads, res_smem<64, 2>(), s>>>(A);
   else spade_pairs_kernel<0><<<grid, kThreads, kPairSmem, s>>>(A);
   if (e1 && (e = cudaEventRecord(e1, s)) != cudaSuccess) return e;
   spade_resolve_kernel<<<1, kSB, 0, s>>>(A);
