@@ -45,7 +45,8 @@ DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
 STAGE_KERNELS = ("prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
 # Source file of each stage's kernel (a change to it voids a stored ncu traffic figure).
 KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu", "bf16": "km_assign_tc.cu", "fp8": "km_assign_tc.cu",
-                             "bf16x3": "km_assign_tc.cu"}}
+                             "bf16x3": "km_assign_tc.cu"},
+                  "spade_pairs": {"f32": "km_spade.cu"}}
 
 
 def parse_args(argv=None):
@@ -586,7 +587,7 @@ def run_spade(args, torch, dev, dist, rank, world, local):
                          "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz / 2 FP32 ops per element",
                          "issued_frac": (issued / (pairs_ms / args.steps / 1e3) / 1e12) / peak,
                          "note": "algorithmic elements = evaluated rows x n x d; issued adds speculative rows",
-                         "traffic": None},
+                         "traffic": stored_traffic("spade_pairs", "f32", sw.name)},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "peaks_source": peak_src,
         }
         print(json.dumps(line), flush=True)

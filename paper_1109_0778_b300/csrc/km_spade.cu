@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(kSB) spade_select_kernel(SpadeArgs A) {
   // clear the batch state
   A.ccount[tid] = 0;
   A.inP[tid] = 0;
-  for (int w = 0; w < kSB / 32; ++w) A.nbr[(size_t)tid * (kSB / 32) + w] = 0u;
+  uint4* nbr4 = reinterpret_cast<uint4*>(A.nbr);  // coalesced: consecutive threads, consecutive 16 bytes
+  for (int w = tid; w < kSB * (kSB / 32) / 4; w += kSB) nbr4[w] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   for (int64_t base = start; base < A.n; base += kSB) {
     const int found = s_found;
@@ -512,8 +513,17 @@ __global__ void __launch_bounds__(kSB) spade_resolve_kernel(SpadeArgs A) {
   if (nb == 0) return;
   const int k = threadIdx.x, lane = k & 31, warp = k >> 5;
   uint32_t w[kSB / 32];
+  {
+    const uint4* row = reinterpret_cast<const uint4*>(A.nbr + (size_t)k * (kSB / 32));
 #pragma unroll
-  for (int i = 0; i < kSB / 32; ++i) w[i] = k < nb ? A.nbr[(size_t)k * (kSB / 32) + i] : 0u;
+    for (int i = 0; i < kSB / 128; ++i) {
+      const uint4 v = k < nb ? row[i] : make_uint4(0u, 0u, 0u, 0u);
+      w[4 * i] = v.x;
+      w[4 * i + 1] = v.y;
+      w[4 * i + 2] = v.z;
+      w[4 * i + 3] = v.w;
+    }
+  }
   int st = k < nb ? 0 : 2;  // 0 undecided, 1 evaluated, 2 skipped
   {
     const unsigned u = __ballot_sync(0xffffffffu, st == 0);
