@@ -188,8 +188,8 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
-      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, xss, labs, fq_rows, fq_old, X_sub, xn_sub, flags2,
-      total;
+      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
+      flags2, total;
   int64_t fq_cap;
 };
 
@@ -243,12 +243,24 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
     L.flags2 = take(sizeof(FlagRec) * (size_t)L.fq_cap);
     const int width = simt_slab_width(d);  // the queued rows' FP32 pass may carry state across slabs
     L.state = (width > 0 && width < k) ? take(16 * (size_t)L.fq_cap) : 0;
+    L.state3 = (width > 0 && width < k) ? take(4 * (size_t)L.fq_cap) : 0;
   } else {
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
-    L.fq_rows = L.fq_old = L.X_sub = L.xn_sub = L.flags2 = 0;
-    L.fq_cap = 0;
     const int width = simt_slab_width(d);
-    L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;
+    L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;  // also serves the re-check pass
+    if (width > 0) {
+      // flagged points are gathered and re-scored by the slab kernel keeping two candidates and a third score
+      L.fq_cap = requeue_cap(n);
+      L.fq_rows = take(4 * (size_t)L.fq_cap);
+      L.fq_old = take(4 * (size_t)L.fq_cap);
+      L.X_sub = take(4 * (size_t)L.fq_cap * d);
+      L.xn_sub = take(4 * (size_t)L.fq_cap);
+      L.flags2 = take(sizeof(FlagRec) * (size_t)L.fq_cap);
+      L.state3 = width < k ? take(4 * (size_t)L.fq_cap) : 0;
+    } else {
+      L.fq_rows = L.fq_old = L.X_sub = L.xn_sub = L.flags2 = L.state3 = 0;
+      L.fq_cap = 0;
+    }
   }
   L.total = o;
   return L;
@@ -301,6 +313,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
   w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
+  w.state3 = L.state3 ? (float*)(b + L.state3) : nullptr;
   w.xs16 = L.xs16 ? (float4*)(b + L.xs16) : nullptr;
   w.xs_sorted = L.xss ? (float4*)(b + L.xss) : nullptr;
   w.lab_sorted = L.labs ? (int32_t*)(b + L.labs) : nullptr;

@@ -22,6 +22,8 @@
 // the point is flagged and re-checked with compensated FP32 distances. The
 // FMA chain is the same whether it runs as scalar or paired (FFMA2) FMAs: each
 // accumulator takes one rounding per term, so the bound does not change.
+#include <type_traits>
+
 #include "km_internal.cuh"
 
 namespace km {
@@ -62,6 +64,65 @@ __device__ __forceinline__ Top2 top2_merge(const Top2& a, const Top2& b) {
     r.b2 = fminf(b.b1, a.b2);
   }
   return r;
+}
+
+// Re-check passes over gathered rows keep the best two (score, index) pairs
+// and the third-best score: when the third lies outside the margin, the two
+// are the complete candidate list of the point.
+struct Top3s {
+  float b1, b2, b3;
+  int i1, i2;
+};
+
+__device__ __forceinline__ void top_push(Top2& t, float s, int j) { top2_push(t, s, j); }
+__device__ __forceinline__ void top_push(Top3s& t, float s, int j) {
+  // branch-free sorted insert; columns arrive in increasing j, so strict
+  // comparisons keep the lowest index first; a NaN score changes nothing
+  const bool lt1 = s < t.b1, lt2 = s < t.b2;
+  t.b3 = lt2 ? t.b2 : fminf(t.b3, s);
+  t.i2 = lt1 ? t.i1 : (lt2 ? j : t.i2);
+  t.b2 = lt1 ? t.b1 : (lt2 ? s : t.b2);
+  t.i1 = lt1 ? j : t.i1;
+  t.b1 = lt1 ? s : t.b1;
+}
+
+__device__ __forceinline__ Top2 top_merge(const Top2& a, const Top2& b) { return top2_merge(a, b); }
+__device__ __forceinline__ Top3s top_merge(Top3s a, Top3s b) {
+  if (lex_less(b.b1, b.i1, a.b1, a.i1)) {
+    const Top3s t = a;
+    a = b;
+    b = t;
+  }
+  Top3s r;
+  r.b1 = a.b1;
+  r.i1 = a.i1;
+  if (lex_less(b.b1, b.i1, a.b2, a.i2)) {
+    r.b2 = b.b1;
+    r.i2 = b.i1;
+    r.b3 = fminf(a.b2, b.b2);
+  } else {
+    r.b2 = a.b2;
+    r.i2 = a.i2;
+    r.b3 = fminf(a.b3, b.b1);
+  }
+  return r;
+}
+
+__device__ __forceinline__ Top2 top_shfl_xor(const Top2& t, int o) {
+  Top2 p;
+  p.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
+  p.b2 = __shfl_xor_sync(0xffffffffu, t.b2, o);
+  p.i1 = __shfl_xor_sync(0xffffffffu, t.i1, o);
+  return p;
+}
+__device__ __forceinline__ Top3s top_shfl_xor(const Top3s& t, int o) {
+  Top3s p;
+  p.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
+  p.b2 = __shfl_xor_sync(0xffffffffu, t.b2, o);
+  p.b3 = __shfl_xor_sync(0xffffffffu, t.b3, o);
+  p.i1 = __shfl_xor_sync(0xffffffffu, t.i1, o);
+  p.i2 = __shfl_xor_sync(0xffffffffu, t.i2, o);
+  return p;
 }
 
 // Loads a BK-wide slice [k0, k0+BK) of `rows` rows starting at r0 of a
@@ -250,12 +311,18 @@ __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const 
   }
 }
 
-template <bool V16>
+// T3 (re-check passes over gathered rows): the best two candidates and the
+// third-best score are kept, and a flagged row whose third-best score lies
+// outside the margin is recorded with its two candidates; the third-best
+// score crosses slabs in state3.
+template <bool V16, bool T3>
 __global__ void __launch_bounds__(ST, 1)
 assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
-                   int first, int first_slab, int last_slab, float gam, const SubRows sr) {
+                   float* __restrict__ state3, int first, int first_slab, int last_slab, float gam,
+                   const SubRows sr) {
+  using TopT = typename std::conditional<T3, Top3s, Top2>::type;
   if (halted(ctl)) return;
   if (sr.n_dev) n = min(n, (int64_t)*sr.n_dev);  // gathered rows of the re-check stage (n = capacity)
   if ((int64_t)blockIdx.x * BM >= n) return;    // no tile for this CTA: skip the slab load
@@ -293,17 +360,26 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     __syncthreads();
 
     const int64_t m0 = tile * BM;
-    Top2 top[SR];
+    TopT top[SR];
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
       const int64_t i = m0 + srow_of(ty, r);
       // the carried state enters through one of the 16 threads sharing the row,
       // so the cross-thread merge sees it once
-      if (!first_slab && tx == 0 && i < n) {
-        const float4 st = state[i];
-        top[r] = Top2{st.x, st.z, __float_as_int(st.y)};
+      if constexpr (T3) {
+        if (!first_slab && tx == 0 && i < n) {
+          const float4 st = state[i];
+          top[r] = Top3s{st.x, st.z, state3[i], __float_as_int(st.y), __float_as_int(st.w)};
+        } else {
+          top[r] = Top3s{INFINITY, INFINITY, INFINITY, 0, 0};
+        }
       } else {
-        top[r] = Top2{INFINITY, INFINITY, 0};
+        if (!first_slab && tx == 0 && i < n) {
+          const float4 st = state[i];
+          top[r] = Top2{st.x, st.z, __float_as_int(st.y)};
+        } else {
+          top[r] = Top2{INFINITY, INFINITY, 0};
+        }
       }
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
@@ -347,19 +423,13 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
         const int jl = j0 + col_of(tx, c);
         const float hj = Hs[jl];
 #pragma unroll
-        for (int r = 0; r < SR; ++r) top2_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
+        for (int r = 0; r < SR; ++r) top_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
       }
     }
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
 #pragma unroll
-      for (int o = 8; o; o >>= 1) {
-        Top2 p;
-        p.b1 = __shfl_xor_sync(0xffffffffu, top[r].b1, o);
-        p.b2 = __shfl_xor_sync(0xffffffffu, top[r].b2, o);
-        p.i1 = __shfl_xor_sync(0xffffffffu, top[r].i1, o);
-        top[r] = top2_merge(top[r], p);
-      }
+      for (int o = 8; o; o >>= 1) top[r] = top_merge(top[r], top_shfl_xor(top[r], o));
     }
     if (tid == 0) s_changed = 0;
     __syncthreads();  // also: every thread is done reading Xs before it is refilled
@@ -370,7 +440,12 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
         const int64_t i = m0 + srow_of(ty, r);
         if (i >= n) continue;
         if (!last_slab) {
-          state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
+          if constexpr (T3) {
+            state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, __int_as_float(top[r].i2));
+            state3[i] = top[r].b3;
+          } else {
+            state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
+          }
           continue;
         }
         const int64_t pt = sr.rows ? (int64_t)sr.rows[i] : i;  // the point of row i
@@ -384,6 +459,13 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
           FlagRec rec;
           rec.i = (int32_t)pt; rec.old = old; rec.nc = 0; rec.pad = 0;
           rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
+          if constexpr (T3) {
+            if (__fsub_rn(top[r].b3, top[r].b1) > margin) {  // no third centroid can be the nearest
+              rec.nc = 2;
+              rec.cand[0] = min(j1, top[r].i2);
+              rec.cand[1] = max(j1, top[r].i2);
+            }
+          }
           (sr.flags ? sr.flags : flags)[slot] = rec;
           if (!sr.rows) atomicAdd(&ctl->n_full, 1ull);
         } else {
@@ -413,14 +495,15 @@ cudaError_t init_assign_simt() {
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaFuncAttributes fa;
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, assign_slab_kernel<true>);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(assign_slab_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
-  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, assign_slab_kernel<false>);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(assign_slab_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             optin - (int)fa.sharedSizeBytes);
+  auto raise = [&](auto kernel) {
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  };
+  raise(assign_slab_kernel<true, false>);
+  raise(assign_slab_kernel<false, false>);
+  raise(assign_slab_kernel<true, true>);
+  raise(assign_slab_kernel<false, true>);
   return e;
 }
 
@@ -452,14 +535,20 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* cha
     const int nsp = (ns + BN - 1) / BN * BN;
     const size_t smem = slab_smem_bytes(dp, nsp);
     const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
-    if (v16)
-      assign_slab_kernel<true><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
-                                                            w.ctl, p.assign, w.flags, w.state, first, first_slab,
-                                                            last_slab, gam, sr);
-    else
-      assign_slab_kernel<false><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm,
-                                                             w.ctl, p.assign, w.flags, w.state, first, first_slab,
-                                                             last_slab, gam, sr);
+    // passes over gathered re-check rows keep a third score (candidate lists of two)
+    const bool t3 = sr.rows != nullptr;
+#define KM_SLAB(V, T)                                                                                        \
+  assign_slab_kernel<V, T><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm, w.ctl, \
+                                                    p.assign, w.flags, w.state, w.state3, first, first_slab,      \
+                                                    last_slab, gam, sr)
+    if (v16) {
+      if (t3) KM_SLAB(true, true);
+      else KM_SLAB(true, false);
+    } else {
+      if (t3) KM_SLAB(false, true);
+      else KM_SLAB(false, false);
+    }
+#undef KM_SLAB
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

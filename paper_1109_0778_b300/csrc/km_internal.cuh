@@ -75,12 +75,14 @@ struct Work {
   uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
   float* hq;           // [kp] h_j of the quantised path (+inf for padding)
   float* scq;          // [kp] centroid code scales
-  float4* state;       // [n] per-row (best, index, second) between centroid slabs (FP32 path)
+  float4* state;       // [n] per-row (best, index, second, second's index) between centroid slabs
+  float* state3;       // [fq_cap] third-best score between slabs (re-check passes over gathered rows)
   float4* xs16;        // [n] BF16 statistics of a cold first step of an E4M3 run
   float4* xs_sorted;   // [n] xs in this step's cluster-sorted order (quantised paths)
   int32_t* lab_sorted; // [n] label of each sorted position (scatter stage)
-  // points the quantised assignment could not narrow to a short list: gathered
-  // and re-scored by the tiled FP32 kernel (quantised paths; null for FP32)
+  // points the assignment could not narrow to a short list: gathered and
+  // re-scored by the tiled FP32 kernel keeping two candidates and a third score
+  // (null when that kernel does not apply)
   int64_t fq_cap;      // rows the queue holds
   int32_t* fq_rows;    // [fq_cap] point index
   int32_t* fq_old;     // [fq_cap] previous label

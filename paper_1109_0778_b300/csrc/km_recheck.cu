@@ -70,12 +70,12 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
   if (lane == 0 && changed) atomicAdd(&ctl->n_changed, (unsigned long long)changed);
 }
 
-// Copies the queued rows into X_sub and their norm bounds (xs.w) into xn_sub;
-// one warp per row.
+// Copies the queued rows into X_sub and their norm bounds (xs.w on the
+// quantised paths, xnorm on the FP32 path) into xn_sub; one warp per row.
 __global__ void __launch_bounds__(256)
-gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict__ xs, const Ctl* ctl,
-                    const int32_t* __restrict__ q_rows, int64_t q_cap, float* __restrict__ X_sub,
-                    float* __restrict__ xn_sub) {
+gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict__ xs,
+                    const float* __restrict__ xnorm, const Ctl* ctl, const int32_t* __restrict__ q_rows,
+                    int64_t q_cap, float* __restrict__ X_sub, float* __restrict__ xn_sub) {
   if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -86,7 +86,7 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
     const float* x = X + i * d;
     float* y = X_sub + r * d;
     for (int t = lane; t < d; t += 32) y[t] = x[t];
-    if (lane == 0) xn_sub[r] = xs[i].w;
+    if (lane == 0) xn_sub[r] = xs ? xs[i].w : xnorm[i];
   }
 }
 
@@ -117,18 +117,22 @@ cudaError_t recheck_pass(const Problem& p, const Work& w, const float* h, const 
   }
 }
 
-// The re-check stage. Short candidate lists are settled directly. On the
-// quantised paths, points whose candidates could not be narrowed are queued,
-// gathered, and assigned again by the tiled FP32 kernel (the distances of many
-// points against all centroids, each centroid tile read once per 128 points);
-// the few it still flags get the compensated distances against all k. The FP32
-// path settles every flag directly (its flags come from that same kernel).
+// The re-check stage. Short candidate lists are settled directly. Points whose
+// candidates could not be narrowed are queued, gathered, and scored again by
+// the tiled FP32 kernel (the distances of many points against all centroids,
+// each centroid tile read once per 128 points), which this time keeps the best
+// two candidates and the third-best score: a point whose third score lies
+// outside the margin is settled between its two candidates, the few others by
+// compensated distances against all k. (The FP32 path's own flags come from
+// that kernel's top-two pass, so all of them take this route when d allows the
+// slab kernel.)
 cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s) {
   (void)first;  // the stored old label is -1 in a call's first step
   const bool queue = w.fq_rows != nullptr;
   cudaError_t e = recheck_pass(p, w, h, w.flags, &w.ctl->n_flagged, queue, s);
   if (e != cudaSuccess || !queue) return e;
-  gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xs, w.ctl, w.fq_rows, w.fq_cap, w.X_sub, w.xn_sub);
+  gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xs, w.xnorm, w.ctl, w.fq_rows, w.fq_cap, w.X_sub,
+                                                    w.xn_sub);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_assign_simt_sub(p, w, h, s)) != cudaSuccess) return e;
   return recheck_pass(p, w, h, w.flags2, &w.ctl->n_flagged2, false, s);
