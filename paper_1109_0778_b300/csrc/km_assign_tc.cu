@@ -312,6 +312,53 @@ __device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float
     if (mn <= thr) fold_block(top, s, mn, j0, thr, margin);
 }
 
+// Two consecutive 32-column blocks: both score sets, one vote on the smaller
+// block minimum, then the folds in column order (the first may tighten thr).
+__device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint32_t (&v2)[32], const float* hb,
+                                             float w, Cand (&top)[kT], int j0, float& thr, float margin) {
+  float s[32], s2[32];
+  const float4* h4 = reinterpret_cast<const float4*>(hb);
+  const float2 w2 = make_float2(w, w);
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const float4 hh = h4[t], hg = h4[t + 8];
+    const float2 a0 = make_float2(__uint_as_float(v[4 * t]), __uint_as_float(v[4 * t + 1]));
+    const float2 a1 = make_float2(__uint_as_float(v[4 * t + 2]), __uint_as_float(v[4 * t + 3]));
+    const float2 c0 = make_float2(__uint_as_float(v2[4 * t]), __uint_as_float(v2[4 * t + 1]));
+    const float2 c1 = make_float2(__uint_as_float(v2[4 * t + 2]), __uint_as_float(v2[4 * t + 3]));
+    const float2 s0 = __ffma2_rn(w2, a0, make_float2(hh.x, hh.y));
+    const float2 s1 = __ffma2_rn(w2, a1, make_float2(hh.z, hh.w));
+    const float2 t0 = __ffma2_rn(w2, c0, make_float2(hg.x, hg.y));
+    const float2 t1 = __ffma2_rn(w2, c1, make_float2(hg.z, hg.w));
+    s[4 * t] = s0.x;
+    s[4 * t + 1] = s0.y;
+    s[4 * t + 2] = s1.x;
+    s[4 * t + 3] = s1.y;
+    s2[4 * t] = t0.x;
+    s2[4 * t + 1] = t0.y;
+    s2[4 * t + 2] = t1.x;
+    s2[4 * t + 3] = t1.y;
+  }
+  float m11[11], n11[11];
+#pragma unroll
+  for (int u = 0; u < 10; ++u) {
+    m11[u] = min3f(s[3 * u], s[3 * u + 1], s[3 * u + 2]);
+    n11[u] = min3f(s2[3 * u], s2[3 * u + 1], s2[3 * u + 2]);
+  }
+  m11[10] = fminf(s[30], s[31]);
+  n11[10] = fminf(s2[30], s2[31]);
+  const float mn = fminf(min3f(min3f(m11[0], m11[1], m11[2]), min3f(m11[3], m11[4], m11[5]),
+                               min3f(m11[6], m11[7], m11[8])),
+                         fminf(m11[9], m11[10]));
+  const float mn2 = fminf(min3f(min3f(n11[0], n11[1], n11[2]), min3f(n11[3], n11[4], n11[5]),
+                                min3f(n11[6], n11[7], n11[8])),
+                          fminf(n11[9], n11[10]));
+  if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
+    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin);
+    if (mn2 <= thr) fold_block(top, s2, mn2, j0 + 32, thr, margin);
+  }
+}
+
 template <int FP8, bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 1)
 assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
@@ -596,10 +643,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const uint32_t trow = tmem_base + ((uint32_t)(q * 32) << 16);
       // the tile's 32-column blocks in chunk order
       const int nall = it.nchunks * nblk;
-      uint32_t v[32];
+      uint32_t v[32], v2[32];
       int c = c0;
 #pragma unroll 1
-      for (int kb = 0; kb < nall && ok; ++kb) {
+      for (int kb = 0; kb < nall && ok;) {
         const int blk = kb % nblk;
         const int buf = 2 * (gu & 1) + grp;
         if (blk == 0) {  // a new chunk: wait for its accumulators
@@ -609,16 +656,23 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           }
           tc_fence_after_sync();
         }
+        // two blocks of this chunk per load and vote (single launches: the batched kernel keeps one,
+        // for registers)
+        const bool two = !BATCH && blk + 1 < nblk;
         tmem_ld_32x32b_x32(trow + (uint32_t)(buf * 128 + blk * 32), v);
+        if (two) tmem_ld_32x32b_x32(trow + (uint32_t)(buf * 128 + blk * 32 + 32), v2);
         tmem_ld_wait();
-        if (blk == nblk - 1) {  // the chunk's accumulators are all in registers: release the buffer
+        const int lastb = two ? blk + 1 : blk;
+        if (lastb == nblk - 1) {  // the chunk's accumulators are all in registers: release the buffer
           tc_fence_before_sync();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
         const int j0 = c * BN + blk * 32;
-        score_block(v, Hs + j0, wrow, top, j0, thr, margin);
-        if (blk == nblk - 1) {
+        if (two) score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
+        else score_block(v, Hs + j0, wrow, top, j0, thr, margin);
+        kb += two ? 2 : 1;
+        if (lastb == nblk - 1) {
           ++gu;
           c = (c + 1 == it.nchunks) ? 0 : c + 1;
         }
