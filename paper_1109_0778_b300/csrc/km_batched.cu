@@ -107,11 +107,14 @@ __global__ void __launch_bounds__(256) b_camax_kernel(BWork W) {
 template <int FP8>
 __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
   constexpr int ESZ = FP8 ? 1 : 2;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g = warp; g < W.KP; g += nwarps) {
-    const int b = find_block(W.kp_off, W.nb, g);
+  __shared__ int s_lh[2][2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // block rounds of 8 consecutive centroids, one warp each
+  for (int64_t base = (int64_t)blockIdx.x * 8, rnd = 0; base < W.KP; base += (int64_t)gridDim.x * 8, ++rnd) {
+    block_instances(W.kp_off, W.nb, base, min(base + 7, W.KP - 1), s_lh[rnd & 1]);
+    const int64_t g = base + wib;
+    if (g >= W.KP) continue;
+    const int b = find_block_in(W.kp_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
     Ctl* ctl = W.ctls + b;
     if (halted(ctl)) continue;
     const BInst& I = W.inst[b];
@@ -212,14 +215,17 @@ __global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
 }
 
 __global__ void __launch_bounds__(256) b_count_kernel(BWork W) {
+  __shared__ int s_lh[2][2];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride) {
+  int rnd = 0;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride, ++rnd) {
+    block_instances(W.row_off, W.nb, base, min(base + (int64_t)blockDim.x - 1, W.R - 1), s_lh[rnd & 1]);
     const int64_t g = base + threadIdx.x;
     bool act = g < W.R;
     int b = 0, j = 0;
     if (act) {
-      b = find_block(W.row_off, W.nb, g);
+      b = find_block_in(W.row_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
       act = !halted(W.ctls + b);
       if (act) j = W.inst[b].assign[g - W.inst[b].row_off];
     }
@@ -276,15 +282,18 @@ __global__ void __launch_bounds__(1024) b_scan_kernel(BWork W) {
 }
 
 __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
+  __shared__ int s_lh[2][2];
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride) {
+  int rnd = 0;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride, ++rnd) {
+    block_instances(W.row_off, W.nb, base, min(base + (int64_t)blockDim.x - 1, W.R - 1), s_lh[rnd & 1]);
     const int64_t g = base + threadIdx.x;
     bool act = g < W.R;
     int b = 0, j = 0;
     int64_t i = 0;
     if (act) {
-      b = find_block(W.row_off, W.nb, g);
+      b = find_block_in(W.row_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
       act = !halted(W.ctls + b);
       if (act) {
         i = g - W.inst[b].row_off;
@@ -307,7 +316,8 @@ __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
 
 // Segmented sums over the flattened sorted positions: each warp walks one
 // contiguous range; the rows are gathered into shared memory with cp.async one
-// batch ahead (as in km_reduce.cu). A batch never crosses an instance
+// batch ahead (as in km_reduce.cu); rows of d <= 16 are packed several per
+// warp step. A batch never crosses an instance
 // boundary and holds as many rows of its instance's width as fit a stage, up
 // to 32. A run may cross instance boundaries, which flush like cluster
 // boundaries. With QM the codes and row statistics of each row are rewritten at
@@ -380,6 +390,60 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
   }
 }
 
+// Rows of d <= 16 (dp = the power of two >= d, 32 / dp rows per step): lane
+// group g = lane / dp takes row r0 + g, lane t = lane % dp its column t. Each
+// lane keeps its own run (cluster cur_j) and flushes it alone.
+template <int QM, typename Flush>
+__device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* st, int lane, int d, int dp,
+                                                const float* C, uint8_t* xq, int kp, int64_t row0, float4* xs_sorted,
+                                                float& s, float& c, float& cj, float& objS, float& objC, int& cur_j,
+                                                Flush&& flush) {
+  const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
+  for (int r0 = 0; r0 < B.bn; r0 += G) {
+    const int r = r0 + g;
+    const bool ok = r < B.bn;
+    const int src = ok ? r : 0;
+    const int j = __shfl_sync(0xffffffffu, B.j, src);
+    float4 xs = make_float4(1.f, 0.f, 0.f, 0.f);
+    if constexpr (QM != 0) {
+      xs.x = __shfl_sync(0xffffffffu, B.xs.x, src);
+      xs.y = __shfl_sync(0xffffffffu, B.xs.y, src);
+      xs.z = __shfl_sync(0xffffffffu, B.xs.z, src);
+      xs.w = __shfl_sync(0xffffffffu, B.xs.w, src);
+    }
+    if (!ok) continue;
+    if (j != cur_j) {
+      flush();
+      cur_j = j;
+      cj = t < d ? C[(int64_t)j * d + t] : 0.f;
+    }
+    const float xr = t < d ? st[r * B.rs + t] : 0.f;
+    kahan_add(s, c, xr);
+    const float df = __fsub_rn(xr, cj);
+    kahan_add(objS, objC, df * df);
+    if constexpr (QM != 0) {
+      const int64_t gp = B.bs + r;  // flattened sorted position
+      const int64_t pr = gp - row0;
+      if (t == 0) xs_sorted[gp] = xs;
+      if (t < d) {
+        if constexpr (QM == 1) {
+          reinterpret_cast<__nv_bfloat16*>(xq)[pr * kp + t] = __float2bfloat16_rn(xr);
+        } else {
+          xq[pr * kp + t] = __nv_fp8_e4m3(xr * pow2_inv(xs.x)).__x;
+        }
+      }
+    }
+  }
+}
+
+// Power of two >= d for the packed rows (d <= 16), 0 otherwise.
+__device__ __forceinline__ int packed_width(int d) {
+  if (d > 16) return 0;
+  int p = 1;
+  while (p < d) p <<= 1;
+  return p;
+}
+
 template <int QM>
 __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
@@ -402,7 +466,8 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
     const BInst& I = W.inst[qw];
     B.d = I.d;
     B.X = I.X;
-    B.rs = 32 * ((B.d + 31) / 32);
+    const int dp = packed_width(B.d);
+    B.rs = dp ? dp : 32 * ((B.d + 31) / 32);
     B.bs = cursor;
     B.bn = (int)min(min((int64_t)min(32, kSegStage / B.rs), W.row_off[qw + 1] - cursor), P1 - cursor);
     cursor += B.bn;
@@ -421,15 +486,15 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
 #pragma unroll
   for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
   float objS = 0.f, objC = 0.f;
-  int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0;
+  int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0, cur_dp = 0;
   int64_t cur_row0 = 0, cur_sum0 = 0;
   const float* cur_C = nullptr;
   uint8_t* cur_xq = nullptr;
-  auto flush = [&]() {
+  auto flush = [&]() {  // this lane's partial sums of run cur_j (packed rows: column lane % cur_dp)
     if (cur_j < 0) return;
 #pragma unroll
     for (int v = 0; v < kMaxV; ++v) {
-      const int t = v * 32 + lane;
+      const int t = cur_dp ? (v == 0 ? (lane & (cur_dp - 1)) : cur_d) : v * 32 + lane;
       if (t < cur_d) atomicAdd(W.sums64 + cur_sum0 + (int64_t)cur_j * cur_d + t, (double)s[v] - (double)c[v]);
       s[v] = 0.f;
       c[v] = 0.f;
@@ -471,6 +536,7 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
         const BInst* I = W.inst + b;
         // the instance's fields in registers (the code stores below may alias them)
         cur_d = I->d;
+        cur_dp = packed_width(cur_d);
         cur_kp = I->Kp;
         cur_row0 = I->row_off;
         cur_sum0 = I->sum_off;
@@ -478,7 +544,10 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
         cur_xq = W.Xq + I->xq_off;
       }
       const int d = cur_d;
-      if (d <= 32)
+      if (cur_dp)
+        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s[0], c[0], cj[0],
+                            objS, objC, cur_j, flush);
+      else if (d <= 32)
         seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
                         flush);
       else if (d <= 64)
@@ -499,11 +568,14 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
 // Divide per centroid of every instance; the warp that finishes an instance's
 // last centroid records its step statistics and evaluates its stop rule.
 __global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t g = gw; g < W.KC; g += nw) {
-    const int b = find_block(W.kc_off, W.nb, g);
+  __shared__ int s_lh[2][2];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // block rounds of 8 consecutive centroids, one warp each
+  for (int64_t base = (int64_t)blockIdx.x * 8, rnd = 0; base < W.KC; base += (int64_t)gridDim.x * 8, ++rnd) {
+    block_instances(W.kc_off, W.nb, base, min(base + 7, W.KC - 1), s_lh[rnd & 1]);
+    const int64_t g = base + wib;
+    if (g >= W.KC) continue;
+    const int b = find_block_in(W.kc_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
     Ctl* ctl = W.ctls + b;
     if (halted(ctl)) continue;
     const BInst& I = W.inst[b];

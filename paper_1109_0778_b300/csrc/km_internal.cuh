@@ -216,6 +216,26 @@ __device__ __forceinline__ int find_block(const int64_t* off, int nb, int64_t g)
   return lo;
 }
 
+// find_block restricted to the instances lo..hi (off[lo] <= g < off[hi + 1]).
+__device__ __forceinline__ int find_block_in(const int64_t* off, int lo, int hi, int64_t g) {
+  int l = lo, h = hi + 1;
+  while (h - l > 1) {
+    const int mid = (l + h) >> 1;
+    if (off[mid] <= g) l = mid;
+    else h = mid;
+  }
+  return l;
+}
+
+// Instances of the first and last element a block works on this round (two
+// threads search the whole table, the block's threads then search only that
+// range). s_lh: two ints of shared memory; contains a barrier.
+__device__ __forceinline__ void block_instances(const int64_t* off, int nb, int64_t first, int64_t last, int* s_lh) {
+  if (threadIdx.x == 0) s_lh[0] = find_block(off, nb, first);
+  if (threadIdx.x == 32) s_lh[1] = find_block(off, nb, last);
+  __syncthreads();
+}
+
 cudaError_t init_batched();
 // keyed-reduce training (km_classes.cu)
 cudaError_t launch_check_classes(const int32_t* y, int64_t n, int ncls, Ctl* ctl, cudaStream_t s);

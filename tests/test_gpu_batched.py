@@ -56,6 +56,24 @@ def test_batched_single_step_parity(km, ref, precision):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_small_d_parity(km, ref, precision):
+    """Rows of d <= 16 are packed several per warp step in the segmented sum (d = 1 ... 16,
+    powers of two and not, mixed with unpacked instances)."""
+    shapes = [(2000, 3, 9), (1111, 13, 20), (640, 16, 33), (800, 5, 6), (999, 2, 4), (1500, 24, 11), (700, 9, 70)]
+    data = make_batch(shapes, seed0=4100)
+    probs = to_device(km, data)
+    stats = km.run_batched(probs, 2, precision=precision)
+    # one more step from the result, checked against the oracle's step from the same centroids
+    C_ins = [p[1].cpu().numpy().astype(np.float64) for p in probs]
+    stats = km.run_batched(probs, 1, precision=precision, warm_start=True)
+    for (X, _), (Xd, Cd, a, s, c), C_in, st in zip(data, probs, C_ins, stats):
+        ag = a.cpu().numpy()
+        parity.check_assign(ref, X, C_in, ag)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
+        parity.check_objective(ref, X, C_in, ag, st["objective"])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_batched_warm_steps_parity(km, ref, precision):
     """Steps after the first pass the previous assignment in (warm start), one step per call."""
     data = make_batch(SHAPES, seed0=900)
