@@ -1084,6 +1084,7 @@ struct BatchPlan {
   std::vector<int> order;  // flattened position -> caller's instance index
   std::vector<BInst> inst;
   std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
+  std::vector<int64_t> seg_off;   // prefix sums of the segmented sum's row costs
   std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
   int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
   int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0;
@@ -1106,6 +1107,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
   P.kc_off.assign(count + 1, 0);
   P.kp_off.assign(count + 1, 0);
   P.tile_off.assign(count + 1, 0);
+  P.seg_off.assign(count + 1, 0);
   for (int q = 0; q < count; ++q) {
     const km_instance& s = in[P.order[q]];
     BInst& I = P.inst[q];
@@ -1144,6 +1146,8 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.kc_off[q + 1] = P.KC;
     P.kp_off[q + 1] = P.KP;
     P.tile_off[q + 1] = P.T;
+    // a row of the segmented sum costs about its bytes: the FP32 row, its codes, labels and statistics
+    P.seg_off[q + 1] = P.seg_off[q] + s.n * (int64_t)(4 * s.d + esz * s.d + 40);
     P.nkb_max = std::max(P.nkb_max, I.nkb);
     P.kp_max = std::max(P.kp_max, I.kp);
   }
@@ -1209,8 +1213,8 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 
 // Byte offsets of the batch workspace.
 struct BLayout {
-  size_t ctl, inst, row, kc, kp, tile, cta, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq, xq,
-      cq, csave, hist, total;
+  size_t ctl, inst, row, kc, kp, tile, seg, cta, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq,
+      xq, cq, csave, hist, total;
 };
 
 BLayout batch_layout(const BatchPlan& P, int iters) {
@@ -1229,6 +1233,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.kc = take(8 * (nb + 1));
   L.kp = take(8 * (nb + 1));
   L.tile = take(8 * (nb + 1));
+  L.seg = take(8 * (nb + 1));
   L.cta = take(8 * P.cta_tile.size());
   L.maps = take(sizeof(CUtensorMap) * 2 * nb, 128);
   L.slots = take(8);
@@ -1299,6 +1304,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.kc_off = (const int64_t*)(B + o_kc);
   W.kp_off = (const int64_t*)(B + o_kp);
   W.tile_off = (const int64_t*)(B + o_tile);
+  W.seg_off = (const int64_t*)(B + BL.seg);
   W.cta_tile = (const int64_t*)(B + BL.cta);
   W.cta_grid = (int)P.cta_tile.size() - 1;
   W.R = P.R;
@@ -1340,6 +1346,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   KM_CUDA(cudaMemcpyAsync(B + o_kc, P.kc_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_kp, P.kp_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.seg_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));

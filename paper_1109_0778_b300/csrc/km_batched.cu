@@ -451,7 +451,16 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
   float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
   float* stage1 = stage0 + kSegStage;
   const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
-  const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
+  // this warp's positions: an equal share of the total row cost (rows of larger d cost more)
+  auto pos_at = [&](int64_t t) -> int64_t {
+    const int64_t T = W.seg_off[W.nb];
+    if (t >= T) return W.R;
+    const int b = find_block(W.seg_off, W.nb, t);
+    const int64_t per = (W.seg_off[b + 1] - W.seg_off[b]) / (W.row_off[b + 1] - W.row_off[b]);
+    return W.row_off[b] + (t - W.seg_off[b] + per - 1) / per;
+  };
+  const int64_t Tc = W.seg_off[W.nb];
+  const int64_t P0 = pos_at((int64_t)((double)Tc * gw / nw)), P1 = pos_at((int64_t)((double)Tc * (gw + 1) / nw));
 
   // batch cursor: batches are cut in increasing order, the instance found by walking forward
   int64_t cursor = P0;
