@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <functional>
 #include <initializer_list>
 #include <mutex>
 #include <string>
@@ -189,9 +190,13 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, total;
   int64_t fq_cap;
+  int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
+
+// E4M3 runs re-score queued points with BF16 codes on the tensor cores when that shape fits.
+bool rescore16(int precision, int d, int k) { return precision == KM_FP8E4M3 && tc_shape(KM_BF16, d, k).stages >= 2; }
 
 // Rows the re-check queue of the quantised paths holds: an eighth of the points
 // (at least 4096, at most n); further unresolved points are settled one by one.
@@ -244,7 +249,21 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
     const int width = simt_slab_width(d);  // the queued rows' FP32 pass may carry state across slabs
     L.state = (width > 0 && width < k) ? take(16 * (size_t)L.fq_cap) : 0;
     L.state3 = (width > 0 && width < k) ? take(4 * (size_t)L.fq_cap) : 0;
+    if (rescore16(precision, d, k)) {
+      const TcShape t16 = tc_shape(KM_BF16, d, k);
+      L.Kp16 = t16.Kp;
+      L.xq16 = take((size_t)L.fq_cap * t16.Kp * 2);
+      L.xs16q = take(16 * (size_t)L.fq_cap);
+      L.cq16 = take((size_t)t16.kp * t16.Kp * 2);
+      L.hq16 = take(4 * (size_t)t16.kp);
+      L.scq16 = take(4 * (size_t)t16.kp);
+    } else {
+      L.Kp16 = 0;
+      L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
+    }
   } else {
+    L.Kp16 = 0;
+    L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;  // also serves the re-check pass
@@ -323,6 +342,9 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.X_sub = L.X_sub ? (float*)(b + L.X_sub) : nullptr;
   w.xn_sub = L.xn_sub ? (float*)(b + L.xn_sub) : nullptr;
   w.flags2 = L.flags2 ? (FlagRec*)(b + L.flags2) : nullptr;
+  w.Xq16 = L.xq16 ? (uint8_t*)(b + L.xq16) : nullptr;
+  w.xs16q = L.xs16q ? (float4*)(b + L.xs16q) : nullptr;
+  w.Kp16 = L.Kp16;
   return w;
 }
 
@@ -369,6 +391,13 @@ struct StepCfg {
   TcShape t0;
   TcLaunch L0;
   TcParams P0;
+  // E4M3 runs: BF16 re-score of the queued points (centroid codes Cq16 / hq16 / scq16)
+  bool rs16;
+  TcShape t16;
+  TcLaunch L16;
+  TcParams P16;
+  uint8_t* Cq16;
+  float *hq16, *scq16;
 };
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -467,7 +496,21 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   }
   if (e) return e;
   if ((e = at(2))) return e;
-  if (cfg.recheck && (e = launch_recheck(p, w, tcp ? w.hq : w.chalf, first, s))) return e;
+  if (cfg.recheck) {
+    std::function<cudaError_t(cudaStream_t)> tc16;
+    if (cfg.rs16 && !cold)
+      tc16 = [&](cudaStream_t st) {
+        const TcShape& t16 = cfg.t16;
+        cudaError_t r = launch_quant_c(p, w, 0, t16.kp, t16.Kp, cfg.Cq16, cfg.hq16, cfg.scq16, st, true);
+        if (r != cudaSuccess) return r;
+        Problem q = p;
+        q.n = w.fq_cap;
+        TcParams P = cfg.P16;
+        P.first = first;
+        return launch_assign_tc(q, cfg.L16, P, st);
+      };
+    if ((e = launch_recheck(p, w, tcp ? w.hq : w.chalf, first, s, tc16))) return e;
+  }
   if ((e = at(3))) return e;
   if ((e = launch_count(p, w, s))) return e;
   if ((e = at(4))) return e;
@@ -610,6 +653,34 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     KM_TRACE("main shape Kp=%d nkb=%d bn=%d kp=%d stages=%d abufs=%d cold=%d\n", cfg.t.Kp, cfg.t.nkb, cfg.t.bn,
              cfg.t.kp, cfg.t.stages, cfg.t.abufs, (int)cfg.cold);
     if (cfg.cold && (rc = fill_tc(KM_BF16, w.xs16, cfg.t0, cfg.L0, cfg.P0))) return rc;
+    cfg.rs16 = w.Xq16 != nullptr;
+    if (cfg.rs16) {
+      // BF16 re-score of the queued points: codes of the gathered rows (Xq16, row r = point
+      // fq_rows[r]), this step's BF16 centroid codes, its own flag list and statistics
+      if ((rc = fill_tc(KM_BF16, w.xs16q, cfg.t16, cfg.L16, cfg.P16))) return rc;
+      char* wb = (char*)c->ws;
+      cfg.Cq16 = (uint8_t*)(wb + L.cq16);
+      cfg.hq16 = (float*)(wb + L.hq16);
+      cfg.scq16 = (float*)(wb + L.scq16);
+      if ((rc = encode_codes_map(&cfg.L16.mapX, w.Xq16, w.fq_cap, cfg.t16.Kw, cfg.t16.esz, 128))) return rc;
+      if ((rc = encode_codes_map(&cfg.L16.mapC, cfg.Cq16, cfg.t16.kp, cfg.t16.Kw, cfg.t16.esz, cfg.t16.bn)))
+        return rc;
+      TcParams& Q = cfg.P16;
+      Q.h = cfg.hq16;
+      Q.sc = cfg.scq16;
+      Q.Cq = cfg.Cq16;
+      Q.rows = w.fq_rows;
+      Q.xs_sorted = w.xs16q;
+      Q.lab_sorted = w.fq_old;
+      Q.flags = w.flags2;
+      Q.flag_slots = &w.ctl->n_flagged2;
+      Q.flag_cap = w.fq_cap;
+      Q.n = w.fq_cap;
+      Q.n_dev = &w.ctl->n_fullq;
+      Q.stats16 = 1;
+      Q.debug_stall = 0;
+      Q.wait_ns = 2000000000ull;
+    }
     if (cfg.cold)
       KM_TRACE("cold shape Kp=%d nkb=%d bn=%d kp=%d stages=%d abufs=%d\n", cfg.t0.Kp, cfg.t0.nkb, cfg.t0.bn,
                cfg.t0.kp, cfg.t0.stages, cfg.t0.abufs);

@@ -129,7 +129,7 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.b = 0;
     it.tile0 = 0;
     it.tend = INT64_MAX;
-    it.n = P.n;
+    it.n = P.n_dev ? min(P.n, (int64_t)*P.n_dev) : P.n;
     it.k = P.k;
     it.Kp = P.Kp;
     it.nkb = P.nkb;
@@ -180,7 +180,7 @@ struct TileRange {
 template <bool BATCH>
 __device__ __forceinline__ TileRange tile_range(const TcParams& P) {
   if constexpr (BATCH) return TileRange{P.bcta[blockIdx.x], P.bcta[blockIdx.x + 1], 1};
-  else return TileRange{blockIdx.x, (P.n + BM - 1) / BM, gridDim.x};
+  else return TileRange{blockIdx.x, ((P.n_dev ? min(P.n, (int64_t)*P.n_dev) : P.n) + BM - 1) / BM, gridDim.x};
 }
 
 // Moves `it` to the instance of flattened tile gt (tiles are visited in
@@ -593,8 +593,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           const Ctl* ctl = it.ctl;
           H = __uint_as_float(ctl->hmax_bits);
           Cmax = __uint_as_float(ctl->cmax_bits);
-          QCmax = __uint_as_float(ctl->qcmax_bits);
-          DCmax = __uint_as_float(ctl->dcmax_bits);
+          QCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->qcmax16_bits : ctl->qcmax_bits);
+          DCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->dcmax16_bits : ctl->dcmax_bits);
           if (FP8) csc = __ldg(it.sc);  // the same for every centroid of the step
         }
       }
@@ -700,7 +700,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           if (lane == leader) {
             slot = atomicAdd(P.flag_slots, (unsigned long long)__popc(fm));
             if (BATCH) atomicAdd(&it.ctl->n_flagged, (unsigned long long)__popc(fm));
-            if (fullm) atomicAdd(&it.ctl->n_full, (unsigned long long)__popc(fullm));
+            if (fullm && (BATCH || !P.n_dev))  // a re-check pass does not count its points again
+              atomicAdd(&it.ctl->n_full, (unsigned long long)__popc(fullm));
           }
           slot = __shfl_sync(0xffffffffu, slot, leader) + __popc(fm & ((1u << lane) - 1u));
         }

@@ -3,6 +3,8 @@
 // helpers. Nothing here is part of the C ABI (include/kmeans.h).
 #pragma once
 
+#include <functional>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,6 +33,8 @@ struct Ctl {
   unsigned int qcmax_bits;         // max_j ||c~_j|| of the quantised centroids (rounded up)
   unsigned int dcmax_bits;         // max_j ||c~_j - c_j|| (quantisation residual, rounded up)
   unsigned int camax_bits;         // max_{j,t} |c_jt| (FP32 bits): sets the E4M3 centroid scale
+  unsigned int qcmax16_bits;       // the same two maxima for the BF16 codes of an E4M3 run's
+  unsigned int dcmax16_bits;       //   re-check pass (queued points re-scored with BF16)
   int n_empty;
   unsigned int blocks_done;        // last-block detection in the divide stage
   // ---- per run (cleared once) ----
@@ -89,6 +93,10 @@ struct Work {
   float* X_sub;        // [fq_cap][d] gathered rows
   float* xn_sub;       // [fq_cap] ||x|| bounds of the gathered rows
   FlagRec* flags2;     // [fq_cap] points the tiled FP32 pass leaves flagged
+  // E4M3 runs re-score the queued points with BF16 codes on the tensor cores
+  uint8_t* Xq16;       // [fq_cap][Kp16] BF16 codes of the gathered rows (null: tiled FP32 pass)
+  float4* xs16q;       // [fq_cap] their row statistics
+  int Kp16;            // BF16 code row width
 };
 
 // Row map of an FP32 assignment pass over gathered rows: row r of X is point
@@ -118,6 +126,8 @@ struct TcParams {
   int64_t n;
   int k, Kp, nkb, bn, nchunks, stages, abufs, first;
   uint32_t idesc;
+  const unsigned long long* n_dev;  // non-null: the rows are the first min(n, *n_dev) (re-check pass)
+  int stats16;        // read the code statistics of the BF16 re-check codes (qcmax16, dcmax16)
   int split;          // two-part BF16 codes: a row holds nkb / 2 blocks of hi, then as many of lo;
                       // x.c = hi.hi + lo.hi + hi.lo (single launches only)
   float gam_tc;       // coefficient of ||x~|| max ||c~|| in the contraction's error bound
@@ -276,7 +286,8 @@ cudaError_t launch_prep(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_assign_simt(const Problem& p, const Work& w, int first, cudaStream_t s);
 // FP32 assignment of the queued rows of the re-check stage (quantised paths); h = h_j of C.
 cudaError_t launch_assign_simt_sub(const Problem& p, const Work& w, const float* h, cudaStream_t s);
-cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s);
+cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s,
+                           const std::function<cudaError_t(cudaStream_t)>& tc16 = nullptr);
 cudaError_t launch_count(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
@@ -289,8 +300,9 @@ cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, ui
                            cudaStream_t s);
 cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
                                 cudaStream_t s);
+// stats16: the code statistics go to qcmax16 / dcmax16 (BF16 re-check codes of an E4M3 run)
 cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
-                           float* sc, cudaStream_t s);
+                           float* sc, cudaStream_t s, bool stats16 = false);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs);

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C,
 template <int MODE>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
-               float* __restrict__ hq, float* __restrict__ scq, int32_t* __restrict__ counts, Ctl* ctl) {
+               float* __restrict__ hq, float* __restrict__ scq, int32_t* __restrict__ counts, Ctl* ctl,
+               int stats16) {
   constexpr int FP8 = MODE == 1;
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
@@ -202,11 +203,11 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
       hq[j] = h;
       scq[j] = sc;
-      counts[j] = 0;
+      if (counts) counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
       atomic_max_nonneg(&ctl->cmax_bits, cn);
-      atomic_max_nonneg(&ctl->qcmax_bits, qn);
-      atomic_max_nonneg(&ctl->dcmax_bits, dn);
+      atomic_max_nonneg(stats16 ? &ctl->qcmax16_bits : &ctl->qcmax_bits, qn);
+      atomic_max_nonneg(stats16 ? &ctl->dcmax16_bits : &ctl->dcmax_bits, dn);
     }
   }
 }
@@ -234,20 +235,21 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
 }
 
 cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
-                           float* sc, cudaStream_t s) {
+                           float* sc, cudaStream_t s, bool stats16) {
+  int32_t* counts = stats16 ? nullptr : p.counts;  // the re-check codes leave the counts alone
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (mode == 2) {
-    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
   } else if (mode == 1) {
     const int64_t kd = (int64_t)p.k * p.d;
     int mb = (int)((kd + 255) / 256);
     if (mb > num_sms() * 4) mb = num_sms() * 4;
     camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, w.ctl);
-    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
   } else {
-    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, p.counts, w.ctl);
+    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
   }
   return cudaGetLastError();
 }

@@ -4,6 +4,9 @@
 // stage) is evaluated directly; otherwise all k centroids are screened with
 // plain FP32 scores and a rigorous bound first (km_recheck.cuh). The
 // distances, the tie rule and the error argument are those of km_recheck.cuh.
+#include <functional>
+
+#include "km_quant.cuh"
 #include "km_recheck.cuh"
 
 namespace km {
@@ -72,10 +75,14 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
 
 // Copies the queued rows into X_sub and their norm bounds (xs.w on the
 // quantised paths, xnorm on the FP32 path) into xn_sub; one warp per row.
+// With Xq16 (E4M3 runs) it also writes each row's BF16 codes (Kp16 columns,
+// zero padded) and their statistics (1, ||x~||, ||x~ - x||, ||x||) for the
+// tensor-core re-score, as the BF16 quantisation stage does.
 __global__ void __launch_bounds__(256)
 gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict__ xs,
                     const float* __restrict__ xnorm, const Ctl* ctl, const int32_t* __restrict__ q_rows,
-                    int64_t q_cap, float* __restrict__ X_sub, float* __restrict__ xn_sub) {
+                    int64_t q_cap, float* __restrict__ X_sub, float* __restrict__ xn_sub, uint8_t* __restrict__ Xq16,
+                    float4* __restrict__ xs16q, int Kp16) {
   if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -87,6 +94,21 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
     float* y = X_sub + r * d;
     for (int t = lane; t < d; t += 32) y[t] = x[t];
     if (lane == 0) xn_sub[r] = xs ? xs[i].w : xnorm[i];
+    if (Xq16) {
+      float sxx = 0.f, sqq = 0.f, sdd = 0.f;
+      uint8_t* row = Xq16 + r * (int64_t)Kp16 * 2;
+      for (int t = lane; t < Kp16; t += 32) {
+        const float v = t < d ? x[t] : 0.f;
+        const float vq = quantise<0>(v, 1.f, 1.f, row + 2 * t);
+        sxx = fmaf(v, v, sxx);
+        sqq = fmaf(vq, vq, sqq);
+        sdd = fmaf(vq - v, vq - v, sdd);
+      }
+      sxx = warp_sum(sxx);
+      sqq = warp_sum(sqq);
+      sdd = warp_sum(sdd);
+      if (lane == 0) xs16q[r] = make_float4(1.f, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+    }
   }
 }
 
@@ -123,18 +145,23 @@ cudaError_t recheck_pass(const Problem& p, const Work& w, const float* h, const 
 // each centroid tile read once per 128 points), which this time keeps the best
 // two candidates and the third-best score: a point whose third score lies
 // outside the margin is settled between its two candidates, the few others by
-// compensated distances against all k. (The FP32 path's own flags come from
+// compensated distances against all k. E4M3 runs instead re-score the queued
+// points with BF16 codes on the tensor cores (tc16: a margin ~16 x tighter
+// than E4M3's), then settle the short lists. (The FP32 path's own flags come from
 // that kernel's top-two pass, so all of them take this route when d allows the
 // slab kernel.)
-cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s) {
+cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int first, cudaStream_t s,
+                           const std::function<cudaError_t(cudaStream_t)>& tc16) {
   (void)first;  // the stored old label is -1 in a call's first step
   const bool queue = w.fq_rows != nullptr;
   cudaError_t e = recheck_pass(p, w, h, w.flags, &w.ctl->n_flagged, queue, s);
   if (e != cudaSuccess || !queue) return e;
   gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xs, w.xnorm, w.ctl, w.fq_rows, w.fq_cap, w.X_sub,
-                                                    w.xn_sub);
+                                                    w.xn_sub, tc16 ? w.Xq16 : nullptr, w.xs16q, w.Kp16);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = launch_assign_simt_sub(p, w, h, s)) != cudaSuccess) return e;
+  if (tc16) e = tc16(s);  // E4M3 runs: BF16 codes on the tensor cores, then the short lists
+  else e = launch_assign_simt_sub(p, w, h, s);
+  if (e != cudaSuccess) return e;
   return recheck_pass(p, w, h, w.flags2, &w.ctl->n_flagged2, false, s);
 }
 
