@@ -363,6 +363,25 @@ def test_warm_start_ignores_bad_labels(km, ref):
         parity.check_assign(ref, X, C_in, out.assign.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", ["fp8", "bf16"])
+def test_queued_points_rescored(km, ref, precision):
+    """Centroids duplicated nine times: every point has nine equal candidates (more than the eight
+    slots), so it is queued, re-scored (E4M3 runs: BF16 codes on the tensor cores; BF16 runs: the
+    FP32 slab kernel), still tied, and settled over all k with the lowest index."""
+    X = synth.mixture(61, 20000, 48, 12, 6.0, 1.0)
+    base = X[:12].copy()
+    C0 = np.repeat(base, 9, axis=0)  # centroid 9 q + r is a copy of point q
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(C0).to(DEV)
+    a, s, c = km.alloc_outputs(Xd, Cd)
+    a.copy_(torch.from_numpy(np.zeros(20000, np.int32)))
+    out = km.step(Xd, Cd, a, s, c, precision=precision, warm_start=True)
+    assert out.stats["n_full"] > 0
+    ag = out.assign.cpu().numpy()
+    parity.check_assign(ref, X, C0.astype(np.float64), ag)
+    assert np.all(ag % 9 == 0)  # the lowest index of each tied group
+
+
 def test_tc_recheck_off_still_runs(km):
     X = synth.mixture(3, 5000, 32, 20, 5.0, 1.0)
     Xd = torch.from_numpy(X).to(DEV)
