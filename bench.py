@@ -327,6 +327,7 @@ def run_batched(args, torch, dev, dist, rank, world, local):
     barrier(dist)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     call_ms = 0.0
+    launches_tot = 0
     stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
     with ClockSampler(local) as clk:
         ev0.record(stream)
@@ -336,6 +337,7 @@ def run_batched(args, torch, dev, dist, rank, world, local):
             for si, kname in enumerate(km.STAGES):
                 stage_tot[kname] += float(st["stage_ms"][0][si])
             flagged = (int(st["n_flagged"].sum()), int(st["n_full"].sum()))
+            launches_tot += int(st["launches"][0])
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(dist)
@@ -363,6 +365,7 @@ def run_batched(args, torch, dev, dist, rank, world, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "kernel": "whole batched step",
                          "note": "algorithmic bytes = one FP32 read of every X per iteration", "traffic": None},
+            "gpu_launches": launches_tot,
             "clocks": clocks, "e2e": None, "cpu_baseline": None, "peaks_source": peak_src,
         }
         print(json.dumps(line), flush=True)
@@ -488,6 +491,9 @@ def run_training(args, torch, dev, dist, rank, world, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "kernel": "whole training call",
                          "note": f"algorithmic bytes = {passes} FP32 read(s) of X + labels", "traffic": None},
+            # per call: label check, count, scan, scatter, segmented sum (+ means, covariance tiles and
+            # their reduction for GDA; the smoothed distributions for NB)
+            "gpu_launches": args.steps * (8 if tw["kind"] == "gda" else 6),
             "clocks": clk.summary(), "e2e": None, "cpu_baseline": cpu, "peaks_source": peak_src,
         }
         print(json.dumps(line), flush=True)
@@ -641,6 +647,7 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
     flagged = []
+    launches_tot = 0  # kernel launches the library reports (kernel nodes of the captured graph + 1)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize(dev)
         barrier(dist)
@@ -650,6 +657,7 @@ def run_ours(args):
             for kname, v in out.stats["stage_ms"].items():
                 stage_tot[kname] += v
             flagged.append(out.stats["n_flagged"])
+            launches_tot += out.stats["launches"]
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(dist)
@@ -739,7 +747,7 @@ def run_ours(args):
             "roofline": roof, "stage_ms_per_iter": stage_share,
             "flagged_per_step_last_iter": flagged[-1] if flagged else None,
             "clocks": clocks, "e2e": e2e, "precision_variants": variants, "split_bf16_same_workload": split,
-            "gpu_launches": args.steps * (1 + len(STAGE_KERNELS) * iters),
+            "gpu_launches": launches_tot,
             "cpu_baseline": cpu,
             "peaks_source": peak_src,
         }

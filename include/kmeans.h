@@ -116,7 +116,8 @@ typedef struct {
   int32_t n_empty;      /* empty clusters after the last step */
   int32_t iters_done;   /* Lloyd steps executed */
   float ms;             /* device time of the call (CUDA events) */
-  int32_t reserved;
+  int32_t launches;     /* kernel launches of the call when its steps run as one
+                           captured graph (iters > 1), else 0 */
   float stage_ms[12];   /* with opts->profile: device time per stage summed
                            over the call's steps (KM_STAGE_*), else zeros */
 } km_stats;

@@ -95,6 +95,7 @@ struct DevCtx {
   void* host = nullptr;   // pinned read-back of Ctl and the per-step history
   size_t host_bytes = 0;
   bool graph_valid = false;
+  int graph_kernels = 0;  // kernel nodes of the cached graph
   GraphKey gkey{};
   cudaGraphExec_t gexec = nullptr;
   std::vector<cudaEvent_t> prof;  // stage-boundary events of profiled calls
@@ -529,6 +530,22 @@ const cudaEvent_t* step_events(DevCtx* c, bool profile, int it) {
   return profile ? c->prof.data() + 2 + (size_t)it * kEvPerStep : nullptr;
 }
 
+// Kernel nodes of a captured graph (the launches one replay makes).
+int kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  int k = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+      for (size_t i = 0; i < nn; ++i) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+      }
+  }
+  cudaGetLastError();
+  return k;
+}
+
 int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, const StepCfg& cfg, int iters,
               double tol, bool profile, cudaGraphExec_t* out) {
   if (c->graph_valid && c->gkey == key) {
@@ -551,6 +568,7 @@ int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, c
     cudaGetLastError();
     return fail(KM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e ? e : e2));
   }
+  c->graph_kernels = kernel_nodes(g);
   e = cudaGraphInstantiate(&c->gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -700,6 +718,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     KM_CUDA(r);
   }
   if (profile) KM_CUDA(cudaEventRecord(c->prof[1], s));
+  int launches = 0;
   if (graph && iters > 1 && !debug_sync()) {
     GraphKey key;
     memset(&key, 0, sizeof key);
@@ -711,6 +730,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     cudaGraphExec_t ge = nullptr;
     if ((rc = get_graph(c, key, p, w, cfg, iters, tol, profile, &ge))) return rc;
     KM_CUDA(cudaGraphLaunch(ge, s));
+    launches = 1 + c->graph_kernels;  // the point-norm / quantisation kernel, then the graph
   } else {
     for (int it = 0; it < iters; ++it)
       KM_CUDA(enqueue_step(p, w, cfg, it == 0 && !cfg.warm, it > 0, tol, s, step_events(c, profile, it)));
@@ -749,6 +769,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     memset(st, 0, sizeof *st);
     const int last = hc->iters_done - 1;
     st->iters_done = hc->iters_done;
+    st->launches = launches;
     if (last >= 0) {
       st->objective = hobj[last];
       st->shift = hshift[last];
@@ -1259,6 +1280,7 @@ struct BatchCtx {
   void* host = nullptr;
   size_t host_bytes = 0;
   cudaGraphExec_t gexec = nullptr;
+  int graph_kernels = 0;  // kernel nodes of the cached graph
   std::vector<unsigned char> gkey;
   std::vector<BatchCache> tuned;
 };
@@ -1486,6 +1508,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
       cudaGetLastError();
       return fail(KM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e ? e : e2));
     }
+    bc.graph_kernels = kernel_nodes(g);
     e = cudaGraphInstantiate(&bc.gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -1562,6 +1585,8 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
         st.n_empty = he[h];
       }
       st.ms = ms;
+      st.launches = 1 + bc.graph_kernels;  // the whole batch's launches (point quantisation + graph),
+                                           // reported for every instance
       memcpy(st.stage_ms, stage_ms, sizeof stage_ms);
     }
   }

@@ -60,10 +60,10 @@ class Stats(ctypes.Structure):
                 ("n_changed", ctypes.c_int64), ("n_flagged", ctypes.c_int64),
                 ("n_full", ctypes.c_int64), ("n_empty", ctypes.c_int32),
                 ("iters_done", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12)]
+                ("launches", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "stage_ms")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "stage_ms"}
         d["stage_ms"] = {name: float(self.stage_ms[i]) for i, name in enumerate(STAGES)}
         return d
 
