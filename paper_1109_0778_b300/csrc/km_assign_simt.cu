@@ -329,7 +329,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = dp + 4;             // floats per staged point row
-  float* Cs = smem;                          // [dp][nsp]
+  float* Cs = smem;                          // [nsp / BN][dp][BN]: per chunk, K rows BN floats apart
   float* Hs = Cs + (size_t)dp * nsp;         // [nsp]
   float* Xs0 = Hs + nsp;                     // 2 x [BM][xs_stride]
   __shared__ unsigned int s_changed;
@@ -338,7 +338,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   // slab of centroids, transposed; zero padding in [d, dp) and [ns, nsp)
   for (int e = tid; e < dp * nsp; e += ST) {
     const int j = e % nsp, t = e / nsp;
-    Cs[e] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
+    Cs[((size_t)(j / BN) * dp + t) * BN + (j % BN)] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
   }
   for (int j = tid; j < nsp; j += ST) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
   // zero both point buffers once: padding columns [d, dp) and rows past n stay zero
@@ -383,6 +383,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
       }
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
+      const float* Cc = Cs + (size_t)(j0 / BN) * dp * BN;  // this chunk's [dp][BN] block
       float2 acc2[SR][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
 #pragma unroll
       for (int r = 0; r < SR; ++r)
@@ -397,7 +398,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           float2 b2[4];
-          const float* cr = Cs + (size_t)(kk + q) * nsp + j0;
+          const float* cr = Cc + (kk + q) * BN;
           const float4 b0 = *reinterpret_cast<const float4*>(cr + tx * 4);
           const float4 b1 = *reinterpret_cast<const float4*>(cr + 64 + tx * 4);
           b2[0] = make_float2(b0.x, b0.y); b2[1] = make_float2(b0.z, b0.w);
