@@ -32,7 +32,14 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, PAD = 4;
 constexpr int THREADS = 256;
-constexpr int ST = 512, SR = 4;  // slab kernel: 512 threads, 4 rows x 8 columns each (16 warps per SM)
+constexpr int SR = 4;  // slab kernel: 4 rows x 8 columns of scores per thread
+// Slab kernel geometries: G = 0, 512 threads on 128-row tiles, one CTA per SM
+// (the largest slab); G = 1, 256 threads on 64-row tiles, two CTAs per SM (half
+// the slab each; their barriers and epilogues no longer line up).
+template <int G>
+struct SlabGeo {
+  static constexpr int T = G ? 256 : 512, M = G ? 64 : 128, CTAS = G ? 2 : 1;
+};
 __device__ __forceinline__ int srow_of(int ty, int r) { return ty * 4 + r; }
 
 __device__ __forceinline__ int row_of(int ty, int r) { return r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4); }
@@ -293,18 +300,19 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Issues the copies of point tile `tile` (rows of d floats) into Xs (row stride xs_stride floats).
-template <bool V16>
+template <bool V16, int G>
 __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const float* __restrict__ X, int64_t n,
                                                 int d, int64_t tile) {
-  const int64_t m0 = tile * BM;
+  constexpr int SBM = SlabGeo<G>::M, ST = SlabGeo<G>::T;
+  const int64_t m0 = tile * SBM;
   if (V16) {
     const int per_row = d >> 2;
-    for (int e = threadIdx.x; e < BM * per_row; e += ST) {
+    for (int e = threadIdx.x; e < SBM * per_row; e += ST) {
       const int r = e / per_row, c4 = e - r * per_row;
       if (m0 + r < n) cp_async16(Xs + r * xs_stride + 4 * c4, X + (m0 + r) * d + 4 * c4);
     }
   } else {
-    for (int e = threadIdx.x; e < BM * d; e += ST) {
+    for (int e = threadIdx.x; e < SBM * d; e += ST) {
       const int r = e / d, c = e - r * d;
       if (m0 + r < n) cp_async4(Xs + r * xs_stride + c, X + (m0 + r) * d + c);
     }
@@ -315,23 +323,24 @@ __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const 
 // third-best score are kept, and a flagged row whose third-best score lies
 // outside the margin is recorded with its two candidates; the third-best
 // score crosses slabs in state3.
-template <bool V16, bool T3>
-__global__ void __launch_bounds__(ST, 1)
+template <bool V16, bool T3, int G>
+__global__ void __launch_bounds__(SlabGeo<G>::T, SlabGeo<G>::CTAS)
 assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
                    int32_t* __restrict__ assign, FlagRec* __restrict__ flags, float4* __restrict__ state,
                    float* __restrict__ state3, int first, int first_slab, int last_slab, float gam,
                    const SubRows sr) {
   using TopT = typename std::conditional<T3, Top3s, Top2>::type;
+  constexpr int ST = SlabGeo<G>::T, SBM = SlabGeo<G>::M;
   if (halted(ctl)) return;
   if (sr.n_dev) n = min(n, (int64_t)*sr.n_dev);  // gathered rows of the re-check stage (n = capacity)
-  if ((int64_t)blockIdx.x * BM >= n) return;    // no tile for this CTA: skip the slab load
+  if ((int64_t)blockIdx.x * SBM >= n) return;    // no tile for this CTA: skip the slab load
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = dp + 4;             // floats per staged point row
   float* Cs = smem;                          // [nsp / BN][dp][BN]: per chunk, K rows BN floats apart
   float* Hs = Cs + (size_t)dp * nsp;         // [nsp]
-  float* Xs0 = Hs + nsp;                     // 2 x [BM][xs_stride]
+  float* Xs0 = Hs + nsp;                     // 2 x [SBM][xs_stride]
   __shared__ unsigned int s_changed;
 
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -342,24 +351,24 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   }
   for (int j = tid; j < nsp; j += ST) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
   // zero both point buffers once: padding columns [d, dp) and rows past n stay zero
-  for (int e = tid; e < 2 * BM * xs_stride; e += ST) Xs0[e] = 0.f;
+  for (int e = tid; e < 2 * SBM * xs_stride; e += ST) Xs0[e] = 0.f;
   __syncthreads();
 
   const float H = __uint_as_float(ctl->hmax_bits);
   const float Cmax = __uint_as_float(ctl->cmax_bits);
-  const int64_t ntiles = (n + BM - 1) / BM;
+  const int64_t ntiles = (n + SBM - 1) / SBM;
   int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles) load_tile_async<V16>(Xs0, xs_stride, X, n, d, blockIdx.x);
+  if ((int64_t)blockIdx.x < ntiles) load_tile_async<V16, G>(Xs0, xs_stride, X, n, d, blockIdx.x);
   cp_async_commit();
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t next = tile + gridDim.x;
-    float* Xs = Xs0 + buf * BM * xs_stride;
-    if (next < ntiles) load_tile_async<V16>(Xs0 + (buf ^ 1) * BM * xs_stride, xs_stride, X, n, d, next);
+    float* Xs = Xs0 + buf * SBM * xs_stride;
+    if (next < ntiles) load_tile_async<V16, G>(Xs0 + (buf ^ 1) * SBM * xs_stride, xs_stride, X, n, d, next);
     cp_async_commit();
     cp_async_wait_1();
     __syncthreads();
 
-    const int64_t m0 = tile * BM;
+    const int64_t m0 = tile * SBM;
     TopT top[SR];
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
@@ -483,8 +492,19 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   cp_async_wait_1();
 }
 
-size_t slab_smem_bytes(int dp, int nsp) {
-  return ((size_t)dp * nsp + nsp + 2 * (size_t)BM * (dp + 4)) * sizeof(float);
+size_t slab_smem_bytes(int dp, int nsp, int rows) {
+  return ((size_t)dp * nsp + nsp + 2 * (size_t)rows * (dp + 4)) * sizeof(float);
+}
+
+// Centroids per slab of geometry G for dimension d (0: does not fit).
+int slab_width_g(int d, int G) {
+  if (d > kSlabMaxD) return 0;
+  const int dp = (d + 3) / 4 * 4;
+  const size_t budget = (G ? 113 : 227) * 1024 - 2048;  // per CTA
+  const size_t fixed = 2 * (size_t)(G ? SlabGeo<1>::M : SlabGeo<0>::M) * (dp + 4) * sizeof(float);
+  if (fixed >= budget) return 0;
+  int ns = (int)((budget - fixed) / (((size_t)dp + 1) * sizeof(float))) / BN * BN;
+  return ns >= BN ? ns : 0;
 }
 
 }  // namespace
@@ -501,23 +521,19 @@ cudaError_t init_assign_simt() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   };
-  raise(assign_slab_kernel<true, false>);
-  raise(assign_slab_kernel<false, false>);
-  raise(assign_slab_kernel<true, true>);
-  raise(assign_slab_kernel<false, true>);
+  raise(assign_slab_kernel<true, false, 0>);
+  raise(assign_slab_kernel<false, false, 0>);
+  raise(assign_slab_kernel<true, true, 0>);
+  raise(assign_slab_kernel<false, true, 0>);
+  raise(assign_slab_kernel<true, false, 1>);
+  raise(assign_slab_kernel<false, false, 1>);
+  raise(assign_slab_kernel<true, true, 1>);
+  raise(assign_slab_kernel<false, true, 1>);
   return e;
 }
 
 // Centroids per slab for dimension d (0: the slab kernel does not apply).
-int simt_slab_width(int d) {
-  if (d > kSlabMaxD) return 0;
-  const int dp = (d + 3) / 4 * 4;
-  const size_t budget = 227 * 1024 - 2048;
-  const size_t fixed = 2 * (size_t)BM * (dp + 4) * sizeof(float);
-  if (fixed >= budget) return 0;
-  int ns = (int)((budget - fixed) / (((size_t)dp + 1) * sizeof(float))) / BN * BN;
-  return ns >= BN ? ns : 0;
-}
+int simt_slab_width(int d) { return slab_width_g(d, 0); }
 
 // p.X / p.n: the rows to assign (the gathered rows and their capacity for a
 // re-check pass); chalf, xnorm: h_j and the rows' norm bounds.
@@ -527,28 +543,35 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* cha
   const double m = p.d + 1;
   const float gam = (float)(m * u / (1.0 - m * u) * (1.0 + 1e-6));
   const int dp = (p.d + 3) / 4 * 4;
-  const int width = simt_slab_width(p.d);
-  const int64_t tiles = (p.n + BM - 1) / BM;
-  const int blocks = (int)(tiles < num_sms() ? tiles : num_sms());
+  // two CTAs per SM when all k centroids fit the half-size slab, else one CTA with the larger slab
+  const int G = (slab_width_g(p.d, 1) >= p.k) ? 1 : 0;
+  const int width = slab_width_g(p.d, G), rows = G ? SlabGeo<1>::M : SlabGeo<0>::M;
+  const int64_t tiles = (p.n + rows - 1) / rows;
+  const int64_t cap = (int64_t)num_sms() * (G ? SlabGeo<1>::CTAS : SlabGeo<0>::CTAS);
+  const int blocks = (int)(tiles < cap ? tiles : cap);
   const bool v16 = (p.d % 4 == 0) && ((uintptr_t)p.X % 16 == 0);
   for (int j_lo = 0; j_lo < p.k; j_lo += width) {
     const int ns = p.k - j_lo < width ? p.k - j_lo : width;
     const int nsp = (ns + BN - 1) / BN * BN;
-    const size_t smem = slab_smem_bytes(dp, nsp);
+    const size_t smem = slab_smem_bytes(dp, nsp, rows);
     const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
     // passes over gathered re-check rows keep a third score (candidate lists of two)
     const bool t3 = sr.rows != nullptr;
-#define KM_SLAB(V, T)                                                                                        \
-  assign_slab_kernel<V, T><<<blocks, ST, smem, s>>>(p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm, w.ctl, \
-                                                    p.assign, w.flags, w.state, w.state3, first, first_slab,      \
-                                                    last_slab, gam, sr)
+#define KM_SLAB(V_, T3_, G_)                                                                                \
+  assign_slab_kernel<V_, T3_, G_><<<blocks, SlabGeo<G_>::T, smem, s>>>(                                     \
+      p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm, w.ctl, p.assign, w.flags, w.state, w.state3, first, \
+      first_slab, last_slab, gam, sr)
+#define KM_SLAB_G(V_, T3_) \
+  if (G) KM_SLAB(V_, T3_, 1);  \
+  else KM_SLAB(V_, T3_, 0)
     if (v16) {
-      if (t3) KM_SLAB(true, true);
-      else KM_SLAB(true, false);
+      if (t3) KM_SLAB_G(true, true);
+      else KM_SLAB_G(true, false);
     } else {
-      if (t3) KM_SLAB(false, true);
-      else KM_SLAB(false, false);
+      if (t3) KM_SLAB_G(false, true);
+      else KM_SLAB_G(false, false);
     }
+#undef KM_SLAB_G
 #undef KM_SLAB
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
