@@ -443,37 +443,42 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     }
     if (tid == 0) s_changed = 0;
     __syncthreads();  // also: every thread is done reading Xs before it is refilled
-    if (tx == 0) {
+    // after the merge every lane of a row group holds the rows' results: lane tx < SR settles row tx
+    if (tx < SR) {
       unsigned int changed = 0;
+      TopT tr = top[0];
 #pragma unroll
-      for (int r = 0; r < SR; ++r) {
+      for (int q = 1; q < SR; ++q)
+        if (tx == q) tr = top[q];
+      {
+        const int r = tx;
         const int64_t i = m0 + srow_of(ty, r);
-        if (i >= n) continue;
+        if (i >= n) goto row_done;
         if (!last_slab) {
           if constexpr (T3) {
-            state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, __int_as_float(top[r].i2));
-            state3[i] = top[r].b3;
+            state[i] = make_float4(tr.b1, __int_as_float(tr.i1), tr.b2, __int_as_float(tr.i2));
+            state3[i] = tr.b3;
           } else {
-            state[i] = make_float4(top[r].b1, __int_as_float(top[r].i1), top[r].b2, 0.f);
+            state[i] = make_float4(tr.b1, __int_as_float(tr.i1), tr.b2, 0.f);
           }
-          continue;
+          goto row_done;
         }
         const int64_t pt = sr.rows ? (int64_t)sr.rows[i] : i;  // the point of row i
         int old = sr.rows ? sr.old[i] : (first ? -1 : assign[pt]);
         if (old < 0 || old >= k) old = -1;
         const float E = fmaf(3.f * kU, H, gam * xnorm[i] * Cmax);
         const float margin = 2.f * E * (1.f + 0x1p-10f);
-        const int j1 = top[r].i1;
-        if (__fsub_rn(top[r].b2, top[r].b1) <= margin) {
+        const int j1 = tr.i1;
+        if (__fsub_rn(tr.b2, tr.b1) <= margin) {
           const unsigned long long slot = atomicAdd(sr.nflag ? sr.nflag : &ctl->n_flagged, 1ull);
           FlagRec rec;
           rec.i = (int32_t)pt; rec.old = old; rec.nc = 0; rec.pad = 0;
           rec.cand[0] = rec.cand[1] = rec.cand[2] = rec.cand[3] = 0;
           if constexpr (T3) {
-            if (__fsub_rn(top[r].b3, top[r].b1) > margin) {  // no third centroid can be the nearest
+            if (__fsub_rn(tr.b3, tr.b1) > margin) {  // no third centroid can be the nearest
               rec.nc = 2;
-              rec.cand[0] = min(j1, top[r].i2);
-              rec.cand[1] = max(j1, top[r].i2);
+              rec.cand[0] = min(j1, tr.i2);
+              rec.cand[1] = max(j1, tr.i2);
             }
           }
           (sr.flags ? sr.flags : flags)[slot] = rec;
@@ -483,6 +488,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
         }
         assign[pt] = j1;
       }
+    row_done:
       if (changed) atomicAdd(&s_changed, changed);
     }
     __syncthreads();
