@@ -115,6 +115,34 @@ __device__ __forceinline__ Top3s top_merge(Top3s a, Top3s b) {
   return r;
 }
 
+// Order-preserving integer key of a score (-0 first made +0, so equal scores
+// give equal keys; scores here are never NaN).
+__device__ __forceinline__ int score_key(float x) {
+  const int k = __float_as_int(x + 0.f);
+  return k ^ ((k >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ float key_score(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+
+// Minimum of v over this lane's half-warp (lanes 0-15 or 16-31), by two
+// full-warp reductions.
+__device__ __forceinline__ int half_min(int v, int lane) {
+  const int lo = __reduce_min_sync(0xffffffffu, lane < 16 ? v : INT_MAX);
+  const int hi = __reduce_min_sync(0xffffffffu, lane < 16 ? INT_MAX : v);
+  return lane < 16 ? lo : hi;
+}
+
+// The merged top-2 of the 16 lanes of a row group (a half-warp): the best
+// score, its lowest index among equal scores, and the second-best score.
+__device__ __forceinline__ Top2 group_top2(const Top2& t, int lane) {
+  const int k1 = score_key(t.b1);
+  const int m1 = half_min(k1, lane);
+  const bool win = k1 == m1;
+  const int i1 = half_min(win ? t.i1 : INT_MAX, lane);
+  const bool me = win && t.i1 == i1;  // the lane holding the winner (indices are distinct across lanes)
+  const int m2 = half_min(score_key(me ? t.b2 : t.b1), lane);
+  return Top2{key_score(m1), key_score(m2), i1};
+}
+
 __device__ __forceinline__ Top2 top_shfl_xor(const Top2& t, int o) {
   Top2 p;
   p.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
@@ -438,8 +466,12 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     }
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
+      if constexpr (T3) {
 #pragma unroll
-      for (int o = 8; o; o >>= 1) top[r] = top_merge(top[r], top_shfl_xor(top[r], o));
+        for (int o = 8; o; o >>= 1) top[r] = top_merge(top[r], top_shfl_xor(top[r], o));
+      } else {
+        top[r] = group_top2(top[r], tid & 31);
+      }
     }
     if (tid == 0) s_changed = 0;
     __syncthreads();  // also: every thread is done reading Xs before it is refilled
