@@ -368,13 +368,14 @@ def test_queued_points_rescored(km, ref, precision):
     """Centroids duplicated nine times: every point has nine equal candidates (more than the eight
     slots), so it is queued, re-scored (E4M3 runs: BF16 codes on the tensor cores; BF16 runs: the
     FP32 slab kernel), still tied, and settled over all k with the lowest index."""
-    X = synth.mixture(61, 20000, 48, 12, 6.0, 1.0)
+    n = 60000  # enough tied points that the full re-checks are queued rather than settled one by one
+    X = synth.mixture(61, n, 64, 12, 6.0, 1.0)
     base = X[:12].copy()
     C0 = np.repeat(base, 9, axis=0)  # centroid 9 q + r is a copy of point q
     Xd = torch.from_numpy(X).to(DEV)
     Cd = torch.from_numpy(C0).to(DEV)
     a, s, c = km.alloc_outputs(Xd, Cd)
-    a.copy_(torch.from_numpy(np.zeros(20000, np.int32)))
+    a.copy_(torch.from_numpy(np.zeros(n, np.int32)))
     out = km.step(Xd, Cd, a, s, c, precision=precision, warm_start=True)
     assert out.stats["n_full"] > 0
     ag = out.assign.cpu().numpy()
