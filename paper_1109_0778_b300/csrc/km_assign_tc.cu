@@ -645,9 +645,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const int nall = it.nchunks * nblk;
       uint32_t v[32], v2[32];
       int c = c0;
+      int blk = 0;  // 32-column block within the current chunk
 #pragma unroll 1
       for (int kb = 0; kb < nall && ok;) {
-        const int blk = kb % nblk;
         const int buf = 2 * (gu & 1) + grp;
         if (blk == 0) {  // a new chunk: wait for its accumulators
           if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gu >> 1) & 1, &abort_s, P.wait_ns))) {
@@ -672,7 +672,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (two) score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
         else score_block(v, Hs + j0, wrow, top, j0, thr, margin);
         kb += two ? 2 : 1;
+        blk = lastb + 1;
         if (lastb == nblk - 1) {
+          blk = 0;
           ++gu;
           c = (c + 1 == it.nchunks) ? 0 : c + 1;
         }
