@@ -32,7 +32,13 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, PAD = 4;
 constexpr int THREADS = 256;
-constexpr int SR = 4;  // slab kernel: 4 rows x 8 columns of scores per thread
+// Slab kernel: 8 rows x 4 columns of scores per thread. The 32 lanes of a warp
+// take the 128 columns of a chunk (4 adjacent columns each) and share its 8
+// rows: a centroid load is 32 distinct 16-byte words, a point load one
+// broadcast word holding 4 rows of one dimension (the point tile is staged
+// transposed), and each paired FMA takes two adjacent rows against one
+// centroid coordinate.
+constexpr int SR = 8;
 // Slab kernel geometries: G = 0, 512 threads on 128-row tiles, one CTA per SM
 // (the largest slab); G = 1, 256 threads on 64-row tiles, two CTAs per SM (half
 // the slab each; their barriers and epilogues no longer line up).
@@ -40,7 +46,7 @@ template <int G>
 struct SlabGeo {
   static constexpr int T = G ? 256 : 512, M = G ? 64 : 128, CTAS = G ? 2 : 1;
 };
-__device__ __forceinline__ int srow_of(int ty, int r) { return ty * 4 + r; }
+__device__ __forceinline__ int srow_of(int wq, int r) { return wq * SR + r; }
 
 __device__ __forceinline__ int row_of(int ty, int r) { return r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4); }
 __device__ __forceinline__ int col_of(int tx, int c) { return c < 4 ? tx * 4 + c : 64 + tx * 4 + (c - 4); }
@@ -93,7 +99,6 @@ __device__ __forceinline__ void top_push(Top3s& t, float s, int j) {
   t.b1 = lt1 ? s : t.b1;
 }
 
-__device__ __forceinline__ Top2 top_merge(const Top2& a, const Top2& b) { return top2_merge(a, b); }
 __device__ __forceinline__ Top3s top_merge(Top3s a, Top3s b) {
   if (lex_less(b.b1, b.i1, a.b1, a.i1)) {
     const Top3s t = a;
@@ -123,33 +128,19 @@ __device__ __forceinline__ int score_key(float x) {
 }
 __device__ __forceinline__ float key_score(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
 
-// Minimum of v over this lane's half-warp (lanes 0-15 or 16-31), by two
-// full-warp reductions.
-__device__ __forceinline__ int half_min(int v, int lane) {
-  const int lo = __reduce_min_sync(0xffffffffu, lane < 16 ? v : INT_MAX);
-  const int hi = __reduce_min_sync(0xffffffffu, lane < 16 ? INT_MAX : v);
-  return lane < 16 ? lo : hi;
-}
-
-// The merged top-2 of the 16 lanes of a row group (a half-warp): the best
-// score, its lowest index among equal scores, and the second-best score.
-__device__ __forceinline__ Top2 group_top2(const Top2& t, int lane) {
+// The merged top-2 of a warp's 32 lanes for one row: the best score, its
+// lowest index among equal scores, and the second-best score (three full-warp
+// minimum reductions over order-preserving keys).
+__device__ __forceinline__ Top2 warp_top2(const Top2& t) {
   const int k1 = score_key(t.b1);
-  const int m1 = half_min(k1, lane);
+  const int m1 = __reduce_min_sync(0xffffffffu, k1);
   const bool win = k1 == m1;
-  const int i1 = half_min(win ? t.i1 : INT_MAX, lane);
+  const int i1 = __reduce_min_sync(0xffffffffu, win ? t.i1 : INT_MAX);
   const bool me = win && t.i1 == i1;  // the lane holding the winner (indices are distinct across lanes)
-  const int m2 = half_min(score_key(me ? t.b2 : t.b1), lane);
+  const int m2 = __reduce_min_sync(0xffffffffu, score_key(me ? t.b2 : t.b1));
   return Top2{key_score(m1), key_score(m2), i1};
 }
 
-__device__ __forceinline__ Top2 top_shfl_xor(const Top2& t, int o) {
-  Top2 p;
-  p.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
-  p.b2 = __shfl_xor_sync(0xffffffffu, t.b2, o);
-  p.i1 = __shfl_xor_sync(0xffffffffu, t.i1, o);
-  return p;
-}
 __device__ __forceinline__ Top3s top_shfl_xor(const Top3s& t, int o) {
   Top3s p;
   p.b1 = __shfl_xor_sync(0xffffffffu, t.b1, o);
@@ -310,8 +301,8 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
 // ---------------------------------------------------------------------------
 // Slab-resident variant (d <= 128). A slab of up to kSlab centroids is loaded
 // into shared memory once per CTA (transposed, with its h_j); point tiles
-// stream through a cp.async double buffer, and each of 512 threads reads its
-// 4 rows four K-elements at a time. A row's running (best, index, second) lives in
+// stream through a cp.async double buffer, staged transposed, and each thread
+// keeps 8 rows x 4 columns of scores. A row's running (best, index, second) lives in
 // registers within a slab and in `state` between slabs; the last slab applies
 // the same error-bound test as the streaming kernel above.
 constexpr int kSlabMaxD = 128;
@@ -320,30 +311,26 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Issues the copies of point tile `tile` (rows of d floats) into Xs (row stride xs_stride floats).
-template <bool V16, int G>
-__device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const float* __restrict__ X, int64_t n,
+// Issues the copies of point tile `tile` into XsT, transposed: dimension t of
+// tile row r goes to XsT[t * xs_stride + r] (xs_stride = tile rows + 4). A warp
+// copies 8 consecutive dimensions of 4 rows per instruction: 4 fully used
+// 32-byte sectors from global memory, and 32 distinct banks in shared memory
+// (xs_stride is 4 modulo 32). Rows past n are not copied.
+template <int G>
+__device__ __forceinline__ void load_tile_async(float* XsT, int xs_stride, const float* __restrict__ X, int64_t n,
                                                 int d, int64_t tile) {
   constexpr int SBM = SlabGeo<G>::M, ST = SlabGeo<G>::T;
   const int64_t m0 = tile * SBM;
-  if (V16) {
-    const int per_row = d >> 2;
-    for (int e = threadIdx.x; e < SBM * per_row; e += ST) {
-      const int r = e / per_row, c4 = e - r * per_row;
-      if (m0 + r < n) cp_async16(Xs + r * xs_stride + 4 * c4, X + (m0 + r) * d + 4 * c4);
-    }
-  } else {
-    for (int e = threadIdx.x; e < SBM * d; e += ST) {
-      const int r = e / d, c = e - r * d;
-      if (m0 + r < n) cp_async4(Xs + r * xs_stride + c, X + (m0 + r) * d + c);
-    }
+  const int rows = (int)(n - m0 < SBM ? n - m0 : SBM);
+  const int lane = threadIdx.x & 31, tl = lane & 7;
+  // warp: groups of 4 rows; lane: row lane / 8 of the group, dimensions lane % 8 + 8 m
+  for (int r = (threadIdx.x >> 5) * 4 + (lane >> 3); r < rows; r += ST / 8) {
+    const float* src = X + (m0 + r) * d + tl;
+    float* dst = XsT + tl * xs_stride + r;
+    for (int t = tl; t < d; t += 8, src += 8, dst += 8 * xs_stride) cp_async4(dst, src);
   }
 }
 
@@ -351,7 +338,7 @@ __device__ __forceinline__ void load_tile_async(float* Xs, int xs_stride, const 
 // third-best score are kept, and a flagged row whose third-best score lies
 // outside the margin is recorded with its two candidates; the third-best
 // score crosses slabs in state3.
-template <bool V16, bool T3, int G>
+template <bool T3, int G>
 __global__ void __launch_bounds__(SlabGeo<G>::T, SlabGeo<G>::CTAS)
 assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const float* __restrict__ C, int k,
                    int j_lo, int ns, const float* __restrict__ chalf, const float* __restrict__ xnorm, Ctl* ctl,
@@ -365,33 +352,33 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   if ((int64_t)blockIdx.x * SBM >= n) return;    // no tile for this CTA: skip the slab load
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
-  const int xs_stride = dp + 4;             // floats per staged point row
+  const int xs_stride = SBM + 4;            // floats per staged dimension (a row of the transposed tile)
   float* Cs = smem;                          // [nsp / BN][dp][BN]: per chunk, K rows BN floats apart
   float* Hs = Cs + (size_t)dp * nsp;         // [nsp]
-  float* Xs0 = Hs + nsp;                     // 2 x [SBM][xs_stride]
+  float* Xs0 = Hs + nsp;                     // 2 x [dp][xs_stride]: point tiles, transposed
   __shared__ unsigned int s_changed;
 
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
   // slab of centroids, transposed; zero padding in [d, dp) and [ns, nsp)
   for (int e = tid; e < dp * nsp; e += ST) {
     const int j = e % nsp, t = e / nsp;
     Cs[((size_t)(j / BN) * dp + t) * BN + (j % BN)] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
   }
   for (int j = tid; j < nsp; j += ST) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
-  // zero both point buffers once: padding columns [d, dp) and rows past n stay zero
-  for (int e = tid; e < 2 * SBM * xs_stride; e += ST) Xs0[e] = 0.f;
+  // zero both point buffers once: padding dimensions [d, dp) stay zero
+  for (int e = tid; e < 2 * dp * xs_stride; e += ST) Xs0[e] = 0.f;
   __syncthreads();
 
   const float H = __uint_as_float(ctl->hmax_bits);
   const float Cmax = __uint_as_float(ctl->cmax_bits);
   const int64_t ntiles = (n + SBM - 1) / SBM;
   int buf = 0;
-  if ((int64_t)blockIdx.x < ntiles) load_tile_async<V16, G>(Xs0, xs_stride, X, n, d, blockIdx.x);
+  if ((int64_t)blockIdx.x < ntiles) load_tile_async<G>(Xs0, xs_stride, X, n, d, blockIdx.x);
   cp_async_commit();
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t next = tile + gridDim.x;
-    float* Xs = Xs0 + buf * SBM * xs_stride;
-    if (next < ntiles) load_tile_async<V16, G>(Xs0 + (buf ^ 1) * SBM * xs_stride, xs_stride, X, n, d, next);
+    float* Xs = Xs0 + buf * dp * xs_stride;
+    if (next < ntiles) load_tile_async<G>(Xs0 + (buf ^ 1) * dp * xs_stride, xs_stride, X, n, d, next);
     cp_async_commit();
     cp_async_wait_1();
     __syncthreads();
@@ -400,18 +387,18 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     TopT top[SR];
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
-      const int64_t i = m0 + srow_of(ty, r);
-      // the carried state enters through one of the 16 threads sharing the row,
+      const int64_t i = m0 + srow_of(wq, r);
+      // the carried state enters through one of the 32 lanes sharing the row,
       // so the cross-thread merge sees it once
       if constexpr (T3) {
-        if (!first_slab && tx == 0 && i < n) {
+        if (!first_slab && lane == 0 && i < n) {
           const float4 st = state[i];
           top[r] = Top3s{st.x, st.z, state3[i], __float_as_int(st.y), __float_as_int(st.w)};
         } else {
           top[r] = Top3s{INFINITY, INFINITY, INFINITY, 0, 0};
         }
       } else {
-        if (!first_slab && tx == 0 && i < n) {
+        if (!first_slab && lane == 0 && i < n) {
           const float4 st = state[i];
           top[r] = Top2{st.x, st.z, __float_as_int(st.y)};
         } else {
@@ -421,70 +408,61 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
       const float* Cc = Cs + (size_t)(j0 / BN) * dp * BN;  // this chunk's [dp][BN] block
-      float2 acc2[SR][4];  // (acc[r][2c], acc[r][2c + 1]): one paired FMA per two columns
+      float2 acc2[SR / 2][4];  // (acc[2p][c], acc[2p + 1][c]): one paired FMA per two rows
 #pragma unroll
-      for (int r = 0; r < SR; ++r)
+      for (int p = 0; p < SR / 2; ++p)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc2[r][c] = make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int kk = 0; kk < dp; kk += 4) {
-        float a[SR][4];
-#pragma unroll
-        for (int r = 0; r < SR; ++r)
-          *reinterpret_cast<float4*>(a[r]) = *reinterpret_cast<const float4*>(Xs + srow_of(ty, r) * xs_stride + kk);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float2 b2[4];
-          const float* cr = Cc + (kk + q) * BN;
-          const float4 b0 = *reinterpret_cast<const float4*>(cr + tx * 4);
-          const float4 b1 = *reinterpret_cast<const float4*>(cr + 64 + tx * 4);
-          b2[0] = make_float2(b0.x, b0.y); b2[1] = make_float2(b0.z, b0.w);
-          b2[2] = make_float2(b1.x, b1.y); b2[3] = make_float2(b1.z, b1.w);
-#pragma unroll
-          for (int r = 0; r < SR; ++r) {
-            const float2 ar = make_float2(a[r][q], a[r][q]);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc2[r][c] = __ffma2_rn(ar, b2[c], acc2[r][c]);
-          }
-        }
-      }
-      float acc[SR][8];
-#pragma unroll
-      for (int r = 0; r < SR; ++r)
+        for (int c = 0; c < 4; ++c) acc2[p][c] = make_float2(0.f, 0.f);
+      const float* xr = Xs + wq * SR;
+      const float* cr = Cc + lane * 4;
+#pragma unroll 8
+      for (int kk = 0; kk < dp; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(xr + kk * xs_stride);
+        const float4 a1 = *reinterpret_cast<const float4*>(xr + kk * xs_stride + 4);
+        const float4 b = *reinterpret_cast<const float4*>(cr + kk * BN);
+        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                              make_float2(a1.z, a1.w)};
+        const float bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          acc[r][2 * c] = acc2[r][c].x;
-          acc[r][2 * c + 1] = acc2[r][c].y;
+          const float2 bc = make_float2(bv[c], bv[c]);
+#pragma unroll
+          for (int p = 0; p < SR / 2; ++p) acc2[p][c] = __ffma2_rn(ap[p], bc, acc2[p][c]);
         }
+      }
+      const float4 h4 = *reinterpret_cast<const float4*>(Hs + j0 + lane * 4);
+      const float hj[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        const int jl = j0 + col_of(tx, c);
-        const float hj = Hs[jl];
+      for (int c = 0; c < 4; ++c) {
+        const int j = j_lo + j0 + lane * 4 + c;
 #pragma unroll
-        for (int r = 0; r < SR; ++r) top_push(top[r], __fsub_rn(hj, acc[r][c]), j_lo + jl);
+        for (int p = 0; p < SR / 2; ++p) {
+          top_push(top[2 * p], __fsub_rn(hj[c], acc2[p][c].x), j);
+          top_push(top[2 * p + 1], __fsub_rn(hj[c], acc2[p][c].y), j);
+        }
       }
     }
 #pragma unroll
     for (int r = 0; r < SR; ++r) {
       if constexpr (T3) {
 #pragma unroll
-        for (int o = 8; o; o >>= 1) top[r] = top_merge(top[r], top_shfl_xor(top[r], o));
+        for (int o = 16; o; o >>= 1) top[r] = top_merge(top[r], top_shfl_xor(top[r], o));
       } else {
-        top[r] = group_top2(top[r], tid & 31);
+        top[r] = warp_top2(top[r]);
       }
     }
     if (tid == 0) s_changed = 0;
     __syncthreads();  // also: every thread is done reading Xs before it is refilled
-    // after the merge every lane of a row group holds the rows' results: lane tx < SR settles row tx
-    if (tx < SR) {
+    // after the merge every lane of the warp holds its rows' results: lane r < SR settles row r
+    if (lane < SR) {
       unsigned int changed = 0;
       TopT tr = top[0];
 #pragma unroll
       for (int q = 1; q < SR; ++q)
-        if (tx == q) tr = top[q];
+        if (lane == q) tr = top[q];
       {
-        const int r = tx;
-        const int64_t i = m0 + srow_of(ty, r);
+        const int r = lane;
+        const int64_t i = m0 + srow_of(wq, r);
         if (i >= n) goto row_done;
         if (!last_slab) {
           if constexpr (T3) {
@@ -531,7 +509,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
 }
 
 size_t slab_smem_bytes(int dp, int nsp, int rows) {
-  return ((size_t)dp * nsp + nsp + 2 * (size_t)rows * (dp + 4)) * sizeof(float);
+  return ((size_t)dp * nsp + nsp + 2 * (size_t)dp * (rows + 4)) * sizeof(float);
 }
 
 // Centroids per slab of geometry G for dimension d (0: does not fit).
@@ -539,7 +517,7 @@ int slab_width_g(int d, int G) {
   if (d > kSlabMaxD) return 0;
   const int dp = (d + 3) / 4 * 4;
   const size_t budget = (G ? 113 : 227) * 1024 - 2048;  // per CTA
-  const size_t fixed = 2 * (size_t)(G ? SlabGeo<1>::M : SlabGeo<0>::M) * (dp + 4) * sizeof(float);
+  const size_t fixed = 2 * (size_t)dp * ((G ? SlabGeo<1>::M : SlabGeo<0>::M) + 4) * sizeof(float);
   if (fixed >= budget) return 0;
   int ns = (int)((budget - fixed) / (((size_t)dp + 1) * sizeof(float))) / BN * BN;
   return ns >= BN ? ns : 0;
@@ -559,14 +537,10 @@ cudaError_t init_assign_simt() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   };
-  raise(assign_slab_kernel<true, false, 0>);
-  raise(assign_slab_kernel<false, false, 0>);
-  raise(assign_slab_kernel<true, true, 0>);
-  raise(assign_slab_kernel<false, true, 0>);
-  raise(assign_slab_kernel<true, false, 1>);
-  raise(assign_slab_kernel<false, false, 1>);
-  raise(assign_slab_kernel<true, true, 1>);
-  raise(assign_slab_kernel<false, true, 1>);
+  raise(assign_slab_kernel<false, 0>);
+  raise(assign_slab_kernel<true, 0>);
+  raise(assign_slab_kernel<false, 1>);
+  raise(assign_slab_kernel<true, 1>);
   return e;
 }
 
@@ -587,7 +561,6 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* cha
   const int64_t tiles = (p.n + rows - 1) / rows;
   const int64_t cap = (int64_t)num_sms() * (G ? SlabGeo<1>::CTAS : SlabGeo<0>::CTAS);
   const int blocks = (int)(tiles < cap ? tiles : cap);
-  const bool v16 = (p.d % 4 == 0) && ((uintptr_t)p.X % 16 == 0);
   for (int j_lo = 0; j_lo < p.k; j_lo += width) {
     const int ns = p.k - j_lo < width ? p.k - j_lo : width;
     const int nsp = (ns + BN - 1) / BN * BN;
@@ -595,21 +568,17 @@ cudaError_t launch_assign_slab(const Problem& p, const Work& w, const float* cha
     const int first_slab = j_lo == 0, last_slab = j_lo + width >= p.k;
     // passes over gathered re-check rows keep a third score (candidate lists of two)
     const bool t3 = sr.rows != nullptr;
-#define KM_SLAB(V_, T3_, G_)                                                                                \
-  assign_slab_kernel<V_, T3_, G_><<<blocks, SlabGeo<G_>::T, smem, s>>>(                                     \
+#define KM_SLAB(T3_, G_)                                                                                    \
+  assign_slab_kernel<T3_, G_><<<blocks, SlabGeo<G_>::T, smem, s>>>(                                         \
       p.X, p.n, p.d, dp, p.C, p.k, j_lo, ns, chalf, xnorm, w.ctl, p.assign, w.flags, w.state, w.state3, first, \
       first_slab, last_slab, gam, sr)
-#define KM_SLAB_G(V_, T3_) \
-  if (G) KM_SLAB(V_, T3_, 1);  \
-  else KM_SLAB(V_, T3_, 0)
-    if (v16) {
-      if (t3) KM_SLAB_G(true, true);
-      else KM_SLAB_G(true, false);
+    if (G) {
+      if (t3) KM_SLAB(true, 1);
+      else KM_SLAB(false, 1);
     } else {
-      if (t3) KM_SLAB_G(false, true);
-      else KM_SLAB_G(false, false);
+      if (t3) KM_SLAB(true, 0);
+      else KM_SLAB(false, 0);
     }
-#undef KM_SLAB_G
 #undef KM_SLAB
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
