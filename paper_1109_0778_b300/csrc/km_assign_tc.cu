@@ -365,7 +365,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                  const TcParams P) {
   constexpr int KBE = ROWB / (FP8 ? 1 : 2);  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // 1024-byte aligned by an offset into the shared array (not an integer round trip), so that
+  // accesses through derived pointers (h_j in the epilogue) compile to shared-memory loads
+  uint8_t* smem = smem_raw + ((1024u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t a_full[MAX_ABUF], a_empty[MAX_ABUF], b_full[MAX_STAGES], b_empty[MAX_STAGES];
   __shared__ uint64_t acc_full[NACC], acc_empty[NACC], drain_bar, never_bar;
   __shared__ uint32_t tmem_base_s;
