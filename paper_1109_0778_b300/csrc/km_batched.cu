@@ -342,7 +342,7 @@ struct SegBatch {
 template <int QM, int V, typename Flush>
 __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int lane, int d, const float* C,
                                          uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&pb)[kMaxV],
-                                         float (&cj)[kMaxV], float& ob, int& cur_j, Flush&& flush) {
+                                         float (&cj)[kMaxV], float& objS, float& objC, int& cur_j, Flush&& flush) {
   for (int r = 0; r < B.bn; ++r) {
     const int j = __shfl_sync(0xffffffffu, B.j, r);
     const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
@@ -364,7 +364,7 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
       const float df = __fsub_rn(xr[v], cj[v]);
       qd = fmaf(df, df, qd);
     }
-    ob = __fadd_rn(ob, qd);
+    kahan_add(objS, objC, qd);
     if constexpr (QM != 0) {
       const int64_t g = B.bs + r;  // flattened sorted position
       const int64_t pr = g - row0;
@@ -395,7 +395,8 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
 template <int QM, typename Flush>
 __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* st, int lane, int d, int dp,
                                                 const float* C, uint8_t* xq, int kp, int64_t row0, float4* xs_sorted,
-                                                float& pb, float& cj, float& ob, int& cur_j, Flush&& flush) {
+                                                float& pb, float& cj, float& objS, float& objC, int& cur_j,
+                                                Flush&& flush) {
   const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
   for (int r0 = 0; r0 < B.bn; r0 += G) {
     const int r = r0 + g;
@@ -418,7 +419,7 @@ __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* 
     const float xr = t < d ? st[r * B.rs + t] : 0.f;
     pb = __fadd_rn(pb, xr);
     const float df = __fsub_rn(xr, cj);
-    ob = fmaf(df, df, ob);
+    kahan_add(objS, objC, df * df);
     if constexpr (QM != 0) {
       const int64_t gp = B.bs + r;  // flattened sorted position
       const int64_t pr = gp - row0;
@@ -489,20 +490,19 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
     else cp_async_commit();
   };
 
-  // pb / ob: plain FP32 partials of the current run within the current batch (at most 32 rows),
-  // Kahan-added into s / objS at the end of each batch and before every flush
+  // pb: plain FP32 partials of the current run within the current batch (at most 32 rows),
+  // Kahan-added into s at the end of each batch and before every flush (the objective is
+  // Kahan-added row by row: its 1e-6 relative tolerance leaves no room for plain batch sums)
   float s[kMaxV], c[kMaxV], cj[kMaxV], pb[kMaxV];
 #pragma unroll
   for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; pb[v] = 0.f; }
-  float objS = 0.f, objC = 0.f, ob = 0.f;
+  float objS = 0.f, objC = 0.f;
   auto fold = [&]() {
 #pragma unroll
     for (int v = 0; v < kMaxV; ++v) {
       kahan_add(s[v], c[v], pb[v]);
       pb[v] = 0.f;
     }
-    kahan_add(objS, objC, ob);
-    ob = 0.f;
   };
   int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0, cur_dp = 0;
   int64_t cur_row0 = 0, cur_sum0 = 0;
@@ -521,7 +521,6 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
   };
   auto flush_obj = [&]() {
     if (cur_b < 0) return;
-    fold();
     double o = (double)objS - (double)objC;
 #pragma unroll
     for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
@@ -565,14 +564,17 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
       }
       const int d = cur_d;
       if (cur_dp)
-        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb[0], cj[0], ob,
-                            cur_j, flush);
+        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb[0], cj[0], objS,
+                            objC, cur_j, flush);
       else if (d <= 32)
-        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, ob, cur_j, flush);
+        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC, cur_j,
+                        flush);
       else if (d <= 64)
-        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, ob, cur_j, flush);
+        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC, cur_j,
+                        flush);
       else
-        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, ob, cur_j, flush);
+        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC,
+                            cur_j, flush);
       fold();
     }
     __syncwarp();  // every lane is done with this stage before it is refilled

@@ -19,7 +19,8 @@
 //              when the running sum is flushed into an FP64 sum (one atomic
 //              add per coordinate). The objective term ||x_i - c_{a_i}||^2 is
 //              formed in the same pass from the centroid held in registers
-//              for the segment, and summed the same way.
+//              for the segment and Kahan-added row by row (its 1e-6 relative
+//              tolerance leaves no room for plain batch sums).
 // Error: a plain sum of at most 32 rows is within 31u of their summed
 // magnitudes, a Kahan-summed sequence of such partials carries <= 2u + O(m u^2)
 // more, and the FP64 combine adds ~2^-53 per partial, so every sum is within
@@ -233,7 +234,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
   float s[V], c[V], cj[V], pb[V];  // pb: the current run's plain partial within this batch
 #pragma unroll
   for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; pb[v] = 0.f; }
-  float objS = 0.f, objC = 0.f, ob = 0.f;
+  float objS = 0.f, objC = 0.f;
   int cur = -1;
   int i_c = 0, j_c = -1, i_n = 0, j_n = -1;
   float4 xs_c = make_float4(1.f, 0.f, 0.f, 0.f), xs_n = xs_c;
@@ -280,7 +281,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
         const float df = __fsub_rn(xr[v], cj[v]);
         q = fmaf(df, df, q);
       }
-      ob = __fadd_rn(ob, q);
+      kahan_add(objS, objC, q);
       if constexpr (QM != 0) {
         const int64_t prow = P0 + b * RB + r;
         if (lane == r) xs_sorted[prow] = xs_c;
@@ -315,8 +316,6 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       kahan_add(s[v], c[v], pb[v]);
       pb[v] = 0.f;
     }
-    kahan_add(objS, objC, ob);
-    ob = 0.f;
     __syncwarp();  // every lane is done with this stage before it is refilled
     i_c = i_n;
     j_c = j_n;
