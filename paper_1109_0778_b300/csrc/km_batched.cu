@@ -341,8 +341,9 @@ struct SegBatch {
 // `flush` adds the partial sums of cur_j to the FP64 sums.
 template <int QM, int V, typename Flush>
 __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int lane, int d, const float* C,
-                                         uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&pb)[kMaxV],
-                                         float (&cj)[kMaxV], float& objS, float& objC, int& cur_j, Flush&& flush) {
+                                         uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&s)[kMaxV],
+                                         float (&c)[kMaxV], float (&cj)[kMaxV], float& objS, float& objC,
+                                         int& cur_j, Flush&& flush) {
   for (int r = 0; r < B.bn; ++r) {
     const int j = __shfl_sync(0xffffffffu, B.j, r);
     const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
@@ -360,7 +361,7 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
     for (int v = 0; v < V; ++v) {
       const int t = v * 32 + lane;
       xr[v] = t < d ? st[r * B.rs + t] : 0.f;
-      pb[v] = __fadd_rn(pb[v], xr[v]);
+      kahan_add(s[v], c[v], xr[v]);
       const float df = __fsub_rn(xr[v], cj[v]);
       qd = fmaf(df, df, qd);
     }
@@ -395,7 +396,7 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
 template <int QM, typename Flush>
 __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* st, int lane, int d, int dp,
                                                 const float* C, uint8_t* xq, int kp, int64_t row0, float4* xs_sorted,
-                                                float& pb, float& cj, float& objS, float& objC, int& cur_j,
+                                                float& s, float& c, float& cj, float& objS, float& objC, int& cur_j,
                                                 Flush&& flush) {
   const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
   for (int r0 = 0; r0 < B.bn; r0 += G) {
@@ -417,7 +418,7 @@ __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* 
       cj = t < d ? C[(int64_t)j * d + t] : 0.f;
     }
     const float xr = t < d ? st[r * B.rs + t] : 0.f;
-    pb = __fadd_rn(pb, xr);
+    kahan_add(s, c, xr);
     const float df = __fsub_rn(xr, cj);
     kahan_add(objS, objC, df * df);
     if constexpr (QM != 0) {
@@ -490,27 +491,16 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
     else cp_async_commit();
   };
 
-  // pb: plain FP32 partials of the current run within the current batch (at most 32 rows),
-  // Kahan-added into s at the end of each batch and before every flush (the objective is
-  // Kahan-added row by row: its 1e-6 relative tolerance leaves no room for plain batch sums)
-  float s[kMaxV], c[kMaxV], cj[kMaxV], pb[kMaxV];
+  float s[kMaxV], c[kMaxV], cj[kMaxV];
 #pragma unroll
-  for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; pb[v] = 0.f; }
+  for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
   float objS = 0.f, objC = 0.f;
-  auto fold = [&]() {
-#pragma unroll
-    for (int v = 0; v < kMaxV; ++v) {
-      kahan_add(s[v], c[v], pb[v]);
-      pb[v] = 0.f;
-    }
-  };
   int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0, cur_dp = 0;
   int64_t cur_row0 = 0, cur_sum0 = 0;
   const float* cur_C = nullptr;
   uint8_t* cur_xq = nullptr;
   auto flush = [&]() {  // this lane's partial sums of run cur_j (packed rows: column lane % cur_dp)
     if (cur_j < 0) return;
-    fold();
 #pragma unroll
     for (int v = 0; v < kMaxV; ++v) {
       const int t = cur_dp ? (v == 0 ? (lane & (cur_dp - 1)) : cur_d) : v * 32 + lane;
@@ -564,18 +554,17 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
       }
       const int d = cur_d;
       if (cur_dp)
-        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb[0], cj[0], objS,
-                            objC, cur_j, flush);
+        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s[0], c[0], cj[0],
+                            objS, objC, cur_j, flush);
       else if (d <= 32)
-        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC, cur_j,
+        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
                         flush);
       else if (d <= 64)
-        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC, cur_j,
+        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
                         flush);
       else
-        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, pb, cj, objS, objC,
+        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC,
                             cur_j, flush);
-      fold();
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
     Bc = Bn;

@@ -12,20 +12,16 @@
 //              unspecified);
 //   segsum  -- each warp walks one contiguous range of sorted positions; the
 //              rows are gathered into shared memory with cp.async, one batch
-//              ahead of the batch being summed. Within a batch (at most 32
-//              rows) the rows of a cluster are added plainly in FP32; that
-//              partial is Kahan-added into the warp's running sum of the
-//              cluster at the end of the batch and on every cluster change,
-//              when the running sum is flushed into an FP64 sum (one atomic
-//              add per coordinate). The objective term ||x_i - c_{a_i}||^2 is
-//              formed in the same pass from the centroid held in registers
-//              for the segment and Kahan-added row by row (its 1e-6 relative
-//              tolerance leaves no room for plain batch sums).
-// Error: a plain sum of at most 32 rows is within 31u of their summed
-// magnitudes, a Kahan-summed sequence of such partials carries <= 2u + O(m u^2)
-// more, and the FP64 combine adds ~2^-53 per partial, so every sum is within
-// ~33u ~ 2e-6 of sum |x_it| regardless of cluster size or order, inside the
-// 1e-5 centroid tolerance.
+//              ahead of the batch being summed. While the cluster stays the
+//              same the warp Kahan-accumulates the rows in FP32 registers, and
+//              on every cluster change it flushes its partial into an FP64 sum
+//              (one atomic add per coordinate). The objective term
+//              ||x_i - c_{a_i}||^2 is formed in the same pass from the
+//              centroid held in registers for the segment.
+// Error: a Kahan-summed run of m rows carries <= 2u + O(m u^2) of the summed
+// magnitudes, and the FP64 combine adds ~2^-53 per partial, so every sum is
+// within ~1.2e-7 of sum |x_it| regardless of cluster size or order, far
+// inside the 1e-5 centroid tolerance.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -231,9 +227,9 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     gather_rows(st, RS, X, d, rows, (int64_t)i_lane * d, lane);
   };
 
-  float s[V], c[V], cj[V], pb[V];  // pb: the current run's plain partial within this batch
+  float s[V], c[V], cj[V];
 #pragma unroll
-  for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; pb[v] = 0.f; }
+  for (int v = 0; v < V; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
   float objS = 0.f, objC = 0.f;
   int cur = -1;
   int i_c = 0, j_c = -1, i_n = 0, j_n = -1;
@@ -259,11 +255,6 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     for (int r = 0; r < rows; ++r) {
       const int j = __shfl_sync(0xffffffffu, j_c, r);
       if (j != cur) {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          kahan_add(s[v], c[v], pb[v]);
-          pb[v] = 0.f;
-        }
         if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
         cur = j;
 #pragma unroll
@@ -277,7 +268,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       for (int v = 0; v < V; ++v) {
         const int t = v * 32 + lane;
         xr[v] = t < d ? st[r * RS + t] : 0.f;
-        pb[v] = __fadd_rn(pb[v], xr[v]);
+        kahan_add(s[v], c[v], xr[v]);
         const float df = __fsub_rn(xr[v], cj[v]);
         q = fmaf(df, df, q);
       }
@@ -310,11 +301,6 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
           }
         }
       }
-    }
-#pragma unroll
-    for (int v = 0; v < V; ++v) {  // the batch's partials into the running (compensated) sums
-      kahan_add(s[v], c[v], pb[v]);
-      pb[v] = 0.f;
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
     i_c = i_n;
