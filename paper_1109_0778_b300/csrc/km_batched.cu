@@ -367,9 +367,7 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
     }
     kahan_add(objS, objC, qd);
     if constexpr (QM != 0) {
-      const int64_t g = B.bs + r;  // flattened sorted position
-      const int64_t pr = g - row0;
-      if (lane == r) xs_sorted[g] = B.xs;
+      const int64_t pr = B.bs + r - row0;  // sorted position within the instance
       if constexpr (QM == 1) {
         __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(xq) + pr * kp;
 #pragma unroll
@@ -404,13 +402,8 @@ __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* 
     const bool ok = r < B.bn;
     const int src = ok ? r : 0;
     const int j = __shfl_sync(0xffffffffu, B.j, src);
-    float4 xs = make_float4(1.f, 0.f, 0.f, 0.f);
-    if constexpr (QM != 0) {
-      xs.x = __shfl_sync(0xffffffffu, B.xs.x, src);
-      xs.y = __shfl_sync(0xffffffffu, B.xs.y, src);
-      xs.z = __shfl_sync(0xffffffffu, B.xs.z, src);
-      xs.w = __shfl_sync(0xffffffffu, B.xs.w, src);
-    }
+    float sxr = 1.f;  // the row's code scale (E4M3)
+    if constexpr (QM == 2) sxr = __shfl_sync(0xffffffffu, B.xs.x, src);
     if (!ok) continue;
     if (j != cur_j) {
       flush();
@@ -422,14 +415,12 @@ __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* 
     const float df = __fsub_rn(xr, cj);
     kahan_add(objS, objC, df * df);
     if constexpr (QM != 0) {
-      const int64_t gp = B.bs + r;  // flattened sorted position
-      const int64_t pr = gp - row0;
-      if (t == 0) xs_sorted[gp] = xs;
+      const int64_t pr = B.bs + r - row0;  // sorted position within the instance
       if (t < d) {
         if constexpr (QM == 1) {
           reinterpret_cast<__nv_bfloat16*>(xq)[pr * kp + t] = __float2bfloat16_rn(xr);
         } else {
-          xq[pr * kp + t] = __nv_fp8_e4m3(xr * pow2_inv(xs.x)).__x;
+          xq[pr * kp + t] = __nv_fp8_e4m3(xr * pow2_inv(sxr)).__x;
         }
       }
     }
@@ -553,6 +544,8 @@ __global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
         cur_xq = W.Xq + I->xq_off;
       }
       const int d = cur_d;
+      // lane r holds row r's statistics: one coalesced store of the batch's sorted statistics
+      if (QM != 0 && lane < Bc.bn) W.xs_sorted[Bc.bs + lane] = Bc.xs;
       if (cur_dp)
         seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s[0], c[0], cj[0],
                             objS, objC, cur_j, flush);

@@ -252,6 +252,8 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     else cp_async_wait<0>();
     __syncwarp();
     const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
+    // lane r holds row r's statistics: one coalesced store of the batch's sorted statistics
+    if (QM != 0 && lane < rows) xs_sorted[P0 + b * RB + lane] = xs_c;
     for (int r = 0; r < rows; ++r) {
       const int j = __shfl_sync(0xffffffffu, j_c, r);
       if (j != cur) {
@@ -275,7 +277,6 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       kahan_add(objS, objC, q);
       if constexpr (QM != 0) {
         const int64_t prow = P0 + b * RB + r;
-        if (lane == r) xs_sorted[prow] = xs_c;
         if constexpr (QM == 1) {
           __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * Kp;
 #pragma unroll
