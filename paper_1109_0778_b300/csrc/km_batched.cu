@@ -344,44 +344,50 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
                                          uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&s)[kMaxV],
                                          float (&c)[kMaxV], float (&cj)[kMaxV], float& objS, float& objC,
                                          int& cur_j, Flush&& flush) {
-  for (int r = 0; r < B.bn; ++r) {
-    const int j = __shfl_sync(0xffffffffu, B.j, r);
-    const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
-    if (j != cur_j) {
+  // rows that start a cluster run (lane r holds row r's label), found once per batch
+  const int jprev = __shfl_up_sync(0xffffffffu, B.j, 1);
+  const unsigned starts = __ballot_sync(0xffffffffu, lane < B.bn && B.j != (lane == 0 ? cur_j : jprev));
+  for (int r = 0; r < B.bn;) {
+    if ((starts >> r) & 1u) {  // the same for every lane
       flush();
-      cur_j = j;
+      cur_j = __shfl_sync(0xffffffffu, B.j, r);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int t = v * 32 + lane;
-        cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+        cj[v] = t < d ? C[(int64_t)cur_j * d + t] : 0.f;
       }
     }
-    float xr[V], qd = 0.f;
+    const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
+    const int rend = later ? __ffs(later) - 1 : B.bn;
+    for (; r < rend; ++r) {
+      const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
+      float xr[V], qd = 0.f;
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int t = v * 32 + lane;
-      xr[v] = t < d ? st[r * B.rs + t] : 0.f;
-      kahan_add(s[v], c[v], xr[v]);
-      const float df = __fsub_rn(xr[v], cj[v]);
-      qd = fmaf(df, df, qd);
-    }
-    kahan_add(objS, objC, qd);
-    if constexpr (QM != 0) {
-      const int64_t pr = B.bs + r - row0;  // sorted position within the instance
-      if constexpr (QM == 1) {
-        __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(xq) + pr * kp;
+      for (int v = 0; v < V; ++v) {
+        const int t = v * 32 + lane;
+        xr[v] = t < d ? st[r * B.rs + t] : 0.f;
+        kahan_add(s[v], c[v], xr[v]);
+        const float df = __fsub_rn(xr[v], cj[v]);
+        qd = fmaf(df, df, qd);
+      }
+      kahan_add(objS, objC, qd);
+      if constexpr (QM != 0) {
+        const int64_t pr = B.bs + r - row0;  // sorted position within the instance
+        if constexpr (QM == 1) {
+          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(xq) + pr * kp;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
-          if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
-        }
-      } else {
-        const float inv = pow2_inv(sxr);  // 1 / row scale, exact
-        uint8_t* row = xq + pr * kp;
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+          }
+        } else {
+          const float inv = pow2_inv(sxr);  // 1 / row scale, exact
+          uint8_t* row = xq + pr * kp;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
-          if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+          }
         }
       }
     }

@@ -254,51 +254,57 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
     // lane r holds row r's statistics: one coalesced store of the batch's sorted statistics
     if (QM != 0 && lane < rows) xs_sorted[P0 + b * RB + lane] = xs_c;
-    for (int r = 0; r < rows; ++r) {
-      const int j = __shfl_sync(0xffffffffu, j_c, r);
-      if (j != cur) {
+    // rows that start a cluster run (lane r holds row r's label), found once per batch
+    const int jprev = __shfl_up_sync(0xffffffffu, j_c, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lane < rows && j_c != (lane == 0 ? cur : jprev));
+    for (int r = 0; r < rows;) {
+      if ((starts >> r) & 1u) {  // the same for every lane
         if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
-        cur = j;
+        cur = __shfl_sync(0xffffffffu, j_c, r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int t = v * 32 + lane;
-          cj[v] = t < d ? C[(int64_t)j * d + t] : 0.f;
+          cj[v] = t < d ? C[(int64_t)cur * d + t] : 0.f;
         }
       }
-      float xr[V], q = 0.f;
+      const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
+      const int rend = later ? __ffs(later) - 1 : rows;
+      for (; r < rend; ++r) {
+        float xr[V], q = 0.f;
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int t = v * 32 + lane;
-        xr[v] = t < d ? st[r * RS + t] : 0.f;
-        kahan_add(s[v], c[v], xr[v]);
-        const float df = __fsub_rn(xr[v], cj[v]);
-        q = fmaf(df, df, q);
-      }
-      kahan_add(objS, objC, q);
-      if constexpr (QM != 0) {
-        const int64_t prow = P0 + b * RB + r;
-        if constexpr (QM == 1) {
-          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * Kp;
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          xr[v] = t < d ? st[r * RS + t] : 0.f;
+          kahan_add(s[v], c[v], xr[v]);
+          const float df = __fsub_rn(xr[v], cj[v]);
+          q = fmaf(df, df, q);
+        }
+        kahan_add(objS, objC, q);
+        if constexpr (QM != 0) {
+          const int64_t prow = P0 + b * RB + r;
+          if constexpr (QM == 1) {
+            __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * Kp;
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
-          }
-        } else if constexpr (QM == 3) {
-          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * 2 * Kp;
+            for (int v = 0; v < V; ++v) {
+              const int t = v * 32 + lane;
+              if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+            }
+          } else if constexpr (QM == 3) {
+            __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * 2 * Kp;
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            float hi, lo;
-            if (t < d) split_bf16(xr[v], row + t, row + Kp + t, hi, lo);
-          }
-        } else {
-          const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
-          uint8_t* row = Xq + prow * Kp;
+            for (int v = 0; v < V; ++v) {
+              const int t = v * 32 + lane;
+              float hi, lo;
+              if (t < d) split_bf16(xr[v], row + t, row + Kp + t, hi, lo);
+            }
+          } else {
+            const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
+            uint8_t* row = Xq + prow * Kp;
 #pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+            for (int v = 0; v < V; ++v) {
+              const int t = v * 32 + lane;
+              if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+            }
           }
         }
       }
