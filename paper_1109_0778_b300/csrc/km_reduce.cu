@@ -178,7 +178,7 @@ __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, i
 }
 
 // Rows of one gathered batch per stage of the segmented sum (two stages of at
-// most 4 KB per warp, so that two CTAs of 8 warps share an SM).
+// most 4 KB per warp, so that three CTAs of 8 warps share an SM).
 template <int V>
 __host__ __device__ constexpr int seg_rows() {
   return V == 1 ? 32 : (V == 2 ? 16 : (V <= 4 ? 8 : 4));
@@ -195,7 +195,7 @@ __host__ __device__ constexpr size_t seg_smem_bytes() {
 // xs at p; the codes equal those the quantisation stage produces for the same
 // point.
 template <int V, int QM>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
               const int32_t* __restrict__ perm, const int32_t* __restrict__ slab, double* __restrict__ sums64,
               Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs, int Kp,
@@ -439,7 +439,7 @@ cudaError_t init_segsum() {
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode, int Kp) {
   // two CTAs of 8 warps per SM; each warp takes a contiguous range of at least 64 positions
   int64_t blocks = (p.n + 8 * 64 - 1) / (8 * 64);
-  if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
+  if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
   const int V = (p.d + 31) / 32;
   switch (V) {
 #define KM_CASE(v)                                                                                               \
