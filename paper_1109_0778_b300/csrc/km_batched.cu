@@ -442,7 +442,7 @@ __device__ __forceinline__ int packed_width(int d) {
 }
 
 template <int QM>
-__global__ void __launch_bounds__(256, 2) b_segsum_kernel(BWork W) {
+__global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
@@ -689,7 +689,7 @@ cudaError_t init_batched() {
 
 cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s) {
   int64_t blocks = (W.R + 8 * 64 - 1) / (8 * 64);
-  if (blocks > 2 * num_sms()) blocks = 2 * num_sms();
+  if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
   if (qmode == 1) b_segsum_kernel<1><<<(int)blocks, 256, kSegSmem, s>>>(W);
   else if (qmode == 2) b_segsum_kernel<2><<<(int)blocks, 256, kSegSmem, s>>>(W);
   else b_segsum_kernel<0><<<(int)blocks, 256, kSegSmem, s>>>(W);
