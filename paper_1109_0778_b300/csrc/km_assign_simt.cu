@@ -306,6 +306,10 @@ assign_simt_kernel(const float* __restrict__ X, int64_t n, int d, const float* _
 // registers within a slab and in `state` between slabs; the last slab applies
 // the same error-bound test as the streaming kernel above.
 constexpr int kSlabMaxD = 128;
+// Floats between consecutive K rows of a staged centroid chunk (BN columns +
+// 4): 4 modulo 32, so that the slab fill (8 dimensions of 4 centroids per warp
+// copy) meets 32 distinct banks; rows stay 16-byte aligned.
+constexpr int BNP = BN + 4;
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -353,17 +357,24 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
   extern __shared__ __align__(16) float smem[];
   const int nsp = (ns + BN - 1) / BN * BN;  // slab columns padded to whole chunks
   const int xs_stride = SBM + 4;            // floats per staged dimension (a row of the transposed tile)
-  float* Cs = smem;                          // [nsp / BN][dp][BN]: per chunk, K rows BN floats apart
-  float* Hs = Cs + (size_t)dp * nsp;         // [nsp]
+  float* Cs = smem;                          // [nsp / BN][dp][BNP]: per chunk, K rows BNP floats apart
+  float* Hs = Cs + (size_t)dp * (nsp / BN) * BNP;  // [nsp]
   float* Xs0 = Hs + nsp;                     // 2 x [dp][xs_stride]: point tiles, transposed
   __shared__ unsigned int s_changed;
 
   const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
-  // slab of centroids, transposed; zero padding in [d, dp) and [ns, nsp)
-  for (int e = tid; e < dp * nsp; e += ST) {
-    const int j = e % nsp, t = e / nsp;
-    Cs[((size_t)(j / BN) * dp + t) * BN + (j % BN)] = (j < ns && t < d) ? __ldg(C + (int64_t)(j_lo + j) * d + t) : 0.f;
+  // slab of centroids, transposed, by 4-byte cp.async (every load in flight at once; the first
+  // tile's wait completes them): a warp copies 8 dimensions of 4 centroids per instruction;
+  // zero padding in [d, dp) and [ns, nsp)
+  for (int j = (tid >> 5) * 4 + (lane >> 3); j < nsp; j += ST / 8) {
+    float* dst = Cs + (size_t)(j / BN) * dp * BNP + (j % BN);
+    const float* src = C + (int64_t)(j_lo + (j < ns ? j : 0)) * d;
+    for (int t = lane & 7; t < dp; t += 8) {
+      if (j < ns && t < d) cp_async4(dst + t * BNP, src + t);
+      else dst[t * BNP] = 0.f;
+    }
   }
+  cp_async_commit();
   for (int j = tid; j < nsp; j += ST) Hs[j] = j < ns ? __ldg(chalf + j_lo + j) : INFINITY;
   // zero both point buffers once: padding dimensions [d, dp) stay zero
   for (int e = tid; e < 2 * dp * xs_stride; e += ST) Xs0[e] = 0.f;
@@ -407,7 +418,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
       }
     }
     for (int j0 = 0; j0 < nsp; j0 += BN) {
-      const float* Cc = Cs + (size_t)(j0 / BN) * dp * BN;  // this chunk's [dp][BN] block
+      const float* Cc = Cs + (size_t)(j0 / BN) * dp * BNP;  // this chunk's [dp][BNP] block
       float2 acc2[SR / 2][4];  // (acc[2p][c], acc[2p + 1][c]): one paired FMA per two rows
 #pragma unroll
       for (int p = 0; p < SR / 2; ++p)
@@ -419,7 +430,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
       for (int kk = 0; kk < dp; ++kk) {
         const float4 a0 = *reinterpret_cast<const float4*>(xr + kk * xs_stride);
         const float4 a1 = *reinterpret_cast<const float4*>(xr + kk * xs_stride + 4);
-        const float4 b = *reinterpret_cast<const float4*>(cr + kk * BN);
+        const float4 b = *reinterpret_cast<const float4*>(cr + kk * BNP);
         const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
                               make_float2(a1.z, a1.w)};
         const float bv[4] = {b.x, b.y, b.z, b.w};
@@ -509,7 +520,7 @@ assign_slab_kernel(const float* __restrict__ X, int64_t n, int d, int dp, const 
 }
 
 size_t slab_smem_bytes(int dp, int nsp, int rows) {
-  return ((size_t)dp * nsp + nsp + 2 * (size_t)dp * (rows + 4)) * sizeof(float);
+  return ((size_t)dp * (nsp / BN) * BNP + nsp + 2 * (size_t)dp * (rows + 4)) * sizeof(float);
 }
 
 // Centroids per slab of geometry G for dimension d (0: does not fit).
@@ -519,7 +530,8 @@ int slab_width_g(int d, int G) {
   const size_t budget = (G ? 113 : 227) * 1024 - 2048;  // per CTA
   const size_t fixed = 2 * (size_t)dp * ((G ? SlabGeo<1>::M : SlabGeo<0>::M) + 4) * sizeof(float);
   if (fixed >= budget) return 0;
-  int ns = (int)((budget - fixed) / (((size_t)dp + 1) * sizeof(float))) / BN * BN;
+  const size_t per_chunk = ((size_t)dp * BNP + BN) * sizeof(float);  // one chunk of BN centroids and its h_j
+  const int ns = (int)((budget - fixed) / per_chunk) * BN;
   return ns >= BN ? ns : 0;
 }
 

@@ -117,7 +117,7 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
 template <int V>
 cudaError_t recheck_v(const Problem& p, const Work& w, const float* h, const FlagRec* flags,
                       const unsigned long long* nflag, bool queue, cudaStream_t s) {
-  const int blocks = num_sms() * 8;  // latency-bound (dependent loads per flag): many warps in flight
+  const int blocks = num_sms() * 4;  // latency-bound: as many warps as are resident (4 CTAs at 64 registers)
   recheck_kernel<V><<<blocks, 256, 0, s>>>(p.X, p.d, p.C, h, p.k, flags, nflag, w.ctl, p.assign,
                                            queue ? w.fq_rows : nullptr, queue ? w.fq_old : nullptr,
                                            queue ? w.fq_cap : 0);
