@@ -659,7 +659,7 @@ cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s) {
 }
 
 cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
-  b_recheck_kernel<<<num_sms() * 8, 256, 0, s>>>(W);  // latency-bound: many warps in flight
+  b_recheck_kernel<<<num_sms() * 4, 256, 0, s>>>(W);  // latency-bound: as many warps as are resident (64 registers)
   return cudaGetLastError();
 }
 
