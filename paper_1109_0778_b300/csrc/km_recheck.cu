@@ -28,46 +28,65 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
   const int64_t nflag = (int64_t)*nflag_ptr;
   const float H = __uint_as_float(ctl->hmax_bits), Cmax = __uint_as_float(ctl->cmax_bits);
   unsigned int changed = 0;
-  for (int64_t f = warp; f < nflag; f += nwarps) {
-    const FlagRec rec = flags[f];
-    if (rec.nc == 0 && q_rows) {
+  // 32 flags per warp step, nwarps apart (few flags still spread one per warp): lane l reads
+  // flag f0 + l nwarps's header; the points whose candidates could not be narrowed are queued
+  // with one atomic per warp, the others are settled one at a time below
+  for (int64_t f0 = warp; f0 < nflag; f0 += nwarps * 32) {
+    const int64_t fl = f0 + lane * nwarps;
+    const bool have = fl < nflag;
+    int nc_l = -1, i_l = 0, old_l = 0;
+    if (have) {
+      nc_l = flags[fl].nc;
+      i_l = flags[fl].i;
+      old_l = flags[fl].old;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, have);
+    if (q_rows) {
       // all k candidates: queue the point for the tiled FP32 pass while the queue has room
-      unsigned long long slot = 0;
-      if (lane == 0) slot = atomicAdd(&ctl->n_fullq, 1ull);
-      slot = __shfl_sync(0xffffffffu, slot, 0);
-      if (slot < (unsigned long long)q_cap) {
-        if (lane == 0) {
-          q_rows[slot] = rec.i;
-          q_old[slot] = rec.old;
+      const unsigned qm = __ballot_sync(0xffffffffu, have && nc_l == 0);
+      if (qm) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->n_fullq, (unsigned long long)__popc(qm));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long slot = base + __popc(qm & ((1u << lane) - 1u));
+        const bool queued = ((qm >> lane) & 1u) && slot < (unsigned long long)q_cap;
+        if (queued) {
+          q_rows[slot] = i_l;
+          q_old[slot] = old_l;
         }
-        continue;
+        todo &= ~__ballot_sync(0xffffffffu, queued);
       }
     }
-    const float* x = X + (int64_t)rec.i * d;
-    float xv[V];
+    while (todo) {
+      const int l = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const FlagRec rec = flags[f0 + l * nwarps];
+      const float* x = X + (int64_t)rec.i * d;
+      float xv[V];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int t = v * 32 + lane;
-      xv[v] = t < d ? x[t] : 0.f;
-    }
-    int jb;
-    if (rec.nc > 0) {
-      float best = INFINITY;
-      jb = rec.cand[0];
-      for (int q = 0; q < rec.nc; ++q) {
-        const int j = rec.cand[q];
-        const float D = warp_sqdist<V>(xv, C + (int64_t)j * d, d, lane);
-        if (D < best) {  // candidates arrive in increasing index order
-          best = D;
-          jb = j;
-        }
+      for (int v = 0; v < V; ++v) {
+        const int t = v * 32 + lane;
+        xv[v] = t < d ? x[t] : 0.f;
       }
-    } else {
-      jb = nearest_all<V>(xv, xsh, C, h, k, d, lane, H, Cmax);
-    }
-    if (lane == 0) {
-      assign[rec.i] = jb;
-      changed += (rec.old != jb);
+      int jb;
+      if (rec.nc > 0) {
+        float best = INFINITY;
+        jb = rec.cand[0];
+        for (int q = 0; q < rec.nc; ++q) {
+          const int j = rec.cand[q];
+          const float D = warp_sqdist<V>(xv, C + (int64_t)j * d, d, lane);
+          if (D < best) {  // candidates arrive in increasing index order
+            best = D;
+            jb = j;
+          }
+        }
+      } else {
+        jb = nearest_all<V>(xv, xsh, C, h, k, d, lane, H, Cmax);
+      }
+      if (lane == 0) {
+        assign[rec.i] = jb;
+        changed += (rec.old != jb);
+      }
     }
   }
   if (lane == 0 && changed) atomicAdd(&ctl->n_changed, (unsigned long long)changed);
