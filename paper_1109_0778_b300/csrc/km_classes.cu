@@ -93,7 +93,8 @@ gda_cov_kernel(const float* __restrict__ X, int64_t n, int d, const int32_t* __r
   const int sr = tid >> 3, sg = tid & 7;                  // staged rows sr, sr + 32; 16-column group
   const int side = sg >> 2, c0 = (sg & 3) * 16;           // a or b range, first column in it
   const int t0 = (side ? b0 : a0) + c0;                   // first matrix column of the group
-  const bool v4 = (d & 3) == 0;                           // rows start on 16-byte boundaries
+  // rows start on 16-byte boundaries (d a multiple of 4, X and the class means 16-byte aligned)
+  const bool v4 = (d & 3) == 0 && (((uintptr_t)X | (uintptr_t)mu) & 15) == 0;
   float stage[2][16];
   auto load_row = [&](int64_t i, float (&st)[16]) {  // centred values of row i, columns t0 .. t0 + 15
     if (i < r1) {

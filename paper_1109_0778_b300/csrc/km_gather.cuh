@@ -26,9 +26,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // elements. The warp's lanes split into groups of L (a power of two covering a
 // row's 16-byte pieces, at most 32), one row per group, so a warp instruction
 // moves 32 / L rows. 16-byte pieces when rows start on 16-byte boundaries
-// (d a multiple of 4), else 4-byte ones. Commits one group.
+// (d a multiple of 4 and X itself 16-byte aligned), else 4-byte ones. Commits
+// one group.
 __device__ __forceinline__ void gather_rows(float* st, int rs, const float* X, int d, int bn, int64_t off, int lane) {
-  const bool v4 = (d & 3) == 0;
+  const bool v4 = (d & 3) == 0 && ((uintptr_t)X & 15) == 0;
   const int cpr = v4 ? d >> 2 : d;  // pieces per row
   int lg = 0;
   while ((1 << lg) < cpr && lg < 5) ++lg;

@@ -107,7 +107,7 @@ __device__ int nearest_all(const float (&xv)[V], float* xsh, const float* __rest
   // screen: plain FP32 scores, lanes over centroids
   Top3 t3;
   t3.init();
-  const bool vec4 = (d & 3) == 0;
+  const bool vec4 = (d & 3) == 0 && ((uintptr_t)C & 15) == 0;  // centroid rows on 16-byte boundaries
   for (int j = lane; j < k; j += 32) {
     const float* c = C + (int64_t)j * d;
     float dot = 0.f;

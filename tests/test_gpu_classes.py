@@ -71,6 +71,19 @@ def test_gda_matches_oracle(km, ref, n, d, ncls):
     check_gda(ref, X, y, ncls, phi, mu, sigma)
 
 
+def test_gda_rows_not_16_byte_aligned(km, ref):
+    """X one float into a buffer (4-byte but not 16-byte aligned): the gathers and the covariance
+    staging must fall back to 4-byte loads."""
+    n, d, ncls = 3000, 64, 6
+    X, y = labelled(4242, n, d, ncls)
+    buf = torch.zeros(n * d + 1, dtype=torch.float32, device=DEV)
+    Xd = buf[1:].view(n, d)
+    Xd.copy_(torch.from_numpy(X))
+    assert Xd.is_contiguous() and Xd.data_ptr() % 16 == 4
+    phi, mu, sigma = km.gda_train(Xd, torch.from_numpy(y).to(DEV), ncls)
+    check_gda(ref, X, y, ncls, phi, mu, sigma)
+
+
 @pytest.mark.parametrize("n,d,ncls", [(1, 1, 1), (6, 4, 9), (2000, 30, 5), (30000, 256, 20), (4097, 129, 2)])
 def test_nb_matches_oracle(km, ref, n, d, ncls):
     rng = np.random.default_rng(n + d)

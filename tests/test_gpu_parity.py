@@ -63,6 +63,31 @@ def test_shapes_ragged(km, ref, n, d, k):
     assert near <= max(2, n // 1000)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("n,d,k", [(3000, 64, 256), (2100, 20, 70)])
+def test_rows_not_16_byte_aligned(km, ref, precision, n, d, k):
+    """X and C starting 4 bytes past a 16-byte boundary (contiguous views one float into a
+    buffer): every kernel that reads them in 16-byte pieces must fall back to 4-byte ones, so
+    any float-aligned X and C give the same parity."""
+    X = synth.mixture(5150 + n + d, n, d, k, 5.0, 1.0)
+    buf = torch.zeros(n * d + 1, dtype=torch.float32, device=DEV)
+    Xd = buf[1:].view(n, d)
+    Xd.copy_(torch.from_numpy(X))
+    assert Xd.is_contiguous() and Xd.data_ptr() % 16 == 4
+    cbuf = torch.zeros(k * d + 1, dtype=torch.float32, device=DEV)
+    Cd = cbuf[1:].view(k, d)
+    Cd.copy_(torch.from_numpy(X[:k].copy()))
+    assert Cd.is_contiguous() and Cd.data_ptr() % 16 == 4
+    assign, sums, counts = km.alloc_outputs(Xd, Cd)
+    for it in range(2):
+        C_in = Cd.cpu().numpy().astype(np.float64)
+        out = km.step(Xd, Cd, assign, sums, counts, precision=precision, warm_start=it > 0)
+        a = out.assign.cpu().numpy()
+        near, _ = parity.check_assign(ref, X, C_in, a)
+        assert near <= 2
+        parity.check_update(ref, X, C_in, a, Cd.cpu().numpy(), out.sums.cpu().numpy(), out.counts.cpu().numpy())
+
+
 def test_k_equals_one_and_n(km, ref):
     X = synth.mixture(77, 700, 9, 3, 4.0, 1.0)
     gpu_steps(km, ref, X, X[:1].copy(), 2)
