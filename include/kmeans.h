@@ -29,7 +29,9 @@
  * is a DEVICE pointer (cudaMalloc'd or managed) owned by the caller; the
  * library never frees it. The library owns only its workspace (cached per
  * device, grown on demand, released at process exit). X must not overlap any
- * output array.
+ * output array. Arrays need only the alignment of their element type (4
+ * bytes for float and int32): kernels that read X or C in 16-byte pieces
+ * check the base address and fall back to 4-byte accesses.
  *
  * Streams: work is issued on opts->stream (NULL = the legacy default stream)
  * and the call synchronises that stream before it returns, so outputs and
