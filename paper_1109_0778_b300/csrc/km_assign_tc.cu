@@ -527,15 +527,20 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             tc_fence_after_sync();
             const uint32_t a_addr = smem_u32(A0 + abs_[u] * a_bytes);
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
+            // descriptors of the slot's first K block; a byte offset o inside shared memory
+            // advances the 14-bit start-address field by o / 16 without a carry (< 256 KB)
+            const uint64_t a_desc = sdesc_k_sw128(a_addr), b_desc = sdesc_k_sw128(b_addr);
             // K blocks of one product; two-part codes take three: (hi, hi), (lo, hi), (hi, lo)
             const int mk = split ? it.nkb >> 1 : it.nkb;
             for (int seg = 0; seg < (split ? 3 : 1); ++seg) {
               const int ka = seg == 1 ? mk : 0, kc = seg == 2 ? mk : 0;
               for (int kb = 0; kb < mk; ++kb) {
+                const uint64_t a_kb = a_desc + (uint64_t)(((ka + kb) * (BM * ROWB)) >> 4);
+                const uint64_t b_kb = b_desc + (uint64_t)(((kc + kb) * b_kblk) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                  const uint64_t ad = sdesc_k_sw128(a_addr + (ka + kb) * (BM * ROWB) + kk * 32);
-                  const uint64_t bd = sdesc_k_sw128(b_addr + (kc + kb) * b_kblk + kk * 32);
+                  const uint64_t ad = a_kb + (uint64_t)(kk * 2);  // + 32 bytes
+                  const uint64_t bd = b_kb + (uint64_t)(kk * 2);
                   if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
                   else mma_bf16(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
                 }
