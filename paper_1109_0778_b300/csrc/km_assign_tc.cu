@@ -441,6 +441,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       Item it;
       it.b = -1;
       int labn = -2;                   // label of the next pair's first row, loaded a pair ahead (-2: not loaded)
+      int ab = 0, sb = 0;              // next A slot and B stage (lt % nab, gc % stages, kept incrementally)
+      uint32_t aph = 0, sph = 0;       // and their phase bits ((lt / nab) & 1, (gc / stages) & 1)
       for (int64_t ga = tr.t0; ga < tr.t1 && ok;) {
         if (seek<BATCH>(P, &mapX, &mapC, ga, it)) {
           labn = -2;
@@ -463,23 +465,30 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           labn = (gn < tr.t1 && gn < it.tend) ? tile_label(P, it, gn - it.tile0) : -2;
         }
         for (int u = 0; u < ntp && ok; ++u, ++lt) {
-          const int ab = lt % nab;
-          if (!mbar_wait(&a_empty[ab], ((lt / nab) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
+          if (!mbar_wait(&a_empty[ab], aph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB);
           const int row0 = (int)((u ? gb - it.tile0 : tile0) * BM);
           for (int kb = 0; kb < it.nkb; ++kb)
             tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, row0);
           last_a = ab;
-          last_aph = (lt / nab) & 1;
+          last_aph = aph;
+          if (++ab == nab) {
+            ab = 0;
+            aph ^= 1;
+          }
         }
         for (int cc = 0, c = c0; cc < it.nchunks && ok; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
-          const int s = gc % stages;
-          if (!mbar_wait(&b_empty[s], ((gc / stages) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
+          const int s = sb;
+          if (!mbar_wait(&b_empty[s], sph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
           mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk);
           for (int kb = 0; kb < it.nkb; ++kb)
             tma_load_2d(B0 + s * b_bytes + kb * b_kblk, it.mapC, &b_full[s], kb * KBE, c * BN);
           last_s = s;
-          last_sph = (gc / stages) & 1;
+          last_sph = sph;
+          if (++sb == stages) {
+            sb = 0;
+            sph ^= 1;
+          }
         }
         ga = ntp == 2 ? gb + tr.ts : gb;
       }
@@ -497,6 +506,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     if (lane == 0) {
       int lt = 0, gc = 0;
       int gu[2] = {0, 0};  // chunks issued per epilogue group
+      int sb = 0;          // B stage gc % stages and its phase (gc / stages) & 1, kept incrementally
+      uint32_t sph = 0;
       bool ok = true, issued = false;
       const bool split = !BATCH && !FP8 && P.split;
       Item it;
@@ -517,8 +528,12 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (!ok) break;
         tc_fence_after_sync();
         for (int cc = 0; cc < it.nchunks && ok; ++cc, ++gc) {
-          const int s = gc % stages;
-          if (!mbar_wait(&b_full[s], (gc / stages) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
+          const int s = sb;
+          if (!mbar_wait(&b_full[s], sph, &abort_s, P.wait_ns)) { ok = false; break; }
+          if (++sb == stages) {
+            sb = 0;
+            sph ^= 1;
+          }
           tc_fence_after_sync();
           const uint32_t b_addr = smem_u32(B0 + s * b_bytes);
           for (int u = 0; u < ntp; ++u) {
