@@ -16,11 +16,13 @@
 // instance once and walks its tiles in order. The epilogue loads the row
 // metadata of the CTA's next tile while it works on the current one.
 //
-// Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer and TMEM
-// owner, warps 2-9 = epilogue in two groups of four (one warp per TMEM lane
-// quarter). Row tiles go in pairs: each B chunk is loaded once and multiplied
-// with both tiles of the pair, group u scores tile u (accumulators in TMEM
-// buffers u and u + 2), and each row has a single owner thread that sees all of
+// Roles (352 threads): warp 0 = TMA producer, warp 1 = MMA issuer of the first
+// tile of each pair and TMEM owner, warps 2-9 = epilogue in two groups of four
+// (one warp per TMEM lane quarter), warp 10 = MMA issuer of the second tile.
+// Row tiles go in pairs: each B chunk is loaded once and multiplied with both
+// tiles of the pair (each issuer commits the B stage, so it is refilled after
+// both), group u scores tile u (accumulators in TMEM buffers u and u + 2), and
+// each row has a single owner thread that sees all of
 // its columns. h_j (and the FP8 scales) are staged in shared memory once per
 // CTA. Every mbarrier wait is bounded in time; on
 // expiry the kernel records KM_ETIMEOUT, drains what it issued, frees TMEM and
@@ -67,7 +69,7 @@ using namespace tc;
 
 constexpr int BM = 128;
 constexpr int NEPI = 8;                      // epilogue warps: two per TMEM lane quarter
-constexpr int NTHREADS = 64 + 32 * NEPI;
+constexpr int NTHREADS = 96 + 32 * NEPI;  // producer, MMA issuer 0, epilogue, MMA issuer 1
 constexpr uint32_t ROWB = 128;               // bytes of one K block row
 constexpr uint32_t TMEM_COLS = 512;          // 4 accumulator buffers x up to 128 columns
 constexpr int NACC = 4;
@@ -369,7 +371,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   // accesses through derived pointers (h_j in the epilogue) compile to shared-memory loads
   uint8_t* smem = smem_raw + ((1024u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 1023u)) & 1023u);
   __shared__ uint64_t a_full[MAX_ABUF], a_empty[MAX_ABUF], b_full[MAX_STAGES], b_empty[MAX_STAGES];
-  __shared__ uint64_t acc_full[NACC], acc_empty[NACC], drain_bar, never_bar;
+  __shared__ uint64_t acc_full[NACC], acc_empty[NACC], drain_bar, drain_bar1, never_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s, halt_s;
 
@@ -405,9 +407,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     }
     for (int s = 0; s < stages; ++s) {
       mbar_init(&b_full[s], 1);
-      mbar_init(&b_empty[s], 1);
+      mbar_init(&b_empty[s], pairs ? 2 : 1);  // one commit per MMA issuer
     }
     mbar_init(&drain_bar, 1);
+    mbar_init(&drain_bar1, 1);
     mbar_init(&never_bar, 1);  // nothing ever arrives: the timeout test waits on it
     fence_mbar_init();
   }
@@ -419,7 +422,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     tmem_alloc(&tmem_base_s, TMEM_COLS);
     tmem_relinquish();
   }
-  if (!BATCH && warp >= 2) {  // batched launches stage h per instance in the epilogue
+  if (!BATCH && warp >= 2 && warp < 2 + NEPI) {  // batched launches stage h per instance in the epilogue
     for (int j = threadIdx.x - 64; j < kpmax; j += 32 * NEPI) Hs[j] = __ldg(P.h + j);
   }
   tc_fence_before_sync();
@@ -501,12 +504,16 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (last_s >= 0) mbar_wait(&b_full[last_s], last_sph, &no_abort, 10000000ull);
       }
     }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer
-    if (lane == 0) {
-      int lt = 0, gc = 0;
-      int gu[2] = {0, 0};  // chunks issued per epilogue group
-      int sb = 0;          // B stage gc % stages and its phase (gc / stages) & 1, kept incrementally
+  } else if (warp == 1 || warp == 2 + NEPI) {
+    // ---------------------------------------------------------------- MMA issuers
+    // Two issuers, each one thread: issuer me (warp 1, or the warp after the epilogue) issues the
+    // MMAs of tile u = me of every pair, so that the two tiles' instruction streams run side by
+    // side (one issuing thread was the limiter); both walk every chunk and each commits the B stage.
+    const int me = warp == 1 ? 0 : 1;
+    if (lane == 0 && (me == 0 || pairs)) {
+      int lt = 0;
+      int gu = 0;          // chunks issued for this issuer's epilogue group
+      int sb = 0;          // B stage and its phase, kept incrementally
       uint32_t sph = 0;
       bool ok = true, issued = false;
       const bool split = !BATCH && !FP8 && P.split;
@@ -520,14 +527,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         }
         const int64_t gb = ga + tr.ts;
         const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
-        int abs_[2];
-        for (int u = 0; u < ntp; ++u) {
-          abs_[u] = (lt + u) % nab;
-          if (!mbar_wait(&a_full[abs_[u]], ((lt + u) / nab) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
-        }
-        if (!ok) break;
+        const bool mine = me < ntp;
+        const int ab = (lt + me) % nab;
+        if (mine && !mbar_wait(&a_full[ab], ((lt + me) / nab) & 1, &abort_s, P.wait_ns)) { ok = false; break; }
         tc_fence_after_sync();
-        for (int cc = 0; cc < it.nchunks && ok; ++cc, ++gc) {
+        for (int cc = 0; cc < it.nchunks && ok; ++cc) {
           const int s = sb;
           if (!mbar_wait(&b_full[s], sph, &abort_s, P.wait_ns)) { ok = false; break; }
           if (++sb == stages) {
@@ -535,17 +539,14 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             sph ^= 1;
           }
           tc_fence_after_sync();
-          const uint32_t b_addr = smem_u32(B0 + s * b_bytes);
-          for (int u = 0; u < ntp; ++u) {
-            const int buf = 2 * (gu[u] & 1) + u;
-            if (!mbar_wait(&acc_empty[buf], ((gu[u] >> 1) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
+          if (mine) {
+            const uint32_t b_addr = smem_u32(B0 + s * b_bytes);
+            const int buf = 2 * (gu & 1) + me;
+            if (!mbar_wait(&acc_empty[buf], ((gu >> 1) & 1) ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
             tc_fence_after_sync();
-            const uint32_t a_addr = smem_u32(A0 + abs_[u] * a_bytes);
+            const uint32_t a_addr = smem_u32(A0 + ab * a_bytes);
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
-            // descriptors of the slot's first K block; a byte offset o inside shared memory
-            // advances the 14-bit start-address field by o / 16 without a carry (< 256 KB)
             const uint64_t a_desc = sdesc_k_sw128(a_addr), b_desc = sdesc_k_sw128(b_addr);
-            // K blocks of one product; two-part codes take three: (hi, hi), (lo, hi), (hi, lo)
             const int mk = split ? it.nkb >> 1 : it.nkb;
             for (int seg = 0; seg < (split ? 3 : 1); ++seg) {
               const int ka = seg == 1 ? mk : 0, kc = seg == 2 ? mk : 0;
@@ -563,12 +564,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             }
             issued = true;
             mma_commit(&acc_full[buf]);
-            ++gu[u];
+            ++gu;
           }
-          if (ok) mma_commit(&b_empty[s]);
+          mma_commit(&b_empty[s]);
         }
-        if (ok)
-          for (int u = 0; u < ntp; ++u) mma_commit(&a_empty[abs_[u]]);
+        if (ok && mine) mma_commit(&a_empty[ab]);
         lt += ntp;
         ga = ntp == 2 ? gb + tr.ts : gb;
       }
@@ -576,10 +576,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         abort_s = 1;
         record_timeout<BATCH>(P);
       }
-      if (issued) {  // every MMA this thread issued has completed once drain_bar flips
-        mma_commit(&drain_bar);
+      if (issued) {  // every MMA this thread issued has completed once its drain barrier flips
+        uint64_t* db = me ? &drain_bar1 : &drain_bar;
+        mma_commit(db);
         int dummy = 0;
-        mbar_wait(&drain_bar, 0, &dummy, P.wait_ns);
+        mbar_wait(db, 0, &dummy, P.wait_ns);
       }
     }
   } else {
