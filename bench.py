@@ -4,11 +4,17 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
 A step is one ``kmeans_run`` call: every Lloyd iteration of the workload (20 for
-the default 1M x 64 x 256 FP32 workload) as one graph-captured sequence of the
-library's kernels, on inputs already resident in HBM. ``value`` is Lloyd
-iterations per second over all ranks; the distance TFLOP/s (2nkd per iteration)
-is reported beside it. ``e2e`` times the same runs through ``kmeans_run_host``
-from pinned host buffers, copies included.
+the default 4,194,304 x 128 x 1024 precision workload) as one graph-captured
+sequence of the library's kernels, on inputs already resident in HBM. The
+headline is the BF16 distance contraction with the FP32 near-tie re-check;
+``value`` is Lloyd iterations per second over all ranks and the distance
+TFLOP/s (2nkd per iteration) is reported beside it. ``e2e`` times the same runs
+through ``kmeans_run_host`` from pinned host buffers, copies included.
+
+On one GPU the default run also measures, on the same data, the metric's
+comparison arms (plain FP32, E4M3 + re-check, two-part BF16 + re-check), the
+other workloads (8M x 256 x 8192 E4M3, the 512-instance batch, 10k x 16 x 8),
+and the FP32 FFMA and FP8 tensor peaks that their roofline fractions use.
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (a
 bounded sample of the same workload per step), the one other place this script
@@ -41,7 +47,10 @@ import synth  # noqa: E402
 from synth import SPADE_WORKLOADS, WORKLOADS  # noqa: E402
 
 METRIC = "Lloyd iter/s + distance TFLOP/s: FP32 vs BF16/FP8+recheck, exact assignments"
-DEFAULT_WORKLOAD = "fp32_n1M_d64_k256"
+DEFAULT_WORKLOAD = "prec_n4M_d128_k1024"
+# precision of a workload's headline line (else the workload's first)
+HEADLINE_PRECISION = {"prec_n4M_d128_k1024": "bf16", "large_n8M_d256_k8192": "fp8"}
+DTYPE_NAMES = {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3", "bf16x3": "bf16x3"}
 STAGE_KERNELS = ("prep", "assign", "recheck", "count", "scan", "scatter", "segsum", "divide")
 # Source file of each stage's kernel (a change to it voids a stored ncu traffic figure).
 KERNEL_SOURCES = {"assign": {"fp32": "km_assign_simt.cu", "bf16": "km_assign_tc.cu", "fp8": "km_assign_tc.cu",
@@ -57,7 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + sorted(TRAIN_WORKLOADS) + sorted(SPADE_WORKLOADS))
-    ap.add_argument("--precision", default=None, help="fp32 | bf16 | fp8 | bf16x3 (default: the workload's first)")
+    ap.add_argument("--precision", default=None,
+                    help="fp32 | bf16 | fp8 | bf16x3 (default: bf16 on the precision workload, else the workload's first)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle sample")
     ap.add_argument("--rows", type=int, default=0, help="use only the first ROWS points (profiling cases)")
     ap.add_argument("--instances", type=int, default=0,
@@ -65,7 +75,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip the FP32/BF16/FP8 comparison on the 4M x 128 x 1024 precision workload")
+                    help="headline only: skip the precision arms, the other workloads and the peak measurements")
     return ap.parse_args(argv)
 
 
@@ -304,7 +314,7 @@ def batched_problems(torch, dev, w, limit=0):
     return inst, probs, flops, xbytes, (c_flat, c0_flat)
 
 
-def run_batched(args, torch, dev, dist, rank, world, local):
+def run_batched(args, torch, dev, dist, rank, world, local, emit=True):
     from paper_1109_0778_b300 import kmeans as km
 
     w = WORKLOADS["batched_512"]
@@ -368,54 +378,12 @@ def run_batched(args, torch, dev, dist, rank, world, local):
             "gpu_launches": launches_tot,
             "clocks": clocks, "e2e": None, "cpu_baseline": None, "peaks_source": peak_src,
         }
+        if not emit:
+            return {k: line[k] for k in ("value", "unit", "ms_per_step", "config", "distance_tflops",
+                                          "stage_ms_per_iter", "flagged_last_iter", "roofline", "gpu_launches",
+                                          "clocks")} | {"ms_per_iter": ms_iter, "steps": args.steps}
         print(json.dumps(line), flush=True)
     return 0
-
-
-def precision_variants(torch, dev, steps=2, warmup=1):
-    """FP32 vs BF16 vs FP8 vs two-part BF16 (each + FP32 re-check) on the 4M x 128 x 1024 workload,
-    kmeans_run per step. The two-part BF16 path runs three BF16 products per distance, so its
-    tensor roofline counts 3 x 2nkd flops per iteration."""
-    from paper_1109_0778_b300 import kmeans as km
-
-    w = WORKLOADS["prec_n4M_d128_k1024"]
-    peaks, _ = measured_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    X, _ = synth.workload_data(w, rows=w.n)
-    Xd = torch.from_numpy(X).to(dev)
-    C0 = Xd[: w.k].clone()
-    del X
-    out = {"workload": w.name, "iters_per_step": w.iters}
-    for prec in ("fp32", "bf16", "fp8", "bf16x3"):
-        C = C0.clone()
-        a, s, c = km.alloc_outputs(Xd, C)
-        for _ in range(warmup):
-            C.copy_(C0)
-            km.run(Xd, C, w.iters, assign=a, sums=s, counts=c, precision=prec)
-        ms = 0.0
-        for _ in range(steps):
-            C.copy_(C0)
-            o = km.run(Xd, C, w.iters, assign=a, sums=s, counts=c, precision=prec, profile=True)
-            ms += o.stats["ms"]
-        ips = steps * w.iters / (ms / 1e3)
-        assign_ms = o.stats["stage_ms"]["assign"] / w.iters
-        products = 3 if prec == "bf16x3" else 1
-        achieved = products * w.flops_per_iter / (assign_ms / 1e3) / 1e12
-        if prec == "fp32":
-            peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
-            bound = "alu"
-        else:
-            peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
-            bound = "tensor"
-        out[prec] = {"iter_s": ips, "distance_tflops": ips * w.flops_per_iter / 1e12,
-                     "assign_ms_per_iter": assign_ms,
-                     "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": achieved / peak, "traffic": stored_traffic("assign", prec, w.name)},
-                     "stage_ms_per_iter": {k: v / w.iters for k, v in o.stats["stage_ms"].items()},
-                     "flagged_last_iter": o.stats["n_flagged"], "objective": o.stats["objective"]}
-    for prec in ("bf16", "fp8", "bf16x3"):
-        out[prec]["speedup_vs_fp32"] = out[prec]["iter_s"] / out["fp32"]["iter_s"]
-    return out
 
 
 # Keyed-reduce training workloads (GDA: labelled Gaussian mixture; NB: Poisson feature counts).
@@ -602,6 +570,203 @@ def run_spade(args, torch, dev, dist, rank, world, local):
     return 0
 
 
+def single_problem(torch, dev, w, pinned=True):
+    """Host (pinned) and device copies of a single-instance workload: X, C0."""
+    if pinned:
+        Xh = torch.empty((w.n, w.d), dtype=torch.float32, pin_memory=True)
+        synth.mixture(w.seed, w.n, w.d, w.m, w.R, w.sigma, out=Xh.numpy())
+    else:
+        Xh = torch.from_numpy(synth.mixture(w.seed, w.n, w.d, w.m, w.R, w.sigma))
+    C0h = Xh[: w.k].clone()
+    if pinned:
+        C0h = C0h.pin_memory()
+    return Xh, C0h, Xh.to(dev), C0h.to(dev)
+
+
+def time_runs(torch, km, dev, local, dist, Xd, C0d, w, prec, steps, warmup):
+    """Device-timed kmeans_run calls (each = w.iters graph-captured Lloyd iterations from C0).
+
+    ``warmup`` untimed calls, then ``steps`` calls between two CUDA events on the launching
+    stream, bracketed by a synchronize (and a barrier under torchrun); clocks sampled meanwhile.
+    Returns the slowest rank's time, per-stage device times (CUDA events recorded between the
+    stages inside the captured graph) and the last call's statistics."""
+    stream = torch.cuda.current_stream(dev)
+    Cd = C0d.clone()
+    a, s, c = km.alloc_outputs(Xd, Cd)
+
+    def one():
+        Cd.copy_(C0d)
+        return km.run(Xd, Cd, w.iters, assign=a, sums=s, counts=c, precision=prec, profile=True, stream=stream)
+
+    for _ in range(max(warmup, 0)):
+        one()
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
+    launches = 0
+    out = None
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        ev0.record(stream)
+        for _ in range(steps):
+            out = one()
+            for kname, v in out.stats["stage_ms"].items():
+                stage_tot[kname] += v
+            launches += out.stats["launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    t = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, dev)
+    st = out.stats
+    return {"t": t, "iter_s": steps * w.iters / t, "ms_per_step": t * 1e3 / steps,
+            "stage_ms_per_iter": {k: v / steps / w.iters for k, v in stage_tot.items()},
+            "assign_ms": stage_tot["assign"] / (steps * w.iters), "launches": launches, "clocks": clk.summary(),
+            "last": {"objective": st["objective"], "n_flagged": st["n_flagged"], "n_full": st["n_full"],
+                     "n_queued": st["n_queued"], "iters_bf16": st["iters_bf16"], "n_empty": st["n_empty"]}}
+
+
+def time_e2e(torch, km, dist, dev, Xh, C0h, w, prec, reps):
+    """The same runs through kmeans_run_host from pinned host buffers: the copy of X and C in and
+    of C, assign, sums and counts out are inside the timed region."""
+    Ch = C0h.clone().pin_memory()
+    ah = torch.empty(w.n, dtype=torch.int32, pin_memory=True)
+    sh = torch.empty((w.k, w.d), dtype=torch.float32, pin_memory=True)
+    ch = torch.empty(w.k, dtype=torch.int32, pin_memory=True)
+    km.run_host(Xh, Ch, w.iters, 0.0, ah, sh, ch, precision=prec)  # warm-up (staging buffers, graph)
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        Ch.copy_(C0h)
+        km.run_host(Xh, Ch, w.iters, 0.0, ah, sh, ch, precision=prec)
+    te = max_over_ranks(dist, time.perf_counter() - t0, dev)
+    _, world, _ = dist_env()
+    return {"value": aggregate_rate(reps * w.iters, world, te), "unit": "iter/s",
+            "h2d_bytes_per_step": 4 * w.n * w.d + 4 * w.k * w.d,
+            "d2h_bytes_per_step": 4 * w.k * w.d * 2 + 4 * w.n + 4 * w.k, "reps": reps,
+            "api": "kmeans_run_host (pinned host buffers)"}
+
+
+def measure_peaks(torch, km, dev):
+    """FP32 SIMT and FP8 tensor peaks measured on this GPU now (best of several, CUDA events).
+
+    FFMA: the library's probe kernel (independent FMA chains, 8 CTAs x 256 threads per SM,
+    scalar FFMA and packed FFMA2; the faster counts). FP8: torch._scaled_mm (cuBLASLt) E4M3 x
+    E4M3 -> BF16 on 8192^3 with unit scales, 2 x 8192^3 flop."""
+    res = {}
+    for packed in (False, True):
+        km.probe_ffma(1 << 12, packed=packed)
+        best = 0.0
+        for _ in range(3):
+            fl, ms = km.probe_ffma(1 << 16, packed=packed)
+            best = max(best, fl / (ms / 1e3) / 1e12)
+        res["ffma2_tflops" if packed else "ffma_tflops"] = best
+    res["fp32_simt_tflops"] = max(res["ffma_tflops"], res["ffma2_tflops"])
+    try:
+        N = 8192
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn(N, N, device=dev, generator=g).to(torch.float8_e4m3fn)
+        b = torch.randn(N, N, device=dev, generator=g).to(torch.float8_e4m3fn).t()
+        one = torch.tensor(1.0, device=dev)
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 0.0
+        for _ in range(10):
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            best = max(best, 2.0 * N ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        res["fp8_tflops"] = best
+        del a, b
+    except Exception as exc:  # noqa: BLE001 -- reported, the nominal ratio then stands in
+        res["fp8_tflops"] = None
+        res["fp8_error"] = f"{type(exc).__name__}: {exc}"[:200]
+    res["how"] = ("FFMA: kmeans_probe_ffma, 2 x FMAs / CUDA-event time of one launch, best of 3, max of scalar "
+                  "and packed; FP8: torch._scaled_mm E4M3 8192^3 -> BF16, best of 10 after 3 warm-ups")
+    torch.cuda.empty_cache()
+    return res
+
+
+def tensor_peak(prec, peaks, live, burst):
+    """(peak TFLOP/s, source) of the tensor-core arithmetic a precision runs on."""
+    key = "bf16_tflops" if burst else "bf16_tflops_sustained"
+    if prec == "fp8":
+        if live and live.get("fp8_tflops"):
+            if burst:
+                return live["fp8_tflops"], "FP8 E4M3 measured now (torch._scaled_mm 8192^3, burst)"
+            ratio = peaks["bf16_tflops_sustained"] / peaks["bf16_tflops"]
+            return live["fp8_tflops"] * ratio, "FP8 measured now x (BF16 sustained / burst)"
+        return 2.0 * peaks[key], f"2 x BF16 {'burst' if burst else 'sustained'} (nominal FP8/BF16 ratio)"
+    return peaks[key], f"BF16 {'burst' if burst else 'sustained'} ({'MEASURED_PEAKS.json'})"
+
+
+def assign_roofline(prec, w, r, peaks, peak_src, live, sms):
+    """Roofline of the dominant kernel (the fused assignment): 2nkd algorithmic flop per launch
+    (3 x for the two-part BF16 products) over the launch's mean CUDA-event time. A timed region
+    under 1.5 s is compared with the burst peak, a longer one with the sustained peak."""
+    burst = r["t"] < 1.5
+    products = 3 if prec == "bf16x3" else 1
+    achieved = products * w.flops_per_iter / (r["assign_ms"] / 1e3) / 1e12
+    if prec == "fp32":
+        if live and live.get("fp32_simt_tflops"):
+            peak, src = live["fp32_simt_tflops"], "FP32 FFMA measured now (kmeans_probe_ffma)"
+        else:
+            peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
+            src = f"nominal FFMA: {sms} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz"
+        bound, kern = "alu", "assign_simt (FP32 FFMA)"
+    else:
+        peak, src = tensor_peak(prec, peaks, live, burst)
+        bound, kern = "tensor", f"assign_tc ({prec})"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": f"{src}; {peak_src}", "peak_kind": "burst" if burst else "sustained",
+            "kernel": kern, "launch_ms": r["assign_ms"],
+            "algorithmic": f"{products} x 2 n k d = {products * w.flops_per_iter:.4g} flop per launch",
+            "traffic": stored_traffic("assign", prec, w.name)}
+
+
+def arm_summary(prec, w, r, roof, e2e=None):
+    d = {"iter_s": r["iter_s"], "ms_per_step": r["ms_per_step"], "distance_tflops": r["iter_s"] * w.flops_per_iter / 1e12,
+         "assign_ms_per_iter": r["assign_ms"], "roofline": roof, "stage_ms_per_iter": r["stage_ms_per_iter"],
+         "last_iter": r["last"], "clocks": r["clocks"], "gpu_launches": r["launches"], "e2e": e2e}
+    if prec == "fp8":
+        d["arithmetic"] = (f"{r['last']['iters_bf16']} of {w.iters} steps per call with BF16 codes (cold start), "
+                           f"the rest E4M3; queued points re-scored with BF16 codes "
+                           f"({r['last']['n_queued']} in the last step)")
+    return d
+
+
+def run_large(torch, km, dev, local, args, peaks, peak_src, live, sms):
+    """8M x 256 x 8192 E4M3 + re-check, 10 iterations per call (the largest single-GPU workload)."""
+    w = WORKLOADS["large_n8M_d256_k8192"]
+    _, _, Xd, C0d = single_problem(torch, dev, w, pinned=False)
+    reps = max(5, min(args.steps, 8))
+    r = time_runs(torch, km, dev, local, None, Xd, C0d, w, "fp8", reps, 1)
+    roof = assign_roofline("fp8", w, r, peaks, peak_src, live, sms)
+    out = arm_summary("fp8", w, r, roof)
+    out.update({"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "iters_per_step": w.iters, "steps": reps,
+                "near_ties": {"flagged_last_iter": r["last"]["n_flagged"], "full_recheck_last_iter": r["last"]["n_full"],
+                              "note": "points whose low-precision top-2 margin fell under the rigorous bound and "
+                                      "were re-checked in FP32 (the library's near-tie set)"}})
+    del Xd, C0d
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_plain(torch, km, dev, local, args):
+    """10,000 x 16 x 8 FP32, 10 iterations per call: launch-latency bound, microseconds per iteration."""
+    w = WORKLOADS["plain_n10k_d16_k8"]
+    _, _, Xd, C0d = single_problem(torch, dev, w, pinned=False)
+    reps = max(20, args.steps)
+    r = time_runs(torch, km, dev, local, None, Xd, C0d, w, "fp32", reps, 3)
+    return {"workload": w.name, "us_per_iter": 1e6 / r["iter_s"], "iter_s": r["iter_s"], "steps": reps,
+            "kernel_launches_per_call": r["launches"] // reps,
+            "note": "one kmeans_run call = one captured graph of 10 iterations (plus the point-norm kernel)",
+            "clocks": r["clocks"]}
+
+
 def run_ours(args):
     import torch
 
@@ -624,132 +789,61 @@ def run_ours(args):
         import dataclasses
 
         w = dataclasses.replace(w, n=min(w.n, args.rows), name=f"{w.name}[:{min(w.n, args.rows)}]")
-    prec = args.precision or w.precision[0]
-    iters = w.iters
-    # pinned host copy of the workload, then the device copy
-    Xh = torch.empty((w.n, w.d), dtype=torch.float32, pin_memory=True)
-    synth.mixture(w.seed, w.n, w.d, w.m, w.R, w.sigma, out=Xh.numpy())
-    C0h = Xh[: w.k].clone().pin_memory()
-    Xd = Xh.to(dev)
-    C0d = C0h.to(dev)
-    Cd = C0d.clone()
-    a, s, c = km.alloc_outputs(Xd, Cd)
-    stream = torch.cuda.current_stream(dev)
-
-    def one_step():
-        Cd.copy_(C0d)
-        return km.run(Xd, Cd, iters, assign=a, sums=s, counts=c, precision=prec, profile=True, stream=stream)
-
-    for _ in range(max(args.warmup, 0)):
-        one_step()
-    torch.cuda.synchronize(dev)
-    barrier(dist)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stage_tot = {k: 0.0 for k in ("xnorm",) + STAGE_KERNELS}
-    flagged = []
-    launches_tot = 0  # kernel launches the library reports (kernel nodes of the captured graph + 1)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize(dev)
-        barrier(dist)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            out = one_step()
-            for kname, v in out.stats["stage_ms"].items():
-                stage_tot[kname] += v
-            flagged.append(out.stats["n_flagged"])
-            launches_tot += out.stats["launches"]
-        ev1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(dist)
-    clocks = clk.summary()
-    t = ev0.elapsed_time(ev1) / 1e3
-    t_max = max_over_ranks(dist, t, dev)
-    value = aggregate_rate(args.steps * iters, world, t_max)
-    flops_iter = 2.0 * w.n * w.k * w.d
-
-    # dominant kernel: the fused assignment (per-launch time from the events around it)
-    launches = args.steps * iters
-    assign_ms = stage_tot["assign"] / launches
-    achieved = (3 if prec == "bf16x3" else 1) * flops_iter / (assign_ms / 1e3) / 1e12  # tensor products run
+    prec = args.precision or HEADLINE_PRECISION.get(w.name, w.precision[0])
+    full = rank == 0 and world == 1 and not args.no_variants and w.name == DEFAULT_WORKLOAD
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    if prec == "fp32":
-        peak = fp32_simt_peak_tflops(sms, peaks.get("sm_max_mhz", 2032.0))
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"FFMA: {sms} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz",
-                "kernel": "assign_simt", "launch_ms": assign_ms,
-                "traffic": stored_traffic("assign", prec, w.name)}
-    else:
-        peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peak_src} bf16 sustained" + (" x 2 (fp8 nominal ratio)" if prec == "fp8" else ""),
-                "kernel": f"assign_{prec}", "launch_ms": assign_ms, "traffic": stored_traffic("assign", prec, w.name)}
-    stage_share = {k: v / args.steps / iters for k, v in stage_tot.items()}
+    live = measure_peaks(torch, km, dev) if full else None
 
-    # the same workload through the two-part BF16 tensor-core path (exact assignments too)
-    split = None
-    if rank == 0 and world == 1 and not args.no_variants and w.name == DEFAULT_WORKLOAD and prec == "fp32":
-        res = []
-        for _ in range(3):
-            Cd.copy_(C0d)
-            o = km.run(Xd, Cd, iters, assign=a, sums=s, counts=c, precision="bf16x3", profile=True, stream=stream)
-            res.append(o.stats)
-        best = min(res[1:], key=lambda st: st["ms"])
-        sa_ms = best["stage_ms"]["assign"] / iters
-        sp = peaks["bf16_tflops_sustained"]
-        split = {"iter_s": iters / (best["ms"] / 1e3), "assign_ms_per_iter": sa_ms,
-                 "speedup_vs_fp32": (iters / (best["ms"] / 1e3)) / value,
-                 "roofline": {"bound": "tensor", "achieved": 3 * flops_iter / (sa_ms / 1e3) / 1e12, "peak": sp,
-                              "unit": "TFLOP/s", "frac": 3 * flops_iter / (sa_ms / 1e3) / 1e12 / sp,
-                              "note": "three BF16 products per distance"},
-                 "flagged_last_iter": best["n_flagged"], "objective": best["objective"],
-                 "note": "kmeans_run with precision bf16x3 on the same data; best of 2 after 1 warm-up"}
+    Xh, C0h, Xd, C0d = single_problem(torch, dev, w)
+    r = time_runs(torch, km, dev, local, dist, Xd, C0d, w, prec, args.steps, args.warmup)
+    value = aggregate_rate(args.steps * w.iters, world, r["t"])
+    roof = assign_roofline(prec, w, r, peaks, peak_src, live, sms)
+    e2e = None if args.no_e2e else time_e2e(torch, km, dist, dev, Xh, C0h, w, prec, args.steps)
 
-    # end to end through the host-pointer entry point (copies inside the timed region)
-    e2e = None
-    if not args.no_e2e:
-        Ch = C0h.clone().pin_memory()
-        ah = torch.empty(w.n, dtype=torch.int32, pin_memory=True)
-        sh = torch.empty((w.k, w.d), dtype=torch.float32, pin_memory=True)
-        ch = torch.empty(w.k, dtype=torch.int32, pin_memory=True)
-        Ch.copy_(C0h)
-        km.run_host(Xh, Ch, iters, 0.0, ah, sh, ch, precision=prec)  # warm-up (staging buffers)
-        barrier(dist)
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            Ch.copy_(C0h)
-            km.run_host(Xh, Ch, iters, 0.0, ah, sh, ch, precision=prec)
-        te = time.perf_counter() - t0
-        te = max_over_ranks(dist, te, dev)
-        e2e = {"value": aggregate_rate(args.steps * iters, world, te), "unit": "iter/s",
-               "h2d_bytes_per_step": 4 * w.n * w.d + 4 * w.k * w.d,
-               "d2h_bytes_per_step": 4 * w.k * w.d * 2 + 4 * w.n + 4 * w.k,
-               "api": "kmeans_run_host (pinned host buffers)"}
+    arms = None
+    if full:  # the metric's comparison on the same data: FP32, E4M3 and two-part BF16, each + re-check
+        arms = {}
+        reps = max(5, min(args.steps, 10))
+        for p2 in ("fp32", "fp8", "bf16x3"):
+            ra = time_runs(torch, km, dev, local, None, Xd, C0d, w, p2, reps, 1)
+            e2 = None if (args.no_e2e or p2 == "bf16x3") else time_e2e(torch, km, None, dev, Xh, C0h, w, p2,
+                                                                       min(reps, 5))
+            arms[p2] = arm_summary(p2, w, ra, assign_roofline(p2, w, ra, peaks, peak_src, live, sms), e2)
+            arms[p2]["steps"] = reps
+        for p2 in ("bf16", "fp8", "bf16x3"):
+            base = arms["fp32"]["iter_s"]
+            if p2 == "bf16":
+                arms.setdefault("speedup_vs_fp32", {})["bf16"] = value / base
+            else:
+                arms["speedup_vs_fp32"][p2] = arms[p2]["iter_s"] / base
+    del Xd, C0d
+    torch.cuda.empty_cache()
 
-    variants = None
-    if rank == 0 and world == 1 and not args.no_variants and w.name == DEFAULT_WORKLOAD:
-        del Xd, Xh
-        torch.cuda.empty_cache()
-        variants = precision_variants(torch, dev)
+    others = None
+    if full:
+        others = {"large_n8M_d256_k8192": run_large(torch, km, dev, local, args, peaks, peak_src, live, sms)}
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup, bargs.precision, bargs.instances = max(5, min(args.steps, 10)), 2, None, 0
+        others["batched_512"] = run_batched(bargs, torch, dev, None, 0, 1, local, emit=False)
+        others["plain_n10k_d16_k8"] = run_plain(torch, km, dev, local, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = oracle_sample_rate(w, args.cpu_seconds)
+        rate, cores, sample = oracle_sample_rate(w, args.cpu_seconds, X=Xh.numpy())
         cpu = {"value": rate, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else prec,
+            "warmup": args.warmup, "ms_per_step": r["t"] * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES.get(prec, prec),
             "data": "synthetic", "config": workload_config(w, prec),
-            "distance_tflops": value * flops_iter / 1e12,
-            "roofline": roof, "stage_ms_per_iter": stage_share,
-            "flagged_per_step_last_iter": flagged[-1] if flagged else None,
-            "clocks": clocks, "e2e": e2e, "precision_variants": variants, "split_bf16_same_workload": split,
-            "gpu_launches": launches_tot,
-            "cpu_baseline": cpu,
-            "peaks_source": peak_src,
+            "distance_tflops": value * w.flops_per_iter / 1e12,
+            "roofline": roof, "stage_ms_per_iter": r["stage_ms_per_iter"], "last_iter": r["last"],
+            "clocks": r["clocks"], "e2e": e2e, "gpu_launches": r["launches"],
+            "precision_arms": arms, "other_configs": others, "peaks_live": live,
+            "cpu_baseline": cpu, "peaks_source": peak_src,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

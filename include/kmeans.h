@@ -122,6 +122,14 @@ typedef struct {
                            captured graph (iters > 1), else 0 */
   float stage_ms[12];   /* with opts->profile: device time per stage summed
                            over the call's steps (KM_STAGE_*), else zeros */
+  int64_t n_queued;     /* of the n_full points of the last step, those gathered
+                           and re-scored by the second pass before the compensated
+                           distances (BF16 tensor-core codes for KM_FP8E4M3, the
+                           FP32 SIMT kernel otherwise); 0 for batched calls */
+  int32_t iters_bf16;   /* steps of the call whose distance contraction ran with
+                           BF16 codes instead of the requested precision (1 for a
+                           KM_FP8E4M3 call without warm_start: its first step) */
+  int32_t reserved;
 } km_stats;
 
 /* Fills *opts with the defaults (FP32, recheck on, legacy stream). */
@@ -206,11 +214,15 @@ int kmeans_run_batched(const km_opts* opts, const km_instance* inst,
  * k <= 8192, k * d <= 262144, 1 <= d <= 256; larger sizes return KM_EINVAL.
  * X: const float[n*d], C: const float[k*d], assign: const int32[n] with labels
  * in [0, k) (else KM_EINVAL), sums: float[k*d] out, counts: int32[k] out; all
- * device pointers. Work is issued on `stream` (NULL = legacy stream), which is
- * synchronised before returning. The first call on a device looks up the
- * scratch array's device address and should come before any stream capture.
- * Every call shares the one scratch array (it clears what must start at
- * zero), so calls that overlap on the GPU race with each other.
+ * device pointers. Work is issued on `stream` (NULL = legacy stream); every
+ * call synchronises `stream` and reads a status word back before it returns.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it for the
+ * lifetime of the device's primary context; that first call should come
+ * before any stream capture. Every call shares the one scratch array (it
+ * clears what must start at zero, so a call rejected for a bad label leaves
+ * nothing behind for the next one), and calls that overlap on the GPU race
+ * with each other.
  */
 int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C,
                           int32_t k, const int32_t* assign, float* sums,
@@ -287,6 +299,32 @@ typedef struct {
 int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n, int32_t d, double apprx_width,
                            double kernel_width, int32_t policy, int32_t* densities, int32_t* counts,
                            uint8_t* processed, km_spade_stats* stats);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics (not on the Lloyd path; used by the tests and the benchmark).
+ *
+ * kmeans_probe_mma: one 128 x 128 FP32 tile D = A B^T of the tensor-core
+ * contraction formed exactly as the distance kernel forms it (operands staged
+ * K-major with the 128-byte swizzle, the kernel's shared-memory and
+ * instruction descriptors, one tcgen05.mma per 32 bytes of K accumulating in
+ * K order into one TMEM accumulator, read back with tcgen05.ld). It exposes
+ * the accumulator's rounding, on which the near-tie margin's gamma'_K term
+ * rests. precision: KM_BF16 (A, B hold BF16 bit patterns, 2 bytes) or
+ * KM_FP8E4M3 (E4M3 bytes). A: DEVICE [128][K] codes, B: DEVICE [128][K]
+ * codes, both row-major, 16-byte aligned; K = 64, 128, 192 or 256 (BF16) or
+ * 128, 256, 384 or 512 (E4M3). D: DEVICE float[128 * 128], D[m*128 + n] =
+ * sum_k A[m][k] B[n][k] as accumulated by the tensor core. The call
+ * synchronises `stream` (NULL = legacy stream). KM_EINVAL for bad sizes,
+ * KM_ETIMEOUT if the completion wait (bounded at 1 s) expired.
+ *
+ * kmeans_probe_ffma: times one launch of independent FP32 FMA chains over
+ * every SM (8 CTAs of 256 threads per SM, 16 FMAs per thread and iteration,
+ * `iters` iterations; packed != 0 uses the two-lane FFMA2 instruction) with
+ * CUDA events on `stream`. *flops = 2 x FMAs executed, *ms = device time: the
+ * measured FP32 SIMT peak is *flops / *ms.
+ */
+int kmeans_probe_mma(int32_t precision, const void* A, const void* B, int32_t K, float* D, void* stream);
+int kmeans_probe_ffma(int32_t packed, int32_t iters, double* flops, float* ms, void* stream);
 
 /* Message of the calling thread's last failing call ("" if none). */
 const char* kmeans_last_error(void);

@@ -190,7 +190,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
-      flagged, full, empty, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
+      flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
       flags2, xq16, xs16q, cq16, hq16, scq16, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
@@ -224,6 +224,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   L.flagged = take(8 * (size_t)iters);
   L.full = take(8 * (size_t)iters);
   L.empty = take(4 * (size_t)iters);
+  L.queued = take(8 * (size_t)iters);
   L.labs = take(4 * (size_t)n);  // labels in cluster-sorted order (scatter stage)
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
@@ -327,6 +328,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.flagged_hist = (unsigned long long*)(b + L.flagged);
   w.full_hist = (unsigned long long*)(b + L.full);
   w.empty_hist = (int*)(b + L.empty);
+  w.queued_hist = (unsigned long long*)(b + L.queued);
   w.Xq = L.Xq ? (uint8_t*)(b + L.Xq) : nullptr;
   w.xs = L.xs ? (float4*)(b + L.xs) : nullptr;
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
@@ -603,7 +605,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   KM_TRACE("layout: %zu bytes (n=%lld d=%d k=%d prec=%d)\n", L.total, (long long)p.n, p.d, p.k, o.precision);
   if ((rc = ensure_ws(c, L, s))) return rc;
   KM_TRACE("workspace ready at %p (%zu bytes)\n", c->ws, c->ws_bytes);
-  const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 5 + 4) + 64;
+  const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 6 + 4) + 64;
   if (host_need > c->host_bytes) {
     if (c->host) cudaFreeHost(c->host);
     c->host = nullptr;
@@ -743,13 +745,15 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   unsigned long long* hchanged = (unsigned long long*)(hshift + iters);
   unsigned long long* hflag = hchanged + iters;
   unsigned long long* hfull = hflag + iters;
-  int* hempty = (int*)(hfull + iters);
+  unsigned long long* hqueued = hfull + iters;
+  int* hempty = (int*)(hqueued + iters);
   KM_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hobj, w.obj_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hshift, w.shift_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hchanged, w.changed_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hflag, w.flagged_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hfull, w.full_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaMemcpyAsync(hqueued, w.queued_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaMemcpyAsync(hempty, w.empty_hist, 4 * (size_t)iters, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaStreamSynchronize(s));
   if (hc->iters_done < 0 || hc->iters_done > iters)
@@ -777,6 +781,9 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
       st->n_flagged = (int64_t)hflag[last];
       st->n_full = (int64_t)hfull[last];
       st->n_empty = hempty[last];
+      st->n_queued = (int64_t)hqueued[last];
+      // a cold E4M3 call computes its first step's distances with BF16 codes
+      st->iters_bf16 = (o.precision == KM_FP8E4M3 && cfg.cold) ? 1 : 0;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -1159,7 +1166,7 @@ KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n
 
 KM_API const char* kmeans_last_error(void) { return g_err.c_str(); }
 
-KM_API int32_t kmeans_version(void) { return 100; }
+KM_API int32_t kmeans_version(void) { return 200; }
 
 // ============================================================================ batched runs
 

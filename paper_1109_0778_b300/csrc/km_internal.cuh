@@ -73,6 +73,7 @@ struct Work {
   unsigned long long* flagged_hist;  // [iters]
   unsigned long long* full_hist;     // [iters]
   int* empty_hist;     // [iters]
+  unsigned long long* queued_hist;   // [iters] points re-scored by the queued pass
   // quantised operands of the tensor-core path (null for FP32)
   uint8_t* Xq;         // [n][Kp] point codes (cached for the call)
   float4* xs;          // [n] row scale and norm bounds

@@ -371,6 +371,7 @@ divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ c
       w.flagged_hist[it] = vc->n_flagged;
       w.full_hist[it] = vc->n_full;
       w.empty_hist[it] = vc->n_empty;
+      w.queued_hist[it] = min(vc->n_fullq, (unsigned long long)w.fq_cap);
       vc->iters_done = it + 1;
       if (tol > 0.0 && (changed == 0 || shift <= tol)) vc->done = 1;
     }

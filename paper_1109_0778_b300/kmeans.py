@@ -23,7 +23,8 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 #: Entry points declared in include/kmeans.h (checked by the ABI test).
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
            "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc",
-           "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train", "kmeans_spade_densities")
+           "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train", "kmeans_spade_densities",
+           "kmeans_probe_mma", "kmeans_probe_ffma")
 SPADE_POLICY = {"last": 0, "first": 1}
 
 
@@ -60,10 +61,11 @@ class Stats(ctypes.Structure):
                 ("n_changed", ctypes.c_int64), ("n_flagged", ctypes.c_int64),
                 ("n_full", ctypes.c_int64), ("n_empty", ctypes.c_int32),
                 ("iters_done", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("launches", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12)]
+                ("launches", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12),
+                ("n_queued", ctypes.c_int64), ("iters_bf16", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "stage_ms"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_ms", "reserved")}
         d["stage_ms"] = {name: float(self.stage_ms[i]) for i, name in enumerate(STAGES)}
         return d
 
@@ -100,6 +102,10 @@ def load(path: str = LIB_PATH):
     lib.kmeans_nb_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp]
     lib.kmeans_spade_densities.restype = ctypes.c_int
     lib.kmeans_spade_densities.argtypes = [P(Opts), vp, i64, i32, dbl, dbl, i32, vp, vp, vp, P(SpadeStats)]
+    lib.kmeans_probe_mma.restype = ctypes.c_int
+    lib.kmeans_probe_mma.argtypes = [i32, vp, vp, i32, vp, vp]
+    lib.kmeans_probe_ffma.restype = ctypes.c_int
+    lib.kmeans_probe_ffma.argtypes = [i32, i32, P(dbl), P(ctypes.c_float), vp]
     return lib
 
 
@@ -320,3 +326,33 @@ def spade_densities(X, apprx_width: float, kernel_width: float, *, policy: str =
 
 def version() -> int:
     return int(_lib.kmeans_version())
+
+
+# ----------------------------------------------------------------------------- diagnostics
+
+def probe_mma(A, B, *, precision="bf16", stream=None):
+    """D = A B^T (128 x 128, FP32) as the tensor core accumulates it (kmeans_probe_mma).
+
+    A, B: contiguous CUDA tensors of shape (128, K): torch.bfloat16 for ``bf16``,
+    torch.float8_e4m3fn (or uint8 bit patterns) for ``fp8``.
+    """
+    import torch
+
+    for name, t in (("A", A), ("B", B)):
+        if not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.shape[0] != 128:
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of shape (128, K)")
+    if A.shape != B.shape or A.dtype != B.dtype:
+        raise ValueError("A and B must have the same shape and dtype")
+    D = torch.empty(128, 128, dtype=torch.float32, device=A.device)
+    _check(_lib.kmeans_probe_mma(PRECISION[precision], A.data_ptr(), B.data_ptr(), int(A.shape[1]), D.data_ptr(),
+                                 _stream_handle(stream)))
+    return D
+
+
+def probe_ffma(iters=1 << 15, *, packed=True, stream=None):
+    """(flops, ms) of one device-wide launch of independent FP32 FMA chains (kmeans_probe_ffma)."""
+    fl = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(_lib.kmeans_probe_ffma(1 if packed else 0, int(iters), ctypes.byref(fl), ctypes.byref(ms),
+                                  _stream_handle(stream)))
+    return fl.value, ms.value

@@ -31,7 +31,7 @@ def test_exports_every_declared_symbol():
 
 
 def test_version_and_defaults():
-    assert kmeans.version() == 100
+    assert kmeans.version() == 200
     o = kmeans.make_opts()
     assert o.precision == 0 and o.recheck == 1 and not o.stream
 
