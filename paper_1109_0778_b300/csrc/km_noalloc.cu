@@ -76,7 +76,9 @@ __global__ void finish_sums_kernel(double* __restrict__ sums64, float* __restric
 /*
  * See include/kmeans.h. The first call on a device looks up the device
  * address of the static scratch array (cudaGetSymbolAddress with that device
- * current); make that first call before any stream capture.
+ * current) and caches it: the address stays valid while the device's primary
+ * context lives (a cudaDeviceReset ends it, and the cached address with it).
+ * Make that first call before any stream capture.
  */
 KM_API int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C, int32_t k,
                                  const int32_t* assign, float* sums, int32_t* counts, double* objective,
