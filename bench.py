@@ -20,9 +20,13 @@ and the FP32 FFMA and FP8 tensor peaks that their roofline fractions use.
 bounded sample of the same workload per step), the one other place this script
 runs oracle code; so does the ``cpu_baseline`` leg of the default arm.
 
-Multi-GPU (torchrun): every rank runs its own replica of the workload (the step
-needs no exchange between independent problems); value = all ranks' iterations /
-the slowest rank's time.
+Multi-GPU (torchrun, one rank per GPU): the single-instance workloads run as one
+sharded problem (strong scaling): every rank holds a contiguous shard of the
+points and all centroids, and each Lloyd iteration is kmeans_step_partial on the
+shard, one NCCL sum all-reduce of the k*d + k + 2 partials, and
+kmeans_apply_partials (paper_1109_0778_b300.sharded); value = the problem's
+iterations / the slowest rank's time. The training and SPADE workloads run
+independent replicas (weak scaling).
 """
 from __future__ import annotations
 
@@ -767,6 +771,85 @@ def run_plain(torch, km, dev, local, args):
             "clocks": r["clocks"]}
 
 
+def run_sharded(args, torch, dev, dist, rank, world, local):
+    """The single-instance workload as one problem sharded over the ranks (strong scaling)."""
+    from paper_1109_0778_b300 import kmeans as km
+    from paper_1109_0778_b300.sharded import ShardedLloyd, shard_bounds
+
+    w = WORKLOADS[args.workload]
+    prec = args.precision or HEADLINE_PRECISION.get(w.name, w.precision[0])
+    lo, hi = shard_bounds(w.n, rank, world)
+    Xh = torch.empty((hi - lo, w.d), dtype=torch.float32, pin_memory=True)
+    synth.mixture(w.seed, hi - lo, w.d, w.m, w.R, w.sigma, row0=lo, out=Xh.numpy())
+    C0h = torch.from_numpy(synth.mixture(w.seed, w.k, w.d, w.m, w.R, w.sigma))  # the first k points of the data set
+    Xd, C0d = Xh.to(dev), C0h.to(dev)
+    Cd = C0d.clone()
+    stream = torch.cuda.current_stream(dev)
+
+    def one_run(Xsrc=None):
+        Cd.copy_(C0d)
+        sl = ShardedLloyd(Xd, Cd, precision=prec, stream=stream)
+        if Xsrc is not None:
+            Xd.copy_(Xsrc, non_blocking=True)
+        st = sl.run(w.iters)
+        return sl, st
+
+    # kernels per Lloyd step of this shard: the kernel nodes of a captured kmeans_run graph of the
+    # same shard (one per-call point pass + iters steps); a sharded step launches the same stages
+    # (the partials finish in place of the divide) plus the two kernels of kmeans_apply_partials
+    probe = km.run(Xd, C0d.clone(), w.iters, precision=prec)
+    per_step = (probe.stats["launches"] - 1) // w.iters
+    launches_per_run = 1 + w.iters * (per_step + 2)
+    for _ in range(max(args.warmup, 0)):
+        one_run()
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = one_run()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+    t = max_over_ranks(dist, ev0.elapsed_time(ev1) / 1e3, dev)
+    value = args.steps * w.iters / t
+    # end to end: every step copies the shard in from pinned host memory and reads C and the labels back
+    e2e = None
+    if not args.no_e2e:
+        ah = torch.empty(hi - lo, dtype=torch.int32, pin_memory=True)
+        Ch = torch.empty((w.k, w.d), dtype=torch.float32, pin_memory=True)
+        barrier(dist)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sl, _ = one_run(Xh)
+            ah.copy_(sl.assign)
+            Ch.copy_(Cd)
+        te = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        e2e = {"value": args.steps * w.iters / te, "unit": "iter/s", "h2d_bytes_per_step": 4 * (hi - lo) * w.d,
+               "d2h_bytes_per_step": 4 * (hi - lo) + 4 * w.k * w.d,
+               "api": "ShardedLloyd over kmeans_step_partial / kmeans_apply_partials, per rank"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": DTYPE_NAMES.get(prec, prec), "data": "synthetic",
+            "config": dict(workload_config(w, prec), parallelism=f"points sharded over {world} GPUs; one NCCL "
+                                                                 f"all-reduce of k*d + k + 2 FP64 partials per iteration"),
+            "distance_tflops": value * w.flops_per_iter / 1e12,
+            "last_iter": {"objective": st["objective"], "n_changed": st["n_changed"],
+                          "n_flagged_rank0": st["n_flagged_shard"]},
+            "clocks": clk.summary(), "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_run, "cpu_baseline": None, "peaks_source": measured_peaks()[1],
+            "note": "each iteration: kmeans_step_partial + all-reduce + kmeans_apply_partials (host-sequenced)",
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -784,6 +867,8 @@ def run_ours(args):
         return run_spade(args, torch, dev, dist, rank, world, local)
     if args.workload == "batched_512":
         return run_batched(args, torch, dev, dist, rank, world, local)
+    if world > 1:
+        return run_sharded(args, torch, dev, dist, rank, world, local)
     w = WORKLOADS[args.workload]
     if args.rows:
         import dataclasses

@@ -88,6 +88,28 @@ typedef struct {
                          threshold and n_changed counts against it. Labels
                          outside [0, k) are ignored. 0 (default): assign is
                          output only and every point counts as changed */
+  int32_t deterministic; /* 1: bit-reproducible results. The keyed reduce adds the
+                         points in exact fixed point (every coordinate split into
+                         three 21-bit integer parts on a grid set by max_i ||x_i||,
+                         summed in 64-bit integers, so the order of the additions
+                         does not matter) and forms sums, centroids and the
+                         objective from those integers in a fixed order; two calls
+                         on the same inputs return identical bits. The dropped
+                         remainder is below 2^-62 of max_i ||x_i|| per point.
+                         Single-instance calls only (KM_EUNSUPPORTED for batches).
+                         0 (default): Kahan-compensated FP32 runs combined with
+                         FP64 atomics (within the accuracy contract, but the last
+                         bit of a sum can depend on the order of the atomics) */
+  int32_t reuse_x;    /* 1: X is the same array, with the same contents, n, d, k and
+                         precision, as in this device's previous successful call
+                         of kmeans_step_ex / kmeans_run_ex / kmeans_step_partial,
+                         and no other call of the library used the device in
+                         between: the point codes, norms and cluster-sorted order
+                         that call left in the workspace are reused and the first
+                         step continues from its last assignment (as a warm start
+                         would), so that a sequence of one-step calls runs like
+                         one kmeans_run. When the cache does not match, the flag
+                         is ignored. 0 (default): everything is recomputed */
   void* stream;       /* cudaStream_t to issue work on; NULL = legacy stream */
 } km_opts;
 
@@ -201,6 +223,55 @@ typedef struct {
 int kmeans_run_batched(const km_opts* opts, const km_instance* inst,
                        int32_t count, int32_t iters, double tol,
                        km_stats* per_inst);
+
+/* ------------------------------------------------------------------------
+ * Sharded Lloyd step (data-parallel over devices). The n points are split into
+ * contiguous shards, one per device; every device holds all k centroids. One
+ * step is: kmeans_step_partial on every shard, one sum all-reduce of the
+ * partials buffer across the devices (the caller's collective, e.g. NCCL),
+ * then kmeans_apply_partials with the reduced buffer on every device, which
+ * gives every device the same new centroids. This is the keyed reduce split
+ * into chunks whose per-chunk results are merged by a combine (Sec. 2.4,
+ * DeliteReduceElem's alloc / combine), with the runtime spreading the loop
+ * over several devices (Sec. 2.4, the Delite runtime).
+ *
+ * Partials buffer: double[KM_PARTIALS_LEN(k, d)] on the device,
+ *   [0, k d)         sum of x_i over the shard's members of each cluster
+ *                    (row-major k x d, FP64 from the reduce's partials),
+ *   [k d, k d + k)   member counts (exact integers stored as FP64),
+ *   [k d + k]        the shard's objective sum ||x_i - c_{a_i}||^2 (FP64),
+ *   [k d + k + 1]    the shard's count of points whose assignment changed.
+ * Every entry is a sum over points, so the element-wise sum of the shards'
+ * buffers is the buffer of the whole data set.
+ */
+#define KM_PARTIALS_LEN(k, d) ((int64_t)(k) * (int64_t)(d) + (int64_t)(k) + 2)
+
+/*
+ * The shard's part of one Lloyd step: assignment (with the near-tie re-check
+ * of opts->precision) and the partials buffer. X: const float[n*d] (the
+ * shard's points), C: const float[k*d] (the centroids, unchanged), assign:
+ * int32[n] out (with opts->warm_start: the previous labels on entry),
+ * part: double[KM_PARTIALS_LEN(k, d)] out. All DEVICE pointers. stats: as for
+ * kmeans_step_ex except shift and n_empty (0 here; see kmeans_apply_partials).
+ * Use opts->reuse_x on the second and later steps of a sequence on the same
+ * shard to keep the cached codes and cluster-sorted order.
+ */
+int kmeans_step_partial(const km_opts* opts, const float* X, int64_t n, int32_t d, const float* C,
+                        int32_t k, int32_t* assign, double* part, km_stats* stats);
+
+/*
+ * The divide of a sharded step from a reduced partials buffer: for every
+ * cluster with a nonzero count, c_j = RN32(sum_j / count_j) in FP64; an empty
+ * cluster keeps c_j. part: const double[KM_PARTIALS_LEN(k, d)], C: float[k*d]
+ * in/out, sums: float[k*d] out (the sums rounded to FP32) or NULL, counts:
+ * int32[k] out or NULL; all DEVICE pointers. stats (NULL = not wanted):
+ * objective and n_changed from the buffer, shift = max_j ||c_j' - c_j||_2,
+ * n_empty; the other fields 0. Given the same buffer every device computes
+ * the same bits. opts: only `stream` is used. Counts in the buffer must be
+ * non-negative integers below 2^31 (KM_EINVAL otherwise, C unchanged).
+ */
+int kmeans_apply_partials(const km_opts* opts, const double* part, int32_t k, int32_t d, float* C,
+                          float* sums, int32_t* counts, km_stats* stats);
 
 /*
  * Keyed reduce of a Lloyd step for a given assignment, without allocating:

@@ -95,6 +95,16 @@ struct DevCtx {
   void* host = nullptr;   // pinned read-back of Ctl and the per-step history
   size_t host_bytes = 0;
   bool graph_valid = false;
+  // What the workspace holds after the last successful single-instance call
+  // (opts->reuse_x): point codes, norms and cluster-sorted order of that X.
+  struct XCache {
+    bool valid = false;
+    const void* X = nullptr;
+    int64_t n = 0;
+    int d = 0, k = 0, prec = -1, lay_warm = 0, det = 0;
+    uint64_t ws_gen = 0;
+  } xc;
+  unsigned long long* actl = nullptr;  // status words of kmeans_apply_partials
   int graph_kernels = 0;  // kernel nodes of the cached graph
   GraphKey gkey{};
   cudaGraphExec_t gexec = nullptr;
@@ -191,7 +201,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, pcounts, xmax, facc, oacc, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -203,7 +213,10 @@ bool rescore16(int precision, int d, int k) { return precision == KM_FP8E4M3 && 
 // (at least 4096, at most n); further unresolved points are settled one by one.
 int64_t requeue_cap(int64_t n) { return std::min<int64_t>(n, std::max<int64_t>(4096, n / 8)); }
 
-Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
+// Regions whose contents a later call may reuse (opts->reuse_x: codes, norms,
+// sorted order) come first and depend only on (n, k, d, precision, warm); the
+// per-step histories (sized by iters) and the deterministic accumulators follow.
+Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, int det) {
   Layout L;
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
@@ -218,13 +231,8 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
   L.chalf = take(4 * (size_t)k);
   L.cnorm = take(4 * (size_t)k);
   L.Csave = take(4 * kd);
-  L.obj = take(8 * (size_t)iters);
-  L.shift = take(8 * (size_t)iters);
-  L.changed = take(8 * (size_t)iters);
-  L.flagged = take(8 * (size_t)iters);
-  L.full = take(8 * (size_t)iters);
-  L.empty = take(4 * (size_t)iters);
-  L.queued = take(8 * (size_t)iters);
+  L.pcounts = take(4 * (size_t)k);
+  L.xmax = take(4);
   L.labs = take(4 * (size_t)n);  // labels in cluster-sorted order (scatter stage)
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
@@ -283,6 +291,15 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm) {
       L.fq_cap = 0;
     }
   }
+  L.obj = take(8 * (size_t)iters);
+  L.shift = take(8 * (size_t)iters);
+  L.changed = take(8 * (size_t)iters);
+  L.flagged = take(8 * (size_t)iters);
+  L.full = take(8 * (size_t)iters);
+  L.empty = take(4 * (size_t)iters);
+  L.queued = take(8 * (size_t)iters);
+  L.facc = det ? take(3 * 8 * kd) : 0;
+  L.oacc = det ? take(3 * 8) : 0;
   L.total = o;
   return L;
 }
@@ -329,6 +346,10 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.full_hist = (unsigned long long*)(b + L.full);
   w.empty_hist = (int*)(b + L.empty);
   w.queued_hist = (unsigned long long*)(b + L.queued);
+  w.pcounts = (int32_t*)(b + L.pcounts);
+  w.xmax = (unsigned int*)(b + L.xmax);
+  w.facc = L.facc ? (unsigned long long*)(b + L.facc) : nullptr;
+  w.oacc = L.oacc ? (unsigned long long*)(b + L.oacc) : nullptr;
   w.Xq = L.Xq ? (uint8_t*)(b + L.Xq) : nullptr;
   w.xs = L.xs ? (float4*)(b + L.xs) : nullptr;
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
@@ -387,6 +408,9 @@ struct StepCfg {
   int precision;
   int recheck;
   int warm;  // assign holds a valid assignment on entry
+  int det;   // exact fixed-point reduce (opts->deterministic)
+  int reuse; // the first step continues from the cached sorted codes and labels of the previous call
+  double* part;  // non-null: a shard's partial step (no divide; partials into part)
   TcShape t;
   TcLaunch L;
   TcParams P;
@@ -421,9 +445,8 @@ int check_device_ptr(const void* p, const char* name, int dev) {
   return KM_OK;
 }
 
-// Argument checks that need no CUDA call.
-int validate_args(const km_opts& o, const Problem& p, int iters) {
-  if (!p.X || !p.C || !p.assign || !p.sums || !p.counts) return fail(KM_EINVAL, "null array pointer");
+// Argument checks that need no CUDA call: sizes, iterations, precision and shape.
+int validate_shape(const km_opts& o, const Problem& p, int iters) {
   if (p.n < 1 || p.n > INT32_MAX) return fail(KM_EINVAL, "n = %lld outside [1, 2^31)", (long long)p.n);
   if (p.k < 1 || (int64_t)p.k > p.n) return fail(KM_EINVAL, "k = %d outside [1, n]", p.k);
   if (p.d < 1 || p.d > kMaxD) return fail(KM_EINVAL, "d = %d outside [1, %d]", p.d, kMaxD);
@@ -433,6 +456,14 @@ int validate_args(const km_opts& o, const Problem& p, int iters) {
   if (o.precision != KM_FP32 && tc_shape(o.precision, p.d, p.k).stages < 2)
     return fail(KM_EUNSUPPORTED, "d = %d, k = %d do not fit the tensor-core tile pipeline (k is staged in shared memory)",
                 p.d, p.k);
+  return KM_OK;
+}
+
+// Argument checks that need no CUDA call.
+int validate_args(const km_opts& o, const Problem& p, int iters) {
+  if (!p.X || !p.C || !p.assign || !p.sums || !p.counts) return fail(KM_EINVAL, "null array pointer");
+  int rc = validate_shape(o, p, iters);
+  if (rc) return rc;
   const size_t nd = (size_t)p.n * p.d * 4, kd = (size_t)p.k * p.d * 4;
   const size_t na = (size_t)p.n * 4, nk = (size_t)p.k * 4;
   if (overlaps(p.X, nd, p.C, kd) || overlaps(p.X, nd, p.assign, na) || overlaps(p.X, nd, p.sums, kd) ||
@@ -521,12 +552,23 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   if ((e = at(5))) return e;
   if ((e = launch_scatter(p, w, s))) return e;
   if ((e = at(6))) return e;
-  if ((e = launch_segsum(p, w, s, tcp ? cfg.t.qmode() + 1 : 0, tcp ? cfg.t.Kp : 0))) return e;
+  if ((e = launch_segsum(p, w, s, tcp ? cfg.t.qmode() + 1 : 0, tcp ? cfg.t.Kp : 0, cfg.det))) return e;
   if ((e = at(7))) return e;
-  if ((e = launch_divide(p, w, first ? 0 : 1, tol, s))) return e;
+  if (cfg.part) e = launch_finish_partial(p, w, cfg.part, cfg.det, s);
+  else e = launch_divide(p, w, first ? 0 : 1, tol, s, cfg.det);
+  if (e) return e;
   if ((e = at(8))) return e;
   return cudaSuccess;
 }
+
+// Whether a step of the call starts from the unsorted point codes and no
+// previous labels (`first`), and whether its rows are in the previous step's
+// cluster-sorted order (`sorted`: the quantised paths after their first step,
+// and from the first step on when the call reuses the previous call's codes).
+int step_first(const StepCfg& cfg, int it) {
+  return it == 0 && !cfg.warm && !(cfg.reuse && cfg.precision != KM_FP32);
+}
+int step_sorted(const StepCfg& cfg, int it) { return it > 0 || (cfg.reuse && cfg.precision != KM_FP32); }
 
 const cudaEvent_t* step_events(DevCtx* c, bool profile, int it) {
   return profile ? c->prof.data() + 2 + (size_t)it * kEvPerStep : nullptr;
@@ -563,7 +605,8 @@ int get_graph(DevCtx* c, const GraphKey& key, const Problem& p, const Work& w, c
   KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < iters && e == cudaSuccess; ++it)
-    e = enqueue_step(p, w, cfg, it == 0 && !cfg.warm, it > 0, tol, c->cap_stream, step_events(c, profile, it));
+    e = enqueue_step(p, w, cfg, step_first(cfg, it), step_sorted(cfg, it), tol, c->cap_stream,
+                     step_events(c, profile, it));
   cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -595,15 +638,25 @@ struct HostReadback {
     }                                         \
   } while (0)
 
-// Runs `iters` steps on device arrays. The caller holds c->mu.
-int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double tol, bool graph,
-               km_stats* st) {
+// Runs `iters` steps on device arrays. The caller holds c->mu. part != null:
+// one partial step of a shard (kmeans_step_partial; iters = 1, C unchanged).
+int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, double tol, bool graph,
+               km_stats* st, double* part = nullptr) {
+  Problem p = p_in;
   int rc = init_ctx(c);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)o.stream;
-  const Layout L = layout_for(p.n, p.k, p.d, iters, o.precision, o.warm_start);
+  const int det = o.deterministic ? 1 : 0;
+  // the previous call's codes and sorted order are reused only when everything they depend on matches
+  const DevCtx::XCache xc = c->xc;
+  bool reuse = o.reuse_x && xc.valid && xc.X == (const void*)p.X && xc.n == p.n && xc.d == p.d && xc.k == p.k &&
+               xc.prec == o.precision && xc.det == det;
+  c->xc.valid = false;  // until this call succeeds
+  const int lay_warm = reuse ? xc.lay_warm : o.warm_start;
+  const Layout L = layout_for(p.n, p.k, p.d, iters, o.precision, lay_warm, det);
   KM_TRACE("layout: %zu bytes (n=%lld d=%d k=%d prec=%d)\n", L.total, (long long)p.n, p.d, p.k, o.precision);
   if ((rc = ensure_ws(c, L, s))) return rc;
+  if (reuse && c->ws_gen != xc.ws_gen) reuse = false;  // the workspace was reallocated
   KM_TRACE("workspace ready at %p (%zu bytes)\n", c->ws, c->ws_bytes);
   const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 6 + 4) + 64;
   if (host_need > c->host_bytes) {
@@ -616,7 +669,11 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     }
     c->host_bytes = host_need * 2;
   }
-  const Work w = make_work(c, L);
+  Work w = make_work(c, L);
+  if (part) {  // a partial step sums straight into the caller's buffer; its counts stay in the workspace
+    w.sums64 = part;
+    p.counts = w.pcounts;
+  }
   const bool profile = o.profile != 0;
   if (profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   StepCfg cfg;
@@ -624,6 +681,9 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   cfg.precision = o.precision;
   cfg.recheck = o.recheck;
   cfg.warm = o.warm_start;
+  cfg.det = det;
+  cfg.reuse = reuse ? 1 : 0;
+  cfg.part = part;
   auto fill_tc = [&](int precision, const float4* xs, TcShape& t, TcLaunch& Lc, TcParams& P) -> int {
     t = tc_shape(precision, p.d, p.k);
     Lc.fp8 = t.fp8;
@@ -668,7 +728,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     return KM_OK;
   };
   if (o.precision != KM_FP32) {
-    cfg.cold = cold_bf16_first(o.precision, o.warm_start, p.d, p.k);
+    cfg.cold = !reuse && cold_bf16_first(o.precision, o.warm_start, p.d, p.k);
     if ((rc = fill_tc(o.precision, w.xs, cfg.t, cfg.L, cfg.P))) return rc;
     KM_TRACE("main shape Kp=%d nkb=%d bn=%d kp=%d stages=%d abufs=%d cold=%d\n", cfg.t.Kp, cfg.t.nkb, cfg.t.bn,
              cfg.t.kp, cfg.t.stages, cfg.t.abufs, (int)cfg.cold);
@@ -707,13 +767,24 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   }
   KM_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(Ctl), s));
   KM_CUDA(cudaMemsetAsync(w.sums64, 0, 8 * (size_t)p.k * p.d, s));
-  KM_CUDA(cudaMemcpyAsync(w.Csave, p.C, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
+  if (det) {
+    KM_CUDA(cudaMemsetAsync(w.facc, 0, 3 * 8 * (size_t)p.k * p.d, s));
+    KM_CUDA(cudaMemsetAsync(w.oacc, 0, 3 * 8, s));
+  }
+  if (!part) KM_CUDA(cudaMemcpyAsync(w.Csave, p.C, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
-  KM_TRACE("prologue copies queued\n");
-  if (o.precision != KM_FP32 && cfg.cold) KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
-  else if (o.precision != KM_FP32) KM_CUDA(launch_quant_x(p, w, cfg.t.qmode(), cfg.t.Kp, w.Xq, w.xs, s));
-  else KM_CUDA(launch_xnorm(p, w, s));
+  KM_TRACE("prologue copies queued (reuse=%d det=%d partial=%d)\n", (int)reuse, det, part ? 1 : 0);
+  if (reuse) {
+    // codes, row statistics, norms, sorted order and max ||x|| are those the previous call left
+  } else if (o.precision != KM_FP32 && cfg.cold) {
+    KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
+  } else if (o.precision != KM_FP32) {
+    KM_CUDA(launch_quant_x(p, w, cfg.t.qmode(), cfg.t.Kp, w.Xq, w.xs, s));
+  } else {
+    KM_CUDA(launch_xnorm(p, w, s));
+  }
+  if (!reuse && det) KM_CUDA(launch_xmax(o.precision == KM_FP32 ? w.xnorm : nullptr, w.xs, p.n, w, s));
   if (debug_sync()) {
     cudaError_t r = cudaStreamSynchronize(s);
     KM_TRACE("point quantisation / norms: %s\n", cudaGetErrorString(r));
@@ -727,7 +798,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     key.X = p.X; key.C = p.C; key.assign = p.assign; key.sums = p.sums; key.counts = p.counts;
     key.n = p.n; key.d = p.d; key.k = p.k; key.iters = iters; key.prec = o.precision; key.tol = tol;
     key.profile = (profile ? 1 : 0) | (o.recheck ? 2 : 0) | (o.warm_start ? 4 : 0) |
-                  (getenv("KM_DEBUG_STALL") ? 8 : 0);
+                  (getenv("KM_DEBUG_STALL") ? 8 : 0) | (det ? 16 : 0) | (reuse ? 32 : 0);
     key.ws_gen = c->ws_gen;
     cudaGraphExec_t ge = nullptr;
     if ((rc = get_graph(c, key, p, w, cfg, iters, tol, profile, &ge))) return rc;
@@ -735,7 +806,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
     launches = 1 + c->graph_kernels;  // the point-norm / quantisation kernel, then the graph
   } else {
     for (int it = 0; it < iters; ++it)
-      KM_CUDA(enqueue_step(p, w, cfg, it == 0 && !cfg.warm, it > 0, tol, s, step_events(c, profile, it)));
+      KM_CUDA(enqueue_step(p, w, cfg, step_first(cfg, it), step_sorted(cfg, it), tol, s, step_events(c, profile, it)));
   }
   KM_CUDA(cudaEventRecord(c->ev1, s));
   char* h = (char*)c->host;
@@ -759,8 +830,10 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
   if (hc->iters_done < 0 || hc->iters_done > iters)
     return fail(KM_ECUDA, "device control block is inconsistent (%d steps recorded, %d run)", hc->iters_done, iters);
   if (hc->nonfinite || hc->error) {
-    KM_CUDA(cudaMemcpyAsync(p.C, w.Csave, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
-    KM_CUDA(cudaStreamSynchronize(s));
+    if (!part) {  // a partial step leaves C alone
+      KM_CUDA(cudaMemcpyAsync(p.C, w.Csave, (size_t)p.k * p.d * 4, cudaMemcpyDeviceToDevice, s));
+      KM_CUDA(cudaStreamSynchronize(s));
+    }
     if (hc->nonfinite) return fail(KM_ENONFINITE, "X or C holds a non-finite value (or a norm overflows FP32)");
     return fail(hc->error, "device stage reported error %d", hc->error);
   }
@@ -801,6 +874,16 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p, int iters, double 
       }
     }
   }
+  // the workspace now holds this X's codes, norms and (quantised paths) sorted order
+  c->xc.valid = true;
+  c->xc.X = p.X;
+  c->xc.n = p.n;
+  c->xc.d = p.d;
+  c->xc.k = p.k;
+  c->xc.prec = o.precision;
+  c->xc.lay_warm = lay_warm;
+  c->xc.det = det;
+  c->xc.ws_gen = c->ws_gen;
   return KM_OK;
 }
 
@@ -858,11 +941,89 @@ KM_API int kmeans_run_ex(const km_opts* opts, const float* X, int64_t n, int32_t
   return device_entry(opts, X, n, d, C, k, assign, sums, counts, iters, tol, true, stats);
 }
 
+KM_API int kmeans_step_partial(const km_opts* opts, const float* X, int64_t n, int32_t d, const float* C,
+                               int32_t k, int32_t* assign, double* part, km_stats* stats) {
+  g_err.clear();
+  const km_opts o = resolve(opts);
+  if (!X || !C || !assign || !part) return fail(KM_EINVAL, "null array pointer");
+  Problem p{X, n, d, const_cast<float*>(C), k, assign, nullptr, nullptr};
+  int rc = validate_shape(o, p, 1);
+  if (rc) return rc;
+  const size_t nd = (size_t)n * d * 4, kd = (size_t)k * d * 4, na = (size_t)n * 4;
+  const size_t np = 8 * (size_t)KM_PARTIALS_LEN(k, d);
+  if (overlaps(X, nd, C, kd) || overlaps(X, nd, assign, na) || overlaps(X, nd, part, np) || overlaps(C, kd, assign, na) ||
+      overlaps(C, kd, part, np) || overlaps(assign, na, part, np))
+    return fail(KM_EINVAL, "arrays overlap");
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(KM_EUNSUPPORTED, "device index %d", dev);
+  if ((rc = check_device_ptr(X, "X", dev)) || (rc = check_device_ptr(C, "C", dev)) ||
+      (rc = check_device_ptr(assign, "assign", dev)) || (rc = check_device_ptr(part, "part", dev)))
+    return rc;
+  DevCtx* c = get_ctx(dev);
+  std::lock_guard<std::mutex> lk(c->mu);
+  return run_locked(c, o, p, 1, 0.0, false, stats, part);
+}
+
+KM_API int kmeans_apply_partials(const km_opts* opts, const double* part, int32_t k, int32_t d, float* C,
+                                 float* sums, int32_t* counts, km_stats* stats) {
+  g_err.clear();
+  const km_opts o = resolve(opts);
+  if (!part || !C) return fail(KM_EINVAL, "null array pointer");
+  if (k < 1 || d < 1 || d > kMaxD) return fail(KM_EINVAL, "k = %d, d = %d: need k >= 1, 1 <= d <= %d", k, d, kMaxD);
+  const size_t kd = (size_t)k * d * 4, nk = (size_t)k * 4, np = 8 * (size_t)KM_PARTIALS_LEN(k, d);
+  if (overlaps(part, np, C, kd) || (sums && (overlaps(part, np, sums, kd) || overlaps(C, kd, sums, kd))) ||
+      (counts && (overlaps(part, np, counts, nk) || overlaps(C, kd, counts, nk))) ||
+      (sums && counts && overlaps(sums, kd, counts, nk)))
+    return fail(KM_EINVAL, "arrays overlap");
+  int dev = 0;
+  KM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(KM_EUNSUPPORTED, "device index %d", dev);
+  int rc;
+  if ((rc = check_device_ptr(part, "part", dev)) || (rc = check_device_ptr(C, "C", dev)) ||
+      (sums && (rc = check_device_ptr(sums, "sums", dev))) || (counts && (rc = check_device_ptr(counts, "counts", dev))))
+    return rc;
+  DevCtx* c = get_ctx(dev);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if ((rc = init_ctx(c))) return rc;
+  cudaStream_t s = (cudaStream_t)o.stream;
+  if (!c->actl) {
+    if (cudaMalloc(&c->actl, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(KM_ENOMEM, "status allocation failed");
+    }
+  }
+  KM_CUDA(cudaEventRecord(c->ev0, s));
+  KM_CUDA(launch_apply_partials(part, k, d, C, sums, counts, c->actl, s));
+  KM_CUDA(cudaEventRecord(c->ev1, s));
+  unsigned long long h[4] = {0, 0, 0, 0};
+  double tail[2] = {0.0, 0.0};
+  KM_CUDA(cudaMemcpyAsync(h, c->actl, sizeof h, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaMemcpyAsync(tail, part + (int64_t)k * d + k, sizeof tail, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaStreamSynchronize(s));
+  if (h[0]) return fail(KM_EINVAL, "the partials buffer holds a count that is not an integer in [0, 2^31)");
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->objective = tail[0];
+    stats->n_changed = (int64_t)tail[1];
+    double s2;
+    memcpy(&s2, &h[1], sizeof s2);
+    stats->shift = sqrt(s2);
+    stats->n_empty = (int32_t)h[2];
+    stats->iters_done = 1;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    stats->ms = ms;
+  }
+  return KM_OK;
+}
+
 KM_API int kmeans_run_host(const km_opts* opts, const float* X, int64_t n, int32_t d, float* C,
                            int32_t k, int32_t* assign, float* sums, int32_t* counts, int32_t iters,
                            double tol, km_stats* stats) {
   g_err.clear();
-  const km_opts o = resolve(opts);
+  km_opts o = resolve(opts);
+  o.reuse_x = 0;  // the device copy of X is refreshed by every call
   Problem hp{X, n, d, C, k, assign, sums, counts};
   int rc = validate_args(o, hp, iters);
   if (rc) return rc;
@@ -932,9 +1093,10 @@ int class_train(const km_opts* opts, const float* X, int64_t n, int32_t d, const
   }
   DevCtx* c = get_ctx(dev);
   std::lock_guard<std::mutex> lk(c->mu);
+  c->xc.valid = false;  // this call overwrites the workspace
   if ((rc = init_ctx(c))) return rc;
   cudaStream_t s = (cudaStream_t)o.stream;
-  const Layout L = layout_for(n, ncls, d, 1, KM_FP32, 0);
+  const Layout L = layout_for(n, ncls, d, 1, KM_FP32, 0, 0);
   if ((rc = ensure_ws(c, L, s))) return rc;
   const Work w = make_work(c, L);
   const size_t cnt_bytes = align_up(4 * (size_t)ncls), need = cnt_bytes + align_up(cov_bytes) + 1024;
@@ -1047,6 +1209,7 @@ KM_API int kmeans_spade_densities(const km_opts* opts, const float* X, int64_t n
     return fail(KM_EINVAL, "outputs overlap X");
   DevCtx* c = get_ctx(dev);
   std::lock_guard<std::mutex> lk(c->mu);
+  c->xc.valid = false;  // this call overwrites the workspace
   if ((rc = init_ctx(c))) return rc;
   cudaStream_t s = (cudaStream_t)o.stream;
 
@@ -1611,6 +1774,7 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
   if (o.precision != KM_BF16 && o.precision != KM_FP8E4M3)
     return fail(o.precision == KM_FP32 || o.precision == KM_BF16X3 ? KM_EUNSUPPORTED : KM_EINVAL,
                 "batched runs use the tensor-core path: precision must be KM_BF16 or KM_FP8E4M3");
+  if (o.deterministic) return fail(KM_EUNSUPPORTED, "deterministic reduces are available for single-instance calls only");
   for (int b = 0; b < count; ++b) {
     const km_instance& s = inst[b];
     if (!s.X || !s.C || !s.assign || !s.sums || !s.counts) return fail(KM_EINVAL, "instance %d: null pointer", b);
@@ -1627,6 +1791,7 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
   }
   DevCtx* c = get_ctx(dev);
   std::lock_guard<std::mutex> lk(c->mu);
+  c->xc.valid = false;  // this call overwrites the workspace
   BatchCtx& bc = g_batch[dev];
   const uint64_t sig = batch_signature(inst, count, o.precision);
   BatchTune tune{128, 0};

@@ -74,6 +74,11 @@ struct Work {
   unsigned long long* full_hist;     // [iters]
   int* empty_hist;     // [iters]
   unsigned long long* queued_hist;   // [iters] points re-scored by the queued pass
+  // deterministic reduce (null otherwise): exact fixed-point sums on the grid of *xmax
+  int32_t* pcounts;    // [k] counts of a partial step (the caller passes no counts array)
+  unsigned int* xmax;  // max_i ||x_i|| upper bound (FP32 bits), computed once per call
+  unsigned long long* facc;  // [3][k*d] integer parts of the coordinate sums (two's complement)
+  unsigned long long* oacc;  // [3] integer parts of the objective
   // quantised operands of the tensor-core path (null for FP32)
   uint8_t* Xq;         // [n][Kp] point codes (cached for the call)
   float4* xs;          // [n] row scale and norm bounds
@@ -295,8 +300,16 @@ cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s);
 // qmode 0: sums only; 1 / 2: also rewrite the BF16 / E4M3 point codes in the
 // cluster-sorted order of this step (row p of w.Xq = point perm[p]).
 cudaError_t init_segsum();
-cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0);
-cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s);
+// det: exact fixed-point sums and objective into w.facc / w.oacc (grid of *w.xmax)
+cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0, int det = 0);
+cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s, int det = 0);
+// max_i ||x_i|| bound into *w.xmax from per-point bounds (FP32 norms, or the .w of quantised row stats)
+cudaError_t launch_xmax(const float* xnorm, const float4* xs, int64_t n, const Work& w, cudaStream_t s);
+// Sharded step: the shard's partials (sums64 / facc, counts, objective, n_changed) into part
+cudaError_t launch_finish_partial(const Problem& p, const Work& w, double* part, int det, cudaStream_t s);
+// The divide from a reduced partials buffer; actl: 4 words of device scratch (status, shift, empties, ticket)
+cudaError_t launch_apply_partials(const double* part, int k, int d, float* C, float* sums, int32_t* counts,
+                                  unsigned long long* actl, cudaStream_t s);
 cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
                            cudaStream_t s);
 cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
@@ -336,6 +349,49 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float term) {
   float t = __fadd_rn(s, y);
   c = __fsub_rn(__fsub_rn(t, s), y);
   s = t;
+}
+
+// ---------------------------------------------------------------- exact fixed-point sums
+// A value |v| <= 2^E is split into three integers q1, q2, q3 with |q_l| <= 2^20:
+//   v = q1 2^(E-20) + q2 2^(E-41) + q3 2^(E-62) + r,  |r| <= 2^(E-63),
+// each q_l taken by rounding to the nearest integer (ties to even) and every
+// remainder exact in FP32 (it is the difference of v and a multiple of a power
+// of two at least as fine as v's own spacing, or v itself). Integer sums of the
+// q_l do not depend on the order of the additions. E is clamped to [-60, 128]
+// so that every scale is a normal FP32 number.
+struct FxScale {
+  float inv[3];   // 2^(20 - E), 2^(41 - E), 2^(62 - E)
+  float step[3];  // 2^(E - 20), 2^(E - 41), 2^(E - 62)
+};
+
+__device__ __forceinline__ FxScale fx_scale(float bound) {
+  int e = 0;
+  if (bound > 0.f && isfinite(bound)) frexpf(bound, &e);  // bound < 2^e
+  e = e < -60 ? -60 : (e > 128 ? 128 : e);
+  FxScale f;
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    f.inv[l] = ldexpf(1.f, 20 + 21 * l - e);
+    f.step[l] = ldexpf(1.f, e - 20 - 21 * l);
+  }
+  return f;
+}
+
+// Adds the three integer parts of v to q (|v| <= 2^E of the scale).
+__device__ __forceinline__ void fx_add(float v, const FxScale& f, int (&q)[3]) {
+  constexpr float kMagic = 12582912.f;  // 1.5 2^23: y = kMagic + RN(v s) exactly while |v s| < 2^22
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const float y = fmaf(v, f.inv[l], kMagic);
+    q[l] += __float_as_int(y) - __float_as_int(kMagic);
+    v = fmaf(-(y - kMagic), f.step[l], v);  // exact remainder
+  }
+}
+
+// The FP64 value of integer sums a[0..2] on the scale's grid (fixed order; each
+// product exact, |a_l| < 2^53).
+__device__ __forceinline__ double fx_value(long long a0, long long a1, long long a2, const FxScale& f) {
+  return ((double)a0 * (double)f.step[0] + (double)a1 * (double)f.step[1]) + (double)a2 * (double)f.step[2];
 }
 
 // Lexicographic (value, index) order used by every argmin: lower value first,

@@ -22,6 +22,16 @@
 // magnitudes, and the FP64 combine adds ~2^-53 per partial, so every sum is
 // within ~1.2e-7 of sum |x_it| regardless of cluster size or order, far
 // inside the 1e-5 centroid tolerance.
+//
+// Deterministic mode (DET): the same passes, but every coordinate of a row is
+// split into three integer parts on the grid of 2^E >= max_i ||x_i||
+// (fx_add), summed in 32-bit integers per run (at most 1024 rows, |sum| <=
+// 2^30) and added into 64-bit integer accumulators; the objective terms of a
+// lane likewise on the grid of (max ||x|| + max ||c||)^2. Integer sums do not
+// depend on the order of the additions, so sums, centroids and the objective
+// come out bit-identical run after run; the divide forms each FP64 sum from
+// its three integers in a fixed order. Dropped per point and coordinate:
+// <= 2^(E-63).
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -177,6 +187,36 @@ __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, i
   }
 }
 
+// Deterministic flush: the run's integer parts into the 64-bit accumulators
+// facc[l][j d + t] (two's-complement adds through unsigned atomics).
+template <int V>
+__device__ __forceinline__ void flush_fixed(unsigned long long* __restrict__ facc, int64_t kd, int j, int d, int lane,
+                                            int (&q)[V][3]) {
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int t = v * 32 + lane;
+    if (t < d) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        if (q[v][l]) atomicAdd(facc + l * kd + (int64_t)j * d + t, (unsigned long long)(long long)q[v][l]);
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) q[v][l] = 0;
+  }
+}
+
+// The warp's objective integer parts (lane sums widened to 64 bits) into oacc[0..2].
+__device__ __forceinline__ void flush_objective_fixed(unsigned long long* __restrict__ oacc, int lane, int (&o)[3]) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    long long v = o[l];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0 && v) atomicAdd(oacc + l, (unsigned long long)v);
+    o[l] = 0;
+  }
+}
+
 // Rows of one gathered batch per stage of the segmented sum (two stages of at
 // most 4 KB per warp, so that three CTAs of 8 warps share an SM).
 template <int V>
@@ -194,16 +234,29 @@ __host__ __device__ constexpr size_t seg_smem_bytes() {
 // for the two-part codes), using the row scale in xs, and the row statistics
 // xs at p; the codes equal those the quantisation stage produces for the same
 // point.
-template <int V, int QM>
+template <int V, int QM, bool DET>
 __global__ void __launch_bounds__(256, 3)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
               const int32_t* __restrict__ perm, const int32_t* __restrict__ slab, double* __restrict__ sums64,
               Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs, int Kp,
-              float4* __restrict__ xs_sorted) {
+              float4* __restrict__ xs_sorted, int k, unsigned long long* __restrict__ facc,
+              unsigned long long* __restrict__ oacc, const unsigned int* __restrict__ xmax) {
   constexpr int RB = seg_rows<V>();  // rows per batch (lane r < RB holds row r's indices)
   constexpr int RS = 32 * V;         // shared-memory floats per row
   extern __shared__ __align__(16) float seg_smem[];
   if (halted(ctl)) return;
+  // deterministic mode: grids of the coordinate sums and of the objective terms
+  FxScale fxs, fxo;
+  int q[DET ? V : 1][3], oq[3] = {0, 0, 0}, run_rows = 0, obj_rows = 0;
+  const int64_t kd = (int64_t)k * d;
+  if constexpr (DET) {
+    const float xm = __uint_as_float(*xmax), cm = __uint_as_float(ctl->cmax_bits);
+    fxs = fx_scale(xm);
+    const float ob = __fmul_ru(__fadd_ru(xm, cm), __fadd_ru(xm, cm));  // >= every lane's sum of squares
+    fxo = fx_scale(__fmul_ru(ob, 1.f + 0x1p-12f));
+#pragma unroll
+    for (int v = 0; v < V; ++v) q[v][0] = q[v][1] = q[v][2] = 0;
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* stage0 = seg_smem + (size_t)wib * 2 * RB * RS;
   float* stage1 = stage0 + RB * RS;
@@ -259,7 +312,12 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     const unsigned starts = __ballot_sync(0xffffffffu, lane < rows && j_c != (lane == 0 ? cur : jprev));
     for (int r = 0; r < rows;) {
       if ((starts >> r) & 1u) {  // the same for every lane
-        if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+        if constexpr (DET) {
+          if (cur >= 0) flush_fixed<V>(facc, kd, cur, d, lane, q);
+          run_rows = 0;
+        } else {
+          if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+        }
         cur = __shfl_sync(0xffffffffu, j_c, r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -270,16 +328,29 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
       const int rend = later ? __ffs(later) - 1 : rows;
       for (; r < rend; ++r) {
-        float xr[V], q = 0.f;
+        float xr[V], qo = 0.f;
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int t = v * 32 + lane;
           xr[v] = t < d ? st[r * RS + t] : 0.f;
-          kahan_add(s[v], c[v], xr[v]);
+          if constexpr (DET) fx_add(xr[v], fxs, q[v]);
+          else kahan_add(s[v], c[v], xr[v]);
           const float df = __fsub_rn(xr[v], cj[v]);
-          q = fmaf(df, df, q);
+          qo = fmaf(df, df, qo);
         }
-        kahan_add(objS, objC, q);
+        if constexpr (DET) {
+          fx_add(qo, fxo, oq);
+          if (++run_rows == 1024) {  // keeps every 32-bit run sum within 2^30
+            flush_fixed<V>(facc, kd, cur, d, lane, q);
+            run_rows = 0;
+          }
+          if (++obj_rows == 1024) {
+            flush_objective_fixed(oacc, lane, oq);
+            obj_rows = 0;
+          }
+        } else {
+          kahan_add(objS, objC, qo);
+        }
         if constexpr (QM != 0) {
           const int64_t prow = P0 + b * RB + r;
           if constexpr (QM == 1) {
@@ -316,17 +387,47 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     i_n = i_nn;
     j_n = j_nn;
   }
-  if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
-  double o = (double)objS - (double)objC;
+  if constexpr (DET) {
+    if (cur >= 0) flush_fixed<V>(facc, kd, cur, d, lane, q);
+    flush_objective_fixed(oacc, lane, oq);
+  } else {
+    if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+    double o = (double)objS - (double)objC;
 #pragma unroll
-  for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
-  if (lane == 0 && o != 0.0) atomicAdd(&ctl->objective, o);
+    for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+    if (lane == 0 && o != 0.0) atomicAdd(&ctl->objective, o);
+  }
+}
+
+// Deterministic mode: the grids the segmented sum used (same inputs, same values).
+__device__ __forceinline__ void det_scales(const Work& w, const Ctl* ctl, FxScale& fxs, FxScale& fxo) {
+  const float xm = __uint_as_float(*w.xmax), cm = __uint_as_float(ctl->cmax_bits);
+  fxs = fx_scale(xm);
+  const float ob = __fmul_ru(__fadd_ru(xm, cm), __fadd_ru(xm, cm));
+  fxo = fx_scale(__fmul_ru(ob, 1.f + 0x1p-12f));
+}
+
+// Deterministic mode: the FP64 value of coordinate sum e, its accumulators cleared.
+__device__ __forceinline__ double det_take_sum(const Work& w, int64_t kd, int64_t e, const FxScale& fxs) {
+  const long long a0 = (long long)w.facc[e], a1 = (long long)w.facc[kd + e], a2 = (long long)w.facc[2 * kd + e];
+  w.facc[e] = 0ull;
+  w.facc[kd + e] = 0ull;
+  w.facc[2 * kd + e] = 0ull;
+  return fx_value(a0, a1, a2, fxs);
+}
+
+__device__ __forceinline__ double det_take_objective(const Work& w, const FxScale& fxo) {
+  const long long a0 = (long long)w.oacc[0], a1 = (long long)w.oacc[1], a2 = (long long)w.oacc[2];
+  w.oacc[0] = w.oacc[1] = w.oacc[2] = 0ull;
+  return fx_value(a0, a1, a2, fxo);
 }
 
 // c_j = sums_j / counts_j in FP64, rounded to FP32 (an empty cluster keeps
 // c_j); sums are returned rounded to FP32 and the FP64 accumulators are
 // cleared for the next step. The last block to finish records the step's
-// statistics and evaluates the stop rule. One warp per centroid.
+// statistics and evaluates the stop rule. One warp per centroid. DET: the sums
+// and the objective come from the exact integer accumulators.
+template <bool DET>
 __global__ void __launch_bounds__(256)
 divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ counts,
               double* __restrict__ sums64, float* __restrict__ sums, Ctl* ctl, Work w, double tol) {
@@ -334,13 +435,21 @@ divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ c
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int64_t kd = (int64_t)k * d;
+  FxScale fxs, fxo;
+  if constexpr (DET) det_scales(w, ctl, fxs, fxo);
   for (int j = gw; j < k; j += nw) {
     const int cnt = counts[j];
     double acc = 0.0;
     for (int t = lane; t < d; t += 32) {
       const int64_t e = (int64_t)j * d + t;
-      const double sv = sums64[e];
-      sums64[e] = 0.0;
+      double sv;
+      if constexpr (DET) {
+        sv = det_take_sum(w, kd, e, fxs);
+      } else {
+        sv = sums64[e];
+        sums64[e] = 0.0;
+      }
       sums[e] = (float)sv;
       const float co = C[e];
       const float cn = cnt > 0 ? (float)(sv / (double)cnt) : co;
@@ -365,6 +474,7 @@ divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ c
       const int it = vc->iters_done;
       const double shift = sqrt(__longlong_as_double((long long)vc->shift2_bits));
       const unsigned long long changed = vc->n_changed;
+      if constexpr (DET) vc->objective = det_take_objective(w, fxo);
       w.obj_hist[it] = vc->objective;
       w.shift_hist[it] = shift;
       w.changed_hist[it] = changed;
@@ -374,6 +484,105 @@ divide_kernel(float* __restrict__ C, int k, int d, const int32_t* __restrict__ c
       w.queued_hist[it] = min(vc->n_fullq, (unsigned long long)w.fq_cap);
       vc->iters_done = it + 1;
       if (tol > 0.0 && (changed == 0 || shift <= tol)) vc->done = 1;
+    }
+  }
+}
+
+// max_i of the per-point norm bounds (FP32 path: xnorm; quantised paths: xs[i].w).
+__global__ void __launch_bounds__(256)
+xmax_kernel(const float* __restrict__ xnorm, const float4* __restrict__ xs, int64_t n, unsigned int* xmax,
+            const Ctl* ctl) {
+  if (halted(ctl)) return;
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, xnorm ? xnorm[i] : xs[i].w);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomic_max_nonneg(xmax, m);
+}
+
+// A shard's partials: part[0, kd) already holds the FP64 sums (the segmented sum
+// accumulates into it) or, DET, is formed from the integer accumulators;
+// part[kd, kd + k) = counts, part[kd + k] = objective, part[kd + k + 1] =
+// n_changed. The last block records the step's statistics (as the divide does,
+// with shift and empties 0) and counts the step.
+template <bool DET>
+__global__ void __launch_bounds__(256)
+finish_partial_kernel(const int32_t* __restrict__ counts, int k, int d, double* __restrict__ part, Ctl* ctl,
+                      Work w) {
+  if (halted(ctl)) return;
+  const int64_t kd = (int64_t)k * d;
+  FxScale fxs, fxo;
+  if constexpr (DET) det_scales(w, ctl, fxs, fxo);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kd + k; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < kd) {
+      if constexpr (DET) part[e] = det_take_sum(w, kd, e, fxs);
+    } else {
+      part[e] = (double)counts[e - kd];
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned ticket = atomicAdd(&ctl->blocks_done, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      volatile Ctl* vc = ctl;
+      const int it = vc->iters_done;
+      if constexpr (DET) vc->objective = det_take_objective(w, fxo);
+      part[kd + k] = vc->objective;
+      part[kd + k + 1] = (double)vc->n_changed;
+      w.obj_hist[it] = vc->objective;
+      w.shift_hist[it] = 0.0;
+      w.changed_hist[it] = vc->n_changed;
+      w.flagged_hist[it] = vc->n_flagged;
+      w.full_hist[it] = vc->n_full;
+      w.empty_hist[it] = 0;
+      w.queued_hist[it] = min(vc->n_fullq, (unsigned long long)w.fq_cap);
+      vc->iters_done = it + 1;
+    }
+  }
+}
+
+// actl[0] = 1 when a count of the reduced buffer is not an integer in [0, 2^31).
+__global__ void __launch_bounds__(256)
+check_partials_kernel(const double* __restrict__ part, int k, int d, unsigned long long* actl) {
+  const int64_t kd = (int64_t)k * d;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+    const double c = part[kd + j];
+    if (!(c >= 0.0 && c < 2147483648.0 && c == floor(c))) atomicExch(actl, 1ull);
+  }
+}
+
+// The divide from a reduced buffer (one warp per centroid): as divide_kernel,
+// with actl[1] = max_j ||dc_j||^2 (FP64 bits) and actl[2] = empty clusters.
+__global__ void __launch_bounds__(256)
+apply_partials_kernel(const double* __restrict__ part, int k, int d, float* __restrict__ C, float* __restrict__ sums,
+                      int32_t* __restrict__ counts, unsigned long long* actl) {
+  if (*(volatile unsigned long long*)actl) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int64_t kd = (int64_t)k * d;
+  for (int j = gw; j < k; j += nw) {
+    const int cnt = (int)part[kd + j];
+    double acc = 0.0;
+    for (int t = lane; t < d; t += 32) {
+      const int64_t e = (int64_t)j * d + t;
+      const double sv = part[e];
+      if (sums) sums[e] = (float)sv;
+      const float co = C[e];
+      const float cn = cnt > 0 ? (float)(sv / (double)cnt) : co;
+      C[e] = cn;
+      const double df = (double)cn - (double)co;
+      acc = fma(df, df, acc);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      atomic_max_nonneg(&actl[1], acc);
+      if (cnt == 0) atomicAdd(&actl[2], 1ull);
+      if (counts) counts[j] = cnt;
     }
   }
 }
@@ -410,18 +619,22 @@ cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int V, int QM>
+template <int V, int QM, bool DET>
 cudaError_t seg_attr() {
-  return cudaFuncSetAttribute(segsum_kernel<V, QM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(segsum_kernel<V, QM, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)seg_smem_bytes<V>());
 }
 
 template <int V>
 cudaError_t seg_attrs() {
-  cudaError_t e = seg_attr<V, 0>();
-  if (e == cudaSuccess) e = seg_attr<V, 1>();
-  if (e == cudaSuccess) e = seg_attr<V, 2>();
-  if (e == cudaSuccess) e = seg_attr<V, 3>();
+  cudaError_t e = seg_attr<V, 0, false>();
+  if (e == cudaSuccess) e = seg_attr<V, 1, false>();
+  if (e == cudaSuccess) e = seg_attr<V, 2, false>();
+  if (e == cudaSuccess) e = seg_attr<V, 3, false>();
+  if (e == cudaSuccess) e = seg_attr<V, 0, true>();
+  if (e == cudaSuccess) e = seg_attr<V, 1, true>();
+  if (e == cudaSuccess) e = seg_attr<V, 2, true>();
+  if (e == cudaSuccess) e = seg_attr<V, 3, true>();
   return e;
 }
 
@@ -437,44 +650,86 @@ cudaError_t init_segsum() {
   return e;
 }
 
-cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode, int Kp) {
+template <int V, int QM, bool DET>
+void seg_launch(int blocks, const Problem& p, const Work& w, int Kp, cudaStream_t s) {
+  segsum_kernel<V, QM, DET><<<blocks, 256, seg_smem_bytes<V>(), s>>>(
+      p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, w.sums64, w.ctl, QM ? w.Xq : nullptr, QM ? w.xs : nullptr,
+      QM ? Kp : 0, QM ? w.xs_sorted : nullptr, p.k, w.facc, w.oacc, w.xmax);
+}
+
+template <int V, bool DET>
+void seg_launch_q(int qmode, int blocks, const Problem& p, const Work& w, int Kp, cudaStream_t s) {
+  if (qmode == 1) seg_launch<V, 1, DET>(blocks, p, w, Kp, s);
+  else if (qmode == 2) seg_launch<V, 2, DET>(blocks, p, w, Kp, s);
+  else if (qmode == 3) seg_launch<V, 3, DET>(blocks, p, w, Kp, s);
+  else seg_launch<V, 0, DET>(blocks, p, w, Kp, s);
+}
+
+template <int V>
+void seg_launch_v(int qmode, int det, int blocks, const Problem& p, const Work& w, int Kp, cudaStream_t s) {
+  if (det) seg_launch_q<V, true>(qmode, blocks, p, w, Kp, s);
+  else seg_launch_q<V, false>(qmode, blocks, p, w, Kp, s);
+}
+
+cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode, int Kp, int det) {
   // two CTAs of 8 warps per SM; each warp takes a contiguous range of at least 64 positions
   int64_t blocks = (p.n + 8 * 64 - 1) / (8 * 64);
   if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
+  if (det && (!w.facc || !w.oacc || !w.xmax)) return cudaErrorInvalidValue;
   const int V = (p.d + 31) / 32;
   switch (V) {
-#define KM_CASE(v)                                                                                               \
-  case v:                                                                                                         \
-    if (qmode == 1)                                                                                               \
-      segsum_kernel<v, 1><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
-                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
-                                                                        w.xs_sorted);                             \
-    else if (qmode == 2)                                                                                          \
-      segsum_kernel<v, 2><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
-                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
-                                                                        w.xs_sorted);                             \
-    else if (qmode == 3)                                                                                          \
-      segsum_kernel<v, 3><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
-                                                                        w.sums64, w.ctl, w.Xq, w.xs, Kp,          \
-                                                                        w.xs_sorted);                             \
-    else                                                                                                          \
-      segsum_kernel<v, 0><<<(int)blocks, 256, seg_smem_bytes<v>(), s>>>(p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, \
-                                                                        w.sums64, w.ctl, nullptr, nullptr, 0,     \
-                                                                        nullptr);                                 \
-    break;
-    KM_CASE(1) KM_CASE(2) KM_CASE(3) KM_CASE(4) KM_CASE(5) KM_CASE(6) KM_CASE(7) KM_CASE(8)
-#undef KM_CASE
+    case 1: seg_launch_v<1>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 2: seg_launch_v<2>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 3: seg_launch_v<3>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 4: seg_launch_v<4>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 5: seg_launch_v<5>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 6: seg_launch_v<6>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 7: seg_launch_v<7>(qmode, det, (int)blocks, p, w, Kp, s); break;
+    case 8: seg_launch_v<8>(qmode, det, (int)blocks, p, w, Kp, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s) {
+cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s, int det) {
   (void)iter;
   int blocks = (p.k + 7) / 8;
   const int cap = num_sms() * 4;
   if (blocks > cap) blocks = cap;
-  divide_kernel<<<blocks, 256, 0, s>>>(p.C, p.k, p.d, p.counts, w.sums64, p.sums, w.ctl, w, tol);
+  if (det) divide_kernel<true><<<blocks, 256, 0, s>>>(p.C, p.k, p.d, p.counts, w.sums64, p.sums, w.ctl, w, tol);
+  else divide_kernel<false><<<blocks, 256, 0, s>>>(p.C, p.k, p.d, p.counts, w.sums64, p.sums, w.ctl, w, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xmax(const float* xnorm, const float4* xs, int64_t n, const Work& w, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(w.xmax, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > num_sms() * 4) blocks = num_sms() * 4;
+  xmax_kernel<<<(int)blocks, 256, 0, s>>>(xnorm, xs, n, w.xmax, w.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_partial(const Problem& p, const Work& w, double* part, int det, cudaStream_t s) {
+  const int64_t kd = (int64_t)p.k * p.d;
+  int64_t blocks = (kd + p.k + 255) / 256;
+  if (blocks > num_sms() * 4) blocks = num_sms() * 4;
+  if (det) finish_partial_kernel<true><<<(int)blocks, 256, 0, s>>>(p.counts, p.k, p.d, part, w.ctl, w);
+  else finish_partial_kernel<false><<<(int)blocks, 256, 0, s>>>(p.counts, p.k, p.d, part, w.ctl, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_partials(const double* part, int k, int d, float* C, float* sums, int32_t* counts,
+                                  unsigned long long* actl, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(actl, 0, 4 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  int blocks = (k + 255) / 256;
+  if (blocks > num_sms() * 4) blocks = num_sms() * 4;
+  check_partials_kernel<<<blocks, 256, 0, s>>>(part, k, d, actl);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  blocks = (k + 7) / 8;
+  if (blocks > num_sms() * 4) blocks = num_sms() * 4;
+  apply_partials_kernel<<<blocks, 256, 0, s>>>(part, k, d, C, sums, counts, actl);
   return cudaGetLastError();
 }
 

@@ -24,7 +24,7 @@ STAGES = ("xnorm", "prep", "assign", "recheck", "count", "scan", "scatter", "seg
 EXPORTS = ("kmeans_default_opts", "kmeans_step", "kmeans_run", "kmeans_step_ex", "kmeans_run_ex",
            "kmeans_run_host", "kmeans_last_error", "kmeans_version", "kmeans_reduce_noalloc",
            "kmeans_run_batched", "kmeans_gda_train", "kmeans_nb_train", "kmeans_spade_densities",
-           "kmeans_probe_mma", "kmeans_probe_ffma")
+           "kmeans_probe_mma", "kmeans_probe_ffma", "kmeans_step_partial", "kmeans_apply_partials")
 SPADE_POLICY = {"last": 0, "first": 1}
 
 
@@ -37,6 +37,7 @@ class KMeansError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("recheck", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("reuse_x", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -102,6 +103,10 @@ def load(path: str = LIB_PATH):
     lib.kmeans_nb_train.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp]
     lib.kmeans_spade_densities.restype = ctypes.c_int
     lib.kmeans_spade_densities.argtypes = [P(Opts), vp, i64, i32, dbl, dbl, i32, vp, vp, vp, P(SpadeStats)]
+    lib.kmeans_step_partial.restype = ctypes.c_int
+    lib.kmeans_step_partial.argtypes = [P(Opts), vp, i64, i32, vp, i32, vp, vp, P(Stats)]
+    lib.kmeans_apply_partials.restype = ctypes.c_int
+    lib.kmeans_apply_partials.argtypes = [P(Opts), vp, i32, i32, vp, vp, vp, P(Stats)]
     lib.kmeans_probe_mma.restype = ctypes.c_int
     lib.kmeans_probe_mma.argtypes = [i32, vp, vp, i32, vp, vp]
     lib.kmeans_probe_ffma.restype = ctypes.c_int
@@ -122,13 +127,15 @@ def _check(rc: int):
 
 
 def make_opts(precision: str = "fp32", recheck: bool = True, stream=None, profile: bool = False,
-              warm_start: bool = False) -> Opts:
+              warm_start: bool = False, deterministic: bool = False, reuse_x: bool = False) -> Opts:
     o = Opts()
     _lib.kmeans_default_opts(ctypes.byref(o))
     o.precision = PRECISION[precision]
     o.recheck = 1 if recheck else 0
     o.profile = 1 if profile else 0
     o.warm_start = 1 if warm_start else 0
+    o.deterministic = 1 if deterministic else 0
+    o.reuse_x = 1 if reuse_x else 0
     o.stream = stream
     return o
 
@@ -177,12 +184,12 @@ def alloc_outputs(X, C):
 
 
 def step(X, C, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True, stream=None,
-         profile=False, warm_start=False) -> Outputs:
+         profile=False, warm_start=False, deterministic=False, reuse_x=False) -> Outputs:
     """One Lloyd step on device tensors; C is updated in place (kmeans_step_ex)."""
     if assign is None:
         assign, sums, counts = alloc_outputs(X, C)
     n, d, k = _check_tensors(X, C, assign, sums, counts)
-    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start, deterministic, reuse_x)
     st = Stats()
     _check(_lib.kmeans_step_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
                                sums.data_ptr(), counts.data_ptr(), ctypes.byref(st)))
@@ -190,12 +197,12 @@ def step(X, C, assign=None, sums=None, counts=None, *, precision="fp32", recheck
 
 
 def run(X, C, iters, tol=0.0, assign=None, sums=None, counts=None, *, precision="fp32", recheck=True,
-        stream=None, profile=False, warm_start=False) -> Outputs:
+        stream=None, profile=False, warm_start=False, deterministic=False, reuse_x=False) -> Outputs:
     """Up to ``iters`` Lloyd steps on device tensors; C is updated in place (kmeans_run_ex)."""
     if assign is None:
         assign, sums, counts = alloc_outputs(X, C)
     n, d, k = _check_tensors(X, C, assign, sums, counts)
-    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start)
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start, deterministic, reuse_x)
     st = Stats()
     _check(_lib.kmeans_run_ex(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
                               sums.data_ptr(), counts.data_ptr(), int(iters), float(tol), ctypes.byref(st)))
@@ -326,6 +333,49 @@ def spade_densities(X, apprx_width: float, kernel_width: float, *, policy: str =
 
 def version() -> int:
     return int(_lib.kmeans_version())
+
+
+# ----------------------------------------------------------------------------- sharded step
+
+def partials_len(k: int, d: int) -> int:
+    """Entries of a partials buffer (KM_PARTIALS_LEN): k*d sums, k counts, objective, n_changed."""
+    return k * d + k + 2
+
+
+def step_partial(X, C, assign, part, *, precision="fp32", recheck=True, stream=None, warm_start=False,
+                 deterministic=False, reuse_x=False, profile=False) -> dict:
+    """A shard's part of a Lloyd step (kmeans_step_partial): assign is written, C is left alone, and
+    ``part`` (float64, partials_len(k, d)) receives the shard's sums, counts, objective and n_changed."""
+    import torch
+
+    n, d = X.shape
+    k = C.shape[0]
+    for name, t, dt, shape in (("X", X, torch.float32, (n, d)), ("C", C, torch.float32, (k, d)),
+                               ("assign", assign, torch.int32, (n,)),
+                               ("part", part, torch.float64, (partials_len(k, d),))):
+        if not t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor of shape {shape}")
+    o = make_opts(precision, recheck, _stream_handle(stream), profile, warm_start, deterministic, reuse_x)
+    st = Stats()
+    _check(_lib.kmeans_step_partial(ctypes.byref(o), X.data_ptr(), n, d, C.data_ptr(), k, assign.data_ptr(),
+                                    part.data_ptr(), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def apply_partials(part, C, sums=None, counts=None, *, stream=None) -> dict:
+    """The divide of a sharded step from a reduced partials buffer (kmeans_apply_partials); C is
+    updated in place, sums / counts (optional) filled. Returns objective, n_changed, shift, n_empty."""
+    import torch
+
+    k, d = C.shape
+    if not part.is_cuda or part.dtype != torch.float64 or part.numel() != partials_len(k, d) or not part.is_contiguous():
+        raise ValueError("part must be a contiguous CUDA float64 tensor of partials_len(k, d) entries")
+    o = make_opts(stream=_stream_handle(stream))
+    st = Stats()
+    _check(_lib.kmeans_apply_partials(ctypes.byref(o), part.data_ptr(), k, d, C.data_ptr(),
+                                      sums.data_ptr() if sums is not None else None,
+                                      counts.data_ptr() if counts is not None else None, ctypes.byref(st)))
+    return st.as_dict()
 
 
 # ----------------------------------------------------------------------------- diagnostics
