@@ -668,9 +668,37 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const int nall = it.nchunks * nblk;
       uint32_t v[32], v2[32];
       int c = c0;
+      if (!BATCH && BN == 128) {
+        // 128-column chunks in straight-line code: two 64-column halves, each two TMEM loads and
+        // one wait; the buffer is released once the second half is in registers
+#pragma unroll 1
+        for (int cc = 0; cc < it.nchunks && ok; ++cc) {
+          const int buf = 2 * (gu & 1) + grp;
+          if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gu >> 1) & 1, &abort_s, P.wait_ns))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after_sync();
+          const uint32_t ta = trow + (uint32_t)(buf * 128);
+          const int j0 = c * 128;
+          tmem_ld_32x32b_x32(ta, v);
+          tmem_ld_32x32b_x32(ta + 32u, v2);
+          tmem_ld_wait();
+          score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
+          tmem_ld_32x32b_x32(ta + 64u, v);
+          tmem_ld_32x32b_x32(ta + 96u, v2);
+          tmem_ld_wait();
+          tc_fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+          score_block2(v, v2, Hs + j0 + 64, wrow, top, j0 + 64, thr, margin);
+          ++gu;
+          c = (c + 1 == it.nchunks) ? 0 : c + 1;
+        }
+      }
       int blk = 0;  // 32-column block within the current chunk
 #pragma unroll 1
-      for (int kb = 0; kb < nall && ok;) {
+      for (int kb = (!BATCH && BN == 128) ? nall : 0; kb < nall && ok;) {
         const int buf = 2 * (gu & 1) + grp;
         if (blk == 0) {  // a new chunk: wait for its accumulators
           if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (gu >> 1) & 1, &abort_s, P.wait_ns))) {
