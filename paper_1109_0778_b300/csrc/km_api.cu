@@ -162,10 +162,14 @@ int init_ctx(DevCtx* c) {
 size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 
 // Shape of the tensor-core path for (d, k, precision).
-// Kp: d padded to whole 128-byte K blocks; Kw: elements of one code row (Kp,
-// or 2 Kp for the two-part BF16 codes); nkb: K blocks of one code row.
+// Kp: d padded to whole 128-byte K blocks; Kw: elements of one point code row
+// (Kp, or 2 Kp for the two-part BF16 codes); nkb: K blocks of one point code
+// row. fold (BF16 with 128-centroid chunks): every centroid also has a 16-element
+// BF16 slice holding -h_j (Hc, staged with the 32-byte swizzle), contracted
+// with a slice of ones, so the accumulators hold x.c_j - h_j and the epilogue
+// takes no h_j and no multiply-add. Kc: elements of one centroid code row.
 struct TcShape {
-  int fp8, split, esz, Kp, Kw, nkb, bn, kp, nchunks, stages, abufs;
+  int fp8, split, esz, Kp, Kw, nkb, bn, kp, nchunks, stages, abufs, fold, Kc;
   int qmode() const { return split ? 2 : fp8 ? 1 : 0; }  // quantisation stage mode
 };
 
@@ -179,6 +183,17 @@ TcShape tc_shape(int precision, int d, int k) {
   t.Kw = t.split ? 2 * t.Kp : t.Kp;
   t.nkb = t.Kw / kbe;
   t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of any width
+  t.Kc = t.Kw;
+  t.fold = 0;
+  if (!t.fp8 && !t.split && t.nkb <= 2) {  // BF16, 128-centroid chunks, -h_j folded in when it fits
+    t.bn = 128;
+    t.nchunks = t.kp / 128;
+    t.stages = tc_pick_buffers(t.nkb, 128, t.kp, 0, &t.abufs, 1);
+    if (t.stages >= 2) {
+      t.fold = 1;
+      return t;
+    }
+  }
   // chunk width: 128 centroids for short rows, else 64; 32 when only that
   // leaves room for two B stages (the widest two-part codes)
   for (int bn = t.nkb <= 2 ? 128 : 64; bn >= 32; bn /= 2) {
@@ -201,7 +216,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, pcounts, xmax, facc, oacc, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, pcounts, xmax, facc, oacc, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -236,17 +251,20 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
   L.labs = take(4 * (size_t)n);  // labels in cluster-sorted order (scatter stage)
   if (precision != KM_FP32) {
     const TcShape t = tc_shape(precision, d, k);
-    size_t xq = (size_t)n * t.Kw * t.esz, cq = (size_t)t.kp * t.Kw * t.esz;
+    size_t xq = (size_t)n * t.Kw * t.esz, cq = (size_t)t.kp * t.Kc * t.esz;
     const bool cold = cold_bf16_first(precision, warm, d, k);
     if (cold) {
       const TcShape t16 = tc_shape(KM_BF16, d, k);
       xq = std::max(xq, (size_t)n * t16.Kp * 2);
-      cq = std::max(cq, (size_t)t16.kp * t16.Kp * 2);
+      cq = std::max(cq, (size_t)t16.kp * t16.Kc * 2);
     }
     L.Xq = take(xq);
     L.xs = take(16 * (size_t)n);
     L.xs16 = cold ? take(16 * (size_t)n) : 0;
     L.Cq = take(cq);
+    // -h_j slices of the folded BF16 contraction (the main shape, or the BF16 first step of a cold call)
+    const bool hfold = t.fold || (cold && tc_shape(KM_BF16, d, k).fold);
+    L.hc = hfold ? take(32 * (size_t)std::max(t.kp, tc_shape(KM_BF16, d, k).kp)) : 0;
     L.hq = take(4 * (size_t)t.kp);
     L.scq = take(4 * (size_t)t.kp);
     L.xss = take(16 * (size_t)n);
@@ -264,14 +282,16 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
       L.Kp16 = t16.Kp;
       L.xq16 = take((size_t)L.fq_cap * t16.Kp * 2);
       L.xs16q = take(16 * (size_t)L.fq_cap);
-      L.cq16 = take((size_t)t16.kp * t16.Kp * 2);
+      L.cq16 = take((size_t)t16.kp * t16.Kc * 2);
+      L.hc16 = t16.fold ? take(32 * (size_t)t16.kp) : 0;
       L.hq16 = take(4 * (size_t)t16.kp);
       L.scq16 = take(4 * (size_t)t16.kp);
     } else {
       L.Kp16 = 0;
-      L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
+      L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.hc16 = 0;
     }
   } else {
+    L.hc = L.hc16 = 0;
     L.Kp16 = 0;
     L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
@@ -355,6 +375,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
   w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
   w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
+  w.Hc = L.hc ? (void*)(b + L.hc) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
   w.state3 = L.state3 ? (float*)(b + L.state3) : nullptr;
   w.xs16 = L.xs16 ? (float4*)(b + L.xs16) : nullptr;
@@ -403,6 +424,20 @@ int encode_codes_map(CUtensorMap* m, void* base, int64_t rows, int Kp, int esz, 
   return KM_OK;
 }
 
+// [rows][16] BF16 -h_j slices -> boxes of 16 elements (32 B) x box_rows, 32-byte swizzle.
+int encode_h_map(CUtensorMap* m, void* base, int64_t rows, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(KM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[2] = {16, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {32};
+  cuuint32_t box[2] = {16, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(KM_ECUDA, "cuTensorMapEncodeTiled (h slices) failed (%d)", (int)r);
+  return KM_OK;
+}
+
 // Per-call state of a step sequence: precision, recheck switch, tensor-core launch data.
 struct StepCfg {
   int precision;
@@ -424,6 +459,7 @@ struct StepCfg {
   TcLaunch L16;
   TcParams P16;
   uint8_t* Cq16;
+  void* Hc16;  // -h_j slices of the re-score codes (folded BF16), null otherwise
   float *hq16, *scq16;
 };
 
@@ -514,7 +550,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   const TcShape& t = cold ? cfg.t0 : cfg.t;
   if ((e = cudaMemsetAsync(w.ctl, 0, kCtlIterBytes, s))) return e;
   if ((e = at(0))) return e;
-  if (tcp) e = launch_quant_c(p, w, t.qmode(), t.kp, t.Kp, w.Cq, w.hq, w.scq, s);
+  if (tcp) e = launch_quant_c(p, w, t.qmode(), t.kp, t.Kp, w.Cq, t.fold ? w.Hc : nullptr, w.hq, w.scq, s);
   else e = launch_prep(p, w, s);
   if (e) return e;
   if ((e = at(1))) return e;
@@ -535,7 +571,8 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
     if (cfg.rs16 && !cold)
       tc16 = [&](cudaStream_t st) {
         const TcShape& t16 = cfg.t16;
-        cudaError_t r = launch_quant_c(p, w, 0, t16.kp, t16.Kp, cfg.Cq16, cfg.hq16, cfg.scq16, st, true);
+        cudaError_t r = launch_quant_c(p, w, 0, t16.kp, t16.Kp, cfg.Cq16, t16.fold ? cfg.Hc16 : nullptr, cfg.hq16,
+                                       cfg.scq16, st, true);
         if (r != cudaSuccess) return r;
         Problem q = p;
         q.n = w.fq_cap;
@@ -689,7 +726,9 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
     Lc.fp8 = t.fp8;
     int r2;
     if ((r2 = encode_codes_map(&Lc.mapX, w.Xq, p.n, t.Kw, t.esz, 128))) return r2;
-    if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kw, t.esz, t.bn))) return r2;
+    if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kc, t.esz, t.bn))) return r2;
+    memset(&Lc.mapH, 0, sizeof Lc.mapH);  // the re-score codes' map is encoded by the caller (own slices)
+    if (t.fold && w.Hc && (r2 = encode_h_map(&Lc.mapH, w.Hc, t.kp, t.bn))) return r2;
     memset(&P, 0, sizeof P);
     P.h = w.hq;
     P.sc = w.scq;
@@ -715,11 +754,20 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
     P.split = t.split;
     // truncating FP32 accumulation of K products; the two-part codes sum 3 Kp
     // products and drop lo.lo, |x_lo . c_lo| <= u^2 (1 + u)^2 ||x_hi|| ||c_hi||
-    // (u = 2^-8, split_bf16 keeps |lo| <= u (1 + u) |hi| per element)
-    const double K = t.split ? 3.0 * t.Kp : t.Kp;
-    double gam = K * 0x1p-23 / (1.0 - K * 0x1p-23);
+    // (u = 2^-8, split_bf16 keeps |lo| <= u (1 + u) |hi| per element). Folded
+    // BF16 adds the extra K = 16 slice: products 1 x (-h1, -h2, -h3) of total
+    // magnitude <= (1 + 2^-7) h_j enter the accumulation, and -(h1 + h2 + h3)
+    // differs from the FP32 h_j by <= 2^-27 h_j.
+    const double K = t.split ? 3.0 * t.Kp : (t.fold ? t.Kp + 16.0 : t.Kp);
+    const double gk = K * 0x1p-23 / (1.0 - K * 0x1p-23);
+    double gam = gk;
     if (t.split) gam += 0x1p-16 * (1.0 + 0x1p-8) * (1.0 + 0x1p-8);
     P.gam_tc = (float)(gam * (1.0 + 1e-6));
+    P.fold = t.fold;
+    // score error from h_j: RN to FP32 of the FP64 h (u) and, without folding,
+    // the epilogue's multiply-add (2u); folded: u, the three-part remainder and
+    // the accumulation of the -h_j products
+    P.hcoef = t.fold ? (float)((0x1p-24 + 0x1p-27 + gk * (1.0 + 0x1p-7)) * (1.0 + 1e-6)) : 3.f * 0x1p-24f;
     P.wait_ns = 2000000000ull;
     if (getenv("KM_DEBUG_STALL")) {  // test knob: make a bounded wait expire (50 ms)
       P.debug_stall = 1;
@@ -743,8 +791,10 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
       cfg.hq16 = (float*)(wb + L.hq16);
       cfg.scq16 = (float*)(wb + L.scq16);
       if ((rc = encode_codes_map(&cfg.L16.mapX, w.Xq16, w.fq_cap, cfg.t16.Kw, cfg.t16.esz, 128))) return rc;
-      if ((rc = encode_codes_map(&cfg.L16.mapC, cfg.Cq16, cfg.t16.kp, cfg.t16.Kw, cfg.t16.esz, cfg.t16.bn)))
+      if ((rc = encode_codes_map(&cfg.L16.mapC, cfg.Cq16, cfg.t16.kp, cfg.t16.Kc, cfg.t16.esz, cfg.t16.bn)))
         return rc;
+      cfg.Hc16 = L.hc16 ? (void*)(wb + L.hc16) : nullptr;
+      if (cfg.t16.fold && (rc = encode_h_map(&cfg.L16.mapH, cfg.Hc16, cfg.t16.kp, cfg.t16.bn))) return rc;
       TcParams& Q = cfg.P16;
       Q.h = cfg.hq16;
       Q.sc = cfg.scq16;

@@ -100,6 +100,12 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   return r;
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Per-instance parameters of the tiles a role is working on: the only
 // instance (single launches) or the instance that owns the current flattened
 // tile (batched launches).
@@ -251,15 +257,22 @@ __device__ __forceinline__ int first_chunk(int lab, const Item& it, int bn) {
   return (lab >= 0 && lab < it.k) ? lab / bn : 0;
 }
 
+template <bool NEG>
+__device__ __forceinline__ float score_of(float x) { return NEG ? -x : x; }
+template <bool NEG>
+__device__ __forceinline__ float score_of(uint32_t x) { return NEG ? -__uint_as_float(x) : __uint_as_float(x); }
+
 // Folds a 32-column score block into the row's candidate list: the columns
 // within min(thr, mn + margin) of the block minimum mn (every column that can
-// end within the margin of the row's final minimum), in index order.
-__device__ __forceinline__ void fold_block(Cand (&top)[kT], const float (&s)[32], float mn, int j0, float& thr,
+// end within the margin of the row's final minimum), in index order. NEG: the
+// block holds accumulator bits whose negation is the score (folded BF16).
+template <bool NEG = false, typename T>
+__device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], float mn, int j0, float& thr,
                                            float margin) {
   const float lim = fminf(thr, __fadd_ru(mn, margin));
   unsigned mask = 0;
 #pragma unroll
-  for (int t = 0; t < 32; ++t) mask |= (s[t] <= lim ? 1u : 0u) << t;
+  for (int t = 0; t < 32; ++t) mask |= (score_of<NEG>(s[t]) <= lim ? 1u : 0u) << t;
 #pragma unroll 1
   while (mask) {
     const int t = __ffs(mask) - 1;
@@ -267,7 +280,7 @@ __device__ __forceinline__ void fold_block(Cand (&top)[kT], const float (&s)[32]
     // s[t] through a 5-level select tree
     float x16[16], x8[8], x4[4];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) x16[u] = (t & 1) ? s[2 * u + 1] : s[2 * u];
+    for (int u = 0; u < 16; ++u) x16[u] = (t & 1) ? score_of<NEG>(s[2 * u + 1]) : score_of<NEG>(s[2 * u]);
 #pragma unroll
     for (int u = 0; u < 8; ++u) x8[u] = (t & 2) ? x16[2 * u + 1] : x16[2 * u];
 #pragma unroll
@@ -361,10 +374,48 @@ __device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint
   }
 }
 
-template <int FP8, bool BATCH>
+// Folded BF16 (the accumulators hold acc_j = x.c_j - h_j, the score is -acc_j):
+// the block minimum of the scores is minus the maximum of the accumulators, so
+// a 64-column half costs two trees of 3-input maxima and a vote.
+__device__ __forceinline__ void score_block2_fold(const uint32_t (&v)[32], const uint32_t (&v2)[32], Cand (&top)[kT],
+                                                  int j0, float& thr, float margin) {
+  float m11[11], n11[11];
+#pragma unroll
+  for (int u = 0; u < 10; ++u) {
+    m11[u] = max3f(__uint_as_float(v[3 * u]), __uint_as_float(v[3 * u + 1]), __uint_as_float(v[3 * u + 2]));
+    n11[u] = max3f(__uint_as_float(v2[3 * u]), __uint_as_float(v2[3 * u + 1]), __uint_as_float(v2[3 * u + 2]));
+  }
+  m11[10] = fmaxf(__uint_as_float(v[30]), __uint_as_float(v[31]));
+  n11[10] = fmaxf(__uint_as_float(v2[30]), __uint_as_float(v2[31]));
+  const float mn = -fmaxf(max3f(max3f(m11[0], m11[1], m11[2]), max3f(m11[3], m11[4], m11[5]),
+                                max3f(m11[6], m11[7], m11[8])),
+                          fmaxf(m11[9], m11[10]));
+  const float mn2 = -fmaxf(max3f(max3f(n11[0], n11[1], n11[2]), max3f(n11[3], n11[4], n11[5]),
+                                 max3f(n11[6], n11[7], n11[8])),
+                           fmaxf(n11[9], n11[10]));
+  if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
+    if (mn <= thr) fold_block<true>(top, v, mn, j0, thr, margin);
+    if (mn2 <= thr) fold_block<true>(top, v2, mn2, j0 + 32, thr, margin);
+  }
+}
+
+// The constant A operand of the folded -h_j slice: 128 rows of 16 BF16
+// [1, 1, 1, 0, ...] in the 32-byte swizzled K-major layout (row r at byte
+// 32 r, its 16-byte chunk c at chunk c ^ ((r >> 2) & 1)), one K = 16 MMA step.
+constexpr uint32_t HROWB = 32;  // bytes of one row of the -h_j slice
+__device__ __forceinline__ void fill_ones_block(uint8_t* blk) {
+  for (int e = threadIdx.x; e < BM * 2; e += blockDim.x) {
+    const int r = e >> 1, c = e & 1;
+    const uint4 ones = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);  // BF16 1.0, 1.0, 1.0, 0, 0, ...
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(blk + r * HROWB + ((c ^ ((r >> 2) & 1)) << 4)) = c == 0 ? ones : zero;
+  }
+}
+
+template <int FP8, bool BATCH, bool FOLD>
 __global__ void __launch_bounds__(NTHREADS, 1)
 assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
-                 const TcParams P) {
+                 const __grid_constant__ CUtensorMap mapH, const TcParams P) {
   constexpr int KBE = ROWB / (FP8 ? 1 : 2);  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned by an offset into the shared array (not an integer round trip), so that
@@ -386,13 +437,14 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   const int BN = P.bn, stages = P.stages;
   const uint32_t a_bytes = (uint32_t)P.nkb * BM * ROWB;      // one A slot
   const uint32_t b_kblk = (uint32_t)BN * ROWB;               // one K block of a B stage
-  const uint32_t b_bytes = (uint32_t)P.nkb * b_kblk;         // one B stage
+  const uint32_t b_bytes = (uint32_t)P.nkb * b_kblk + (FOLD ? BN * HROWB : 0);  // one B stage (+ -h_j slice)
   const int nab = P.abufs;                                    // A slots (ring)
   const bool pairs = nab >= 2;                                // two row tiles per B chunk
   uint8_t* A0 = smem;
   uint8_t* B0 = smem + nab * a_bytes;
   const int kpmax = P.nchunks * BN;
-  float* Hs = reinterpret_cast<float*>(B0 + (size_t)stages * b_bytes);  // [kpmax]
+  uint8_t* Aex = B0 + (size_t)stages * b_bytes;                         // folded: the constant ones slice
+  float* Hs = reinterpret_cast<float*>(Aex + (FOLD ? BM * HROWB : 0));  // [kpmax] (unfolded launches)
   const TileRange tr = tile_range<BATCH>(P);
 
   if (threadIdx.x == 0) {
@@ -417,13 +469,18 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   if (!BATCH && warp == 0 && lane == 0) {
     prefetch_tensormap(&mapX);
     prefetch_tensormap(&mapC);
+    if (FOLD) prefetch_tensormap(&mapH);
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base_s, TMEM_COLS);
     tmem_relinquish();
   }
-  if (!BATCH && warp >= 2 && warp < 2 + NEPI) {  // batched launches stage h per instance in the epilogue
+  if (!BATCH && !FOLD && warp >= 2 && warp < 2 + NEPI) {  // batched launches stage h per instance in the epilogue
     for (int j = threadIdx.x - 64; j < kpmax; j += 32 * NEPI) Hs[j] = __ldg(P.h + j);
+  }
+  if (FOLD) {  // generic-proxy writes the MMA (async proxy) reads after the barrier
+    fill_ones_block(Aex);
+    fence_proxy_async_smem();
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -483,9 +540,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (int cc = 0, c = c0; cc < it.nchunks && ok; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
           const int s = sb;
           if (!mbar_wait(&b_empty[s], sph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
-          mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk);
+          mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk + (FOLD ? BN * HROWB : 0u));
           for (int kb = 0; kb < it.nkb; ++kb)
             tma_load_2d(B0 + s * b_bytes + kb * b_kblk, it.mapC, &b_full[s], kb * KBE, c * BN);
+          if (FOLD) tma_load_2d(B0 + s * b_bytes + it.nkb * b_kblk, &mapH, &b_full[s], 0, c * BN);
           last_s = s;
           last_sph = sph;
           if (++sb == stages) {
@@ -562,6 +620,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 }
               }
             }
+            if constexpr (FOLD)  // + [1, 1, 1, 0, ...] . [-h1, -h2, -h3, 0, ...] (one K = 16 step)
+              mma_bf16(d_tmem, sdesc_k_sw32(smem_u32(Aex)), sdesc_k_sw32(b_addr + it.nkb * b_kblk), P.idesc, 1u);
             issued = true;
             mma_commit(&acc_full[buf]);
             ++gu;
@@ -652,7 +712,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       int old = m.old;
       if (old < 0 || old >= it.k) old = -1;
       // per-row error bound and margin
-      const float E = fmaf(3.f * kU, H,
+      const float E = fmaf(BATCH ? 3.f * kU : P.hcoef, H,
                            fmaf(it.gam_tc + 2.f * kU, xs.y * QCmax,
                                 fmaf(xs.z, Cmax, fmaf(xs.w, DCmax, xs.z * DCmax))));
       const float margin = 2.f * E * (1.f + 0x1p-10f);
@@ -684,14 +744,16 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           tmem_ld_32x32b_x32(ta, v);
           tmem_ld_32x32b_x32(ta + 32u, v2);
           tmem_ld_wait();
-          score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
+          if constexpr (FOLD) score_block2_fold(v, v2, top, j0, thr, margin);
+          else score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
           tmem_ld_32x32b_x32(ta + 64u, v);
           tmem_ld_32x32b_x32(ta + 96u, v2);
           tmem_ld_wait();
           tc_fence_before_sync();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
-          score_block2(v, v2, Hs + j0 + 64, wrow, top, j0 + 64, thr, margin);
+          if constexpr (FOLD) score_block2_fold(v, v2, top, j0 + 64, thr, margin);
+          else score_block2(v, v2, Hs + j0 + 64, wrow, top, j0 + 64, thr, margin);
           ++gu;
           c = (c + 1 == it.nchunks) ? 0 : c + 1;
         }
@@ -811,19 +873,20 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 
 }  // namespace
 
-size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs) {
+size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs, int fold) {
   (void)fp8;
-  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * nkb * bn * ROWB + (size_t)kp * 4;
+  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * (nkb * bn * ROWB + fold * bn * HROWB) +
+         (fold ? (size_t)BM * HROWB : (size_t)kp * 4);
 }
 
 // A slots and B stages that fit the shared memory: the most A slots (up to 4,
 // so that the next tile pair's A tiles load while a pair is scored) that leave
 // at least three B stages; failing that two A slots and at least two stages;
 // failing that one slot. Returns the number of B stages (< 2: does not fit).
-int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs) {
-  const size_t budget = 227 * 1024 - 1024, b = (size_t)nkb * bn * ROWB;
+int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs, int fold) {
+  const size_t budget = 227 * 1024 - 1024, b = (size_t)nkb * bn * ROWB + (size_t)fold * bn * HROWB;
   auto stages_for = [&](int na) -> int {
-    const size_t fixed = tc_smem_bytes(nkb, bn, 0, kp, fp8, na);
+    const size_t fixed = tc_smem_bytes(nkb, bn, 0, kp, fp8, na, fold);
     return fixed + 2 * b <= budget ? (int)std::min<size_t>(MAX_STAGES, (budget - fixed) / b) : 0;
   };
   for (int na = MAX_ABUF; na >= 3; --na)
@@ -855,21 +918,24 @@ cudaError_t init_assign_tc() {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, false>, optin);
-  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, false>, optin);
-  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, true>, optin);
-  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, true>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, false, false>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, false, true>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, false, false>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, true, false>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, true, false>, optin);
   return e;
 }
 
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s) {
   const int64_t tiles = (p.n + BM - 1) / BM;
   const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-  const size_t smem = tc_smem_bytes(P.nkb, P.bn, P.stages, P.nchunks * P.bn, L.fp8, P.abufs);
+  const size_t smem = tc_smem_bytes(P.nkb, P.bn, P.stages, P.nchunks * P.bn, L.fp8, P.abufs, P.fold);
   if (L.fp8)
-    assign_tc_kernel<1, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, P);
+    assign_tc_kernel<1, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
+  else if (P.fold)
+    assign_tc_kernel<0, false, true><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
   else
-    assign_tc_kernel<0, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, P);
+    assign_tc_kernel<0, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
   return cudaGetLastError();
 }
 
@@ -910,8 +976,8 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   const size_t smem = tc_smem_bytes(nkb_max, bn, stages, kp_max, fp8, abufs);
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);
-  if (fp8) assign_tc_kernel<1, true><<<grid, NTHREADS, smem, s>>>(dummy, dummy, P);
-  else assign_tc_kernel<0, true><<<grid, NTHREADS, smem, s>>>(dummy, dummy, P);
+  if (fp8) assign_tc_kernel<1, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, P);
+  else assign_tc_kernel<0, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, P);
   return cudaGetLastError();
 }
 

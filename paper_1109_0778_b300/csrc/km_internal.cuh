@@ -85,6 +85,7 @@ struct Work {
   uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
   float* hq;           // [kp] h_j of the quantised path (+inf for padding)
   float* scq;          // [kp] centroid code scales
+  void* Hc;            // [kp][16] BF16 -h_j slices (folded BF16 contraction), null otherwise
   float4* state;       // [n] per-row (best, index, second, second's index) between centroid slabs
   float* state3;       // [fq_cap] third-best score between slabs (re-check passes over gathered rows)
   float4* xs16;        // [n] BF16 statistics of a cold first step of an E4M3 run
@@ -137,6 +138,8 @@ struct TcParams {
   int split;          // two-part BF16 codes: a row holds nkb / 2 blocks of hi, then as many of lo;
                       // x.c = hi.hi + lo.hi + hi.lo (single launches only)
   float gam_tc;       // coefficient of ||x~|| max ||c~|| in the contraction's error bound
+  float hcoef;        // coefficient of max_j h_j in the score's error bound
+  int fold;           // BF16: the accumulators hold x.c_j - h_j (extra K block of -h_j parts); score = -acc
   uint64_t wait_ns;   // bound of every mbarrier wait
   int debug_stall;    // test knob: the epilogue also waits on a barrier nothing arrives on
   unsigned long long* flag_slots;  // slot counter of the flag list
@@ -162,6 +165,7 @@ struct TcParams {
 struct TcLaunch {
   CUtensorMap mapX;   // codes of X: rows n, Kp elements, box (128 B, 128 rows), 128B swizzle
   CUtensorMap mapC;   // codes of C: rows kp, Kp elements, box (128 B, bn rows), 128B swizzle
+  CUtensorMap mapH;   // folded BF16: -h_j slices, rows kp, 16 elements, box (32 B, bn rows), 32B swizzle
   int fp8;
 };
 
@@ -315,12 +319,14 @@ cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, ui
 cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
                                 cudaStream_t s);
 // stats16: the code statistics go to qcmax16 / dcmax16 (BF16 re-check codes of an E4M3 run)
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
+// Hc: BF16 [kp][16] slices of -h_j for the folded BF16 contraction (null: not folded)
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, void* Hc, float* h,
                            float* sc, cudaStream_t s, bool stats16 = false);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
-size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs);
-int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs);
+// fold: BF16 with -h_j folded into the contraction (a 32-byte slice per B stage row, a constant A slice)
+size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs, int fold = 0);
+int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs, int fold = 0);
 
 int num_sms();
 void set_last_error(const char* msg);  // message returned by kmeans_last_error()

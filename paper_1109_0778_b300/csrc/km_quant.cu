@@ -146,15 +146,22 @@ __global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C,
 
 // MODE 0: BF16, 1: E4M3, 2: two-part BF16 (hi in columns [0, Kp), lo in
 // [Kp, 2 Kp); the code norm statistic is ||hi|| + ||lo||).
+// Hc (BF16 "folded" scores; null otherwise): row j of the [kp][16] BF16 array
+// holds -h_j as three BF16 parts (-h1, -h2, -h3; h1 = RN(h), h2 = RN(h - h1),
+// h3 = RN(h - h1 - h2), each remainder exact by Sterbenz's lemma,
+// |h - h1 - h2 - h3| <= 2^-27 h) and zeros, so that the contraction against a
+// slice of ones yields x.c_j - h_j in the accumulator; a padding row holds
+// -inf there (score +inf).
 template <int MODE>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
-               float* __restrict__ hq, float* __restrict__ scq, int32_t* __restrict__ counts, Ctl* ctl,
-               int stats16) {
+               __nv_bfloat16* __restrict__ Hc, float* __restrict__ hq, float* __restrict__ scq,
+               int32_t* __restrict__ counts, Ctl* ctl, int stats16) {
   constexpr int FP8 = MODE == 1;
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
   if (halted(ctl)) return;
+  const bool fold = MODE == 0 && Hc != nullptr;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -162,6 +169,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     uint8_t* row = Cq + (int64_t)j * W * Kp * ESZ;
     if (j >= k) {  // padding centroid: zero codes, score +inf
       for (int t = lane; t < W * Kp * ESZ; t += 32) row[t] = 0;
+      if (fold && lane < 16) Hc[(int64_t)j * 16 + lane] = __float2bfloat16_rn(lane == 0 ? -INFINITY : 0.f);
       if (lane == 0) {
         hq[j] = INFINITY;
         scq[j] = 1.f;
@@ -195,6 +203,17 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     sqq = warp_sum(sqq);
     if (MODE == 2) sll = warp_sum(sll);
     sdd = warp_sum(sdd);
+    if (fold) {  // -h_j as three BF16 parts in the extra block (h computed by every lane alike)
+      const float h = __double2float_rn(0.5 * s2);
+      const __nv_bfloat16 h1 = __float2bfloat16_rn(h);
+      const float r1 = h - __bfloat162float(h1);
+      const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(h2);
+      const __nv_bfloat16 h3 = __float2bfloat16_rn(r2);
+      if (lane < 16)
+        Hc[(int64_t)j * 16 + lane] =
+            lane == 0 ? __hneg(h1) : lane == 1 ? __hneg(h2) : lane == 2 ? __hneg(h3) : __float2bfloat16_rn(0.f);
+    }
     if (lane == 0) {
       const float h = __double2float_rn(0.5 * s2);
       const float cn = __double2float_ru(sqrt(s2) * (1.0 + 1e-13));
@@ -234,22 +253,23 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, float* h,
+cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, void* Hc, float* h,
                            float* sc, cudaStream_t s, bool stats16) {
+  __nv_bfloat16* hc = mode == 0 ? reinterpret_cast<__nv_bfloat16*>(Hc) : nullptr;
   int32_t* counts = stats16 ? nullptr : p.counts;  // the re-check codes leave the counts alone
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (mode == 2) {
-    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
   } else if (mode == 1) {
     const int64_t kd = (int64_t)p.k * p.d;
     int mb = (int)((kd + 255) / 256);
     if (mb > num_sms() * 4) mb = num_sms() * 4;
     camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, w.ctl);
-    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
   } else {
-    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
   }
   return cudaGetLastError();
 }

@@ -182,6 +182,20 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// As sdesc_k_sw128 for a K-major block of 32-byte rows with the 32-byte swizzle
+// (16-byte chunk index XOR bit 2 of the row inside each 256-byte group of 8
+// rows): stride byte offset 256, layout SWIZZLE_32B (6 in bits 61-63). One
+// BF16 MMA step (K = 16) spans exactly one such row.
+__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(256u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)6u << 61;
+  return d;
+}
+
 // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A / B formats
 // (bits 7-9 / 10-12), both operands K-major (bits 15, 16 = 0), N >> 3 in bits
 // 17-22, M >> 4 in bits 24-28. Formats: kind::f16 BF16 = 1; kind::f8f6f4 E4M3 = 0.

@@ -175,9 +175,11 @@ def test_near_margin_gaps_bf16_parity(km, ref):
     """Points whose exact score gap to the second centroid is 1.3-2 x the BF16 margin.
 
     Data and centroids are BF16 values, so the codes are exact and the margin reduces to
-    2 (3u H + (gamma'_K + 2u) ||x|| C~max) (1 + 2^-10) (u = 2^-24; the library's formula with
-    zero quantisation residuals). Such points are not flagged, their argmin comes from the
-    tensor-core scores alone, and it must be the exact one."""
+    2 (c_h H + (gamma'_K' + 2u) ||x|| C~max) (1 + 2^-10) with u = 2^-24, K' = 128 + 16 (the
+    contraction also accumulates the -h_j slice: 1 x (-h1, -h2, -h3)) and
+    c_h = u + 2^-27 + gamma'_K' (1 + 2^-7) (the library's formula for BF16 with -h_j folded into
+    the contraction, zero quantisation residuals). Such points are not flagged, their argmin
+    comes from the tensor-core scores alone, and it must be the exact one."""
     rng = np.random.default_rng(2024)
     d, pairs, per = 128, 48, 64
     u = 2.0 ** -24
@@ -191,7 +193,8 @@ def test_near_margin_gaps_bf16_parity(km, ref):
     C[0::2], C[1::2] = ya, yb
     h = 0.5 * np.sum(C * C, axis=1)
     H, Cmax = h.max(), np.sqrt(np.sum(C * C, axis=1)).max()
-    gam = gamma_k(128)
+    gam = gamma_k(128 + 16)
+    ch = u + 2.0 ** -27 + gam * (1 + 2.0 ** -7)
     pts, wanted = [], []
     for p in range(pairs):
         ca, cb = C[2 * p], C[2 * p + 1]
@@ -201,11 +204,11 @@ def test_near_margin_gaps_bf16_parity(km, ref):
             x = bf((ca + cb) / 2 + rng.normal(0, 1.0, d))
             sign = 1.0 if q % 2 == 0 else -1.0
             for _ in range(4):  # move coordinate t so that the gap hits the target, then re-round
-                margin = 2 * (3 * u * H + (gam + 2 * u) * np.linalg.norm(x) * Cmax) * (1 + 2.0 ** -10)
+                margin = 2 * (ch * H + (gam + 2 * u) * np.linalg.norm(x) * Cmax) * (1 + 2.0 ** -10)
                 target = sign * rng.uniform(1.45, 1.85) * margin
                 g = 0.5 * (cb @ cb - ca @ ca) - x @ w  # s_b - s_a
                 x[t] = bf(x[t] + (g - target) / w[t])
-            margin = 2 * (3 * u * H + (gam + 2 * u) * np.linalg.norm(x) * Cmax) * (1 + 2.0 ** -10)
+            margin = 2 * (ch * H + (gam + 2 * u) * np.linalg.norm(x) * Cmax) * (1 + 2.0 ** -10)
             g = 0.5 * (cb @ cb - ca @ ca) - x @ w
             if 1.3 * margin <= abs(g) <= 2.0 * margin:
                 pts.append(x)
