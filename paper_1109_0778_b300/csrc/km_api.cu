@@ -164,10 +164,12 @@ size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
 // Shape of the tensor-core path for (d, k, precision).
 // Kp: d padded to whole 128-byte K blocks; Kw: elements of one point code row
 // (Kp, or 2 Kp for the two-part BF16 codes); nkb: K blocks of one point code
-// row. fold (BF16 with 128-centroid chunks): every centroid also has a 16-element
-// BF16 slice holding -h_j (Hc, staged with the 32-byte swizzle), contracted
-// with a slice of ones, so the accumulators hold x.c_j - h_j and the epilogue
-// takes no h_j and no multiply-add. Kc: elements of one centroid code row.
+// row. fold (128-centroid chunks): every centroid also has a 16-element BF16
+// slice holding -h_j (E4M3: -h_j / s_c; Hc, staged with the 32-byte swizzle),
+// contracted with a slice of ones (E4M3: each point row's [1/s_x, ...] slice,
+// Xh) by one BF16 MMA step on the same accumulator, so the accumulators hold
+// (x.c_j - h_j) / (s_x s_c) and the epilogue takes no h_j and no multiply-add.
+// Kc: elements of one centroid code row.
 struct TcShape {
   int fp8, split, esz, Kp, Kw, nkb, bn, kp, nchunks, stages, abufs, fold, Kc;
   int qmode() const { return split ? 2 : fp8 ? 1 : 0; }  // quantisation stage mode
@@ -185,10 +187,10 @@ TcShape tc_shape(int precision, int d, int k) {
   t.kp = (k + 127) / 128 * 128;  // padded to whole chunks of any width
   t.Kc = t.Kw;
   t.fold = 0;
-  if (!t.fp8 && !t.split && t.nkb <= 2) {  // BF16, 128-centroid chunks, -h_j folded in when it fits
+  if (!t.split && t.nkb <= 2) {  // BF16 / E4M3, 128-centroid chunks, -h_j folded in when it fits
     t.bn = 128;
     t.nchunks = t.kp / 128;
-    t.stages = tc_pick_buffers(t.nkb, 128, t.kp, 0, &t.abufs, 1);
+    t.stages = tc_pick_buffers(t.nkb, 128, t.kp, t.fp8, &t.abufs, 1);
     if (t.stages >= 2) {
       t.fold = 1;
       return t;
@@ -216,7 +218,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, pcounts, xmax, facc, oacc, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -265,6 +267,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
     // -h_j slices of the folded BF16 contraction (the main shape, or the BF16 first step of a cold call)
     const bool hfold = t.fold || (cold && tc_shape(KM_BF16, d, k).fold);
     L.hc = hfold ? take(32 * (size_t)std::max(t.kp, tc_shape(KM_BF16, d, k).kp)) : 0;
+    L.xh = (t.fp8 && t.fold) ? take(32 * (size_t)n) : 0;  // the points' 1/s_x slices (folded E4M3)
     L.hq = take(4 * (size_t)t.kp);
     L.scq = take(4 * (size_t)t.kp);
     L.xss = take(16 * (size_t)n);
@@ -291,7 +294,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
       L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.hc16 = 0;
     }
   } else {
-    L.hc = L.hc16 = 0;
+    L.hc = L.hc16 = L.xh = 0;
     L.Kp16 = 0;
     L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
@@ -376,6 +379,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
   w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
   w.Hc = L.hc ? (void*)(b + L.hc) : nullptr;
+  w.Xh = L.xh ? (void*)(b + L.xh) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
   w.state3 = L.state3 ? (float*)(b + L.state3) : nullptr;
   w.xs16 = L.xs16 ? (float4*)(b + L.xs16) : nullptr;
@@ -728,7 +732,9 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
     if ((r2 = encode_codes_map(&Lc.mapX, w.Xq, p.n, t.Kw, t.esz, 128))) return r2;
     if ((r2 = encode_codes_map(&Lc.mapC, w.Cq, t.kp, t.Kc, t.esz, t.bn))) return r2;
     memset(&Lc.mapH, 0, sizeof Lc.mapH);  // the re-score codes' map is encoded by the caller (own slices)
+    memset(&Lc.mapXh, 0, sizeof Lc.mapXh);
     if (t.fold && w.Hc && (r2 = encode_h_map(&Lc.mapH, w.Hc, t.kp, t.bn))) return r2;
+    if (t.fold && t.fp8 && (r2 = encode_h_map(&Lc.mapXh, w.Xh, p.n, 128))) return r2;
     memset(&P, 0, sizeof P);
     P.h = w.hq;
     P.sc = w.scq;
@@ -764,6 +770,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
     if (t.split) gam += 0x1p-16 * (1.0 + 0x1p-8) * (1.0 + 0x1p-8);
     P.gam_tc = (float)(gam * (1.0 + 1e-6));
     P.fold = t.fold;
+    P.idesc16 = tc::idesc_f32acc(1u, 128, (uint32_t)t.bn);  // the folded -h_j slice is a BF16 step
     // score error from h_j: RN to FP32 of the FP64 h (u) and, without folding,
     // the epilogue's multiply-add (2u); folded: u, the three-part remainder and
     // the accumulation of the -h_j products

@@ -415,7 +415,8 @@ __device__ __forceinline__ void fill_ones_block(uint8_t* blk) {
 template <int FP8, bool BATCH, bool FOLD>
 __global__ void __launch_bounds__(NTHREADS, 1)
 assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapC,
-                 const __grid_constant__ CUtensorMap mapH, const TcParams P) {
+                 const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapXh,
+                 const TcParams P) {
   constexpr int KBE = ROWB / (FP8 ? 1 : 2);  // elements per 128-byte K block
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned by an offset into the shared array (not an integer round trip), so that
@@ -435,7 +436,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // buffer sizes follow the launch maxima (P.nkb, P.nchunks); a tile uses its own nkb, nchunks
   const int BN = P.bn, stages = P.stages;
-  const uint32_t a_bytes = (uint32_t)P.nkb * BM * ROWB;      // one A slot
+  constexpr bool AXS = FP8 && FOLD;                          // A slots carry each row's 1/s_x slice
+  const uint32_t a_bytes = (uint32_t)P.nkb * BM * ROWB + (AXS ? BM * HROWB : 0);  // one A slot
   const uint32_t b_kblk = (uint32_t)BN * ROWB;               // one K block of a B stage
   const uint32_t b_bytes = (uint32_t)P.nkb * b_kblk + (FOLD ? BN * HROWB : 0);  // one B stage (+ -h_j slice)
   const int nab = P.abufs;                                    // A slots (ring)
@@ -443,8 +445,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   uint8_t* A0 = smem;
   uint8_t* B0 = smem + nab * a_bytes;
   const int kpmax = P.nchunks * BN;
-  uint8_t* Aex = B0 + (size_t)stages * b_bytes;                         // folded: the constant ones slice
-  float* Hs = reinterpret_cast<float*>(Aex + (FOLD ? BM * HROWB : 0));  // [kpmax] (unfolded launches)
+  uint8_t* Aex = B0 + (size_t)stages * b_bytes;                         // folded BF16: the constant ones slice
+  float* Hs = reinterpret_cast<float*>(Aex + (FOLD && !FP8 ? BM * HROWB : 0));  // [kpmax] (unfolded launches)
   const TileRange tr = tile_range<BATCH>(P);
 
   if (threadIdx.x == 0) {
@@ -470,6 +472,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     prefetch_tensormap(&mapX);
     prefetch_tensormap(&mapC);
     if (FOLD) prefetch_tensormap(&mapH);
+    if (AXS) prefetch_tensormap(&mapXh);
   }
   if (warp == 1) {
     tmem_alloc(&tmem_base_s, TMEM_COLS);
@@ -478,7 +481,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
   if (!BATCH && !FOLD && warp >= 2 && warp < 2 + NEPI) {  // batched launches stage h per instance in the epilogue
     for (int j = threadIdx.x - 64; j < kpmax; j += 32 * NEPI) Hs[j] = __ldg(P.h + j);
   }
-  if (FOLD) {  // generic-proxy writes the MMA (async proxy) reads after the barrier
+  if (FOLD && !FP8) {  // generic-proxy writes the MMA (async proxy) reads after the barrier
     fill_ones_block(Aex);
     fence_proxy_async_smem();
   }
@@ -526,10 +529,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         }
         for (int u = 0; u < ntp && ok; ++u, ++lt) {
           if (!mbar_wait(&a_empty[ab], aph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
-          mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB);
+          mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB + (AXS ? BM * HROWB : 0u));
           const int row0 = (int)((u ? gb - it.tile0 : tile0) * BM);
           for (int kb = 0; kb < it.nkb; ++kb)
             tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, row0);
+          if (AXS) tma_load_2d(A0 + ab * a_bytes + it.nkb * (BM * ROWB), &mapXh, &a_full[ab], 0, row0);
           last_a = ab;
           last_aph = aph;
           if (++ab == nab) {
@@ -620,8 +624,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
                 }
               }
             }
-            if constexpr (FOLD)  // + [1, 1, 1, 0, ...] . [-h1, -h2, -h3, 0, ...] (one K = 16 step)
-              mma_bf16(d_tmem, sdesc_k_sw32(smem_u32(Aex)), sdesc_k_sw32(b_addr + it.nkb * b_kblk), P.idesc, 1u);
+            if constexpr (FOLD) {  // + [r, r, r, 0, ...] . [-h1, -h2, -h3, 0, ...]: one BF16 K = 16 step (r = 1, or
+                                   // 1 / s_x of the row for E4M3, whose accumulator it adds to)
+              const uint32_t ax = AXS ? a_addr + (uint32_t)it.nkb * (BM * ROWB) : smem_u32(Aex);
+              mma_bf16(d_tmem, sdesc_k_sw32(ax), sdesc_k_sw32(b_addr + it.nkb * b_kblk), AXS ? P.idesc16 : P.idesc, 1u);
+            }
             issued = true;
             mma_commit(&acc_full[buf]);
             ++gu;
@@ -715,7 +722,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const float E = fmaf(BATCH ? 3.f * kU : P.hcoef, H,
                            fmaf(it.gam_tc + 2.f * kU, xs.y * QCmax,
                                 fmaf(xs.z, Cmax, fmaf(xs.w, DCmax, xs.z * DCmax))));
-      const float margin = 2.f * E * (1.f + 0x1p-10f);
+      // folded E4M3 launches compare accumulators (scores / (s_x s_c), an exact power-of-two factor)
+      const float margin = 2.f * E * (1.f + 0x1p-10f) * (FP8 && FOLD ? __frcp_rn(xs.x * csc) : 1.f);
       float thr = FLT_MAX;  // finite: padding columns (score +inf) never become candidates
       if (ok && P.debug_stall && !__all_sync(0xffffffffu, mbar_wait(&never_bar, 0, &abort_s, P.wait_ns))) ok = false;
 
@@ -874,9 +882,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
 }  // namespace
 
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs, int fold) {
-  (void)fp8;
-  return 1024 + (size_t)abufs * nkb * BM * ROWB + (size_t)stages * (nkb * bn * ROWB + fold * bn * HROWB) +
-         (fold ? (size_t)BM * HROWB : (size_t)kp * 4);
+  const size_t a_slot = (size_t)nkb * BM * ROWB + (fp8 && fold ? (size_t)BM * HROWB : 0);
+  return 1024 + (size_t)abufs * a_slot + (size_t)stages * (nkb * bn * ROWB + fold * bn * HROWB) +
+         (fold ? (fp8 ? 0 : (size_t)BM * HROWB) : (size_t)kp * 4);
 }
 
 // A slots and B stages that fit the shared memory: the most A slots (up to 4,
@@ -921,6 +929,7 @@ cudaError_t init_assign_tc() {
   if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, false, false>, optin);
   if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, false, true>, optin);
   if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, false, false>, optin);
+  if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, false, true>, optin);
   if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<0, true, false>, optin);
   if (e == cudaSuccess) e = raise_smem(assign_tc_kernel<1, true, false>, optin);
   return e;
@@ -930,12 +939,14 @@ cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams
   const int64_t tiles = (p.n + BM - 1) / BM;
   const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
   const size_t smem = tc_smem_bytes(P.nkb, P.bn, P.stages, P.nchunks * P.bn, L.fp8, P.abufs, P.fold);
-  if (L.fp8)
-    assign_tc_kernel<1, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
+  if (L.fp8 && P.fold)
+    assign_tc_kernel<1, false, true><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, L.mapXh, P);
+  else if (L.fp8)
+    assign_tc_kernel<1, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, L.mapXh, P);
   else if (P.fold)
-    assign_tc_kernel<0, false, true><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
+    assign_tc_kernel<0, false, true><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, L.mapXh, P);
   else
-    assign_tc_kernel<0, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, P);
+    assign_tc_kernel<0, false, false><<<grid, NTHREADS, smem, s>>>(L.mapX, L.mapC, L.mapH, L.mapXh, P);
   return cudaGetLastError();
 }
 
@@ -976,8 +987,8 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   const size_t smem = tc_smem_bytes(nkb_max, bn, stages, kp_max, fp8, abufs);
   CUtensorMap dummy;
   memset(&dummy, 0, sizeof dummy);
-  if (fp8) assign_tc_kernel<1, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, P);
-  else assign_tc_kernel<0, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, P);
+  if (fp8) assign_tc_kernel<1, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, dummy, P);
+  else assign_tc_kernel<0, true, false><<<grid, NTHREADS, smem, s>>>(dummy, dummy, dummy, dummy, P);
   return cudaGetLastError();
 }
 

@@ -85,7 +85,9 @@ struct Work {
   uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
   float* hq;           // [kp] h_j of the quantised path (+inf for padding)
   float* scq;          // [kp] centroid code scales
-  void* Hc;            // [kp][16] BF16 -h_j slices (folded BF16 contraction), null otherwise
+  void* Hc;            // [kp][16] BF16 -h_j slices (folded contraction), null otherwise
+  void* Xh;            // [n][16] BF16 [1/s_i, 1/s_i, 1/s_i, 0...] slices of a folded E4M3 contraction, in the
+                       // codes' row order (null otherwise)
   float4* state;       // [n] per-row (best, index, second, second's index) between centroid slabs
   float* state3;       // [fq_cap] third-best score between slabs (re-check passes over gathered rows)
   float4* xs16;        // [n] BF16 statistics of a cold first step of an E4M3 run
@@ -139,7 +141,9 @@ struct TcParams {
                       // x.c = hi.hi + lo.hi + hi.lo (single launches only)
   float gam_tc;       // coefficient of ||x~|| max ||c~|| in the contraction's error bound
   float hcoef;        // coefficient of max_j h_j in the score's error bound
-  int fold;           // BF16: the accumulators hold x.c_j - h_j (extra K block of -h_j parts); score = -acc
+  int fold;           // the accumulators hold (x.c_j - h_j) / (s_x s_c) (a K = 16 BF16 slice of -h_j parts);
+                      // score = -(s_x s_c) acc
+  uint32_t idesc16;   // instruction descriptor of that BF16 slice (E4M3 launches: a BF16 MMA on the same accumulator)
   uint64_t wait_ns;   // bound of every mbarrier wait
   int debug_stall;    // test knob: the epilogue also waits on a barrier nothing arrives on
   unsigned long long* flag_slots;  // slot counter of the flag list
@@ -165,7 +169,8 @@ struct TcParams {
 struct TcLaunch {
   CUtensorMap mapX;   // codes of X: rows n, Kp elements, box (128 B, 128 rows), 128B swizzle
   CUtensorMap mapC;   // codes of C: rows kp, Kp elements, box (128 B, bn rows), 128B swizzle
-  CUtensorMap mapH;   // folded BF16: -h_j slices, rows kp, 16 elements, box (32 B, bn rows), 32B swizzle
+  CUtensorMap mapH;   // folded: -h_j slices, rows kp, 16 elements, box (32 B, bn rows), 32B swizzle
+  CUtensorMap mapXh;  // folded E4M3: 1/s_i slices of the point rows, box (32 B, 128 rows), 32B swizzle
   int fp8;
 };
 
@@ -324,7 +329,8 @@ cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, in
                            float* sc, cudaStream_t s, bool stats16 = false);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
-// fold: BF16 with -h_j folded into the contraction (a 32-byte slice per B stage row, a constant A slice)
+// fold: -h_j folded into the contraction (a 32-byte slice per B stage row; A: a constant slice (BF16) or a
+// 32-byte slice per A slot row (E4M3))
 size_t tc_smem_bytes(int nkb, int bn, int stages, int kp, int fp8, int abufs, int fold = 0);
 int tc_pick_buffers(int nkb, int bn, int kp, int fp8, int* abufs, int fold = 0);
 

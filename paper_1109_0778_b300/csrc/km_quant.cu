@@ -23,10 +23,12 @@ namespace km {
 
 namespace {
 
+// Xh (E4M3 with -h_j folded into the contraction; null otherwise): row i's
+// [1/s_i, 1/s_i, 1/s_i, 0, ...] slice (store_row_slice).
 template <int FP8>
 __global__ void __launch_bounds__(256)
 quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
-               float4* __restrict__ xs, Ctl* ctl) {
+               float4* __restrict__ xs, uint4* __restrict__ Xh, Ctl* ctl) {
   constexpr int ESZ = FP8 ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -54,6 +56,7 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
     if (lane == 0) {
       if (!isfinite(sxx) || !isfinite(sqq)) ctl->nonfinite = 1;
       xs[i] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+      if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
     }
   }
 }
@@ -161,7 +164,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
   if (halted(ctl)) return;
-  const bool fold = MODE == 0 && Hc != nullptr;
+  const bool fold = MODE != 2 && Hc != nullptr;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -203,8 +206,8 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     sqq = warp_sum(sqq);
     if (MODE == 2) sll = warp_sum(sll);
     sdd = warp_sum(sdd);
-    if (fold) {  // -h_j as three BF16 parts in the extra block (h computed by every lane alike)
-      const float h = __double2float_rn(0.5 * s2);
+    if (fold) {  // -h_j (E4M3: -h_j / s_c, exact) as three BF16 parts (every lane computes h alike)
+      const float h = __double2float_rn(0.5 * s2) * inv;
       const __nv_bfloat16 h1 = __float2bfloat16_rn(h);
       const float r1 = h - __bfloat162float(h1);
       const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
@@ -238,9 +241,10 @@ cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, ui
   int64_t blocks = (p.n + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
+  uint4* xh = reinterpret_cast<uint4*>(w.Xh);
   if (mode == 2) quant_x_split_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
-  else if (mode == 1) quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
-  else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
+  else if (mode == 1) quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, xh, w.ctl);
+  else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, nullptr, w.ctl);
   return cudaGetLastError();
 }
 
@@ -255,7 +259,7 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
 
 cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, void* Hc, float* h,
                            float* sc, cudaStream_t s, bool stats16) {
-  __nv_bfloat16* hc = mode == 0 ? reinterpret_cast<__nv_bfloat16*>(Hc) : nullptr;
+  __nv_bfloat16* hc = mode != 2 ? reinterpret_cast<__nv_bfloat16*>(Hc) : nullptr;
   int32_t* counts = stats16 ? nullptr : p.counts;  // the re-check codes leave the counts alone
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;

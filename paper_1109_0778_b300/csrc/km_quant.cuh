@@ -57,6 +57,14 @@ static __device__ __forceinline__ float split_bf16(float v, __nv_bfloat16* hi_ds
   return r1 - lo;
 }
 
+// The per-row slice of a folded E4M3 contraction: BF16 [1/s, 1/s, 1/s, 0 x 13]
+// (1/s exact: s is a power of two), two 16-byte words of a 32-byte row.
+static __device__ __forceinline__ void store_row_slice(uint4* dst, float s) {
+  const uint32_t b = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(__frcp_rn(s)));
+  dst[0] = make_uint4(b | (b << 16), b, 0u, 0u);
+  dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 static __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

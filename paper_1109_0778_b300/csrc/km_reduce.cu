@@ -240,7 +240,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
               const int32_t* __restrict__ perm, const int32_t* __restrict__ slab, double* __restrict__ sums64,
               Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs, int Kp,
               float4* __restrict__ xs_sorted, int k, unsigned long long* __restrict__ facc,
-              unsigned long long* __restrict__ oacc, const unsigned int* __restrict__ xmax) {
+              unsigned long long* __restrict__ oacc, const unsigned int* __restrict__ xmax, uint4* __restrict__ Xh) {
   constexpr int RB = seg_rows<V>();  // rows per batch (lane r < RB holds row r's indices)
   constexpr int RS = 32 * V;         // shared-memory floats per row
   extern __shared__ __align__(16) float seg_smem[];
@@ -306,7 +306,10 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     __syncwarp();
     const int rows = (int)min((int64_t)RB, P1 - (P0 + b * RB));
     // lane r holds row r's statistics: one coalesced store of the batch's sorted statistics
-    if (QM != 0 && lane < rows) xs_sorted[P0 + b * RB + lane] = xs_c;
+    if (QM != 0 && lane < rows) {
+      xs_sorted[P0 + b * RB + lane] = xs_c;
+      if (QM == 2 && Xh) store_row_slice(Xh + 2 * (P0 + b * RB + lane), xs_c.x);  // folded E4M3: 1/s slice
+    }
     // rows that start a cluster run (lane r holds row r's label), found once per batch
     const int jprev = __shfl_up_sync(0xffffffffu, j_c, 1);
     const unsigned starts = __ballot_sync(0xffffffffu, lane < rows && j_c != (lane == 0 ? cur : jprev));
@@ -654,7 +657,8 @@ template <int V, int QM, bool DET>
 void seg_launch(int blocks, const Problem& p, const Work& w, int Kp, cudaStream_t s) {
   segsum_kernel<V, QM, DET><<<blocks, 256, seg_smem_bytes<V>(), s>>>(
       p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, w.sums64, w.ctl, QM ? w.Xq : nullptr, QM ? w.xs : nullptr,
-      QM ? Kp : 0, QM ? w.xs_sorted : nullptr, p.k, w.facc, w.oacc, w.xmax);
+      QM ? Kp : 0, QM ? w.xs_sorted : nullptr, p.k, w.facc, w.oacc, w.xmax,
+      QM == 2 ? reinterpret_cast<uint4*>(w.Xh) : nullptr);
 }
 
 template <int V, bool DET>
