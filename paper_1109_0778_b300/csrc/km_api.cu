@@ -832,7 +832,13 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
   KM_TRACE("prologue copies queued (reuse=%d det=%d partial=%d)\n", (int)reuse, det, part ? 1 : 0);
-  if (reuse) {
+  // small FP32 problems: the whole call is one single-CTA kernel (km_small.cu); profiled, deterministic
+  // and partial calls take the staged path, which records their stage events and partials
+  const bool small = o.precision == KM_FP32 && !profile && !det && !part && !debug_sync() &&
+                     small_path_fits(p.n, p.d, p.k);
+  if (small) {
+    // the kernel computes the point norms it needs itself
+  } else if (reuse) {
     // codes, row statistics, norms, sorted order and max ||x|| are those the previous call left
   } else if (o.precision != KM_FP32 && cfg.cold) {
     KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
@@ -849,7 +855,10 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   }
   if (profile) KM_CUDA(cudaEventRecord(c->prof[1], s));
   int launches = 0;
-  if (graph && iters > 1 && !debug_sync()) {
+  if (small) {
+    KM_CUDA(launch_small_run(p, w, iters, tol, step_first(cfg, 0), o.recheck, s));
+    launches = 1;
+  } else if (graph && iters > 1 && !debug_sync()) {
     GraphKey key;
     memset(&key, 0, sizeof key);
     key.X = p.X; key.C = p.C; key.assign = p.assign; key.sums = p.sums; key.counts = p.counts;

@@ -312,6 +312,10 @@ cudaError_t init_segsum();
 // det: exact fixed-point sums and objective into w.facc / w.oacc (grid of *w.xmax)
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0, int det = 0);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s, int det = 0);
+// Small FP32 problems: every step of a call in one single-CTA launch (km_small.cu)
+bool small_path_fits(int64_t n, int d, int k);
+cudaError_t launch_small_run(const Problem& p, const Work& w, int iters, double tol, int first, int recheck,
+                             cudaStream_t s);
 // max_i ||x_i|| bound into *w.xmax from per-point bounds (FP32 norms, or the .w of quantised row stats)
 cudaError_t launch_xmax(const float* xnorm, const float4* xs, int64_t n, const Work& w, cudaStream_t s);
 // Sharded step: the shard's partials (sums64 / facc, counts, objective, n_changed) into part

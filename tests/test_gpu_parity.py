@@ -432,3 +432,31 @@ def test_profiled_runs(km, ref, precision):
     C = C0.clone()
     r = ref.run(X, X[:50].astype(np.float64), 5)
     assert (out.assign.cpu().numpy() != r["assign"]).sum() <= 3
+
+
+@pytest.mark.parametrize("n,d,k", [(10000, 16, 8), (16384, 16, 32), (2048, 64, 64), (777, 3, 5), (4096, 33, 40),
+                                   (5000, 8, 1)])
+def test_small_problems_single_launch(km, ref, n, d, k):
+    """Small FP32 problems (n <= 16384, k <= 64, d <= 64, n k d <= 2^23; the cases include both limits)
+    run every step of a call in one kernel launch; each step keeps parity with the oracle (teacher
+    forcing) and the result equals the staged path's (opts.profile forces it)."""
+    X = synth.mixture(4400 + n + d + k, n, d, max(k, 2), 6.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    Cd = torch.from_numpy(X[:k].copy()).to(DEV)
+    a, s, c = km.alloc_outputs(Xd, Cd)
+    for it in range(3):
+        C_in = Cd.cpu().numpy().astype(np.float64)
+        out = km.step(Xd, Cd, a, s, c, warm_start=it > 0)
+        ag = out.assign.cpu().numpy()
+        parity.check_assign(ref, X, C_in, ag)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), out.sums.cpu().numpy(), out.counts.cpu().numpy())
+        parity.check_objective(ref, X, C_in, ag, out.stats["objective"])
+    C1 = torch.from_numpy(X[:k].copy()).to(DEV)
+    o1 = km.run(Xd, C1, 6)
+    assert o1.stats["launches"] == 1, o1.stats
+    C2 = torch.from_numpy(X[:k].copy()).to(DEV)
+    o2 = km.run(Xd, C2, 6, profile=True)
+    assert o2.stats["launches"] > 6
+    assert (o1.assign != o2.assign).sum().item() <= 2
+    assert torch.allclose(C1, C2, rtol=1e-6, atol=1e-6)
+    assert abs(o1.stats["objective"] - o2.stats["objective"]) <= 1e-6 * abs(o2.stats["objective"])
