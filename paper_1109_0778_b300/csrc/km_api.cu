@@ -218,7 +218,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, small, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -323,6 +323,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
   L.queued = take(8 * (size_t)iters);
   L.facc = det ? take(3 * 8 * kd) : 0;
   L.oacc = det ? take(3 * 8) : 0;
+  L.small = (precision == KM_FP32 && small_path_fits(n, d, k)) ? take(small_scratch_bytes(n, d, k)) : 0;
   L.total = o;
   return L;
 }
@@ -373,6 +374,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.xmax = (unsigned int*)(b + L.xmax);
   w.facc = L.facc ? (unsigned long long*)(b + L.facc) : nullptr;
   w.oacc = L.oacc ? (unsigned long long*)(b + L.oacc) : nullptr;
+  w.small = L.small ? (void*)(b + L.small) : nullptr;
   w.Xq = L.Xq ? (uint8_t*)(b + L.Xq) : nullptr;
   w.xs = L.xs ? (float4*)(b + L.xs) : nullptr;
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
@@ -832,9 +834,9 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
   KM_TRACE("prologue copies queued (reuse=%d det=%d partial=%d)\n", (int)reuse, det, part ? 1 : 0);
-  // small FP32 problems: the whole call is one single-CTA kernel (km_small.cu); profiled, deterministic
+  // small FP32 problems: the whole call is one cooperative kernel (km_small.cu); profiled, deterministic
   // and partial calls take the staged path, which records their stage events and partials
-  const bool small = o.precision == KM_FP32 && !profile && !det && !part && !debug_sync() &&
+  const bool small = o.precision == KM_FP32 && !profile && !det && !part && !debug_sync() && w.small &&
                      small_path_fits(p.n, p.d, p.k);
   if (small) {
     // the kernel computes the point norms it needs itself

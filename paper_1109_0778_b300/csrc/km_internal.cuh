@@ -106,6 +106,7 @@ struct Work {
   uint8_t* Xq16;       // [fq_cap][Kp16] BF16 codes of the gathered rows (null: tiled FP32 pass)
   float4* xs16q;       // [fq_cap] their row statistics
   int Kp16;            // BF16 code row width
+  void* small;         // state of the one-launch small-problem path (null when it does not apply)
 };
 
 // Row map of an FP32 assignment pass over gathered rows: row r of X is point
@@ -312,8 +313,9 @@ cudaError_t init_segsum();
 // det: exact fixed-point sums and objective into w.facc / w.oacc (grid of *w.xmax)
 cudaError_t launch_segsum(const Problem& p, const Work& w, cudaStream_t s, int qmode = 0, int Kp = 0, int det = 0);
 cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol, cudaStream_t s, int det = 0);
-// Small FP32 problems: every step of a call in one single-CTA launch (km_small.cu)
+// Small FP32 problems: every step of a call in one cooperative launch (km_small.cu)
 bool small_path_fits(int64_t n, int d, int k);
+size_t small_scratch_bytes(int64_t n, int d, int k);  // bytes of Work::small
 cudaError_t launch_small_run(const Problem& p, const Work& w, int iters, double tol, int first, int recheck,
                              cudaStream_t s);
 // max_i ||x_i|| bound into *w.xmax from per-point bounds (FP32 norms, or the .w of quantised row stats)

@@ -460,3 +460,27 @@ def test_small_problems_single_launch(km, ref, n, d, k):
     assert (o1.assign != o2.assign).sum().item() <= 2
     assert torch.allclose(C1, C2, rtol=1e-6, atol=1e-6)
     assert abs(o1.stats["objective"] - o2.stats["objective"]) <= 1e-6 * abs(o2.stats["objective"])
+
+
+@pytest.mark.parametrize("n,d,k,tol", [(10000, 16, 8, 1e-4), (3000, 40, 64, 1e-3), (16384, 64, 8, 0.0)])
+def test_small_problems_stop_rule_and_reproducible(km, n, d, k, tol):
+    """The one-launch path stops after the same step as the staged path (tol > 0; tol = 0 runs every
+    step), its last step's counts agree, and two calls return identical bits: each cluster's sum is
+    taken in a fixed order whatever the scheduling."""
+    X = synth.mixture(5100 + n + d + k, n, d, k, 6.0, 1.0)
+    Xd = torch.from_numpy(X).to(DEV)
+    outs = []
+    for prof in (False, False, True):
+        C = torch.from_numpy(X[:k].copy()).to(DEV)
+        outs.append((C, km.run(Xd, C, 60, tol=tol, profile=prof)))
+    (C1, o1), (C2, o2), (C3, o3) = outs
+    assert o1.stats["launches"] == 1 and o3.stats["launches"] > 1
+    assert o1.stats["iters_done"] == o3.stats["iters_done"]
+    assert (o1.stats["iters_done"] < 60) == (tol > 0)
+    assert o1.stats["n_changed"] == o3.stats["n_changed"]
+    assert o1.stats["n_empty"] == o3.stats["n_empty"]
+    assert torch.equal(C1, C2) and torch.equal(o1.assign, o2.assign) and torch.equal(o1.sums, o2.sums)
+    assert torch.equal(o1.counts, o2.counts) and o1.stats["objective"] == o2.stats["objective"]
+    assert torch.equal(o1.counts, o3.counts)
+    assert torch.allclose(C1, C3, rtol=1e-6, atol=1e-6)
+    assert abs(o1.stats["objective"] - o3.stats["objective"]) <= 1e-6 * abs(o3.stats["objective"])
