@@ -351,6 +351,7 @@ def run_batched(args, torch, dev, dist, rank, world, local, emit=True):
             for si, kname in enumerate(km.STAGES):
                 stage_tot[kname] += float(st["stage_ms"][0][si])
             flagged = (int(st["n_flagged"].sum()), int(st["n_full"].sum()))
+            shape = int(st["batch_shape"][0])
             launches_tot += int(st["launches"][0])
         ev1.record(stream)
         torch.cuda.synchronize(dev)
@@ -371,7 +372,9 @@ def run_batched(args, torch, dev, dist, rank, world, local, emit=True):
                        "iters_per_step": w.iters, "precision": prec,
                        "step": f"one kmeans_run_batched call = {w.iters} graph-captured Lloyd iterations of all "
                                f"{len(inst)} instances; value counts iterations of the whole batch",
-                       "l2": f"inputs larger than L2 (X = {xbytes / 1e9:.2f} GB)"},
+                       "l2": f"inputs larger than L2 (X = {xbytes / 1e9:.2f} GB)",
+                       "autotuned_shape": {"chunk_width": shape % 1000, "instance_order": ["as given", "by work"][
+                           (shape // 1000) % 10], "code_order": ["order of X", "cluster-sorted"][shape // 10000]}},
             "distance_tflops": value * flops_iter / 1e12,
             "stage_ms_per_iter": {k: v / args.steps / w.iters for k, v in stage_tot.items()},
             "flagged_last_iter": {"flagged": flagged[0], "full_recheck": flagged[1],

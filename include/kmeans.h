@@ -151,7 +151,11 @@ typedef struct {
   int32_t iters_bf16;   /* steps of the call whose distance contraction ran with
                            BF16 codes instead of the requested precision (1 for a
                            KM_FP8E4M3 call without warm_start: its first step) */
-  int32_t reserved;
+  int32_t batch_shape;  /* kmeans_run_batched: the autotuned launch shape, chunk
+                           width + 1000 x instance order (0: as given, 1: by work
+                           per tile) + 10000 x code order (0: the point codes in
+                           the order of X, 1: rewritten in cluster-sorted order
+                           each step); 0 for other calls */
 } km_stats;
 
 /* Fills *opts with the defaults (FP32, recheck on, legacy stream). */

@@ -416,16 +416,22 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 2-D K-major code matrix [rows][Kp] -> boxes of (128 bytes of K) x box_rows, 128-byte swizzle.
-int encode_codes_map(CUtensorMap* m, void* base, int64_t rows, int Kp, int esz, int box_rows) {
+// Codes [rows][Kp] -> boxes of rowb bytes (128: the 128-byte swizzle; 64 / 32: a
+// single block of the 64- / 32-byte swizzle, Kp * esz == rowb) x box_rows.
+int encode_codes_map(CUtensorMap* m, void* base, int64_t rows, int Kp, int esz, int box_rows, int rowb = 128) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(KM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (rowb != 128 && Kp * esz != rowb) return fail(KM_EINVAL, "code rows of %d bytes in %d-byte boxes", Kp * esz, rowb);
   cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)(rowb / esz), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
+  const CUtensorMapSwizzle sw =
+      rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : rowb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
   CUresult r = enc(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims,
-                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                   rowb == 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(KM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return KM_OK;
 }
@@ -1403,11 +1409,16 @@ KM_API int32_t kmeans_version(void) { return 200; }
 
 namespace {
 
-// Launch shape of a batch: chunk width and the order of the instances in the
-// flattened tile space (0: as given, 1: by decreasing work per row tile).
+// Launch shape of a batch: chunk width, the order of the instances in the
+// flattened tile space (0: as given, 1: by decreasing work per row tile), and
+// whether the reduce stage rewrites the point codes in cluster-sorted order for
+// the next step (1; a tile then mostly holds rows of one previous cluster, so
+// its candidate tracking is cheap and starts with that cluster's chunk) or the
+// codes keep the order of X (0; the reduce stage then writes no codes).
 struct BatchTune {
   int bn;
   int order;
+  int sorted;
 };
 
 struct BatchPlan {
@@ -1417,13 +1428,24 @@ struct BatchPlan {
   std::vector<int64_t> seg_off;   // prefix sums of the segmented sum's row costs
   std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
   int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
-  int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0;
+  int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0, sorted = 1;
+  int shape = 0;  // the tune, as km_stats.batch_shape reports it
 };
+
+// Work model of one 128-row tile of an instance, in units of a 128-column chunk
+// with one 128-byte K block: epilogue work ~ the columns, MMA ~ columns x K, plus
+// a fixed per-tile cost.
+double tile_work(const BInst& I) {
+  const double cols = (double)I.kp / 128.0;
+  return cols * (0.5 + 0.5 * I.nkb * I.rowb / 128.0) + 1.5;
+}
 
 int plan_batch(const km_instance* in, int count, int precision, const BatchTune& tune, BatchPlan& P) {
   P = BatchPlan();
   P.fp8 = precision == KM_FP8E4M3;
   P.bn = tune.bn;
+  P.sorted = tune.sorted;
+  P.shape = tune.bn + 1000 * tune.order + 10000 * tune.sorted;
   const int esz = P.fp8 ? 1 : 2, kbe = 128 / esz;
   P.order.resize(count);
   for (int b = 0; b < count; ++b) P.order[b] = b;
@@ -1450,10 +1472,16 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     I.n = s.n;
     I.d = s.d;
     I.k = s.k;
-    I.Kp = (s.d + kbe - 1) / kbe * kbe;
-    I.nkb = I.Kp / kbe;
-    I.kp = (s.k + P.bn - 1) / P.bn * P.bn;
-    I.nchunks = I.kp / P.bn;
+    // K: rows of 32 or 64 bytes (one MMA step or two, with the swizzle of that width) when d fits,
+    // else whole 128-byte blocks; N: k rounded up to 32 columns when one chunk holds it
+    if (s.d * esz <= 32) I.rowb = 32;
+    else if (s.d * esz <= 64) I.rowb = 64;
+    else I.rowb = 128;
+    I.Kp = I.rowb < 128 ? I.rowb / esz : (s.d + kbe - 1) / kbe * kbe;
+    I.nkb = I.rowb < 128 ? 1 : I.Kp / kbe;
+    I.bn = s.k < P.bn ? (s.k + 31) / 32 * 32 : P.bn;
+    I.kp = (s.k + I.bn - 1) / I.bn * I.bn;
+    I.nchunks = I.kp / I.bn;
     const double K = I.Kp;
     I.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));
     I.row_off = P.R;
@@ -1489,7 +1517,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
   std::vector<double> wsum(count + 1, 0.0);
   for (int q = 0; q < count; ++q) {
     const BInst& I = P.inst[q];
-    const double per_tile = (double)I.nchunks * I.nkb + 2.0;
+    const double per_tile = tile_work(I);
     wsum[q + 1] = wsum[q] + per_tile * (double)(P.tile_off[q + 1] - P.tile_off[q]);
   }
   P.cta_tile.assign(grid + 1, P.T);
@@ -1499,7 +1527,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     const double target = wsum[count] * c / grid;
     while (q < count - 1 && wsum[q + 1] <= target) ++q;
     const BInst& I = P.inst[q];
-    const double per_tile = (double)I.nchunks * I.nkb + 2.0;
+    const double per_tile = tile_work(I);
     int64_t t = P.tile_off[q] + (int64_t)((target - wsum[q]) / per_tile);
     t = std::min(std::max(t, P.cta_tile[c - 1]), P.tile_off[q + 1]);
     P.cta_tile[c] = t;
@@ -1509,7 +1537,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
 
 struct BatchCache {
   uint64_t sig = 0;
-  BatchTune tune{128, 0};
+  BatchTune tune{128, 0, 1};
 };
 
 struct BatchCtx {
@@ -1669,8 +1697,8 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   const int esz = P.fp8 ? 1 : 2;
   for (int b = 0; b < nb; ++b) {
     const BInst& I = P.inst[b];
-    if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128))) return rc;
-    if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, P.bn))) return rc;
+    if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128, I.rowb))) return rc;
+    if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, I.bn, I.rowb))) return rc;
   }
   KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
@@ -1701,6 +1729,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   app(&o.recheck, sizeof o.recheck);
   app(&o.warm_start, sizeof o.warm_start);
   app(&P.bn, sizeof P.bn);
+  app(&P.sorted, sizeof P.sorted);
   app(&o.profile, sizeof o.profile);
   void* base = bc.ws;
   app(&base, sizeof base);
@@ -1713,7 +1742,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
     KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     const uint32_t idesc = tc::idesc_f32acc(P.fp8 ? 0u : 1u, 128, (uint32_t)P.bn);
-    const int qmode = P.fp8 ? 2 : 1;
+    const int qmode = P.sorted ? (P.fp8 ? 2 : 1) : 0;
     cudaStream_t cs = c->cap_stream;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
       // stage boundaries as in enqueue_step (events only when profiling)
@@ -1724,7 +1753,8 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
       if (!e) e = launch_b_quant_c(W, P.fp8, cs);
       if (!e) e = at(1);
       if (!e)
-        e = launch_b_assign(W, P.fp8, it == 0 && !o.warm_start, it > 0, P.nkb_max, P.kp_max, P.bn, P.stages, P.abufs,
+        e = launch_b_assign(W, P.fp8, it == 0 && !o.warm_start, it > 0 && P.sorted, P.nkb_max, P.kp_max, P.bn,
+                            P.stages, P.abufs,
                             idesc, cs);
       if (!e) e = at(2);
       if (!e && o.recheck) e = launch_b_recheck(W, cs);
@@ -1826,6 +1856,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
       st.launches = 1 + bc.graph_kernels;  // the whole batch's launches (point quantisation + graph),
                                            // reported for every instance
       memcpy(st.stage_ms, stage_ms, sizeof stage_ms);
+      st.batch_shape = P.shape;
     }
   }
   return KM_OK;
@@ -1862,7 +1893,7 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
   c->xc.valid = false;  // this call overwrites the workspace
   BatchCtx& bc = g_batch[dev];
   const uint64_t sig = batch_signature(inst, count, o.precision);
-  BatchTune tune{128, 0};
+  BatchTune tune{128, 0, 1};
   bool known = false;
   for (const BatchCache& t : bc.tuned)
     if (t.sig == sig) {
@@ -1871,17 +1902,19 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
     }
   int rc;
   if (!known) {
-    // autotune: time two steps of every candidate shape on the caller's data, keep the fastest
-    const BatchTune cands[4] = {{128, 0}, {128, 1}, {64, 0}, {64, 1}};
+    // autotune: time three steps of every candidate shape on the caller's data, keep the fastest
+    const BatchTune cands[8] = {{128, 0, 1}, {128, 1, 1}, {64, 0, 1}, {64, 1, 1},
+                                {128, 0, 0}, {128, 1, 0}, {64, 0, 0}, {64, 1, 0}};
     float best = 1e30f;
     for (const BatchTune& cand : cands) {
       BatchPlan P;
       if (plan_batch(inst, count, o.precision, cand, P)) continue;
       std::vector<int> idx(P.order);
       float ms = 0.f;
-      if ((rc = run_batch_locked(c, bc, o, P, 2, 0.0, nullptr, idx.data(), &ms))) return rc;
+      // three steps: the sorted order of the codes pays off from the second step on
+      if ((rc = run_batch_locked(c, bc, o, P, 3, 0.0, nullptr, idx.data(), &ms))) return rc;
       // the trial steps moved C: put every instance back before the next candidate
-      if ((rc = restore_batch_c(bc, P, 2, (cudaStream_t)o.stream))) return rc;
+      if ((rc = restore_batch_c(bc, P, 3, (cudaStream_t)o.stream))) return rc;
       if (ms < best) {
         best = ms;
         tune = cand;

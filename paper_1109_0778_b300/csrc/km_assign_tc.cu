@@ -116,6 +116,8 @@ struct Item {
   int64_t tend;     // one past its last flattened tile
   int64_t n;
   int k, Kp, nkb, nchunks;
+  int rowb;  // bytes of a code row of one K block (32, 64 or 128; batched instances may be narrower)
+  int bn;    // centroid chunk width
   const CUtensorMap* mapX;
   const CUtensorMap* mapC;
   const float* h;
@@ -142,6 +144,8 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.Kp = P.Kp;
     it.nkb = P.nkb;
     it.nchunks = P.nchunks;
+    it.rowb = (int)ROWB;
+    it.bn = P.bn;
     it.mapX = mx;
     it.mapC = mc;
     it.h = P.h;
@@ -164,6 +168,8 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.Kp = I.Kp;
     it.nkb = I.nkb;
     it.nchunks = I.nchunks;
+    it.rowb = I.rowb;
+    it.bn = I.bn;
     it.mapX = P.bmaps + 2 * b;
     it.mapC = P.bmaps + 2 * b + 1;
     it.h = P.bh + I.kp_off;
@@ -522,17 +528,18 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const int64_t gb = ga + tr.ts;
         const int ntp = (pairs && gb < tr.t1 && gb < it.tend) ? 2 : 1;
         const int64_t tile0 = ga - it.tile0;
-        const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile0), it, BN);
+        const int c0 = first_chunk(labn != -2 ? labn : tile_label(P, it, tile0), it, it.bn);
         {
           const int64_t gn = ntp == 2 ? gb + tr.ts : gb;
           labn = (gn < tr.t1 && gn < it.tend) ? tile_label(P, it, gn - it.tile0) : -2;
         }
         for (int u = 0; u < ntp && ok; ++u, ++lt) {
           if (!mbar_wait(&a_empty[ab], aph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
-          mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * ROWB + (AXS ? BM * HROWB : 0u));
+          const uint32_t rowb = BATCH ? (uint32_t)it.rowb : ROWB;  // (narrower rows come as one K block: x = 0)
+          mbar_arrive_expect_tx(&a_full[ab], (uint32_t)it.nkb * BM * rowb + (AXS ? BM * HROWB : 0u));
           const int row0 = (int)((u ? gb - it.tile0 : tile0) * BM);
           for (int kb = 0; kb < it.nkb; ++kb)
-            tma_load_2d(A0 + ab * a_bytes + kb * (BM * ROWB), it.mapX, &a_full[ab], kb * KBE, row0);
+            tma_load_2d(A0 + ab * a_bytes + kb * (BM * rowb), it.mapX, &a_full[ab], kb * KBE, row0);
           if (AXS) tma_load_2d(A0 + ab * a_bytes + it.nkb * (BM * ROWB), &mapXh, &a_full[ab], 0, row0);
           last_a = ab;
           last_aph = aph;
@@ -544,9 +551,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         for (int cc = 0, c = c0; cc < it.nchunks && ok; ++cc, ++gc, c = (c + 1 == it.nchunks) ? 0 : c + 1) {
           const int s = sb;
           if (!mbar_wait(&b_empty[s], sph ^ 1, &abort_s, P.wait_ns)) { ok = false; break; }
-          mbar_arrive_expect_tx(&b_full[s], (uint32_t)it.nkb * b_kblk + (FOLD ? BN * HROWB : 0u));
+          mbar_arrive_expect_tx(&b_full[s], (BATCH ? (uint32_t)(it.nkb * it.bn * it.rowb) : (uint32_t)it.nkb * b_kblk) +
+                                                (FOLD ? BN * HROWB : 0u));
           for (int kb = 0; kb < it.nkb; ++kb)
-            tma_load_2d(B0 + s * b_bytes + kb * b_kblk, it.mapC, &b_full[s], kb * KBE, c * BN);
+            tma_load_2d(B0 + s * b_bytes + kb * b_kblk, it.mapC, &b_full[s], kb * KBE, c * (BATCH ? it.bn : BN));
           if (FOLD) tma_load_2d(B0 + s * b_bytes + it.nkb * b_kblk, &mapH, &b_full[s], 0, c * BN);
           last_s = s;
           last_sph = sph;
@@ -608,19 +616,23 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             tc_fence_after_sync();
             const uint32_t a_addr = smem_u32(A0 + ab * a_bytes);
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 128);
-            const uint64_t a_desc = sdesc_k_sw128(a_addr), b_desc = sdesc_k_sw128(b_addr);
+            const uint64_t a_desc = BATCH ? sdesc_k(a_addr, (uint32_t)it.rowb) : sdesc_k_sw128(a_addr);
+            const uint64_t b_desc = BATCH ? sdesc_k(b_addr, (uint32_t)it.rowb) : sdesc_k_sw128(b_addr);
+            // a batched instance's N is its own chunk width
+            const uint32_t idesc = BATCH ? ((P.idesc & ~(0x3Fu << 17)) | ((uint32_t)(it.bn >> 3) << 17)) : P.idesc;
+            const int ksteps = BATCH ? it.rowb >> 5 : 4;  // 32-byte MMA steps per K block row
             const int mk = split ? it.nkb >> 1 : it.nkb;
             for (int seg = 0; seg < (split ? 3 : 1); ++seg) {
               const int ka = seg == 1 ? mk : 0, kc = seg == 2 ? mk : 0;
               for (int kb = 0; kb < mk; ++kb) {
-                const uint64_t a_kb = a_desc + (uint64_t)(((ka + kb) * (BM * ROWB)) >> 4);
+                const uint64_t a_kb = a_desc + (uint64_t)(((ka + kb) * (BM * (BATCH ? (uint32_t)it.rowb : ROWB))) >> 4);
                 const uint64_t b_kb = b_desc + (uint64_t)(((kc + kb) * b_kblk) >> 4);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
+                for (int kk = 0; kk < (BATCH ? ksteps : 4); ++kk) {
                   const uint64_t ad = a_kb + (uint64_t)(kk * 2);  // + 32 bytes
                   const uint64_t bd = b_kb + (uint64_t)(kk * 2);
-                  if constexpr (FP8) mma_fp8(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
-                  else mma_bf16(d_tmem, ad, bd, P.idesc, (seg | kb | kk) != 0);
+                  if constexpr (FP8) mma_fp8(d_tmem, ad, bd, idesc, (seg | kb | kk) != 0);
+                  else mma_bf16(d_tmem, ad, bd, idesc, (seg | kb | kk) != 0);
                 }
               }
             }
@@ -655,7 +667,6 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     const int q = warp & 3;                // TMEM lane quarter this warp may access
     const int grp = (warp - 2) >> 2;       // epilogue group: tile u = grp of each pair
     const int r = q * 32 + lane;           // row of the tile this thread owns
-    const int nblk = BN / 32;              // 32-column blocks per chunk
     int gu = 0;                            // chunks of this group consumed so far
     bool ok = true;
     unsigned int changed = 0;
@@ -676,7 +687,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (BATCH && !it.skip) {
           // this instance's h_j (and scales) into shared memory
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
-          for (int j = threadIdx.x - 64; j < it.nchunks * BN; j += 32 * NEPI) Hs[j] = __ldg(it.h + j);
+          for (int j = threadIdx.x - 64; j < it.nchunks * it.bn; j += 32 * NEPI) Hs[j] = __ldg(it.h + j);
           asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
         }
         if (!it.skip) {
@@ -703,7 +714,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         continue;
       }
       const int64_t tile = grp ? gb - it.tile0 : tile0;
-      const int c0 = first_chunk(lab, it, BN);
+      const int c0 = first_chunk(lab, it, it.bn);
+      const int nblk = it.bn / 32;  // 32-column blocks per chunk
       const RowMeta m = have_nxt ? nxt : fetch_meta<BATCH>(P, it, tile, r);
       // this group's tile of the next pair, when it belongs to the same instance: its loads overlap this tile
       {
@@ -789,7 +801,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
-        const int j0 = c * BN + blk * 32;
+        const int j0 = c * it.bn + blk * 32;
         if (two) score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
         else score_block(v, Hs + j0, wrow, top, j0, thr, margin);
         kb += two ? 2 : 1;
@@ -958,7 +970,7 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   memset(&P, 0, sizeof P);
   P.nkb = nkb_max;
   P.bn = bn;
-  P.nchunks = kp_max / bn;
+  P.nchunks = (kp_max + bn - 1) / bn;
   P.stages = stages;
   P.abufs = abufs;
   P.first = first;

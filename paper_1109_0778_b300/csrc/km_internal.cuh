@@ -196,7 +196,8 @@ struct BInst {
   int64_t cq_off;    // bytes: centroid codes [kp][Kp]
   int Kp, nkb, kp, nchunks;
   float gam_tc;
-  int pad0, pad1;
+  int rowb;  // bytes of one code row of a K block: 32 or 64 (one block, 32- or 64-byte swizzle), or 128
+  int bn;    // centroid chunk width: a multiple of 32, at most the launch's (k rounded up to 32 when smaller)
 };
 
 struct BWork {

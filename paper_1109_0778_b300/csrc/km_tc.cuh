@@ -196,6 +196,26 @@ __device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
   return d;
 }
 
+// As sdesc_k_sw128 for a K-major block of 64-byte rows with the 64-byte swizzle
+// (16-byte chunk index XOR bits 1-2 of the row inside each 512-byte group of 8
+// rows): stride byte offset 512, layout SWIZZLE_64B (4 in bits 61-63). Two MMA
+// steps of 32 bytes span one row (advance the start address by 32 bytes).
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
+// Descriptor of a K-major block whose rows are `rowb` bytes (32, 64 or 128) with
+// the swizzle of that width.
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr, uint32_t rowb) {
+  return rowb == 128u ? sdesc_k_sw128(saddr) : rowb == 64u ? sdesc_k_sw64(saddr) : sdesc_k_sw32(saddr);
+}
+
 // Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A / B formats
 // (bits 7-9 / 10-12), both operands K-major (bits 15, 16 = 0), N >> 3 in bits
 // 17-22, M >> 4 in bits 24-28. Formats: kind::f16 BF16 = 1; kind::f8f6f4 E4M3 = 0.

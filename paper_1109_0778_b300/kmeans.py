@@ -63,10 +63,10 @@ class Stats(ctypes.Structure):
                 ("n_full", ctypes.c_int64), ("n_empty", ctypes.c_int32),
                 ("iters_done", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("launches", ctypes.c_int32), ("stage_ms", ctypes.c_float * 12),
-                ("n_queued", ctypes.c_int64), ("iters_bf16", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_queued", ctypes.c_int64), ("iters_bf16", ctypes.c_int32), ("batch_shape", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("stage_ms", "reserved")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "stage_ms"}
         d["stage_ms"] = {name: float(self.stage_ms[i]) for i, name in enumerate(STAGES)}
         return d
 
