@@ -218,7 +218,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, small, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, small, cst, cst16, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -270,6 +270,8 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
     L.xh = (t.fp8 && t.fold) ? take(32 * (size_t)n) : 0;  // the points' 1/s_x slices (folded E4M3)
     L.hq = take(4 * (size_t)t.kp);
     L.scq = take(4 * (size_t)t.kp);
+    // per-centroid error terms of the main codes (or of a cold call's BF16 first step)
+    L.cst = take(16 * (size_t)std::max(t.kp, tc_shape(KM_BF16, d, k).kp));
     L.xss = take(16 * (size_t)n);
     L.fq_cap = requeue_cap(n);
     L.fq_rows = take(4 * (size_t)L.fq_cap);
@@ -289,14 +291,15 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
       L.hc16 = t16.fold ? take(32 * (size_t)t16.kp) : 0;
       L.hq16 = take(4 * (size_t)t16.kp);
       L.scq16 = take(4 * (size_t)t16.kp);
+      L.cst16 = take(16 * (size_t)t16.kp);
     } else {
       L.Kp16 = 0;
-      L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.hc16 = 0;
+      L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.hc16 = L.cst16 = 0;
     }
   } else {
     L.hc = L.hc16 = L.xh = 0;
     L.Kp16 = 0;
-    L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = 0;
+    L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.cst = L.cst16 = 0;
     L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;  // also serves the re-check pass
@@ -380,6 +383,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.Cq = L.Cq ? (uint8_t*)(b + L.Cq) : nullptr;
   w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
   w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
+  w.cst = L.cst ? (float4*)(b + L.cst) : nullptr;
   w.Hc = L.hc ? (void*)(b + L.hc) : nullptr;
   w.Xh = L.xh ? (void*)(b + L.xh) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
@@ -473,6 +477,7 @@ struct StepCfg {
   uint8_t* Cq16;
   void* Hc16;  // -h_j slices of the re-score codes (folded BF16), null otherwise
   float *hq16, *scq16;
+  float4* cst16;
 };
 
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
@@ -562,7 +567,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
   const TcShape& t = cold ? cfg.t0 : cfg.t;
   if ((e = cudaMemsetAsync(w.ctl, 0, kCtlIterBytes, s))) return e;
   if ((e = at(0))) return e;
-  if (tcp) e = launch_quant_c(p, w, t.qmode(), t.kp, t.Kp, w.Cq, t.fold ? w.Hc : nullptr, w.hq, w.scq, s);
+  if (tcp) e = launch_quant_c(p, w, t.qmode(), t.kp, t.Kp, w.Cq, t.fold ? w.Hc : nullptr, w.hq, w.scq, w.cst, s);
   else e = launch_prep(p, w, s);
   if (e) return e;
   if ((e = at(1))) return e;
@@ -584,7 +589,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
       tc16 = [&](cudaStream_t st) {
         const TcShape& t16 = cfg.t16;
         cudaError_t r = launch_quant_c(p, w, 0, t16.kp, t16.Kp, cfg.Cq16, t16.fold ? cfg.Hc16 : nullptr, cfg.hq16,
-                                       cfg.scq16, st, true);
+                                       cfg.scq16, cfg.cst16, st, true);
         if (r != cudaSuccess) return r;
         Problem q = p;
         q.n = w.fq_cap;
@@ -746,6 +751,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
     memset(&P, 0, sizeof P);
     P.h = w.hq;
     P.sc = w.scq;
+    P.cst = w.cst;
     P.rows = nullptr;
     P.xs = xs;
     P.xs_sorted = w.xs_sorted;
@@ -805,6 +811,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
       cfg.Cq16 = (uint8_t*)(wb + L.cq16);
       cfg.hq16 = (float*)(wb + L.hq16);
       cfg.scq16 = (float*)(wb + L.scq16);
+      cfg.cst16 = (float4*)(wb + L.cst16);
       if ((rc = encode_codes_map(&cfg.L16.mapX, w.Xq16, w.fq_cap, cfg.t16.Kw, cfg.t16.esz, 128))) return rc;
       if ((rc = encode_codes_map(&cfg.L16.mapC, cfg.Cq16, cfg.t16.kp, cfg.t16.Kc, cfg.t16.esz, cfg.t16.bn)))
         return rc;
@@ -813,6 +820,7 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
       TcParams& Q = cfg.P16;
       Q.h = cfg.hq16;
       Q.sc = cfg.scq16;
+      Q.cst = cfg.cst16;
       Q.Cq = cfg.Cq16;
       Q.rows = w.fq_rows;
       Q.xs_sorted = w.xs16q;
@@ -1573,7 +1581,7 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 // Byte offsets of the batch workspace.
 struct BLayout {
   size_t ctl, inst, row, kc, kp, tile, seg, cta, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq,
-      xq, cq, csave, hist, total;
+      cst, xq, cq, csave, hist, total;
 };
 
 BLayout batch_layout(const BatchPlan& P, int iters) {
@@ -1606,6 +1614,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.sums = take(8 * (size_t)P.SUMS);
   L.hq = take(4 * (size_t)P.KP);
   L.scq = take(4 * (size_t)P.KP);
+  L.cst = take(16 * (size_t)P.KP);
   L.xq = take((size_t)P.XQ);
   L.cq = take((size_t)P.CQ);
   L.csave = take(4 * (size_t)P.CSAVE);
@@ -1683,6 +1692,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.sums64 = (double*)(B + o_sums);
   W.hq = (float*)(B + o_hq);
   W.scq = (float*)(B + o_scq);
+  W.cst = (float4*)(B + BL.cst);
   W.Xq = (uint8_t*)(B + o_xq);
   W.Cq = (uint8_t*)(B + o_cq);
   char* hb = B + o_hist;

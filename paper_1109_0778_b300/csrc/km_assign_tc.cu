@@ -36,17 +36,26 @@
 //
 // Error bound (u = 2^-24; the tensor core accumulates in FP32 with truncation,
 // so gamma'_K = K 2^-23 / (1 - K 2^-23)): for every j
-//   |s^_j - s_j| <= E_i = 3u H + (gamma'_K + 2u) ||x~_i|| C~max
-//                       + ||dx_i|| Cmax + ||x_i|| DCmax + ||dx_i|| DCmax,
-// where dx = x~ - x, dc = c~ - c, and H, Cmax, C~max, DCmax are the per-step
-// maxima over the centroids (hoisted, Sec. 3.1). With margin_i = 2 E_i
-// (1 + 2^-10), the true argmin is among the candidates {j : s^_j - s^_1 <=
-// margin_i}. A row whose only candidate is j1 is final; otherwise its
-// candidates (or, past 7 of them, all k) go to the FP32 re-check.
+//   |s^_j - s_j| <= e_ij = 3u h_j + (gamma'_K + 2u) ||x~_i|| ||c~_j||
+//                        + ||dx_i|| ||c_j|| + ||x_i|| ||dc_j|| + ||dx_i|| ||dc_j||,
+// where dx = x~ - x, dc = c~ - c (the centroid's own terms come from a table
+// the centroid quantisation writes), and e_ij <= E_i, the same expression with
+// the per-step maxima H, C~max, Cmax, DCmax (hoisted, Sec. 3.1); both carry a
+// factor 1 + 2^-10 for the rounding of their evaluation. The exact minimum is
+// at most U_i = min_j (s^_j + e_ij), so the true argmin is among the
+// candidates {j : s^_j - e_ij <= U_i}. A row whose only candidate is j1 is
+// final; otherwise its candidates (or, past 7 of them, all k) go to the FP32
+// re-check. On centroid sets of widely different norms the per-centroid terms
+// keep the candidates of rows near small centroids few where E_i, set by the
+// largest centroids, would flag them all.
 //
-// Threshold. Rows keep the 8 smallest scores seen among elements <= thr, with
-// thr = best + margin rounded up (infinite before the first chunk), so a
-// 32-column block costs one minimum unless it holds a candidate. From the
+// Threshold. Columns are examined only below thr = U + E_i (rounded up;
+// FLT_MAX before the first), a superset of the candidates, so a 32-column block
+// costs one minimum unless it holds one; an examined column gets its own e_ij,
+// tightens U, and enters the row's list of 7 (ordered by lower bound) while its
+// lower bound is <= U. The list's prefix with lower bound <= U at the end is the
+// candidate set; a dropped entry that qualifies too sends the row to the
+// all-centroid re-check. From the
 // second step of a call on, rows are the points in the previous step's
 // cluster-sorted order (the codes are rewritten in that order by the reduce
 // stage) and a tile's chunks are visited starting with the chunk of its first
@@ -76,7 +85,7 @@ constexpr int NACC = 4;
 constexpr int MAX_STAGES = 8;
 constexpr int MAX_ABUF = 4;                  // A slots (row tiles) in the smem ring
 
-constexpr int kT = kMaxCand;  // candidate slots per row
+constexpr int kT = kMaxCand - 1;  // candidate slots per row (a flag record holds up to kMaxCand)
 
 struct Cand {
   float v;
@@ -122,6 +131,7 @@ struct Item {
   const CUtensorMap* mapC;
   const float* h;
   const float* sc;
+  const float4* cst;  // per-centroid error-bound terms
   const int32_t* rows;
   const float4* xs;
   const float4* xs_sorted;
@@ -150,6 +160,7 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.mapC = mc;
     it.h = P.h;
     it.sc = P.sc;
+    it.cst = P.cst;
     it.rows = P.rows;
     it.xs = P.xs;
     it.xs_sorted = P.xs_sorted;
@@ -174,6 +185,7 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.mapC = P.bmaps + 2 * b + 1;
     it.h = P.bh + I.kp_off;
     it.sc = P.bsc + I.kp_off;
+    it.cst = P.bcst + I.kp_off;
     it.rows = P.sorted ? P.bperm + I.row_off : nullptr;
     it.xs = P.bxs + I.row_off;
     it.xs_sorted = P.bxs_sorted + I.row_off;
@@ -268,13 +280,38 @@ __device__ __forceinline__ float score_of(float x) { return NEG ? -x : x; }
 template <bool NEG>
 __device__ __forceinline__ float score_of(uint32_t x) { return NEG ? -__uint_as_float(x) : __uint_as_float(x); }
 
+// Per-centroid error bound of a row. Column j's computed score s^_j is within
+//   e_j = (a0 h_j + a1 ||c~_j|| + a2 ||c_j|| + a3 ||c~_j - c_j||) ks
+// of its exact value (the terms of E_i with the centroid's own values in place
+// of the step's maxima; cst[j] holds them; ks = 1 + 2^-10 covers the rounding
+// of this evaluation, times the folded E4M3 accumulator scale). U = min over
+// the columns seen of s^_j + e_j bounds the row's exact minimum from above, so
+// the true argmin is among {j : s^_j - e_j <= U} (its lower bound cannot exceed
+// any column's upper bound). err(j) is monotone in the four terms, so
+// errv(step maxima) >= e_j for every j.
+struct RowErr {
+  const float4* cst;
+  float a0, a1, a2, a3, ks;
+  float U;    // running upper bound of the row's exact minimum score
+  float Lev;  // smallest lower bound dropped from a full candidate list (+inf: none)
+  __device__ __forceinline__ float errv(float h, float q, float c, float dc) const {
+    return fmaf(a0, h, fmaf(a1, q, fmaf(a2, c, a3 * dc))) * ks;
+  }
+  __device__ __forceinline__ float err(int j) const {
+    const float4 v = __ldg(cst + j);
+    return errv(v.x, v.y, v.z, v.w);
+  }
+};
+
 // Folds a 32-column score block into the row's candidate list: the columns
-// within min(thr, mn + margin) of the block minimum mn (every column that can
-// end within the margin of the row's final minimum), in index order. NEG: the
-// block holds accumulator bits whose negation is the score (folded BF16).
+// within min(thr, mn + margin) of the block minimum mn (a superset of those
+// whose lower bound can end below U), in index order; each gets its own error
+// bound e_j, tightens U, and enters the list (ordered by lower bound) while
+// its lower bound is <= U. thr = U + margin / 2 >= U + e_j for every j. NEG:
+// the block holds accumulator bits whose negation is the score (folded BF16).
 template <bool NEG = false, typename T>
 __device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], float mn, int j0, float& thr,
-                                           float margin) {
+                                           float margin, RowErr& re) {
   const float lim = fminf(thr, __fadd_ru(mn, margin));
   unsigned mask = 0;
 #pragma unroll
@@ -294,8 +331,19 @@ __device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], fl
     const float x2a = (t & 8) ? x4[1] : x4[0], x2b = (t & 8) ? x4[3] : x4[2];
     const float v = (t & 16) ? x2b : x2a;
     if (v <= thr) {
-      cand_insert(top, v, j0 + t);
-      thr = fminf(thr, __fadd_ru(top[0].v, margin));
+      const float ej = re.err(j0 + t);
+      re.U = fminf(re.U, __fadd_ru(v, ej));
+      thr = fminf(thr, __fadd_ru(re.U, 0.5f * margin));
+      const float lo = __fsub_rd(v, ej);
+      if (lo <= re.U) {
+        const float last = top[kT - 1].v;  // dropped when the list is full (+inf: it has room)
+        if (lo < last) {
+          re.Lev = fminf(re.Lev, last);
+          cand_insert(top, lo, j0 + t);
+        } else {
+          re.Lev = fminf(re.Lev, lo);
+        }
+      }
     }
   }
 }
@@ -305,7 +353,7 @@ __device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], fl
 // packed operation), their minimum, and the fold of the block's candidates
 // (rare once thr is tight).
 __device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float* hb, float w, Cand (&top)[kT],
-                                            int j0, float& thr, float margin) {
+                                            int j0, float& thr, float margin, RowErr& re) {
   float s[32];
   const float4* h4 = reinterpret_cast<const float4*>(hb);
   const float2 w2 = make_float2(w, w);
@@ -330,13 +378,13 @@ __device__ __forceinline__ void score_block(const uint32_t (&v)[32], const float
                                min3f(m11[6], m11[7], m11[8])),
                          fminf(m11[9], m11[10]));
   if (__any_sync(0xffffffffu, mn <= thr))
-    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin);
+    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin, re);
 }
 
 // Two consecutive 32-column blocks: both score sets, one vote on the smaller
 // block minimum, then the folds in column order (the first may tighten thr).
 __device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint32_t (&v2)[32], const float* hb,
-                                             float w, Cand (&top)[kT], int j0, float& thr, float margin) {
+                                             float w, Cand (&top)[kT], int j0, float& thr, float margin, RowErr& re) {
   float s[32], s2[32];
   const float4* h4 = reinterpret_cast<const float4*>(hb);
   const float2 w2 = make_float2(w, w);
@@ -375,8 +423,8 @@ __device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint
                                 min3f(n11[6], n11[7], n11[8])),
                           fminf(n11[9], n11[10]));
   if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
-    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin);
-    if (mn2 <= thr) fold_block(top, s2, mn2, j0 + 32, thr, margin);
+    if (mn <= thr) fold_block(top, s, mn, j0, thr, margin, re);
+    if (mn2 <= thr) fold_block(top, s2, mn2, j0 + 32, thr, margin, re);
   }
 }
 
@@ -384,7 +432,7 @@ __device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint
 // the block minimum of the scores is minus the maximum of the accumulators, so
 // a 64-column half costs two trees of 3-input maxima and a vote.
 __device__ __forceinline__ void score_block2_fold(const uint32_t (&v)[32], const uint32_t (&v2)[32], Cand (&top)[kT],
-                                                  int j0, float& thr, float margin) {
+                                                  int j0, float& thr, float margin, RowErr& re) {
   float m11[11], n11[11];
 #pragma unroll
   for (int u = 0; u < 10; ++u) {
@@ -400,8 +448,8 @@ __device__ __forceinline__ void score_block2_fold(const uint32_t (&v)[32], const
                                  max3f(n11[6], n11[7], n11[8])),
                            fmaxf(n11[9], n11[10]));
   if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
-    if (mn <= thr) fold_block<true>(top, v, mn, j0, thr, margin);
-    if (mn2 <= thr) fold_block<true>(top, v2, mn2, j0 + 32, thr, margin);
+    if (mn <= thr) fold_block<true>(top, v, mn, j0, thr, margin, re);
+    if (mn2 <= thr) fold_block<true>(top, v2, mn2, j0 + 32, thr, margin, re);
   }
 }
 
@@ -730,12 +778,18 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       const float4 xs = m.xs;
       int old = m.old;
       if (old < 0 || old >= it.k) old = -1;
-      // per-row error bound and margin
-      const float E = fmaf(BATCH ? 3.f * kU : P.hcoef, H,
-                           fmaf(it.gam_tc + 2.f * kU, xs.y * QCmax,
-                                fmaf(xs.z, Cmax, fmaf(xs.w, DCmax, xs.z * DCmax))));
-      // folded E4M3 launches compare accumulators (scores / (s_x s_c), an exact power-of-two factor)
-      const float margin = 2.f * E * (1.f + 0x1p-10f) * (FP8 && FOLD ? __frcp_rn(xs.x * csc) : 1.f);
+      // per-row error bounds: each centroid's own (candidates), and the step maxima's (margin / 2 >= e_j
+      // for every j; folded E4M3 launches compare accumulators, scores / (s_x s_c), an exact power of two)
+      RowErr re;
+      re.cst = BATCH ? it.cst : P.cst;  // (single launches: read from the parameter space)
+      re.a0 = BATCH ? 3.f * kU : P.hcoef;
+      re.a1 = (it.gam_tc + 2.f * kU) * xs.y;
+      re.a2 = xs.z;
+      re.a3 = xs.w + xs.z;
+      re.ks = (1.f + 0x1p-10f) * (FP8 && FOLD ? __frcp_rn(xs.x * csc) : 1.f);
+      re.U = INFINITY;
+      re.Lev = INFINITY;
+      const float margin = 2.f * re.errv(H, QCmax, Cmax, DCmax);
       float thr = FLT_MAX;  // finite: padding columns (score +inf) never become candidates
       if (ok && P.debug_stall && !__all_sync(0xffffffffu, mbar_wait(&never_bar, 0, &abort_s, P.wait_ns))) ok = false;
 
@@ -764,16 +818,16 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           tmem_ld_32x32b_x32(ta, v);
           tmem_ld_32x32b_x32(ta + 32u, v2);
           tmem_ld_wait();
-          if constexpr (FOLD) score_block2_fold(v, v2, top, j0, thr, margin);
-          else score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
+          if constexpr (FOLD) score_block2_fold(v, v2, top, j0, thr, margin, re);
+          else score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin, re);
           tmem_ld_32x32b_x32(ta + 64u, v);
           tmem_ld_32x32b_x32(ta + 96u, v2);
           tmem_ld_wait();
           tc_fence_before_sync();
           __syncwarp();
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
-          if constexpr (FOLD) score_block2_fold(v, v2, top, j0 + 64, thr, margin);
-          else score_block2(v, v2, Hs + j0 + 64, wrow, top, j0 + 64, thr, margin);
+          if constexpr (FOLD) score_block2_fold(v, v2, top, j0 + 64, thr, margin, re);
+          else score_block2(v, v2, Hs + j0 + 64, wrow, top, j0 + 64, thr, margin, re);
           ++gu;
           c = (c + 1 == it.nchunks) ? 0 : c + 1;
         }
@@ -802,8 +856,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
         const int j0 = c * it.bn + blk * 32;
-        if (two) score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin);
-        else score_block(v, Hs + j0, wrow, top, j0, thr, margin);
+        if (two) score_block2(v, v2, Hs + j0, wrow, top, j0, thr, margin, re);
+        else score_block(v, Hs + j0, wrow, top, j0, thr, margin, re);
         kb += two ? 2 : 1;
         blk = lastb + 1;
         if (lastb == nblk - 1) {
@@ -816,15 +870,13 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         const bool live = ok && valid;
         int nc = -1;  // -1: final; 0: all k; >0: candidate count
         if (live) {
-          if (top[0].i < 0) {
-            nc = 0;
-          } else {
-            int cnt = 1;
+          // the candidates: the list's prefix with lower bound <= U (ordered by lower bound); a
+          // dropped entry that qualifies too means the list cannot hold them all
+          int cnt = 0;
 #pragma unroll
-            for (int t = 1; t < kT; ++t) cnt += (top[t].i >= 0 && __fsub_rn(top[t].v, top[0].v) <= margin) ? 1 : 0;
-            if (cnt == kT) nc = 0;        // maybe more than kT within the margin
-            else if (cnt > 1) nc = cnt;
-          }
+          for (int t = 0; t < kT; ++t) cnt += (top[t].i >= 0 && top[t].v <= re.U) ? 1 : 0;
+          if (cnt == 0 || re.Lev <= re.U) nc = 0;
+          else if (cnt > 1) nc = cnt;
         }
         const bool flag = live && nc >= 0;
         const unsigned fm = __ballot_sync(0xffffffffu, flag);
@@ -866,6 +918,8 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
             rec.cand[a] = (a < nc) ? nxt_j : 0;
             if (a < nc) prev = nxt_j;
           }
+#pragma unroll
+          for (int a = kT; a < kMaxCand; ++a) rec.cand[a] = 0;
           if (slot < (unsigned long long)P.flag_cap) P.flags[slot] = rec;
           it.assign[i] = top[0].i >= 0 ? top[0].i : 0;
         }
@@ -990,6 +1044,7 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   P.bmaps = W.maps;
   P.bh = W.hq;
   P.bsc = W.scq;
+  P.bcst = W.cst;
   P.bCq = W.Cq;
   P.bxs = W.xs;
   P.bxs_sorted = W.xs_sorted;

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
       if (lane == 0) {
         W.hq[g] = INFINITY;
         W.scq[g] = 1.f;
+        W.cst[g] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       continue;
     }
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
       if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
       W.hq[g] = h;
       W.scq[g] = sc;
+      W.cst[g] = make_float4(h, qn, cn, dn);
       I.counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
       atomic_max_nonneg(&ctl->cmax_bits, cn);

@@ -85,6 +85,7 @@ struct Work {
   uint8_t* Cq;         // [kp][Kp] centroid codes (per step)
   float* hq;           // [kp] h_j of the quantised path (+inf for padding)
   float* scq;          // [kp] centroid code scales
+  float4* cst;         // [kp] per-centroid error-bound terms of the codes (TcParams::cst)
   void* Hc;            // [kp][16] BF16 -h_j slices (folded contraction), null otherwise
   void* Xh;            // [n][16] BF16 [1/s_i, 1/s_i, 1/s_i, 0...] slices of a folded E4M3 contraction, in the
                        // codes' row order (null otherwise)
@@ -125,6 +126,8 @@ struct BInst;
 struct TcParams {
   const float* h;     // [kp] h_j = ||c_j||^2 / 2; +inf for padding rows j >= k
   const float* sc;    // [kp] power-of-two row scale of the centroid codes
+  const float4* cst;  // [kp] per-centroid error-bound terms (h_j, ||c~_j||, ||c_j||, ||c~_j - c_j||), rounded up;
+                      // zeros for padding rows
   const int32_t* rows;  // row p of the code matrix holds point rows[p] (null: point p)
   const float4* xs;   // [n] (sx_i, ||x~_i||, ||x~_i - x_i||, ||x_i||), norms rounded up
   const float4* xs_sorted;  // with rows: xs of row p's point, written by the reduce stage
@@ -160,6 +163,7 @@ struct TcParams {
   const CUtensorMap* bmaps;
   float* bh;
   float* bsc;
+  const float4* bcst;
   const uint8_t* bCq;
   const float4* bxs;
   const float4* bxs_sorted;
@@ -224,6 +228,7 @@ struct BWork {
   double* sums64;
   float* hq;
   float* scq;
+  float4* cst;  // [KP] per-centroid error-bound terms
   uint8_t* Xq;
   uint8_t* Cq;
   double* obj_hist;                  // [nb][iters]
@@ -333,7 +338,7 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
 // stats16: the code statistics go to qcmax16 / dcmax16 (BF16 re-check codes of an E4M3 run)
 // Hc: BF16 [kp][16] slices of -h_j for the folded BF16 contraction (null: not folded)
 cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, void* Hc, float* h,
-                           float* sc, cudaStream_t s, bool stats16 = false);
+                           float* sc, float4* cst, cudaStream_t s, bool stats16 = false);
 cudaError_t launch_assign_tc(const Problem& p, const TcLaunch& L, const TcParams& P, cudaStream_t s);
 cudaError_t init_assign_tc();
 // fold: -h_j folded into the contraction (a 32-byte slice per B stage row; A: a constant slice (BF16) or a

@@ -155,11 +155,14 @@ __global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C,
 // |h - h1 - h2 - h3| <= 2^-27 h) and zeros, so that the contraction against a
 // slice of ones yields x.c_j - h_j in the accumulator; a padding row holds
 // -inf there (score +inf).
+// cst[j] = (h_j, ||c~_j||, ||c_j||, ||c~_j - c_j||): the per-centroid terms of
+// the assignment's error bound, the same values whose maxima the step records
+// (h_j as the scores use it, the norms rounded up); zeros for padding rows.
 template <int MODE>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
                __nv_bfloat16* __restrict__ Hc, float* __restrict__ hq, float* __restrict__ scq,
-               int32_t* __restrict__ counts, Ctl* ctl, int stats16) {
+               float4* __restrict__ cst, int32_t* __restrict__ counts, Ctl* ctl, int stats16) {
   constexpr int FP8 = MODE == 1;
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
@@ -176,6 +179,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       if (lane == 0) {
         hq[j] = INFINITY;
         scq[j] = 1.f;
+        cst[j] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       continue;
     }
@@ -225,6 +229,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
       hq[j] = h;
       scq[j] = sc;
+      cst[j] = make_float4(h, qn, cn, dn);
       if (counts) counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
       atomic_max_nonneg(&ctl->cmax_bits, cn);
@@ -258,22 +263,22 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
 }
 
 cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, int Kp, uint8_t* Cq, void* Hc, float* h,
-                           float* sc, cudaStream_t s, bool stats16) {
+                           float* sc, float4* cst, cudaStream_t s, bool stats16) {
   __nv_bfloat16* hc = mode != 2 ? reinterpret_cast<__nv_bfloat16*>(Hc) : nullptr;
   int32_t* counts = stats16 ? nullptr : p.counts;  // the re-check codes leave the counts alone
   int blocks = (kp + 7) / 8;
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (mode == 2) {
-    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
   } else if (mode == 1) {
     const int64_t kd = (int64_t)p.k * p.d;
     int mb = (int)((kd + 255) / 256);
     if (mb > num_sms() * 4) mb = num_sms() * 4;
     camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, w.ctl);
-    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
   } else {
-    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, counts, w.ctl, stats16);
+    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
   }
   return cudaGetLastError();
 }

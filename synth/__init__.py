@@ -101,6 +101,14 @@ def mixture(seed: int, n: int, d: int, m: int, R: float, sigma: float, *,
     return (out, comp) if with_comp else out
 
 
+def multiscale_mixture(seed: int, n: int, d: int, m: int, R: float, sigma: float, span_log2: float):
+    """The seeded mixture with component c (means and spread) scaled by 2^(-span_log2 c / (m - 1)),
+    so that the component means' norms span a factor 2^span_log2; float32 (n, d)."""
+    X, comp = mixture(seed, n, d, m, R, sigma, with_comp=True)
+    f = np.exp2(-span_log2 * comp.astype(np.float64) / max(m - 1, 1)).astype(np.float32)
+    return np.ascontiguousarray(X * f[:, None])
+
+
 def instance_shape(seed: int):
     n, d, k = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
     _load().synth_instance_shape(seed, ctypes.byref(n), ctypes.byref(d), ctypes.byref(k))
