@@ -294,6 +294,7 @@ struct RowErr {
   float a0, a1, a2, a3, ks;
   float U;    // running upper bound of the row's exact minimum score
   float Lev;  // smallest lower bound dropped from a full candidate list (+inf: none)
+  bool perc;  // per-centroid bounds this step (else the step maxima, candidates within the margin of the best)
   __device__ __forceinline__ float errv(float h, float q, float c, float dc) const {
     return fmaf(a0, h, fmaf(a1, q, fmaf(a2, c, a3 * dc))) * ks;
   }
@@ -304,11 +305,13 @@ struct RowErr {
 };
 
 // Folds a 32-column score block into the row's candidate list: the columns
-// within min(thr, mn + margin) of the block minimum mn (a superset of those
-// whose lower bound can end below U), in index order; each gets its own error
-// bound e_j, tightens U, and enters the list (ordered by lower bound) while
-// its lower bound is <= U. thr = U + margin / 2 >= U + e_j for every j. NEG:
-// the block holds accumulator bits whose negation is the score (folded BF16).
+// within min(thr, mn + margin) of the block minimum mn, in index order. With
+// per-centroid bounds (a superset of the columns whose lower bound can end
+// below U) each gets its own error bound e_j, tightens U, and enters the list
+// (ordered by lower bound) while its lower bound is <= U; thr = U + margin / 2
+// >= U + e_j for every j. Otherwise the list holds the smallest scores and thr =
+// best + margin. NEG: the block holds accumulator bits whose negation is the
+// score (folded BF16).
 template <bool NEG = false, typename T>
 __device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], float mn, int j0, float& thr,
                                            float margin, RowErr& re) {
@@ -330,7 +333,10 @@ __device__ __forceinline__ void fold_block(Cand (&top)[kT], const T (&s)[32], fl
     for (int u = 0; u < 4; ++u) x4[u] = (t & 4) ? x8[2 * u + 1] : x8[2 * u];
     const float x2a = (t & 8) ? x4[1] : x4[0], x2b = (t & 8) ? x4[3] : x4[2];
     const float v = (t & 16) ? x2b : x2a;
-    if (v <= thr) {
+    if (v <= thr && !re.perc) {
+      cand_insert(top, v, j0 + t);
+      thr = fminf(thr, __fadd_ru(top[0].v, margin));
+    } else if (v <= thr) {
       const float ej = re.err(j0 + t);
       re.U = fminf(re.U, __fadd_ru(v, ej));
       thr = fminf(thr, __fadd_ru(re.U, 0.5f * margin));
@@ -721,6 +727,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
     Item it;
     it.b = -1;
     float H = 0.f, Cmax = 0.f, QCmax = 0.f, DCmax = 0.f;  // per-step maxima of the instance
+    bool perc = false;                                    // per-centroid error bounds this step
     float csc = 1.f;                                      // the instance's centroid code scale (E4M3)
     RowMeta nxt;
     bool have_nxt = false;
@@ -741,6 +748,9 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         if (!it.skip) {
           const Ctl* ctl = it.ctl;
           H = __uint_as_float(ctl->hmax_bits);
+          // per-centroid bounds pay when the centroids' h_j spread over more than a factor 64 (norms 8):
+          // below that their candidate-by-candidate evaluation costs more than the re-checks it saves
+          perc = H > 64.f * __uint_as_float(0x7f800000u - ctl->hmin_neg);
           Cmax = __uint_as_float(ctl->cmax_bits);
           QCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->qcmax16_bits : ctl->qcmax_bits);
           DCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->dcmax16_bits : ctl->dcmax_bits);
@@ -789,6 +799,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       re.ks = (1.f + 0x1p-10f) * (FP8 && FOLD ? __frcp_rn(xs.x * csc) : 1.f);
       re.U = INFINITY;
       re.Lev = INFINITY;
+      re.perc = perc;
       const float margin = 2.f * re.errv(H, QCmax, Cmax, DCmax);
       float thr = FLT_MAX;  // finite: padding columns (score +inf) never become candidates
       if (ok && P.debug_stall && !__all_sync(0xffffffffu, mbar_wait(&never_bar, 0, &abort_s, P.wait_ns))) ok = false;
@@ -869,7 +880,7 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
       {  // warp-uniform: the flag slots are reserved once per warp
         const bool live = ok && valid;
         int nc = -1;  // -1: final; 0: all k; >0: candidate count
-        if (live) {
+        if (live && perc) {
           // the candidates: the list's prefix with lower bound <= U (ordered by lower bound); a
           // dropped entry that qualifies too means the list cannot hold them all
           int cnt = 0;
@@ -877,6 +888,16 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           for (int t = 0; t < kT; ++t) cnt += (top[t].i >= 0 && top[t].v <= re.U) ? 1 : 0;
           if (cnt == 0 || re.Lev <= re.U) nc = 0;
           else if (cnt > 1) nc = cnt;
+        } else if (live) {  // the scores within the margin of the best
+          if (top[0].i < 0) {
+            nc = 0;
+          } else {
+            int cnt = 1;
+#pragma unroll
+            for (int t = 1; t < kT; ++t) cnt += (top[t].i >= 0 && __fsub_rn(top[t].v, top[0].v) <= margin) ? 1 : 0;
+            if (cnt == kT) nc = 0;  // maybe more than kT within the margin
+            else if (cnt > 1) nc = cnt;
+          }
         }
         const bool flag = live && nc >= 0;
         const unsigned fm = __ballot_sync(0xffffffffu, flag);

@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
       W.cst[g] = make_float4(h, qn, cn, dn);
       I.counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
+      if (h >= 0.f && h < INFINITY) atomicMax(&ctl->hmin_neg, 0x7f800000u - __float_as_uint(h));
       atomic_max_nonneg(&ctl->cmax_bits, cn);
       atomic_max_nonneg(&ctl->qcmax_bits, qn);
       atomic_max_nonneg(&ctl->dcmax_bits, dn);

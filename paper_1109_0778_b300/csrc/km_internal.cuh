@@ -30,6 +30,8 @@ struct Ctl {
   unsigned long long shift2_bits;  // max_j ||dc_j||^2 as FP64 bits (>= 0)
   unsigned int cmax_bits;          // max_j ||c_j|| (FP32 bits, rounded up)
   unsigned int hmax_bits;          // max_j h_j = max_j ||c_j||^2 / 2
+  unsigned int hmin_neg;           // min_j h_j of the quantised paths as 0x7f800000 - its bits (an atomicMax
+                                   // of the complement; 0: none recorded)
   unsigned int qcmax_bits;         // max_j ||c~_j|| of the quantised centroids (rounded up)
   unsigned int dcmax_bits;         // max_j ||c~_j - c_j|| (quantisation residual, rounded up)
   unsigned int camax_bits;         // max_{j,t} |c_jt| (FP32 bits): sets the E4M3 centroid scale

@@ -232,6 +232,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       cst[j] = make_float4(h, qn, cn, dn);
       if (counts) counts[j] = 0;
       atomic_max_nonneg(&ctl->hmax_bits, h);
+      if (h >= 0.f && h < INFINITY) atomicMax(&ctl->hmin_neg, 0x7f800000u - __float_as_uint(h));
       atomic_max_nonneg(&ctl->cmax_bits, cn);
       atomic_max_nonneg(stats16 ? &ctl->qcmax16_bits : &ctl->qcmax_bits, qn);
       atomic_max_nonneg(stats16 ? &ctl->dcmax16_bits : &ctl->dcmax_bits, dn);
