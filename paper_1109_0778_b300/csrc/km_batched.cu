@@ -195,24 +195,73 @@ __device__ __forceinline__ int b_settle(const BWork& W, const FlagRec& rec, cons
                         __uint_as_float(W.ctls[b].cmax_bits));
 }
 
-__global__ void __launch_bounds__(256) b_recheck_kernel(BWork W) {
+// Short candidate lists: points of d <= 32 V by groups of G lanes (group_settle),
+// 32 / G points at a time.
+template <int G, int F>
+__device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sm, const FlagRec& r, int lane) {
+  const int g = lane / G, sub = lane % G;
+  while (sm) {  // warp-uniform
+    const int src = nth_set_bit(sm, g);
+    const int from = src < 0 ? __ffs(sm) - 1 : src;  // (a group without a point repeats the first one)
+    const int ri = __shfl_sync(0xffffffffu, r.i, from), rnc = __shfl_sync(0xffffffffu, r.nc, from);
+    const int rold = __shfl_sync(0xffffffffu, r.old, from), b = __shfl_sync(0xffffffffu, r.pad, from);
+    int cand[kMaxCand];
+#pragma unroll
+    for (int a = 0; a < kMaxCand; ++a) cand[a] = __shfl_sync(0xffffffffu, r.cand[a], from);
+    const BInst& I = W.inst[b];
+    const int ncw = __reduce_max_sync(0xffffffffu, src >= 0 ? rnc : 0);
+    const int jb = group_settle<G, F>(I.X + (int64_t)ri * I.d, I.C, I.d, rnc, ncw, cand, sub);
+    if (src >= 0 && sub == 0) {
+      I.assign[ri] = jb;
+      if (rold != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
+    }
+    for (int a = 0; a < 32 / G && sm; ++a) sm &= sm - 1;  // the points of this round
+  }
+}
+
+// A warp takes 32 flags at a time (nwarps apart); lane l loads flag l's record.
+// Short lists go to b_settle_short, the points to check against all k are
+// settled one at a time by the whole warp (b_settle).
+__global__ void __launch_bounds__(256, 2) b_recheck_kernel(BWork W) {
   __shared__ __align__(16) float xs_all[8][kMaxV * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* xsh = xs_all[wib];
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
   const int64_t nflag = min((int64_t)*W.flag_slots, W.R);
-  for (int64_t f = warp; f < nflag; f += nwarps) {
-    const FlagRec rec = W.flags[f];
-    const int b = rec.pad;
-    if (halted(W.ctls + b)) continue;
-    const BInst& I = W.inst[b];
-    const int d = I.d;
-    const int jb = d <= 32 ? b_settle<1>(W, rec, I, b, xsh, lane)
-                           : (d <= 64 ? b_settle<2>(W, rec, I, b, xsh, lane) : b_settle<kMaxV>(W, rec, I, b, xsh, lane));
-    if (lane == 0) {
-      I.assign[rec.i] = jb;
-      if (rec.old != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
+  for (int64_t f0 = warp; f0 < nflag; f0 += nwarps * 32) {
+    const int64_t fl = f0 + lane * nwarps;
+    bool have = fl < nflag;
+    FlagRec r;
+    r.i = 0;
+    r.nc = 0;
+    r.old = -1;
+    r.pad = 0;
+#pragma unroll
+    for (int a = 0; a < kMaxCand; ++a) r.cand[a] = 0;
+    int d = 0;
+    if (have) {
+      r = W.flags[fl];
+      have = !halted(W.ctls + r.pad);
+      d = W.inst[r.pad].d;
+    }
+    const bool shortl = have && r.nc > 0;
+    b_settle_short<8, 1>(W, __ballot_sync(0xffffffffu, shortl && d <= 32), r, lane);
+    b_settle_short<16, 2>(W, __ballot_sync(0xffffffffu, shortl && d > 32), r, lane);  // d <= 128
+    unsigned todo = __ballot_sync(0xffffffffu, have && !shortl);
+    while (todo) {
+      const int l = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const FlagRec rec = W.flags[f0 + l * nwarps];
+      const int b = rec.pad;
+      const BInst& I = W.inst[b];
+      const int jb = I.d <= 32 ? b_settle<1>(W, rec, I, b, xsh, lane)
+                               : (I.d <= 64 ? b_settle<2>(W, rec, I, b, xsh, lane)
+                                            : b_settle<kMaxV>(W, rec, I, b, xsh, lane));
+      if (lane == 0) {
+        I.assign[rec.i] = jb;
+        if (rec.old != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
+      }
     }
   }
 }
@@ -662,7 +711,7 @@ cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s) {
 }
 
 cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
-  b_recheck_kernel<<<num_sms() * 4, 256, 0, s>>>(W);  // latency-bound: as many warps as are resident (64 registers)
+  b_recheck_kernel<<<num_sms() * 2, 256, 0, s>>>(W);  // every CTA resident (two per SM)
   return cudaGetLastError();
 }
 

@@ -1,9 +1,11 @@
 // Exact re-check of flagged near-ties with compensated FP32 distances.
 //
-// One warp per flagged point. A short candidate list (kept by the assignment
-// stage) is evaluated directly; otherwise all k centroids are screened with
-// plain FP32 scores and a rigorous bound first (km_recheck.cuh). The
-// distances, the tie rule and the error argument are those of km_recheck.cuh.
+// A warp takes 32 flagged points at a time. Each lane settles its own point
+// when the assignment stage kept a short candidate list (lane_settle); the
+// points it could not narrow are queued for the re-score pass or, failing
+// that, screened against all k centroids one at a time by the whole warp
+// (nearest_all). The distances, the tie rule and the error argument are those
+// of km_recheck.cuh.
 #include <functional>
 
 #include "km_quant.cuh"
@@ -14,7 +16,7 @@ namespace km {
 namespace {
 
 template <int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, const float* __restrict__ h, int k,
                const FlagRec* __restrict__ flags, const unsigned long long* nflag_ptr, Ctl* ctl,
                int32_t* __restrict__ assign, int32_t* __restrict__ q_rows, int32_t* __restrict__ q_old,
@@ -35,10 +37,17 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
     const int64_t fl = f0 + lane * nwarps;
     const bool have = fl < nflag;
     int nc_l = -1, i_l = 0, old_l = 0;
+    int cand_l[kMaxCand];
     if (have) {
-      nc_l = flags[fl].nc;
-      i_l = flags[fl].i;
-      old_l = flags[fl].old;
+      const FlagRec r = flags[fl];
+      nc_l = r.nc;
+      i_l = r.i;
+      old_l = r.old;
+#pragma unroll
+      for (int a = 0; a < kMaxCand; ++a) cand_l[a] = r.cand[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < kMaxCand; ++a) cand_l[a] = 0;
     }
     unsigned todo = __ballot_sync(0xffffffffu, have);
     if (q_rows) {
@@ -57,38 +66,49 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
         todo &= ~__ballot_sync(0xffffffffu, queued);
       }
     }
+    // short candidate lists: a group of G lanes per point, 32 / G points at a time (group_settle)
+    unsigned sm = __ballot_sync(0xffffffffu, ((todo >> lane) & 1u) && nc_l > 0);
+    todo &= ~sm;
+    constexpr int G = V <= 1 ? 8 : 16;  // lanes per point: 4 or 2 points per round
+    constexpr int F = (V * 8 + G - 1) / G;  // float4 slices of the point per lane (16 G F >= 32 V >= d)
+    const int g = lane / G, sub = lane % G;
+    while (sm) {  // warp-uniform
+      const int src = nth_set_bit(sm, g);
+      const int from = src < 0 ? __ffs(sm) - 1 : src;  // (a group without a point repeats the first one)
+      const int ri = __shfl_sync(0xffffffffu, i_l, from), rnc = __shfl_sync(0xffffffffu, nc_l, from);
+      const int rold = __shfl_sync(0xffffffffu, old_l, from);
+      int cand[kMaxCand];
+#pragma unroll
+      for (int a = 0; a < kMaxCand; ++a) cand[a] = __shfl_sync(0xffffffffu, cand_l[a], from);
+      const int ncw = __reduce_max_sync(0xffffffffu, src >= 0 ? rnc : 0);
+      const int jb = group_settle<G, F>(X + (int64_t)ri * d, C, d, rnc, ncw, cand, sub);
+      if (src >= 0 && sub == 0) {
+        assign[ri] = jb;
+        changed += (rold != jb);
+      }
+      for (int a = 0; a < 32 / G && sm; ++a) sm &= sm - 1;  // the points of this round
+    }
+    // the rest (all k candidates, not queued): one point at a time, lanes over dimensions
     while (todo) {
       const int l = __ffs(todo) - 1;
       todo &= todo - 1;
-      const FlagRec rec = flags[f0 + l * nwarps];
-      const float* x = X + (int64_t)rec.i * d;
+      const int ri = __shfl_sync(0xffffffffu, i_l, l), rold = __shfl_sync(0xffffffffu, old_l, l);
+      const float* x = X + (int64_t)ri * d;
       float xv[V];
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         const int t = v * 32 + lane;
         xv[v] = t < d ? x[t] : 0.f;
       }
-      int jb;
-      if (rec.nc > 0) {
-        float best = INFINITY;
-        jb = rec.cand[0];
-        for (int q = 0; q < rec.nc; ++q) {
-          const int j = rec.cand[q];
-          const float D = warp_sqdist<V>(xv, C + (int64_t)j * d, d, lane);
-          if (D < best) {  // candidates arrive in increasing index order
-            best = D;
-            jb = j;
-          }
-        }
-      } else {
-        jb = nearest_all<V>(xv, xsh, C, h, k, d, lane, H, Cmax);
-      }
+      const int jb = nearest_all<V>(xv, xsh, C, h, k, d, lane, H, Cmax);
       if (lane == 0) {
-        assign[rec.i] = jb;
-        changed += (rec.old != jb);
+        assign[ri] = jb;
+        changed += (rold != jb);
       }
     }
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) changed += __shfl_xor_sync(0xffffffffu, changed, o);  // (every lane counted its own)
   if (lane == 0 && changed) atomicAdd(&ctl->n_changed, (unsigned long long)changed);
 }
 
@@ -136,7 +156,7 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
 template <int V>
 cudaError_t recheck_v(const Problem& p, const Work& w, const float* h, const FlagRec* flags,
                       const unsigned long long* nflag, bool queue, cudaStream_t s) {
-  const int blocks = num_sms() * 4;  // latency-bound: as many warps as are resident (4 CTAs at 64 registers)
+  const int blocks = num_sms() * 2;  // every CTA resident (two per SM at up to 128 registers)
   recheck_kernel<V><<<blocks, 256, 0, s>>>(p.X, p.d, p.C, h, p.k, flags, nflag, w.ctl, p.assign,
                                            queue ? w.fq_rows : nullptr, queue ? w.fq_old : nullptr,
                                            queue ? w.fq_cap : 0);

@@ -49,6 +49,87 @@ __device__ __forceinline__ float warp_sqdist(const float (&xv)[V], const float* 
   return __fadd_rn(hi, lo);
 }
 
+// Settles one point in a group of G lanes (G a power of two, the group
+// aligned to G lanes; sub = lane % G) between nc >= 1 candidates (ascending
+// indices cand[0..nc)), d <= 16 G F. Lane sub holds coordinates 4 (f G + sub)
+// .. + 3 for f < F (a group's loads cover 16 G contiguous bytes) of the point
+// in registers; the candidates are taken four at a time, all their slices
+// loaded before any arithmetic, so a short list costs about one round trip to
+// memory per four candidates. For every coordinate the difference and its
+// square are rounded once each and added in a Kahan pair per candidate (the
+// lane's coordinates in order), and the G pairs are combined with TwoSum
+// (error ~5u of the sum, the accuracy of warp_sqdist). ncw = the largest nc
+// over the warp (the loop bound, so that every lane takes part in the
+// shuffles). Equal distances go to the lower index. Every lane of the group
+// returns the same index.
+template <int G, int F>
+__device__ __forceinline__ int group_settle(const float* __restrict__ x, const float* __restrict__ C, int d, int nc,
+                                            int ncw, const int (&cand)[kMaxCand], int sub) {
+  const bool vec = (d & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(C)) & 15) == 0;
+  auto load4 = [&](const float* p, int t, bool ok) -> float4 {
+    if (!ok || t >= d) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vec) return __ldg(reinterpret_cast<const float4*>(p + t));
+    return make_float4(__ldg(p + t), t + 1 < d ? __ldg(p + t + 1) : 0.f, t + 2 < d ? __ldg(p + t + 2) : 0.f,
+                       t + 3 < d ? __ldg(p + t + 3) : 0.f);
+  };
+  float4 xv[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) xv[f] = load4(x, 4 * (f * G + sub), true);
+  float best = INFINITY;
+  int jb = cand[0];
+  for (int q0 = 0; q0 < ncw; q0 += 4) {
+    int jq[4];
+    float4 cv[4][F];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      jq[u] = cand[0];
+#pragma unroll
+      for (int a = 0; a < kMaxCand; ++a)
+        if (a == q0 + u) jq[u] = cand[a];
+      const float* c = C + (int64_t)jq[u] * d;
+#pragma unroll
+      for (int f = 0; f < F; ++f) cv[u][f] = load4(c, 4 * (f * G + sub), q0 + u < nc);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float sq = 0.f, cp = 0.f;
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        float df = __fsub_rn(xv[f].x, cv[u][f].x);
+        kahan_add(sq, cp, __fmul_rn(df, df));
+        df = __fsub_rn(xv[f].y, cv[u][f].y);
+        kahan_add(sq, cp, __fmul_rn(df, df));
+        df = __fsub_rn(xv[f].z, cv[u][f].z);
+        kahan_add(sq, cp, __fmul_rn(df, df));
+        df = __fsub_rn(xv[f].w, cv[u][f].w);
+        kahan_add(sq, cp, __fmul_rn(df, df));
+      }
+      float hi = sq, lo = -cp;  // the lane's pair s - c as (hi, lo)
+#pragma unroll
+      for (int o = G >> 1; o; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float sh, e;
+        two_sum(hi, ohi, sh, e);
+        lo = __fadd_rn(__fadd_rn(lo, olo), e);
+        hi = sh;
+      }
+      const float D = __fadd_rn(hi, lo);
+      if (q0 + u < nc && D < best) {  // candidates in increasing index order: strict < keeps the lower index
+        best = D;
+        jb = jq[u];
+      }
+    }
+  }
+  return jb;
+}
+
+// Index of the n-th (0-based) set bit of m, or -1.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  for (int i = 0; i < n && m; ++i) m &= m - 1;
+  return m ? __ffs(m) - 1 : -1;
+}
+
 // Keeps a lane's three smallest (score, index) pairs; indices arrive in
 // increasing order, so strict comparisons keep the lower index first.
 struct Top3 {
