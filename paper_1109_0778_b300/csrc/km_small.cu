@@ -93,6 +93,7 @@ struct SmallArgs {
   int first;    // no previous labels (the first step counts every point as changed)
   int recheck;  // 0: keep the FP32 argmin of the scores
   int T;        // lanes per point
+  int stall;    // test knob: the first grid barrier waits for one CTA more than the grid has (it expires)
   Work w;
   char* scr;
 };
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_run_kernel(SmallArgs A
     }
     __syncthreads();
     if (tid == 0 && nonfinite_s) atomicCAS(&scr->error, 0, (int)KM_ENONFINITE);
-    if (!(ok = grid_barrier(scr, G))) break;
+    if (!(ok = grid_barrier(scr, G + (it == 0 ? A.stall : 0)))) break;
 
     // ---------------------------------------------------------------- reduce + divide (owners)
     if (cta == 0 && tid == 0) {  // the previous step's counters (every CTA read them before the barrier)
@@ -534,7 +535,7 @@ cudaError_t launch_small_run(const Problem& p, const Work& w, int iters, double 
                              cudaStream_t s) {
   const int G = small_ctas(p.n, p.k);
   SmallArgs A{p.X, p.n, p.d, p.k, p.C, p.assign, p.sums, p.counts, iters, tol, first, recheck,
-              small_lanes(p.n, p.k), w, reinterpret_cast<char*>(w.small)};
+              small_lanes(p.n, p.k), getenv("KM_DEBUG_STALL") ? 1 : 0, w, reinterpret_cast<char*>(w.small)};
   const SmallLayout L(G, p.d, p.k);
   cudaError_t e = cudaMemsetAsync(w.small, 0, L.part, s);  // header and tickets
   if (e != cudaSuccess) return e;
