@@ -51,7 +51,7 @@ __device__ __forceinline__ float warp_sqdist(const float (&xv)[V], const float* 
 
 // Settles one point in a group of G lanes (G a power of two, the group
 // aligned to G lanes; sub = lane % G) between nc >= 1 candidates (ascending
-// indices cand[0..nc)), d <= 16 G F. Lane sub holds coordinates 4 (f G + sub)
+// indices cand[0..nc)), d <= 4 G F. Lane sub holds coordinates 4 (f G + sub)
 // .. + 3 for f < F (a group's loads cover 16 G contiguous bytes) of the point
 // in registers; the candidates are taken four at a time, all their slices
 // loaded before any arithmetic, so a short list costs about one round trip to
