@@ -69,7 +69,7 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
     // short candidate lists: a group of G lanes per point, 32 / G points at a time (group_settle)
     unsigned sm = __ballot_sync(0xffffffffu, ((todo >> lane) & 1u) && nc_l > 0);
     todo &= ~sm;
-    constexpr int G = V <= 4 ? 8 : 16;  // lanes per point: 4 points per round for d <= 128, else 2
+    constexpr int G = 8;                    // lanes per point: 4 points per round
     constexpr int F = (V * 8 + G - 1) / G;  // float4 slices of the point per lane (4 G F >= 32 V >= d)
     const int g = lane / G, sub = lane % G;
     while (sm) {  // warp-uniform

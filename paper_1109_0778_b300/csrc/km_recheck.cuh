@@ -53,16 +53,16 @@ __device__ __forceinline__ float warp_sqdist(const float (&xv)[V], const float* 
 // aligned to G lanes; sub = lane % G) between nc >= 1 candidates (ascending
 // indices cand[0..nc)), d <= 4 G F. Lane sub holds coordinates 4 (f G + sub)
 // .. + 3 for f < F (a group's loads cover 16 G contiguous bytes) of the point
-// in registers; the candidates are taken four at a time, all their slices
-// loaded before any arithmetic, so a short list costs about one round trip to
-// memory per four candidates. For every coordinate the difference and its
+// in registers; the candidates are taken NQ at a time (four, or two when the
+// slices are long), all their slices loaded before any arithmetic, so a short
+// list costs about one round trip to memory per NQ candidates. For every coordinate the difference and its
 // square are rounded once each and added in a Kahan pair per candidate (the
 // lane's coordinates in order), and the G pairs are combined with TwoSum
 // (error ~5u of the sum, the accuracy of warp_sqdist). ncw = the largest nc
 // over the warp (the loop bound, so that every lane takes part in the
 // shuffles). Equal distances go to the lower index. Every lane of the group
 // returns the same index.
-template <int G, int F>
+template <int G, int F, int NQ = (F <= 4 ? 4 : 2)>
 __device__ __forceinline__ int group_settle(const float* __restrict__ x, const float* __restrict__ C, int d, int nc,
                                             int ncw, const int (&cand)[kMaxCand], int sub) {
   const bool vec = (d & 3) == 0 && ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(C)) & 15) == 0;
@@ -77,11 +77,11 @@ __device__ __forceinline__ int group_settle(const float* __restrict__ x, const f
   for (int f = 0; f < F; ++f) xv[f] = load4(x, 4 * (f * G + sub), true);
   float best = INFINITY;
   int jb = cand[0];
-  for (int q0 = 0; q0 < ncw; q0 += 4) {
-    int jq[4];
-    float4 cv[4][F];
+  for (int q0 = 0; q0 < ncw; q0 += NQ) {
+    int jq[NQ];
+    float4 cv[NQ][F];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NQ; ++u) {
       jq[u] = cand[0];
 #pragma unroll
       for (int a = 0; a < kMaxCand; ++a)
@@ -91,7 +91,7 @@ __device__ __forceinline__ int group_settle(const float* __restrict__ x, const f
       for (int f = 0; f < F; ++f) cv[u][f] = load4(c, 4 * (f * G + sub), q0 + u < nc);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < NQ; ++u) {
       float sq = 0.f, cp = 0.f;
 #pragma unroll
       for (int f = 0; f < F; ++f) {
