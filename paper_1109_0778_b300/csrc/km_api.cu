@@ -218,7 +218,7 @@ bool cold_bf16_first(int precision, int warm, int d, int k) {
 struct Layout {
   size_t ctl, xnorm, flags, perm, offs, cursor, sums64, chalf, cnorm, Csave, obj, shift, changed,
       flagged, full, empty, queued, Xq, xs, xs16, Cq, hq, scq, state, state3, xss, labs, fq_rows, fq_old, X_sub, xn_sub,
-      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, small, cst, cst16, total;
+      flags2, xq16, xs16q, cq16, hq16, scq16, hc, hc16, xh, pcounts, xmax, facc, oacc, small, cst, cst16, mu, total;
   int64_t fq_cap;
   int Kp16;  // BF16 code width of an E4M3 run's re-check codes (0: none)
 };
@@ -262,6 +262,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
     }
     L.Xq = take(xq);
     L.xs = take(16 * (size_t)n);
+    L.mu = take(4 * (size_t)d);  // the codes' centring vector (reused with them)
     L.xs16 = cold ? take(16 * (size_t)n) : 0;
     L.Cq = take(cq);
     // -h_j slices of the folded BF16 contraction (the main shape, or the BF16 first step of a cold call)
@@ -300,7 +301,7 @@ Layout layout_for(int64_t n, int k, int d, int iters, int precision, int warm, i
     L.hc = L.hc16 = L.xh = 0;
     L.Kp16 = 0;
     L.xq16 = L.xs16q = L.cq16 = L.hq16 = L.scq16 = L.cst = L.cst16 = 0;
-    L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = 0;
+    L.Xq = L.xs = L.xs16 = L.Cq = L.hq = L.scq = L.xss = L.mu = 0;
     const int width = simt_slab_width(d);
     L.state = (width > 0 && width < k) ? take(16 * (size_t)n) : 0;  // also serves the re-check pass
     if (width > 0) {
@@ -384,6 +385,7 @@ Work make_work(DevCtx* c, const Layout& L) {
   w.hq = L.hq ? (float*)(b + L.hq) : nullptr;
   w.scq = L.scq ? (float*)(b + L.scq) : nullptr;
   w.cst = L.cst ? (float4*)(b + L.cst) : nullptr;
+  w.mu = L.mu ? (float*)(b + L.mu) : nullptr;
   w.Hc = L.hc ? (void*)(b + L.hc) : nullptr;
   w.Xh = L.xh ? (void*)(b + L.xh) : nullptr;
   w.state = L.state ? (float4*)(b + L.state) : nullptr;
@@ -597,7 +599,7 @@ cudaError_t enqueue_step(const Problem& p, const Work& w, const StepCfg& cfg, in
         P.first = first;
         return launch_assign_tc(q, cfg.L16, P, st);
       };
-    if ((e = launch_recheck(p, w, tcp ? w.hq : w.chalf, first, s, tc16))) return e;
+    if ((e = launch_recheck(p, w, w.chalf, first, s, tc16))) return e;  // (uncentred h_j: it scores x itself)
   }
   if ((e = at(3))) return e;
   if ((e = launch_count(p, w, s))) return e;
@@ -857,13 +859,15 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   } else if (reuse) {
     // codes, row statistics, norms, sorted order and max ||x|| are those the previous call left
   } else if (o.precision != KM_FP32 && cfg.cold) {
+    KM_CUDA(launch_centre(p, w, s));
     KM_CUDA(launch_quant_x_dual(p, w, cfg.t0.Kp, w.Xq, w.xs16, w.xs, s));
   } else if (o.precision != KM_FP32) {
+    KM_CUDA(launch_centre(p, w, s));
     KM_CUDA(launch_quant_x(p, w, cfg.t.qmode(), cfg.t.Kp, w.Xq, w.xs, s));
   } else {
     KM_CUDA(launch_xnorm(p, w, s));
   }
-  if (!reuse && det) KM_CUDA(launch_xmax(o.precision == KM_FP32 ? w.xnorm : nullptr, w.xs, p.n, w, s));
+  if (!reuse && det) KM_CUDA(launch_xmax(w.xnorm, nullptr, p.n, w, s));  // (uncentred norms on every path)
   if (debug_sync()) {
     cudaError_t r = cudaStreamSynchronize(s);
     KM_TRACE("point quantisation / norms: %s\n", cudaGetErrorString(r));

@@ -47,7 +47,10 @@
 // final; otherwise its candidates (or, past 7 of them, all k) go to the FP32
 // re-check. On centroid sets of widely different norms the per-centroid terms
 // keep the candidates of rows near small centroids few where E_i, set by the
-// largest centroids, would flag them all.
+// largest centroids, would flag them all. Codes may be those of x - mu and
+// c - mu for a fixed centring vector mu (distances unchanged); every norm and
+// residual above is then that of the centred rows, and the centring's
+// rounding is inside the residual bounds the quantisation stages write.
 //
 // Threshold. Columns are examined only below thr = U + E_i (rounded up;
 // FLT_MAX before the first), a superset of the candidates, so a 32-column block
@@ -747,11 +750,11 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
         }
         if (!it.skip) {
           const Ctl* ctl = it.ctl;
-          H = __uint_as_float(ctl->hmax_bits);
+          H = __uint_as_float(ctl->hmax_c_bits);  // (the centred centroids' maxima)
           // per-centroid bounds pay when the centroids' h_j spread over more than a factor 64 (norms 8):
           // below that their candidate-by-candidate evaluation costs more than the re-checks it saves
           perc = H > 64.f * __uint_as_float(0x7f800000u - ctl->hmin_neg);
-          Cmax = __uint_as_float(ctl->cmax_bits);
+          Cmax = __uint_as_float(ctl->cmax_c_bits);
           QCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->qcmax16_bits : ctl->qcmax_bits);
           DCmax = __uint_as_float(!BATCH && P.stats16 ? ctl->dcmax16_bits : ctl->dcmax_bits);
           if (FP8) csc = __ldg(it.sc);  // the same for every centroid of the step

@@ -158,6 +158,8 @@ __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
       atomic_max_nonneg(&ctl->hmax_bits, h);
       if (h >= 0.f && h < INFINITY) atomicMax(&ctl->hmin_neg, 0x7f800000u - __float_as_uint(h));
       atomic_max_nonneg(&ctl->cmax_bits, cn);
+      atomic_max_nonneg(&ctl->hmax_c_bits, h);  // (batched codes are not centred)
+      atomic_max_nonneg(&ctl->cmax_c_bits, cn);
       atomic_max_nonneg(&ctl->qcmax_bits, qn);
       atomic_max_nonneg(&ctl->dcmax_bits, dn);
     }

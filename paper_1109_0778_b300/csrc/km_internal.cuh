@@ -30,6 +30,8 @@ struct Ctl {
   unsigned long long shift2_bits;  // max_j ||dc_j||^2 as FP64 bits (>= 0)
   unsigned int cmax_bits;          // max_j ||c_j|| (FP32 bits, rounded up)
   unsigned int hmax_bits;          // max_j h_j = max_j ||c_j||^2 / 2
+  unsigned int hmax_c_bits;        // the same two maxima of the centred centroids c_j - mu of the quantised
+  unsigned int cmax_c_bits;        //   paths (equal to hmax, cmax without centring)
   unsigned int hmin_neg;           // min_j h_j of the quantised paths as 0x7f800000 - its bits (an atomicMax
                                    // of the complement; 0: none recorded)
   unsigned int qcmax_bits;         // max_j ||c~_j|| of the quantised centroids (rounded up)
@@ -88,6 +90,7 @@ struct Work {
   float* hq;           // [kp] h_j of the quantised path (+inf for padding)
   float* scq;          // [kp] centroid code scales
   float4* cst;         // [kp] per-centroid error-bound terms of the codes (TcParams::cst)
+  float* mu;           // [d] centring vector of the quantised paths' codes (null: none)
   void* Hc;            // [kp][16] BF16 -h_j slices (folded contraction), null otherwise
   void* Xh;            // [n][16] BF16 [1/s_i, 1/s_i, 1/s_i, 0...] slices of a folded E4M3 contraction, in the
                        // codes' row order (null otherwise)
@@ -324,6 +327,8 @@ cudaError_t launch_divide(const Problem& p, const Work& w, int iter, double tol,
 // Small FP32 problems: every step of a call in one cooperative launch (km_small.cu)
 bool small_path_fits(int64_t n, int d, int k);
 size_t small_scratch_bytes(int64_t n, int d, int k);  // bytes of Work::small
+// The quantised paths' centring vector (mean of the call's initial centroids) into w.mu
+cudaError_t launch_centre(const Problem& p, const Work& w, cudaStream_t s);
 cudaError_t launch_small_run(const Problem& p, const Work& w, int iters, double tol, int first, int recheck,
                              cudaStream_t s);
 // max_i ||x_i|| bound into *w.xmax from per-point bounds (FP32 norms, or the .w of quantised row stats)

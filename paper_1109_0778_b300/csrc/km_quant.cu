@@ -25,37 +25,48 @@ namespace {
 
 // Xh (E4M3 with -h_j folded into the contraction; null otherwise): row i's
 // [1/s_i, 1/s_i, 1/s_i, 0, ...] slice (store_row_slice).
+// mu (null: no centring): the codes and statistics are those of the centred
+// rows (km_quant.cuh); xnorm[i] gets the bound of the uncentred ||x_i|| (the
+// FP32 consumers: re-check screen, deterministic grid).
 template <int FP8>
 __global__ void __launch_bounds__(256)
 quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
-               float4* __restrict__ xs, uint4* __restrict__ Xh, Ctl* ctl) {
+               float4* __restrict__ xs, uint4* __restrict__ Xh, const float* __restrict__ mu,
+               float* __restrict__ xnorm, Ctl* ctl) {
   constexpr int ESZ = FP8 ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ float mus[kMaxD];
+  stage_mu(mus, mu, d);
   for (int64_t i = warp; i < n; i += nwarps) {
     const float* x = X + i * d;
     float amax = 0.f;
     if (FP8)
-      for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
+      for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(__fsub_rn(x[t], mus[t])));
     const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
     const float inv = FP8 ? pow2_inv(sc) : 1.f;
-    float sxx = 0.f, sqq = 0.f, sdd = 0.f;
+    float sxx = 0.f, sqq = 0.f, sdd = 0.f, sraw = 0.f;
     uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
     for (int t = lane; t < Kp; t += 32) {
-      const float v = t < d ? x[t] : 0.f;
+      const float xt = t < d ? x[t] : 0.f;
+      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
       const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
       const float r = vq - v;
       sxx = fmaf(v, v, sxx);
       sqq = fmaf(vq, vq, sqq);
       sdd = fmaf(r, r, sdd);
+      sraw = fmaf(xt, xt, sraw);
     }
     sxx = warp_sum(sxx);
     sqq = warp_sum(sqq);
     sdd = warp_sum(sdd);
+    sraw = warp_sum(sraw);
     if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(sqq)) ctl->nonfinite = 1;
-      xs[i] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+      if (!isfinite(sxx) || !isfinite(sqq) || !isfinite(sraw)) ctl->nonfinite = 1;
+      const float nbv = norm_bound(sxx, d);
+      xs[i] = make_float4(sc, norm_bound(sqq, d), centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
+      if (xnorm) xnorm[i] = norm_bound(sraw, d);
       if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
     }
   }
@@ -66,31 +77,38 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
 // norms rounded up.
 __global__ void __launch_bounds__(256)
 quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
-                     float4* __restrict__ xs, Ctl* ctl) {
+                     float4* __restrict__ xs, const float* __restrict__ mu, float* __restrict__ xnorm, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ float mus[kMaxD];
+  stage_mu(mus, mu, d);
   for (int64_t i = warp; i < n; i += nwarps) {
     const float* x = X + i * d;
-    float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f;
+    float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f, sraw = 0.f;
     __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
     for (int t = lane; t < Kp; t += 32) {
-      const float v = t < d ? x[t] : 0.f;
+      const float xt = t < d ? x[t] : 0.f;
+      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
       float hi, lo;
       const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
       sxx = fmaf(v, v, sxx);
       shh = fmaf(hi, hi, shh);
       sll = fmaf(lo, lo, sll);
       sdd = fmaf(r, r, sdd);
+      sraw = fmaf(xt, xt, sraw);
     }
     sxx = warp_sum(sxx);
     shh = warp_sum(shh);
     sll = warp_sum(sll);
     sdd = warp_sum(sdd);
+    sraw = warp_sum(sraw);
     if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(shh)) ctl->nonfinite = 1;
-      xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)), norm_bound(sdd, d),
-                          norm_bound(sxx, d));
+      if (!isfinite(sxx) || !isfinite(shh) || !isfinite(sraw)) ctl->nonfinite = 1;
+      const float nbv = norm_bound(sxx, d);
+      xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)),
+                          centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
+      if (xnorm) xnorm[i] = norm_bound(sraw, d);
     }
   }
 }
@@ -100,20 +118,25 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
 // stage in sorted order).
 __global__ void __launch_bounds__(256)
 quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uint8_t* __restrict__ Xq,
-                    float4* __restrict__ xs16, float4* __restrict__ xs8, Ctl* ctl) {
+                    float4* __restrict__ xs16, float4* __restrict__ xs8, const float* __restrict__ mu,
+                    float* __restrict__ xnorm, Ctl* ctl) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ float mus[kMaxD];
+  stage_mu(mus, mu, d);
   for (int64_t i = warp; i < n; i += nwarps) {
     const float* x = X + i * d;
     float amax = 0.f;
-    for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(x[t]));
+    for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(__fsub_rn(x[t], mus[t])));
     const float sc8 = pow2_scale(warp_max(amax));
     const float inv8 = pow2_inv(sc8);
-    float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f;
+    float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f, sraw = 0.f;
     uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
     for (int t = lane; t < Kp16; t += 32) {
-      const float v = t < d ? x[t] : 0.f;
+      const float xt = t < d ? x[t] : 0.f;
+      sraw = fmaf(xt, xt, sraw);
+      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
       const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
       uint8_t dummy;
       const float q8 = quantise<1>(v, sc8, inv8, &dummy);
@@ -128,21 +151,26 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
     sdd16 = warp_sum(sdd16);
     sqq8 = warp_sum(sqq8);
     sdd8 = warp_sum(sdd8);
+    sraw = warp_sum(sraw);
     if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8)) ctl->nonfinite = 1;
-      const float xn = norm_bound(sxx, d);
-      xs16[i] = make_float4(1.f, norm_bound(sqq16, d), norm_bound(sdd16, d), xn);
-      xs8[i] = make_float4(sc8, norm_bound(sqq8, d), norm_bound(sdd8, d), xn);
+      if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8) || !isfinite(sraw)) ctl->nonfinite = 1;
+      const float nbv = norm_bound(sxx, d), xn = centred_norm(nbv, mu);
+      xs16[i] = make_float4(1.f, norm_bound(sqq16, d), centred_resid(nbv, norm_bound(sdd16, d), mu), xn);
+      xs8[i] = make_float4(sc8, norm_bound(sqq8, d), centred_resid(nbv, norm_bound(sdd8, d), mu), xn);
+      if (xnorm) xnorm[i] = norm_bound(sraw, d);
     }
   }
 }
 
 // max_{j,t} |c_jt| of the step's centroids into ctl->camax_bits.
-__global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C, int64_t kd, Ctl* ctl) {
+__global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C, int64_t kd, int d,
+                                                    const float* __restrict__ mu, Ctl* ctl) {
   if (halted(ctl)) return;
+  __shared__ float mus[kMaxD];
+  stage_mu(mus, mu, d);
   float m = 0.f;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < kd; e += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf(C[e]));
+    m = fmaxf(m, fabsf(mu ? __fsub_rn(C[e], mus[e % d]) : C[e]));
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomic_max_nonneg(&ctl->camax_bits, m);
 }
@@ -158,11 +186,16 @@ __global__ void __launch_bounds__(256) camax_kernel(const float* __restrict__ C,
 // cst[j] = (h_j, ||c~_j||, ||c_j||, ||c~_j - c_j||): the per-centroid terms of
 // the assignment's error bound, the same values whose maxima the step records
 // (h_j as the scores use it, the norms rounded up); zeros for padding rows.
+// mu (null: no centring): codes, h_j (hq, Hc), cst and the maxima hmax_c /
+// cmax_c / qcmax / dcmax are those of c_j - mu (h_j from the exact FP64
+// differences); chalf[j] (j < k) and hmax / cmax keep the uncentred h_j and
+// ||c_j|| bound for the FP32 consumers (re-check screen, deterministic grid).
 template <int MODE>
 __global__ void __launch_bounds__(256)
 quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_t* __restrict__ Cq,
                __nv_bfloat16* __restrict__ Hc, float* __restrict__ hq, float* __restrict__ scq,
-               float4* __restrict__ cst, int32_t* __restrict__ counts, Ctl* ctl, int stats16) {
+               float4* __restrict__ cst, const float* __restrict__ mu, float* __restrict__ chalf,
+               int32_t* __restrict__ counts, Ctl* ctl, int stats16) {
   constexpr int FP8 = MODE == 1;
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int W = MODE == 2 ? 2 : 1;  // code parts per element
@@ -171,6 +204,8 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  __shared__ float mus[kMaxD];
+  stage_mu(mus, mu, d);
   for (int j = warp; j < kp; j += nwarps) {
     uint8_t* row = Cq + (int64_t)j * W * Kp * ESZ;
     if (j >= k) {  // padding centroid: zero codes, score +inf
@@ -184,15 +219,23 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
       continue;
     }
     const float* c = C + (int64_t)j * d;
-    double s2 = 0.0;
-    for (int t = lane; t < d; t += 32) s2 = fma((double)c[t], (double)c[t], s2);
+    double s2 = 0.0, s2r = 0.0;  // ||c_j - mu||^2 (exact differences), ||c_j||^2
+    for (int t = lane; t < d; t += 32) {
+      const double e = (double)c[t] - (double)mus[t];
+      s2 = fma(e, e, s2);
+      s2r = fma((double)c[t], (double)c[t], s2r);
+    }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    for (int o = 16; o; o >>= 1) {
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      s2r += __shfl_xor_sync(0xffffffffu, s2r, o);
+    }
     const float sc = FP8 ? pow2_scale(__uint_as_float(ctl->camax_bits)) : 1.f;  // one scale for all centroids
     const float inv = FP8 ? pow2_inv(sc) : 1.f;
-    float sqq = 0.f, sll = 0.f, sdd = 0.f;
+    float sqq = 0.f, sll = 0.f, sdd = 0.f, svv = 0.f;
     for (int t = lane; t < Kp; t += 32) {
-      const float v = t < d ? c[t] : 0.f;
+      const float v = t < d ? __fsub_rn(c[t], mus[t]) : 0.f;
+      svv = fmaf(v, v, svv);
       if constexpr (MODE == 2) {
         __nv_bfloat16* r16 = reinterpret_cast<__nv_bfloat16*>(row);
         float hi, lo;
@@ -210,6 +253,7 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     sqq = warp_sum(sqq);
     if (MODE == 2) sll = warp_sum(sll);
     sdd = warp_sum(sdd);
+    svv = warp_sum(svv);
     if (fold) {  // -h_j (E4M3: -h_j / s_c, exact) as three BF16 parts (every lane computes h alike)
       const float h = __double2float_rn(0.5 * s2) * inv;
       const __nv_bfloat16 h1 = __float2bfloat16_rn(h);
@@ -224,23 +268,103 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
     if (lane == 0) {
       const float h = __double2float_rn(0.5 * s2);
       const float cn = __double2float_ru(sqrt(s2) * (1.0 + 1e-13));
+      const float hr = __double2float_rn(0.5 * s2r);
+      const float cnr = __double2float_ru(sqrt(s2r) * (1.0 + 1e-13));
       const float qn = MODE == 2 ? __fadd_ru(norm_bound(sqq, d), norm_bound(sll, d)) : norm_bound(sqq, d);
-      const float dn = norm_bound(sdd, d);
-      if (!isfinite(h) || !isfinite(cn) || !isfinite(qn)) ctl->nonfinite = 1;
+      const float dn = centred_resid(norm_bound(svv, d), norm_bound(sdd, d), mu);
+      if (!isfinite(h) || !isfinite(cn) || !isfinite(qn) || !isfinite(hr) || !isfinite(cnr)) ctl->nonfinite = 1;
       hq[j] = h;
       scq[j] = sc;
       cst[j] = make_float4(h, qn, cn, dn);
+      chalf[j] = hr;
       if (counts) counts[j] = 0;
-      atomic_max_nonneg(&ctl->hmax_bits, h);
+      atomic_max_nonneg(&ctl->hmax_bits, hr);
+      atomic_max_nonneg(&ctl->cmax_bits, cnr);
+      atomic_max_nonneg(&ctl->hmax_c_bits, h);
+      atomic_max_nonneg(&ctl->cmax_c_bits, cn);
       if (h >= 0.f && h < INFINITY) atomicMax(&ctl->hmin_neg, 0x7f800000u - __float_as_uint(h));
-      atomic_max_nonneg(&ctl->cmax_bits, cn);
       atomic_max_nonneg(stats16 ? &ctl->qcmax16_bits : &ctl->qcmax_bits, qn);
       atomic_max_nonneg(stats16 ? &ctl->dcmax16_bits : &ctl->dcmax_bits, dn);
     }
   }
 }
 
+constexpr int kCentreThreads = 512;
+
+// The centring vector of a call (one block): mu_t = RN(mean_j c_jt) over the
+// call's initial centroids (FP64 sums), kept only when it pays -- when the
+// centred centroids' largest norm is at most half the uncentred one (a common
+// offset of the data dominates its spread); otherwise mu = 0 (the codes of x
+// itself). Any fixed vector keeps every distance.
+__global__ void __launch_bounds__(kCentreThreads) centre_kernel(const float* __restrict__ C, int k, int d,
+                                                                float* __restrict__ mu) {
+  constexpr int NW = kCentreThreads / 32, V = kMaxD / 32;
+  __shared__ double part[NW][kMaxD];  // per-warp column sums, added in warp order
+  __shared__ float mus[kMaxD];
+  __shared__ double mx[2][NW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.0;
+  for (int j = warp; j < k; j += NW) {  // warp w: rows w, w + NW, ...; lane: columns lane + 32 v
+    const float* c = C + (int64_t)j * d;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = v * 32 + lane;
+      if (t < d) acc[v] += (double)__ldg(c + t);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) part[warp][v * 32 + lane] = acc[v];
+  __syncthreads();
+  for (int t = tid; t < d; t += kCentreThreads) {
+    double s = 0.0;
+    for (int w = 0; w < NW; ++w) s += part[w][t];
+    mus[t] = __double2float_rn(s / (double)k);
+  }
+  __syncthreads();
+  double m0 = 0.0, m1 = 0.0;  // max_j ||c_j||^2, max_j ||c_j - mu||^2
+  for (int j = warp; j < k; j += NW) {
+    const float* c = C + (int64_t)j * d;
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = v * 32 + lane;
+      if (t < d) {
+        const double x = (double)__ldg(c + t), e = x - (double)mus[t];
+        a = fma(x, x, a);
+        b = fma(e, e, b);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    m0 = fmax(m0, a);
+    m1 = fmax(m1, b);
+  }
+  if (lane == 0) {
+    mx[0][warp] = m0;
+    mx[1][warp] = m1;
+  }
+  __syncthreads();
+  double M0 = mx[0][0], M1 = mx[1][0];
+  for (int w = 1; w < NW; ++w) {
+    M0 = fmax(M0, mx[0][w]);
+    M1 = fmax(M1, mx[1][w]);
+  }
+  const bool keep = M1 <= 0.25 * M0;
+  for (int t = tid; t < d; t += kCentreThreads) mu[t] = keep ? mus[t] : 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_centre(const Problem& p, const Work& w, cudaStream_t s) {
+  if (!w.mu) return cudaSuccess;
+  centre_kernel<<<1, kCentreThreads, 0, s>>>(p.C, p.k, p.d, w.mu);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
                            cudaStream_t s) {
@@ -248,9 +372,10 @@ cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, ui
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
   uint4* xh = reinterpret_cast<uint4*>(w.Xh);
-  if (mode == 2) quant_x_split_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.ctl);
-  else if (mode == 1) quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, xh, w.ctl);
-  else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, nullptr, w.ctl);
+  if (mode == 2) quant_x_split_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.mu, w.xnorm, w.ctl);
+  else if (mode == 1)
+    quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, xh, w.mu, w.xnorm, w.ctl);
+  else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, nullptr, w.mu, w.xnorm, w.ctl);
   return cudaGetLastError();
 }
 
@@ -259,7 +384,7 @@ cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8
   int64_t blocks = (p.n + 7) / 8;
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
-  quant_x_dual_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.ctl);
+  quant_x_dual_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl);
   return cudaGetLastError();
 }
 
@@ -271,15 +396,18 @@ cudaError_t launch_quant_c(const Problem& p, const Work& w, int mode, int kp, in
   const int cap = num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (mode == 2) {
-    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
+    quant_c_kernel<2><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, w.mu, w.chalf, counts, w.ctl,
+                                             stats16);
   } else if (mode == 1) {
     const int64_t kd = (int64_t)p.k * p.d;
     int mb = (int)((kd + 255) / 256);
     if (mb > num_sms() * 4) mb = num_sms() * 4;
-    camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, w.ctl);
-    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
+    camax_kernel<<<mb, 256, 0, s>>>(p.C, kd, p.d, w.mu, w.ctl);
+    quant_c_kernel<1><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, w.mu, w.chalf, counts, w.ctl,
+                                             stats16);
   } else {
-    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, counts, w.ctl, stats16);
+    quant_c_kernel<0><<<blocks, 256, 0, s>>>(p.C, p.k, kp, p.d, Kp, Cq, hc, h, sc, cst, w.mu, w.chalf, counts, w.ctl,
+                                             stats16);
   }
   return cudaGetLastError();
 }

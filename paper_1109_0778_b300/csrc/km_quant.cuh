@@ -10,6 +10,27 @@
 
 namespace km {
 
+// Centring of the quantised paths: the codes are those of v = RN(x - mu_t)
+// (mu null: v = x), a translation that leaves every distance unchanged. The
+// rounding leaves |v - (x - mu_t)| <= kEu |v| (kEu >= u / (1 - u)), which the
+// row statistics add to the residual bound: ||v~ - (x - mu)|| <= ||v~ - v|| +
+// kEu ||v||, ||x - mu|| <= (1 + kEu) ||v||.
+constexpr float kEu = 0x1.000002p-24f;
+static __device__ __forceinline__ float centred(float x, const float* __restrict__ mu, int t) {
+  return mu ? __fsub_rn(x, __ldg(mu + t)) : x;
+}
+// Stages the centring vector in shared memory, zeros without one (x - 0 = x
+// exactly); every thread of the block calls it.
+static __device__ __forceinline__ void stage_mu(float* mus, const float* __restrict__ mu, int d) {
+  for (int t = threadIdx.x; t < d; t += blockDim.x) mus[t] = mu ? __ldg(mu + t) : 0.f;
+  __syncthreads();
+}
+// Residual and norm bounds of a centred row from nb(sum v^2) and nb(sum (v~ - v)^2).
+static __device__ __forceinline__ float centred_resid(float nbv, float nbd, bool c) {
+  return c ? __fmaf_ru(kEu, nbv, nbd) : nbd;
+}
+static __device__ __forceinline__ float centred_norm(float nbv, bool c) { return c ? __fmul_ru(nbv, 1.f + kEu) : nbv; }
+
 static __device__ __forceinline__ float pow2_scale(float amax) {
   if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
   int e;

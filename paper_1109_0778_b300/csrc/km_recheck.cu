@@ -118,10 +118,10 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
 // zero padded) and their statistics (1, ||x~||, ||x~ - x||, ||x||) for the
 // tensor-core re-score, as the BF16 quantisation stage does.
 __global__ void __launch_bounds__(256)
-gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict__ xs,
-                    const float* __restrict__ xnorm, const Ctl* ctl, const int32_t* __restrict__ q_rows,
-                    int64_t q_cap, float* __restrict__ X_sub, float* __restrict__ xn_sub, uint8_t* __restrict__ Xq16,
-                    float4* __restrict__ xs16q, int Kp16) {
+gather_queue_kernel(const float* __restrict__ X, int d, const float* __restrict__ xnorm, const Ctl* ctl,
+                    const int32_t* __restrict__ q_rows, int64_t q_cap, float* __restrict__ X_sub,
+                    float* __restrict__ xn_sub, uint8_t* __restrict__ Xq16, float4* __restrict__ xs16q, int Kp16,
+                    const float* __restrict__ mu) {
   if (halted(ctl)) return;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -132,12 +132,12 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
     const float* x = X + i * d;
     float* y = X_sub + r * d;
     for (int t = lane; t < d; t += 32) y[t] = x[t];
-    if (lane == 0) xn_sub[r] = xs ? xs[i].w : xnorm[i];
-    if (Xq16) {
+    if (lane == 0) xn_sub[r] = xnorm[i];  // the uncentred norm bound (the FP32 pass scores x itself)
+    if (Xq16) {  // the BF16 codes of the centred row, as the quantisation stage forms them
       float sxx = 0.f, sqq = 0.f, sdd = 0.f;
       uint8_t* row = Xq16 + r * (int64_t)Kp16 * 2;
       for (int t = lane; t < Kp16; t += 32) {
-        const float v = t < d ? x[t] : 0.f;
+        const float v = t < d ? centred(x[t], mu, t) : 0.f;
         const float vq = quantise<0>(v, 1.f, 1.f, row + 2 * t);
         sxx = fmaf(v, v, sxx);
         sqq = fmaf(vq, vq, sqq);
@@ -146,7 +146,11 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float4* __restrict
       sxx = warp_sum(sxx);
       sqq = warp_sum(sqq);
       sdd = warp_sum(sdd);
-      if (lane == 0) xs16q[r] = make_float4(1.f, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+      if (lane == 0) {
+        const float nbv = norm_bound(sxx, d);
+        xs16q[r] = make_float4(1.f, norm_bound(sqq, d), centred_resid(nbv, norm_bound(sdd, d), mu),
+                               centred_norm(nbv, mu));
+      }
     }
   }
 }
@@ -195,8 +199,8 @@ cudaError_t launch_recheck(const Problem& p, const Work& w, const float* h, int 
   const bool queue = w.fq_rows != nullptr;
   cudaError_t e = recheck_pass(p, w, h, w.flags, &w.ctl->n_flagged, queue, s);
   if (e != cudaSuccess || !queue) return e;
-  gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xs, w.xnorm, w.ctl, w.fq_rows, w.fq_cap, w.X_sub,
-                                                    w.xn_sub, tc16 ? w.Xq16 : nullptr, w.xs16q, w.Kp16);
+  gather_queue_kernel<<<num_sms() * 4, 256, 0, s>>>(p.X, p.d, w.xnorm, w.ctl, w.fq_rows, w.fq_cap, w.X_sub, w.xn_sub,
+                                                    tc16 ? w.Xq16 : nullptr, w.xs16q, w.Kp16, w.mu);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (tc16) e = tc16(s);  // E4M3 runs: BF16 codes on the tensor cores, then the short lists
   else e = launch_assign_simt_sub(p, w, h, s);

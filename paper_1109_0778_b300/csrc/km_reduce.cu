@@ -233,14 +233,15 @@ __host__ __device__ constexpr size_t seg_smem_bytes() {
 // of each row it reads at its sorted position p (row stride Kp elements, 2 Kp
 // for the two-part codes), using the row scale in xs, and the row statistics
 // xs at p; the codes equal those the quantisation stage produces for the same
-// point.
+// point (of the centred row x - mu when mu is given).
 template <int V, int QM, bool DET>
 __global__ void __launch_bounds__(256, 3)
 segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __restrict__ C,
               const int32_t* __restrict__ perm, const int32_t* __restrict__ slab, double* __restrict__ sums64,
               Ctl* ctl, uint8_t* __restrict__ Xq, const float4* __restrict__ xs, int Kp,
               float4* __restrict__ xs_sorted, int k, unsigned long long* __restrict__ facc,
-              unsigned long long* __restrict__ oacc, const unsigned int* __restrict__ xmax, uint4* __restrict__ Xh) {
+              unsigned long long* __restrict__ oacc, const unsigned int* __restrict__ xmax, uint4* __restrict__ Xh,
+              const float* __restrict__ mu) {
   constexpr int RB = seg_rows<V>();  // rows per batch (lane r < RB holds row r's indices)
   constexpr int RS = 32 * V;         // shared-memory floats per row
   extern __shared__ __align__(16) float seg_smem[];
@@ -258,6 +259,13 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     for (int v = 0; v < V; ++v) q[v][0] = q[v][1] = q[v][2] = 0;
   }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // the lane's slices of the codes' centring vector (0 without one): x - 0 = x exactly
+  float muv[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int t = v * 32 + lane;
+    muv[v] = (QM != 0 && mu && t < d) ? __ldg(mu + t) : 0.f;
+  }
   float* stage0 = seg_smem + (size_t)wib * 2 * RB * RS;
   float* stage1 = stage0 + RB * RS;
   const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
@@ -361,7 +369,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               const int t = v * 32 + lane;
-              if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
+              if (t < d) row[t] = __float2bfloat16_rn(__fsub_rn(xr[v], muv[v]));
             }
           } else if constexpr (QM == 3) {
             __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * 2 * Kp;
@@ -369,7 +377,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
             for (int v = 0; v < V; ++v) {
               const int t = v * 32 + lane;
               float hi, lo;
-              if (t < d) split_bf16(xr[v], row + t, row + Kp + t, hi, lo);
+              if (t < d) split_bf16(__fsub_rn(xr[v], muv[v]), row + t, row + Kp + t, hi, lo);
             }
           } else {
             const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
@@ -377,7 +385,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               const int t = v * 32 + lane;
-              if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
+              if (t < d) row[t] = __nv_fp8_e4m3(__fsub_rn(xr[v], muv[v]) * inv).__x;
             }
           }
         }
@@ -658,7 +666,7 @@ void seg_launch(int blocks, const Problem& p, const Work& w, int Kp, cudaStream_
   segsum_kernel<V, QM, DET><<<blocks, 256, seg_smem_bytes<V>(), s>>>(
       p.X, p.n, p.d, p.C, w.perm, w.lab_sorted, w.sums64, w.ctl, QM ? w.Xq : nullptr, QM ? w.xs : nullptr,
       QM ? Kp : 0, QM ? w.xs_sorted : nullptr, p.k, w.facc, w.oacc, w.xmax,
-      QM == 2 ? reinterpret_cast<uint4*>(w.Xh) : nullptr);
+      QM == 2 ? reinterpret_cast<uint4*>(w.Xh) : nullptr, QM ? w.mu : nullptr);
 }
 
 template <int V, bool DET>

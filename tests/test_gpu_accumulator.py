@@ -174,7 +174,9 @@ def test_random_mixed_exponents_within_gamma_k(km, precision):
 def test_near_margin_gaps_bf16_parity(km, ref):
     """Points whose exact score gap to the second centroid is 1.3-2 x the BF16 margin.
 
-    Data and centroids are BF16 values, so the codes are exact and the margin reduces to
+    Data and centroids are BF16 values and the centroid set is symmetric about 0 (each pair
+    also appears negated, far from every point), so the codes' centring vector -- the mean of
+    the centroids -- is exactly 0, the codes are exact and the margin reduces to
     2 (c_h H + (gamma'_K' + 2u) ||x|| C~max) (1 + 2^-10) with u = 2^-24, K' = 128 + 16 (the
     contraction also accumulates the -h_j slice: 1 x (-h1, -h2, -h3)) and
     c_h = u + 2^-27 + gamma'_K' (1 + 2^-7) (the library's formula for BF16 with -h_j folded into
@@ -189,8 +191,9 @@ def test_near_margin_gaps_bf16_parity(km, ref):
 
     ya = bf(rng.uniform(-20, 20, (pairs, d)))
     yb = bf(ya + rng.normal(0, 0.25, (pairs, d)))
-    C = np.empty((2 * pairs, d))
-    C[0::2], C[1::2] = ya, yb
+    C = np.empty((4 * pairs, d))
+    C[0:2 * pairs:2], C[1:2 * pairs:2] = ya, yb
+    C[2 * pairs:] = -C[:2 * pairs]  # the mirrored half: the centroids' mean is exactly 0
     h = 0.5 * np.sum(C * C, axis=1)
     H, Cmax = h.max(), np.sqrt(np.sum(C * C, axis=1)).max()
     gam = gamma_k(128 + 16)

@@ -484,3 +484,29 @@ def test_small_problems_stop_rule_and_reproducible(km, n, d, k, tol):
     assert torch.equal(o1.counts, o3.counts)
     assert torch.allclose(C1, C3, rtol=1e-6, atol=1e-6)
     assert abs(o1.stats["objective"] - o3.stats["objective"]) <= 1e-6 * abs(o3.stats["objective"])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8", "bf16x3"])
+def test_offset_data_centred_codes(km, ref, precision):
+    """A common offset of 1000 in every coordinate: the quantised paths code x - mu and c - mu (mu =
+    the mean of the call's initial centroids), so the margin is that of the centred data. Before
+    centring, BF16 and E4M3 flagged every point (all-centroid re-checks); parity per step, and the
+    flag rate stays that of the data without the offset."""
+    n, d, k = 120_000, 64, 48
+    X0 = synth.mixture(0xABD, n, d, k, 20.0, 1.0)
+    rates = []
+    for off in (0.0, 1000.0):
+        X = (X0 + np.float32(off)).astype(np.float32)
+        Xd = torch.from_numpy(X).to(DEV)
+        Cd = torch.from_numpy(X[:k].copy()).to(DEV)
+        a, s, c = km.alloc_outputs(Xd, Cd)
+        for it in range(3):
+            C_in = Cd.cpu().numpy().astype(np.float64)
+            out = km.step(Xd, Cd, a, s, c, precision=precision, warm_start=it > 0)
+            ag = out.assign.cpu().numpy()
+            parity.check_assign(ref, X, C_in, ag)
+            parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), out.sums.cpu().numpy(), out.counts.cpu().numpy())
+            parity.check_objective(ref, X, C_in, ag, out.stats["objective"])
+        rates.append((out.stats["n_flagged"] / n, out.stats["n_full"] / n))
+    (f0, _), (f1, full1) = rates
+    assert f1 <= f0 + 0.02 and full1 <= 0.01, rates
