@@ -1439,6 +1439,9 @@ struct BatchPlan {
   std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
   std::vector<int64_t> seg_off;   // prefix sums of the segmented sum's row costs
   std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
+  std::vector<BChunk> rchunks;    // row chunks of the count and scatter stages
+  std::vector<int32_t> kc_inst, kp_inst;  // instance of each flattened (padded) centroid
+  int kmax = 0;
   int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
   int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0, sorted = 1;
   int shape = 0;  // the tune, as km_stats.batch_shape reports it
@@ -1520,6 +1523,11 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.seg_off[q + 1] = P.seg_off[q] + s.n * (int64_t)(4 * s.d + esz * s.d + 40);
     P.nkb_max = std::max(P.nkb_max, I.nkb);
     P.kp_max = std::max(P.kp_max, I.kp);
+    P.kmax = std::max(P.kmax, s.k);
+    for (int64_t r = 0; r < s.n; r += kBRowChunk)
+      P.rchunks.push_back(BChunk{I.row_off + r, q, (int)std::min<int64_t>(kBRowChunk, s.n - r)});
+    P.kc_inst.insert(P.kc_inst.end(), (size_t)s.k, q);
+    P.kp_inst.insert(P.kp_inst.end(), (size_t)I.kp, q);
   }
   P.stages = tc_pick_buffers(P.nkb_max, P.bn, P.kp_max, P.fp8, &P.abufs);
   if (P.stages < 2) return fail(KM_EUNSUPPORTED, "largest k of the batch does not fit the tensor-core pipeline");
@@ -1584,8 +1592,8 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 
 // Byte offsets of the batch workspace.
 struct BLayout {
-  size_t ctl, inst, row, kc, kp, tile, seg, cta, maps, slots, xs, xss, labs, perm, flags, offs, cur, sums, hq, scq,
-      cst, xq, cq, csave, hist, total;
+  size_t ctl, inst, row, kc, kp, tile, seg, cta, rch, kci, kpi, maps, slots, xs, xss, labs, perm, flags, offs, cur,
+      sums, hq, scq, cst, xq, cq, csave, hist, total;
 };
 
 BLayout batch_layout(const BatchPlan& P, int iters) {
@@ -1606,6 +1614,9 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.tile = take(8 * (nb + 1));
   L.seg = take(8 * (nb + 1));
   L.cta = take(8 * P.cta_tile.size());
+  L.rch = take(sizeof(BChunk) * P.rchunks.size());
+  L.kci = take(4 * P.kc_inst.size());
+  L.kpi = take(4 * P.kp_inst.size());
   L.maps = take(sizeof(CUtensorMap) * 2 * nb, 128);
   L.slots = take(8);
   L.xs = take(16 * (size_t)P.R);
@@ -1679,6 +1690,11 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.seg_off = (const int64_t*)(B + BL.seg);
   W.cta_tile = (const int64_t*)(B + BL.cta);
   W.cta_grid = (int)P.cta_tile.size() - 1;
+  W.rchunks = (const BChunk*)(B + BL.rch);
+  W.nrchunks = (int)P.rchunks.size();
+  W.kmax = P.kmax;
+  W.kc_inst = (const int32_t*)(B + BL.kci);
+  W.kp_inst = (const int32_t*)(B + BL.kpi);
   W.R = P.R;
   W.KC = P.KC;
   W.KP = P.KP;
@@ -1721,6 +1737,9 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.seg_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.rch, P.rchunks.data(), sizeof(BChunk) * P.rchunks.size(), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.kci, P.kc_inst.data(), 4 * P.kc_inst.size(), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.kpi, P.kp_inst.data(), 4 * P.kp_inst.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));
   KM_CUDA(cudaMemsetAsync(W.sums64, 0, 8 * (size_t)P.SUMS, s));

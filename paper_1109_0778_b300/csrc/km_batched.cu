@@ -107,14 +107,11 @@ __global__ void __launch_bounds__(256) b_camax_kernel(BWork W) {
 template <int FP8>
 __global__ void __launch_bounds__(256) b_quant_c_kernel(BWork W) {
   constexpr int ESZ = FP8 ? 1 : 2;
-  __shared__ int s_lh[2][2];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // block rounds of 8 consecutive centroids, one warp each
-  for (int64_t base = (int64_t)blockIdx.x * 8, rnd = 0; base < W.KP; base += (int64_t)gridDim.x * 8, ++rnd) {
-    block_instances(W.kp_off, W.nb, base, min(base + 7, W.KP - 1), s_lh[rnd & 1]);
-    const int64_t g = base + wib;
-    if (g >= W.KP) continue;
-    const int b = find_block_in(W.kp_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
+  const int lane = threadIdx.x & 31;
+  // one warp per padded centroid; its instance from the table
+  for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < W.KP;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int b = __ldg(W.kp_inst + g);
     Ctl* ctl = W.ctls + b;
     if (halted(ctl)) continue;
     const BInst& I = W.inst[b];
@@ -269,26 +266,38 @@ __global__ void __launch_bounds__(256, 2) b_recheck_kernel(BWork W) {
   }
 }
 
+// Counts per cluster: each block takes whole row chunks (one instance each),
+// counts them in a shared-memory histogram and adds its nonzero bins to the
+// instance's counts; instances with more than kBHistMax clusters add warp-
+// aggregated global atomics instead.
 __global__ void __launch_bounds__(256) b_count_kernel(BWork W) {
-  __shared__ int s_lh[2][2];
+  extern __shared__ int hist[];
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int rnd = 0;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride, ++rnd) {
-    block_instances(W.row_off, W.nb, base, min(base + (int64_t)blockDim.x - 1, W.R - 1), s_lh[rnd & 1]);
-    const int64_t g = base + threadIdx.x;
-    bool act = g < W.R;
-    int b = 0, j = 0;
-    if (act) {
-      b = find_block_in(W.row_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
-      act = !halted(W.ctls + b);
-      if (act) j = W.inst[b].assign[g - W.inst[b].row_off];
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, act);
-    if (act) {
-      const unsigned long long key = ((unsigned long long)b << 32) | (unsigned)j;
-      const unsigned peers = __match_any_sync(m, key);
-      if (lane == __ffs(peers) - 1) atomicAdd(&W.inst[b].counts[j], __popc(peers));
+  for (int c = blockIdx.x; c < W.nrchunks; c += gridDim.x) {
+    const BChunk ch = W.rchunks[c];
+    if (halted(W.ctls + ch.b)) continue;  // block-uniform
+    const BInst& I = W.inst[ch.b];
+    const int k = I.k;
+    const int32_t* a = I.assign + (ch.r0 - I.row_off);
+    if (k <= kBHistMax) {
+      for (int j = threadIdx.x; j < k; j += blockDim.x) hist[j] = 0;
+      __syncthreads();
+      for (int r = threadIdx.x; r < ch.n; r += blockDim.x) atomicAdd(&hist[__ldg(a + r)], 1);
+      __syncthreads();
+      for (int j = threadIdx.x; j < k; j += blockDim.x)
+        if (hist[j]) atomicAdd(&I.counts[j], hist[j]);
+      __syncthreads();
+    } else {
+      for (int r0 = 0; r0 < ch.n; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const bool act = r < ch.n;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) {
+          const int j = __ldg(a + r);
+          const unsigned peers = __match_any_sync(m, j);
+          if (lane == __ffs(peers) - 1) atomicAdd(&I.counts[j], __popc(peers));
+        }
+      }
     }
   }
 }
@@ -336,35 +345,65 @@ __global__ void __launch_bounds__(1024) b_scan_kernel(BWork W) {
   if (threadIdx.x == 0) W.offs[I.offs_off + I.k] = carry_s;
 }
 
+// Cluster-sorted order of every instance: each block takes whole row chunks,
+// ranks a chunk's points per cluster with shared-memory atomics, reserves one
+// range per (chunk, cluster) in the instance's cursors and writes its points
+// there (the order within a cluster varies from run to run). Instances with
+// more than kBHistMax clusters reserve per warp-aggregated group instead.
+constexpr int kBScatterPer = kBRowChunk / 256;  // rows per thread of a chunk
+
 __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
-  __shared__ int s_lh[2][2];
+  extern __shared__ int cnt[];  // per-cluster count, then the chunk's base position
   const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int rnd = 0;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < W.R; base += stride, ++rnd) {
-    block_instances(W.row_off, W.nb, base, min(base + (int64_t)blockDim.x - 1, W.R - 1), s_lh[rnd & 1]);
-    const int64_t g = base + threadIdx.x;
-    bool act = g < W.R;
-    int b = 0, j = 0;
-    int64_t i = 0;
-    if (act) {
-      b = find_block_in(W.row_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
-      act = !halted(W.ctls + b);
-      if (act) {
-        i = g - W.inst[b].row_off;
-        j = W.inst[b].assign[i];
+  for (int c = blockIdx.x; c < W.nrchunks; c += gridDim.x) {
+    const BChunk ch = W.rchunks[c];
+    if (halted(W.ctls + ch.b)) continue;  // block-uniform
+    const BInst& I = W.inst[ch.b];
+    const int k = I.k;
+    const int64_t i0 = ch.r0 - I.row_off;  // the chunk's first point within its instance
+    const int32_t* a = I.assign + i0;
+    int32_t* cur = W.cursor + I.kp_off;
+    int32_t* perm = W.perm + I.row_off;
+    int32_t* slab = W.lab_sorted + I.row_off;
+    if (k <= kBHistMax) {
+      for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
+      __syncthreads();
+      int lab[kBScatterPer], rank[kBScatterPer];
+#pragma unroll
+      for (int q = 0; q < kBScatterPer; ++q) {
+        const int r = q * 256 + threadIdx.x;
+        lab[q] = r < ch.n ? __ldg(a + r) : -1;
+        rank[q] = lab[q] >= 0 ? atomicAdd(&cnt[lab[q]], 1) : 0;
       }
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, act);
-    if (act) {
-      const unsigned long long key = ((unsigned long long)b << 32) | (unsigned)j;
-      const unsigned peers = __match_any_sync(m, key);
-      const int leader = __ffs(peers) - 1;
-      int pos = 0;
-      if (lane == leader) pos = atomicAdd(&W.cursor[W.inst[b].kp_off + j], __popc(peers));
-      pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1));
-      W.perm[W.inst[b].row_off + pos] = (int32_t)i;
-      W.lab_sorted[W.inst[b].row_off + pos] = j;
+      __syncthreads();
+      for (int j = threadIdx.x; j < k; j += blockDim.x)
+        if (cnt[j]) cnt[j] = atomicAdd(&cur[j], cnt[j]);
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kBScatterPer; ++q) {
+        if (lab[q] >= 0) {
+          const int pos = cnt[lab[q]] + rank[q];
+          perm[pos] = (int32_t)(i0 + q * 256 + threadIdx.x);
+          slab[pos] = lab[q];
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int r0 = 0; r0 < ch.n; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x;
+        const bool act = r < ch.n;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) {
+          const int j = __ldg(a + r);
+          const unsigned peers = __match_any_sync(m, j);
+          const int leader = __ffs(peers) - 1;
+          int pos = 0;
+          if (lane == leader) pos = atomicAdd(&cur[j], __popc(peers));
+          pos = __shfl_sync(peers, pos, leader) + __popc(peers & ((1u << lane) - 1));
+          perm[pos] = (int32_t)(i0 + r);
+          slab[pos] = j;
+        }
+      }
     }
   }
 }
@@ -631,14 +670,11 @@ __global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
 // Divide per centroid of every instance; the warp that finishes an instance's
 // last centroid records its step statistics and evaluates its stop rule.
 __global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
-  __shared__ int s_lh[2][2];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // block rounds of 8 consecutive centroids, one warp each
-  for (int64_t base = (int64_t)blockIdx.x * 8, rnd = 0; base < W.KC; base += (int64_t)gridDim.x * 8, ++rnd) {
-    block_instances(W.kc_off, W.nb, base, min(base + 7, W.KC - 1), s_lh[rnd & 1]);
-    const int64_t g = base + wib;
-    if (g >= W.KC) continue;
-    const int b = find_block_in(W.kc_off, s_lh[rnd & 1][0], s_lh[rnd & 1][1], g);
+  const int lane = threadIdx.x & 31;
+  // one warp per centroid; its instance from the table
+  for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < W.KC;
+       g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int b = __ldg(W.kc_inst + g);
     Ctl* ctl = W.ctls + b;
     if (halted(ctl)) continue;
     const BInst& I = W.inst[b];
@@ -718,8 +754,10 @@ cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static size_t b_hist_bytes(const BWork& W) { return sizeof(int) * (size_t)(W.kmax < kBHistMax ? W.kmax : kBHistMax); }
+
 cudaError_t launch_b_count(const BWork& W, cudaStream_t s) {
-  b_count_kernel<<<grid_for(W.R, 256, 8), 256, 0, s>>>(W);
+  b_count_kernel<<<grid_for(W.nrchunks, 1, 8), 256, b_hist_bytes(W), s>>>(W);
   return cudaGetLastError();
 }
 
@@ -729,7 +767,7 @@ cudaError_t launch_b_scan(const BWork& W, cudaStream_t s) {
 }
 
 cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s) {
-  b_scatter_kernel<<<grid_for(W.R, 256, 8), 256, 0, s>>>(W);
+  b_scatter_kernel<<<grid_for(W.nrchunks, 1, 8), 256, b_hist_bytes(W), s>>>(W);
   return cudaGetLastError();
 }
 

@@ -209,9 +209,24 @@ struct BInst {
   int bn;    // centroid chunk width: a multiple of 32, at most the launch's (k rounded up to 32 when smaller)
 };
 
+// A contiguous range of one instance's flattened rows: the work item of the
+// batched count and scatter stages (no instance search per row).
+struct BChunk {
+  int64_t r0;  // first flattened row
+  int b;       // instance
+  int n;       // rows (at most kBRowChunk)
+};
+constexpr int kBRowChunk = 4096;  // rows per chunk: 16 per thread of a 256-thread block
+constexpr int kBHistMax = 8192;   // clusters of an instance counted in shared memory (more: global atomics)
+
 struct BWork {
   const BInst* inst;
   int nb, iters;
+  const BChunk* rchunks;    // [nrchunks] row chunks, in flattened order
+  int nrchunks;
+  int kmax;                 // largest k of the batch
+  const int32_t* kc_inst;   // [KC] instance of each flattened centroid
+  const int32_t* kp_inst;   // [KP] instance of each flattened padded centroid
   const int64_t* row_off;   // [nb + 1] prefix sums (binary searched)
   const int64_t* kc_off;    // [nb + 1]
   const int64_t* kp_off;    // [nb + 1]
