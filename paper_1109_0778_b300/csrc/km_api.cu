@@ -1423,10 +1423,12 @@ namespace {
 
 // Launch shape of a batch: chunk width, the order of the instances in the
 // flattened tile space (0: as given, 1: by decreasing work per row tile), and
-// whether the reduce stage rewrites the point codes in cluster-sorted order for
-// the next step (1; a tile then mostly holds rows of one previous cluster, so
-// its candidate tracking is cheap and starts with that cluster's chunk) or the
-// codes keep the order of X (0; the reduce stage then writes no codes).
+// whether the instances whose k spans several chunks run their tiles in the
+// previous step's cluster-sorted order (1; a tile then mostly holds rows of one
+// previous cluster, so its candidate tracking is cheap and starts with that
+// cluster's chunk; their codes are copied in that order after each scatter) or
+// every instance keeps the order of X (0). An instance with one chunk gains
+// nothing from the order: its rows see every column in one block anyway.
 struct BatchTune {
   int bn;
   int order;
@@ -1442,7 +1444,7 @@ struct BatchPlan {
   std::vector<BChunk> rchunks;    // row chunks of the count and scatter stages
   std::vector<int32_t> kc_inst, kp_inst;  // instance of each flattened (padded) centroid
   int kmax = 0;
-  int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, CQ = 0, CSAVE = 0;
+  int64_t R = 0, KC = 0, KP = 0, T = 0, SUMS = 0, XQ = 0, XQS = 0, CQ = 0, CSAVE = 0;
   int nkb_max = 1, kp_max = 0, stages = 0, abufs = 2, bn = 128, fp8 = 0, sorted = 1;
   int shape = 0;  // the tune, as km_stats.batch_shape reports it
 };
@@ -1497,6 +1499,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     I.bn = s.k < P.bn ? (s.k + 31) / 32 * 32 : P.bn;
     I.kp = (s.k + I.bn - 1) / I.bn * I.bn;
     I.nchunks = I.kp / I.bn;
+    I.gsort = tune.sorted && I.nchunks > 1;
     const double K = I.Kp;
     I.gam_tc = (float)(K * 0x1p-23 / (1.0 - K * 0x1p-23) * (1.0 + 1e-6));
     I.row_off = P.R;
@@ -1506,6 +1509,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     I.sum_off = P.SUMS;
     I.tile_off = P.T;
     I.xq_off = P.XQ;
+    I.xqs_off = P.XQS;
     I.cq_off = P.CQ;
     P.R += s.n;
     P.KC += s.k;
@@ -1514,6 +1518,7 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.CSAVE += (int64_t)s.k * s.d;
     P.T += (s.n + 127) / 128;
     P.XQ += align_up((size_t)s.n * I.Kp * esz, 256);
+    if (I.gsort) P.XQS += align_up((size_t)s.n * I.Kp * esz, 256);
     P.CQ += align_up((size_t)I.kp * I.Kp * esz, 256);
     P.row_off[q + 1] = P.R;
     P.kc_off[q + 1] = P.KC;
@@ -1592,8 +1597,8 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 
 // Byte offsets of the batch workspace.
 struct BLayout {
-  size_t ctl, inst, row, kc, kp, tile, seg, cta, rch, kci, kpi, maps, slots, xs, xss, labs, perm, flags, offs, cur,
-      sums, hq, scq, cst, xq, cq, csave, hist, total;
+  size_t ctl, inst, row, kc, kp, tile, seg, cta, rch, kci, kpi, maps, maps_s, slots, xs, xss, labs, perm, flags, offs, cur,
+      sums, hq, scq, cst, xq, xqs, cq, csave, hist, total;
 };
 
 BLayout batch_layout(const BatchPlan& P, int iters) {
@@ -1618,6 +1623,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.kci = take(4 * P.kc_inst.size());
   L.kpi = take(4 * P.kp_inst.size());
   L.maps = take(sizeof(CUtensorMap) * 2 * nb, 128);
+  L.maps_s = take(sizeof(CUtensorMap) * nb, 128);
   L.slots = take(8);
   L.xs = take(16 * (size_t)P.R);
   L.xss = take(16 * (size_t)P.R);
@@ -1631,6 +1637,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.scq = take(4 * (size_t)P.KP);
   L.cst = take(16 * (size_t)P.KP);
   L.xq = take((size_t)P.XQ);
+  L.xqs = take((size_t)P.XQS);
   L.cq = take((size_t)P.CQ);
   L.csave = take(4 * (size_t)P.CSAVE);
   L.hist = take((8 * 5 + 4) * (size_t)nb * iters);
@@ -1702,6 +1709,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.ctls = (Ctl*)(B + o_ctl);
   W.flag_slots = (unsigned long long*)(B + o_slots);
   W.maps = (const CUtensorMap*)(B + o_maps);
+  W.maps_s = (const CUtensorMap*)(B + BL.maps_s);
   W.xs = (float4*)(B + o_xs);
   W.xs_sorted = (float4*)(B + o_xss);
   W.lab_sorted = (int32_t*)(B + o_labs);
@@ -1714,6 +1722,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.scq = (float*)(B + o_scq);
   W.cst = (float4*)(B + BL.cst);
   W.Xq = (uint8_t*)(B + o_xq);
+  W.Xqs = (uint8_t*)(B + BL.xqs);
   W.Cq = (uint8_t*)(B + o_cq);
   char* hb = B + o_hist;
   W.obj_hist = (double*)hb;
@@ -1723,12 +1732,15 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.full_hist = W.flagged_hist + (size_t)nb * iters;
   W.empty_hist = (int*)(W.full_hist + (size_t)nb * iters);
   // tensor maps of every instance's codes
-  std::vector<CUtensorMap> maps(2 * nb);
+  std::vector<CUtensorMap> maps(3 * nb);  // codes of X, codes of C; then the sorted copies
+  memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
   const int esz = P.fp8 ? 1 : 2;
   for (int b = 0; b < nb; ++b) {
     const BInst& I = P.inst[b];
     if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128, I.rowb))) return rc;
     if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, I.bn, I.rowb))) return rc;
+    if (I.gsort && (rc = encode_codes_map(&maps[2 * nb + b], W.Xqs + I.xqs_off, I.n, I.Kp, esz, 128, I.rowb)))
+      return rc;
   }
   KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
@@ -1741,6 +1753,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   KM_CUDA(cudaMemcpyAsync(B + BL.kci, P.kc_inst.data(), 4 * P.kc_inst.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.kpi, P.kp_inst.data(), 4 * P.kp_inst.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.maps_s, maps.data() + 2 * nb, sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));
   KM_CUDA(cudaMemsetAsync(W.sums64, 0, 8 * (size_t)P.SUMS, s));
   // C on entry, restored on error
@@ -1775,7 +1788,6 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
     KM_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     const uint32_t idesc = tc::idesc_f32acc(P.fp8 ? 0u : 1u, 128, (uint32_t)P.bn);
-    const int qmode = P.sorted ? (P.fp8 ? 2 : 1) : 0;
     cudaStream_t cs = c->cap_stream;
     for (int it = 0; it < iters && e == cudaSuccess; ++it) {
       // stage boundaries as in enqueue_step (events only when profiling)
@@ -1797,8 +1809,9 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
       if (!e) e = launch_b_scan(W, cs);
       if (!e) e = at(5);
       if (!e) e = launch_b_scatter(W, cs);
+      if (!e && P.sorted && it + 1 < iters) e = launch_b_permute(W, cs);  // the next step's sorted code copies
       if (!e) e = at(6);
-      if (!e) e = launch_b_segsum(W, qmode, cs);
+      if (!e) e = launch_b_segsum(W, cs);
       if (!e) e = at(7);
       if (!e) e = launch_b_divide(W, tol, cs);
       if (!e) e = at(8);
@@ -1933,6 +1946,16 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
       tune = t.tune;
       known = true;
     }
+  // test knob: KM_BATCH_SHAPE="bn,order,sorted" runs that launch shape without tuning (every shape must
+  // give the same results, so tests cover each one)
+  if (const char* fs = getenv("KM_BATCH_SHAPE")) {
+    BatchTune f{0, -1, -1};
+    if (sscanf(fs, "%d,%d,%d", &f.bn, &f.order, &f.sorted) != 3 || (f.bn != 64 && f.bn != 128) || f.order < 0 ||
+        f.order > 1 || f.sorted < 0 || f.sorted > 1)
+      return fail(KM_EINVAL, "KM_BATCH_SHAPE must be \"bn,order,sorted\" with bn 64 or 128, order and sorted 0 or 1");
+    tune = f;
+    known = true;
+  }
   int rc;
   if (!known) {
     // autotune: time three steps of every candidate shape on the caller's data, keep the fastest

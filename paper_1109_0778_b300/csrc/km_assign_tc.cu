@@ -184,12 +184,14 @@ __device__ __forceinline__ void set_instance(const TcParams& P, const CUtensorMa
     it.nchunks = I.nchunks;
     it.rowb = I.rowb;
     it.bn = I.bn;
-    it.mapX = P.bmaps + 2 * b;
+    // an instance whose tiles run in cluster-sorted order reads the sorted copy of its codes
+    const bool srt = P.sorted && I.gsort;
+    it.mapX = srt ? P.bmaps_s + b : P.bmaps + 2 * b;
     it.mapC = P.bmaps + 2 * b + 1;
     it.h = P.bh + I.kp_off;
     it.sc = P.bsc + I.kp_off;
     it.cst = P.bcst + I.kp_off;
-    it.rows = P.sorted ? P.bperm + I.row_off : nullptr;
+    it.rows = srt ? P.bperm + I.row_off : nullptr;
     it.xs = P.bxs + I.row_off;
     it.xs_sorted = P.bxs_sorted + I.row_off;
     it.lab_sorted = P.blab_sorted + I.row_off;
@@ -1066,6 +1068,7 @@ cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int 
   P.ntiles = W.T;
   P.bctls = W.ctls;
   P.bmaps = W.maps;
+  P.bmaps_s = W.maps_s;
   P.bh = W.hq;
   P.bsc = W.scq;
   P.bcst = W.cst;

@@ -408,36 +408,84 @@ __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
   }
 }
 
+// Cluster-sorted copies for the instances whose tiles run in that order
+// (gsort: k spans several chunks, where a tile of one previous cluster keeps
+// its candidate tracking cheap): sorted row p of the copy holds the codes of
+// point perm[p], and the row statistics go to xs_sorted[p]. A warp copies
+// 32 / (row bytes / 16) rows per step, a lane one 16-byte piece of a row, and
+// takes kPermU steps at a time (their index loads, then their row loads, in
+// flight together).
+constexpr int kPermU = 8;
+
+__global__ void __launch_bounds__(256) b_permute_kernel(BWork W) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (int c = blockIdx.x; c < W.nrchunks; c += gridDim.x) {
+    const BChunk ch = W.rchunks[c];
+    const BInst& I = W.inst[ch.b];
+    if (!I.gsort || halted(W.ctls + ch.b)) continue;  // block-uniform
+    const int pieces = (I.nkb * I.rowb) >> 4;  // 16-byte pieces of a code row: 2, 4, 8 or 16
+    const int rpw = 32 / pieces, q = lane % pieces;
+    const int64_t p0 = ch.r0 - I.row_off;  // sorted position of the chunk's first row
+    const int32_t* perm = W.perm + I.row_off;
+    const float4* xs = W.xs + I.row_off;
+    float4* xss = W.xs_sorted + I.row_off;
+    const uint4* src = reinterpret_cast<const uint4*>(W.Xq + I.xq_off);
+    uint4* dst = reinterpret_cast<uint4*>(W.Xqs + I.xqs_off);
+    for (int r0 = wib * rpw * kPermU + lane / pieces; r0 < ch.n; r0 += 8 * rpw * kPermU) {
+      int idx[kPermU];
+#pragma unroll
+      for (int u = 0; u < kPermU; ++u) {
+        const int r = r0 + u * rpw;
+        idx[u] = r < ch.n ? __ldg(perm + p0 + r) : -1;
+      }
+      uint4 v[kPermU];
+      float4 st[kPermU];
+#pragma unroll
+      for (int u = 0; u < kPermU; ++u) {
+        if (idx[u] >= 0) {
+          v[u] = __ldg(src + (int64_t)idx[u] * pieces + q);
+          if (q == 0) st[u] = __ldg(xs + idx[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPermU; ++u) {
+        if (idx[u] >= 0) {
+          const int64_t p = p0 + r0 + u * rpw;
+          dst[p * pieces + q] = v[u];
+          if (q == 0) xss[p] = st[u];
+        }
+      }
+    }
+  }
+}
+
 // Segmented sums over the flattened sorted positions: each warp walks one
 // contiguous range; the rows are gathered into shared memory with cp.async one
 // batch ahead (as in km_reduce.cu); rows of d <= 16 are packed several per
 // warp step. A batch never crosses an instance
 // boundary and holds as many rows of its instance's width as fit a stage, up
 // to 32. A run may cross instance boundaries, which flush like cluster
-// boundaries. With QM the codes and row statistics of each row are rewritten at
-// its sorted position.
+// boundaries.
 constexpr int kSegStage = 1024;                                 // floats per stage (8 rows of 128)
 constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;      // 8 warps x 2 stages
 
 // One batch of the segmented sum: rows [bs, bs + bn) of instance q (halted
 // instances: q = -1), row stride rs floats in the stage; lane r < bn holds row
-// r's point i, label j and (with QM) row statistics.
+// r's point i and label j.
 struct SegBatch {
   int64_t bs;
   int bn, rs, q, d;
   const float* X;
   int i, j;
-  float4 xs;
 };
 
 // The rows of one batch, V = ceil(d / 32) registers per lane (only the first V
 // of the kMaxV accumulators are touched). cur_j: the cluster being summed;
 // `flush` adds the partial sums of cur_j to the FP64 sums.
-template <int QM, int V, typename Flush>
+template <int V, typename Flush>
 __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int lane, int d, const float* C,
-                                         uint8_t* xq, int kp, int64_t row0, float4* xs_sorted, float (&s)[kMaxV],
-                                         float (&c)[kMaxV], float (&cj)[kMaxV], float& objS, float& objC,
-                                         int& cur_j, Flush&& flush) {
+                                         float (&s)[kMaxV], float (&c)[kMaxV], float (&cj)[kMaxV], float& objS,
+                                         float& objC, int& cur_j, Flush&& flush) {
   // rows that start a cluster run (lane r holds row r's label), found once per batch
   const int jprev = __shfl_up_sync(0xffffffffu, B.j, 1);
   const unsigned starts = __ballot_sync(0xffffffffu, lane < B.bn && B.j != (lane == 0 ? cur_j : jprev));
@@ -454,7 +502,6 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
     const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
     const int rend = later ? __ffs(later) - 1 : B.bn;
     for (; r < rend; ++r) {
-      const float sxr = QM == 2 ? __shfl_sync(0xffffffffu, B.xs.x, r) : 1.f;
       float xr[V], qd = 0.f;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -465,25 +512,6 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
         qd = fmaf(df, df, qd);
       }
       kahan_add(objS, objC, qd);
-      if constexpr (QM != 0) {
-        const int64_t pr = B.bs + r - row0;  // sorted position within the instance
-        if constexpr (QM == 1) {
-          __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(xq) + pr * kp;
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            if (t < d) row[t] = __float2bfloat16_rn(xr[v]);
-          }
-        } else {
-          const float inv = pow2_inv(sxr);  // 1 / row scale, exact
-          uint8_t* row = xq + pr * kp;
-#pragma unroll
-          for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            if (t < d) row[t] = __nv_fp8_e4m3(xr[v] * inv).__x;
-          }
-        }
-      }
     }
   }
 }
@@ -491,19 +519,16 @@ __device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int
 // Rows of d <= 16 (dp = the power of two >= d, 32 / dp rows per step): lane
 // group g = lane / dp takes row r0 + g, lane t = lane % dp its column t. Each
 // lane keeps its own run (cluster cur_j) and flushes it alone.
-template <int QM, typename Flush>
+template <typename Flush>
 __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* st, int lane, int d, int dp,
-                                                const float* C, uint8_t* xq, int kp, int64_t row0, float4* xs_sorted,
-                                                float& s, float& c, float& cj, float& objS, float& objC, int& cur_j,
-                                                Flush&& flush) {
+                                                const float* C, float& s, float& c, float& cj, float& objS,
+                                                float& objC, int& cur_j, Flush&& flush) {
   const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
   for (int r0 = 0; r0 < B.bn; r0 += G) {
     const int r = r0 + g;
     const bool ok = r < B.bn;
     const int src = ok ? r : 0;
     const int j = __shfl_sync(0xffffffffu, B.j, src);
-    float sxr = 1.f;  // the row's code scale (E4M3)
-    if constexpr (QM == 2) sxr = __shfl_sync(0xffffffffu, B.xs.x, src);
     if (!ok) continue;
     if (j != cur_j) {
       flush();
@@ -514,16 +539,6 @@ __device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* 
     kahan_add(s, c, xr);
     const float df = __fsub_rn(xr, cj);
     kahan_add(objS, objC, df * df);
-    if constexpr (QM != 0) {
-      const int64_t pr = B.bs + r - row0;  // sorted position within the instance
-      if (t < d) {
-        if constexpr (QM == 1) {
-          reinterpret_cast<__nv_bfloat16*>(xq)[pr * kp + t] = __float2bfloat16_rn(xr);
-        } else {
-          xq[pr * kp + t] = __nv_fp8_e4m3(xr * pow2_inv(sxr)).__x;
-        }
-      }
-    }
   }
 }
 
@@ -535,7 +550,6 @@ __device__ __forceinline__ int packed_width(int d) {
   return p;
 }
 
-template <int QM>
 __global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -586,10 +600,9 @@ __global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
 #pragma unroll
   for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
   float objS = 0.f, objC = 0.f;
-  int cur_b = -1, cur_j = -1, cur_d = 0, cur_kp = 0, cur_dp = 0;
-  int64_t cur_row0 = 0, cur_sum0 = 0;
+  int cur_b = -1, cur_j = -1, cur_d = 0, cur_dp = 0;
+  int64_t cur_sum0 = 0;
   const float* cur_C = nullptr;
-  uint8_t* cur_xq = nullptr;
   auto flush = [&]() {  // this lane's partial sums of run cur_j (packed rows: column lane % cur_dp)
     if (cur_j < 0) return;
 #pragma unroll
@@ -613,14 +626,12 @@ __global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
   cut(Bc);
   if (Bc.bn > 0) {
     gather(Bc, stage0);
-    if (QM != 0 && Bc.q >= 0 && lane < Bc.bn) Bc.xs = __ldg(&W.xs[W.inst[Bc.q].row_off + Bc.i]);
   }
   cut(Bn);
   for (int64_t bt = 0; Bc.bn > 0; ++bt) {
     float* st = (bt & 1) ? stage1 : stage0;
     if (Bn.bn > 0) {
       gather(Bn, (bt & 1) ? stage0 : stage1);
-      if (QM != 0 && Bn.q >= 0 && lane < Bn.bn) Bn.xs = __ldg(&W.xs[W.inst[Bn.q].row_off + Bn.i]);
     }
     cut(Bnn);
     if (Bn.bn > 0) cp_async_wait<1>();
@@ -634,30 +645,21 @@ __global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
         cur_b = b;
         cur_j = -1;
         const BInst* I = W.inst + b;
-        // the instance's fields in registers (the code stores below may alias them)
+        // the instance's fields in registers
         cur_d = I->d;
         cur_dp = packed_width(cur_d);
-        cur_kp = I->Kp;
-        cur_row0 = I->row_off;
         cur_sum0 = I->sum_off;
         cur_C = I->C;
-        cur_xq = W.Xq + I->xq_off;
       }
       const int d = cur_d;
-      // lane r holds row r's statistics: one coalesced store of the batch's sorted statistics
-      if (QM != 0 && lane < Bc.bn) W.xs_sorted[Bc.bs + lane] = Bc.xs;
       if (cur_dp)
-        seg_rows_packed<QM>(Bc, st, lane, d, cur_dp, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s[0], c[0], cj[0],
-                            objS, objC, cur_j, flush);
+        seg_rows_packed(Bc, st, lane, d, cur_dp, cur_C, s[0], c[0], cj[0], objS, objC, cur_j, flush);
       else if (d <= 32)
-        seg_rows<QM, 1>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
-                        flush);
+        seg_rows<1>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
       else if (d <= 64)
-        seg_rows<QM, 2>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC, cur_j,
-                        flush);
+        seg_rows<2>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
       else
-        seg_rows<QM, kMaxV>(Bc, st, lane, d, cur_C, cur_xq, cur_kp, cur_row0, W.xs_sorted, s, c, cj, objS, objC,
-                            cur_j, flush);
+        seg_rows<kMaxV>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
     Bc = Bn;
@@ -680,6 +682,10 @@ __global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
     const BInst& I = W.inst[b];
     const int j = (int)(g - I.kc_off), d = I.d;
     const int cnt = I.counts[j];
+    // FP64 quotients: a lane with more than one coordinate divides once, y = RN(1 / cnt), and
+    // corrects each quotient (div_by_recip: the same correctly rounded result as a division)
+    const bool recip = d > 32 && cnt > 0;
+    const double y = recip ? 1.0 / (double)cnt : 0.0;
     double acc = 0.0;
     for (int t = lane; t < d; t += 32) {
       const int64_t e = (int64_t)j * d + t;
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
       *sp = 0.0;
       I.sums[e] = (float)sv;
       const float co = I.C[e];
-      const float cn = cnt > 0 ? (float)(sv / (double)cnt) : co;
+      const float cn = cnt > 0 ? (float)(recip ? div_by_recip(sv, (double)cnt, y) : sv / (double)cnt) : co;
       I.C[e] = cn;
       const double df = (double)cn - (double)co;
       acc = fma(df, df, acc);
@@ -771,21 +777,19 @@ cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t init_batched() {
-  cudaError_t e = cudaFuncSetAttribute(b_segsum_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(b_segsum_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(b_segsum_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
-  return e;
+cudaError_t launch_b_permute(const BWork& W, cudaStream_t s) {
+  b_permute_kernel<<<grid_for(W.nrchunks, 1, 8), 256, 0, s>>>(W);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s) {
+cudaError_t init_batched() {
+  return cudaFuncSetAttribute(b_segsum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmem);
+}
+
+cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s) {
   int64_t blocks = (W.R + 8 * 64 - 1) / (8 * 64);
   if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
-  if (qmode == 1) b_segsum_kernel<1><<<(int)blocks, 256, kSegSmem, s>>>(W);
-  else if (qmode == 2) b_segsum_kernel<2><<<(int)blocks, 256, kSegSmem, s>>>(W);
-  else b_segsum_kernel<0><<<(int)blocks, 256, kSegSmem, s>>>(W);
+  b_segsum_kernel<<<(int)blocks, 256, kSegSmem, s>>>(W);
   return cudaGetLastError();
 }
 

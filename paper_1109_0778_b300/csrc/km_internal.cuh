@@ -166,6 +166,7 @@ struct TcParams {
   int64_t ntiles;
   Ctl* bctls;
   const CUtensorMap* bmaps;
+  const CUtensorMap* bmaps_s;  // [nb] maps of the cluster-sorted code copies (gsort instances)
   float* bh;
   float* bsc;
   const float4* bcst;
@@ -207,6 +208,9 @@ struct BInst {
   float gam_tc;
   int rowb;  // bytes of one code row of a K block: 32 or 64 (one block, 32- or 64-byte swizzle), or 128
   int bn;    // centroid chunk width: a multiple of 32, at most the launch's (k rounded up to 32 when smaller)
+  int gsort;        // from the second step on, the instance's tiles are its points in cluster-sorted order
+                    // (k spans several chunks; the codes are copied in that order after each scatter)
+  int64_t xqs_off;  // bytes: the cluster-sorted copy of the point codes (gsort instances)
 };
 
 // A contiguous range of one instance's flattened rows: the work item of the
@@ -238,6 +242,7 @@ struct BWork {
   Ctl* ctls;                // [nb]
   unsigned long long* flag_slots;  // entries in the shared flag list
   const CUtensorMap* maps;  // [2 nb]: codes of X, codes of C
+  const CUtensorMap* maps_s;  // [nb]: cluster-sorted code copies (gsort instances; zeros otherwise)
   float4* xs;
   float4* xs_sorted;
   int32_t* lab_sorted;
@@ -250,6 +255,7 @@ struct BWork {
   float* scq;
   float4* cst;  // [KP] per-centroid error-bound terms
   uint8_t* Xq;
+  uint8_t* Xqs;   // cluster-sorted copies of the gsort instances' point codes
   uint8_t* Cq;
   double* obj_hist;                  // [nb][iters]
   double* shift_hist;
@@ -258,6 +264,20 @@ struct BWork {
   unsigned long long* full_hist;
   int* empty_hist;
 };
+
+// RN(a / b) in FP64 from y = RN(1 / b), one division per divisor instead of
+// one per quotient: q = RN(a y) is within an ulp of a / b, the remainder
+// r = a - b q is then exact (one FMA), and RN(q + r y) is the correctly
+// rounded quotient (Markstein's theorem on the final correction step of a
+// division: P. Markstein, IBM J. Res. Dev. 34(1), 1990; J.-M. Muller et al.,
+// Handbook of Floating-Point Arithmetic). Valid while no intermediate
+// overflows or underflows: here a is a sum of FP32 values (|a| >= 2^-149 or
+// 0, well inside the FP64 normal range) and b a count in [1, 2^31).
+__device__ __forceinline__ double div_by_recip(double a, double b, double y) {
+  const double q = a * y;
+  const double r = fma(-q, b, a);
+  return fma(r, y, q);
+}
 
 __device__ __forceinline__ int find_block(const int64_t* off, int nb, int64_t g) {
   int lo = 0, hi = nb;  // off[lo] <= g < off[hi]
@@ -308,7 +328,9 @@ cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_count(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_scan(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s);
-cudaError_t launch_b_segsum(const BWork& W, int qmode, cudaStream_t s);
+// Cluster-sorted code copies and row statistics of the gsort instances (after the scatter)
+cudaError_t launch_b_permute(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s);
 cudaError_t launch_b_divide(const BWork& W, double tol, cudaStream_t s);
 
 struct Problem {

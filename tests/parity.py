@@ -53,8 +53,12 @@ def check_assign(orc, X, C_in, a_gpu, rows=None):
     return int(mism.sum()), int(len(ag))
 
 
-def check_update(orc, X, C_in, a_gpu, C_out, sums_gpu, counts_gpu):
-    """Counts, sums and the new centroids against the oracle's update for the GPU's assignment."""
+def check_update(orc, X, C_in, a_gpu, C_out, sums_gpu, counts_gpu, empty_rtol=0.0):
+    """Counts, sums and the new centroids against the oracle's update for the GPU's assignment.
+
+    empty_rtol: empty clusters keep their centroid exactly (0), or within this distance relative
+    to the row's largest coordinate when C_in comes from another run (whose reduce order may
+    differ in the last bits, and so may the trajectory at a near-tie)."""
     k = C_in.shape[0]
     assert a_gpu.min() >= 0 and a_gpu.max() < k
     sums_ref, counts_ref, C_ref = orc.update(X, a_gpu, C_in)
@@ -65,7 +69,13 @@ def check_update(orc, X, C_in, a_gpu, C_out, sums_gpu, counts_gpu):
     nz = cnt > 0
     bad = nz & (err > CENTROID_TOL * np.maximum(scale, np.finfo(np.float64).tiny))
     assert not bad.any(), f"centroid tolerance exceeded for clusters {np.flatnonzero(bad)[:8]}: {err[bad][:8]} vs {scale[bad][:8]}"
-    assert np.array_equal(C_out[~nz], C_in[~nz].astype(np.float32)), "empty clusters must keep their centroid"
+    keep = C_in[~nz].astype(np.float32)
+    if empty_rtol == 0.0:
+        assert np.array_equal(C_out[~nz], keep), "empty clusters must keep their centroid"
+    else:
+        rowmax = np.abs(keep.astype(np.float64)).max(axis=1, keepdims=True)
+        dev = np.abs(C_out[~nz].astype(np.float64) - keep) - empty_rtol * rowmax
+        assert np.all(dev <= 0.0), f"empty clusters moved: {np.abs(C_out[~nz] - keep).max()}"
     serr = np.abs(sums_gpu.astype(np.float64) - sums_ref).max(axis=1)
     assert np.all(serr <= CENTROID_TOL * scale * np.maximum(cnt, 1) + 1e-30), "sums tolerance exceeded"
     return float(err[nz].max() / max(scale[nz].max(), 1e-300)) if nz.any() else 0.0

@@ -158,3 +158,65 @@ def test_batched_errors(km):
     with pytest.raises(km.KMeansError) as e:
         km.run_batched([(X, C, a, s, c)], 1, precision="bf16x3")
     assert e.value.status == km.KM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", ["128,0,1", "64,1,1", "128,1,0", "64,0,0"])
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_launch_shapes_sorted_steps_parity(km, ref, monkeypatch, shape, precision):
+    """Every launch shape the autotuner may pick gives oracle parity, including the steps whose
+    tiles run in cluster-sorted order (the second step of a call on, for instances whose k spans
+    several chunks). A 2-step run gives the centroids the third step of a 3-step run assigns with
+    (the reduce's order can change them by an ulp, within the near-tie and centroid tolerances)."""
+    monkeypatch.setenv("KM_BATCH_SHAPE", shape)
+    data = make_batch(SHAPES, seed0=2100)
+    probs = to_device(km, data)
+    km.run_batched(probs, 2, precision=precision)
+    C_ins = [p[1].cpu().numpy().astype(np.float64) for p in probs]
+    for (X, C0), p in zip(data, probs):
+        p[1].copy_(torch.from_numpy(C0).to(DEV))
+    stats = km.run_batched(probs, 3, precision=precision)
+    for (X, _), (Xd, Cd, a, s, c), C_in, st in zip(data, probs, C_ins, stats):
+        ag = a.cpu().numpy()
+        assert st["iters_done"] == 3
+        assert st["batch_shape"] == int(shape.split(",")[0]) + 1000 * int(shape.split(",")[1]) + \
+            10000 * int(shape.split(",")[2])
+        parity.check_assign(ref, X, C_in, ag)
+        # (an empty cluster keeps the 3-step run's own second-step centroid, equal to C_in up to
+        # the reduce order: within the centroid tolerance of the row's magnitude)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy(),
+                            empty_rtol=parity.CENTROID_TOL)
+        parity.check_objective(ref, X, C_in, ag, st["objective"])
+
+
+def test_batched_launch_shape_knob_rejects_bad_values(km, monkeypatch):
+    monkeypatch.setenv("KM_BATCH_SHAPE", "96,0,1")
+    probs = to_device(km, make_batch(SHAPES[:2]))
+    with pytest.raises(RuntimeError, match="KM_BATCH_SHAPE"):
+        km.run_batched(probs, 1, precision="bf16")
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_divide_correctly_rounded(km, precision):
+    """The divide rounds each FP64 quotient sum / count correctly and then to FP32 (the reciprocal
+    of each count once, then Markstein's correction step). Integer-valued points keep every
+    cluster sum exact, so every new coordinate must equal float32(float64(sum) / count) bit for bit."""
+    shapes = [(20000, 8, 300), (12000, 32, 7), (9000, 64, 150), (15000, 128, 40), (5000, 3, 1)]
+    data = []
+    for b, (n, d, k) in enumerate(shapes):
+        X = np.clip(np.rint(synth.mixture(7700 + b, n, d, k, 10.0, 1.0) * 25.0), -500, 500).astype(np.float32)
+        data.append((X, X[:k].copy()))
+    probs = to_device(km, data)
+    km.run_batched(probs, 1, precision=precision)
+    for (X, C0), (Xd, Cd, a, s, c) in zip(data, probs):
+        ag = a.cpu().numpy().astype(np.int64)
+        k, d = C0.shape
+        cnt = np.bincount(ag, minlength=k)
+        assert np.array_equal(c.cpu().numpy(), cnt)
+        S = np.zeros((k, d))
+        np.add.at(S, ag, X.astype(np.float64))
+        assert np.abs(S).max() < 2.0 ** 24  # exact in every partial
+        nz = cnt > 0
+        want = (S[nz] / cnt[nz, None]).astype(np.float32)
+        got = Cd.cpu().numpy()[nz]
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), int((got != want).sum())
+        assert np.array_equal(s.cpu().numpy(), S.astype(np.float32))
