@@ -374,7 +374,7 @@ def run_batched(args, torch, dev, dist, rank, world, local, emit=True):
                                f"{len(inst)} instances; value counts iterations of the whole batch",
                        "l2": f"inputs larger than L2 (X = {xbytes / 1e9:.2f} GB)",
                        "autotuned_shape": {"chunk_width": shape % 1000, "instance_order": ["as given", "by work"][
-                           (shape // 1000) % 10], "code_order": ["order of X", "cluster-sorted"][shape // 10000]}},
+                           (shape // 1000) % 10], "row_order": ["order of X", "cluster-sorted for multi-chunk k"][shape // 10000]}},
             "distance_tflops": value * flops_iter / 1e12,
             "stage_ms_per_iter": {k: v / args.steps / w.iters for k, v in stage_tot.items()},
             "flagged_last_iter": {"flagged": flagged[0], "full_recheck": flagged[1],

@@ -153,9 +153,11 @@ typedef struct {
                            KM_FP8E4M3 call without warm_start: its first step) */
   int32_t batch_shape;  /* kmeans_run_batched: the autotuned launch shape, chunk
                            width + 1000 x instance order (0: as given, 1: by work
-                           per tile) + 10000 x code order (0: the point codes in
-                           the order of X, 1: rewritten in cluster-sorted order
-                           each step); 0 for other calls */
+                           per tile) + 10000 x row order (0: every instance in
+                           the order of X, 1: instances whose k spans several
+                           chunks in the previous step's cluster-sorted order,
+                           from a sorted copy of their codes); 0 for other
+                           calls */
 } km_stats;
 
 /* Fills *opts with the defaults (FP32, recheck on, legacy stream). */

@@ -135,7 +135,7 @@ def test_batched_repeat_uses_tuned_shape(km):
     s2 = km.run_batched(p2, 3, precision="bf16")  # same shapes: cached tuning and graph
     for a, b in zip(p1, p2):
         assert (a[2] != b[2]).sum().item() <= 2
-    # every instance reports the batch's autotuned shape: chunk width, instance order, code order
+    # every instance reports the batch's autotuned shape: chunk width, instance order, row order
     shapes = {st["batch_shape"] for st in s1 + s2}
     assert len(shapes) == 1
     shape = shapes.pop()
