@@ -927,23 +927,10 @@ assign_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant
           rec.old = old;
           rec.nc = nc;
           rec.pad = it.b;
-          // the candidates within the margin, in increasing index order (the
-          // re-check breaks exact ties toward the lowest index)
-          int prev = -1;
+          // the candidates: the list's first nc entries, in list order (the
+          // re-check gives exact ties to the lowest index itself)
 #pragma unroll
-          for (int a = 0; a < kT; ++a) {
-            int nxt_j = INT_MAX;
-            if (nc > 0) {
-#pragma unroll
-              for (int t = 0; t < kT; ++t) {
-                const bool in = t < nc;  // the first nc entries are the ones within the margin
-                const int j = top[t].i;
-                if (in && j > prev && j < nxt_j) nxt_j = j;
-              }
-            }
-            rec.cand[a] = (a < nc) ? nxt_j : 0;
-            if (a < nc) prev = nxt_j;
-          }
+          for (int a = 0; a < kT; ++a) rec.cand[a] = (a < nc) ? top[a].i : 0;
 #pragma unroll
           for (int a = kT; a < kMaxCand; ++a) rec.cand[a] = 0;
           if (slot < (unsigned long long)P.flag_cap) P.flags[slot] = rec;

@@ -183,7 +183,7 @@ __device__ __forceinline__ int b_settle(const BWork& W, const FlagRec& rec, cons
     for (int q = 0; q < rec.nc; ++q) {
       const int j = rec.cand[q];
       const float D = warp_sqdist<V>(xv, I.C + (int64_t)j * d, d, lane);
-      if (D < best) {  // candidates arrive in increasing index order
+      if (D < best || (D == best && j < jb)) {  // equal distances: the lower index
         best = D;
         jb = j;
       }

@@ -50,13 +50,14 @@ struct Ctl {
 constexpr size_t kCtlIterBytes = offsetof(Ctl, done);
 
 // A point whose top-2 margin is under its error bound. nc = 0: re-check
-// against all k centroids; otherwise against cand[0..nc) (increasing order).
+// against all k centroids; otherwise against cand[0..nc), in any order (the
+// re-check gives exactly equal distances to the lower index).
 struct __align__(16) FlagRec {
   int32_t i;
   int32_t old;
   int32_t nc;
   int32_t pad;
-  int32_t cand[kMaxCand];  // increasing index order
+  int32_t cand[kMaxCand];
 };
 
 // Device workspace of one call (pointers into one allocation).

@@ -50,8 +50,8 @@ __device__ __forceinline__ float warp_sqdist(const float (&xv)[V], const float* 
 }
 
 // Settles one point in a group of G lanes (G a power of two, the group
-// aligned to G lanes; sub = lane % G) between nc >= 1 candidates (ascending
-// indices cand[0..nc)), d <= 4 G F. Lane sub holds coordinates 4 (f G + sub)
+// aligned to G lanes; sub = lane % G) between nc >= 1 candidates (indices
+// cand[0..nc), any order), d <= 4 G F. Lane sub holds coordinates 4 (f G + sub)
 // .. + 3 for f < F (a group's loads cover 16 G contiguous bytes) of the point
 // in registers; the candidates are taken NQ at a time (four, or two when the
 // slices are long), all their slices loaded before any arithmetic, so a short
@@ -115,7 +115,7 @@ __device__ __forceinline__ int group_settle(const float* __restrict__ x, const f
         hi = sh;
       }
       const float D = __fadd_rn(hi, lo);
-      if (q0 + u < nc && D < best) {  // candidates in increasing index order: strict < keeps the lower index
+      if (q0 + u < nc && (D < best || (D == best && jq[u] < jb))) {  // equal distances: the lower index
         best = D;
         jb = jq[u];
       }
