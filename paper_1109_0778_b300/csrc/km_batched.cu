@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(256) b_permute_kernel(BWork W) {
 // boundary and holds as many rows of its instance's width as fit a stage, up
 // to 32. A run may cross instance boundaries, which flush like cluster
 // boundaries.
-constexpr int kSegStage = 1024;                                 // floats per stage (8 rows of 128)
+constexpr int kSegStage = 768;                                  // floats per stage (6 rows of 128)
 constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;      // 8 warps x 2 stages
 
 // One batch of the segmented sum: rows [bs, bs + bn) of instance q (halted
@@ -550,7 +550,7 @@ __device__ __forceinline__ int packed_width(int d) {
   return p;
 }
 
-__global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
+__global__ void __launch_bounds__(256, 4) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
@@ -788,7 +788,7 @@ cudaError_t init_batched() {
 
 cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s) {
   int64_t blocks = (W.R + 8 * 64 - 1) / (8 * 64);
-  if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
+  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();  // four CTAs of 8 warps per SM
   b_segsum_kernel<<<(int)blocks, 256, kSegSmem, s>>>(W);
   return cudaGetLastError();
 }
