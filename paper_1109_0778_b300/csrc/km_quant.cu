@@ -23,6 +23,24 @@ namespace km {
 
 namespace {
 
+// Rows of X a warp of the point quantisation loads at once (their loads in
+// flight together), and the lane slices of one row (d <= kMaxD).
+constexpr int kQU = 4;
+constexpr int kQV = kMaxD / 32;
+
+// xv[u][v] = x[i0 + u][v 32 + lane] (0 past d or past the last row).
+__device__ __forceinline__ void load_rows(const float* __restrict__ X, int64_t n, int d, int64_t i0, int lane,
+                                          float (&xv)[kQU][kQV]) {
+#pragma unroll
+  for (int u = 0; u < kQU; ++u) {
+#pragma unroll
+    for (int v = 0; v < kQV; ++v) {
+      const int t = v * 32 + lane;
+      xv[u][v] = (i0 + u < n && t < d) ? __ldg(X + (i0 + u) * d + t) : 0.f;
+    }
+  }
+}
+
 // Xh (E4M3 with -h_j folded into the contraction; null otherwise): row i's
 // [1/s_i, 1/s_i, 1/s_i, 0, ...] slice (store_row_slice).
 // mu (null: no centring): the codes and statistics are those of the centred
@@ -39,35 +57,46 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const float* x = X + i * d;
-    float amax = 0.f;
-    if (FP8)
-      for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(__fsub_rn(x[t], mus[t])));
-    const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
-    const float inv = FP8 ? pow2_inv(sc) : 1.f;
-    float sxx = 0.f, sqq = 0.f, sdd = 0.f, sraw = 0.f;
-    uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
-    for (int t = lane; t < Kp; t += 32) {
-      const float xt = t < d ? x[t] : 0.f;
-      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-      const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
-      const float r = vq - v;
-      sxx = fmaf(v, v, sxx);
-      sqq = fmaf(vq, vq, sqq);
-      sdd = fmaf(r, r, sdd);
-      sraw = fmaf(xt, xt, sraw);
-    }
-    sxx = warp_sum(sxx);
-    sqq = warp_sum(sqq);
-    sdd = warp_sum(sdd);
-    sraw = warp_sum(sraw);
-    if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(sqq) || !isfinite(sraw)) ctl->nonfinite = 1;
-      const float nbv = norm_bound(sxx, d);
-      xs[i] = make_float4(sc, norm_bound(sqq, d), centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
-      if (xnorm) xnorm[i] = norm_bound(sraw, d);
-      if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
+  for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
+    float xv[kQU][kQV];
+    load_rows(X, n, d, i0, lane, xv);
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const int64_t i = i0 + u;
+      if (i >= n) break;
+      float amax = 0.f;
+      if (FP8)
+#pragma unroll
+        for (int v = 0; v < kQV; ++v)
+          if (v * 32 + lane < d) amax = fmaxf(amax, fabsf(__fsub_rn(xv[u][v], mus[v * 32 + lane])));
+      const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
+      const float inv = FP8 ? pow2_inv(sc) : 1.f;
+      float sxx = 0.f, sqq = 0.f, sdd = 0.f, sraw = 0.f;
+      uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
+#pragma unroll
+      for (int sl = 0; sl < kQV; ++sl) {
+        const int t = sl * 32 + lane;
+        if (t >= Kp) break;
+        const float xt = xv[u][sl];
+        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+        const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
+        const float r = vq - v;
+        sxx = fmaf(v, v, sxx);
+        sqq = fmaf(vq, vq, sqq);
+        sdd = fmaf(r, r, sdd);
+        sraw = fmaf(xt, xt, sraw);
+      }
+      sxx = warp_sum(sxx);
+      sqq = warp_sum(sqq);
+      sdd = warp_sum(sdd);
+      sraw = warp_sum(sraw);
+      if (lane == 0) {
+        if (!isfinite(sxx) || !isfinite(sqq) || !isfinite(sraw)) ctl->nonfinite = 1;
+        const float nbv = norm_bound(sxx, d);
+        xs[i] = make_float4(sc, norm_bound(sqq, d), centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
+        if (xnorm) xnorm[i] = norm_bound(sraw, d);
+        if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
+      }
     }
   }
 }
@@ -83,32 +112,41 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const float* x = X + i * d;
-    float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f, sraw = 0.f;
-    __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
-    for (int t = lane; t < Kp; t += 32) {
-      const float xt = t < d ? x[t] : 0.f;
-      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-      float hi, lo;
-      const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
-      sxx = fmaf(v, v, sxx);
-      shh = fmaf(hi, hi, shh);
-      sll = fmaf(lo, lo, sll);
-      sdd = fmaf(r, r, sdd);
-      sraw = fmaf(xt, xt, sraw);
-    }
-    sxx = warp_sum(sxx);
-    shh = warp_sum(shh);
-    sll = warp_sum(sll);
-    sdd = warp_sum(sdd);
-    sraw = warp_sum(sraw);
-    if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(shh) || !isfinite(sraw)) ctl->nonfinite = 1;
-      const float nbv = norm_bound(sxx, d);
-      xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)),
-                          centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
-      if (xnorm) xnorm[i] = norm_bound(sraw, d);
+  for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
+    float xv[kQU][kQV];
+    load_rows(X, n, d, i0, lane, xv);
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const int64_t i = i0 + u;
+      if (i >= n) break;
+      float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f, sraw = 0.f;
+      __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
+#pragma unroll
+      for (int sl = 0; sl < kQV; ++sl) {
+        const int t = sl * 32 + lane;
+        if (t >= Kp) break;
+        const float xt = xv[u][sl];
+        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+        float hi, lo;
+        const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
+        sxx = fmaf(v, v, sxx);
+        shh = fmaf(hi, hi, shh);
+        sll = fmaf(lo, lo, sll);
+        sdd = fmaf(r, r, sdd);
+        sraw = fmaf(xt, xt, sraw);
+      }
+      sxx = warp_sum(sxx);
+      shh = warp_sum(shh);
+      sll = warp_sum(sll);
+      sdd = warp_sum(sdd);
+      sraw = warp_sum(sraw);
+      if (lane == 0) {
+        if (!isfinite(sxx) || !isfinite(shh) || !isfinite(sraw)) ctl->nonfinite = 1;
+        const float nbv = norm_bound(sxx, d);
+        xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)),
+                            centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
+        if (xnorm) xnorm[i] = norm_bound(sraw, d);
+      }
     }
   }
 }
@@ -125,39 +163,50 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
-  for (int64_t i = warp; i < n; i += nwarps) {
-    const float* x = X + i * d;
-    float amax = 0.f;
-    for (int t = lane; t < d; t += 32) amax = fmaxf(amax, fabsf(__fsub_rn(x[t], mus[t])));
-    const float sc8 = pow2_scale(warp_max(amax));
-    const float inv8 = pow2_inv(sc8);
-    float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f, sraw = 0.f;
-    uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
-    for (int t = lane; t < Kp16; t += 32) {
-      const float xt = t < d ? x[t] : 0.f;
-      sraw = fmaf(xt, xt, sraw);
-      const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-      const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
-      uint8_t dummy;
-      const float q8 = quantise<1>(v, sc8, inv8, &dummy);
-      sxx = fmaf(v, v, sxx);
-      sqq16 = fmaf(q16, q16, sqq16);
-      sdd16 = fmaf(q16 - v, q16 - v, sdd16);
-      sqq8 = fmaf(q8, q8, sqq8);
-      sdd8 = fmaf(q8 - v, q8 - v, sdd8);
-    }
-    sxx = warp_sum(sxx);
-    sqq16 = warp_sum(sqq16);
-    sdd16 = warp_sum(sdd16);
-    sqq8 = warp_sum(sqq8);
-    sdd8 = warp_sum(sdd8);
-    sraw = warp_sum(sraw);
-    if (lane == 0) {
-      if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8) || !isfinite(sraw)) ctl->nonfinite = 1;
-      const float nbv = norm_bound(sxx, d), xn = centred_norm(nbv, mu);
-      xs16[i] = make_float4(1.f, norm_bound(sqq16, d), centred_resid(nbv, norm_bound(sdd16, d), mu), xn);
-      xs8[i] = make_float4(sc8, norm_bound(sqq8, d), centred_resid(nbv, norm_bound(sdd8, d), mu), xn);
-      if (xnorm) xnorm[i] = norm_bound(sraw, d);
+  for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
+    float xv[kQU][kQV];
+    load_rows(X, n, d, i0, lane, xv);
+#pragma unroll
+    for (int u = 0; u < kQU; ++u) {
+      const int64_t i = i0 + u;
+      if (i >= n) break;
+      float amax = 0.f;
+#pragma unroll
+      for (int v = 0; v < kQV; ++v)
+        if (v * 32 + lane < d) amax = fmaxf(amax, fabsf(__fsub_rn(xv[u][v], mus[v * 32 + lane])));
+      const float sc8 = pow2_scale(warp_max(amax));
+      const float inv8 = pow2_inv(sc8);
+      float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f, sraw = 0.f;
+      uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
+#pragma unroll
+      for (int sl = 0; sl < kQV; ++sl) {
+        const int t = sl * 32 + lane;
+        if (t >= Kp16) break;
+        const float xt = xv[u][sl];
+        sraw = fmaf(xt, xt, sraw);
+        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+        const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
+        uint8_t dummy;
+        const float q8 = quantise<1>(v, sc8, inv8, &dummy);
+        sxx = fmaf(v, v, sxx);
+        sqq16 = fmaf(q16, q16, sqq16);
+        sdd16 = fmaf(q16 - v, q16 - v, sdd16);
+        sqq8 = fmaf(q8, q8, sqq8);
+        sdd8 = fmaf(q8 - v, q8 - v, sdd8);
+      }
+      sxx = warp_sum(sxx);
+      sqq16 = warp_sum(sqq16);
+      sdd16 = warp_sum(sdd16);
+      sqq8 = warp_sum(sqq8);
+      sdd8 = warp_sum(sdd8);
+      sraw = warp_sum(sraw);
+      if (lane == 0) {
+        if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8) || !isfinite(sraw)) ctl->nonfinite = 1;
+        const float nbv = norm_bound(sxx, d), xn = centred_norm(nbv, mu);
+        xs16[i] = make_float4(1.f, norm_bound(sqq16, d), centred_resid(nbv, norm_bound(sdd16, d), mu), xn);
+        xs8[i] = make_float4(sc8, norm_bound(sqq8, d), centred_resid(nbv, norm_bound(sdd8, d), mu), xn);
+        if (xnorm) xnorm[i] = norm_bound(sraw, d);
+      }
     }
   }
 }
@@ -291,70 +340,69 @@ quant_c_kernel(const float* __restrict__ C, int k, int kp, int d, int Kp, uint8_
 
 constexpr int kCentreThreads = 512;
 
-// The centring vector of a call (one block): mu_t = RN(mean_j c_jt) over the
-// call's initial centroids (FP64 sums), kept only when it pays -- when the
-// centred centroids' largest norm is at most half the uncentred one (a common
-// offset of the data dominates its spread); otherwise mu = 0 (the codes of x
-// itself). Any fixed vector keeps every distance.
+// The centring vector of a call (one block): mu_t = the mean of column t of
+// the call's initial centroids, kept only when it pays -- when the centred
+// centroids' largest norm is at most half the uncentred one (a common offset of
+// the data dominates its spread); otherwise mu = 0 (the codes of x itself).
+// Any fixed vector keeps every distance, so mu need not be the exact mean: FP32
+// sums in a fixed order (per warp over its rows, then the warps in order) make
+// it a deterministic function of C at FP32 speed.
 __global__ void __launch_bounds__(kCentreThreads) centre_kernel(const float* __restrict__ C, int k, int d,
                                                                 float* __restrict__ mu) {
   constexpr int NW = kCentreThreads / 32, V = kMaxD / 32;
-  __shared__ double part[NW][kMaxD];  // per-warp column sums, added in warp order
+  __shared__ float part[NW][kMaxD];  // per-warp column sums, added in warp order
   __shared__ float mus[kMaxD];
-  __shared__ double mx[2][NW];
+  __shared__ float mx[2][NW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double acc[V];
+  float acc[V];
 #pragma unroll
-  for (int v = 0; v < V; ++v) acc[v] = 0.0;
+  for (int v = 0; v < V; ++v) acc[v] = 0.f;
   for (int j = warp; j < k; j += NW) {  // warp w: rows w, w + NW, ...; lane: columns lane + 32 v
     const float* c = C + (int64_t)j * d;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int t = v * 32 + lane;
-      if (t < d) acc[v] += (double)__ldg(c + t);
+      if (t < d) acc[v] += __ldg(c + t);
     }
   }
 #pragma unroll
   for (int v = 0; v < V; ++v) part[warp][v * 32 + lane] = acc[v];
   __syncthreads();
   for (int t = tid; t < d; t += kCentreThreads) {
-    double s = 0.0;
+    float s = 0.f;
     for (int w = 0; w < NW; ++w) s += part[w][t];
-    mus[t] = __double2float_rn(s / (double)k);
+    mus[t] = s / (float)k;
   }
   __syncthreads();
-  double m0 = 0.0, m1 = 0.0;  // max_j ||c_j||^2, max_j ||c_j - mu||^2
+  float m0 = 0.f, m1 = 0.f;  // max_j ||c_j||^2, max_j ||c_j - mu||^2
   for (int j = warp; j < k; j += NW) {
     const float* c = C + (int64_t)j * d;
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int t = v * 32 + lane;
       if (t < d) {
-        const double x = (double)__ldg(c + t), e = x - (double)mus[t];
-        a = fma(x, x, a);
-        b = fma(e, e, b);
+        const float x = __ldg(c + t), e = x - mus[t];
+        a = fmaf(x, x, a);
+        b = fmaf(e, e, b);
       }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    m0 = fmax(m0, a);
-    m1 = fmax(m1, b);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    m0 = fmaxf(m0, a);
+    m1 = fmaxf(m1, b);
   }
   if (lane == 0) {
     mx[0][warp] = m0;
     mx[1][warp] = m1;
   }
   __syncthreads();
-  double M0 = mx[0][0], M1 = mx[1][0];
+  float M0 = mx[0][0], M1 = mx[1][0];
   for (int w = 1; w < NW; ++w) {
-    M0 = fmax(M0, mx[0][w]);
-    M1 = fmax(M1, mx[1][w]);
+    M0 = fmaxf(M0, mx[0][w]);
+    M1 = fmaxf(M1, mx[1][w]);
   }
-  const bool keep = M1 <= 0.25 * M0;
+  const bool keep = M1 <= 0.25f * M0;
   for (int t = tid; t < d; t += kCentreThreads) mu[t] = keep ? mus[t] : 0.f;
 }
 
