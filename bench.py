@@ -772,7 +772,7 @@ def run_plain(torch, km, dev, local, args):
     per call; the staged path (one launch per stage, graph-captured) is timed beside it."""
     w = WORKLOADS["plain_n10k_d16_k8"]
     _, _, Xd, C0d = single_problem(torch, dev, w, pinned=False)
-    reps = max(20, args.steps)
+    reps = max(400, args.steps)  # ~0.1 s of calls, so one slow call does not set the mean
     r = time_runs(torch, km, dev, local, None, Xd, C0d, w, "fp32", reps, 3, profile=False)
     rs = time_runs(torch, km, dev, local, None, Xd, C0d, w, "fp32", reps, 3, profile=True)
     return {"workload": w.name, "us_per_iter": 1e6 / r["iter_s"], "iter_s": r["iter_s"], "steps": reps,

@@ -714,7 +714,10 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   if ((rc = ensure_ws(c, L, s))) return rc;
   if (reuse && c->ws_gen != xc.ws_gen) reuse = false;  // the workspace was reallocated
   KM_TRACE("workspace ready at %p (%zu bytes)\n", c->ws, c->ws_bytes);
-  const size_t host_need = sizeof(Ctl) + (size_t)iters * (8 * 6 + 4) + 64;
+  // the per-step histories are consecutive regions of the workspace: read back with the control block in
+  // two copies (host layout: the control block, then the histories at their workspace offsets from L.obj)
+  const size_t hist_bytes = L.queued + 8 * (size_t)iters - L.obj;
+  const size_t host_need = align_up(sizeof(Ctl), 64) + hist_bytes + 64;
   if (host_need > c->host_bytes) {
     if (c->host) cudaFreeHost(c->host);
     c->host = nullptr;
@@ -897,21 +900,16 @@ int run_locked(DevCtx* c, const km_opts& o, const Problem& p_in, int iters, doub
   KM_CUDA(cudaEventRecord(c->ev1, s));
   char* h = (char*)c->host;
   Ctl* hc = (Ctl*)h;
-  double* hobj = (double*)(h + align_up(sizeof(Ctl), 64));
-  double* hshift = hobj + iters;
-  unsigned long long* hchanged = (unsigned long long*)(hshift + iters);
-  unsigned long long* hflag = hchanged + iters;
-  unsigned long long* hfull = hflag + iters;
-  unsigned long long* hqueued = hfull + iters;
-  int* hempty = (int*)(hqueued + iters);
+  char* hh = h + align_up(sizeof(Ctl), 64);  // the histories, at their offsets from L.obj
+  const double* hobj = (const double*)hh;
+  const double* hshift = (const double*)(hh + (L.shift - L.obj));
+  const unsigned long long* hchanged = (const unsigned long long*)(hh + (L.changed - L.obj));
+  const unsigned long long* hflag = (const unsigned long long*)(hh + (L.flagged - L.obj));
+  const unsigned long long* hfull = (const unsigned long long*)(hh + (L.full - L.obj));
+  const unsigned long long* hqueued = (const unsigned long long*)(hh + (L.queued - L.obj));
+  const int* hempty = (const int*)(hh + (L.empty - L.obj));
   KM_CUDA(cudaMemcpyAsync(hc, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hobj, w.obj_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hshift, w.shift_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hchanged, w.changed_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hflag, w.flagged_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hfull, w.full_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hqueued, w.queued_hist, 8 * (size_t)iters, cudaMemcpyDeviceToHost, s));
-  KM_CUDA(cudaMemcpyAsync(hempty, w.empty_hist, 4 * (size_t)iters, cudaMemcpyDeviceToHost, s));
+  KM_CUDA(cudaMemcpyAsync(hh, (const char*)c->ws + L.obj, hist_bytes, cudaMemcpyDeviceToHost, s));
   KM_CUDA(cudaStreamSynchronize(s));
   if (hc->iters_done < 0 || hc->iters_done > iters)
     return fail(KM_ECUDA, "device control block is inconsistent (%d steps recorded, %d run)", hc->iters_done, iters);
