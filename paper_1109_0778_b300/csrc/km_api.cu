@@ -1437,7 +1437,7 @@ struct BatchPlan {
   std::vector<int> order;  // flattened position -> caller's instance index
   std::vector<BInst> inst;
   std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
-  std::vector<int64_t> seg_off;   // prefix sums of the segmented sum's row costs
+  std::vector<BChunk> sitems;     // work items of the segmented sum: about 96 KB of X each
   std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
   std::vector<BChunk> rchunks;    // row chunks of the count and scatter stages
   std::vector<int32_t> kc_inst, kp_inst;  // instance of each flattened (padded) centroid
@@ -1474,7 +1474,6 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
   P.kc_off.assign(count + 1, 0);
   P.kp_off.assign(count + 1, 0);
   P.tile_off.assign(count + 1, 0);
-  P.seg_off.assign(count + 1, 0);
   for (int q = 0; q < count; ++q) {
     const km_instance& s = in[P.order[q]];
     BInst& I = P.inst[q];
@@ -1522,8 +1521,11 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     P.kc_off[q + 1] = P.KC;
     P.kp_off[q + 1] = P.KP;
     P.tile_off[q + 1] = P.T;
-    // a row of the segmented sum costs about its bytes: the FP32 row, its codes, labels and statistics
-    P.seg_off[q + 1] = P.seg_off[q] + s.n * (int64_t)(4 * s.d + esz * s.d + 40);
+    {  // segmented-sum items: about 96 KB of rows, a multiple of 32 rows, at most 4096
+      const int64_t per = std::min<int64_t>(4096, std::max<int64_t>(32, (98304 / (4 * s.d)) / 32 * 32));
+      for (int64_t r = 0; r < s.n; r += per)
+        P.sitems.push_back(BChunk{I.row_off + r, q, (int)std::min<int64_t>(per, s.n - r)});
+    }
     P.nkb_max = std::max(P.nkb_max, I.nkb);
     P.kp_max = std::max(P.kp_max, I.kp);
     P.kmax = std::max(P.kmax, s.k);
@@ -1615,7 +1617,7 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.kc = take(8 * (nb + 1));
   L.kp = take(8 * (nb + 1));
   L.tile = take(8 * (nb + 1));
-  L.seg = take(8 * (nb + 1));
+  L.seg = take(sizeof(BChunk) * P.sitems.size());
   L.cta = take(8 * P.cta_tile.size());
   L.rch = take(sizeof(BChunk) * P.rchunks.size());
   L.kci = take(4 * P.kc_inst.size());
@@ -1692,7 +1694,8 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.kc_off = (const int64_t*)(B + o_kc);
   W.kp_off = (const int64_t*)(B + o_kp);
   W.tile_off = (const int64_t*)(B + o_tile);
-  W.seg_off = (const int64_t*)(B + BL.seg);
+  W.sitems = (const BChunk*)(B + BL.seg);
+  W.nsitems = (int64_t)P.sitems.size();
   W.cta_tile = (const int64_t*)(B + BL.cta);
   W.cta_grid = (int)P.cta_tile.size() - 1;
   W.rchunks = (const BChunk*)(B + BL.rch);
@@ -1745,7 +1748,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   KM_CUDA(cudaMemcpyAsync(B + o_kc, P.kc_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_kp, P.kp_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.seg_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+  KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.sitems.data(), sizeof(BChunk) * P.sitems.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.rch, P.rchunks.data(), sizeof(BChunk) * P.rchunks.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.kci, P.kc_inst.data(), 4 * P.kc_inst.size(), cudaMemcpyHostToDevice, s));

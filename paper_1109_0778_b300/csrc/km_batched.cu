@@ -459,88 +459,19 @@ __global__ void __launch_bounds__(256) b_permute_kernel(BWork W) {
   }
 }
 
-// Segmented sums over the flattened sorted positions: each warp walks one
-// contiguous range; the rows are gathered into shared memory with cp.async one
-// batch ahead (as in km_reduce.cu); rows of d <= 16 are packed several per
-// warp step. A batch never crosses an instance
-// boundary and holds as many rows of its instance's width as fit a stage, up
-// to 32. A run may cross instance boundaries, which flush like cluster
-// boundaries.
-constexpr int kSegStage = 768;                                  // floats per stage (6 rows of 128)
-constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;      // 8 warps x 2 stages
-
-// One batch of the segmented sum: rows [bs, bs + bn) of instance q (halted
-// instances: q = -1), row stride rs floats in the stage; lane r < bn holds row
-// r's point i and label j.
-struct SegBatch {
-  int64_t bs;
-  int bn, rs, q, d;
-  const float* X;
-  int i, j;
-};
-
-// The rows of one batch, V = ceil(d / 32) registers per lane (only the first V
-// of the kMaxV accumulators are touched). cur_j: the cluster being summed;
-// `flush` adds the partial sums of cur_j to the FP64 sums.
-template <int V, typename Flush>
-__device__ __forceinline__ void seg_rows(const SegBatch& B, const float* st, int lane, int d, const float* C,
-                                         float (&s)[kMaxV], float (&c)[kMaxV], float (&cj)[kMaxV], float& objS,
-                                         float& objC, int& cur_j, Flush&& flush) {
-  // rows that start a cluster run (lane r holds row r's label), found once per batch
-  const int jprev = __shfl_up_sync(0xffffffffu, B.j, 1);
-  const unsigned starts = __ballot_sync(0xffffffffu, lane < B.bn && B.j != (lane == 0 ? cur_j : jprev));
-  for (int r = 0; r < B.bn;) {
-    if ((starts >> r) & 1u) {  // the same for every lane
-      flush();
-      cur_j = __shfl_sync(0xffffffffu, B.j, r);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int t = v * 32 + lane;
-        cj[v] = t < d ? C[(int64_t)cur_j * d + t] : 0.f;
-      }
-    }
-    const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
-    const int rend = later ? __ffs(later) - 1 : B.bn;
-    for (; r < rend; ++r) {
-      float xr[V], qd = 0.f;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int t = v * 32 + lane;
-        xr[v] = t < d ? st[r * B.rs + t] : 0.f;
-        kahan_add(s[v], c[v], xr[v]);
-        const float df = __fsub_rn(xr[v], cj[v]);
-        qd = fmaf(df, df, qd);
-      }
-      kahan_add(objS, objC, qd);
-    }
-  }
-}
-
-// Rows of d <= 16 (dp = the power of two >= d, 32 / dp rows per step): lane
-// group g = lane / dp takes row r0 + g, lane t = lane % dp its column t. Each
-// lane keeps its own run (cluster cur_j) and flushes it alone.
-template <typename Flush>
-__device__ __forceinline__ void seg_rows_packed(const SegBatch& B, const float* st, int lane, int d, int dp,
-                                                const float* C, float& s, float& c, float& cj, float& objS,
-                                                float& objC, int& cur_j, Flush&& flush) {
-  const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
-  for (int r0 = 0; r0 < B.bn; r0 += G) {
-    const int r = r0 + g;
-    const bool ok = r < B.bn;
-    const int src = ok ? r : 0;
-    const int j = __shfl_sync(0xffffffffu, B.j, src);
-    if (!ok) continue;
-    if (j != cur_j) {
-      flush();
-      cur_j = j;
-      cj = t < d ? C[(int64_t)j * d + t] : 0.f;
-    }
-    const float xr = t < d ? st[r * B.rs + t] : 0.f;
-    kahan_add(s, c, xr);
-    const float df = __fsub_rn(xr, cj);
-    kahan_add(objS, objC, df * df);
-  }
-}
+// Segmented sums over the cluster-sorted positions of every instance. The
+// work items are host-built chunks of one instance's sorted positions (about
+// 96 KB of X each, a table as for the count and scatter), which warps take in
+// turn; within an item the instance and its row width are fixed, so the row
+// loop is specialised for V = ceil(d / 32) slices per lane, or packs 32 / dp
+// rows per warp step for d <= 16 (dp the power of two >= d). Rows are gathered
+// into shared memory with cp.async one batch ahead (their indices two batches
+// ahead), as in km_reduce.cu; each run of a cluster is summed in Kahan FP32 per
+// coordinate and added to the FP64 sums with one atomic per coordinate, and
+// the objective terms ||x_i - c_j||^2 of the item go to the instance's control
+// block with one atomic.
+constexpr int kSegStage = 1024;                              // floats per stage (8 rows of 128, 32 of 32)
+constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;   // 8 warps x 2 stages
 
 // Power of two >= d for the packed rows (d <= 16), 0 otherwise.
 __device__ __forceinline__ int packed_width(int d) {
@@ -550,123 +481,212 @@ __device__ __forceinline__ int packed_width(int d) {
   return p;
 }
 
-__global__ void __launch_bounds__(256, 4) b_segsum_kernel(BWork W) {
+// One item: sorted positions [it.r0, it.r0 + it.n) of instance it.b, V
+// slices of 32 coordinates per lane (16 < d <= 32 V).
+template <int V>
+__device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float* stage0, float* stage1, int lane) {
+  constexpr int RB = V == 1 ? 32 : (V == 2 ? 16 : 8);  // rows per batch (4 KB of stage)
+  constexpr int rs = 32 * V;                           // stage floats per row
+  const BInst& I = W.inst[it.b];
+  const int d = I.d;
+  const float* __restrict__ X = I.X;
+  const float* __restrict__ C = I.C;
+  double* sums = W.sums64 + I.sum_off;
+  const int32_t* perm = W.perm + it.r0;
+  const int32_t* labs = W.lab_sorted + it.r0;
+  const int nb = (it.n + RB - 1) / RB;
+  auto meta = [&](int bt, int& i, int& j) {  // lane r < RB: row bt RB + r
+    const int r = bt * RB + lane;
+    i = 0;
+    j = -1;
+    if (lane < RB && r < it.n) {
+      i = __ldg(perm + r);
+      j = __ldg(labs + r);
+    }
+  };
+  auto gather = [&](int bt, float* st, int i_lane) {
+    gather_rows(st, rs, X, d, min(RB, it.n - bt * RB), (int64_t)i_lane * d, lane);
+  };
+  float s[V], c[V], cj[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) s[v] = c[v] = cj[v] = 0.f;
+  float objS = 0.f, objC = 0.f;
+  int cur = -1;  // the run being summed
+  // this lane's partial sums of run cur into the FP64 sums
+  auto flush = [&]() {
+    if (cur < 0) return;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = v * 32 + lane;
+      if (t < d) atomicAdd(sums + (int64_t)cur * d + t, (double)s[v] - (double)c[v]);
+      s[v] = c[v] = 0.f;
+    }
+  };
+  int i_c = 0, j_c = -1, i_n = 0, j_n = -1;
+  meta(0, i_c, j_c);
+  gather(0, stage0, i_c);
+  if (nb > 1) meta(1, i_n, j_n);
+  for (int bt = 0; bt < nb; ++bt) {
+    float* st = (bt & 1) ? stage1 : stage0;
+    if (bt + 1 < nb) gather(bt + 1, (bt & 1) ? stage0 : stage1, i_n);
+    int i_nn = 0, j_nn = -1;
+    if (bt + 2 < nb) meta(bt + 2, i_nn, j_nn);
+    if (bt + 1 < nb) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncwarp();
+    const int rows = min(RB, it.n - bt * RB);
+    {
+      // rows that start a run (lane r holds row r's label), found once per batch
+      const int jprev = __shfl_up_sync(0xffffffffu, j_c, 1);
+      const unsigned starts = __ballot_sync(0xffffffffu, lane < rows && j_c != (lane == 0 ? cur : jprev));
+      for (int r = 0; r < rows;) {
+        if ((starts >> r) & 1u) {  // the same for every lane
+          flush();
+          cur = __shfl_sync(0xffffffffu, j_c, r);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            cj[v] = t < d ? C[(int64_t)cur * d + t] : 0.f;
+          }
+        }
+        const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
+        const int rend = later ? __ffs(later) - 1 : rows;
+        for (; r < rend; ++r) {
+          float qd = 0.f;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            const float xr = t < d ? st[r * rs + t] : 0.f;
+            kahan_add(s[v], c[v], xr);
+            const float df = __fsub_rn(xr, cj[v]);
+            qd = fmaf(df, df, qd);
+          }
+          kahan_add(objS, objC, qd);
+        }
+      }
+    }
+    __syncwarp();  // every lane is done with this stage before it is refilled
+    i_c = i_n;
+    j_c = j_n;
+    i_n = i_nn;
+    j_n = j_nn;
+  }
+  flush();
+  double o = (double)objS - (double)objC;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+  if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[it.b].objective, o);
+}
+
+// Packed rows (d <= 16, dp the power of two >= d): batches of up to 128 rows
+// (lane l holds the indices of rows l, l + 32, l + 64, l + 96), so that a warp
+// keeps a few KB of these short rows in flight; lane group g = lane / dp takes
+// row r0 + g of each step, lane t = lane mod dp its column t, and keeps its own
+// run (flushed alone).
+__device__ __forceinline__ void seg_item_packed(const BWork& W, const BChunk& it, float* stage0, float* stage1,
+                                                int lane) {
+  const BInst& I = W.inst[it.b];
+  const int d = I.d, dp = packed_width(d);
+  const int RB = min(128, kSegStage / dp);  // rows per batch (a multiple of 32)
+  const float* __restrict__ X = I.X;
+  const float* __restrict__ C = I.C;
+  double* sums = W.sums64 + I.sum_off;
+  const int32_t* perm = W.perm + it.r0;
+  const int32_t* labs = W.lab_sorted + it.r0;
+  const int nb = (it.n + RB - 1) / RB;
+  auto meta = [&](int bt, int (&i)[4], int (&j)[4]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int r = bt * RB + m * 32 + lane;
+      i[m] = 0;
+      j[m] = -1;
+      if (m * 32 < RB && r < it.n) {
+        i[m] = __ldg(perm + r);
+        j[m] = __ldg(labs + r);
+      }
+    }
+  };
+  auto gather = [&](int bt, float* st, const int (&i)[4]) {
+    const int rows = min(RB, it.n - bt * RB);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+      if (m * 32 < rows) gather_rows(st + m * 32 * dp, dp, X, d, min(32, rows - m * 32), (int64_t)i[m] * d, lane, false);
+    cp_async_commit();
+  };
+  const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
+  float s = 0.f, c = 0.f, cj = 0.f, objS = 0.f, objC = 0.f;
+  int cur = -1;  // this lane's run
+  auto flush = [&]() {
+    if (cur < 0) return;
+    if (t < d) atomicAdd(sums + (int64_t)cur * d + t, (double)s - (double)c);
+    s = c = 0.f;
+  };
+  int i_c[4], j_c[4], i_n[4], j_n[4];
+  meta(0, i_c, j_c);
+  gather(0, stage0, i_c);
+  if (nb > 1) meta(1, i_n, j_n);
+  for (int bt = 0; bt < nb; ++bt) {
+    float* st = (bt & 1) ? stage1 : stage0;
+    if (bt + 1 < nb) gather(bt + 1, (bt & 1) ? stage0 : stage1, i_n);
+    int i_nn[4], j_nn[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      i_nn[m] = 0;
+      j_nn[m] = -1;
+    }
+    if (bt + 2 < nb) meta(bt + 2, i_nn, j_nn);
+    if (bt + 1 < nb) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncwarp();
+    const int rows = min(RB, it.n - bt * RB);
+    for (int r0 = 0; r0 < rows; r0 += G) {
+      const int m = r0 >> 5;  // the same for every lane (G divides 32)
+      const int jm = m == 0 ? j_c[0] : (m == 1 ? j_c[1] : (m == 2 ? j_c[2] : j_c[3]));
+      const int r = r0 + g;
+      const bool ok = r < rows;
+      const int j = __shfl_sync(0xffffffffu, jm, ok ? (r & 31) : 0);
+      if (!ok) continue;
+      if (j != cur) {
+        flush();
+        cur = j;
+        cj = t < d ? C[(int64_t)j * d + t] : 0.f;
+      }
+      const float xr = t < d ? st[r * dp + t] : 0.f;
+      kahan_add(s, c, xr);
+      const float df = __fsub_rn(xr, cj);
+      kahan_add(objS, objC, df * df);
+    }
+    __syncwarp();  // every lane is done with this stage before it is refilled
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      i_c[m] = i_n[m];
+      j_c[m] = j_n[m];
+      i_n[m] = i_nn[m];
+      j_n[m] = j_nn[m];
+    }
+  }
+  flush();
+  double o = (double)objS - (double)objC;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
+  if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[it.b].objective, o);
+}
+
+__global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
   float* stage1 = stage0 + kSegStage;
-  const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
-  // this warp's positions: an equal share of the total row cost (rows of larger d cost more)
-  auto pos_at = [&](int64_t t) -> int64_t {
-    const int64_t T = W.seg_off[W.nb];
-    if (t >= T) return W.R;
-    const int b = find_block(W.seg_off, W.nb, t);
-    const int64_t per = (W.seg_off[b + 1] - W.seg_off[b]) / (W.row_off[b + 1] - W.row_off[b]);
-    return W.row_off[b] + (t - W.seg_off[b] + per - 1) / per;
-  };
-  const int64_t Tc = W.seg_off[W.nb];
-  const int64_t P0 = pos_at((int64_t)((double)Tc * gw / nw)), P1 = pos_at((int64_t)((double)Tc * (gw + 1) / nw));
-
-  // batch cursor: batches are cut in increasing order, the instance found by walking forward
-  int64_t cursor = P0;
-  int qw = P0 < P1 ? find_block(W.row_off, W.nb, P0) : 0;
-  auto cut = [&](SegBatch& B) {
-    B.bn = 0;
-    B.q = -1;
-    B.i = 0;
-    B.j = -1;
-    if (cursor >= P1) return;
-    while (W.row_off[qw + 1] <= cursor) ++qw;
-    const BInst& I = W.inst[qw];
-    B.d = I.d;
-    B.X = I.X;
-    const int dp = packed_width(B.d);
-    B.rs = dp ? dp : 32 * ((B.d + 31) / 32);
-    B.bs = cursor;
-    B.bn = (int)min(min((int64_t)min(32, kSegStage / B.rs), W.row_off[qw + 1] - cursor), P1 - cursor);
-    cursor += B.bn;
-    B.q = halted(W.ctls + qw) ? -1 : qw;
-    if (B.q >= 0 && lane < B.bn) {
-      B.i = W.perm[B.bs + lane];
-      B.j = W.lab_sorted[B.bs + lane];
-    }
-  };
-  auto gather = [&](const SegBatch& B, float* st) {
-    if (B.q >= 0) gather_rows(st, B.rs, B.X, B.d, B.bn, (int64_t)B.i * B.d, lane);
-    else cp_async_commit();
-  };
-
-  float s[kMaxV], c[kMaxV], cj[kMaxV];
-#pragma unroll
-  for (int v = 0; v < kMaxV; ++v) { s[v] = 0.f; c[v] = 0.f; cj[v] = 0.f; }
-  float objS = 0.f, objC = 0.f;
-  int cur_b = -1, cur_j = -1, cur_d = 0, cur_dp = 0;
-  int64_t cur_sum0 = 0;
-  const float* cur_C = nullptr;
-  auto flush = [&]() {  // this lane's partial sums of run cur_j (packed rows: column lane % cur_dp)
-    if (cur_j < 0) return;
-#pragma unroll
-    for (int v = 0; v < kMaxV; ++v) {
-      const int t = cur_dp ? (v == 0 ? (lane & (cur_dp - 1)) : cur_d) : v * 32 + lane;
-      if (t < cur_d) atomicAdd(W.sums64 + cur_sum0 + (int64_t)cur_j * cur_d + t, (double)s[v] - (double)c[v]);
-      s[v] = 0.f;
-      c[v] = 0.f;
-    }
-  };
-  auto flush_obj = [&]() {
-    if (cur_b < 0) return;
-    double o = (double)objS - (double)objC;
-#pragma unroll
-    for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
-    if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[cur_b].objective, o);
-    objS = objC = 0.f;
-  };
-
-  SegBatch Bc, Bn, Bnn;
-  cut(Bc);
-  if (Bc.bn > 0) {
-    gather(Bc, stage0);
+  const int64_t nw = (int64_t)gridDim.x * 8;
+  for (int64_t q = (int64_t)blockIdx.x * 8 + wib; q < W.nsitems; q += nw) {
+    const BChunk it = W.sitems[q];
+    if (halted(W.ctls + it.b)) continue;
+    const int d = W.inst[it.b].d;
+    if (d <= 16) seg_item_packed(W, it, stage0, stage1, lane);
+    else if (d <= 32) seg_item<1>(W, it, stage0, stage1, lane);
+    else if (d <= 64) seg_item<2>(W, it, stage0, stage1, lane);
+    else seg_item<4>(W, it, stage0, stage1, lane);
   }
-  cut(Bn);
-  for (int64_t bt = 0; Bc.bn > 0; ++bt) {
-    float* st = (bt & 1) ? stage1 : stage0;
-    if (Bn.bn > 0) {
-      gather(Bn, (bt & 1) ? stage0 : stage1);
-    }
-    cut(Bnn);
-    if (Bn.bn > 0) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    __syncwarp();
-    const int b = Bc.q;
-    if (b >= 0) {
-      if (b != cur_b) {
-        flush();
-        flush_obj();
-        cur_b = b;
-        cur_j = -1;
-        const BInst* I = W.inst + b;
-        // the instance's fields in registers
-        cur_d = I->d;
-        cur_dp = packed_width(cur_d);
-        cur_sum0 = I->sum_off;
-        cur_C = I->C;
-      }
-      const int d = cur_d;
-      if (cur_dp)
-        seg_rows_packed(Bc, st, lane, d, cur_dp, cur_C, s[0], c[0], cj[0], objS, objC, cur_j, flush);
-      else if (d <= 32)
-        seg_rows<1>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
-      else if (d <= 64)
-        seg_rows<2>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
-      else
-        seg_rows<kMaxV>(Bc, st, lane, d, cur_C, s, c, cj, objS, objC, cur_j, flush);
-    }
-    __syncwarp();  // every lane is done with this stage before it is refilled
-    Bc = Bn;
-    Bn = Bnn;
-  }
-  flush();
-  flush_obj();
 }
 
 // Divide per centroid of every instance; the warp that finishes an instance's
@@ -787,9 +807,9 @@ cudaError_t init_batched() {
 }
 
 cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s) {
-  int64_t blocks = (W.R + 8 * 64 - 1) / (8 * 64);
-  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();  // four CTAs of 8 warps per SM
-  b_segsum_kernel<<<(int)blocks, 256, kSegSmem, s>>>(W);
+  int64_t blocks = (W.nsitems + 7) / 8;
+  if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
+  b_segsum_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, kSegSmem, s>>>(W);
   return cudaGetLastError();
 }
 

@@ -27,8 +27,9 @@ __device__ __forceinline__ void cp_async_wait() {
 // row's 16-byte pieces, at most 32), one row per group, so a warp instruction
 // moves 32 / L rows. 16-byte pieces when rows start on 16-byte boundaries
 // (d a multiple of 4 and X itself 16-byte aligned), else 4-byte ones. Commits
-// one group.
-__device__ __forceinline__ void gather_rows(float* st, int rs, const float* X, int d, int bn, int64_t off, int lane) {
+// one group (unless commit is false: the caller commits several gathers as one).
+__device__ __forceinline__ void gather_rows(float* st, int rs, const float* X, int d, int bn, int64_t off, int lane,
+                                            bool commit = true) {
   const bool v4 = (d & 3) == 0 && ((uintptr_t)X & 15) == 0;
   const int cpr = v4 ? d >> 2 : d;  // pieces per row
   int lg = 0;
@@ -48,7 +49,7 @@ __device__ __forceinline__ void gather_rows(float* st, int rs, const float* X, i
       }
     }
   }
-  cp_async_commit();
+  if (commit) cp_async_commit();
 }
 
 }  // namespace km

@@ -236,7 +236,8 @@ struct BWork {
   const int64_t* kc_off;    // [nb + 1]
   const int64_t* kp_off;    // [nb + 1]
   const int64_t* tile_off;  // [nb + 1]
-  const int64_t* seg_off;   // [nb + 1] prefix sums of row costs (segmented-sum balance)
+  const BChunk* sitems;     // [nsitems] work items of the segmented sum (sorted positions of one instance)
+  int64_t nsitems;
   const int64_t* cta_tile;  // [cta_grid + 1] tile range of each CTA of the assignment launch
   int cta_grid;
   int64_t R, KC, KP, T;     // totals: rows, centroids, padded centroids, tiles
