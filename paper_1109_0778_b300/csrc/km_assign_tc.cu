@@ -434,6 +434,9 @@ __device__ __forceinline__ void score_block2(const uint32_t (&v)[32], const uint
                                 min3f(n11[6], n11[7], n11[8])),
                           fminf(n11[9], n11[10]));
   if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
+    // no candidate lies above the pair's minimum + margin (the row's best is at most that minimum),
+    // so a block whose minimum is above it needs no fold
+    thr = fminf(thr, __fadd_ru(fminf(mn, mn2), margin));
     if (mn <= thr) fold_block(top, s, mn, j0, thr, margin, re);
     if (mn2 <= thr) fold_block(top, s2, mn2, j0 + 32, thr, margin, re);
   }
@@ -459,6 +462,7 @@ __device__ __forceinline__ void score_block2_fold(const uint32_t (&v)[32], const
                                  max3f(n11[6], n11[7], n11[8])),
                            fmaxf(n11[9], n11[10]));
   if (__any_sync(0xffffffffu, fminf(mn, mn2) <= thr)) {
+    thr = fminf(thr, __fadd_ru(fminf(mn, mn2), margin));  // (as in score_block2)
     if (mn <= thr) fold_block<true>(top, v, mn, j0, thr, margin, re);
     if (mn2 <= thr) fold_block<true>(top, v2, mn2, j0 + 32, thr, margin, re);
   }
