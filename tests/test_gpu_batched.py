@@ -220,3 +220,20 @@ def test_batched_divide_correctly_rounded(km, precision):
         got = Cd.cpu().numpy()[nz]
         assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), int((got != want).sum())
         assert np.array_equal(s.cpu().numpy(), S.astype(np.float32))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batched_instance_with_more_clusters_than_the_shared_histogram(km, ref, precision):
+    """An instance with k > 8192 is counted and scattered with warp-aggregated global atomics
+    (the others with shared-memory histograms); one warm step of the batch against the oracle."""
+    shapes = [(20000, 8, 9000), (3000, 16, 50), (4000, 64, 300)]
+    data = make_batch(shapes, seed0=5100)
+    probs = to_device(km, data)
+    km.run_batched(probs, 1, precision=precision)
+    C_ins = [p[1].cpu().numpy().astype(np.float64) for p in probs]
+    stats = km.run_batched(probs, 1, precision=precision, warm_start=True)
+    for (X, _), (Xd, Cd, a, s, c), C_in, st in zip(data, probs, C_ins, stats):
+        ag = a.cpu().numpy()
+        parity.check_assign(ref, X, C_in, ag)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
+        parity.check_objective(ref, X, C_in, ag, st["objective"])
