@@ -1436,7 +1436,7 @@ struct BatchTune {
 struct BatchPlan {
   std::vector<int> order;  // flattened position -> caller's instance index
   std::vector<BInst> inst;
-  std::vector<int64_t> row_off, kc_off, kp_off, tile_off;
+  std::vector<int64_t> row_off, tile_off;
   std::vector<BChunk> sitems;     // work items of the segmented sum: about 96 KB of X each
   std::vector<int64_t> cta_tile;  // tile range of each CTA of the assignment launch
   std::vector<BChunk> rchunks;    // row chunks of the count and scatter stages
@@ -1471,8 +1471,6 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
   }
   P.inst.resize(count);
   P.row_off.assign(count + 1, 0);
-  P.kc_off.assign(count + 1, 0);
-  P.kp_off.assign(count + 1, 0);
   P.tile_off.assign(count + 1, 0);
   for (int q = 0; q < count; ++q) {
     const km_instance& s = in[P.order[q]];
@@ -1518,8 +1516,6 @@ int plan_batch(const km_instance* in, int count, int precision, const BatchTune&
     if (I.gsort) P.XQS += align_up((size_t)s.n * I.Kp * esz, 256);
     P.CQ += align_up((size_t)I.kp * I.Kp * esz, 256);
     P.row_off[q + 1] = P.R;
-    P.kc_off[q + 1] = P.KC;
-    P.kp_off[q + 1] = P.KP;
     P.tile_off[q + 1] = P.T;
     {  // segmented-sum items: about 96 KB of rows, a multiple of 32 rows, at most 4096
       const int64_t per = std::min<int64_t>(4096, std::max<int64_t>(32, (98304 / (4 * s.d)) / 32 * 32));
@@ -1597,7 +1593,7 @@ uint64_t batch_signature(const km_instance* in, int count, int precision) {
 
 // Byte offsets of the batch workspace.
 struct BLayout {
-  size_t ctl, inst, row, kc, kp, tile, seg, cta, rch, kci, kpi, maps, maps_s, slots, xs, xss, labs, perm, flags, offs, cur,
+  size_t ctl, inst, row, tile, seg, cta, rch, kci, kpi, maps, maps_s, slots, xs, xss, labs, perm, flags, offs, cur,
       sums, hq, scq, cst, xq, xqs, cq, csave, hist, total;
 };
 
@@ -1614,8 +1610,6 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
   L.ctl = take(sizeof(Ctl) * nb);
   L.inst = take(sizeof(BInst) * nb);
   L.row = take(8 * (nb + 1));
-  L.kc = take(8 * (nb + 1));
-  L.kp = take(8 * (nb + 1));
   L.tile = take(8 * (nb + 1));
   L.seg = take(sizeof(BChunk) * P.sitems.size());
   L.cta = take(8 * P.cta_tile.size());
@@ -1663,7 +1657,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   cudaStream_t s = (cudaStream_t)o.stream;
   const int nb = (int)P.inst.size();
   const BLayout BL = batch_layout(P, iters);
-  const size_t o_ctl = BL.ctl, o_inst = BL.inst, o_row = BL.row, o_kc = BL.kc, o_kp = BL.kp, o_tile = BL.tile,
+  const size_t o_ctl = BL.ctl, o_inst = BL.inst, o_row = BL.row, o_tile = BL.tile,
                o_maps = BL.maps, o_slots = BL.slots, o_xs = BL.xs, o_xss = BL.xss, o_labs = BL.labs,
                o_perm = BL.perm, o_flags = BL.flags, o_offs = BL.offs, o_cur = BL.cur, o_sums = BL.sums,
                o_hq = BL.hq, o_scq = BL.scq, o_xq = BL.xq, o_cq = BL.cq, o_csave = BL.csave, o_hist = BL.hist;
@@ -1691,8 +1685,6 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.nb = nb;
   W.iters = iters;
   W.row_off = (const int64_t*)(B + o_row);
-  W.kc_off = (const int64_t*)(B + o_kc);
-  W.kp_off = (const int64_t*)(B + o_kp);
   W.tile_off = (const int64_t*)(B + o_tile);
   W.sitems = (const BChunk*)(B + BL.seg);
   W.nsitems = (int64_t)P.sitems.size();
@@ -1745,8 +1737,6 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   }
   KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + o_kc, P.kc_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + o_kp, P.kp_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.sitems.data(), sizeof(BChunk) * P.sitems.size(), cudaMemcpyHostToDevice, s));
   KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));

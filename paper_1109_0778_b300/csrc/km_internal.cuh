@@ -233,8 +233,6 @@ struct BWork {
   const int32_t* kc_inst;   // [KC] instance of each flattened centroid
   const int32_t* kp_inst;   // [KP] instance of each flattened padded centroid
   const int64_t* row_off;   // [nb + 1] prefix sums (binary searched)
-  const int64_t* kc_off;    // [nb + 1]
-  const int64_t* kp_off;    // [nb + 1]
   const int64_t* tile_off;  // [nb + 1]
   const BChunk* sitems;     // [nsitems] work items of the segmented sum (sorted positions of one instance)
   int64_t nsitems;
@@ -289,26 +287,6 @@ __device__ __forceinline__ int find_block(const int64_t* off, int nb, int64_t g)
     else hi = mid;
   }
   return lo;
-}
-
-// find_block restricted to the instances lo..hi (off[lo] <= g < off[hi + 1]).
-__device__ __forceinline__ int find_block_in(const int64_t* off, int lo, int hi, int64_t g) {
-  int l = lo, h = hi + 1;
-  while (h - l > 1) {
-    const int mid = (l + h) >> 1;
-    if (off[mid] <= g) l = mid;
-    else h = mid;
-  }
-  return l;
-}
-
-// Instances of the first and last element a block works on this round (two
-// threads search the whole table, the block's threads then search only that
-// range). s_lh: two ints of shared memory; contains a barrier.
-__device__ __forceinline__ void block_instances(const int64_t* off, int nb, int64_t first, int64_t last, int* s_lh) {
-  if (threadIdx.x == 0) s_lh[0] = find_block(off, nb, first);
-  if (threadIdx.x == 32) s_lh[1] = find_block(off, nb, last);
-  __syncthreads();
 }
 
 cudaError_t init_batched();
