@@ -15,8 +15,13 @@ namespace km {
 
 namespace {
 
+// CTAs per SM: three for d <= 128 (up to 85 registers; short lists take two
+// candidates per round), two above (the point's longer slices need more).
 template <int V>
-__global__ void __launch_bounds__(256, 2)
+constexpr int recheck_ctas() { return V <= 4 ? 3 : 2; }
+
+template <int V>
+__global__ void __launch_bounds__(256, recheck_ctas<V>())
 recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, const float* __restrict__ h, int k,
                const FlagRec* __restrict__ flags, const unsigned long long* nflag_ptr, Ctl* ctl,
                int32_t* __restrict__ assign, int32_t* __restrict__ q_rows, int32_t* __restrict__ q_old,
@@ -81,7 +86,7 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
 #pragma unroll
       for (int a = 0; a < kMaxCand; ++a) cand[a] = __shfl_sync(0xffffffffu, cand_l[a], from);
       const int ncw = __reduce_max_sync(0xffffffffu, src >= 0 ? rnc : 0);
-      const int jb = group_settle<G, F>(X + (int64_t)ri * d, C, d, rnc, ncw, cand, sub);
+      const int jb = group_settle<G, F, (V <= 4 ? 2 : (F <= 4 ? 4 : 2))>(X + (int64_t)ri * d, C, d, rnc, ncw, cand, sub);
       if (src >= 0 && sub == 0) {
         assign[ri] = jb;
         changed += (rold != jb);
@@ -160,7 +165,7 @@ gather_queue_kernel(const float* __restrict__ X, int d, const float* __restrict_
 template <int V>
 cudaError_t recheck_v(const Problem& p, const Work& w, const float* h, const FlagRec* flags,
                       const unsigned long long* nflag, bool queue, cudaStream_t s) {
-  const int blocks = num_sms() * 2;  // every CTA resident (two per SM at up to 128 registers)
+  const int blocks = num_sms() * recheck_ctas<V>();  // every CTA resident
   recheck_kernel<V><<<blocks, 256, 0, s>>>(p.X, p.d, p.C, h, p.k, flags, nflag, w.ctl, p.assign,
                                            queue ? w.fq_rows : nullptr, queue ? w.fq_old : nullptr,
                                            queue ? w.fq_cap : 0);
