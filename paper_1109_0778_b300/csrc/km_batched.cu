@@ -210,7 +210,7 @@ __device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sm, cons
     for (int a = 0; a < kMaxCand; ++a) cand[a] = __shfl_sync(0xffffffffu, r.cand[a], from);
     const BInst& I = W.inst[b];
     const int ncw = __reduce_max_sync(0xffffffffu, src >= 0 ? rnc : 0);
-    const int jb = group_settle<G, F>(I.X + (int64_t)ri * I.d, I.C, I.d, rnc, ncw, cand, sub);
+    const int jb = group_settle<G, F, 2>(I.X + (int64_t)ri * I.d, I.C, I.d, rnc, ncw, cand, sub);
     if (src >= 0 && sub == 0) {
       I.assign[ri] = jb;
       if (rold != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sm, cons
 // A warp takes 32 flags at a time (nwarps apart); lane l loads flag l's record.
 // Short lists go to b_settle_short, the points to check against all k are
 // settled one at a time by the whole warp (b_settle).
-__global__ void __launch_bounds__(256, 2) b_recheck_kernel(BWork W) {
+__global__ void __launch_bounds__(256, 3) b_recheck_kernel(BWork W) {
   __shared__ __align__(16) float xs_all[8][kMaxV * 32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* xsh = xs_all[wib];
@@ -776,7 +776,7 @@ cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s) {
 }
 
 cudaError_t launch_b_recheck(const BWork& W, cudaStream_t s) {
-  b_recheck_kernel<<<num_sms() * 2, 256, 0, s>>>(W);  // every CTA resident (two per SM)
+  b_recheck_kernel<<<num_sms() * 3, 256, 0, s>>>(W);  // every CTA resident (three per SM)
   return cudaGetLastError();
 }
 
