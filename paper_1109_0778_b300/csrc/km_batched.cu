@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) b_permute_kernel(BWork W) {
 // coordinate and added to the FP64 sums with one atomic per coordinate, and
 // the objective terms ||x_i - c_j||^2 of the item go to the instance's control
 // block with one atomic.
-constexpr int kSegStage = 1024;                              // floats per stage (8 rows of 128, 32 of 32)
+constexpr int kSegStage = 768;                               // floats per stage (6 rows of 128, 24 of 32)
 constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;   // 8 warps x 2 stages
 
 // Power of two >= d for the packed rows (d <= 16), 0 otherwise.
@@ -485,7 +485,7 @@ __device__ __forceinline__ int packed_width(int d) {
 // slices of 32 coordinates per lane (16 < d <= 32 V).
 template <int V>
 __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float* stage0, float* stage1, int lane) {
-  constexpr int RB = V == 1 ? 32 : (V == 2 ? 16 : 8);  // rows per batch (4 KB of stage)
+  constexpr int RB = kSegStage / (32 * V);  // rows per batch (a 3 KB stage)
   constexpr int rs = 32 * V;                           // stage floats per row
   const BInst& I = W.inst[it.b];
   const int d = I.d;
@@ -672,7 +672,7 @@ __device__ __forceinline__ void seg_item_packed(const BWork& W, const BChunk& it
   if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[it.b].objective, o);
 }
 
-__global__ void __launch_bounds__(256, 3) b_segsum_kernel(BWork W) {
+__global__ void __launch_bounds__(256, 4) b_segsum_kernel(BWork W) {
   extern __shared__ __align__(16) float bseg_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float* stage0 = bseg_smem + (size_t)wib * 2 * kSegStage;
@@ -808,7 +808,7 @@ cudaError_t init_batched() {
 
 cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s) {
   int64_t blocks = (W.nsitems + 7) / 8;
-  if (blocks > 3 * num_sms()) blocks = 3 * num_sms();  // three CTAs of 8 warps per SM
+  if (blocks > 4 * num_sms()) blocks = 4 * num_sms();  // four CTAs of 8 warps per SM
   b_segsum_kernel<<<(int)(blocks > 0 ? blocks : 1), 256, kSegSmem, s>>>(W);
   return cudaGetLastError();
 }
