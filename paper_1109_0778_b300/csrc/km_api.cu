@@ -1569,7 +1569,13 @@ struct BatchCtx {
   cudaGraphExec_t gexec = nullptr;
   int graph_kernels = 0;  // kernel nodes of the cached graph
   std::vector<unsigned char> gkey;
+  std::vector<unsigned char> tkey;  // the plan whose tables and tensor maps the workspace holds
   std::vector<BatchCache> tuned;
+  // the last plan, reused while the caller's instances, precision and launch shape repeat
+  BatchPlan plan;
+  std::vector<km_instance> plan_in;
+  BatchTune plan_tune{0, -1, -1};
+  int plan_prec = -1;
 };
 
 BatchCtx g_batch[64];
@@ -1641,10 +1647,9 @@ BLayout batch_layout(const BatchPlan& P, int iters) {
 
 // Copies every instance's C back from the copy taken on entry of the last run.
 int restore_batch_c(const BatchCtx& bc, const BatchPlan& P, int iters, cudaStream_t s) {
-  const float* csave = (const float*)((const char*)bc.ws + batch_layout(P, iters).csave);
-  for (size_t b = 0, at = 0; b < P.inst.size(); at += (size_t)P.inst[b].k * P.inst[b].d, ++b)
-    KM_CUDA(cudaMemcpyAsync(P.inst[b].C, csave + at, 4 * (size_t)P.inst[b].k * P.inst[b].d, cudaMemcpyDeviceToDevice,
-                            s));
+  const BLayout BL = batch_layout(P, iters);
+  char* B = (char*)bc.ws;
+  KM_CUDA(launch_b_copy_c((const BInst*)(B + BL.inst), (int)P.inst.size(), (float*)(B + BL.csave), 1, s));
   KM_CUDA(cudaStreamSynchronize(s));
   return KM_OK;
 }
@@ -1671,6 +1676,7 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
       bc.ws_bytes = 0;
     }
     bc.gkey.clear();
+    bc.tkey.clear();
     const size_t want = align_up(need + need / 4, 1 << 20);
     if (cudaMalloc(&bc.ws, want) != cudaSuccess) {
       cudaGetLastError();
@@ -1724,34 +1730,52 @@ int run_batch_locked(DevCtx* c, BatchCtx& bc, const km_opts& o, const BatchPlan&
   W.flagged_hist = W.changed_hist + (size_t)nb * iters;
   W.full_hist = W.flagged_hist + (size_t)nb * iters;
   W.empty_hist = (int*)(W.full_hist + (size_t)nb * iters);
-  // tensor maps of every instance's codes
-  std::vector<CUtensorMap> maps(3 * nb);  // codes of X, codes of C; then the sorted copies
-  memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
-  const int esz = P.fp8 ? 1 : 2;
-  for (int b = 0; b < nb; ++b) {
-    const BInst& I = P.inst[b];
-    if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128, I.rowb))) return rc;
-    if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, I.bn, I.rowb))) return rc;
-    if (I.gsort && (rc = encode_codes_map(&maps[2 * nb + b], W.Xqs + I.xqs_off, I.n, I.Kp, esz, 128, I.rowb)))
-      return rc;
+  // Tables and tensor maps depend on the plan and the workspace only: they are
+  // uploaded when either changed since the last call (nothing writes them on the device).
+  std::vector<unsigned char> tk(sizeof(BInst) * nb);
+  memcpy(tk.data(), P.inst.data(), tk.size());
+  {
+    auto tapp = [&](const void* v, size_t n) { tk.insert(tk.end(), (const unsigned char*)v, (const unsigned char*)v + n); };
+    void* base = bc.ws;
+    tapp(&base, sizeof base);
+    tapp(&P.bn, sizeof P.bn);
+    tapp(&P.sorted, sizeof P.sorted);
+    tapp(&P.fp8, sizeof P.fp8);
+    const size_t nt = P.cta_tile.size(), ns = P.sitems.size();
+    tapp(&nt, sizeof nt);
+    tapp(&ns, sizeof ns);
   }
-  KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.sitems.data(), sizeof(BChunk) * P.sitems.size(), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.rch, P.rchunks.data(), sizeof(BChunk) * P.rchunks.size(), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.kci, P.kc_inst.data(), 4 * P.kc_inst.size(), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.kpi, P.kp_inst.data(), 4 * P.kp_inst.size(), cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
-  KM_CUDA(cudaMemcpyAsync(B + BL.maps_s, maps.data() + 2 * nb, sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice, s));
+  if (bc.tkey != tk) {
+    bc.tkey.clear();
+    // tensor maps of every instance's codes
+    std::vector<CUtensorMap> maps(3 * nb);  // codes of X, codes of C; then the sorted copies
+    memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    const int esz = P.fp8 ? 1 : 2;
+    for (int b = 0; b < nb; ++b) {
+      const BInst& I = P.inst[b];
+      if ((rc = encode_codes_map(&maps[2 * b], W.Xq + I.xq_off, I.n, I.Kp, esz, 128, I.rowb))) return rc;
+      if ((rc = encode_codes_map(&maps[2 * b + 1], W.Cq + I.cq_off, I.kp, I.Kp, esz, I.bn, I.rowb))) return rc;
+      if (I.gsort && (rc = encode_codes_map(&maps[2 * nb + b], W.Xqs + I.xqs_off, I.n, I.Kp, esz, 128, I.rowb)))
+        return rc;
+    }
+    KM_CUDA(cudaMemcpyAsync(B + o_inst, P.inst.data(), sizeof(BInst) * nb, cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + o_row, P.row_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + o_tile, P.tile_off.data(), 8 * (nb + 1), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.seg, P.sitems.data(), sizeof(BChunk) * P.sitems.size(), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.cta, P.cta_tile.data(), 8 * P.cta_tile.size(), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.rch, P.rchunks.data(), sizeof(BChunk) * P.rchunks.size(), cudaMemcpyHostToDevice,
+                            s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.kci, P.kc_inst.data(), 4 * P.kc_inst.size(), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.kpi, P.kp_inst.data(), 4 * P.kp_inst.size(), cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + o_maps, maps.data(), sizeof(CUtensorMap) * 2 * nb, cudaMemcpyHostToDevice, s));
+    KM_CUDA(cudaMemcpyAsync(B + BL.maps_s, maps.data() + 2 * nb, sizeof(CUtensorMap) * nb, cudaMemcpyHostToDevice, s));
+    // pageable sources: the copies are staged before cudaMemcpyAsync returns, so `maps` may go
+    bc.tkey.swap(tk);
+  }
   KM_CUDA(cudaMemsetAsync(W.ctls, 0, sizeof(Ctl) * nb, s));
   KM_CUDA(cudaMemsetAsync(W.sums64, 0, 8 * (size_t)P.SUMS, s));
   // C on entry, restored on error
-  float* csave = (float*)(B + o_csave);
-  for (int b = 0, at = 0; b < nb; at += P.inst[b].k * P.inst[b].d, ++b)
-    KM_CUDA(cudaMemcpyAsync(csave + at, P.inst[b].C, 4 * (size_t)P.inst[b].k * P.inst[b].d,
-                            cudaMemcpyDeviceToDevice, s));
+  KM_CUDA(launch_b_copy_c(W.inst, nb, (float*)(B + o_csave), 0, s));
   if (o.profile && (rc = ensure_events(c, 2 + (size_t)iters * kEvPerStep))) return rc;
   KM_CUDA(cudaEventRecord(c->ev0, s));
   if (o.profile) KM_CUDA(cudaEventRecord(c->prof[0], s));
@@ -1969,8 +1993,15 @@ KM_API int kmeans_run_batched(const km_opts* opts, const km_instance* inst, int3
     }
     bc.tuned.push_back(BatchCache{sig, tune});
   }
-  BatchPlan P;
-  if ((rc = plan_batch(inst, count, o.precision, tune, P))) return rc;
-  std::vector<int> idx(P.order);
-  return run_batch_locked(c, bc, o, P, iters, tol, per_inst, idx.data(), nullptr);
+  const bool same = bc.plan_prec == o.precision && bc.plan_tune.bn == tune.bn && bc.plan_tune.order == tune.order &&
+                    bc.plan_tune.sorted == tune.sorted && bc.plan_in.size() == (size_t)count &&
+                    memcmp(bc.plan_in.data(), inst, sizeof(km_instance) * count) == 0;
+  if (!same) {
+    bc.plan_prec = -1;
+    if ((rc = plan_batch(inst, count, o.precision, tune, bc.plan))) return rc;
+    bc.plan_in.assign(inst, inst + count);
+    bc.plan_tune = tune;
+    bc.plan_prec = o.precision;
+  }
+  return run_batch_locked(c, bc, o, bc.plan, iters, tol, per_inst, bc.plan.order.data(), nullptr);
 }

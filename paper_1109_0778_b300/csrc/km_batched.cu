@@ -28,6 +28,21 @@ __global__ void b_reset_kernel(Ctl* ctls, int nb, unsigned long long* flag_slots
   }
 }
 
+// Copies every instance's centroids to (restore = 0) or from (restore = 1) the
+// batch's saved copy, which holds instance b's k x d floats at its sums offset.
+// Grid row y takes instances y, y + gridDim.y, ..., grid-strided over their floats.
+__global__ void b_copy_c_kernel(const BInst* __restrict__ inst, int nb, float* __restrict__ csave, int restore) {
+  for (int b = blockIdx.y; b < nb; b += gridDim.y) {
+    const BInst& I = inst[b];
+    const int64_t m = (int64_t)I.k * I.d;
+    float* save = csave + I.sum_off;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+      if (restore) I.C[e] = save[e];
+      else save[e] = I.C[e];
+    }
+  }
+}
+
 // Codes and row statistics of every point of the batch. Each warp walks one
 // contiguous range of the flattened rows (instances found by walking forward
 // from one search), four rows of one instance at a time with their loads in
@@ -757,6 +772,11 @@ int grid_for(int64_t work_items, int per_block, int cap_per_sm) {
 
 cudaError_t launch_b_reset(const BWork& W, cudaStream_t s) {
   b_reset_kernel<<<(W.nb + 255) / 256, 256, 0, s>>>(W.ctls, W.nb, W.flag_slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_copy_c(const BInst* inst, int nb, float* csave, int restore, cudaStream_t s) {
+  b_copy_c_kernel<<<dim3(8, (unsigned)(nb < 65535 ? nb : 65535)), 256, 0, s>>>(inst, nb, csave, restore);
   return cudaGetLastError();
 }
 

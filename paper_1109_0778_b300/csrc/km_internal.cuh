@@ -300,6 +300,7 @@ cudaError_t launch_gda_cov(const float* X, int64_t n, int d, const int32_t* y, c
                            double* part, float* sigma, const Ctl* ctl, cudaStream_t s);
 size_t gda_cov_scratch_bytes(int64_t n, int d);
 cudaError_t launch_b_reset(const BWork& W, cudaStream_t s);
+cudaError_t launch_b_copy_c(const BInst* inst, int nb, float* csave, int restore, cudaStream_t s);
 cudaError_t launch_b_quant_x(const BWork& W, int fp8, cudaStream_t s);
 cudaError_t launch_b_quant_c(const BWork& W, int fp8, cudaStream_t s);
 cudaError_t launch_b_assign(const BWork& W, int fp8, int first, int sorted, int nkb_max, int kp_max, int bn,
