@@ -237,3 +237,44 @@ def test_batched_instance_with_more_clusters_than_the_shared_histogram(km, ref, 
         parity.check_assign(ref, X, C_in, ag)
         parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
         parity.check_objective(ref, X, C_in, ag, st["objective"])
+
+
+def test_batched_alternating_batches_parity(km, ref):
+    """Two batches of the same shapes (so the same tuned launch shape) on different tensors,
+    run A, B, A: each call must use its own instance tables and tensor maps."""
+    shapes = SHAPES[:5]
+    data_a, data_b = make_batch(shapes, seed0=2100), make_batch(shapes, seed0=2200)
+    pa, pb = to_device(km, data_a), to_device(km, data_b)
+    ba, bb = km.Batch(pa), km.Batch(pb)
+    for batch, data, probs in ((ba, data_a, pa), (bb, data_b, pb), (ba, data_a, pa)):
+        C_ins = [p[1].cpu().numpy().astype(np.float64) for p in probs]
+        stats = batch.run(1, precision="bf16")
+        for (X, _), (Xd, Cd, a, s, c), C_in, st in zip(data, probs, C_ins, stats):
+            ag = a.cpu().numpy()
+            parity.check_assign(ref, X, C_in, ag)
+            parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
+            parity.check_objective(ref, X, C_in, ag, st["objective"])
+
+
+def test_batched_nonfinite_restores_every_c(km, ref):
+    """A NaN in one instance's X fails the whole call with KM_ENONFINITE and puts every
+    instance's C back to its value on entry; the next clean call is unaffected."""
+    shapes = [(1000, 8, 4), (2000, 32, 40), (1500, 64, 300)]
+    data = make_batch(shapes, seed0=2300)
+    probs = to_device(km, data)
+    X1 = probs[1][0]
+    keep = X1[17, 5].item()
+    X1[17, 5] = float("nan")
+    before = [p[1].clone() for p in probs]
+    with pytest.raises(km.KMeansError) as e:
+        km.run_batched(probs, 3, precision="bf16")
+    assert e.value.status == km.KM_ENONFINITE
+    for p, c0 in zip(probs, before):
+        assert torch.equal(p[1], c0), "C must hold its value on entry after an error"
+    X1[17, 5] = keep
+    stats = km.run_batched(probs, 1, precision="bf16")
+    for (X, C0), (Xd, Cd, a, s, c), st in zip(data, probs, stats):
+        C_in = C0.astype(np.float64)
+        ag = a.cpu().numpy()
+        parity.check_assign(ref, X, C_in, ag)
+        parity.check_update(ref, X, C_in, ag, Cd.cpu().numpy(), s.cpu().numpy(), c.cpu().numpy())
