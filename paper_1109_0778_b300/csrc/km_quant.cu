@@ -24,17 +24,19 @@ namespace km {
 namespace {
 
 // Rows of X a warp of the point quantisation loads at once (their loads in
-// flight together), and the lane slices of one row (d <= kMaxD).
+// flight together). The kernels take V = lane slices of one code row
+// (Kp <= 32 V, a power of two up to kMaxD / 32), so that a row of d <= 128
+// holds no registers for the columns it does not have.
 constexpr int kQU = 4;
-constexpr int kQV = kMaxD / 32;
 
 // xv[u][v] = x[i0 + u][v 32 + lane] (0 past d or past the last row).
+template <int V>
 __device__ __forceinline__ void load_rows(const float* __restrict__ X, int64_t n, int d, int64_t i0, int lane,
-                                          float (&xv)[kQU][kQV]) {
+                                          float (&xv)[kQU][V]) {
 #pragma unroll
   for (int u = 0; u < kQU; ++u) {
 #pragma unroll
-    for (int v = 0; v < kQV; ++v) {
+    for (int v = 0; v < V; ++v) {
       const int t = v * 32 + lane;
       xv[u][v] = (i0 + u < n && t < d) ? __ldg(X + (i0 + u) * d + t) : 0.f;
     }
@@ -46,7 +48,7 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ X, int64_t n
 // mu (null: no centring): the codes and statistics are those of the centred
 // rows (km_quant.cuh); xnorm[i] gets the bound of the uncentred ||x_i|| (the
 // FP32 consumers: re-check screen, deterministic grid).
-template <int FP8>
+template <int FP8, int V>
 __global__ void __launch_bounds__(256)
 quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
                float4* __restrict__ xs, uint4* __restrict__ Xh, const float* __restrict__ mu,
@@ -58,7 +60,7 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
-    float xv[kQU][kQV];
+    float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
@@ -67,14 +69,14 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
       float amax = 0.f;
       if (FP8)
 #pragma unroll
-        for (int v = 0; v < kQV; ++v)
+        for (int v = 0; v < V; ++v)
           if (v * 32 + lane < d) amax = fmaxf(amax, fabsf(__fsub_rn(xv[u][v], mus[v * 32 + lane])));
       const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
       const float inv = FP8 ? pow2_inv(sc) : 1.f;
       float sxx = 0.f, sqq = 0.f, sdd = 0.f, sraw = 0.f;
       uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
 #pragma unroll
-      for (int sl = 0; sl < kQV; ++sl) {
+      for (int sl = 0; sl < V; ++sl) {
         const int t = sl * 32 + lane;
         if (t >= Kp) break;
         const float xt = xv[u][sl];
@@ -104,6 +106,7 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
 // Two-part BF16 codes (split_bf16): row i holds hi in columns [0, Kp) and lo
 // in [Kp, 2 Kp). Statistics: (1, ||hi|| + ||lo||, ||v - hi - lo||, ||v||),
 // norms rounded up.
+template <int V>
 __global__ void __launch_bounds__(256)
 quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
                      float4* __restrict__ xs, const float* __restrict__ mu, float* __restrict__ xnorm, Ctl* ctl) {
@@ -113,7 +116,7 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
-    float xv[kQU][kQV];
+    float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
@@ -122,7 +125,7 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
       float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f, sraw = 0.f;
       __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
 #pragma unroll
-      for (int sl = 0; sl < kQV; ++sl) {
+      for (int sl = 0; sl < V; ++sl) {
         const int t = sl * 32 + lane;
         if (t >= Kp) break;
         const float xt = xv[u][sl];
@@ -154,6 +157,7 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
 // BF16 codes and statistics for a cold first step, plus the E4M3 row scale and
 // statistics the later E4M3 steps use (their codes are written by the reduce
 // stage in sorted order).
+template <int V>
 __global__ void __launch_bounds__(256)
 quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uint8_t* __restrict__ Xq,
                     float4* __restrict__ xs16, float4* __restrict__ xs8, const float* __restrict__ mu,
@@ -164,7 +168,7 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
   __shared__ float mus[kMaxD];
   stage_mu(mus, mu, d);
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
-    float xv[kQU][kQV];
+    float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
@@ -172,14 +176,14 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
       if (i >= n) break;
       float amax = 0.f;
 #pragma unroll
-      for (int v = 0; v < kQV; ++v)
+      for (int v = 0; v < V; ++v)
         if (v * 32 + lane < d) amax = fmaxf(amax, fabsf(__fsub_rn(xv[u][v], mus[v * 32 + lane])));
       const float sc8 = pow2_scale(warp_max(amax));
       const float inv8 = pow2_inv(sc8);
       float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f, sraw = 0.f;
       uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
 #pragma unroll
-      for (int sl = 0; sl < kQV; ++sl) {
+      for (int sl = 0; sl < V; ++sl) {
         const int t = sl * 32 + lane;
         if (t >= Kp16) break;
         const float xt = xv[u][sl];
@@ -414,25 +418,51 @@ cudaError_t launch_centre(const Problem& p, const Work& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
-                           cudaStream_t s) {
-  int64_t blocks = (p.n + 7) / 8;
+// Blocks of the point quantisation: one warp per kQU rows, at most 16 blocks per SM.
+int quant_x_blocks(int64_t n) {
+  int64_t blocks = (n + 8 * kQU - 1) / (8 * kQU);
   const int64_t cap = (int64_t)num_sms() * 16;
   if (blocks > cap) blocks = cap;
+  return (int)(blocks > 0 ? blocks : 1);
+}
+
+template <int V>
+void launch_quant_x_v(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs, cudaStream_t s) {
+  const int blocks = quant_x_blocks(p.n);
   uint4* xh = reinterpret_cast<uint4*>(w.Xh);
-  if (mode == 2) quant_x_split_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.mu, w.xnorm, w.ctl);
+  if (mode == 2) quant_x_split_kernel<V><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, w.mu, w.xnorm, w.ctl);
   else if (mode == 1)
-    quant_x_kernel<1><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, xh, w.mu, w.xnorm, w.ctl);
-  else quant_x_kernel<0><<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, nullptr, w.mu, w.xnorm, w.ctl);
+    quant_x_kernel<1, V><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, xh, w.mu, w.xnorm, w.ctl);
+  else quant_x_kernel<0, V><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp, Xq, xs, nullptr, w.mu, w.xnorm, w.ctl);
+}
+
+// Lane slices of a code row of Kp columns (a power of two, d <= Kp <= kMaxD).
+int quant_slices(int Kp) {
+  const int v = (Kp + 31) / 32;
+  return v <= 1 ? 1 : v <= 2 ? 2 : v <= 4 ? 4 : 8;
+}
+
+cudaError_t launch_quant_x(const Problem& p, const Work& w, int mode, int Kp, uint8_t* Xq, float4* xs,
+                           cudaStream_t s) {
+  switch (quant_slices(Kp)) {
+    case 1: launch_quant_x_v<1>(p, w, mode, Kp, Xq, xs, s); break;
+    case 2: launch_quant_x_v<2>(p, w, mode, Kp, Xq, xs, s); break;
+    case 4: launch_quant_x_v<4>(p, w, mode, Kp, Xq, xs, s); break;
+    default: launch_quant_x_v<8>(p, w, mode, Kp, Xq, xs, s); break;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_quant_x_dual(const Problem& p, const Work& w, int Kp16, uint8_t* Xq, float4* xs16, float4* xs8,
                                 cudaStream_t s) {
-  int64_t blocks = (p.n + 7) / 8;
-  const int64_t cap = (int64_t)num_sms() * 16;
-  if (blocks > cap) blocks = cap;
-  quant_x_dual_kernel<<<(int)blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl);
+  const int blocks = quant_x_blocks(p.n);
+  switch (quant_slices(Kp16)) {
+    case 1: quant_x_dual_kernel<1><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl); break;
+    case 2: quant_x_dual_kernel<2><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl); break;
+    case 4: quant_x_dual_kernel<4><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl); break;
+    default:
+      quant_x_dual_kernel<8><<<blocks, 256, 0, s>>>(p.X, p.n, p.d, Kp16, Xq, xs16, xs8, w.mu, w.xnorm, w.ctl);
+  }
   return cudaGetLastError();
 }
 
