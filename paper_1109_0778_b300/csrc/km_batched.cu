@@ -212,9 +212,14 @@ __device__ __forceinline__ int b_settle(const BWork& W, const FlagRec& rec, cons
 // Short candidate lists: groups of G lanes per point (group_settle), 32 / G
 // points at a time; 8 lanes with one float4 slice each for d <= 32, four slices
 // (d <= 128) above. (Narrower groups for small d measured slower: 0.74 -> 0.83 ms.)
+// A round's candidate loop runs to its longest list, so the lists of at most
+// two candidates (one load round) are settled first, among themselves.
 template <int G, int F>
-__device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sm, const FlagRec& r, int lane) {
+__device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sl, const FlagRec& r, int lane) {
   const int g = lane / G, sub = lane % G;
+  const unsigned sm1 = __ballot_sync(0xffffffffu, ((sl >> lane) & 1u) && r.nc <= 2);
+  for (int pass = 0; pass < 2; ++pass) {
+  unsigned sm = pass ? sl & ~sm1 : sm1;
   while (sm) {  // warp-uniform
     const int src = nth_set_bit(sm, g);
     const int from = src < 0 ? __ffs(sm) - 1 : src;  // (a group without a point repeats the first one)
@@ -231,6 +236,7 @@ __device__ __forceinline__ void b_settle_short(const BWork& W, unsigned sm, cons
       if (rold != jb) atomicAdd(&W.ctls[b].n_changed, 1ull);
     }
     for (int a = 0; a < 32 / G && sm; ++a) sm &= sm - 1;  // the points of this round
+  }
   }
 }
 

@@ -71,12 +71,18 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
         todo &= ~__ballot_sync(0xffffffffu, queued);
       }
     }
-    // short candidate lists: a group of G lanes per point, 32 / G points at a time (group_settle)
-    unsigned sm = __ballot_sync(0xffffffffu, ((todo >> lane) & 1u) && nc_l > 0);
-    todo &= ~sm;
+    // short candidate lists: a group of G lanes per point, 32 / G points at a time (group_settle);
+    // a round's candidate loop runs to its longest list, so the lists of at most NQ candidates
+    // (one load round) go first, among themselves, then the longer ones
+    const unsigned sl = __ballot_sync(0xffffffffu, ((todo >> lane) & 1u) && nc_l > 0);
+    todo &= ~sl;
     constexpr int G = 8;                    // lanes per point: 4 points per round
     constexpr int F = (V * 8 + G - 1) / G;  // float4 slices of the point per lane (4 G F >= 32 V >= d)
+    constexpr int NQ = V <= 4 ? 2 : (F <= 4 ? 4 : 2);
     const int g = lane / G, sub = lane % G;
+    const unsigned sm1 = __ballot_sync(0xffffffffu, ((sl >> lane) & 1u) && nc_l <= NQ);
+    for (int pass = 0; pass < 2; ++pass) {
+    unsigned sm = pass ? sl & ~sm1 : sm1;
     while (sm) {  // warp-uniform
       const int src = nth_set_bit(sm, g);
       const int from = src < 0 ? __ffs(sm) - 1 : src;  // (a group without a point repeats the first one)
@@ -86,12 +92,13 @@ recheck_kernel(const float* __restrict__ X, int d, const float* __restrict__ C, 
 #pragma unroll
       for (int a = 0; a < kMaxCand; ++a) cand[a] = __shfl_sync(0xffffffffu, cand_l[a], from);
       const int ncw = __reduce_max_sync(0xffffffffu, src >= 0 ? rnc : 0);
-      const int jb = group_settle<G, F, (V <= 4 ? 2 : (F <= 4 ? 4 : 2))>(X + (int64_t)ri * d, C, d, rnc, ncw, cand, sub);
+      const int jb = group_settle<G, F, NQ>(X + (int64_t)ri * d, C, d, rnc, ncw, cand, sub);
       if (src >= 0 && sub == 0) {
         assign[ri] = jb;
         changed += (rold != jb);
       }
       for (int a = 0; a < 32 / G && sm; ++a) sm &= sm - 1;  // the points of this round
+    }
     }
     // the rest (all k candidates, not queued): one point at a time, lanes over dimensions
     while (todo) {
