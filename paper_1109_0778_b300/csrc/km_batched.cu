@@ -710,11 +710,11 @@ __global__ void __launch_bounds__(256, 4) b_segsum_kernel(BWork W) {
   }
 }
 
-// Divide per centroid of every instance; the warp that finishes an instance's
-// last centroid records its step statistics and evaluates its stop rule.
-__global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
+// Divide per centroid of every instance (one warp per centroid, its instance
+// from the table). A lane's coordinates t = lane, lane + 32, ... are all loaded
+// before any store, so a centroid costs one round trip to memory whatever d.
+__global__ void __launch_bounds__(256) b_divide_kernel(BWork W) {
   const int lane = threadIdx.x & 31;
-  // one warp per centroid; its instance from the table
   for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < W.KC;
        g += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int b = __ldg(W.kc_inst + g);
@@ -722,49 +722,64 @@ __global__ void __launch_bounds__(256) b_divide_kernel(BWork W, double tol) {
     if (halted(ctl)) continue;
     const BInst& I = W.inst[b];
     const int j = (int)(g - I.kc_off), d = I.d;
+    float* __restrict__ Cj = I.C + (int64_t)j * d;
+    float* __restrict__ Sj = I.sums + (int64_t)j * d;
+    double* __restrict__ sp = W.sums64 + I.sum_off + (int64_t)j * d;
     const int cnt = I.counts[j];
+    double sv[kMaxV];
+    float co[kMaxV];
+#pragma unroll
+    for (int v = 0; v < kMaxV; ++v) {
+      const int t = v * 32 + lane;
+      sv[v] = t < d ? sp[t] : 0.0;
+      co[v] = t < d ? Cj[t] : 0.f;
+    }
     // FP64 quotients: a lane with more than one coordinate divides once, y = RN(1 / cnt), and
     // corrects each quotient (div_by_recip: the same correctly rounded result as a division)
     const bool recip = d > 32 && cnt > 0;
     const double y = recip ? 1.0 / (double)cnt : 0.0;
     double acc = 0.0;
-    for (int t = lane; t < d; t += 32) {
-      const int64_t e = (int64_t)j * d + t;
-      double* sp = W.sums64 + I.sum_off + e;
-      const double sv = *sp;
-      *sp = 0.0;
-      I.sums[e] = (float)sv;
-      const float co = I.C[e];
-      const float cn = cnt > 0 ? (float)(recip ? div_by_recip(sv, (double)cnt, y) : sv / (double)cnt) : co;
-      I.C[e] = cn;
-      const double df = (double)cn - (double)co;
-      acc = fma(df, df, acc);
+#pragma unroll
+    for (int v = 0; v < kMaxV; ++v) {
+      const int t = v * 32 + lane;
+      if (t < d) {
+        sp[t] = 0.0;
+        Sj[t] = (float)sv[v];
+        const float cn =
+            cnt > 0 ? (float)(recip ? div_by_recip(sv[v], (double)cnt, y) : sv[v] / (double)cnt) : co[v];
+        Cj[t] = cn;
+        const double df = (double)cn - (double)co[v];
+        acc = fma(df, df, acc);
+      }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
       atomic_max_nonneg(&ctl->shift2_bits, acc);
       if (cnt == 0) atomicAdd(&ctl->n_empty, 1);
-      __threadfence();
-      const unsigned ticket = atomicAdd(&ctl->blocks_done, 1u);
-      if (ticket == (unsigned)I.k - 1) {  // this instance's last centroid
-        __threadfence();
-        volatile Ctl* vc = ctl;
-        const int it = vc->iters_done;
-        const int64_t h = (int64_t)b * W.iters + it;
-        const double shift = sqrt(__longlong_as_double((long long)vc->shift2_bits));
-        const unsigned long long changed = vc->n_changed;
-        W.obj_hist[h] = vc->objective;
-        W.shift_hist[h] = shift;
-        W.changed_hist[h] = changed;
-        W.flagged_hist[h] = vc->n_flagged;
-        W.full_hist[h] = vc->n_full;
-        W.empty_hist[h] = vc->n_empty;
-        vc->iters_done = it + 1;
-        if (tol > 0.0 && (changed == 0 || shift <= tol)) vc->done = 1;
-      }
     }
   }
+}
+
+// After the divide: every running instance records its step statistics and
+// evaluates its stop rule (one thread per instance).
+__global__ void __launch_bounds__(256) b_finish_kernel(BWork W, double tol) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= W.nb) return;
+  Ctl* ctl = W.ctls + b;
+  if (halted(ctl)) return;
+  const int it = ctl->iters_done;
+  const int64_t h = (int64_t)b * W.iters + it;
+  const double shift = sqrt(__longlong_as_double((long long)ctl->shift2_bits));
+  const unsigned long long changed = ctl->n_changed;
+  W.obj_hist[h] = ctl->objective;
+  W.shift_hist[h] = shift;
+  W.changed_hist[h] = changed;
+  W.flagged_hist[h] = ctl->n_flagged;
+  W.full_hist[h] = ctl->n_full;
+  W.empty_hist[h] = ctl->n_empty;
+  ctl->iters_done = it + 1;
+  if (tol > 0.0 && (changed == 0 || shift <= tol)) ctl->done = 1;
 }
 
 int grid_for(int64_t work_items, int per_block, int cap_per_sm) {
@@ -840,7 +855,8 @@ cudaError_t launch_b_segsum(const BWork& W, cudaStream_t s) {
 }
 
 cudaError_t launch_b_divide(const BWork& W, double tol, cudaStream_t s) {
-  b_divide_kernel<<<grid_for(W.KC, 8, 8), 256, 0, s>>>(W, tol);
+  b_divide_kernel<<<grid_for(W.KC, 8, 8), 256, 0, s>>>(W);
+  b_finish_kernel<<<(W.nb + 255) / 256, 256, 0, s>>>(W, tol);
   return cudaGetLastError();
 }
 
