@@ -43,31 +43,38 @@ __global__ void b_copy_c_kernel(const BInst* __restrict__ inst, int nb, float* _
   }
 }
 
-// Codes and row statistics of every point of the batch. Each warp walks one
-// contiguous range of the flattened rows (instances found by walking forward
-// from one search), four rows of one instance at a time with their loads in
-// flight together; lanes over the Kp <= 128 code columns.
-template <int FP8>
-__global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
+// Sum and maximum over the DP lanes of an aligned lane group (DP a power of two).
+template <int DP>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = DP >> 1; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int DP>
+__device__ __forceinline__ float group_max(float v) {
+#pragma unroll
+  for (int o = DP >> 1; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Codes and statistics of flattened rows [p, pend) of instance q with Kp <= 32 V:
+// four rows at a time with their loads in flight together, lanes over the code
+// columns. (Warp-uniform.)
+template <int FP8, int V>
+__device__ __forceinline__ void bq_rows(const BWork& W, int q, int64_t p, int64_t pend, int lane) {
   constexpr int ESZ = FP8 ? 1 : 2;
   constexpr int U = 4;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
-  int q = P0 < P1 ? find_block(W.row_off, W.nb, P0) : 0;
-  for (int64_t p = P0; p < P1;) {
-    while (W.row_off[q + 1] <= p) ++q;
-    const BInst& I = W.inst[q];
-    const int d = I.d, Kp = I.Kp;
+  const BInst& I = W.inst[q];
+  const int d = I.d, Kp = I.Kp;
+  for (; p < pend; p += U) {
     const int64_t i0 = p - I.row_off;
-    const int rows = (int)min(min((int64_t)U, W.row_off[q + 1] - p), P1 - p);
-    float xv[U][kMaxV];
+    const int rows = (int)min((int64_t)U, pend - p);
+    float xv[U][V];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float* x = I.X + (i0 + u) * d;
 #pragma unroll
-      for (int v = 0; v < kMaxV; ++v) {
+      for (int v = 0; v < V; ++v) {
         const int t = v * 32 + lane;
         xv[u][v] = (u < rows && t < d) ? x[t] : 0.f;
       }
@@ -78,14 +85,14 @@ __global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
       float amax = 0.f;
       if (FP8) {
 #pragma unroll
-        for (int v = 0; v < kMaxV; ++v) amax = fmaxf(amax, fabsf(xv[u][v]));
+        for (int v = 0; v < V; ++v) amax = fmaxf(amax, fabsf(xv[u][v]));
       }
       const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
       const float inv = FP8 ? pow2_inv(sc) : 1.f;
       float sxx = 0.f, sqq = 0.f, sdd = 0.f;
       uint8_t* row = W.Xq + I.xq_off + (i0 + u) * (int64_t)Kp * ESZ;
 #pragma unroll
-      for (int v = 0; v < kMaxV; ++v) {
+      for (int v = 0; v < V; ++v) {
         const int t = v * 32 + lane;
         if (t < Kp) {
           const float xt = xv[u][v];
@@ -103,7 +110,78 @@ __global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
         W.xs[p + u] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
       }
     }
-    p += rows;
+  }
+}
+
+// The same for rows of d <= DP <= 16 (DP a power of two): a group of DP lanes
+// per row, 32 / DP rows per warp step, four steps with their loads in flight
+// together; lane s of a group holds coordinate s and writes code columns s,
+// s + DP, ... < Kp (zero past d). (Warp-uniform.)
+template <int FP8, int DP>
+__device__ __forceinline__ void bq_packed(const BWork& W, int q, int64_t p, int64_t pend, int lane) {
+  constexpr int ESZ = FP8 ? 1 : 2;
+  constexpr int RPW = 32 / DP, U = 4;
+  const BInst& I = W.inst[q];
+  const int d = I.d, Kp = I.Kp;
+  const int g = lane / DP, s = lane % DP;
+  for (; p < pend; p += RPW * U) {
+    float xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t pr = p + u * RPW + g;
+      xv[u] = (pr < pend && s < d) ? I.X[(pr - I.row_off) * d + s] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t pr = p + u * RPW + g;
+      const bool live = pr < pend;
+      const float sc = FP8 ? pow2_scale(group_max<DP>(fabsf(xv[u]))) : 1.f;
+      const float inv = FP8 ? pow2_inv(sc) : 1.f;
+      float sxx = 0.f, sqq = 0.f, sdd = 0.f;
+      if (live) {
+        uint8_t* row = W.Xq + I.xq_off + (pr - I.row_off) * (int64_t)Kp * ESZ;
+        for (int t = s; t < Kp; t += DP) {
+          const float xt = t == s ? xv[u] : 0.f;
+          const float vq = quantise<FP8>(xt, sc, inv, row + t * ESZ);
+          sxx = fmaf(xt, xt, sxx);
+          sqq = fmaf(vq, vq, sqq);
+          sdd = fmaf(vq - xt, vq - xt, sdd);
+        }
+      }
+      sxx = group_sum<DP>(sxx);
+      sqq = group_sum<DP>(sqq);
+      sdd = group_sum<DP>(sdd);
+      if (live && s == 0) {
+        if (!isfinite(sxx) || !isfinite(sqq)) W.ctls[q].nonfinite = 1;
+        W.xs[pr] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
+      }
+    }
+  }
+}
+
+// Codes and row statistics of every point of the batch. Each warp walks one
+// contiguous range of the flattened rows (instances found by walking forward
+// from one search), each instance's part with the row loop for its width.
+template <int FP8>
+__global__ void __launch_bounds__(256) b_quant_x_kernel(BWork W) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t P0 = W.R * gw / nw, P1 = W.R * (gw + 1) / nw;
+  int q = P0 < P1 ? find_block(W.row_off, W.nb, P0) : 0;
+  for (int64_t p = P0; p < P1;) {
+    while (W.row_off[q + 1] <= p) ++q;
+    const int64_t pend = min(W.row_off[q + 1], P1);
+    const int d = W.inst[q].d, Kp = W.inst[q].Kp;
+    if (d <= 1) bq_packed<FP8, 1>(W, q, p, pend, lane);
+    else if (d <= 2) bq_packed<FP8, 2>(W, q, p, pend, lane);
+    else if (d <= 4) bq_packed<FP8, 4>(W, q, p, pend, lane);
+    else if (d <= 8) bq_packed<FP8, 8>(W, q, p, pend, lane);
+    else if (d <= 16) bq_packed<FP8, 16>(W, q, p, pend, lane);
+    else if (Kp <= 32) bq_rows<FP8, 1>(W, q, p, pend, lane);
+    else if (Kp <= 64) bq_rows<FP8, 2>(W, q, p, pend, lane);
+    else bq_rows<FP8, kMaxV>(W, q, p, pend, lane);
+    p = pend;
   }
 }
 
