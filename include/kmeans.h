@@ -292,11 +292,12 @@ int kmeans_apply_partials(const km_opts* opts, const double* part, int32_t k, in
  * X: const float[n*d], C: const float[k*d], assign: const int32[n] with labels
  * in [0, k) (else KM_EINVAL), sums: float[k*d] out, counts: int32[k] out; all
  * device pointers. Work is issued on `stream` (NULL = legacy stream); every
- * call synchronises `stream` and reads a status word back before it returns.
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it for the
- * lifetime of the device's primary context; that first call should come
- * before any stream capture. Every call shares the one scratch array (it
+ * call synchronises `stream` and reads a status word back before it returns,
+ * so the call is synchronous and can never be recorded into a stream capture
+ * or a CUDA graph. The first call on a device looks up the scratch array's
+ * device address (cudaGetSymbolAddress, with that device current) and caches
+ * it for the lifetime of the device's primary context (a cudaDeviceReset ends
+ * both). Every call shares the one scratch array (it
  * clears what must start at zero, so a call rejected for a bad label leaves
  * nothing behind for the next one), and calls that overlap on the GPU race
  * with each other.

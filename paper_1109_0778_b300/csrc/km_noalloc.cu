@@ -78,7 +78,8 @@ __global__ void finish_sums_kernel(double* __restrict__ sums64, float* __restric
  * address of the static scratch array (cudaGetSymbolAddress with that device
  * current) and caches it: the address stays valid while the device's primary
  * context lives (a cudaDeviceReset ends it, and the cached address with it).
- * Make that first call before any stream capture.
+ * Every call ends with a device-to-host copy and a stream synchronisation, so
+ * no call can be captured into a stream or graph.
  */
 KM_API int kmeans_reduce_noalloc(const float* X, int64_t n, int32_t d, const float* C, int32_t k,
                                  const int32_t* assign, float* sums, int32_t* counts, double* objective,
