@@ -572,14 +572,6 @@ __global__ void __launch_bounds__(256) b_permute_kernel(BWork W) {
 constexpr int kSegStage = 768;                               // floats per stage (6 rows of 128, 24 of 32)
 constexpr size_t kSegSmem = (size_t)8 * 2 * kSegStage * 4;   // 8 warps x 2 stages
 
-// Power of two >= d for the packed rows (d <= 16), 0 otherwise.
-__device__ __forceinline__ int packed_width(int d) {
-  if (d > 16) return 0;
-  int p = 1;
-  while (p < d) p <<= 1;
-  return p;
-}
-
 // One item: sorted positions [it.r0, it.r0 + it.n) of instance it.b, V
 // slices of 32 coordinates per lane (16 < d <= 32 V).
 template <int V>
@@ -621,6 +613,17 @@ __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float
       s[v] = c[v] = 0.f;
     }
   };
+  // columns [d, 32 V) of every row slot hold zeros (the gathers write only
+  // [0, d)), so rows are read without a column test
+  if (d < rs) {
+    for (int e = lane; e < RB * rs; e += 32)
+      if (e % rs >= d) stage0[e] = stage1[e] = 0.f;
+    __syncwarp();
+  }
+  // the objective terms are added plainly over RF rows (at most 8 terms per
+  // lane: relative error <= 7u of the partial), each partial then Kahan-added
+  constexpr int RF = V >= 8 ? 1 : 8 / V;
+  float qacc = 0.f;
   int i_c = 0, j_c = -1, i_n = 0, j_n = -1;
   meta(0, i_c, j_c);
   gather(0, stage0, i_c);
@@ -650,18 +653,25 @@ __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float
         }
         const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
         const int rend = later ? __ffs(later) - 1 : rows;
-        for (; r < rend; ++r) {
-          float qd = 0.f;
+        auto row = [&](int rr) {
+          const float* xp = st + rr * rs + lane;
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
-            const float xr = t < d ? st[r * rs + t] : 0.f;
+            const float xr = xp[v * 32];
             kahan_add(s[v], c[v], xr);
             const float df = __fsub_rn(xr, cj[v]);
-            qd = fmaf(df, df, qd);
+            qacc = fmaf(df, df, qacc);
           }
-          kahan_add(objS, objC, qd);
+        };
+        for (; r + RF <= rend; r += RF) {
+#pragma unroll
+          for (int u = 0; u < RF; ++u) row(r + u);
+          kahan_add(objS, objC, qacc);
+          qacc = 0.f;
         }
+        for (; r < rend; ++r) row(r);
+        kahan_add(objS, objC, qacc);
+        qacc = 0.f;
       }
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
@@ -677,16 +687,20 @@ __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float
   if (lane == 0 && o != 0.0) atomicAdd(&W.ctls[it.b].objective, o);
 }
 
-// Packed rows (d <= 16, dp the power of two >= d): batches of up to 128 rows
-// (lane l holds the indices of rows l, l + 32, l + 64, l + 96), so that a warp
-// keeps a few KB of these short rows in flight; lane group g = lane / dp takes
-// row r0 + g of each step, lane t = lane mod dp its column t, and keeps its own
-// run (flushed alone).
+// Packed rows (d <= DP <= 16, DP the power of two >= d): batches of up to 128
+// rows (lane l holds the indices of rows l, l + 32, l + 64, l + 96), so that a
+// warp keeps a few KB of these short rows in flight; lane group g = lane / DP
+// takes row r0 + g of each step, lane t = lane mod DP its column t, and keeps
+// its own run (flushed alone). A full batch runs as unrolled steps; the
+// objective terms are added plainly over 8 steps (one term per lane each),
+// each partial then Kahan-added.
+template <int DP>
 __device__ __forceinline__ void seg_item_packed(const BWork& W, const BChunk& it, float* stage0, float* stage1,
                                                 int lane) {
+  constexpr int RB = kSegStage / DP < 128 ? kSegStage / DP : 128;  // rows per batch (a multiple of 32 / DP)
+  constexpr int G = 32 / DP;                                       // rows per warp step
   const BInst& I = W.inst[it.b];
-  const int d = I.d, dp = packed_width(d);
-  const int RB = min(128, kSegStage / dp);  // rows per batch (a multiple of 32)
+  const int d = I.d;
   const float* __restrict__ X = I.X;
   const float* __restrict__ C = I.C;
   double* sums = W.sums64 + I.sum_off;
@@ -709,16 +723,34 @@ __device__ __forceinline__ void seg_item_packed(const BWork& W, const BChunk& it
     const int rows = min(RB, it.n - bt * RB);
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-      if (m * 32 < rows) gather_rows(st + m * 32 * dp, dp, X, d, min(32, rows - m * 32), (int64_t)i[m] * d, lane, false);
+      if (m * 32 < rows) gather_rows(st + m * 32 * DP, DP, X, d, min(32, rows - m * 32), (int64_t)i[m] * d, lane, false);
     cp_async_commit();
   };
-  const int G = 32 / dp, g = lane / dp, t = lane & (dp - 1);
-  float s = 0.f, c = 0.f, cj = 0.f, objS = 0.f, objC = 0.f;
+  const int g = lane / DP, t = lane & (DP - 1);
+  // columns [d, DP) of every row slot hold zeros (the gathers write only [0, d))
+  if (d < DP) {
+    for (int e = lane; e < RB * DP; e += 32)
+      if ((e & (DP - 1)) >= d) stage0[e] = stage1[e] = 0.f;
+    __syncwarp();
+  }
+  float s = 0.f, c = 0.f, cj = 0.f, objS = 0.f, objC = 0.f, qacc = 0.f;
   int cur = -1;  // this lane's run
   auto flush = [&]() {
     if (cur < 0) return;
     if (t < d) atomicAdd(sums + (int64_t)cur * d + t, (double)s - (double)c);
     s = c = 0.f;
+  };
+  // row r of the batch in stage st, label j (every lane of the group)
+  auto step = [&](const float* st, int r, int j) {
+    if (j != cur) {
+      flush();
+      cur = j;
+      cj = t < d ? C[(int64_t)j * d + t] : 0.f;
+    }
+    const float xr = st[r * DP + t];
+    kahan_add(s, c, xr);
+    const float df = __fsub_rn(xr, cj);
+    qacc = fmaf(df, df, qacc);
   };
   int i_c[4], j_c[4], i_n[4], j_n[4];
   meta(0, i_c, j_c);
@@ -738,22 +770,39 @@ __device__ __forceinline__ void seg_item_packed(const BWork& W, const BChunk& it
     else cp_async_wait<0>();
     __syncwarp();
     const int rows = min(RB, it.n - bt * RB);
-    for (int r0 = 0; r0 < rows; r0 += G) {
-      const int m = r0 >> 5;  // the same for every lane (G divides 32)
-      const int jm = m == 0 ? j_c[0] : (m == 1 ? j_c[1] : (m == 2 ? j_c[2] : j_c[3]));
-      const int r = r0 + g;
-      const bool ok = r < rows;
-      const int j = __shfl_sync(0xffffffffu, jm, ok ? (r & 31) : 0);
-      if (!ok) continue;
-      if (j != cur) {
-        flush();
-        cur = j;
-        cj = t < d ? C[(int64_t)j * d + t] : 0.f;
+    if (rows == RB) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m * 32 >= RB) break;
+#pragma unroll
+        for (int q = 0; q < 32 / G; ++q) {
+          if (m * 32 + (q + 1) * G > RB) break;
+          step(st, m * 32 + q * G + g, __shfl_sync(0xffffffffu, j_c[m], q * G + g));
+          if ((q & 7) == 7) {
+            kahan_add(objS, objC, qacc);
+            qacc = 0.f;
+          }
+        }
+        kahan_add(objS, objC, qacc);
+        qacc = 0.f;
       }
-      const float xr = t < d ? st[r * dp + t] : 0.f;
-      kahan_add(s, c, xr);
-      const float df = __fsub_rn(xr, cj);
-      kahan_add(objS, objC, df * df);
+    } else {
+      int q8 = 0;
+      for (int r0 = 0; r0 < rows; r0 += G) {
+        const int m = r0 >> 5;  // the same for every lane (G divides 32)
+        const int jm = m == 0 ? j_c[0] : (m == 1 ? j_c[1] : (m == 2 ? j_c[2] : j_c[3]));
+        const int r = r0 + g;
+        const bool ok = r < rows;
+        const int j = __shfl_sync(0xffffffffu, jm, ok ? (r & 31) : 0);
+        if (ok) step(st, r, j);
+        if (++q8 == 8) {
+          kahan_add(objS, objC, qacc);
+          qacc = 0.f;
+          q8 = 0;
+        }
+      }
+      kahan_add(objS, objC, qacc);
+      qacc = 0.f;
     }
     __syncwarp();  // every lane is done with this stage before it is refilled
 #pragma unroll
@@ -781,7 +830,11 @@ __global__ void __launch_bounds__(256, 4) b_segsum_kernel(BWork W) {
     const BChunk it = W.sitems[q];
     if (halted(W.ctls + it.b)) continue;
     const int d = W.inst[it.b].d;
-    if (d <= 16) seg_item_packed(W, it, stage0, stage1, lane);
+    if (d <= 1) seg_item_packed<1>(W, it, stage0, stage1, lane);
+    else if (d <= 2) seg_item_packed<2>(W, it, stage0, stage1, lane);
+    else if (d <= 4) seg_item_packed<4>(W, it, stage0, stage1, lane);
+    else if (d <= 8) seg_item_packed<8>(W, it, stage0, stage1, lane);
+    else if (d <= 16) seg_item_packed<16>(W, it, stage0, stage1, lane);
     else if (d <= 32) seg_item<1>(W, it, stage0, stage1, lane);
     else if (d <= 64) seg_item<2>(W, it, stage0, stage1, lane);
     else seg_item<4>(W, it, stage0, stage1, lane);
