@@ -175,12 +175,19 @@ scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32
   }
 }
 
-template <int V>
+// Lane column of slice v: v 32 + lane, or lane V + v when BLK (V contiguous
+// columns per lane, V = 2, 4 or 8).
+template <int V, bool BLK>
+__device__ __forceinline__ int seg_col(int v, int lane) {
+  return BLK ? lane * V + v : v * 32 + lane;
+}
+
+template <int V, bool BLK = false>
 __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, int d, int lane,
                                            float (&s)[V], float (&c)[V]) {
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int t = v * 32 + lane;
+    const int t = seg_col<V, BLK>(v, lane);
     if (t < d) atomicAdd(sums64 + (int64_t)j * d + t, (double)s[v] - (double)c[v]);
     s[v] = 0.f;
     c[v] = 0.f;
@@ -189,12 +196,12 @@ __device__ __forceinline__ void flush_sums(double* __restrict__ sums64, int j, i
 
 // Deterministic flush: the run's integer parts into the 64-bit accumulators
 // facc[l][j d + t] (two's-complement adds through unsigned atomics).
-template <int V>
+template <int V, bool BLK = false>
 __device__ __forceinline__ void flush_fixed(unsigned long long* __restrict__ facc, int64_t kd, int j, int d, int lane,
                                             int (&q)[V][3]) {
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int t = v * 32 + lane;
+    const int t = seg_col<V, BLK>(v, lane);
     if (t < d) {
 #pragma unroll
       for (int l = 0; l < 3; ++l)
@@ -244,6 +251,10 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
               const float* __restrict__ mu) {
   constexpr int RB = seg_rows<V>();  // rows per batch (lane r < RB holds row r's indices)
   constexpr int RS = 32 * V;         // shared-memory floats per row
+  // V = 2, 4, 8: a lane owns V contiguous columns, so a row is one shared-memory
+  // vector load and its codes one vector store per lane (not for the two-part
+  // codes, whose element-wise stores would then stride the row)
+  constexpr bool BLK = (V == 2 || V == 4 || V == 8) && QM != 3;
   extern __shared__ __align__(16) float seg_smem[];
   if (halted(ctl)) return;
   // deterministic mode: grids of the coordinate sums and of the objective terms
@@ -263,11 +274,16 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
   float muv[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const int t = v * 32 + lane;
+    const int t = seg_col<V, BLK>(v, lane);
     muv[v] = (QM != 0 && mu && t < d) ? __ldg(mu + t) : 0.f;
   }
   float* stage0 = seg_smem + (size_t)wib * 2 * RB * RS;
   float* stage1 = stage0 + RB * RS;
+  if (BLK && d < RS) {  // columns [d, RS) of every row slot hold zeros (the gathers write only [0, d))
+    for (int e = lane; e < 2 * RB * RS; e += 32)
+      if (e % RS >= d) stage0[e] = 0.f;
+    __syncwarp();
+  }
   const int64_t nw = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + wib;
   const int64_t P0 = n * gw / nw, P1 = n * (gw + 1) / nw;  // this warp's sorted positions
   const int64_t nb = (P1 - P0 + RB - 1) / RB;
@@ -324,15 +340,15 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     for (int r = 0; r < rows;) {
       if ((starts >> r) & 1u) {  // the same for every lane
         if constexpr (DET) {
-          if (cur >= 0) flush_fixed<V>(facc, kd, cur, d, lane, q);
+          if (cur >= 0) flush_fixed<V, BLK>(facc, kd, cur, d, lane, q);
           run_rows = 0;
         } else {
-          if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+          if (cur >= 0) flush_sums<V, BLK>(sums64, cur, d, lane, s, c);
         }
         cur = __shfl_sync(0xffffffffu, j_c, r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
+          const int t = seg_col<V, BLK>(v, lane);
           cj[v] = t < d ? C[(int64_t)cur * d + t] : 0.f;
         }
       }
@@ -340,10 +356,31 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
       const int rend = later ? __ffs(later) - 1 : rows;
       for (; r < rend; ++r) {
         float xr[V], qo = 0.f;
+        if constexpr (BLK) {
+          const float* xp = st + r * RS + lane * V;
+          if constexpr (V == 2) {
+            const float2 a = *reinterpret_cast<const float2*>(xp);
+            xr[0] = a.x;
+            xr[1] = a.y;
+          } else {
+#pragma unroll
+            for (int k4 = 0; k4 < V / 4; ++k4) {
+              const float4 a = reinterpret_cast<const float4*>(xp)[k4];
+              xr[4 * k4] = a.x;
+              xr[4 * k4 + 1] = a.y;
+              xr[4 * k4 + 2] = a.z;
+              xr[4 * k4 + 3] = a.w;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            const int t = v * 32 + lane;
+            xr[v] = t < d ? st[r * RS + t] : 0.f;
+          }
+        }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          const int t = v * 32 + lane;
-          xr[v] = t < d ? st[r * RS + t] : 0.f;
           if constexpr (DET) fx_add(xr[v], fxs, q[v]);
           else kahan_add(s[v], c[v], xr[v]);
           const float df = __fsub_rn(xr[v], cj[v]);
@@ -352,7 +389,7 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
         if constexpr (DET) {
           fx_add(qo, fxo, oq);
           if (++run_rows == 1024) {  // keeps every 32-bit run sum within 2^30
-            flush_fixed<V>(facc, kd, cur, d, lane, q);
+            flush_fixed<V, BLK>(facc, kd, cur, d, lane, q);
             run_rows = 0;
           }
           if (++obj_rows == 1024) {
@@ -364,12 +401,28 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
         }
         if constexpr (QM != 0) {
           const int64_t prow = P0 + b * RB + r;
+          // (BLK: a lane's columns past d get the code of 0, which is what the
+          // quantisation stage leaves there; 32 V <= Kp for every BLK width)
           if constexpr (QM == 1) {
             __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * Kp;
+            if constexpr (BLK) {
+              uint32_t w[V / 2];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const int t = v * 32 + lane;
-              if (t < d) row[t] = __float2bfloat16_rn(__fsub_rn(xr[v], muv[v]));
+              for (int h2 = 0; h2 < V / 2; ++h2) {
+                const __nv_bfloat162 pr = __floats2bfloat162_rn(__fsub_rn(xr[2 * h2], muv[2 * h2]),
+                                                                __fsub_rn(xr[2 * h2 + 1], muv[2 * h2 + 1]));
+                w[h2] = *reinterpret_cast<const uint32_t*>(&pr);
+              }
+              uint32_t* dst = reinterpret_cast<uint32_t*>(row + lane * V);
+              if constexpr (V == 2) dst[0] = w[0];
+              else if constexpr (V == 4) *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+              else *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                const int t = v * 32 + lane;
+                if (t < d) row[t] = __float2bfloat16_rn(__fsub_rn(xr[v], muv[v]));
+              }
             }
           } else if constexpr (QM == 3) {
             __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + prow * 2 * Kp;
@@ -382,10 +435,31 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
           } else {
             const float inv = pow2_inv(__shfl_sync(0xffffffffu, xs_c.x, r));  // 1 / row scale, exact
             uint8_t* row = Xq + prow * Kp;
+            if constexpr (BLK) {
+              uint8_t b[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              const int t = v * 32 + lane;
-              if (t < d) row[t] = __nv_fp8_e4m3(__fsub_rn(xr[v], muv[v]) * inv).__x;
+              for (int v = 0; v < V; ++v) b[v] = __nv_fp8_e4m3(__fsub_rn(xr[v], muv[v]) * inv).__x;
+              uint8_t* dst = row + lane * V;
+              if constexpr (V == 2) {
+                *reinterpret_cast<uint16_t*>(dst) = (uint16_t)(b[0] | (b[1] << 8));
+              } else if constexpr (V == 4) {
+                *reinterpret_cast<uint32_t*>(dst) = (uint32_t)b[0] | ((uint32_t)b[1] << 8) | ((uint32_t)b[2] << 16) |
+                                                    ((uint32_t)b[3] << 24);
+              } else {
+                uint32_t lo4 = 0, hi4 = 0;
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                  lo4 |= (uint32_t)b[v] << (8 * v);
+                  hi4 |= (uint32_t)b[v + 4] << (8 * v);
+                }
+                *reinterpret_cast<uint2*>(dst) = make_uint2(lo4, hi4);
+              }
+            } else {
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                const int t = v * 32 + lane;
+                if (t < d) row[t] = __nv_fp8_e4m3(__fsub_rn(xr[v], muv[v]) * inv).__x;
+              }
             }
           }
         }
@@ -399,10 +473,10 @@ segsum_kernel(const float* __restrict__ X, int64_t n, int d, const float* __rest
     j_n = j_nn;
   }
   if constexpr (DET) {
-    if (cur >= 0) flush_fixed<V>(facc, kd, cur, d, lane, q);
+    if (cur >= 0) flush_fixed<V, BLK>(facc, kd, cur, d, lane, q);
     flush_objective_fixed(oacc, lane, oq);
   } else {
-    if (cur >= 0) flush_sums<V>(sums64, cur, d, lane, s, c);
+    if (cur >= 0) flush_sums<V, BLK>(sums64, cur, d, lane, s, c);
     double o = (double)objS - (double)objC;
 #pragma unroll
     for (int off = 16; off; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
