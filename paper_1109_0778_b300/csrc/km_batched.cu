@@ -578,6 +578,8 @@ template <int V>
 __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float* stage0, float* stage1, int lane) {
   constexpr int RB = kSegStage / (32 * V);  // rows per batch (a 3 KB stage)
   constexpr int rs = 32 * V;                           // stage floats per row
+  constexpr bool BLK = V == 2 || V == 4;               // a lane owns V contiguous columns (vector loads)
+  auto col = [&](int v) { return BLK ? lane * V + v : v * 32 + lane; };
   const BInst& I = W.inst[it.b];
   const int d = I.d;
   const float* __restrict__ X = I.X;
@@ -608,7 +610,7 @@ __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float
     if (cur < 0) return;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      const int t = v * 32 + lane;
+      const int t = col(v);
       if (t < d) atomicAdd(sums + (int64_t)cur * d + t, (double)s[v] - (double)c[v]);
       s[v] = c[v] = 0.f;
     }
@@ -647,17 +649,31 @@ __device__ __forceinline__ void seg_item(const BWork& W, const BChunk& it, float
           cur = __shfl_sync(0xffffffffu, j_c, r);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            const int t = v * 32 + lane;
+            const int t = col(v);
             cj[v] = t < d ? C[(int64_t)cur * d + t] : 0.f;
           }
         }
         const unsigned later = starts & ~((2u << r) - 1u);  // run starts after row r
         const int rend = later ? __ffs(later) - 1 : rows;
         auto row = [&](int rr) {
-          const float* xp = st + rr * rs + lane;
+          float xv[V];
+          if constexpr (V == 2) {
+            const float2 a = *reinterpret_cast<const float2*>(st + rr * rs + lane * 2);
+            xv[0] = a.x;
+            xv[1] = a.y;
+          } else if constexpr (V == 4) {
+            const float4 a = *reinterpret_cast<const float4*>(st + rr * rs + lane * 4);
+            xv[0] = a.x;
+            xv[1] = a.y;
+            xv[2] = a.z;
+            xv[3] = a.w;
+          } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) xv[v] = st[rr * rs + v * 32 + lane];
+          }
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            const float xr = xp[v * 32];
+            const float xr = xv[v];
             kahan_add(s[v], c[v], xr);
             const float df = __fsub_rn(xr, cj[v]);
             qacc = fmaf(df, df, qacc);
