@@ -12,6 +12,7 @@
 #include "km_quant.cuh"
 #include "km_recheck.cuh"
 #include "km_gather.cuh"
+#include "km_scatter.cuh"
 
 namespace km {
 
@@ -450,9 +451,11 @@ __global__ void __launch_bounds__(1024) b_scan_kernel(BWork W) {
 // there (the order within a cluster varies from run to run). Instances with
 // more than kBHistMax clusters reserve per warp-aggregated group instead.
 constexpr int kBScatterPer = kBRowChunk / 256;  // rows per thread of a chunk
+static_assert(kBRowChunk == kScatterChunk, "a row chunk is one sorted-write scatter chunk");
 
 __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
   extern __shared__ int cnt[];  // per-cluster count, then the chunk's base position
+  __shared__ int wsum[8];
   const int lane = threadIdx.x & 31;
   for (int c = blockIdx.x; c < W.nrchunks; c += gridDim.x) {
     const BChunk ch = W.rchunks[c];
@@ -464,7 +467,9 @@ __global__ void __launch_bounds__(256) b_scatter_kernel(BWork W) {
     int32_t* cur = W.cursor + I.kp_off;
     int32_t* perm = W.perm + I.row_off;
     int32_t* slab = W.lab_sorted + I.row_off;
-    if (k <= kBHistMax) {
+    if (W.kmax <= kSortedScatterMax) {  // (the launch gave the sorted write's shared memory)
+      scatter_chunk_sorted(a, ch.n, i0, k, cur, perm, slab, cnt, wsum);
+    } else if (k <= kBHistMax) {
       for (int j = threadIdx.x; j < k; j += blockDim.x) cnt[j] = 0;
       __syncthreads();
       int lab[kBScatterPer], rank[kBScatterPer];
@@ -981,7 +986,8 @@ cudaError_t launch_b_scan(const BWork& W, cudaStream_t s) {
 }
 
 cudaError_t launch_b_scatter(const BWork& W, cudaStream_t s) {
-  b_scatter_kernel<<<grid_for(W.nrchunks, 1, 8), 256, b_hist_bytes(W), s>>>(W);
+  const size_t smem = W.kmax <= kSortedScatterMax ? (size_t)sorted_scatter_ints(W.kmax) * sizeof(int) : b_hist_bytes(W);
+  b_scatter_kernel<<<grid_for(W.nrchunks, 1, 8), 256, smem, s>>>(W);
   return cudaGetLastError();
 }
 

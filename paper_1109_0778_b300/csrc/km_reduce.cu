@@ -38,6 +38,7 @@
 #include "km_gather.cuh"
 #include "km_internal.cuh"
 #include "km_quant.cuh"
+#include "km_scatter.cuh"
 
 namespace km {
 
@@ -175,86 +176,18 @@ scatter_block_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32
   }
 }
 
-// Scatter for k <= kSortedScatterMax: as scatter_block_kernel, but the block
-// first places its points in shared memory in cluster order and then writes
-// them out with consecutive threads on consecutive positions (each (block,
-// cluster) range is contiguous), instead of one scattered 4-byte write per
-// point and array.
-constexpr int kSortedScatterMax = 1536;  // 2 k + 2 chunk ints of shared memory stay under 48 KB
-
+// Scatter for k <= kSortedScatterMax: as scatter_block_kernel, but each chunk
+// is written out in cluster order (scatter_chunk_sorted: runs of consecutive
+// positions instead of one scattered 4-byte write per point and array).
 __global__ void __launch_bounds__(256)
 scatter_sorted_kernel(const int32_t* __restrict__ assign, int64_t n, int k, int32_t* __restrict__ cursor,
                       int32_t* __restrict__ perm, int32_t* __restrict__ slab, const Ctl* ctl) {
   if (halted(ctl)) return;
-  constexpr int kChunk = 256 * kScatterPerThread;
   extern __shared__ int ssm[];
-  int* cnt = ssm;            // [k] per-cluster count, then the cluster's global base
-  int* lst = ssm + k;        // [k] the cluster's first local sorted index
-  int* sidx = ssm + 2 * k;   // [kChunk] point offsets within the chunk, in local sorted order
-  int* slabs = sidx + kChunk;  // [kChunk] their labels
   __shared__ int wsum[8];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int per = (k + 255) / 256;  // scan entries per thread (<= 6)
-  for (int64_t c0 = blockIdx.x * (int64_t)kChunk; c0 < n; c0 += (int64_t)gridDim.x * kChunk) {
-    for (int j = tid; j < k; j += 256) cnt[j] = 0;
-    __syncthreads();
-    int lab[kScatterPerThread], rank[kScatterPerThread];
-#pragma unroll
-    for (int q = 0; q < kScatterPerThread; ++q) {
-      const int64_t i = c0 + q * 256 + tid;
-      lab[q] = i < n ? assign[i] : -1;
-      rank[q] = lab[q] >= 0 ? atomicAdd(&cnt[lab[q]], 1) : 0;
-    }
-    __syncthreads();
-    // exclusive prefix of the counts: thread tid takes entries [tid per, tid per + per)
-    const int j0 = tid * per;
-    int loc = 0;
-    for (int u = 0; u < per; ++u)
-      if (j0 + u < k) loc += cnt[j0 + u];
-    int x = loc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      int w = lane < 8 ? wsum[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      if (lane < 8) wsum[lane] = w;
-    }
-    __syncthreads();
-    int base = (wid ? wsum[wid - 1] : 0) + x - loc;
-    for (int u = 0; u < per; ++u)
-      if (j0 + u < k) {
-        lst[j0 + u] = base;
-        base += cnt[j0 + u];
-      }
-    __syncthreads();
-    for (int j = tid; j < k; j += 256)
-      if (cnt[j]) cnt[j] = atomicAdd(&cursor[j], cnt[j]);
-#pragma unroll
-    for (int q = 0; q < kScatterPerThread; ++q)
-      if (lab[q] >= 0) {
-        const int ls = lst[lab[q]] + rank[q];
-        sidx[ls] = q * 256 + tid;
-        slabs[ls] = lab[q];
-      }
-    __syncthreads();
-    const int m = (int)min((int64_t)kChunk, n - c0);  // the chunk's points, all placed
-    for (int e = tid; e < m; e += 256) {
-      const int j = slabs[e];
-      const int pos = cnt[j] + (e - lst[j]);
-      perm[pos] = (int32_t)(c0 + sidx[e]);
-      slab[pos] = j;
-    }
-    __syncthreads();
-  }
+  for (int64_t c0 = blockIdx.x * (int64_t)kScatterChunk; c0 < n; c0 += (int64_t)gridDim.x * kScatterChunk)
+    scatter_chunk_sorted(assign + c0, (int)min((int64_t)kScatterChunk, n - c0), c0, k, cursor, perm, slab, ssm,
+                         wsum);
 }
 
 // Lane column of slice v: v 32 + lane, or lane V + v when BLK (V contiguous
@@ -772,10 +705,10 @@ cudaError_t launch_scan(const Problem& p, const Work& w, cudaStream_t s) {
 
 cudaError_t launch_scatter(const Problem& p, const Work& w, cudaStream_t s) {
   if (p.k <= kSortedScatterMax) {
-    int64_t blocks = (p.n + 256 * kScatterPerThread - 1) / (256 * kScatterPerThread);
+    int64_t blocks = (p.n + kScatterChunk - 1) / kScatterChunk;
     const int64_t cap = (int64_t)num_sms() * 4;
     if (blocks > cap) blocks = cap;
-    const size_t smem = (size_t)(2 * p.k + 2 * 256 * kScatterPerThread) * sizeof(int);
+    const size_t smem = (size_t)sorted_scatter_ints(p.k) * sizeof(int);
     scatter_sorted_kernel<<<(int)blocks, 256, smem, s>>>(p.assign, p.n, p.k, w.cursor, w.perm, w.lab_sorted, w.ctl);
     return cudaGetLastError();
   }
