@@ -43,16 +43,39 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ X, int64_t n
   }
 }
 
+// Reduce-scatter over the warp: v[0..NV) (NV = 16 or 32) summed over the 32
+// lanes; lane l returns the total of value l >> 1 (NV = 16; lanes l and l ^ 1
+// hold the same total) or l (NV = 32). Each level sends half of the remaining
+// values to the partner lane and keeps the other half, so NV values cost NV - 1
+// shuffles instead of 5 NV. (Any summation tree gives the norm bounds their
+// guarantee: a sum of m non-negative terms has relative error < gamma_m.)
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+  for (int o = 16, c = NV; c > 1; o >>= 1, c >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < c / 2; ++i) {
+      const float send = up ? v[i] : v[i + c / 2];
+      const float keep = up ? v[i + c / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  if (NV == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
 // Xh (E4M3 with -h_j folded into the contraction; null otherwise): row i's
 // [1/s_i, 1/s_i, 1/s_i, 0, ...] slice (store_row_slice).
 // mu (null: no centring): the codes and statistics are those of the centred
 // rows (km_quant.cuh); xnorm[i] gets the bound of the uncentred ||x_i|| (the
 // FP32 consumers: re-check screen, deterministic grid).
 template <int FP8, int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, V <= 4 ? 4 : 2)
 quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
                float4* __restrict__ xs, uint4* __restrict__ Xh, const float* __restrict__ mu,
                float* __restrict__ xnorm, Ctl* ctl) {
+  static_assert(kQU == 4, "four rows of four statistics: one 16-value reduce-scatter");
   constexpr int ESZ = FP8 ? 1 : 2;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -62,10 +85,11 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
     float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
+    float red[4 * kQU];  // row u's lane partials of sum v^2, sum v~^2, sum (v~ - v)^2, sum x^2 at 4 u + s
+    float scs[kQU];
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
       const int64_t i = i0 + u;
-      if (i >= n) break;
       float amax = 0.f;
       if (FP8)
 #pragma unroll
@@ -74,31 +98,42 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
       const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
       const float inv = FP8 ? pow2_inv(sc) : 1.f;
       float sxx = 0.f, sqq = 0.f, sdd = 0.f, sraw = 0.f;
-      uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
+      if (i < n) {
+        uint8_t* row = Xq + i * (int64_t)Kp * ESZ;
 #pragma unroll
-      for (int sl = 0; sl < V; ++sl) {
-        const int t = sl * 32 + lane;
-        if (t >= Kp) break;
-        const float xt = xv[u][sl];
-        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-        const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
-        const float r = vq - v;
-        sxx = fmaf(v, v, sxx);
-        sqq = fmaf(vq, vq, sqq);
-        sdd = fmaf(r, r, sdd);
-        sraw = fmaf(xt, xt, sraw);
+        for (int sl = 0; sl < V; ++sl) {
+          const int t = sl * 32 + lane;
+          if (t >= Kp) break;
+          const float xt = xv[u][sl];
+          const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+          const float vq = quantise<FP8>(v, sc, inv, row + t * ESZ);
+          const float r = vq - v;
+          sxx = fmaf(v, v, sxx);
+          sqq = fmaf(vq, vq, sqq);
+          sdd = fmaf(r, r, sdd);
+          sraw = fmaf(xt, xt, sraw);
+        }
       }
-      sxx = warp_sum(sxx);
-      sqq = warp_sum(sqq);
-      sdd = warp_sum(sdd);
-      sraw = warp_sum(sraw);
-      if (lane == 0) {
-        if (!isfinite(sxx) || !isfinite(sqq) || !isfinite(sraw)) ctl->nonfinite = 1;
-        const float nbv = norm_bound(sxx, d);
-        xs[i] = make_float4(sc, norm_bound(sqq, d), centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
-        if (xnorm) xnorm[i] = norm_bound(sraw, d);
-        if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
-      }
+      red[4 * u] = sxx;
+      red[4 * u + 1] = sqq;
+      red[4 * u + 2] = sdd;
+      red[4 * u + 3] = sraw;
+      scs[u] = sc;
+    }
+    // lane l holds statistic (l >> 1) & 3 of row l >> 3; its bound, then the row's four in lane 8 u
+    const float tot = warp_reduce_scatter<16>(red, lane);
+    const float nb = norm_bound(tot, d);
+    const float nb1 = __shfl_down_sync(0xffffffffu, nb, 2), nb2 = __shfl_down_sync(0xffffffffu, nb, 4);
+    const float nb3 = __shfl_down_sync(0xffffffffu, nb, 6);
+    const float t1 = __shfl_down_sync(0xffffffffu, tot, 2), t3 = __shfl_down_sync(0xffffffffu, tot, 6);
+    const int u = lane >> 3;
+    const int64_t i = i0 + u;
+    if ((lane & 7) == 0 && i < n) {
+      const float sc = u == 0 ? scs[0] : (u == 1 ? scs[1] : (u == 2 ? scs[2] : scs[3]));
+      if (!isfinite(tot) || !isfinite(t1) || !isfinite(t3)) ctl->nonfinite = 1;
+      xs[i] = make_float4(sc, nb1, centred_resid(nb, nb2, mu), centred_norm(nb, mu));
+      if (xnorm) xnorm[i] = nb3;
+      if (FP8 && Xh) store_row_slice(Xh + 2 * i, sc);
     }
   }
 }
