@@ -193,10 +193,11 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
 // statistics the later E4M3 steps use (their codes are written by the reduce
 // stage in sorted order).
 template <int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, V <= 4 ? 4 : 2)
 quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uint8_t* __restrict__ Xq,
                     float4* __restrict__ xs16, float4* __restrict__ xs8, const float* __restrict__ mu,
                     float* __restrict__ xnorm, Ctl* ctl) {
+  static_assert(kQU == 4, "four rows of eight (six used) statistics: one 32-value reduce-scatter");
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -205,10 +206,12 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
     float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
+    // row u's lane partials at 8 u + s: sum v^2, BF16 sum q^2 and (q - v)^2, E4M3 the same, sum x^2
+    float red[8 * kQU];
+    float scs[kQU];
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
       const int64_t i = i0 + u;
-      if (i >= n) break;
       float amax = 0.f;
 #pragma unroll
       for (int v = 0; v < V; ++v)
@@ -216,36 +219,53 @@ quant_x_dual_kernel(const float* __restrict__ X, int64_t n, int d, int Kp16, uin
       const float sc8 = pow2_scale(warp_max(amax));
       const float inv8 = pow2_inv(sc8);
       float sxx = 0.f, sqq16 = 0.f, sdd16 = 0.f, sqq8 = 0.f, sdd8 = 0.f, sraw = 0.f;
-      uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
+      if (i < n) {
+        uint8_t* row = Xq + i * (int64_t)Kp16 * 2;
 #pragma unroll
-      for (int sl = 0; sl < V; ++sl) {
-        const int t = sl * 32 + lane;
-        if (t >= Kp16) break;
-        const float xt = xv[u][sl];
-        sraw = fmaf(xt, xt, sraw);
-        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-        const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
-        uint8_t dummy;
-        const float q8 = quantise<1>(v, sc8, inv8, &dummy);
-        sxx = fmaf(v, v, sxx);
-        sqq16 = fmaf(q16, q16, sqq16);
-        sdd16 = fmaf(q16 - v, q16 - v, sdd16);
-        sqq8 = fmaf(q8, q8, sqq8);
-        sdd8 = fmaf(q8 - v, q8 - v, sdd8);
+        for (int sl = 0; sl < V; ++sl) {
+          const int t = sl * 32 + lane;
+          if (t >= Kp16) break;
+          const float xt = xv[u][sl];
+          sraw = fmaf(xt, xt, sraw);
+          const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+          const float q16 = quantise<0>(v, 1.f, 1.f, row + t * 2);
+          uint8_t dummy;
+          const float q8 = quantise<1>(v, sc8, inv8, &dummy);
+          sxx = fmaf(v, v, sxx);
+          sqq16 = fmaf(q16, q16, sqq16);
+          sdd16 = fmaf(q16 - v, q16 - v, sdd16);
+          sqq8 = fmaf(q8, q8, sqq8);
+          sdd8 = fmaf(q8 - v, q8 - v, sdd8);
+        }
       }
-      sxx = warp_sum(sxx);
-      sqq16 = warp_sum(sqq16);
-      sdd16 = warp_sum(sdd16);
-      sqq8 = warp_sum(sqq8);
-      sdd8 = warp_sum(sdd8);
-      sraw = warp_sum(sraw);
-      if (lane == 0) {
-        if (!isfinite(sxx) || !isfinite(sqq16) || !isfinite(sqq8) || !isfinite(sraw)) ctl->nonfinite = 1;
-        const float nbv = norm_bound(sxx, d), xn = centred_norm(nbv, mu);
-        xs16[i] = make_float4(1.f, norm_bound(sqq16, d), centred_resid(nbv, norm_bound(sdd16, d), mu), xn);
-        xs8[i] = make_float4(sc8, norm_bound(sqq8, d), centred_resid(nbv, norm_bound(sdd8, d), mu), xn);
-        if (xnorm) xnorm[i] = norm_bound(sraw, d);
-      }
+      red[8 * u] = sxx;
+      red[8 * u + 1] = sqq16;
+      red[8 * u + 2] = sdd16;
+      red[8 * u + 3] = sqq8;
+      red[8 * u + 4] = sdd8;
+      red[8 * u + 5] = sraw;
+      red[8 * u + 6] = 0.f;
+      red[8 * u + 7] = 0.f;
+      scs[u] = sc8;
+    }
+    // lane l holds statistic l & 7 of row l >> 3; its bound, then the row's six in lane 8 u
+    const float tot = warp_reduce_scatter<32>(red, lane);
+    const float nb = norm_bound(tot, d);
+    float nbs[6], tots[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      nbs[s] = __shfl_down_sync(0xffffffffu, nb, s);
+      tots[s] = __shfl_down_sync(0xffffffffu, tot, s);
+    }
+    const int u = lane >> 3;
+    const int64_t i = i0 + u;
+    if ((lane & 7) == 0 && i < n) {
+      const float sc8 = u == 0 ? scs[0] : (u == 1 ? scs[1] : (u == 2 ? scs[2] : scs[3]));
+      if (!isfinite(tots[0]) || !isfinite(tots[1]) || !isfinite(tots[3]) || !isfinite(tots[5])) ctl->nonfinite = 1;
+      const float nbv = nbs[0], xn = centred_norm(nbv, mu);
+      xs16[i] = make_float4(1.f, nbs[1], centred_resid(nbv, nbs[2], mu), xn);
+      xs8[i] = make_float4(sc8, nbs[3], centred_resid(nbv, nbs[4], mu), xn);
+      if (xnorm) xnorm[i] = nbs[5];
     }
   }
 }
