@@ -80,9 +80,10 @@ __device__ __forceinline__ void bq_rows(const BWork& W, int q, int64_t p, int64_
         xv[u][v] = (u < rows && t < d) ? x[t] : 0.f;
       }
     }
+    float red[4 * U];  // row u's lane partials at 4 u + s: sum x^2, sum x~^2, sum (x~ - x)^2, 0
+    float scs[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (u >= rows) break;
       float amax = 0.f;
       if (FP8) {
 #pragma unroll
@@ -91,25 +92,36 @@ __device__ __forceinline__ void bq_rows(const BWork& W, int q, int64_t p, int64_
       const float sc = FP8 ? pow2_scale(warp_max(amax)) : 1.f;
       const float inv = FP8 ? pow2_inv(sc) : 1.f;
       float sxx = 0.f, sqq = 0.f, sdd = 0.f;
-      uint8_t* row = W.Xq + I.xq_off + (i0 + u) * (int64_t)Kp * ESZ;
+      if (u < rows) {
+        uint8_t* row = W.Xq + I.xq_off + (i0 + u) * (int64_t)Kp * ESZ;
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int t = v * 32 + lane;
-        if (t < Kp) {
-          const float xt = xv[u][v];
-          const float vq = quantise<FP8>(xt, sc, inv, row + t * ESZ);
-          sxx = fmaf(xt, xt, sxx);
-          sqq = fmaf(vq, vq, sqq);
-          sdd = fmaf(vq - xt, vq - xt, sdd);
+        for (int v = 0; v < V; ++v) {
+          const int t = v * 32 + lane;
+          if (t < Kp) {
+            const float xt = xv[u][v];
+            const float vq = quantise<FP8>(xt, sc, inv, row + t * ESZ);
+            sxx = fmaf(xt, xt, sxx);
+            sqq = fmaf(vq, vq, sqq);
+            sdd = fmaf(vq - xt, vq - xt, sdd);
+          }
         }
       }
-      sxx = warp_sum(sxx);
-      sqq = warp_sum(sqq);
-      sdd = warp_sum(sdd);
-      if (lane == 0) {
-        if (!isfinite(sxx) || !isfinite(sqq)) W.ctls[q].nonfinite = 1;
-        W.xs[p + u] = make_float4(sc, norm_bound(sqq, d), norm_bound(sdd, d), norm_bound(sxx, d));
-      }
+      red[4 * u] = sxx;
+      red[4 * u + 1] = sqq;
+      red[4 * u + 2] = sdd;
+      red[4 * u + 3] = 0.f;
+      scs[u] = sc;
+    }
+    // lane l holds statistic (l >> 1) & 3 of row l >> 3 (warp_reduce_scatter); the row's lane 8 u stores
+    const float tot = warp_reduce_scatter<16>(red, lane);
+    const float nb = norm_bound(tot, d);
+    const float nb1 = __shfl_down_sync(0xffffffffu, nb, 2), nb2 = __shfl_down_sync(0xffffffffu, nb, 4);
+    const float t1 = __shfl_down_sync(0xffffffffu, tot, 2);
+    const int u = lane >> 3;
+    if ((lane & 7) == 0 && u < rows) {
+      const float sc = u == 0 ? scs[0] : (u == 1 ? scs[1] : (u == 2 ? scs[2] : scs[3]));
+      if (!isfinite(tot) || !isfinite(t1)) W.ctls[q].nonfinite = 1;
+      W.xs[p + u] = make_float4(sc, nb1, nb2, nb);
     }
   }
 }

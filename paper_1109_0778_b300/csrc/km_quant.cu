@@ -43,28 +43,6 @@ __device__ __forceinline__ void load_rows(const float* __restrict__ X, int64_t n
   }
 }
 
-// Reduce-scatter over the warp: v[0..NV) (NV = 16 or 32) summed over the 32
-// lanes; lane l returns the total of value l >> 1 (NV = 16; lanes l and l ^ 1
-// hold the same total) or l (NV = 32). Each level sends half of the remaining
-// values to the partner lane and keeps the other half, so NV values cost NV - 1
-// shuffles instead of 5 NV. (Any summation tree gives the norm bounds their
-// guarantee: a sum of m non-negative terms has relative error < gamma_m.)
-template <int NV>
-__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
-#pragma unroll
-  for (int o = 16, c = NV; c > 1; o >>= 1, c >>= 1) {
-    const bool up = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < c / 2; ++i) {
-      const float send = up ? v[i] : v[i + c / 2];
-      const float keep = up ? v[i + c / 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-  }
-  if (NV == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return v[0];
-}
-
 // Xh (E4M3 with -h_j folded into the contraction; null otherwise): row i's
 // [1/s_i, 1/s_i, 1/s_i, 0, ...] slice (store_row_slice).
 // mu (null: no centring): the codes and statistics are those of the centred
@@ -142,9 +120,10 @@ quant_x_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* _
 // in [Kp, 2 Kp). Statistics: (1, ||hi|| + ||lo||, ||v - hi - lo||, ||v||),
 // norms rounded up.
 template <int V>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, V <= 2 ? 4 : (V <= 4 ? 3 : 2))
 quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint8_t* __restrict__ Xq,
                      float4* __restrict__ xs, const float* __restrict__ mu, float* __restrict__ xnorm, Ctl* ctl) {
+  static_assert(kQU == 4, "four rows of eight (five used) statistics: one 32-value reduce-scatter");
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -153,38 +132,52 @@ quant_x_split_kernel(const float* __restrict__ X, int64_t n, int d, int Kp, uint
   for (int64_t i0 = warp * kQU; i0 < n; i0 += nwarps * kQU) {
     float xv[kQU][V];
     load_rows(X, n, d, i0, lane, xv);
+    float red[8 * kQU];  // row u's lane partials at 8 u + s: sum v^2, hi^2, lo^2, (v - hi - lo)^2, x^2
 #pragma unroll
     for (int u = 0; u < kQU; ++u) {
       const int64_t i = i0 + u;
-      if (i >= n) break;
       float sxx = 0.f, shh = 0.f, sll = 0.f, sdd = 0.f, sraw = 0.f;
-      __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
+      if (i < n) {
+        __nv_bfloat16* row = reinterpret_cast<__nv_bfloat16*>(Xq) + i * 2 * (int64_t)Kp;
 #pragma unroll
-      for (int sl = 0; sl < V; ++sl) {
-        const int t = sl * 32 + lane;
-        if (t >= Kp) break;
-        const float xt = xv[u][sl];
-        const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
-        float hi, lo;
-        const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
-        sxx = fmaf(v, v, sxx);
-        shh = fmaf(hi, hi, shh);
-        sll = fmaf(lo, lo, sll);
-        sdd = fmaf(r, r, sdd);
-        sraw = fmaf(xt, xt, sraw);
+        for (int sl = 0; sl < V; ++sl) {
+          const int t = sl * 32 + lane;
+          if (t >= Kp) break;
+          const float xt = xv[u][sl];
+          const float v = t < d ? __fsub_rn(xt, mus[t]) : 0.f;
+          float hi, lo;
+          const float r = split_bf16(v, row + t, row + Kp + t, hi, lo);
+          sxx = fmaf(v, v, sxx);
+          shh = fmaf(hi, hi, shh);
+          sll = fmaf(lo, lo, sll);
+          sdd = fmaf(r, r, sdd);
+          sraw = fmaf(xt, xt, sraw);
+        }
       }
-      sxx = warp_sum(sxx);
-      shh = warp_sum(shh);
-      sll = warp_sum(sll);
-      sdd = warp_sum(sdd);
-      sraw = warp_sum(sraw);
-      if (lane == 0) {
-        if (!isfinite(sxx) || !isfinite(shh) || !isfinite(sraw)) ctl->nonfinite = 1;
-        const float nbv = norm_bound(sxx, d);
-        xs[i] = make_float4(1.f, __fadd_ru(norm_bound(shh, d), norm_bound(sll, d)),
-                            centred_resid(nbv, norm_bound(sdd, d), mu), centred_norm(nbv, mu));
-        if (xnorm) xnorm[i] = norm_bound(sraw, d);
-      }
+      red[8 * u] = sxx;
+      red[8 * u + 1] = shh;
+      red[8 * u + 2] = sll;
+      red[8 * u + 3] = sdd;
+      red[8 * u + 4] = sraw;
+      red[8 * u + 5] = 0.f;
+      red[8 * u + 6] = 0.f;
+      red[8 * u + 7] = 0.f;
+    }
+    // lane l holds statistic l & 7 of row l >> 3; its bound, then the row's five in lane 8 u
+    const float tot = warp_reduce_scatter<32>(red, lane);
+    const float nb = norm_bound(tot, d);
+    float nbs[5], tots[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      nbs[s] = __shfl_down_sync(0xffffffffu, nb, s);
+      tots[s] = __shfl_down_sync(0xffffffffu, tot, s);
+    }
+    const int64_t i = i0 + (lane >> 3);
+    if ((lane & 7) == 0 && i < n) {
+      if (!isfinite(tots[0]) || !isfinite(tots[1]) || !isfinite(tots[4])) ctl->nonfinite = 1;
+      const float nbv = nbs[0];
+      xs[i] = make_float4(1.f, __fadd_ru(nbs[1], nbs[2]), centred_resid(nbv, nbs[3], mu), centred_norm(nbv, mu));
+      if (xnorm) xnorm[i] = nbs[4];
     }
   }
 }

@@ -98,6 +98,28 @@ static __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// Reduce-scatter over the warp: v[0..NV) (NV = 16 or 32) summed over the 32
+// lanes; lane l returns the total of value l >> 1 (NV = 16; lanes l and l ^ 1
+// hold the same total) or l (NV = 32). Each level sends half of the remaining
+// values to the partner lane and keeps the other half, so NV values cost NV - 1
+// shuffles instead of 5 NV. (Any summation tree gives the norm bounds their
+// guarantee: a sum of m non-negative terms has relative error < gamma_m.)
+template <int NV>
+static __device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV], int lane) {
+#pragma unroll
+  for (int o = 16, c = NV; c > 1; o >>= 1, c >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < c / 2; ++i) {
+      const float send = up ? v[i] : v[i + c / 2];
+      const float keep = up ? v[i + c / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  if (NV == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0];
+}
+
 // sqrt of an FP32 sum of m non-negative terms, rounded up and widened to cover
 // the sum's rounding (relative error < gamma_m).
 static __device__ __forceinline__ float norm_bound(float sumsq, int m) {
