@@ -4,11 +4,12 @@
 //   D_j = sum_t (x_t - c_jt)^2
 // (each difference and square rounded once: <= 3u per term; the lanes' sums
 // merged across the warp with TwoSum: <= u). Within a lane the terms are added
-// with Kahan compensation (<= 2u: D_j within about 5u D_j of the exact value,
-// u = 2^-24) or, for the short lists of d <= 128 (at most 16 terms per lane),
-// by a pairwise tree of depth <= 4 (<= 4u: within 8u D_j). Either way two
-// distances whose relative gap is at least 1e-6 (> 16u = 9.5e-7) are always
-// ordered correctly; equal computed distances go to the lower index.
+// with Kahan compensation (the all-centroid path: <= 2u, D_j within about 5u
+// D_j of the exact value, u = 2^-24) or, for the short lists, by pairwise trees
+// of at most 16 terms (depth <= 4: <= 4u), two of them joined exactly by TwoSum
+// when d > 128: within 8u D_j. Either way two distances whose relative gap is
+// at least 1e-6 (> 16u = 9.5e-7) are always ordered correctly; equal computed
+// distances go to the lower index.
 //
 // When the assignment stage could not narrow the candidates (more than seven
 // within its margin, or an FP32 SIMT flag), the re-check first screens all k
@@ -59,10 +60,10 @@ __device__ __forceinline__ float warp_sqdist(const float (&xv)[V], const float* 
 // in registers; the candidates are taken NQ at a time (four, or two when the
 // slices are long), all their slices loaded before any arithmetic, so a short
 // list costs about one round trip to memory per NQ candidates. For every coordinate the difference and its
-// square are rounded once each; a lane's 4F squares are added by a pairwise
-// tree when F <= 4 (depth <= 4: error ~8u of the sum in all), else in a Kahan
-// pair per candidate (the lane's coordinates in order: ~5u, the accuracy of
-// warp_sqdist), and the G lane sums are combined with TwoSum. ncw = the largest nc
+// square are rounded once each; a lane's 4F squares are added by pairwise
+// trees of at most 16 (depth <= 4), two of them joined exactly by TwoSum when
+// F > 4 (error ~8u of the sum in all), and the G lane sums are combined with
+// TwoSum. ncw = the largest nc
 // over the warp (the loop bound, so that every lane takes part in the
 // shuffles). Equal distances go to the lower index. Every lane of the group
 // returns the same index.
@@ -96,34 +97,29 @@ __device__ __forceinline__ int group_settle(const float* __restrict__ x, const f
     }
 #pragma unroll
     for (int u = 0; u < NQ; ++u) {
-      float sq = 0.f, cp = 0.f;
-      if constexpr (F <= 4) {
-        // at most 16 squares per lane: a pairwise tree of depth <= 4 (error <= 4u of the lane sum)
-        float part[F];
+      // the lane's squares: one pairwise tree of depth <= 4 over f < 4 (at most 16
+      // squares, error <= 4u of that part) and, for F > 4, a second over f >= 4,
+      // the two added exactly by TwoSum; the lane's sum as (hi, lo)
+      float part[F];
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-          const float a = __fsub_rn(xv[f].x, cv[u][f].x), b = __fsub_rn(xv[f].y, cv[u][f].y);
-          const float c = __fsub_rn(xv[f].z, cv[u][f].z), e = __fsub_rn(xv[f].w, cv[u][f].w);
-          part[f] = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fadd_rn(__fmul_rn(c, c), __fmul_rn(e, e)));
-        }
-        if constexpr (F == 1) sq = part[0];
-        else if constexpr (F == 2) sq = __fadd_rn(part[0], part[1]);
-        else if constexpr (F == 3) sq = __fadd_rn(__fadd_rn(part[0], part[1]), part[2]);
-        else sq = __fadd_rn(__fadd_rn(part[0], part[1]), __fadd_rn(part[2], part[3]));
-      } else {
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-          float df = __fsub_rn(xv[f].x, cv[u][f].x);
-          kahan_add(sq, cp, __fmul_rn(df, df));
-          df = __fsub_rn(xv[f].y, cv[u][f].y);
-          kahan_add(sq, cp, __fmul_rn(df, df));
-          df = __fsub_rn(xv[f].z, cv[u][f].z);
-          kahan_add(sq, cp, __fmul_rn(df, df));
-          df = __fsub_rn(xv[f].w, cv[u][f].w);
-          kahan_add(sq, cp, __fmul_rn(df, df));
-        }
+      for (int f = 0; f < F; ++f) {
+        const float a = __fsub_rn(xv[f].x, cv[u][f].x), b = __fsub_rn(xv[f].y, cv[u][f].y);
+        const float c = __fsub_rn(xv[f].z, cv[u][f].z), e = __fsub_rn(xv[f].w, cv[u][f].w);
+        part[f] = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fadd_rn(__fmul_rn(c, c), __fmul_rn(e, e)));
       }
-      float hi = sq, lo = -cp;  // the lane's pair s - c as (hi, lo)
+      auto tree = [&](int f0, int m) {  // m = 1 .. 4 partials from f0
+        if (m == 1) return part[f0];
+        if (m == 2) return __fadd_rn(part[f0], part[f0 + 1]);
+        if (m == 3) return __fadd_rn(__fadd_rn(part[f0], part[f0 + 1]), part[f0 + 2]);
+        return __fadd_rn(__fadd_rn(part[f0], part[f0 + 1]), __fadd_rn(part[f0 + 2], part[f0 + 3]));
+      };
+      float hi, lo = 0.f;
+      if constexpr (F <= 4) {
+        hi = tree(0, F);
+      } else {
+        static_assert(F <= 8, "at most two trees of 16 squares per lane");
+        two_sum(tree(0, 4), tree(4, F - 4), hi, lo);
+      }
 #pragma unroll
       for (int o = G >> 1; o; o >>= 1) {
         const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
